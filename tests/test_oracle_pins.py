@@ -1,0 +1,405 @@
+"""Pins of the CPU oracle against facts fixed outside it (no GPU).
+
+Each test ties one oracle function to something independent of its own code: the
+mathematical definition re-evaluated by brute force, a closed form, an invariant, or a
+textbook library routine (scipy's spherical harmonics and rotations, numpy's stable sort).
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.special as sps
+from scipy.spatial.transform import Rotation
+
+import oracle
+import synth
+
+CFG = oracle.make_config()
+
+
+# ------------------------------------------------------------------------------------------
+# exp2r: reproducible binary32 exp2
+# ------------------------------------------------------------------------------------------
+
+def test_exp2r_accuracy_against_exp2():
+    y = np.linspace(-125.0, 125.0, 200_001, dtype=np.float32)
+    got = oracle.exp2r(y).astype(np.float64)
+    ref = np.exp2(y.astype(np.float64))
+    rel = np.abs(got - ref) / ref
+    # degree-6 Taylor remainder (ln2/2)^7/7! = 1.2e-7 plus a few binary32 roundings
+    assert rel.max() < 4e-7
+
+
+def test_exp2r_exact_on_integers_and_monotone():
+    ints = np.arange(-125, 126, dtype=np.float32)
+    assert np.array_equal(oracle.exp2r(ints), np.exp2(ints.astype(np.float64)).astype(np.float32))
+    y = np.linspace(-9.0, 0.5, 400_001, dtype=np.float32)
+    g = oracle.exp2r(y)
+    assert np.all(np.diff(g) >= 0)
+
+
+def test_exp2r_clamps_nan_and_range():
+    out = oracle.exp2r(np.array([np.nan, -1e9, 1e9], np.float32))
+    assert out[0] == np.float32(2.0 ** -125) and out[1] == np.float32(2.0 ** -125)
+    assert out[2] == np.float32(2.0 ** 125)
+
+
+# ------------------------------------------------------------------------------------------
+# activation: covariance and opacity
+# ------------------------------------------------------------------------------------------
+
+def _scene(means, log_scales, quats, logits, sh=None):
+    n = means.shape[1]
+    if sh is None:
+        sh = np.zeros((16, 3, n), np.float32)
+    return synth.Scene(means.astype(np.float32), log_scales.astype(np.float32),
+                       quats.astype(np.float32), logits.astype(np.float32), sh.astype(np.float32))
+
+
+def test_activate_against_scipy_rotation():
+    rng = np.random.default_rng(3)
+    n = 500
+    q = rng.normal(size=(4, n))
+    ls = rng.normal(-2.0, 1.0, size=(3, n))
+    sc = _scene(np.zeros((3, n)), ls, q, rng.normal(0, 2, size=n))
+    cov, op = oracle.activate(sc)
+    R = Rotation.from_quat(np.stack([q[1], q[2], q[3], q[0]], axis=1)).as_matrix()  # scalar last
+    s2 = np.exp(2.0 * ls.T)
+    ref = np.einsum("nij,nj,nkj->nik", R, s2, R)
+    got = np.stack([[cov[0], cov[1], cov[2]], [cov[1], cov[3], cov[4]], [cov[2], cov[4], cov[5]]]).transpose(2, 0, 1)
+    scale = s2.max(axis=1)[:, None, None]
+    assert np.max(np.abs(got - ref) / scale) < 2e-6
+    assert np.max(np.abs(op - sps.expit(sc.opacity_logits.astype(np.float64)))) < 2e-7
+
+
+def test_activate_identity_quaternion_and_zero_logit():
+    ls = np.array([[-1.0], [-2.0], [-3.0]])
+    sc = _scene(np.zeros((3, 1)), ls, np.array([[2.0], [0.0], [0.0], [0.0]]), np.zeros(1))
+    cov, op = oracle.activate(sc)
+    np.testing.assert_allclose(cov[[0, 3, 5], 0], np.exp(2 * ls[:, 0]), rtol=1e-6)
+    assert cov[1, 0] == 0 and cov[2, 0] == 0 and cov[4, 0] == 0
+    assert op[0] == np.float32(0.5)
+
+
+# ------------------------------------------------------------------------------------------
+# projection (EWA), SH colour, tile rectangle
+# ------------------------------------------------------------------------------------------
+
+def test_sh_basis_against_scipy():
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        theta, phi = math.acos(d[2]), math.atan2(d[1], d[0])
+        Y = oracle.sh_basis(d)
+        for l in range(4):
+            for m in range(-l, l + 1):
+                z = sps.sph_harm_y(l, abs(m), theta, phi)  # complex, Condon-Shortley phase included
+                ref = z.real if m == 0 else math.sqrt(2) * (z.real if m > 0 else z.imag)
+                assert abs(Y[l * (l + 1) + m] - ref) < 1e-12, (l, m)
+    # index order of the paper, (l, m) -> l(l+1)+m+1: Y_1 constant, Y_2..Y_4 = -y, z, -x (scaled)
+    Y = oracle.sh_basis([0.0, 0.0, 1.0])
+    assert abs(Y[0] - 0.5 / math.sqrt(math.pi)) < 1e-15 and abs(Y[2] - math.sqrt(3 / (4 * math.pi))) < 1e-15
+
+
+def test_axis_aligned_splat_on_optical_axis():
+    cam = synth.look_at_camera((0.0, 0.0, -3.0), 128, 96)
+    sigma = 0.05
+    sc = _scene(np.zeros((3, 1)), np.full((3, 1), math.log(sigma)), np.array([[1.0], [0], [0], [0]]), np.zeros(1))
+    cov, op = oracle.activate(sc)
+    pr = oracle.project(sc, cov, cam, CFG)
+    f = cam.fy
+    expect = f * f * sigma * sigma / 9.0 + 0.3
+    assert pr["cov2d"][0, 0] == pytest.approx(expect, rel=2e-6)
+    assert pr["cov2d"][2, 0] == pytest.approx(expect, rel=2e-6)
+    assert abs(pr["cov2d"][1, 0]) < 1e-6 * expect
+    assert pr["mean2d"][0, 0] == pytest.approx(64.0, abs=1e-5) and pr["mean2d"][1, 0] == pytest.approx(48.0, abs=1e-5)
+    assert pr["conic"][0, 0] == pytest.approx(1.0 / expect, rel=4e-6)
+    assert pr["radius"][0] == math.ceil(3.0 * math.sqrt(expect) - 1e-6) or pr["radius"][0] == math.ceil(3 * math.sqrt(expect))
+    assert pr["depth"][0] == np.float32(3.0)
+
+
+def _numeric_jacobian(cam, p):
+    """d(pixel)/d(world point) by central differences of the pinhole map (binary64)."""
+    R = cam.w2c.reshape(3, 4)[:, :3].astype(np.float64)
+    t = cam.w2c.reshape(3, 4)[:, 3].astype(np.float64)
+
+    def proj(x):
+        c = R @ x + t
+        return np.array([cam.fx * c[0] / c[2] + cam.cx, cam.fy * c[1] / c[2] + cam.cy])
+
+    J = np.zeros((2, 3))
+    h = 1e-6
+    for j in range(3):
+        e = np.zeros(3)
+        e[j] = h
+        J[:, j] = (proj(p + e) - proj(p - e)) / (2 * h)
+    return proj(p), J
+
+
+def test_projection_is_linearised_pinhole(tiny):
+    sc, cam = tiny.scene, tiny.cameras[0]
+    cov, op = oracle.activate(sc)
+    pr = oracle.project(sc, cov, cam, CFG)
+    vis = np.nonzero(pr["touched"])[0]
+    assert vis.size > 500
+    checked = 0
+    for k in vis[:300]:
+        mu = sc.means[:, k].astype(np.float64)
+        m2, J = _numeric_jacobian(cam, mu)
+        # only splats inside the Jacobian clamp region follow the plain linearisation
+        c = cam.w2c.reshape(3, 4)[:, :3] @ mu + cam.w2c.reshape(3, 4)[:, 3]
+        if abs(c[0] / c[2]) > 1.3 * 0.5 * cam.width / cam.fx or abs(c[1] / c[2]) > 1.3 * 0.5 * cam.height / cam.fy:
+            continue
+        S = np.array([[cov[0, k], cov[1, k], cov[2, k]], [cov[1, k], cov[3, k], cov[4, k]], [cov[2, k], cov[4, k], cov[5, k]]], np.float64)
+        ref = J @ S @ J.T + 0.3 * np.eye(2)
+        got = np.array([[pr["cov2d"][0, k], pr["cov2d"][1, k]], [pr["cov2d"][1, k], pr["cov2d"][2, k]]])
+        assert np.max(np.abs(got - ref)) < 1e-4 * np.max(np.abs(ref)) + 1e-6
+        assert np.max(np.abs(pr["mean2d"][:, k] - m2)) < 1e-4
+        checked += 1
+    assert checked > 200
+
+
+def test_colour_dc_only():
+    cam = synth.look_at_camera((0.0, 0.0, -3.0), 64, 64)
+    sh = np.zeros((16, 3, 1), np.float32)
+    sh[0, :, 0] = [1.0, -0.2, -3.0]
+    sc = _scene(np.zeros((3, 1)), np.full((3, 1), -3.0), np.array([[1.0], [0], [0], [0]]), np.zeros(1), sh)
+    cov, op = oracle.activate(sc)
+    pr = oracle.project(sc, cov, cam, CFG)
+    y0 = 0.5 / math.sqrt(math.pi)
+    np.testing.assert_allclose(pr["rgb"][:, 0], [max(0, v * y0 + 0.5) for v in sh[0, :, 0].astype(np.float64)], rtol=1e-12)
+
+
+def test_rect_encloses_square_and_clamps(tiny):
+    sc, cam = tiny.scene, tiny.cameras[0]
+    cov, op = oracle.activate(sc)
+    pr = oracle.project(sc, cov, cam, CFG)
+    tx, ty = oracle.tiles_of(cam, CFG)
+    for k in np.nonzero(pr["touched"])[0][:400]:
+        mx, my, r = pr["mean2d"][0, k], pr["mean2d"][1, k], pr["radius"][k]
+        want = [(x, y) for y in range(ty) for x in range(tx)
+                if x * 16 <= mx + r and (x + 1) * 16 > mx - r and y * 16 <= my + r and (y + 1) * 16 > my - r]
+        x0, y0, x1, y1 = pr["rect"][:, k]
+        got = [(x, y) for y in range(y0, y1) for x in range(x0, x1)]
+        assert sorted(got) == sorted(want)
+        assert pr["touched"][k] == len(got)
+
+
+def test_cull_behind_and_near():
+    cam = synth.look_at_camera((0.0, 0.0, -3.0), 64, 64)
+    means = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 0.0], [-3.5, -2.9, 0.0]])  # behind, inside near, visible
+    sc = _scene(means, np.full((3, 3), -3.0), np.tile([[1.0], [0], [0], [0]], (1, 3)), np.zeros(3))
+    cov, op = oracle.activate(sc)
+    pr = oracle.project(sc, cov, cam, CFG)
+    assert list(pr["touched"][:2]) == [0, 0] and pr["touched"][2] > 0
+
+
+# ------------------------------------------------------------------------------------------
+# binning and sort
+# ------------------------------------------------------------------------------------------
+
+def test_bin_sort_against_numpy_stable_sort(tiny):
+    sc, cam = tiny.scene, tiny.cameras[0]
+    for tw, th in [(16, 16), (8, 32), (32, 8)]:
+        cfg = oracle.make_config(tile_w=tw, tile_h=th)
+        v = oracle.prepare_view(sc, cam, cfg)
+        tx, ty = oracle.tiles_of(cam, cfg)
+        keys, vals = [], []
+        for k in range(sc.n):
+            x0, y0, x1, y1 = v["rect"][:, k]
+            dbits = int(np.float32(v["depth"][k]).view(np.uint32))
+            for y in range(y0, y1):
+                for x in range(x0, x1):
+                    keys.append(((y * tx + x) << 32) | dbits)
+                    vals.append(k)
+        keys = np.array(keys, np.uint64)
+        order = np.argsort(keys, kind="stable")
+        assert np.array_equal(v["keys"], keys[order])
+        assert np.array_equal(v["vals"], np.array(vals, np.uint32)[order])
+        assert np.array_equal(v["emit"], order.astype(np.uint32))
+        tiles = (keys[order] >> np.uint64(32)).astype(np.int64)
+        for t in range(tx * ty):
+            idx = np.nonzero(tiles == t)[0]
+            if idx.size:
+                assert tuple(v["ranges"][t]) == (idx[0], idx[-1] + 1)
+            else:
+                assert v["ranges"][t][0] == v["ranges"][t][1]
+
+
+def test_depth_bits_order_matches_numeric_order():
+    d = np.sort(np.random.default_rng(1).uniform(0.2, 1e4, 100_000).astype(np.float32))
+    assert np.all(np.diff(d.view(np.uint32).astype(np.int64)) >= 0)
+
+
+# ------------------------------------------------------------------------------------------
+# compositing and removal effect on hand-built splats (closed forms)
+# ------------------------------------------------------------------------------------------
+
+def _flat_view(opac, rgb, depth, w=16, h=16):
+    """Splats whose exponent is 0 everywhere (alpha = opacity exactly), all in one tile."""
+    n = len(opac)
+    v = dict(
+        mean2d=np.zeros((2, n), np.float32), qcoef=np.zeros((3, n), np.float32),
+        opacity=np.array(opac, np.float32), rgb=np.ascontiguousarray(np.array(rgb, np.float64).T),
+        depth=np.array(depth, np.float32),
+    )
+    order = np.argsort(np.array(depth, np.float32), kind="stable")
+    vals = order.astype(np.uint32)
+    ranges = np.array([[0, n]], np.uint32)
+    cam = synth.Camera(np.zeros(12, np.float32), 1.0, 1.0, 0.0, 0.0, w, h)
+    return v, vals, ranges, cam
+
+
+def test_one_splat_closed_form():
+    c0 = np.array([0.7, 0.2, 0.4])
+    v, vals, ranges, cam = _flat_view([0.6], [c0], [1.0])
+    cfg = oracle.make_config(t_min=0.0)
+    img, t32, t64, nl = oracle.render(v, vals, ranges, cam, cfg)
+    a = float(np.float32(0.6))
+    np.testing.assert_allclose(img[:, 0, 0], a * c0, rtol=1e-15)
+    assert t64[0, 0] == pytest.approx(1 - a, rel=1e-15) and nl[0, 0] == 1
+    ct = np.array([0.1, 0.5, 0.3], np.float32)
+    tgt = np.broadcast_to(ct[:, None, None], (3, 16, 16))
+    d, imp = oracle.removal_effect(v, vals, ranges, cam, cfg, tgt)
+    C0 = a * c0
+    per_pix = np.sum(C0 * (C0 - 2 * (C0 - ct.astype(np.float64))))  # PD = -alpha c0
+    assert d[0] == pytest.approx(256 * per_pix, rel=1e-12)
+    assert imp[0] == pytest.approx(256 * a, rel=1e-12)
+
+
+def test_two_splat_closed_form_front_and_back():
+    c0, c1 = np.array([0.9, 0.1, 0.3]), np.array([0.2, 0.8, 0.5])
+    v, vals, ranges, cam = _flat_view([0.99, 0.7], [c0, c1], [1.0, 2.0])
+    cfg = oracle.make_config(t_min=0.0, alpha_max=0.99)
+    a0, a1 = float(np.float32(0.99)), float(np.float32(0.7))
+    img, *_ = oracle.render(v, vals, ranges, cam, cfg)
+    C = a0 * c0 + (1 - a0) * a1 * c1
+    np.testing.assert_allclose(img[:, 3, 5], C, rtol=1e-14)
+    tgt = np.zeros((3, 16, 16), np.float32)
+    d, imp = oracle.removal_effect(v, vals, ranges, cam, cfg, tgt)
+    pd_front = a0 * (a1 * c1 - c0)
+    pd_back = -(1 - a0) * a1 * c1  # the 1/(1 - alpha) renormalisation at alpha_0 = 0.99
+    dse = lambda pd: np.sum(pd * pd + 2 * pd * C)
+    assert d[0] == pytest.approx(256 * dse(pd_front), rel=1e-11)
+    assert d[1] == pytest.approx(256 * dse(pd_back), rel=1e-9)
+    assert imp[0] == pytest.approx(256 * a0, rel=1e-12) and imp[1] == pytest.approx(256 * (1 - a0) * a1, rel=1e-9)
+
+
+def test_alpha_clamp_and_threshold_and_termination():
+    # opacity above alpha_max is clamped; below alpha_min never composites; T_min stops
+    v, vals, ranges, cam = _flat_view([1.0, 0.003, 0.5], [[1, 1, 1], [1, 0, 0], [0, 1, 0]], [1.0, 2.0, 3.0])
+    cfg = oracle.make_config(t_min=0.0)
+    img, t32, t64, nl = oracle.render(v, vals, ranges, cam, cfg)
+    a0 = float(np.float32(0.99))
+    a2 = float(np.float32(0.5))
+    np.testing.assert_allclose(img[:, 0, 0], a0 * np.ones(3) + (1 - a0) * a2 * np.array([0, 1, 0]), rtol=1e-14)
+    assert nl[0, 0] == 3
+    cfg2 = oracle.make_config(t_min=0.006)
+    img2, t32b, _, nl2 = oracle.render(v, vals, ranges, cam, cfg2)
+    assert nl2[0, 0] == 1 and t32b[0, 0] == np.float32(1.0) - np.float32(0.99)  # stops before the last splat
+
+
+# ------------------------------------------------------------------------------------------
+# tiny scene: definition, invariants
+# ------------------------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def tiny_view(tiny):
+    sc, cam = tiny.scene, tiny.cameras[0]
+    v = oracle.prepare_view(sc, cam, CFG)
+    img, t32, t64, nl = oracle.render(v, v["vals"], v["ranges"], cam, CFG)
+    tgt = (img + synth.target_noise(img.shape, 0.02, tiny.seed, 0)).astype(np.float32)
+    return v, img, t32, t64, nl, tgt
+
+
+def test_removal_effect_equals_definition_bruteforce(tiny, tiny_view):
+    v, img, t32, t64, nl, tgt = tiny_view
+    cam = tiny.cameras[0]
+    cfg0 = oracle.make_config(t_min=0.0)
+    img0, *_ = oracle.render(v, v["vals"], v["ranges"], cam, cfg0)
+    d, _ = oracle.removal_effect(v, v["vals"], v["ranges"], cam, cfg0, tgt)
+    nz = 0
+    for k in range(100):
+        b = oracle.removal_bruteforce(v, v["vals"], v["ranges"], cam, cfg0, tgt, img0, k)
+        assert abs(d[k] - b) <= 1e-10 * abs(b) + 1e-13, k
+        nz += b != 0
+    assert nz > 50
+
+
+def test_removal_effect_pd_squared_when_target_is_render(tiny, tiny_view):
+    v, img, t32, t64, nl, tgt = tiny_view
+    d, _ = oracle.removal_effect(v, v["vals"], v["ranges"], tiny.cameras[0], CFG, img.astype(np.float32))
+    # target = render up to binary32 rounding of the target: dSE = PD^2 + O(1e-8 PD)
+    assert d.min() > -1e-6
+
+
+def test_importance_sums_to_coverage(tiny, tiny_view):
+    v, img, t32, t64, nl, tgt = tiny_view
+    _, imp = oracle.removal_effect(v, v["vals"], v["ranges"], tiny.cameras[0], CFG, tgt)
+    assert imp.sum() == pytest.approx((1.0 - t64).sum(), rel=1e-12)
+    assert np.all(img >= 0)
+    assert np.all(t32 >= CFG.t_min) and np.all(t32 <= 1)
+
+
+def test_transparent_and_offscreen_splats_have_zero_effect(tiny):
+    sc = tiny.scene
+    sc2 = synth.Scene(sc.means.copy(), sc.log_scales.copy(), sc.quats.copy(), sc.opacity_logits.copy(), sc.sh.copy())
+    sc2.opacity_logits[:10] = -30.0  # alpha < alpha_min everywhere
+    sc2.means[:, 10:20] = [[50.0], [50.0], [50.0]]  # far outside the view
+    cam = tiny.cameras[0]
+    v = oracle.prepare_view(sc2, cam, CFG)
+    img, *_ = oracle.render(v, v["vals"], v["ranges"], cam, CFG)
+    tgt = (img + 0.05).astype(np.float32)
+    d, imp = oracle.removal_effect(v, v["vals"], v["ranges"], cam, CFG, tgt)
+    assert np.all(d[:20] == 0.0) and np.all(imp[:20] == 0.0)
+    assert np.count_nonzero(d[20:]) > 500
+
+
+def test_affine_in_alpha_identity(tiny, tiny_view):
+    """c is affine in each alpha_i: PD_i = c(alpha_i = 0) - c = 2 c(alpha_i/2) - 2 c(alpha_i),
+    checked for whole splats by halving the opacity (alpha_min = 0, no clamp active)."""
+    v, *_ = tiny_view
+    cam = tiny.cameras[0]
+    cfg = oracle.make_config(t_min=0.0, alpha_min=0.0, alpha_max=1.0)
+    img, *_ = oracle.render(v, v["vals"], v["ranges"], cam, cfg)
+    tgt = np.zeros_like(img, dtype=np.float32)
+    for k in range(5):
+        v2 = dict(v)
+        v2["opacity"] = v["opacity"].copy()
+        v2["opacity"][k] = v["opacity"][k] * np.float32(0.5)  # exact halving in binary32
+        img_half, *_ = oracle.render(v2, v["vals"], v["ranges"], cam, cfg)
+        # exp2r is the same on both renders, so alpha halves exactly except for o*G rounding
+        pd_img = 2 * img_half - 2 * img  # c(alpha=0) - c(alpha)
+        want = np.sum(pd_img * pd_img + 2 * pd_img * img)
+        d, _ = oracle.removal_effect(v, v["vals"], v["ranges"], cam, cfg, tgt)
+        assert d[k] == pytest.approx(want, rel=1e-5, abs=1e-9)
+
+
+def test_dmse_view_normalisation_invariant(tiny):
+    sc, cam = tiny.scene, tiny.cameras[0]
+    v = oracle.prepare_view(sc, cam, CFG)
+    img, *_ = oracle.render(v, v["vals"], v["ranges"], cam, CFG)
+    tgt = (img + 0.01).astype(np.float32)
+    one, i1 = oracle.dmse(sc, [cam], CFG, [tgt])
+    two, i2 = oracle.dmse(sc, [cam, cam], CFG, [tgt, tgt])  # a repeated view leaves the mean unchanged
+    np.testing.assert_allclose(two, one, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(i2, i1, rtol=1e-14)
+    d, _ = oracle.removal_effect(v, v["vals"], v["ranges"], cam, CFG, tgt)
+    np.testing.assert_allclose(one, d / (3 * cam.pixels), rtol=1e-14)
+
+
+def test_colour_direction_is_camera_to_splat():
+    # camera at (0, 0, -3), splat at (1, 0, 0): direction (1, 0, 3)/sqrt(10); only Y_2 = Y_1^0 (l=1, m=0) set
+    cam = synth.look_at_camera((0.0, 0.0, -3.0), 256, 256)
+    sh = np.zeros((16, 3, 1), np.float32)
+    sh[2, :, 0] = 1.0
+    sh[3, 1, 0] = 1.0  # green also gets Y_1^1 = -c x
+    sc = _scene(np.array([[1.0], [0.0], [0.0]]), np.full((3, 1), -3.0), np.array([[1.0], [0], [0], [0]]), np.zeros(1), sh)
+    cov, op = oracle.activate(sc)
+    pr = oracle.project(sc, cov, cam, CFG)
+    c1 = math.sqrt(3 / (4 * math.pi))
+    d = np.array([1.0, 0.0, 3.0]) / math.sqrt(10.0)
+    assert pr["touched"][0] > 0
+    assert pr["rgb"][0, 0] == pytest.approx(c1 * d[2] + 0.5, rel=1e-6)
+    assert pr["rgb"][1, 0] == pytest.approx(c1 * d[2] - c1 * d[0] + 0.5, rel=1e-6)
