@@ -1,0 +1,374 @@
+"""Benchmark of the removal-effect path on one GB300 (or N GPUs of one node, weak scaling).
+
+A step is one pass of the whole path over one frame: activation + EWA projection of 1M
+splats into 16 views of 1280x720, tile binning + radix sort of every (tile, splat) instance,
+and the removal-effect pass with the per-splat dMSE_k / I_k reduction.  Inputs (the 236 MB of
+splat parameters, the 768 MB of per-view raster records, ~1 GB of sort keys) are larger than
+the 129 MB L2, so no L2 flush is needed between steps.
+
+Printed (one JSON line on rank 0): the device-timed throughput of the batched frame
+(``value``, views/s), the same frame replayed as a CUDA graph, the one-view-per-launch form,
+Gblend/s (evaluated pixel-splat pairs per second of the removal kernel), the roofline of the
+removal kernel (FP32 ALU), the end-to-end number through host buffers, the clocks seen
+during the timed region, and the CPU oracle timed on a bounded sample.
+
+``--impl reference`` times the CPU oracle itself on the same workload (one view per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "removal-effect views/s & Gblend/s (batched vs per-view); fwd+bwd ms/step"
+WORKLOAD = "scene"
+CFG = dict(tile_w=16, tile_h=16, batch=256)
+# Algorithmic FP32 work per pair (FMA = 2 FLOP), counted from the kernel's operation spec:
+FLOP_EXPONENT = 9        # dx, dy, A dx^2 + B dx dy + C dy^2 (every examined pair / walked position)
+FLOP_ALPHA = 17          # exp2 (3 add + 6 FMA), o * G, min (pairs passing the prefilter)
+FLOP_COMPOSITE = 9       # T (1 - alpha), w = alpha T, three colour FMAs (composited pairs)
+FLOP_REMOVAL = 26        # T recovery, ratio, PD and dSE over 3 channels, suffix update (composited pairs)
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+PEAK_FP32_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.15)
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------
+# workload construction
+# ------------------------------------------------------------------------------------------
+
+def make_targets_gpu(w, frame_cls, scene_to_device, cams_rec, torch):
+    """Workload recipe: render of the scene with a seeded 5 % of the splats dropped, plus
+    N(0, 0.01) noise per view (input preparation, outside the timed region)."""
+    import synth
+
+    keep = synth.target_drop_mask(w.scene.n, w.target_drop, w.seed)
+    tf = frame_cls(scene_to_device(w.scene.subset(keep)), cams_rec, with_importance=False, **CFG)
+    tf.plan()
+    img = tf.image_buffer()
+    tf.render(img)
+    torch.cuda.synchronize()
+    noise = np.concatenate([synth.target_noise((3, c.height, c.width), w.target_noise, w.seed, v).reshape(-1)
+                            for v, c in enumerate(w.cameras)])
+    img += torch.from_numpy(noise).to(img.device)
+    del tf
+    return img
+
+
+def oracle_view_seconds(w, v: int) -> tuple[float, int]:
+    """CPU oracle on one whole view: activation, projection, binning + sort, removal effect."""
+    import oracle
+    import synth
+
+    ocfg = oracle.make_config(tile_w=CFG["tile_w"], tile_h=CFG["tile_h"])
+    cam = w.cameras[v]
+    keep = synth.target_drop_mask(w.scene.n, w.target_drop, w.seed)
+    tv = oracle.prepare_view(w.scene.subset(keep), cam, ocfg)
+    img, *_ = oracle.render(tv, tv["vals"], tv["ranges"], cam, ocfg)
+    target = (img + synth.target_noise(img.shape, w.target_noise, w.seed, v)).astype(np.float32)
+    t0 = time.perf_counter()
+    pv = oracle.prepare_view(w.scene, cam, ocfg)
+    oracle.removal_effect(pv, pv["vals"], pv["ranges"], cam, ocfg, target)
+    return time.perf_counter() - t0, int(pv["vals"].size)
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    import synth
+    from paper_2601_14821_gb300 import _binding as B
+    from paper_2601_14821_gb300 import build as potr_build
+    from paper_2601_14821_gb300 import dist as D
+    from paper_2601_14821_gb300.pipeline import RemovalEffectFrame, scene_to_device
+
+    rank, local, world = D.env_ranks()
+    potr_build.build()
+    torch.cuda.set_device(local)
+    D.init("nccl")
+    dev = torch.device("cuda", local)
+    w = synth.workload(WORKLOAD)
+    n_views = len(w.cameras)
+    cams_rec = synth.cameras_to_array(w.cameras)
+    scene_d = scene_to_device(w.scene, dev)
+    frame = RemovalEffectFrame(scene_d, cams_rec, device=dev, **CFG)
+    n_inst = frame.plan()
+    targets = make_targets_gpu(w, RemovalEffectFrame, scene_to_device, cams_rec, torch)
+    dmse = torch.zeros(frame.n, dtype=torch.float64, device=dev)
+    imp = torch.zeros(frame.n, dtype=torch.float64, device=dev)
+
+    def step():
+        frame.preprocess()
+        frame.bin_sort()
+        frame.removal_effect(targets, dmse, imp)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps of the batched frame, per-stage events on the launch stream
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    clocks = ClockSampler(f"GPU-{uuid}" if uuid else None)
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    D.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = B.potr_launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record()
+    for i in range(K):
+        ev[i][0].record()
+        frame.preprocess()
+        ev[i][1].record()
+        frame.bin_sort()
+        ev[i][2].record()
+        frame.removal_effect(targets, dmse, imp)
+        ev[i][3].record()
+    t_end.record()
+    torch.cuda.synchronize()
+    D.barrier()
+    launches = B.potr_launch_count() - l0
+    clk = clocks.stop()
+    ms_total = D.max_over_ranks(t_start.elapsed_time(t_end), dev)
+    stage = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])] for e in ev])
+    stage_ms = stage.mean(axis=0)
+    ms_step = ms_total / K
+    value = world * n_views * K / (ms_total / 1e3)
+
+    # ---- CUDA graph of one whole step, replayed
+    graph_vps = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(device=dev)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            step()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            step()
+        for _ in range(args.warmup):
+            g.replay()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(K):
+            g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        graph_vps = world * n_views * K / (D.max_over_ranks(a.elapsed_time(b), dev) / 1e3)
+        del g
+    except Exception as exc:  # reported, not hidden
+        graph_vps = f"capture failed: {exc}"
+
+    # ---- one view per launch chain
+    per_frames = [RemovalEffectFrame(scene_d, cams_rec[v:v + 1], device=dev, **CFG) for v in range(n_views)]
+    for f in per_frames:
+        f.plan()
+    tviews = [targets[3 * int(frame.info_np[v]["pixel_base"]): 3 * int(frame.info_np[v]["pixel_base"])
+                      + 3 * w.cameras[v].pixels] for v in range(n_views)]
+
+    def per_view_step():
+        for f, t in zip(per_frames, tviews):
+            f.step(t, dmse, imp, n_views_total=n_views)
+
+    for _ in range(args.warmup):
+        per_view_step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(K):
+        per_view_step()
+    b.record()
+    torch.cuda.synchronize()
+    per_view_vps = world * n_views * K / (D.max_over_ranks(a.elapsed_time(b), dev) / 1e3)
+    del per_frames
+
+    # ---- exact pair counts -> Gblend/s and the removal kernel's ALU roofline
+    pc = frame.pair_stats()
+    torch.cuda.synchronize()
+    pairs = pc["examined"] + pc["back_positions"]
+    flops = (FLOP_EXPONENT * (pc["examined"] + pc["back_positions"]) + FLOP_ALPHA * (pc["passed"] + pc["back_passed"])
+             + (FLOP_COMPOSITE + FLOP_REMOVAL) * pc["composited"])
+    t_removal = stage_ms[2] / 1e3
+    achieved = flops / t_removal / 1e12
+    gblend = world * pairs / t_removal / 1e9
+
+    # ---- end to end through host buffers (pinned): parameters + targets in, dMSE + I out
+    host_scene = {k: v.cpu().pin_memory() for k, v in scene_d.items()}
+    host_targets = targets.cpu().pin_memory()
+    host_dmse = torch.empty_like(dmse, device="cpu").pin_memory()
+    host_imp = torch.empty_like(imp, device="cpu").pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host_scene.values()) + host_targets.numel() * 4
+    d2h = 2 * dmse.numel() * 8
+
+    def e2e_step():
+        for k, t in host_scene.items():
+            scene_d[k].copy_(t, non_blocking=True)
+        targets.copy_(host_targets, non_blocking=True)
+        step()
+        host_dmse.copy_(dmse, non_blocking=True)
+        host_imp.copy_(imp, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    D.barrier()
+    a.record()
+    for _ in range(K):
+        e2e_step()
+    b.record()
+    torch.cuda.synchronize()
+    e2e_vps = world * n_views * K / (D.max_over_ranks(a.elapsed_time(b), dev) / 1e3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        secs, _ = oracle_view_seconds(w, 0)
+        cpu = {"value": 1.0 / secs, "unit": "views/s", "cores": 1, "kind": "oracle",
+               "sample": f"view 0 of the workload (1 of {n_views} views, {secs:.1f} s single-threaded): "
+                         "activation, projection, binning + stable sort, removal effect and importance"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "scene: 1M splats (70% unit ball, 30% shell 2-10), 16 views 1280x720 on a ring "
+                                   "of radius 4, targets = render with 5% of splats dropped + N(0, 0.01)",
+                       "n_splats": int(frame.n), "views_per_gpu": n_views, "resolution": "1280x720",
+                       "tile": f"{CFG['tile_w']}x{CFG['tile_h']}", "splat_batch": CFG["batch"],
+                       "form": "batched frame (all views in one launch per stage)", "instances": int(n_inst),
+                       "l2": "inputs larger than L2 (236 MB parameters, 768 MB raster records, ~1 GB keys)",
+                       "parallelism": f"views replicated per GPU x{world}"},
+            "stage_ms": {"preprocess": stage_ms[0], "bin_sort": stage_ms[1], "removal_effect": stage_ms[2]},
+            "graph_views_per_s": graph_vps,
+            "per_view_views_per_s": per_view_vps,
+            "gblend_per_s": gblend,
+            "pairs": pc,
+            "fwd_bwd_ms_per_step": None,
+            "roofline": {"kernel": "removal_kernel (memset + tile pass + per-splat reduce)", "bound": "alu",
+                         "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / PEAK_FP32_TFLOPS, "traffic": None,
+                         "flops_per_launch": flops},
+            "e2e": {"value": e2e_vps, "unit": "views/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+
+
+# ------------------------------------------------------------------------------------------
+# reference arm: the CPU oracle as it stands
+# ------------------------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synth
+
+    w = synth.workload(WORKLOAD)
+    n_views = len(w.cameras)
+    for i in range(args.warmup):
+        oracle_view_seconds(w, i % n_views)
+    tot = 0.0
+    for i in range(args.steps):
+        secs, _ = oracle_view_seconds(w, i % n_views)
+        tot += secs
+    value = args.steps / tot
+    line = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "scene: 1M splats, 16 views 1280x720 (one whole view per step)"},
+            "cpu_baseline": {"value": value, "unit": "views/s", "cores": 1, "kind": "oracle",
+                             "sample": "one whole view per step, views 0.. in order"},
+            "e2e": {"value": value, "unit": "views/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,239 @@
+/*
+ * potr.h -- C ABI of the GB300 (sm_103a) removal-effect rasterizer.
+ *
+ * The library computes, for one or many views of a 3D Gaussian splat scene, every splat's
+ * removal effect: the change in squared error against a target image when that splat alone
+ * is dropped from front-to-back alpha compositing (POTR, arXiv 2601.14821, Section IV-B,
+ * Eqs. "pruning difference" and "pixel squared error"), summed over pixels and views into
+ * dMSE_k (Section IV-B, last equation), together with the splat importance I_k (Section IV-A).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* and every pointer inside potr_views / potr_frame are DEVICE
+ *     pointers owned by the caller.  Pointers named h_* are host pointers.  The library
+ *     never allocates or frees memory and keeps no device state between calls.
+ *   - Work is enqueued asynchronously on the caller's stream; no call synchronises the
+ *     host with the device, so a sequence of calls can be captured in a CUDA graph.
+ *   - Return value: POTR_OK, or an error detected on the host before anything was
+ *     enqueued (POTR_ERR_INVALID_ARGUMENT, POTR_ERR_UNSUPPORTED), or POTR_ERR_CUDA when a
+ *     launch failed.  Errors found on the device (instance capacity exceeded) are written
+ *     to a caller-provided potr_device_status, read by the caller after synchronising.
+ *   - Planes: "[3][n]" means three contiguous arrays of n floats (structure of arrays).
+ *   - Index "vk" = v * n + k for view v and splat k of a frame.
+ */
+#ifndef POTR_H_
+#define POTR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define POTR_API __attribute__((visibility("default")))
+#else
+#define POTR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* potr_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef int32_t potr_status;
+enum {
+  POTR_OK = 0,
+  POTR_ERR_INVALID_ARGUMENT = 1,
+  POTR_ERR_CUDA = 2,
+  POTR_ERR_CAPACITY = 3, /* device: more tile instances than instance_capacity */
+  POTR_ERR_TIMEOUT = 4,  /* device: a bounded wait ran out */
+  POTR_ERR_NUMERIC = 5,
+  POTR_ERR_UNSUPPORTED = 6
+};
+
+/* Device-side status word; zero it before the calls that may write it. */
+typedef struct {
+  int32_t code;               /* POTR_OK or a POTR_ERR_* code */
+  int32_t reserved;
+  int64_t required_instances; /* instance count needed when code == POTR_ERR_CAPACITY */
+} potr_device_status;
+
+/*
+ * Splat parameters (Section 3): N splats as SoA planes, all float32 device arrays.
+ *   means[3][n]          centre mu
+ *   log_scales[3][n]     scale = exp(log_scale) per principal axis
+ *   quats[4][n]          rotation quaternion (w, x, y, z), w real; normalised on use
+ *   opacity_logits[n]    base opacity o = sigmoid(logit)
+ *   sh[16][3][n]         SH coefficients L_i per channel, index i = l(l+1)+m (degree <= 3)
+ */
+typedef struct {
+  const float* means;
+  const float* log_scales;
+  const float* quats;
+  const float* opacity_logits;
+  const float* sh;
+  int64_t n;
+} potr_scene;
+
+/* Pinhole camera: world-to-camera rows [R | t], camera space looks along +z, image y down. */
+typedef struct {
+  float w2c[12];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+} potr_camera;
+
+/*
+ * Rasterizer configuration.  tile_w * tile_h must be 256 (16x16, 8x32 or 32x8); batch is
+ * the number of splats staged in shared memory per step (128, 256 or 512).  The remaining
+ * fields are the readings of the original 3DGS renderer the paper modifies (Section 3):
+ *   near_z     cull when camera-space z <= near_z                         (default 0.2)
+ *   lowpass    added to the diagonal of the 2D covariance, pixel^2       (default 0.3)
+ *   alpha_min  a pixel skips a splat whose alpha < alpha_min             (default 1/255)
+ *   alpha_max  alpha is clamped to alpha_max                              (default 0.99)
+ *   t_min      compositing stops before a splat that would take T below t_min (1e-4)
+ */
+typedef struct {
+  int32_t tile_w, tile_h;
+  int32_t batch;
+  float near_z, lowpass, alpha_min, alpha_max, t_min;
+} potr_raster_config;
+
+/* Placement of one view inside a frame (a set of views processed together). */
+typedef struct {
+  int32_t width, height;
+  int32_t tiles_x, tiles_y;
+  int64_t tile_base;  /* first global tile index of the view */
+  int64_t pixel_base; /* first pixel of the view in packed per-pixel arrays */
+} potr_view_info;
+
+/* A frame: views laid out one after another (tiles and pixels in view order). */
+typedef struct {
+  const potr_camera* cams;     /* device [n_views] */
+  const potr_view_info* info;  /* device [n_views], from potr_view_layout */
+  int32_t n_views;
+  int64_t total_tiles;
+  int64_t total_pixels;
+} potr_frame;
+
+/*
+ * Per-(view, splat) buffers produced by potr_preprocess and potr_bin_sort (device, caller
+ * owned).  raster holds 12 floats per vk, 16-byte aligned:
+ *   [0] mean x  [1] mean y  [2] A  [3] B  [4] C  [5] opacity  [6] prefilter  [7] offset bits
+ *   [8] r       [9] g       [10] b [11] rectangle bits (x0 | y0 << 11 | width << 22)
+ * where log2 G(dx, dy) = A dx^2 + B dx dy + C dy^2 and "offset" is the vk's first emission
+ * slot (written by potr_bin_sort).
+ */
+typedef struct {
+  float* cov3d;          /* [6][n] activated covariance (xx, xy, xz, yy, yz, zz) */
+  float* opacity;        /* [n] */
+  float* raster;         /* [V * n][12] */
+  float* depth;          /* [V * n] camera-space z, the sort key's low word */
+  uint32_t* rect;        /* [V * n][2] (x0 | y0 << 16, x1 | y1 << 16), tiles, half open */
+  uint32_t* touched;     /* [V * n] tiles covered, 0 when culled */
+  uint32_t* offsets;     /* [V * n] exclusive prefix sum of touched (emission slots) */
+  uint32_t* n_instances; /* [1] total instances (potr_bin_sort) */
+} potr_views;
+
+/* Text for a status code (static string). */
+POTR_API const char* potr_status_string(potr_status status);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+POTR_API int32_t potr_version(void);
+
+/*
+ * Host only.  Fills h_info[n_views] from h_cams and cfg (tiles per view, tile and pixel
+ * bases in view order) and the frame totals.  Errors: INVALID_ARGUMENT on a bad tile
+ * shape or camera size; UNSUPPORTED when a view has more than 1023 tile columns or 2047
+ * tile rows (the raster record packs the rectangle in 32 bits).
+ */
+POTR_API potr_status potr_view_layout(const potr_camera* h_cams, int32_t n_views, const potr_raster_config* cfg,
+                             potr_view_info* h_info, int64_t* total_tiles, int64_t* total_pixels);
+
+/*
+ * Section 3 (Eqs. 1-2 and the SH colour equation): activation of every splat (exp of the
+ * log-scales, quaternion normalisation, Sigma = R S S^T R^T, o = sigmoid(logit)), then, for
+ * every view of the frame, EWA projection (view transform, near cull, clamped Jacobian,
+ * Sigma2D = J W Sigma W^T J^T + lowpass I, conic, radius ceil(3 sqrt(lambda_max))), pixel
+ * centre, tile rectangle, depth and the SH colour max(0, sum_i L_i Y_i(d) + 0.5) along the
+ * camera-to-splat direction d.  Writes views->cov3d, opacity, raster (all but the offset
+ * word), depth, rect, touched.  Every quantity that decides the binning or the per-pixel
+ * alpha test is computed in binary32 with a fixed operation order (no contraction), with
+ * exp taken by a reproducible exp2 (Cody-Waite reduction plus a degree-6 Taylor polynomial).
+ */
+POTR_API potr_status potr_preprocess(const potr_scene* scene, const potr_frame* frame, const potr_raster_config* cfg,
+                            const potr_views* views, potr_stream_t stream);
+
+/* Workspace bytes potr_bin_sort needs (scan partials, sort double buffers, histograms). */
+POTR_API size_t potr_bin_sort_workspace_size(int64_t n, int32_t n_views, int64_t total_tiles, int64_t instance_capacity);
+
+/*
+ * Binning (Section 3, "ordering these layers according to the splats' approximate depth"):
+ * exclusive scan of touched over vk -> views->offsets and *views->n_instances; one instance
+ * per touched tile emitted in vk order and, within a rectangle, row-major, with key
+ * (global tile << 32) | bits(depth) and value vk; a stable LSD radix sort of the keys
+ * (8-bit digits over the significant bits); and per-global-tile [start, end) ranges into
+ * d_tile_ranges[total_tiles][2] (empty tiles get [0, 0)).  The result equals a stable sort,
+ * so equal keys keep emission order.  d_keys / d_vals hold instance_capacity entries.
+ * If the instance count exceeds instance_capacity, d_status gets POTR_ERR_CAPACITY and the
+ * required count, and every tile range is left empty.
+ */
+POTR_API potr_status potr_bin_sort(const potr_views* views, const potr_frame* frame, const potr_raster_config* cfg,
+                          int64_t n, int64_t instance_capacity, uint64_t* d_keys, uint32_t* d_vals,
+                          uint32_t* d_tile_ranges, potr_device_status* d_status, void* d_ws, size_t ws_bytes,
+                          potr_stream_t stream);
+
+/*
+ * Render (Section 3, Eqs. 2-4): per pixel, front to back over its tile's sorted list,
+ * alpha = min(alpha_max, o G), skip alpha < alpha_min, stop before T (1 - alpha) < t_min,
+ * c = sum T_k alpha_k c_k over a black background.  Outputs (device, per frame pixel):
+ * d_images planar [3][H][W] per view at offset 3 * pixel_base; d_t_final the final
+ * transmittance; d_n_last one past the tile-list position of the last composited splat
+ * (0 if none).  Any output may be NULL.
+ */
+POTR_API potr_status potr_render(const potr_views* views, const potr_frame* frame, const potr_raster_config* cfg,
+                        int64_t n, const uint32_t* d_vals, const uint32_t* d_tile_ranges, float* d_images,
+                        float* d_t_final, uint32_t* d_n_last, potr_stream_t stream);
+
+/*
+ * Removal effect (Section IV-B).  For every pixel: the render above, then a back-to-front
+ * pass over the composited splats that forms, with S_{>i} = P_K - P_{i+1} (suffix sum),
+ *   PD_i  = alpha_i / (1 - alpha_i) S_{>i} - T_i alpha_i c_i     (Eq. pruning difference)
+ *   dSE_i = sum_ch PD_i (PD_i + 2 (c - c_t))                      (Eq. pixel squared error)
+ * reduced per (tile, splat) in a fixed order (warp transpose-sum, then warps in order) into
+ * d_inst_dse[emission slot] (float, instance_capacity entries, required; the same capacity
+ * as potr_bin_sort -- when the frame's instance count exceeded it, nothing is reduced and
+ * d_dmse / d_importance / d_dsse_view are left untouched).  Then, per
+ * splat, the tile partials are summed in binary64 in emission order, giving
+ * dSSE_k(v) = sum_x dSE, and
+ *   d_dmse[k] += dSSE_k(v) / (3 P_v n_views_total)        (views added in order)
+ * so that calls over consecutive view chunks compose (zero d_dmse before the first call).
+ * With d_inst_imp / d_importance non-NULL the same is done for T_i alpha_i, giving
+ * I_k += (sum_x T alpha) / (P_v n_views_total) (Section IV-A).  d_dsse_view (nullable,
+ * [n_views][n] binary64) receives dSSE_k(v) itself.  d_images (nullable) receives the
+ * render.  d_targets: planar [3][H][W] per view at offset 3 * pixel_base.
+ */
+POTR_API potr_status potr_removal_effect(const potr_views* views, const potr_frame* frame, const potr_raster_config* cfg,
+                                int64_t n, const uint32_t* d_vals, const uint32_t* d_tile_ranges,
+                                const float* d_targets, int32_t n_views_total, int64_t instance_capacity,
+                                float* d_inst_dse,
+                                float* d_inst_imp, double* d_dmse, double* d_importance, double* d_dsse_view,
+                                float* d_images, potr_stream_t stream);
+
+/*
+ * Exact pair counts for throughput and roofline accounting (no counterpart in the paper;
+ * the counts define the algorithmic work of Section 3 / IV-B in pairs).  d_counts[5]
+ * (device, uint64, overwritten): [0] (pixel, splat) pairs examined by the front-to-back walk,
+ * [1] of those passing the opacity prefilter, [2] pairs composited, [3] list positions
+ * walked back to front by the removal pass (sum of n_last), [4] of those passing the
+ * prefilter.  Same inputs as potr_render.
+ */
+POTR_API potr_status potr_pair_stats(const potr_views* views, const potr_frame* frame, const potr_raster_config* cfg,
+                                     int64_t n, const uint32_t* d_vals, const uint32_t* d_tile_ranges,
+                                     uint64_t* d_counts, potr_stream_t stream);
+
+/* Number of kernels the library has launched in this process (host-side counter). */
+POTR_API uint64_t potr_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POTR_H_ */

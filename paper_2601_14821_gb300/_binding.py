@@ -1,0 +1,194 @@
+"""ctypes binding of libpotr (include/potr.h): same names, argument marshalling only.
+
+Every compute step runs in the CUDA library; this module converts torch tensors to device
+pointers, Python values to the C structs, and C status codes to exceptions.  It raises
+when the library has not been built -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpotr.so")
+_lock = threading.Lock()
+_lib = None
+
+POTR_OK = 0
+POTR_ERR_INVALID_ARGUMENT = 1
+POTR_ERR_CUDA = 2
+POTR_ERR_CAPACITY = 3
+POTR_ERR_TIMEOUT = 4
+POTR_ERR_NUMERIC = 5
+POTR_ERR_UNSUPPORTED = 6
+
+
+class PotrError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        super().__init__(f"{fn} failed: {status_string(status)} ({status})")
+        self.status = status
+
+
+class Scene(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p), ("n", C.c_int64)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("w2c", C.c_float * 12), ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float),
+                ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class RasterConfig(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("batch", C.c_int32), ("near_z", C.c_float),
+                ("lowpass", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_min", C.c_float)]
+
+
+class ViewInfo(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32),
+                ("tile_base", C.c_int64), ("pixel_base", C.c_int64)]
+
+
+class Frame(C.Structure):
+    _fields_ = [("cams", C.c_void_p), ("info", C.c_void_p), ("n_views", C.c_int32), ("total_tiles", C.c_int64),
+                ("total_pixels", C.c_int64)]
+
+
+class Views(C.Structure):
+    _fields_ = [("cov3d", C.c_void_p), ("opacity", C.c_void_p), ("raster", C.c_void_p), ("depth", C.c_void_p),
+                ("rect", C.c_void_p), ("touched", C.c_void_p), ("offsets", C.c_void_p),
+                ("n_instances", C.c_void_p)]
+
+
+class DeviceStatus(C.Structure):
+    _fields_ = [("code", C.c_int32), ("reserved", C.c_int32), ("required_instances", C.c_int64)]
+
+
+# Every exported symbol of include/potr.h, with its ctypes signature.
+_P, _I32, _I64, _SZ = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
+SIGNATURES = {
+    "potr_status_string": (C.c_char_p, [_I32]),
+    "potr_version": (_I32, []),
+    "potr_view_layout": (_I32, [_P, _I32, C.POINTER(RasterConfig), _P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "potr_preprocess": (_I32, [C.POINTER(Scene), C.POINTER(Frame), C.POINTER(RasterConfig), C.POINTER(Views), _P]),
+    "potr_bin_sort_workspace_size": (_SZ, [_I64, _I32, _I64, _I64]),
+    "potr_bin_sort": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _I64, _P, _P, _P,
+                             _P, _P, _SZ, _P]),
+    "potr_render": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _P, _P, _P, _P, _P,
+                           _P]),
+    "potr_removal_effect": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _P, _P, _P,
+                                   _I32, _I64, _P, _P, _P, _P, _P, _P, _P]),
+    "potr_pair_stats": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _P, _P, _P, _P]),
+    "potr_launch_count": (C.c_uint64, []),
+}
+
+
+def lib():
+    """Load libpotr.so (built by ``paper_2601_14821_gb300.build``); raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libpotr.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().potr_status_string(int(status)).decode()
+
+
+def _check(fn: str, status: int):
+    if status != POTR_OK:
+        raise PotrError(fn, status)
+
+
+def ptr(t) -> int | None:
+    """Device (or host) address of a torch tensor / numpy array, None for None."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def stream_handle(stream=None) -> int | None:
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+DEFAULT_CONFIG = dict(tile_w=16, tile_h=16, batch=256, near_z=0.2, lowpass=0.3, alpha_min=1.0 / 255.0,
+                      alpha_max=0.99, t_min=1e-4)
+
+
+def make_config(**kw) -> RasterConfig:
+    d = dict(DEFAULT_CONFIG)
+    d.update(kw)
+    return RasterConfig(int(d["tile_w"]), int(d["tile_h"]), int(d["batch"]), d["near_z"], d["lowpass"],
+                        d["alpha_min"], d["alpha_max"], d["t_min"])
+
+
+# ------------------------------------------------------------------------------------------
+# the C entry points
+# ------------------------------------------------------------------------------------------
+
+def potr_view_layout(cams_rec: np.ndarray, cfg: RasterConfig):
+    """cams_rec: (V, 18) float32 camera records.  Returns (info (V,) ViewInfo array as
+    uint8 bytes, total_tiles, total_pixels)."""
+    cams_rec = np.ascontiguousarray(cams_rec, np.float32)
+    v = cams_rec.shape[0]
+    info = np.zeros(v * C.sizeof(ViewInfo), np.uint8)
+    tt, tp = C.c_int64(0), C.c_int64(0)
+    _check("potr_view_layout", lib().potr_view_layout(cams_rec.ctypes.data, v, C.byref(cfg), info.ctypes.data,
+                                                      C.byref(tt), C.byref(tp)))
+    return info, tt.value, tp.value
+
+
+def potr_preprocess(scene: Scene, frame: Frame, cfg: RasterConfig, views: Views, stream=None):
+    _check("potr_preprocess", lib().potr_preprocess(C.byref(scene), C.byref(frame), C.byref(cfg), C.byref(views),
+                                                    stream_handle(stream)))
+
+
+def potr_bin_sort_workspace_size(n: int, n_views: int, total_tiles: int, capacity: int) -> int:
+    return int(lib().potr_bin_sort_workspace_size(n, n_views, total_tiles, capacity))
+
+
+def potr_bin_sort(views: Views, frame: Frame, cfg: RasterConfig, n: int, capacity: int, keys, vals, ranges, status,
+                  ws, stream=None):
+    _check("potr_bin_sort", lib().potr_bin_sort(C.byref(views), C.byref(frame), C.byref(cfg), n, capacity, ptr(keys),
+                                                ptr(vals), ptr(ranges), ptr(status), ptr(ws), ws.numel(),
+                                                stream_handle(stream)))
+
+
+def potr_render(views: Views, frame: Frame, cfg: RasterConfig, n: int, vals, ranges, images=None, t_final=None,
+                n_last=None, stream=None):
+    _check("potr_render", lib().potr_render(C.byref(views), C.byref(frame), C.byref(cfg), n, ptr(vals), ptr(ranges),
+                                            ptr(images), ptr(t_final), ptr(n_last), stream_handle(stream)))
+
+
+def potr_removal_effect(views: Views, frame: Frame, cfg: RasterConfig, n: int, vals, ranges, targets,
+                        n_views_total: int, capacity: int, inst_dse, inst_imp=None, dmse=None, importance=None,
+                        dsse_view=None, images=None, stream=None):
+    _check("potr_removal_effect",
+           lib().potr_removal_effect(C.byref(views), C.byref(frame), C.byref(cfg), n, ptr(vals), ptr(ranges),
+                                     ptr(targets), n_views_total, capacity, ptr(inst_dse), ptr(inst_imp), ptr(dmse),
+                                     ptr(importance), ptr(dsse_view), ptr(images), stream_handle(stream)))
+
+
+def potr_pair_stats(views: Views, frame: Frame, cfg: RasterConfig, n: int, vals, ranges, counts, stream=None):
+    _check("potr_pair_stats", lib().potr_pair_stats(C.byref(views), C.byref(frame), C.byref(cfg), n, ptr(vals),
+                                                    ptr(ranges), ptr(counts), stream_handle(stream)))
+
+
+def potr_launch_count() -> int:
+    return int(lib().potr_launch_count())

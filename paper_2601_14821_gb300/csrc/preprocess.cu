@@ -1,0 +1,260 @@
+// preprocess.cu -- activation and EWA projection of every splat into every view of a frame
+// (paper Section 3: the 3D Gaussian, its affine-approximated 2D projection, the SH colour).
+//
+// Two kernels:
+//   activate_kernel   one thread per splat: scale = exp(log_scale), q / |q|, Sigma = (R S)(R S)^T,
+//                     o = sigmoid(logit).  View independent, so it runs once per frame.
+//   project_kernel    one thread per splat, looping over the frame's views: the splat's
+//                     centre, covariance, opacity and (on first visibility) its 48 SH
+//                     coefficients are read once and kept in registers for all views.
+// Both are HBM-bound: 32 B read / 28 B written per splat for activation; 40 B read per splat
+// plus 192 B of SH per splat visible in the frame, and 64 B written per visible (view, splat).
+#include "potr_device.cuh"
+
+namespace potr {
+namespace {
+
+__global__ void __launch_bounds__(256) activate_kernel(const float* __restrict__ log_scales,
+                                                       const float* __restrict__ quats,
+                                                       const float* __restrict__ logits, int64_t n,
+                                                       float* __restrict__ cov3d, float* __restrict__ opacity) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    float s[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) s[a] = exp2r(__fmul_rn(log_scales[a * n + k], kLog2e));
+    float qw = quats[k], qx = quats[n + k], qy = quats[2 * n + k], qz = quats[3 * n + k];
+    const float n2 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(qw, qw), __fmul_rn(qx, qx)), __fmul_rn(qy, qy)),
+                               __fmul_rn(qz, qz));
+    if (n2 > 0.0f) {
+      const float r = __fsqrt_rn(n2);
+      qw = __fdiv_rn(qw, r);
+      qx = __fdiv_rn(qx, r);
+      qy = __fdiv_rn(qy, r);
+      qz = __fdiv_rn(qz, r);
+    } else {
+      qw = 1.0f; qx = 0.0f; qy = 0.0f; qz = 0.0f;
+    }
+    float R[3][3];
+    R[0][0] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(__fmul_rn(qy, qy), __fmul_rn(qz, qz))));
+    R[0][1] = __fmul_rn(2.0f, __fsub_rn(__fmul_rn(qx, qy), __fmul_rn(qw, qz)));
+    R[0][2] = __fmul_rn(2.0f, __fadd_rn(__fmul_rn(qx, qz), __fmul_rn(qw, qy)));
+    R[1][0] = __fmul_rn(2.0f, __fadd_rn(__fmul_rn(qx, qy), __fmul_rn(qw, qz)));
+    R[1][1] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(__fmul_rn(qx, qx), __fmul_rn(qz, qz))));
+    R[1][2] = __fmul_rn(2.0f, __fsub_rn(__fmul_rn(qy, qz), __fmul_rn(qw, qx)));
+    R[2][0] = __fmul_rn(2.0f, __fsub_rn(__fmul_rn(qx, qz), __fmul_rn(qw, qy)));
+    R[2][1] = __fmul_rn(2.0f, __fadd_rn(__fmul_rn(qy, qz), __fmul_rn(qw, qx)));
+    R[2][2] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(__fmul_rn(qx, qx), __fmul_rn(qy, qy))));
+    float M[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) M[i][j] = __fmul_rn(R[i][j], s[j]);
+    const int ii[6] = {0, 0, 0, 1, 1, 2}, jj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      const int i = ii[e], j = jj[e];
+      cov3d[e * n + k] =
+          __fadd_rn(__fadd_rn(__fmul_rn(M[i][0], M[j][0]), __fmul_rn(M[i][1], M[j][1])), __fmul_rn(M[i][2], M[j][2]));
+    }
+    const float ex = exp2r(__fmul_rn(-logits[k], kLog2e));
+    opacity[k] = __fdiv_rn(1.0f, __fadd_rn(1.0f, ex));
+  }
+}
+
+// Real SH basis of degree <= 3 (Condon-Shortley phase), index l(l+1)+m, for a unit direction.
+__device__ __forceinline__ void sh_basis16(float x, float y, float z, float* Y) {
+  const float xx = x * x, yy = y * y, zz = z * z;
+  Y[0] = 0.28209479177387814f;
+  Y[1] = -0.4886025119029199f * y;
+  Y[2] = 0.4886025119029199f * z;
+  Y[3] = -0.4886025119029199f * x;
+  Y[4] = 1.0925484305920792f * x * y;
+  Y[5] = -1.0925484305920792f * y * z;
+  Y[6] = 0.31539156525252005f * (2.0f * zz - xx - yy);
+  Y[7] = -1.0925484305920792f * x * z;
+  Y[8] = 0.5462742152960396f * (xx - yy);
+  Y[9] = -0.5900435899266435f * y * (3.0f * xx - yy);
+  Y[10] = 2.890611442640554f * x * y * z;
+  Y[11] = -0.4570457994644658f * y * (4.0f * zz - xx - yy);
+  Y[12] = 0.3731763325901154f * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+  Y[13] = -0.4570457994644658f * x * (4.0f * zz - xx - yy);
+  Y[14] = 1.445305721320277f * z * (xx - yy);
+  Y[15] = -0.5900435899266435f * x * (xx - 3.0f * yy);
+}
+
+__global__ void __launch_bounds__(256) project_kernel(const float* __restrict__ means, const float* __restrict__ cov3d,
+                                                      const float* __restrict__ opacity, const float* __restrict__ sh,
+                                                      int64_t n, const potr_camera* __restrict__ cams,
+                                                      const potr_view_info* __restrict__ info, int n_views,
+                                                      potr_raster_config cfg, float4* __restrict__ raster,
+                                                      float* __restrict__ depth_out, uint2* __restrict__ rect_out,
+                                                      uint32_t* __restrict__ touched_out) {
+  const float kA = -0.5f * kLog2e;  // exact: a power-of-two scaling
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const float mu0 = means[k], mu1 = means[n + k], mu2 = means[2 * n + k];
+    const float S00 = cov3d[k], S01 = cov3d[n + k], S02 = cov3d[2 * n + k];
+    const float S11 = cov3d[3 * n + k], S12 = cov3d[4 * n + k], S22 = cov3d[5 * n + k];
+    const float o = opacity[k];
+    const float pthr = log2f(cfg.alpha_min / o) - 0.01f;  // conservative prefilter, see render
+    float shc[48];
+    bool have_sh = false;
+    for (int v = 0; v < n_views; ++v) {
+      const int64_t vk = (int64_t)v * n + k;
+      const potr_camera& cam = cams[v];
+      const float* W = cam.w2c;
+      float t[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        t[i] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(W[i * 4 + 0], mu0), __fmul_rn(W[i * 4 + 1], mu1)),
+                                   __fmul_rn(W[i * 4 + 2], mu2)),
+                         W[i * 4 + 3]);
+      if (!(t[2] > cfg.near_z)) {
+        touched_out[vk] = 0;
+        continue;
+      }
+      const float lim_x = __fmul_rn(1.3f, __fdiv_rn(__fmul_rn(0.5f, (float)cam.width), cam.fx));
+      const float lim_y = __fmul_rn(1.3f, __fdiv_rn(__fmul_rn(0.5f, (float)cam.height), cam.fy));
+      const float txz = __fdiv_rn(t[0], t[2]);
+      const float tyz = __fdiv_rn(t[1], t[2]);
+      const float xc = __fmul_rn(fminf(lim_x, fmaxf(-lim_x, txz)), t[2]);
+      const float yc = __fmul_rn(fminf(lim_y, fmaxf(-lim_y, tyz)), t[2]);
+      const float z2 = __fmul_rn(t[2], t[2]);
+      const float j00 = __fdiv_rn(cam.fx, t[2]);
+      const float j02 = __fdiv_rn(-__fmul_rn(cam.fx, xc), z2);
+      const float j11 = __fdiv_rn(cam.fy, t[2]);
+      const float j12 = __fdiv_rn(-__fmul_rn(cam.fy, yc), z2);
+      float T0[3], T1[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T0[j] = __fadd_rn(__fmul_rn(j00, W[0 * 4 + j]), __fmul_rn(j02, W[2 * 4 + j]));
+        T1[j] = __fadd_rn(__fmul_rn(j11, W[1 * 4 + j]), __fmul_rn(j12, W[2 * 4 + j]));
+      }
+      const float S[3][3] = {{S00, S01, S02}, {S01, S11, S12}, {S02, S12, S22}};
+      float U0[3], U1[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        U0[j] = __fadd_rn(__fadd_rn(__fmul_rn(T0[0], S[0][j]), __fmul_rn(T0[1], S[1][j])), __fmul_rn(T0[2], S[2][j]));
+        U1[j] = __fadd_rn(__fadd_rn(__fmul_rn(T1[0], S[0][j]), __fmul_rn(T1[1], S[1][j])), __fmul_rn(T1[2], S[2][j]));
+      }
+      const float a = __fadd_rn(
+          __fadd_rn(__fadd_rn(__fmul_rn(U0[0], T0[0]), __fmul_rn(U0[1], T0[1])), __fmul_rn(U0[2], T0[2])), cfg.lowpass);
+      const float b = __fadd_rn(__fadd_rn(__fmul_rn(U0[0], T1[0]), __fmul_rn(U0[1], T1[1])), __fmul_rn(U0[2], T1[2]));
+      const float c = __fadd_rn(
+          __fadd_rn(__fadd_rn(__fmul_rn(U1[0], T1[0]), __fmul_rn(U1[1], T1[1])), __fmul_rn(U1[2], T1[2])), cfg.lowpass);
+      const float det = __fsub_rn(__fmul_rn(a, c), __fmul_rn(b, b));
+      if (!(det > 0.0f)) {
+        touched_out[vk] = 0;
+        continue;
+      }
+      const float ca = __fdiv_rn(c, det), cb = __fdiv_rn(-b, det), cc = __fdiv_rn(a, det);
+      const float mid = __fmul_rn(0.5f, __fadd_rn(a, c));
+      const float disc = fmaxf(0.1f, __fsub_rn(__fmul_rn(mid, mid), det));
+      const float lam = __fadd_rn(mid, __fsqrt_rn(disc));
+      const float r = ceilf(__fmul_rn(3.0f, __fsqrt_rn(lam)));
+      const float mx = __fadd_rn(__fmul_rn(cam.fx, txz), cam.cx);
+      const float my = __fadd_rn(__fmul_rn(cam.fy, tyz), cam.cy);
+      const potr_view_info vi = info[v];
+      const float tw = (float)cfg.tile_w, th = (float)cfg.tile_h;
+      const float fx0 = floorf(__fdiv_rn(__fsub_rn(mx, r), tw));
+      const float fx1 = __fadd_rn(floorf(__fdiv_rn(__fadd_rn(mx, r), tw)), 1.0f);
+      const float fy0 = floorf(__fdiv_rn(__fsub_rn(my, r), th));
+      const float fy1 = __fadd_rn(floorf(__fdiv_rn(__fadd_rn(my, r), th)), 1.0f);
+      const int x0 = (int)fminf(fmaxf(fx0, 0.0f), (float)vi.tiles_x);
+      const int x1 = (int)fminf(fmaxf(fx1, 0.0f), (float)vi.tiles_x);
+      const int y0 = (int)fminf(fmaxf(fy0, 0.0f), (float)vi.tiles_y);
+      const int y1 = (int)fminf(fmaxf(fy1, 0.0f), (float)vi.tiles_y);
+      if (!(x1 > x0 && y1 > y0)) {
+        touched_out[vk] = 0;
+        continue;
+      }
+      // SH colour along the camera-to-splat direction (values only: plain fp32 arithmetic)
+      if (!have_sh) {
+#pragma unroll
+        for (int i = 0; i < 48; ++i) shc[i] = __ldg(sh + (int64_t)i * n + k);
+        have_sh = true;
+      }
+      const float cx0 = -(W[0] * W[3] + W[4] * W[7] + W[8] * W[11]);
+      const float cy0 = -(W[1] * W[3] + W[5] * W[7] + W[9] * W[11]);
+      const float cz0 = -(W[2] * W[3] + W[6] * W[7] + W[10] * W[11]);
+      float dx = mu0 - cx0, dy = mu1 - cy0, dz = mu2 - cz0;
+      const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+      dx *= inv; dy *= inv; dz *= inv;
+      float Y[16];
+      sh_basis16(dx, dy, dz, Y);
+      float rgb[3];
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc = fmaf(shc[i * 3 + ch], Y[i], acc);
+        rgb[ch] = fmaxf(acc + 0.5f, 0.0f);
+      }
+      const uint32_t rw = pack_rect_word((uint32_t)x0, (uint32_t)y0, (uint32_t)(x1 - x0));
+      float4* rec = raster + vk * 3;
+      rec[0] = make_float4(mx, my, __fmul_rn(ca, kA), __fmul_rn(cb, -kLog2e));
+      rec[1] = make_float4(__fmul_rn(cc, kA), o, pthr, 0.0f);
+      rec[2] = make_float4(rgb[0], rgb[1], rgb[2], __uint_as_float(rw));
+      depth_out[vk] = t[2];
+      rect_out[vk] = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
+      touched_out[vk] = (uint32_t)((x1 - x0) * (y1 - y0));
+    }
+  }
+}
+
+int grid_for(int64_t n, int block, int max_blocks) {
+  int64_t g = (n + block - 1) / block;
+  if (g > max_blocks) g = max_blocks;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+}  // namespace potr
+
+extern "C" potr_status potr_view_layout(const potr_camera* h_cams, int32_t n_views, const potr_raster_config* cfg,
+                                        potr_view_info* h_info, int64_t* total_tiles, int64_t* total_pixels) {
+  if (!h_cams || !cfg || !h_info || n_views < 1) return POTR_ERR_INVALID_ARGUMENT;
+  if (cfg->tile_w <= 0 || cfg->tile_h <= 0 || cfg->tile_w * cfg->tile_h != potr::kTilePixels)
+    return POTR_ERR_INVALID_ARGUMENT;
+  int64_t tb = 0, pb = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const potr_camera& c = h_cams[v];
+    if (c.width <= 0 || c.height <= 0) return POTR_ERR_INVALID_ARGUMENT;
+    potr_view_info& vi = h_info[v];
+    vi.width = c.width;
+    vi.height = c.height;
+    vi.tiles_x = (c.width + cfg->tile_w - 1) / cfg->tile_w;
+    vi.tiles_y = (c.height + cfg->tile_h - 1) / cfg->tile_h;
+    if (vi.tiles_x > 1023 || vi.tiles_y > 2047) return POTR_ERR_UNSUPPORTED;
+    vi.tile_base = tb;
+    vi.pixel_base = pb;
+    tb += (int64_t)vi.tiles_x * vi.tiles_y;
+    pb += (int64_t)c.width * c.height;
+  }
+  if (total_tiles) *total_tiles = tb;
+  if (total_pixels) *total_pixels = pb;
+  return POTR_OK;
+}
+
+extern "C" potr_status potr_preprocess(const potr_scene* scene, const potr_frame* frame, const potr_raster_config* cfg,
+                                       const potr_views* views, potr_stream_t stream) {
+  if (!scene || !frame || !cfg || !views) return POTR_ERR_INVALID_ARGUMENT;
+  if (scene->n <= 0 || frame->n_views < 1 || !frame->cams || !frame->info) return POTR_ERR_INVALID_ARGUMENT;
+  if (!scene->means || !scene->log_scales || !scene->quats || !scene->opacity_logits || !scene->sh)
+    return POTR_ERR_INVALID_ARGUMENT;
+  if (!views->cov3d || !views->opacity || !views->raster || !views->depth || !views->rect || !views->touched)
+    return POTR_ERR_INVALID_ARGUMENT;
+  if ((reinterpret_cast<uintptr_t>(views->raster) & 15) != 0) return POTR_ERR_INVALID_ARGUMENT;
+  if ((int64_t)frame->n_views * scene->n >= (int64_t)UINT32_MAX) return POTR_ERR_UNSUPPORTED;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t n = scene->n;
+  potr::activate_kernel<<<potr::grid_for(n, 256, 152 * 16), 256, 0, s>>>(scene->log_scales, scene->quats,
+                                                                          scene->opacity_logits, n, views->cov3d,
+                                                                          views->opacity);
+  POTR_CHECK_LAUNCH();
+  potr::project_kernel<<<potr::grid_for(n, 256, 152 * 16), 256, 0, s>>>(
+      scene->means, views->cov3d, views->opacity, scene->sh, n, frame->cams, frame->info, frame->n_views, *cfg,
+      reinterpret_cast<float4*>(views->raster), views->depth, reinterpret_cast<uint2*>(views->rect), views->touched);
+  POTR_CHECK_LAUNCH();
+  return POTR_OK;
+}

@@ -1,0 +1,535 @@
+// raster.cu -- per-tile compositing (paper Section 3, Eqs. 2-4) and the removal-effect pass
+// (Section IV-B), plus the per-splat reduction into dMSE_k and I_k (Section IV-B last
+// equation, Section IV-A).
+//
+// One CTA of 256 threads per (view, tile), one pixel per thread.  The tile's depth-sorted
+// list is walked in batches; each batch's 48-byte raster records are gathered into shared
+// memory with cp.async (16-byte copies), so every pixel of the tile reads them as shared-
+// memory broadcasts.  The per-pair work is plain FP32 ALU: these kernels are bound by
+// FP32 issue, not by HBM (one record gather serves 256 pixels).
+//
+// Removal effect: after the forward walk (c, T_final, n_last per pixel) the same list is
+// walked back to front, recovering T_i = T_{i+1} / (1 - alpha_i) and accumulating the
+// suffix S_{>i} = sum_{j>i} T_j alpha_j c_j, so that
+//     PD_i = alpha_i / (1 - alpha_i) S_{>i} - T_i alpha_i c_i
+// which equals the paper's P_i - P_{i+1} / (1 - alpha_i) + alpha_i / (1 - alpha_i) P_K because
+// P_K - P_{i+1} = S_{>i}; every term is a sum of non-negative numbers, so no prefix sums are
+// subtracted.  dSE_i = sum_ch PD_i (PD_i + 2 (c - c_t)).  Per (tile, splat) the 256 pixel
+// values are summed without atomics: 16 consecutive splats at a time, a warp transpose-sum
+// leaves lane l with its warp's total for splat l, the warp totals of a whole batch go to
+// shared memory, and after one barrier the 8 warp totals are added in warp order.  The order
+// is fixed, so the result does not depend on scheduling.
+#include <atomic>
+
+#include "potr_device.cuh"
+
+namespace potr {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit_wait() {
+  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+// Gather the raster records of list entries [first, first + cnt) into smem[0 .. cnt).
+template <int BATCH>
+__device__ __forceinline__ void stage_batch(float4* smem, const float4* __restrict__ raster,
+                                            const uint32_t* __restrict__ vals, uint32_t first, int cnt) {
+  for (int j = threadIdx.x; j < cnt; j += kThreads) {
+    const uint32_t vk = vals[first + j];
+    const float4* src = raster + (size_t)vk * 3;
+    cp_async16(smem + 3 * j + 0, src + 0);
+    cp_async16(smem + 3 * j + 1, src + 1);
+    cp_async16(smem + 3 * j + 2, src + 2);
+  }
+  cp_async_commit_wait();
+}
+
+struct TileCtx {
+  int64_t tile;
+  int view;
+  potr_view_info vi;
+  int px, py;
+  bool inside;
+  float fx, fy;
+  uint32_t s, e;
+  int tx, ty;
+};
+
+__device__ __forceinline__ TileCtx tile_ctx(const potr_view_info* __restrict__ info, int n_views,
+                                            const uint32_t* __restrict__ ranges, const potr_raster_config& cfg) {
+  TileCtx c;
+  c.tile = blockIdx.x;
+  c.view = view_of_tile(info, n_views, c.tile);
+  c.vi = info[c.view];
+  const int64_t local = c.tile - c.vi.tile_base;
+  c.ty = (int)(local / c.vi.tiles_x);
+  c.tx = (int)(local - (int64_t)c.ty * c.vi.tiles_x);
+  c.px = c.tx * cfg.tile_w + (int)(threadIdx.x % cfg.tile_w);
+  c.py = c.ty * cfg.tile_h + (int)(threadIdx.x / cfg.tile_w);
+  c.inside = c.px < c.vi.width && c.py < c.vi.height;
+  c.fx = (float)c.px + 0.5f;
+  c.fy = (float)c.py + 0.5f;
+  c.s = ranges[2 * c.tile];
+  c.e = ranges[2 * c.tile + 1];
+  return c;
+}
+
+// Forward walk of the tile list (Section 3, Eqs. 2-4).  Returns colour, final T and n_last.
+template <int BATCH>
+__device__ __forceinline__ void forward_walk(float4* smem, const float4* __restrict__ raster,
+                                             const uint32_t* __restrict__ vals, const TileCtx& c,
+                                             const potr_raster_config& cfg, float (&C)[3], float& T,
+                                             uint32_t& last) {
+  C[0] = C[1] = C[2] = 0.0f;
+  T = 1.0f;
+  last = 0;
+  bool done = !c.inside;
+  for (uint32_t base = c.s; base < c.e; base += BATCH) {
+    if (__syncthreads_and(done)) break;  // also guards the shared-memory batch
+    const int cnt = (int)min((uint32_t)BATCH, c.e - base);
+    stage_batch<BATCH>(smem, raster, vals, base, cnt);
+    __syncthreads();
+    if (done) continue;
+    for (int j = 0; j < cnt; ++j) {
+      const float4 r0 = smem[3 * j];
+      const float4 r1 = smem[3 * j + 1];
+      const float p = pair_exponent(r0.z, r0.w, r1.x, __fsub_rn(c.fx, r0.x), __fsub_rn(c.fy, r0.y));
+      if (p < r1.z) continue;  // alpha < alpha_min certainly (prefilter with margin)
+      const float a = pair_alpha(r1.y, p, cfg.alpha_max);
+      if (a < cfg.alpha_min) continue;
+      const float Tn = trans_next(a, T);
+      if (Tn < cfg.t_min) {
+        done = true;
+        break;
+      }
+      const float4 r2 = smem[3 * j + 2];
+      const float w = a * T;
+      C[0] = fmaf(w, r2.x, C[0]);
+      C[1] = fmaf(w, r2.y, C[1]);
+      C[2] = fmaf(w, r2.z, C[2]);
+      T = Tn;
+      last = base - c.s + (uint32_t)j + 1;
+    }
+  }
+}
+
+template <int BATCH>
+__global__ void __launch_bounds__(kThreads) render_kernel(const float4* __restrict__ raster,
+                                                          const uint32_t* __restrict__ vals,
+                                                          const uint32_t* __restrict__ ranges,
+                                                          const potr_view_info* __restrict__ info, int n_views,
+                                                          potr_raster_config cfg, float* __restrict__ images,
+                                                          float* __restrict__ t_final, uint32_t* __restrict__ n_last) {
+  extern __shared__ float4 smem[];
+  const TileCtx c = tile_ctx(info, n_views, ranges, cfg);
+  float C[3], T;
+  uint32_t last;
+  forward_walk<BATCH>(smem, raster, vals, c, cfg, C, T, last);
+  if (!c.inside) return;
+  const int64_t pix = c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
+  const int64_t plane = (int64_t)c.vi.width * c.vi.height;
+  if (images) {
+    float* im = images + 3 * c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
+    im[0] = C[0];
+    im[plane] = C[1];
+    im[2 * plane] = C[2];
+  }
+  if (t_final) t_final[pix] = T;
+  if (n_last) n_last[pix] = last;
+}
+
+// Lanes l and l ^ 16 both receive the sum over all 32 lanes of v[l & 15] (fixed order):
+// a transpose-sum inside each 16-lane half, then one exchange between the halves.
+__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 8; off >= 1; off >>= 1) {
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < off; ++i) {
+      const float send = upper ? v[i] : v[i + off];
+      const float keep = upper ? v[i + off] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+}
+
+// Emission slot of the instance of record (r1, r2) that lies in tile (tx, ty).
+__device__ __forceinline__ uint32_t emission_slot(const float4& r1, const float4& r2, int tx, int ty) {
+  const uint32_t off = __float_as_uint(r1.w);
+  const uint32_t rw = __float_as_uint(r2.w);
+  const uint32_t x0 = rw & 0x7ffu, y0 = (rw >> 11) & 0x7ffu, w = rw >> 22;
+  return off + ((uint32_t)ty - y0) * w + ((uint32_t)tx - x0);
+}
+
+constexpr int kChunk = 16;  // splats per warp transpose-sum
+
+template <int BATCH, bool IMP>
+constexpr size_t removal_smem_bytes() {
+  return sizeof(float4) * 3 * BATCH + sizeof(float) * kWarps * BATCH * (IMP ? 2 : 1);
+}
+
+template <int BATCH, bool IMP>
+__global__ void __launch_bounds__(kThreads) removal_kernel(const float4* __restrict__ raster,
+                                                           const uint32_t* __restrict__ vals,
+                                                           const uint32_t* __restrict__ ranges,
+                                                           const potr_view_info* __restrict__ info, int n_views,
+                                                           potr_raster_config cfg, const float* __restrict__ targets,
+                                                           float* __restrict__ images, float* __restrict__ inst_dse,
+                                                           float* __restrict__ inst_imp) {
+  extern __shared__ float4 dyn[];
+  float4* smem = dyn;                                               // [BATCH][3] raster records
+  float* red_d = reinterpret_cast<float*>(dyn + 3 * BATCH);         // [kWarps][BATCH] warp sums of dSE
+  float* red_i = red_d + kWarps * BATCH;                            // [kWarps][BATCH] warp sums of T alpha
+  __shared__ uint32_t max_last_w[kWarps];
+  const TileCtx c = tile_ctx(info, n_views, ranges, cfg);
+  float C[3], T;
+  uint32_t last;
+  forward_walk<BATCH>(smem, raster, vals, c, cfg, C, T, last);
+
+  float e2[3] = {0.0f, 0.0f, 0.0f};  // 2 (c - c_t)
+  if (c.inside) {
+    const int64_t plane = (int64_t)c.vi.width * c.vi.height;
+    const int64_t o = 3 * c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) e2[ch] = 2.0f * (C[ch] - targets[o + ch * plane]);
+    if (images) {
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) images[o + ch * plane] = C[ch];
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t warp_last = __reduce_max_sync(0xffffffffu, last);
+  if (lane == 0) max_last_w[warp] = warp_last;
+  __syncthreads();
+  uint32_t max_last = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) max_last = max(max_last, max_last_w[w]);
+
+  // Back-to-front over list positions [0, max_last): T_i = T_{i+1} / (1 - alpha_i),
+  // S = sum of T_j alpha_j c_j over the composited j > i.
+  float S[3] = {0.0f, 0.0f, 0.0f};
+  for (uint32_t top = max_last; top > 0;) {
+    const uint32_t lo = top > (uint32_t)BATCH ? top - BATCH : 0u;
+    const int cnt = (int)(top - lo);
+    __syncthreads();  // previous batch (records and warp sums) fully consumed
+    stage_batch<BATCH>(smem, raster, vals, c.s + lo, cnt);
+    __syncthreads();
+    for (int hi = cnt; hi > 0; hi -= kChunk) {
+      const int clo = hi > kChunk ? hi - kChunk : 0;
+      float sd = 0.0f, si = 0.0f;
+      if (lo + (uint32_t)clo < warp_last) {  // warp-uniform: some lane may composite here
+        float d[kChunk], im[kChunk];
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) {
+          d[u] = 0.0f;
+          if (IMP) im[u] = 0.0f;
+          const int j = hi - 1 - u;
+          if (j >= clo && lo + (uint32_t)j < last) {
+            const float4 r0 = smem[3 * j];
+            const float4 r1 = smem[3 * j + 1];
+            const float p = pair_exponent(r0.z, r0.w, r1.x, __fsub_rn(c.fx, r0.x), __fsub_rn(c.fy, r0.y));
+            if (p >= r1.z) {
+              const float a = pair_alpha(r1.y, p, cfg.alpha_max);
+              if (a >= cfg.alpha_min) {
+                const float4 r2 = smem[3 * j + 2];
+                const float rcp = __fdividef(1.0f, 1.0f - a);
+                T = T * rcp;                  // T_i = T_{i+1} / (1 - alpha_i)
+                const float w = a * T;        // T_i alpha_i
+                const float ratio = a * rcp;  // alpha_i / (1 - alpha_i)
+                const float wc0 = w * r2.x, wc1 = w * r2.y, wc2 = w * r2.z;
+                const float pd0 = fmaf(ratio, S[0], -wc0);
+                const float pd1 = fmaf(ratio, S[1], -wc1);
+                const float pd2 = fmaf(ratio, S[2], -wc2);
+                float dse = pd0 * (pd0 + e2[0]);
+                dse = fmaf(pd1, pd1 + e2[1], dse);
+                dse = fmaf(pd2, pd2 + e2[2], dse);
+                S[0] += wc0;
+                S[1] += wc1;
+                S[2] += wc2;
+                d[u] = dse;
+                if (IMP) im[u] = w;
+                any = true;
+              }
+            }
+          }
+        }
+        if (__any_sync(0xffffffffu, any)) {
+          sd = warp_transpose_sum16(d);
+          if (IMP) si = warp_transpose_sum16(im);
+        }
+      }
+      if (lane < kChunk) {
+        const int j = hi - 1 - lane;
+        if (j >= clo) {
+          red_d[warp * BATCH + j] = sd;
+          if (IMP) red_i[warp * BATCH + j] = si;
+        }
+      }
+    }
+    __syncthreads();
+    // per (tile, splat): the 8 warp sums in warp order
+    for (int j = threadIdx.x; j < cnt; j += kThreads) {
+      float sd = 0.0f, si = 0.0f;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) {
+        sd += red_d[w * BATCH + j];
+        if (IMP) si += red_i[w * BATCH + j];
+      }
+      if (sd != 0.0f || (IMP && si != 0.0f)) {
+        const uint32_t slot = emission_slot(smem[3 * j + 1], smem[3 * j + 2], c.tx, c.ty);
+        inst_dse[slot] = sd;
+        if (IMP) inst_imp[slot] = si;
+      }
+    }
+    top = lo;
+  }
+}
+
+// Per splat k: dSSE_k(v) = sum over its emission slots (binary64, emission order), then
+// dmse[k] += dSSE_k(v) / (3 P_v) / N views in order; importance likewise with / P_v.
+__global__ void __launch_bounds__(256) splat_reduce_kernel(const uint32_t* __restrict__ touched,
+                                                           const uint32_t* __restrict__ offsets,
+                                                           const uint32_t* __restrict__ n_inst, int64_t capacity,
+                                                           const float* __restrict__ inst_dse,
+                                                           const float* __restrict__ inst_imp, int64_t n, int n_views,
+                                                           const potr_view_info* __restrict__ info, double n_total,
+                                                           double* __restrict__ dmse, double* __restrict__ importance,
+                                                           double* __restrict__ dsse_view) {
+  if ((int64_t)*n_inst > capacity) return;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    double acc_d = dmse ? dmse[k] : 0.0;
+    double acc_i = importance ? importance[k] : 0.0;
+    for (int v = 0; v < n_views; ++v) {
+      const int64_t vk = (int64_t)v * n + k;
+      const uint32_t cnt = touched[vk];
+      double sd = 0.0, si = 0.0;
+      if (cnt) {
+        const uint32_t off = offsets[vk];
+        for (uint32_t i = 0; i < cnt; ++i) sd += (double)inst_dse[off + i];
+        if (inst_imp)
+          for (uint32_t i = 0; i < cnt; ++i) si += (double)inst_imp[off + i];
+      }
+      const double P = (double)info[v].width * (double)info[v].height;
+      acc_d += sd / (3.0 * P) / n_total;
+      acc_i += si / P / n_total;
+      if (dsse_view) dsse_view[vk] = sd;
+    }
+    if (dmse) dmse[k] = acc_d;
+    if (importance) importance[k] = acc_i;
+  }
+}
+
+template <int BATCH>
+cudaError_t launch_render(const potr_views* views, const potr_frame* frame, const potr_raster_config& cfg,
+                          const uint32_t* vals, const uint32_t* ranges, float* images, float* t_final,
+                          uint32_t* n_last, cudaStream_t s) {
+  const size_t smem = sizeof(float4) * 3 * BATCH;
+  render_kernel<BATCH><<<(unsigned)frame->total_tiles, kThreads, smem, s>>>(
+      reinterpret_cast<const float4*>(views->raster), vals, ranges, frame->info, frame->n_views, cfg, images, t_final,
+      n_last);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+template <int BATCH, bool IMP>
+cudaError_t launch_removal(const potr_views* views, const potr_frame* frame, const potr_raster_config& cfg,
+                           const uint32_t* vals, const uint32_t* ranges, const float* targets, float* images,
+                           float* inst_dse, float* inst_imp, cudaStream_t s) {
+  constexpr size_t smem = removal_smem_bytes<BATCH, IMP>();
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(removal_kernel<BATCH, IMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  removal_kernel<BATCH, IMP><<<(unsigned)frame->total_tiles, kThreads, smem, s>>>(
+      reinterpret_cast<const float4*>(views->raster), vals, ranges, frame->info, frame->n_views, cfg, targets, images,
+      inst_dse, inst_imp);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+bool valid_cfg(const potr_raster_config* cfg) {
+  if (!cfg) return false;
+  if (cfg->tile_w * cfg->tile_h != kTilePixels) return false;
+  if (!((cfg->tile_w == 16 && cfg->tile_h == 16) || (cfg->tile_w == 8 && cfg->tile_h == 32) ||
+        (cfg->tile_w == 32 && cfg->tile_h == 8)))
+    return false;
+  return cfg->batch == 128 || cfg->batch == 256 || cfg->batch == 512;
+}
+
+}  // namespace
+}  // namespace potr
+
+extern "C" potr_status potr_render(const potr_views* views, const potr_frame* frame, const potr_raster_config* cfg,
+                                   int64_t n, const uint32_t* d_vals, const uint32_t* d_tile_ranges, float* d_images,
+                                   float* d_t_final, uint32_t* d_n_last, potr_stream_t stream) {
+  using namespace potr;
+  if (!views || !frame || !valid_cfg(cfg) || !d_vals || !d_tile_ranges || !views->raster || !frame->info)
+    return POTR_ERR_INVALID_ARGUMENT;
+  if (n <= 0 || frame->n_views < 1 || frame->total_tiles <= 0 || frame->total_tiles > 0x7fffffffll)
+    return POTR_ERR_INVALID_ARGUMENT;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  switch (cfg->batch) {
+    case 128: e = launch_render<128>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, s); break;
+    case 256: e = launch_render<256>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, s); break;
+    default: e = launch_render<512>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, s); break;
+  }
+  return e == cudaSuccess ? POTR_OK : POTR_ERR_CUDA;
+}
+
+extern "C" potr_status potr_removal_effect(const potr_views* views, const potr_frame* frame,
+                                           const potr_raster_config* cfg, int64_t n, const uint32_t* d_vals,
+                                           const uint32_t* d_tile_ranges, const float* d_targets, int32_t n_views_total,
+                                           int64_t instance_capacity, float* d_inst_dse, float* d_inst_imp,
+                                           double* d_dmse, double* d_importance, double* d_dsse_view, float* d_images,
+                                           potr_stream_t stream) {
+  using namespace potr;
+  if (!views || !frame || !valid_cfg(cfg) || !d_vals || !d_tile_ranges || !d_targets || !d_inst_dse)
+    return POTR_ERR_INVALID_ARGUMENT;
+  if (!views->raster || !views->touched || !views->offsets || !views->n_instances || !frame->info)
+    return POTR_ERR_INVALID_ARGUMENT;
+  if (n <= 0 || frame->n_views < 1 || n_views_total < 1 || instance_capacity <= 0) return POTR_ERR_INVALID_ARGUMENT;
+  if (frame->total_tiles <= 0 || frame->total_tiles > 0x7fffffffll) return POTR_ERR_INVALID_ARGUMENT;
+  if (d_importance && !d_inst_imp) return POTR_ERR_INVALID_ARGUMENT;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(d_inst_dse, 0, sizeof(float) * (size_t)instance_capacity, s) != cudaSuccess) return POTR_ERR_CUDA;
+  if (d_inst_imp && cudaMemsetAsync(d_inst_imp, 0, sizeof(float) * (size_t)instance_capacity, s) != cudaSuccess)
+    return POTR_ERR_CUDA;
+  const bool imp = d_inst_imp != nullptr;
+  cudaError_t e;
+  switch (cfg->batch * 2 + (imp ? 1 : 0)) {
+    case 256: e = launch_removal<128, false>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, s); break;
+    case 257: e = launch_removal<128, true>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, s); break;
+    case 512: e = launch_removal<256, false>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, s); break;
+    case 513: e = launch_removal<256, true>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, s); break;
+    case 1024: e = launch_removal<512, false>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, s); break;
+    default: e = launch_removal<512, true>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, s); break;
+  }
+  if (e != cudaSuccess) return POTR_ERR_CUDA;
+  if (d_dmse || d_importance || d_dsse_view) {
+    int64_t g = (n + 255) / 256;
+    if (g > 152 * 32) g = 152 * 32;
+    splat_reduce_kernel<<<(unsigned)g, 256, 0, s>>>(views->touched, views->offsets, views->n_instances,
+                                                     instance_capacity, d_inst_dse, d_inst_imp, n, frame->n_views,
+                                                     frame->info, (double)n_views_total, d_dmse, d_importance,
+                                                     d_dsse_view);
+    note_launches(1);
+    if (cudaGetLastError() != cudaSuccess) return POTR_ERR_CUDA;
+  }
+  return POTR_OK;
+}
+
+namespace potr {
+namespace {
+
+// Exact pair counts of the forward walk and of the back-to-front walk of the removal pass:
+// c[0] pairs examined forward, c[1] of those passing the prefilter, c[2] composited,
+// c[3] positions walked back to front (sum of n_last), c[4] of those passing the prefilter.
+template <int BATCH>
+__global__ void __launch_bounds__(kThreads) pair_stats_kernel(const float4* __restrict__ raster,
+                                                              const uint32_t* __restrict__ vals,
+                                                              const uint32_t* __restrict__ ranges,
+                                                              const potr_view_info* __restrict__ info, int n_views,
+                                                              potr_raster_config cfg,
+                                                              unsigned long long* __restrict__ counts) {
+  extern __shared__ float4 smem[];
+  __shared__ unsigned long long red[5][kWarps];
+  const TileCtx c = tile_ctx(info, n_views, ranges, cfg);
+  float T = 1.0f;
+  uint32_t n_ex = 0, n_pass = 0, n_comp = 0, last = 0, pass_at_last = 0;
+  bool done = !c.inside;
+  for (uint32_t base = c.s; base < c.e; base += BATCH) {
+    if (__syncthreads_and(done)) break;
+    const int cnt = (int)min((uint32_t)BATCH, c.e - base);
+    stage_batch<BATCH>(smem, raster, vals, base, cnt);
+    __syncthreads();
+    if (done) continue;
+    for (int j = 0; j < cnt; ++j) {
+      const float4 r0 = smem[3 * j];
+      const float4 r1 = smem[3 * j + 1];
+      ++n_ex;
+      const float p = pair_exponent(r0.z, r0.w, r1.x, __fsub_rn(c.fx, r0.x), __fsub_rn(c.fy, r0.y));
+      if (p < r1.z) continue;
+      ++n_pass;
+      const float a = pair_alpha(r1.y, p, cfg.alpha_max);
+      if (a < cfg.alpha_min) continue;
+      const float Tn = trans_next(a, T);
+      if (Tn < cfg.t_min) {
+        done = true;
+        break;
+      }
+      T = Tn;
+      ++n_comp;
+      last = base - c.s + (uint32_t)j + 1;
+      pass_at_last = n_pass;
+    }
+  }
+  const uint32_t v[5] = {n_ex, n_pass, n_comp, last, pass_at_last};
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    unsigned long long x = v[q];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[q][warp] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    unsigned long long x = 0;
+    for (int w = 0; w < kWarps; ++w) x += red[threadIdx.x][w];
+    atomicAdd(counts + threadIdx.x, x);
+  }
+}
+
+std::atomic<unsigned long long> g_launches{0};
+
+}  // namespace
+
+void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+}  // namespace potr
+
+extern "C" potr_status potr_pair_stats(const potr_views* views, const potr_frame* frame, const potr_raster_config* cfg,
+                                       int64_t n, const uint32_t* d_vals, const uint32_t* d_tile_ranges,
+                                       uint64_t* d_counts, potr_stream_t stream) {
+  using namespace potr;
+  if (!views || !frame || !valid_cfg(cfg) || !d_vals || !d_tile_ranges || !d_counts || !views->raster || !frame->info)
+    return POTR_ERR_INVALID_ARGUMENT;
+  if (n <= 0 || frame->total_tiles <= 0 || frame->total_tiles > 0x7fffffffll) return POTR_ERR_INVALID_ARGUMENT;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(d_counts, 0, 5 * sizeof(uint64_t), s) != cudaSuccess) return POTR_ERR_CUDA;
+  pair_stats_kernel<256><<<(unsigned)frame->total_tiles, kThreads, sizeof(float4) * 3 * 256, s>>>(
+      reinterpret_cast<const float4*>(views->raster), d_vals, d_tile_ranges, frame->info, frame->n_views, *cfg,
+      reinterpret_cast<unsigned long long*>(d_counts));
+  POTR_CHECK_LAUNCH();
+  return POTR_OK;
+}
+
+extern "C" uint64_t potr_launch_count(void) { return potr::g_launches.load(); }
+
+extern "C" const char* potr_status_string(potr_status status) {
+  switch (status) {
+    case POTR_OK: return "ok";
+    case POTR_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case POTR_ERR_CUDA: return "CUDA launch or runtime error";
+    case POTR_ERR_CAPACITY: return "tile-instance capacity exceeded";
+    case POTR_ERR_TIMEOUT: return "bounded device wait ran out";
+    case POTR_ERR_NUMERIC: return "non-finite input";
+    case POTR_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+extern "C" int32_t potr_version(void) { return 100; }

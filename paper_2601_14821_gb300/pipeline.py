@@ -1,0 +1,145 @@
+"""Frame-level driver of the C ABI: buffer ownership (torch device memory), instance-capacity
+planning, and the preprocess -> bin_sort -> render / removal_effect chain on one stream.
+
+A *frame* is a set of views processed together (one view for the per-view form, many for
+the batched form).  ``RemovalEffectFrame`` holds every buffer the chain needs, so a step is a
+fixed sequence of asynchronous C calls that can be replayed or captured in a CUDA graph.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _binding as B
+
+SCENE_KEYS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+def scene_to_device(scene, device="cuda") -> dict:
+    """synth.Scene (numpy SoA planes) -> dict of contiguous float32 device tensors."""
+    return {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k), np.float32)).to(device) for k in SCENE_KEYS}
+
+
+def scene_struct(sc: dict) -> B.Scene:
+    return B.Scene(sc["means"].data_ptr(), sc["log_scales"].data_ptr(), sc["quats"].data_ptr(),
+                   sc["opacity_logits"].data_ptr(), sc["sh"].data_ptr(), int(sc["means"].shape[-1]))
+
+
+class RemovalEffectFrame:
+    """All device buffers for one frame (scene x views) and the C calls over them."""
+
+    def __init__(self, scene: dict, cams_rec: np.ndarray, device="cuda", capacity: int | None = None,
+                 with_importance: bool = True, **cfg):
+        self.device = torch.device(device)
+        self.scene = scene
+        self.scene_c = scene_struct(scene)
+        self.n = int(scene["means"].shape[-1])
+        self.cams_rec = np.ascontiguousarray(cams_rec, np.float32).reshape(-1, 18)
+        self.n_views = self.cams_rec.shape[0]
+        self.cfg = B.make_config(**cfg)
+        info, self.total_tiles, self.total_pixels = B.potr_view_layout(self.cams_rec, self.cfg)
+        self.info_np = info.view(np.dtype([("width", "<i4"), ("height", "<i4"), ("tiles_x", "<i4"),
+                                           ("tiles_y", "<i4"), ("tile_base", "<i8"), ("pixel_base", "<i8")]))
+        dev = self.device
+        self.d_cams = torch.from_numpy(self.cams_rec.copy()).to(dev)
+        self.d_info = torch.from_numpy(info.copy()).to(dev)
+        self.frame = B.Frame(self.d_cams.data_ptr(), self.d_info.data_ptr(), self.n_views, self.total_tiles,
+                             self.total_pixels)
+        vn = self.n_views * self.n
+        i32 = torch.int32
+        self.cov3d = torch.empty(6 * self.n, dtype=torch.float32, device=dev)
+        self.opacity = torch.empty(self.n, dtype=torch.float32, device=dev)
+        self.raster = torch.empty(vn * 12, dtype=torch.float32, device=dev)
+        self.depth = torch.empty(vn, dtype=torch.float32, device=dev)
+        self.rect = torch.empty(2 * vn, dtype=i32, device=dev)
+        self.touched = torch.empty(vn, dtype=i32, device=dev)
+        self.offsets = torch.empty(vn, dtype=i32, device=dev)
+        self.n_instances = torch.zeros(1, dtype=i32, device=dev)
+        self.status = torch.zeros(2, dtype=torch.int64, device=dev)
+        self.views = B.Views(self.cov3d.data_ptr(), self.opacity.data_ptr(), self.raster.data_ptr(),
+                             self.depth.data_ptr(), self.rect.data_ptr(), self.touched.data_ptr(),
+                             self.offsets.data_ptr(), self.n_instances.data_ptr())
+        self.ranges = torch.empty(2 * self.total_tiles, dtype=i32, device=dev)
+        self.with_importance = with_importance
+        self.capacity = 0
+        self._alloc(capacity if capacity else 1)
+
+    # -------------------------------------------------------------------------------------
+    def _alloc(self, capacity: int):
+        dev = self.device
+        self.capacity = int(capacity)
+        self.keys = torch.empty(self.capacity, dtype=torch.int64, device=dev)
+        self.vals = torch.empty(self.capacity, dtype=torch.int32, device=dev)
+        ws = B.potr_bin_sort_workspace_size(self.n, self.n_views, self.total_tiles, self.capacity)
+        self.ws = torch.empty(ws, dtype=torch.uint8, device=dev)
+        self.inst_dse = torch.empty(self.capacity, dtype=torch.float32, device=dev)
+        self.inst_imp = torch.empty(self.capacity, dtype=torch.float32, device=dev) if self.with_importance else None
+
+    def plan(self, slack: float = 1.05) -> int:
+        """Run preprocess + binning once, grow the instance capacity to fit, return the count."""
+        self.preprocess()
+        self.bin_sort()
+        torch.cuda.synchronize(self.device)
+        code, need = self.status.tolist()
+        if code == B.POTR_ERR_CAPACITY:
+            self._alloc(max(int(need * slack) + 1024, 1024))
+            self.bin_sort()
+            torch.cuda.synchronize(self.device)
+            code, need = self.status.tolist()
+        if code != 0:
+            raise B.PotrError("potr_bin_sort (device)", int(code))
+        return self.instance_count()
+
+    def instance_count(self) -> int:
+        return int(self.n_instances.cpu().numpy().view(np.uint32)[0])
+
+    # -------------------------------------------------------------------------------------
+    def preprocess(self, stream=None):
+        B.potr_preprocess(self.scene_c, self.frame, self.cfg, self.views, stream)
+
+    def bin_sort(self, stream=None):
+        self.status.zero_()
+        B.potr_bin_sort(self.views, self.frame, self.cfg, self.n, self.capacity, self.keys, self.vals, self.ranges,
+                        self.status, self.ws, stream)
+
+    def render(self, images=None, t_final=None, n_last=None, stream=None):
+        B.potr_render(self.views, self.frame, self.cfg, self.n, self.vals, self.ranges, images, t_final, n_last, stream)
+
+    def removal_effect(self, targets, dmse, importance=None, n_views_total=None, dsse_view=None, images=None,
+                       stream=None):
+        B.potr_removal_effect(self.views, self.frame, self.cfg, self.n, self.vals, self.ranges, targets,
+                              int(n_views_total or self.n_views), self.capacity, self.inst_dse,
+                              self.inst_imp if importance is not None else None, dmse, importance, dsse_view,
+                              images, stream)
+
+    def pair_stats(self, stream=None) -> dict:
+        """Exact pair counts of the forward and removal walks (see potr_pair_stats)."""
+        counts = torch.zeros(5, dtype=torch.int64, device=self.device)
+        B.potr_pair_stats(self.views, self.frame, self.cfg, self.n, self.vals, self.ranges, counts, stream)
+        c = [int(x) for x in counts.cpu().tolist()]
+        return dict(examined=c[0], passed=c[1], composited=c[2], back_positions=c[3], back_passed=c[4])
+
+    def step(self, targets, dmse, importance=None, n_views_total=None, stream=None):
+        """One pass of the whole path: preprocess, bin + sort, removal effect + per-splat reduce."""
+        self.preprocess(stream)
+        self.bin_sort(stream)
+        self.removal_effect(targets, dmse, importance, n_views_total, stream=stream)
+
+    def image_buffer(self):
+        return torch.empty(3 * self.total_pixels, dtype=torch.float32, device=self.device)
+
+    def pixel_buffer(self, dtype=torch.float32):
+        return torch.empty(self.total_pixels, dtype=dtype, device=self.device)
+
+    def view_image(self, flat: torch.Tensor, v: int) -> torch.Tensor:
+        """[3, H, W] view of view v inside a packed per-frame image buffer."""
+        vi = self.info_np[v]
+        h, w, pb = int(vi["height"]), int(vi["width"]), int(vi["pixel_base"])
+        return flat[3 * pb: 3 * pb + 3 * h * w].view(3, h, w)
+
+    def view_pixels(self, flat: torch.Tensor, v: int) -> torch.Tensor:
+        vi = self.info_np[v]
+        h, w, pb = int(vi["height"]), int(vi["width"]), int(vi["pixel_base"])
+        return flat[pb: pb + h * w].view(h, w)

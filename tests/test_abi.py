@@ -1,0 +1,58 @@
+"""The C-ABI library loads without a GPU and exports every entry point include/potr.h declares."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "potr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(potr_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpotr():
+    from paper_2601_14821_gb300 import build
+
+    build.build()
+    return ctypes.CDLL(build.LIB)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("potr_preprocess", "potr_bin_sort", "potr_render", "potr_removal_effect"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(libpotr):
+    for name in declared_functions():
+        assert hasattr(libpotr, name), name
+
+
+def test_binding_covers_every_symbol():
+    from paper_2601_14821_gb300 import _binding
+
+    assert set(declared_functions()) <= set(_binding.SIGNATURES)
+
+
+def test_host_only_layout_and_status_strings(libpotr):
+    import numpy as np
+
+    import synth
+    from paper_2601_14821_gb300 import _binding as B
+
+    assert B.status_string(B.POTR_ERR_CAPACITY) == "tile-instance capacity exceeded"
+    cams = [synth.look_at_camera((0, 0, -3), 100, 75), synth.look_at_camera((0, 0, -3), 1920, 1080)]
+    info, tt, tp = B.potr_view_layout(synth.cameras_to_array(cams), B.make_config())
+    rec = info.view(np.int32).reshape(2, 8)
+    assert tuple(rec[0, :4]) == (100, 75, 7, 5)
+    assert tuple(rec[1, :4]) == (1920, 1080, 120, 68)
+    assert tt == 35 + 120 * 68 and tp == 7500 + 1920 * 1080
+    with pytest.raises(B.PotrError):
+        B.potr_view_layout(synth.cameras_to_array(cams), B.make_config(tile_w=16, tile_h=8))
+    ws = B.potr_bin_sort_workspace_size(1000, 2, tt, 100_000)
+    assert ws >= 12 * 100_000
