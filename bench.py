@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--views", type=int, default=0, help="use only the first V views (profiling cases)")
+    ap.add_argument("--only-batched", action="store_true", help="time the batched frame only (profiling cases)")
     return ap.parse_args()
 
 
@@ -163,6 +165,8 @@ def run_ours(args):
     D.init("nccl")
     dev = torch.device("cuda", local)
     w = synth.workload(WORKLOAD)
+    if args.views:
+        w.cameras = w.cameras[: args.views]
     n_views = len(w.cameras)
     cams_rec = synth.cameras_to_array(w.cameras)
     scene_d = scene_to_device(w.scene, dev)
@@ -212,6 +216,14 @@ def run_ours(args):
     stage_ms = stage.mean(axis=0)
     ms_step = ms_total / K
     value = world * n_views * K / (ms_total / 1e3)
+
+    if args.only_batched:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "views/s", "views": n_views,
+                              "stage_ms": {"preprocess": stage_ms[0], "bin_sort": stage_ms[1],
+                                           "removal_effect": stage_ms[2]}, "instances": int(n_inst),
+                              "gpu_launches": int(launches), "profiling_case": True}))
+        return
 
     # ---- CUDA graph of one whole step, replayed
     graph_vps = None
