@@ -46,7 +46,8 @@ enum {
   POTR_ERR_CAPACITY = 3, /* device: more tile instances than instance_capacity */
   POTR_ERR_TIMEOUT = 4,  /* device: a bounded wait ran out */
   POTR_ERR_NUMERIC = 5,
-  POTR_ERR_UNSUPPORTED = 6
+  POTR_ERR_UNSUPPORTED = 6,
+  POTR_ERR_TOO_LARGE = 7 /* a size exceeds potr_bin_sort_static's fixed scratch */
 };
 
 /* Device-side status word; zero it before the calls that may write it. */
@@ -228,6 +229,23 @@ POTR_API potr_status potr_removal_effect(const potr_views* views, const potr_fra
 POTR_API potr_status potr_pair_stats(const potr_views* views, const potr_frame* frame, const potr_raster_config* cfg,
                                      int64_t n, const uint32_t* d_vals, const uint32_t* d_tile_ranges,
                                      uint64_t* d_counts, potr_stream_t stream);
+
+/*
+ * potr_bin_sort without a workspace argument, for callers that cannot allocate device
+ * memory (no counterpart in the paper).  Same inputs, outputs and device-status behaviour as
+ * potr_bin_sort; the scratch it needs lives in a 56 MiB array inside the library, held by
+ * every GPU that loads the library until the process exits.  Limits: instance_capacity <=
+ * POTR_STATIC_MAX_INSTANCES and n * n_views <= POTR_STATIC_MAX_VIEW_SPLATS, otherwise it
+ * returns POTR_ERR_TOO_LARGE and enqueues nothing.  The first call on a device looks up the
+ * array's device address (make it before any stream capture).  Calls share the array: calls
+ * that overlap on the GPU race, so serialise them.  It allocates nothing.
+ */
+#define POTR_STATIC_MAX_INSTANCES 4194304LL
+#define POTR_STATIC_MAX_VIEW_SPLATS 16777216LL
+POTR_API potr_status potr_bin_sort_static(const potr_views* views, const potr_frame* frame,
+                                          const potr_raster_config* cfg, int64_t n, int64_t instance_capacity,
+                                          uint64_t* d_keys, uint32_t* d_vals, uint32_t* d_tile_ranges,
+                                          potr_device_status* d_status, potr_stream_t stream);
 
 /* Number of kernels the library has launched in this process (host-side counter). */
 POTR_API uint64_t potr_launch_count(void);

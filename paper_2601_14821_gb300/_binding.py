@@ -24,6 +24,9 @@ POTR_ERR_CAPACITY = 3
 POTR_ERR_TIMEOUT = 4
 POTR_ERR_NUMERIC = 5
 POTR_ERR_UNSUPPORTED = 6
+POTR_ERR_TOO_LARGE = 7
+POTR_STATIC_MAX_INSTANCES = 4194304
+POTR_STATIC_MAX_VIEW_SPLATS = 16777216
 
 
 class PotrError(RuntimeError):
@@ -83,6 +86,8 @@ SIGNATURES = {
                                    _I32, _I64, _P, _P, _P, _P, _P, _P, _P]),
     "potr_pair_stats": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _P, _P, _P, _P]),
     "potr_launch_count": (C.c_uint64, []),
+    "potr_bin_sort_static": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _I64, _P, _P,
+                                    _P, _P, _P]),
 }
 
 
@@ -192,3 +197,11 @@ def potr_pair_stats(views: Views, frame: Frame, cfg: RasterConfig, n: int, vals,
 
 def potr_launch_count() -> int:
     return int(lib().potr_launch_count())
+
+
+def potr_bin_sort_static(views: Views, frame: Frame, cfg: RasterConfig, n: int, capacity: int, keys, vals, ranges,
+                         status, stream=None):
+    """potr_bin_sort with the library's fixed scratch instead of a caller workspace."""
+    _check("potr_bin_sort_static", lib().potr_bin_sort_static(C.byref(views), C.byref(frame), C.byref(cfg), n,
+                                                              capacity, ptr(keys), ptr(vals), ptr(ranges),
+                                                              ptr(status), stream_handle(stream)))
