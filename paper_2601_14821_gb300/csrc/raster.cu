@@ -82,9 +82,46 @@ __device__ __forceinline__ TileCtx tile_ctx(const potr_view_info* __restrict__ i
   return c;
 }
 
+// Bit w of the result is set when the splat of record (r0, r1) may pass the opacity
+// prefilter (log2 G >= r1.z) at some pixel centre of warp w's rows of this tile.  For each
+// pixel row y the exponent A u^2 + B u v + C v^2 (v = y - my fixed) is a concave parabola in
+// u = x - mx, maximised over the row's span of pixel centres; a pair whose warp bit is clear
+// therefore has alpha < alpha_min at every pixel of that warp and is skipped without changing
+// any decision.  The margin covers binary32 rounding of both evaluations.
+__device__ __forceinline__ uint32_t warp_mask(const float4& r0, const float4& r1, const TileCtx& c,
+                                              const potr_raster_config& cfg) {
+  const float A = r0.z, B = r0.w, C = r1.x, thr = r1.z;
+  if (!(thr < INFINITY)) return 0u;                             // o = 0: never passes
+  if (!(thr > -INFINITY) || !(A < 0.0f) || !(C < 0.0f)) return 0xffu;  // no bound: keep all
+  const float ux0 = ((float)(c.tx * cfg.tile_w) + 0.5f) - r0.x;
+  const float ux1 = ux0 + (float)(cfg.tile_w - 1);
+  const float k1 = -B / (2.0f * A);
+  const int rows_per_warp = 32 / cfg.tile_w;
+  const float vy0 = ((float)(c.ty * cfg.tile_h) + 0.5f) - r0.y;
+  uint32_t m = 0;
+  for (int r = 0; r < cfg.tile_h; ++r) {
+    const float v = vy0 + (float)r;
+    const float u = fminf(fmaxf(k1 * v, ux0), ux1);
+    const float t1 = A * u * u, t2 = B * u * v, t3 = C * v * v;
+    const float pmax = t1 + t2 + t3;
+    const float margin = 1e-4f * (fabsf(t1) + fabsf(t2) + fabsf(t3)) + 1e-3f;
+    if (pmax + margin >= thr) m |= 1u << (r / rows_per_warp);
+  }
+  return m;
+}
+
+// Gather a batch and compute every staged splat's warp mask.
+template <int BATCH>
+__device__ __forceinline__ void stage_batch_masked(float4* smem, uint8_t* wmask, const float4* __restrict__ raster,
+                                                   const uint32_t* __restrict__ vals, uint32_t first, int cnt,
+                                                   const TileCtx& c, const potr_raster_config& cfg) {
+  stage_batch<BATCH>(smem, raster, vals, first, cnt);
+  for (int j = threadIdx.x; j < cnt; j += kThreads) wmask[j] = (uint8_t)warp_mask(smem[3 * j], smem[3 * j + 1], c, cfg);
+}
+
 // Forward walk of the tile list (Section 3, Eqs. 2-4).  Returns colour, final T and n_last.
 template <int BATCH>
-__device__ __forceinline__ void forward_walk(float4* smem, const float4* __restrict__ raster,
+__device__ __forceinline__ void forward_walk(float4* smem, uint8_t* wmask, const float4* __restrict__ raster,
                                              const uint32_t* __restrict__ vals, const TileCtx& c,
                                              const potr_raster_config& cfg, float (&C)[3], float& T,
                                              uint32_t& last) {
@@ -92,31 +129,39 @@ __device__ __forceinline__ void forward_walk(float4* smem, const float4* __restr
   T = 1.0f;
   last = 0;
   bool done = !c.inside;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint32_t base = c.s; base < c.e; base += BATCH) {
     if (__syncthreads_and(done)) break;  // also guards the shared-memory batch
     const int cnt = (int)min((uint32_t)BATCH, c.e - base);
-    stage_batch<BATCH>(smem, raster, vals, base, cnt);
+    stage_batch_masked<BATCH>(smem, wmask, raster, vals, base, cnt, c, cfg);
     __syncthreads();
-    if (done) continue;
-    for (int j = 0; j < cnt; ++j) {
-      const float4 r0 = smem[3 * j];
-      const float4 r1 = smem[3 * j + 1];
-      const float p = pair_exponent(r0.z, r0.w, r1.x, __fsub_rn(c.fx, r0.x), __fsub_rn(c.fy, r0.y));
-      if (p < r1.z) continue;  // alpha < alpha_min certainly (prefilter with margin)
-      const float a = pair_alpha(r1.y, p, cfg.alpha_max);
-      if (a < cfg.alpha_min) continue;
-      const float Tn = trans_next(a, T);
-      if (Tn < cfg.t_min) {
-        done = true;
-        break;
+    for (int g = 0; g < cnt; g += 32) {
+      if (__all_sync(0xffffffffu, done)) break;
+      const int jl = g + lane;
+      uint32_t m = __ballot_sync(0xffffffffu, jl < cnt && ((wmask[jl] >> warp) & 1u));
+      while (m) {
+        const int j = g + __ffs(m) - 1;
+        m &= m - 1;
+        if (done) continue;
+        const float4 r0 = smem[3 * j];
+        const float4 r1 = smem[3 * j + 1];
+        const float p = pair_exponent(r0.z, r0.w, r1.x, __fsub_rn(c.fx, r0.x), __fsub_rn(c.fy, r0.y));
+        if (p < r1.z) continue;  // alpha < alpha_min certainly (prefilter with margin)
+        const float a = pair_alpha(r1.y, p, cfg.alpha_max);
+        if (a < cfg.alpha_min) continue;
+        const float Tn = trans_next(a, T);
+        if (Tn < cfg.t_min) {
+          done = true;
+          continue;
+        }
+        const float4 r2 = smem[3 * j + 2];
+        const float w = a * T;
+        C[0] = fmaf(w, r2.x, C[0]);
+        C[1] = fmaf(w, r2.y, C[1]);
+        C[2] = fmaf(w, r2.z, C[2]);
+        T = Tn;
+        last = base - c.s + (uint32_t)j + 1;
       }
-      const float4 r2 = smem[3 * j + 2];
-      const float w = a * T;
-      C[0] = fmaf(w, r2.x, C[0]);
-      C[1] = fmaf(w, r2.y, C[1]);
-      C[2] = fmaf(w, r2.z, C[2]);
-      T = Tn;
-      last = base - c.s + (uint32_t)j + 1;
     }
   }
 }
@@ -129,10 +174,11 @@ __global__ void __launch_bounds__(kThreads) render_kernel(const float4* __restri
                                                           potr_raster_config cfg, float* __restrict__ images,
                                                           float* __restrict__ t_final, uint32_t* __restrict__ n_last) {
   extern __shared__ float4 smem[];
+  uint8_t* wmask = reinterpret_cast<uint8_t*>(smem + 3 * BATCH);
   const TileCtx c = tile_ctx(info, n_views, ranges, cfg);
   float C[3], T;
   uint32_t last;
-  forward_walk<BATCH>(smem, raster, vals, c, cfg, C, T, last);
+  forward_walk<BATCH>(smem, wmask, raster, vals, c, cfg, C, T, last);
   if (!c.inside) return;
   const int64_t pix = c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
   const int64_t plane = (int64_t)c.vi.width * c.vi.height;
@@ -175,7 +221,7 @@ constexpr int kChunk = 16;  // splats per warp transpose-sum
 
 template <int BATCH, bool IMP>
 constexpr size_t removal_smem_bytes() {
-  return sizeof(float4) * 3 * BATCH + sizeof(float) * kWarps * BATCH * (IMP ? 2 : 1);
+  return sizeof(float4) * 3 * BATCH + sizeof(float) * kWarps * BATCH * (IMP ? 2 : 1) + BATCH;
 }
 
 template <int BATCH, bool IMP>
@@ -190,11 +236,12 @@ __global__ void __launch_bounds__(kThreads) removal_kernel(const float4* __restr
   float4* smem = dyn;                                               // [BATCH][3] raster records
   float* red_d = reinterpret_cast<float*>(dyn + 3 * BATCH);         // [kWarps][BATCH] warp sums of dSE
   float* red_i = red_d + kWarps * BATCH;                            // [kWarps][BATCH] warp sums of T alpha
+  uint8_t* wmask = reinterpret_cast<uint8_t*>(red_d + kWarps * BATCH * (IMP ? 2 : 1));  // [BATCH]
   __shared__ uint32_t max_last_w[kWarps];
   const TileCtx c = tile_ctx(info, n_views, ranges, cfg);
   float C[3], T;
   uint32_t last;
-  forward_walk<BATCH>(smem, raster, vals, c, cfg, C, T, last);
+  forward_walk<BATCH>(smem, wmask, raster, vals, c, cfg, C, T, last);
 
   float e2[3] = {0.0f, 0.0f, 0.0f};  // 2 (c - c_t)
   if (c.inside) {
@@ -216,64 +263,77 @@ __global__ void __launch_bounds__(kThreads) removal_kernel(const float4* __restr
   for (int w = 0; w < kWarps; ++w) max_last = max(max_last, max_last_w[w]);
 
   // Back-to-front over list positions [0, max_last): T_i = T_{i+1} / (1 - alpha_i),
-  // S = sum of T_j alpha_j c_j over the composited j > i.
+  // S = sum of T_j alpha_j c_j over the composited j > i.  Each warp visits only the splats
+  // of its warp mask, 16 at a time, highest position first.
   float S[3] = {0.0f, 0.0f, 0.0f};
+  float* my_d = red_d + warp * BATCH;
+  float* my_i = red_i + warp * BATCH;
   for (uint32_t top = max_last; top > 0;) {
     const uint32_t lo = top > (uint32_t)BATCH ? top - BATCH : 0u;
     const int cnt = (int)(top - lo);
     __syncthreads();  // previous batch (records and warp sums) fully consumed
-    stage_batch<BATCH>(smem, raster, vals, c.s + lo, cnt);
+    stage_batch_masked<BATCH>(smem, wmask, raster, vals, c.s + lo, cnt, c, cfg);
+    for (int j = lane; j < cnt; j += 32) {
+      my_d[j] = 0.0f;
+      if (IMP) my_i[j] = 0.0f;
+    }
     __syncthreads();
-    for (int hi = cnt; hi > 0; hi -= kChunk) {
-      const int clo = hi > kChunk ? hi - kChunk : 0;
-      float sd = 0.0f, si = 0.0f;
-      if (lo + (uint32_t)clo < warp_last) {  // warp-uniform: some lane may composite here
+    for (int ghi = cnt; ghi > 0; ghi -= 32) {
+      const int glo = ghi > 32 ? ghi - 32 : 0;
+      if (lo + (uint32_t)glo >= warp_last) continue;  // warp-uniform: nothing composited here
+      const int jl = glo + lane;
+      uint32_t m = __ballot_sync(0xffffffffu, jl < ghi && lo + (uint32_t)jl < warp_last && ((wmask[jl] >> warp) & 1u));
+      while (m) {
         float d[kChunk], im[kChunk];
+        int mypos = -1;
         bool any = false;
 #pragma unroll
         for (int u = 0; u < kChunk; ++u) {
           d[u] = 0.0f;
           if (IMP) im[u] = 0.0f;
-          const int j = hi - 1 - u;
-          if (j >= clo && lo + (uint32_t)j < last) {
-            const float4 r0 = smem[3 * j];
-            const float4 r1 = smem[3 * j + 1];
-            const float p = pair_exponent(r0.z, r0.w, r1.x, __fsub_rn(c.fx, r0.x), __fsub_rn(c.fy, r0.y));
-            if (p >= r1.z) {
-              const float a = pair_alpha(r1.y, p, cfg.alpha_max);
-              if (a >= cfg.alpha_min) {
-                const float4 r2 = smem[3 * j + 2];
-                const float rcp = __fdividef(1.0f, 1.0f - a);
-                T = T * rcp;                  // T_i = T_{i+1} / (1 - alpha_i)
-                const float w = a * T;        // T_i alpha_i
-                const float ratio = a * rcp;  // alpha_i / (1 - alpha_i)
-                const float wc0 = w * r2.x, wc1 = w * r2.y, wc2 = w * r2.z;
-                const float pd0 = fmaf(ratio, S[0], -wc0);
-                const float pd1 = fmaf(ratio, S[1], -wc1);
-                const float pd2 = fmaf(ratio, S[2], -wc2);
-                float dse = pd0 * (pd0 + e2[0]);
-                dse = fmaf(pd1, pd1 + e2[1], dse);
-                dse = fmaf(pd2, pd2 + e2[2], dse);
-                S[0] += wc0;
-                S[1] += wc1;
-                S[2] += wc2;
-                d[u] = dse;
-                if (IMP) im[u] = w;
-                any = true;
+          if (m) {
+            const int b = 31 - __clz(m);
+            m &= ~(1u << b);
+            const int j = glo + b;
+            if (lane == u) mypos = j;
+            if (lo + (uint32_t)j < last) {
+              const float4 r0 = smem[3 * j];
+              const float4 r1 = smem[3 * j + 1];
+              const float p = pair_exponent(r0.z, r0.w, r1.x, __fsub_rn(c.fx, r0.x), __fsub_rn(c.fy, r0.y));
+              if (p >= r1.z) {
+                const float a = pair_alpha(r1.y, p, cfg.alpha_max);
+                if (a >= cfg.alpha_min) {
+                  const float4 r2 = smem[3 * j + 2];
+                  const float rcp = __fdividef(1.0f, 1.0f - a);
+                  T = T * rcp;                  // T_i = T_{i+1} / (1 - alpha_i)
+                  const float w = a * T;        // T_i alpha_i
+                  const float ratio = a * rcp;  // alpha_i / (1 - alpha_i)
+                  const float wc0 = w * r2.x, wc1 = w * r2.y, wc2 = w * r2.z;
+                  const float pd0 = fmaf(ratio, S[0], -wc0);
+                  const float pd1 = fmaf(ratio, S[1], -wc1);
+                  const float pd2 = fmaf(ratio, S[2], -wc2);
+                  float dse = pd0 * (pd0 + e2[0]);
+                  dse = fmaf(pd1, pd1 + e2[1], dse);
+                  dse = fmaf(pd2, pd2 + e2[2], dse);
+                  S[0] += wc0;
+                  S[1] += wc1;
+                  S[2] += wc2;
+                  d[u] = dse;
+                  if (IMP) im[u] = w;
+                  any = true;
+                }
               }
             }
           }
         }
+        float sd = 0.0f, si = 0.0f;
         if (__any_sync(0xffffffffu, any)) {
           sd = warp_transpose_sum16(d);
           if (IMP) si = warp_transpose_sum16(im);
         }
-      }
-      if (lane < kChunk) {
-        const int j = hi - 1 - lane;
-        if (j >= clo) {
-          red_d[warp * BATCH + j] = sd;
-          if (IMP) red_i[warp * BATCH + j] = si;
+        if (lane < kChunk && mypos >= 0) {
+          my_d[mypos] = sd;
+          if (IMP) my_i[mypos] = si;
         }
       }
     }
@@ -296,8 +356,23 @@ __global__ void __launch_bounds__(kThreads) removal_kernel(const float4* __restr
   }
 }
 
-// Per splat k: dSSE_k(v) = sum over its emission slots (binary64, emission order), then
-// dmse[k] += dSSE_k(v) / (3 P_v) / N views in order; importance likewise with / P_v.
+// Compensated (Kahan) binary32 summation: s + (-c) carries the sum to about binary64 accuracy
+// for the handful of tile partials one (view, splat) has; plain adds, so nothing is contracted.
+struct KahanSum {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Per splat k: dSSE_k(v) = sum over its emission slots (emission order), then
+// dmse[k] += dSSE_k(v) * scale_d[v] with scale_d[v] = 1 / (3 P_v N), views in order; the
+// importance likewise with scale_i[v] = 1 / (P_v N).  The per-view scales are computed once
+// per view (binary64), so the loop has no division.
 __global__ void __launch_bounds__(256) splat_reduce_kernel(const uint32_t* __restrict__ touched,
                                                            const uint32_t* __restrict__ offsets,
                                                            const uint32_t* __restrict__ n_inst, int64_t capacity,
@@ -306,27 +381,41 @@ __global__ void __launch_bounds__(256) splat_reduce_kernel(const uint32_t* __res
                                                            const potr_view_info* __restrict__ info, double n_total,
                                                            double* __restrict__ dmse, double* __restrict__ importance,
                                                            double* __restrict__ dsse_view) {
+  __shared__ double scale_d[64], scale_i[64];
   if ((int64_t)*n_inst > capacity) return;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    double acc_d = dmse ? dmse[k] : 0.0;
-    double acc_i = importance ? importance[k] : 0.0;
-    for (int v = 0; v < n_views; ++v) {
-      const int64_t vk = (int64_t)v * n + k;
-      const uint32_t cnt = touched[vk];
-      double sd = 0.0, si = 0.0;
-      if (cnt) {
-        const uint32_t off = offsets[vk];
-        for (uint32_t i = 0; i < cnt; ++i) sd += (double)inst_dse[off + i];
-        if (inst_imp)
-          for (uint32_t i = 0; i < cnt; ++i) si += (double)inst_imp[off + i];
-      }
-      const double P = (double)info[v].width * (double)info[v].height;
-      acc_d += sd / (3.0 * P) / n_total;
-      acc_i += si / P / n_total;
-      if (dsse_view) dsse_view[vk] = sd;
+  for (int v0 = 0; v0 < n_views; v0 += 64) {
+    const int nv = min(64, n_views - v0);
+    __syncthreads();
+    if (threadIdx.x < nv) {
+      const double P = (double)info[v0 + threadIdx.x].width * (double)info[v0 + threadIdx.x].height;
+      scale_d[threadIdx.x] = 1.0 / (3.0 * P * n_total);
+      scale_i[threadIdx.x] = 1.0 / (P * n_total);
     }
-    if (dmse) dmse[k] = acc_d;
-    if (importance) importance[k] = acc_i;
+    __syncthreads();
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+      double acc_d = dmse ? dmse[k] : 0.0;
+      double acc_i = importance ? importance[k] : 0.0;
+      for (int vv = 0; vv < nv; ++vv) {
+        const int64_t vk = (int64_t)(v0 + vv) * n + k;
+        const uint32_t cnt = touched[vk];
+        double sd = 0.0, si = 0.0;
+        if (cnt) {
+          const uint32_t off = offsets[vk];
+          KahanSum kd, ki;
+          for (uint32_t i = 0; i < cnt; ++i) kd.add(inst_dse[off + i]);
+          sd = kd.value();
+          if (inst_imp) {
+            for (uint32_t i = 0; i < cnt; ++i) ki.add(inst_imp[off + i]);
+            si = ki.value();
+          }
+        }
+        acc_d += sd * scale_d[vv];
+        acc_i += si * scale_i[vv];
+        if (dsse_view) dsse_view[vk] = sd;
+      }
+      if (dmse) dmse[k] = acc_d;
+      if (importance) importance[k] = acc_i;
+    }
   }
 }
 
@@ -334,7 +423,7 @@ template <int BATCH>
 cudaError_t launch_render(const potr_views* views, const potr_frame* frame, const potr_raster_config& cfg,
                           const uint32_t* vals, const uint32_t* ranges, float* images, float* t_final,
                           uint32_t* n_last, cudaStream_t s) {
-  const size_t smem = sizeof(float4) * 3 * BATCH;
+  const size_t smem = sizeof(float4) * 3 * BATCH + BATCH;
   render_kernel<BATCH><<<(unsigned)frame->total_tiles, kThreads, smem, s>>>(
       reinterpret_cast<const float4*>(views->raster), vals, ranges, frame->info, frame->n_views, cfg, images, t_final,
       n_last);
