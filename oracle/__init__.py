@@ -109,6 +109,9 @@ def lib():
                                      i64, vp, vp, vp, vp, vp]
             L.orc_removal_effect.argtypes = [C.POINTER(Camera), C.POINTER(Config), i64, vp, vp, vp, vp,
                                              vp, vp, vp, vp, vp, vp, vp, vp]
+            L.orc_pixel_lists.restype = i64
+            L.orc_pixel_lists.argtypes = [C.POINTER(Camera), C.POINTER(Config), i64, vp, vp, vp, vp, vp, i64, vp,
+                                          vp, vp]
             L.orc_removal_bruteforce.restype = C.c_double
             L.orc_removal_bruteforce.argtypes = [C.POINTER(Camera), C.POINTER(Config), i64, vp, vp, vp,
                                                  vp, vp, vp, vp, vp, i64]
@@ -235,6 +238,24 @@ def removal_bruteforce(proj: dict, vals, ranges, cam, cfg: Config, target, image
                                         _p(proj["qcoef"]), _p(proj["opacity"]), _p(proj["rgb"]),
                                         _p(vals), _p(ranges), _p(_f32(target)),
                                         _p(np.ascontiguousarray(image, np.float64)), k)
+
+
+def pixel_lists(proj: dict, vals, ranges, cam, cfg: Config):
+    """Composited (pixel, splat, list position) triples of one view, in compositing order."""
+    n = proj["depth"].size
+    ccam = make_camera(cam)
+    vals = np.ascontiguousarray(vals, np.uint32)
+    ranges = np.ascontiguousarray(ranges, np.uint32)
+    cap = max(1, int(vals.size) * cfg.tile_w * cfg.tile_h)
+    while True:
+        pix = np.empty(cap, np.int64)
+        k = np.empty(cap, np.uint32)
+        pos = np.empty(cap, np.uint32)
+        m = lib().orc_pixel_lists(C.byref(ccam), C.byref(cfg), n, _p(proj["mean2d"]), _p(proj["qcoef"]),
+                                  _p(proj["opacity"]), _p(vals), _p(ranges), cap, _p(pix), _p(k), _p(pos))
+        if m >= 0:
+            return pix[:m], k[:m], pos[:m]
+        cap = -m
 
 
 # ------------------------------------------------------------------------------------------

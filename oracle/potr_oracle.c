@@ -602,3 +602,42 @@ double orc_removal_bruteforce(const orc_camera* cam, const orc_config* cfg, int6
   free(img2);
   return acc;
 }
+
+/*
+ * The composited splats of every pixel, in compositing order (the decisions of the walk
+ * above).  Pixels are visited tile by tile, row-major inside a tile; entry e has pixel index
+ * pix[e] = y * W + x, splat k[e] and list position pos[e].  Returns the number of entries,
+ * or -(count) when it exceeds cap (outputs then hold the first cap entries).
+ */
+int64_t orc_pixel_lists(const orc_camera* cam, const orc_config* cfg, int64_t n, const float* mean2d,
+                        const float* qcoef, const float* opacity, const uint32_t* vals,
+                        const uint32_t* ranges, int64_t cap, int64_t* pix, uint32_t* k_out,
+                        uint32_t* pos_out) {
+  const int W = cam->width, H = cam->height;
+  const int tiles_x = (W + cfg->tile_w - 1) / cfg->tile_w;
+  const int tiles_y = (H + cfg->tile_h - 1) / cfg->tile_h;
+  orc_splats sp = {n, mean2d, qcoef, opacity, NULL};
+  uint32_t mx = max_list(ranges, (int64_t)tiles_x * tiles_y);
+  orc_entry* ent = (orc_entry*)malloc(sizeof(orc_entry) * (size_t)(mx > 0 ? mx : 1));
+  int64_t count = 0;
+  for (int ty = 0; ty < tiles_y; ++ty)
+    for (int tx = 0; tx < tiles_x; ++tx) {
+      int64_t t = (int64_t)ty * tiles_x + tx;
+      for (int y = ty * cfg->tile_h; y < (ty + 1) * cfg->tile_h && y < H; ++y)
+        for (int x = tx * cfg->tile_w; x < (tx + 1) * cfg->tile_w && x < W; ++x) {
+          float T32;
+          uint32_t nl;
+          int64_t K = walk_pixel(&sp, cfg, vals, ranges[2 * t], ranges[2 * t + 1], (float)x + 0.5f,
+                                 (float)y + 0.5f, -1, ent, &T32, &nl);
+          for (int64_t i = 0; i < K; ++i, ++count) {
+            if (count < cap) {
+              pix[count] = (int64_t)y * W + x;
+              k_out[count] = ent[i].k;
+              pos_out[count] = ent[i].pos;
+            }
+          }
+        }
+    }
+  free(ent);
+  return count <= cap ? count : -count;
+}
