@@ -314,6 +314,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_vps = world * n_views * K / (D.max_over_ranks(a.elapsed_time(b), dev) / 1e3)
 
+    # ---- fine-tuning step: 1M splats, 8 views 1280x720, L1 + squared-error loss (lambda 0.2)
+    fwd_bwd = fwd_bwd_step_ms(args, dev, D)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         secs, _ = oracle_view_seconds(w, 0)
@@ -338,7 +341,8 @@ def run_ours(args):
             "per_view_views_per_s": per_view_vps,
             "gblend_per_s": gblend,
             "pairs": pc,
-            "fwd_bwd_ms_per_step": None,
+            "fwd_bwd_ms_per_step": fwd_bwd["store"],
+            "fwd_bwd": fwd_bwd,
             "roofline": {"kernel": "removal_kernel (memset + tile pass + per-splat reduce)", "bound": "alu",
                          "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / PEAK_FP32_TFLOPS, "traffic": None,
@@ -349,6 +353,63 @@ def run_ours(args):
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
+
+
+def fwd_bwd_step_ms(args, dev, D) -> dict:
+    """One fine-tuning forward + backward step on the gradient workload (1M splats, 8 views
+    1280x720): preprocess, bin + sort, render, loss and dL/dc, backward rasterizer and the
+    per-splat parameter adjoint.  Timed with the final transmittance stored by the forward
+    pass and with it recomputed inside the backward kernel."""
+    import torch
+
+    import synth
+    from paper_2601_14821_gb300.pipeline import RemovalEffectFrame, scene_to_device
+
+    w = synth.workload("grad")
+    cams_rec = synth.cameras_to_array(w.cameras)
+    scene_d = scene_to_device(w.scene, dev)
+    fr = RemovalEffectFrame(scene_d, cams_rec, device=dev, with_importance=False, **CFG)
+    fr.plan()
+    img = fr.image_buffer()
+    fr.render(img)
+    torch.cuda.synchronize()
+    noise = np.concatenate([synth.target_noise((3, c.height, c.width), w.target_noise, w.seed, v).reshape(-1)
+                            for v, c in enumerate(w.cameras)])
+    targets = img.clone() + torch.from_numpy(noise).to(dev)
+    dL = torch.empty_like(img)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    tf = fr.pixel_buffer()
+    nl = fr.pixel_buffer(torch.int32)
+    grads = {k: torch.empty_like(v) for k, v in scene_d.items()}
+    out = {"workload": "grad: 1M splats, 8 views 1280x720, loss 0.8 L1 + 0.2 SE vs render + N(0, 0.01)",
+           "instances": fr.instance_count()}
+    for mode in ("store", "recompute"):
+        def step():
+            fr.preprocess()
+            fr.bin_sort()
+            if mode == "store":
+                fr.render(img, tf, nl)
+                fr.loss_grad(img, targets, 0.2, dL, loss)
+                fr.render_backward(dL, grads, tf, nl)
+            else:
+                fr.render(img)
+                fr.loss_grad(img, targets, 0.2, dL, loss)
+                fr.render_backward(dL, grads)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        D.barrier()
+        a.record()
+        for _ in range(args.steps):
+            step()
+        b.record()
+        torch.cuda.synchronize()
+        out[mode] = D.max_over_ranks(a.elapsed_time(b), dev) / args.steps
+    out["per_pixel_bytes_stored"] = 8
+    del fr
+    return out
 
 
 # ------------------------------------------------------------------------------------------

@@ -218,6 +218,57 @@ POTR_API potr_status potr_removal_effect(const potr_views* views, const potr_fra
                                 float* d_inst_imp, double* d_dmse, double* d_importance, double* d_dsse_view,
                                 float* d_images, potr_stream_t stream);
 
+/* Gradients of a scene's parameters: the same SoA planes as potr_scene (device, overwritten). */
+typedef struct {
+  float* means;          /* [3][n] */
+  float* log_scales;     /* [3][n] */
+  float* quats;          /* [4][n] */
+  float* opacity_logits; /* [n] */
+  float* sh;             /* [16][3][n] */
+} potr_scene_grads;
+
+/* Workspace bytes of potr_loss_grad (a per-block partial sum when the loss value is wanted). */
+POTR_API size_t potr_loss_workspace_size(int64_t total_pixels);
+
+/*
+ * Fine-tuning loss of POTR-FT (Section IV-F fine-tunes with the original 3DGS training
+ * routine; its SSIM term is replaced by a squared error):
+ *   L = (1 - lambda) mean |c - c_t| + lambda mean (c - c_t)^2
+ * over every channel of every pixel of the frame (d_images, d_targets packed like
+ * potr_render's images).  Writes dL/dc to d_dL_dimages (same layout; the L1 subgradient at
+ * c = c_t is 0) and, when d_loss is non-NULL, L as binary64 (summed in a fixed order; needs
+ * potr_loss_workspace_size bytes of d_ws).  0 <= lambda <= 1.
+ */
+POTR_API potr_status potr_loss_grad(const potr_frame* frame, const float* d_images, const float* d_targets,
+                                    float lambda, double* d_loss, float* d_dL_dimages, void* d_ws, size_t ws_bytes,
+                                    potr_stream_t stream);
+
+/* Workspace bytes of potr_render_backward: 9 float partial gradients per instance slot. */
+POTR_API size_t potr_render_backward_workspace_size(int64_t instance_capacity);
+
+/*
+ * Backward (adjoint) rasterizer, the derivative of potr_render with respect to the scene
+ * parameters for a given dL/dc (d_dL_dimages, packed like the images).  Per pixel, back to
+ * front over the composited splats with S_{>i} = sum_{j>i} T_j alpha_j c_j:
+ *   dL/dc_i     = T_i alpha_i dL/dc
+ *   dL/dalpha_i = T_i c_i . dL/dc - S_{>i} . dL/dc / (1 - alpha_i)      (Section 3, Eqs. 2-4)
+ * then through alpha = o 2^p (zero where alpha is clamped to alpha_max) to the opacity, the
+ * exponent coefficients and the pixel-space centre; per (tile, splat) sums in a fixed order;
+ * per splat, the adjoint of the EWA projection, the SH colour (zero where it is clamped at 0)
+ * and the activation, summed over the frame's views in order.  Decisions (which splats a pixel
+ * composites) are those of the forward pass and carry no gradient.  The depth order and the
+ * tile rectangle carry none either.
+ * Transmittance: pass the forward render's d_t_final and d_n_last (stored), or NULL for both to
+ * recompute them inside the kernel (no per-pixel storage).  The same inputs as potr_render plus
+ * the scene; writes every plane of *grads.  d_ws: potr_render_backward_workspace_size bytes.
+ */
+POTR_API potr_status potr_render_backward(const potr_scene* scene, const potr_views* views, const potr_frame* frame,
+                                          const potr_raster_config* cfg, const uint32_t* d_vals,
+                                          const uint32_t* d_tile_ranges, const float* d_t_final,
+                                          const uint32_t* d_n_last, const float* d_dL_dimages,
+                                          int64_t instance_capacity, const potr_scene_grads* grads, void* d_ws,
+                                          size_t ws_bytes, potr_stream_t stream);
+
 /*
  * Exact pair counts for throughput and roofline accounting (no counterpart in the paper;
  * the counts define the algorithmic work of Section 3 / IV-B in pairs).  d_counts[5]

@@ -66,6 +66,11 @@ class Views(C.Structure):
                 ("n_instances", C.c_void_p)]
 
 
+class SceneGrads(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p)]
+
+
 class DeviceStatus(C.Structure):
     _fields_ = [("code", C.c_int32), ("reserved", C.c_int32), ("required_instances", C.c_int64)]
 
@@ -86,6 +91,11 @@ SIGNATURES = {
                                    _I32, _I64, _P, _P, _P, _P, _P, _P, _P]),
     "potr_pair_stats": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _P, _P, _P, _P]),
     "potr_launch_count": (C.c_uint64, []),
+    "potr_loss_workspace_size": (_SZ, [_I64]),
+    "potr_loss_grad": (_I32, [C.POINTER(Frame), _P, _P, C.c_float, _P, _P, _P, _SZ, _P]),
+    "potr_render_backward_workspace_size": (_SZ, [_I64]),
+    "potr_render_backward": (_I32, [C.POINTER(Scene), C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _P,
+                                    _P, _P, _P, _P, _I64, C.POINTER(SceneGrads), _P, _SZ, _P]),
     "potr_bin_sort_static": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _I64, _P, _P,
                                     _P, _P, _P]),
 }
@@ -205,3 +215,25 @@ def potr_bin_sort_static(views: Views, frame: Frame, cfg: RasterConfig, n: int, 
     _check("potr_bin_sort_static", lib().potr_bin_sort_static(C.byref(views), C.byref(frame), C.byref(cfg), n,
                                                               capacity, ptr(keys), ptr(vals), ptr(ranges),
                                                               ptr(status), stream_handle(stream)))
+
+
+def potr_loss_workspace_size(total_pixels: int) -> int:
+    return int(lib().potr_loss_workspace_size(total_pixels))
+
+
+def potr_loss_grad(frame: Frame, images, targets, lam: float, loss, dL_dimages, ws, stream=None):
+    _check("potr_loss_grad", lib().potr_loss_grad(C.byref(frame), ptr(images), ptr(targets), lam, ptr(loss),
+                                                  ptr(dL_dimages), ptr(ws), 0 if ws is None else ws.numel(),
+                                                  stream_handle(stream)))
+
+
+def potr_render_backward_workspace_size(capacity: int) -> int:
+    return int(lib().potr_render_backward_workspace_size(capacity))
+
+
+def potr_render_backward(scene: Scene, views: Views, frame: Frame, cfg: RasterConfig, vals, ranges, t_final, n_last,
+                         dL_dimages, capacity: int, grads: SceneGrads, ws, stream=None):
+    _check("potr_render_backward",
+           lib().potr_render_backward(C.byref(scene), C.byref(views), C.byref(frame), C.byref(cfg), ptr(vals),
+                                      ptr(ranges), ptr(t_final), ptr(n_last), ptr(dL_dimages), capacity,
+                                      C.byref(grads), ptr(ws), ws.numel(), stream_handle(stream)))

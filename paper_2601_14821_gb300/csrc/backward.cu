@@ -1,0 +1,557 @@
+// backward.cu -- the adjoint of the forward rasterizer for fine-tuning (the paper notes its
+// CUDA pass is meant to interoperate with the standard forward-backward render pass,
+// Section IV-B; POTR-FT fine-tunes with the original 3DGS training routine, Section IV-F).
+//
+//   loss_grad_kernel      L = (1 - l) mean|c - c_t| + l mean (c - c_t)^2 and dL/dc per channel.
+//   render_bwd_kernel     per tile, back to front over each pixel's composited splats: with
+//                         S_{>i} = sum_{j>i} T_j alpha_j c_j (the same suffix as the removal
+//                         pass), dc/dalpha_i = T_i c_i - S_{>i} / (1 - alpha_i) and dc/dc_i =
+//                         T_i alpha_i; through alpha = o 2^p (unclamped) to the opacity, the
+//                         exponent coefficients A, B, C and the pixel-space centre.  The nine
+//                         per-pair gradients are summed per (tile, splat) without atomics (warp
+//                         transpose-sums in a fixed order, then warps in order) into per-instance
+//                         slots.  T_i comes either from the stored final transmittance of the
+//                         forward render or, with none stored, from re-running the forward walk.
+//   preprocess_bwd_kernel per splat: the instance slots summed in emission order per view, then
+//                         the adjoint of the projection (conic inverse, Sigma2D = T Sigma T^T,
+//                         clamped Jacobian, pinhole centre, SH colour and its direction) and of
+//                         the activation (Sigma = M M^T, M = R diag(exp(log_scale)), quaternion
+//                         normalisation, sigmoid), accumulated over views in view order.
+// All sums have a fixed order, so the gradients are bit-identical from run to run.
+#include "raster_common.cuh"
+
+namespace potr {
+namespace {
+
+constexpr int kGradQ = 9;     // per-pair gradients: mx, my, A, B, C, opacity, r, g, b
+constexpr int kBwdChunk = 8;  // splats per warp transpose-sum
+constexpr int kBwdBatch = 128;
+constexpr float kLn2 = 0.69314718055994531f;
+
+size_t bwd_smem_bytes() {
+  return sizeof(float4) * 3 * kBwdBatch + sizeof(float) * kGradQ * kWarps * kBwdBatch + kBwdBatch;
+}
+
+// Lanes l, l^8, l^16, l^24 receive the sum over all 32 lanes of v[l & 7] (fixed order).
+__device__ __forceinline__ float warp_transpose_sum8(float (&v)[kBwdChunk]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 4; off >= 1; off >>= 1) {
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < off; ++i) {
+      const float send = upper ? v[i] : v[i + off];
+      const float keep = upper ? v[i + off] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  float r = v[0];
+  r += __shfl_xor_sync(0xffffffffu, r, 8);
+  r += __shfl_xor_sync(0xffffffffu, r, 16);
+  return r;
+}
+
+// ---------------------------------------------------------------------------------------
+// K11: loss and dL/dc
+// ---------------------------------------------------------------------------------------
+constexpr int kLossBlocks = 1024;
+
+__global__ void __launch_bounds__(256) loss_grad_kernel(const float* __restrict__ img, const float* __restrict__ tgt,
+                                                        int64_t n_elems, float lam, float* __restrict__ grad,
+                                                        double* __restrict__ block_sums) {
+  __shared__ double warp_sums[8];
+  const float inv_n = (float)(1.0 / (double)n_elems);
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_elems; i += (int64_t)gridDim.x * blockDim.x) {
+    const float r = img[i] - tgt[i];
+    const float sg = (r > 0.0f) ? 1.0f : ((r < 0.0f) ? -1.0f : 0.0f);
+    grad[i] = ((1.0f - lam) * sg + 2.0f * lam * r) * inv_n;
+    acc += (double)((1.0f - lam) * fabsf(r) + lam * r * r);
+  }
+  if (block_sums) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < 8; ++w) s += warp_sums[w];
+      block_sums[blockIdx.x] = s;
+    }
+  }
+}
+
+__global__ void loss_finish_kernel(const double* __restrict__ block_sums, int nb, int64_t n_elems,
+                                   double* __restrict__ loss) {
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += block_sums[b];
+  *loss = s / (double)n_elems;
+}
+
+// ---------------------------------------------------------------------------------------
+// K9: back-to-front adjoint of the compositing
+// ---------------------------------------------------------------------------------------
+template <bool RECOMPUTE>
+__global__ void __launch_bounds__(kThreads) render_bwd_kernel(const float4* __restrict__ raster,
+                                                              const uint32_t* __restrict__ vals,
+                                                              const uint32_t* __restrict__ ranges,
+                                                              const potr_view_info* __restrict__ info, int n_views,
+                                                              potr_raster_config cfg, const float* __restrict__ t_final,
+                                                              const uint32_t* __restrict__ n_last,
+                                                              const float* __restrict__ dL_dimg, int64_t capacity,
+                                                              float* __restrict__ inst_grad) {
+  extern __shared__ float4 dyn[];
+  float4* smem = dyn;                                                // [kBwdBatch][3]
+  float* red = reinterpret_cast<float*>(dyn + 3 * kBwdBatch);        // [kGradQ][kWarps][kBwdBatch]
+  uint8_t* wmask = reinterpret_cast<uint8_t*>(red + kGradQ * kWarps * kBwdBatch);
+  __shared__ uint32_t max_last_w[kWarps];
+  const TileCtx c = tile_ctx(info, n_views, ranges, cfg);
+  float T = 1.0f;
+  uint32_t last = 0;
+  if (RECOMPUTE) {
+    float C[3];
+    forward_walk<kBwdBatch>(smem, wmask, raster, vals, c, cfg, C, T, last);
+  } else if (c.inside) {
+    const int64_t pix = c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
+    T = t_final[pix];
+    last = n_last[pix];
+  }
+  float g[3] = {0.0f, 0.0f, 0.0f};
+  if (c.inside) {
+    const int64_t plane = (int64_t)c.vi.width * c.vi.height;
+    const int64_t o = 3 * c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) g[ch] = dL_dimg[o + ch * plane];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t warp_last = __reduce_max_sync(0xffffffffu, last);
+  if (lane == 0) max_last_w[warp] = warp_last;
+  __syncthreads();
+  uint32_t max_last = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) max_last = max(max_last, max_last_w[w]);
+
+  float S[3] = {0.0f, 0.0f, 0.0f};
+  for (uint32_t top = max_last; top > 0;) {
+    const uint32_t lo = top > (uint32_t)kBwdBatch ? top - kBwdBatch : 0u;
+    const int cnt = (int)(top - lo);
+    __syncthreads();
+    stage_batch_masked<kBwdBatch>(smem, wmask, raster, vals, c.s + lo, cnt, c, cfg);
+    for (int q = 0; q < kGradQ; ++q)
+      for (int j = lane; j < cnt; j += 32) red[(q * kWarps + warp) * kBwdBatch + j] = 0.0f;
+    __syncthreads();
+    for (int ghi = cnt; ghi > 0; ghi -= 32) {
+      const int glo = ghi > 32 ? ghi - 32 : 0;
+      if (lo + (uint32_t)glo >= warp_last) continue;
+      const int jl = glo + lane;
+      uint32_t m = __ballot_sync(0xffffffffu, jl < ghi && lo + (uint32_t)jl < warp_last && ((wmask[jl] >> warp) & 1u));
+      while (m) {
+        float v[kGradQ][kBwdChunk];
+        int mypos = -1;
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < kBwdChunk; ++u) {
+#pragma unroll
+          for (int q = 0; q < kGradQ; ++q) v[q][u] = 0.0f;
+          if (m) {
+            const int b = 31 - __clz(m);
+            m &= ~(1u << b);
+            const int j = glo + b;
+            if (lane == u) mypos = j;
+            if (lo + (uint32_t)j < last) {
+              const float4 r0 = smem[3 * j];
+              const float4 r1 = smem[3 * j + 1];
+              const float dx = __fsub_rn(c.fx, r0.x), dy = __fsub_rn(c.fy, r0.y);
+              const float p = pair_exponent(r0.z, r0.w, r1.x, dx, dy);
+              if (p >= r1.z) {
+                const float G = exp2r(p);
+                const float ao = __fmul_rn(r1.y, G);
+                const float a = fminf(cfg.alpha_max, ao);
+                if (a >= cfg.alpha_min) {
+                  const float4 r2 = smem[3 * j + 2];
+                  const float rcp = __fdividef(1.0f, 1.0f - a);
+                  T = T * rcp;            // T_i
+                  const float w = a * T;  // T_i alpha_i
+                  v[6][u] = w * g[0];
+                  v[7][u] = w * g[1];
+                  v[8][u] = w * g[2];
+                  const float dot_c = r2.x * g[0] + r2.y * g[1] + r2.z * g[2];
+                  const float dot_s = S[0] * g[0] + S[1] * g[1] + S[2] * g[2];
+                  const float dLda = T * dot_c - dot_s * rcp;
+                  S[0] += w * r2.x;
+                  S[1] += w * r2.y;
+                  S[2] += w * r2.z;
+                  if (ao <= cfg.alpha_max) {  // alpha = o 2^p (clamp inactive)
+                    v[5][u] = dLda * G;
+                    const float dLdp = dLda * ao * kLn2;
+                    v[2][u] = dLdp * dx * dx;
+                    v[3][u] = dLdp * dx * dy;
+                    v[4][u] = dLdp * dy * dy;
+                    v[0][u] = -dLdp * (2.0f * r0.z * dx + r0.w * dy);
+                    v[1][u] = -dLdp * (r0.w * dx + 2.0f * r1.x * dy);
+                  }
+                  any = true;
+                }
+              }
+            }
+          }
+        }
+        if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+          for (int q = 0; q < kGradQ; ++q) {
+            const float sq = warp_transpose_sum8(v[q]);
+            if (lane < kBwdChunk && mypos >= 0) red[(q * kWarps + warp) * kBwdBatch + mypos] = sq;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += kThreads) {
+      float sq[kGradQ];
+      bool nz = false;
+#pragma unroll
+      for (int q = 0; q < kGradQ; ++q) {
+        float t = 0.0f;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) t += red[(q * kWarps + w) * kBwdBatch + j];
+        sq[q] = t;
+        nz |= t != 0.0f;
+      }
+      if (nz) {
+        const uint32_t slot = emission_slot(smem[3 * j + 1], smem[3 * j + 2], c.tx, c.ty);
+#pragma unroll
+        for (int q = 0; q < kGradQ; ++q) inst_grad[(int64_t)q * capacity + slot] = sq[q];
+      }
+    }
+    top = lo;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// K10: per-splat adjoint of projection, colour and activation
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void sh_basis16(float x, float y, float z, float* Y) {
+  const float xx = x * x, yy = y * y, zz = z * z;
+  Y[0] = 0.28209479177387814f;
+  Y[1] = -0.4886025119029199f * y;
+  Y[2] = 0.4886025119029199f * z;
+  Y[3] = -0.4886025119029199f * x;
+  Y[4] = 1.0925484305920792f * x * y;
+  Y[5] = -1.0925484305920792f * y * z;
+  Y[6] = 0.31539156525252005f * (2.0f * zz - xx - yy);
+  Y[7] = -1.0925484305920792f * x * z;
+  Y[8] = 0.5462742152960396f * (xx - yy);
+  Y[9] = -0.5900435899266435f * y * (3.0f * xx - yy);
+  Y[10] = 2.890611442640554f * x * y * z;
+  Y[11] = -0.4570457994644658f * y * (4.0f * zz - xx - yy);
+  Y[12] = 0.3731763325901154f * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+  Y[13] = -0.4570457994644658f * x * (4.0f * zz - xx - yy);
+  Y[14] = 1.445305721320277f * z * (xx - yy);
+  Y[15] = -0.5900435899266435f * x * (xx - 3.0f * yy);
+}
+
+// sum_i w_i grad Y_i(x, y, z) with the basis polynomials differentiated term by term.
+__device__ __forceinline__ void sh_weighted_grad(float x, float y, float z, const float* w, float& gx, float& gy,
+                                                 float& gz) {
+  const float c1 = 0.4886025119029199f, c2a = 1.0925484305920792f, c2b = 0.31539156525252005f;
+  const float c2c = 0.5462742152960396f, c3a = 0.5900435899266435f, c3b = 2.890611442640554f;
+  const float c3c = 0.4570457994644658f, c3d = 0.3731763325901154f, c3e = 1.445305721320277f;
+  const float xx = x * x, yy = y * y, zz = z * z;
+  gx = 0.0f; gy = 0.0f; gz = 0.0f;
+  gy += w[1] * -c1;
+  gz += w[2] * c1;
+  gx += w[3] * -c1;
+  gx += w[4] * c2a * y;            gy += w[4] * c2a * x;
+  gy += w[5] * -c2a * z;           gz += w[5] * -c2a * y;
+  gx += w[6] * -2.0f * c2b * x;    gy += w[6] * -2.0f * c2b * y;    gz += w[6] * 4.0f * c2b * z;
+  gx += w[7] * -c2a * z;           gz += w[7] * -c2a * x;
+  gx += w[8] * 2.0f * c2c * x;     gy += w[8] * -2.0f * c2c * y;
+  gx += w[9] * -6.0f * c3a * x * y;                gy += w[9] * -3.0f * c3a * (xx - yy);
+  gx += w[10] * c3b * y * z;       gy += w[10] * c3b * x * z;       gz += w[10] * c3b * x * y;
+  gx += w[11] * 2.0f * c3c * x * y;                gy += w[11] * -c3c * (4.0f * zz - xx - 3.0f * yy);
+  gz += w[11] * -8.0f * c3c * y * z;
+  gx += w[12] * -6.0f * c3d * x * z;               gy += w[12] * -6.0f * c3d * y * z;
+  gz += w[12] * c3d * (6.0f * zz - 3.0f * xx - 3.0f * yy);
+  gx += w[13] * -c3c * (4.0f * zz - 3.0f * xx - yy);                gy += w[13] * 2.0f * c3c * x * y;
+  gz += w[13] * -8.0f * c3c * x * z;
+  gx += w[14] * 2.0f * c3e * x * z;                gy += w[14] * -2.0f * c3e * y * z;
+  gz += w[14] * c3e * (xx - yy);
+  gx += w[15] * -3.0f * c3a * (xx - yy);           gy += w[15] * 6.0f * c3a * x * y;
+}
+
+__global__ void __launch_bounds__(128) preprocess_bwd_kernel(
+    const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
+    const float* __restrict__ sh, const float* __restrict__ cov3d, const float* __restrict__ opacity, int64_t n,
+    const potr_camera* __restrict__ cams, int n_views, potr_raster_config cfg, const uint32_t* __restrict__ touched,
+    const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ n_inst, int64_t capacity,
+    const float* __restrict__ inst_grad, float* __restrict__ g_means, float* __restrict__ g_log_scales,
+    float* __restrict__ g_quats, float* __restrict__ g_logits, float* __restrict__ g_sh) {
+  const bool ok = (int64_t)*n_inst <= capacity;
+  const float kA = -0.5f * kLog2e;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    float gmu[3] = {0.0f, 0.0f, 0.0f};
+    float G3[3][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+    float go = 0.0f;
+    float gsh[48];
+#pragma unroll
+    for (int i = 0; i < 48; ++i) gsh[i] = 0.0f;
+    const float mu[3] = {means[k], means[n + k], means[2 * n + k]};
+    const float Sg[3][3] = {{cov3d[k], cov3d[n + k], cov3d[2 * n + k]},
+                            {cov3d[n + k], cov3d[3 * n + k], cov3d[4 * n + k]},
+                            {cov3d[2 * n + k], cov3d[4 * n + k], cov3d[5 * n + k]}};
+    for (int v = 0; ok && v < n_views; ++v) {
+      const int64_t vk = (int64_t)v * n + k;
+      const uint32_t cnt = touched[vk];
+      if (!cnt) continue;
+      const uint32_t off = offsets[vk];
+      float gq[kGradQ];
+      bool nz = false;
+#pragma unroll
+      for (int q = 0; q < kGradQ; ++q) {
+        KahanSum ks;
+        for (uint32_t i = 0; i < cnt; ++i) ks.add(inst_grad[(int64_t)q * capacity + off + i]);
+        gq[q] = (float)ks.value();
+        nz |= gq[q] != 0.0f;
+      }
+      if (!nz) continue;
+      const potr_camera& cam = cams[v];
+      const float* W = cam.w2c;
+      // forward recomputation (values only)
+      float t[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) t[i] = W[i * 4] * mu[0] + W[i * 4 + 1] * mu[1] + W[i * 4 + 2] * mu[2] + W[i * 4 + 3];
+      const float lim_x = 1.3f * (0.5f * (float)cam.width / cam.fx);
+      const float lim_y = 1.3f * (0.5f * (float)cam.height / cam.fy);
+      const float iz = 1.0f / t[2], iz2 = iz * iz, iz3 = iz2 * iz;
+      const float txz = t[0] * iz, tyz = t[1] * iz;
+      const bool inx = txz >= -lim_x && txz <= lim_x;
+      const bool iny = tyz >= -lim_y && tyz <= lim_y;
+      const float xc = fminf(lim_x, fmaxf(-lim_x, txz)) * t[2];
+      const float yc = fminf(lim_y, fmaxf(-lim_y, tyz)) * t[2];
+      const float j00 = cam.fx * iz, j02 = -cam.fx * xc * iz2, j11 = cam.fy * iz, j12 = -cam.fy * yc * iz2;
+      float Tm[2][3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Tm[0][j] = j00 * W[j] + j02 * W[8 + j];
+        Tm[1][j] = j11 * W[4 + j] + j12 * W[8 + j];
+      }
+      float TS[2][3];  // T Sigma
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) TS[i][j] = Tm[i][0] * Sg[0][j] + Tm[i][1] * Sg[1][j] + Tm[i][2] * Sg[2][j];
+      const float a = TS[0][0] * Tm[0][0] + TS[0][1] * Tm[0][1] + TS[0][2] * Tm[0][2] + cfg.lowpass;
+      const float b = TS[0][0] * Tm[1][0] + TS[0][1] * Tm[1][1] + TS[0][2] * Tm[1][2];
+      const float cc2 = TS[1][0] * Tm[1][0] + TS[1][1] * Tm[1][1] + TS[1][2] * Tm[1][2] + cfg.lowpass;
+      const float idet = 1.0f / (a * cc2 - b * b);
+      const float ca = cc2 * idet, cb = -b * idet, cc = a * idet;
+      // conic and Sigma2D adjoint
+      const float gca = kA * gq[2], gcb = -kLog2e * gq[3], gcc = kA * gq[4];
+      const float ga = -(gca * ca * ca + gcb * ca * cb + gcc * cb * cb);
+      const float gc = -(gca * cb * cb + gcb * cb * cc + gcc * cc * cc);
+      const float gb = -(2.0f * gca * ca * cb + gcb * (ca * cc + cb * cb) + 2.0f * gcc * cb * cc);
+      const float G2[2][2] = {{ga, 0.5f * gb}, {0.5f * gb, gc}};
+      // Sigma gradient T^T G2 T
+      float G2T[2][3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        G2T[0][j] = G2[0][0] * Tm[0][j] + G2[0][1] * Tm[1][j];
+        G2T[1][j] = G2[1][0] * Tm[0][j] + G2[1][1] * Tm[1][j];
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) G3[i][j] += Tm[0][i] * G2T[0][j] + Tm[1][i] * G2T[1][j];
+      // T gradient 2 G2 T Sigma, then J gradient (dL/dT) W_rot^T
+      float gT[2][3];
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gT[i][j] = 2.0f * (G2[i][0] * TS[0][j] + G2[i][1] * TS[1][j]);
+      const float gj00 = gT[0][0] * W[0] + gT[0][1] * W[1] + gT[0][2] * W[2];
+      const float gj02 = gT[0][0] * W[8] + gT[0][1] * W[9] + gT[0][2] * W[10];
+      const float gj11 = gT[1][0] * W[4] + gT[1][1] * W[5] + gT[1][2] * W[6];
+      const float gj12 = gT[1][0] * W[8] + gT[1][1] * W[9] + gT[1][2] * W[10];
+      float gt[3] = {0.0f, 0.0f, 0.0f};
+      gt[2] += -gj00 * cam.fx * iz2 - gj11 * cam.fy * iz2;
+      if (inx) {
+        gt[0] += -gj02 * cam.fx * iz2;
+        gt[2] += gj02 * 2.0f * cam.fx * xc * iz3;
+      } else {
+        gt[2] += gj02 * cam.fx * xc * iz3;
+      }
+      if (iny) {
+        gt[1] += -gj12 * cam.fy * iz2;
+        gt[2] += gj12 * 2.0f * cam.fy * yc * iz3;
+      } else {
+        gt[2] += gj12 * cam.fy * yc * iz3;
+      }
+      // pixel-space centre
+      gt[0] += gq[0] * cam.fx * iz;
+      gt[1] += gq[1] * cam.fy * iz;
+      gt[2] += -gq[0] * cam.fx * t[0] * iz2 - gq[1] * cam.fy * t[1] * iz2;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) gmu[j] += W[j] * gt[0] + W[4 + j] * gt[1] + W[8 + j] * gt[2];
+      // colour: clamp mask, SH coefficients, direction
+      float shc_w[16];
+      float cpos[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) cpos[j] = -(W[j] * W[3] + W[4 + j] * W[7] + W[8 + j] * W[11]);
+      const float u0 = mu[0] - cpos[0], u1 = mu[1] - cpos[1], u2 = mu[2] - cpos[2];
+      const float inv_len = rsqrtf(u0 * u0 + u1 * u1 + u2 * u2);
+      const float dx = u0 * inv_len, dy = u1 * inv_len, dz = u2 * inv_len;
+      float Y[16];
+      sh_basis16(dx, dy, dz, Y);
+      float gv[3];
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc = fmaf(sh[(int64_t)(i * 3 + ch) * n + k], Y[i], acc);
+        gv[ch] = (acc + 0.5f > 0.0f) ? gq[6 + ch] : 0.0f;
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        shc_w[i] = 0.0f;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+          gsh[i * 3 + ch] += gv[ch] * Y[i];
+          shc_w[i] += gv[ch] * sh[(int64_t)(i * 3 + ch) * n + k];
+        }
+      }
+      float gdx, gdy, gdz;
+      sh_weighted_grad(dx, dy, dz, shc_w, gdx, gdy, gdz);
+      const float dotg = gdx * dx + gdy * dy + gdz * dz;
+      gmu[0] += (gdx - dx * dotg) * inv_len;
+      gmu[1] += (gdy - dy * dotg) * inv_len;
+      gmu[2] += (gdz - dz * dotg) * inv_len;
+      go += gq[5];
+    }
+    // activation adjoint: Sigma = M M^T, M = R diag(s), s = exp(log_scale), R(q / |q|)
+    float s[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) s[j] = expf(log_scales[j * n + k]);
+    float qw = quats[k], qx = quats[n + k], qy = quats[2 * n + k], qz = quats[3 * n + k];
+    const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    const float iqn = qn > 0.0f ? 1.0f / qn : 0.0f;
+    qw *= iqn; qx *= iqn; qy *= iqn; qz *= iqn;
+    const float R[3][3] = {{1.0f - 2.0f * (qy * qy + qz * qz), 2.0f * (qx * qy - qw * qz), 2.0f * (qx * qz + qw * qy)},
+                           {2.0f * (qx * qy + qw * qz), 1.0f - 2.0f * (qx * qx + qz * qz), 2.0f * (qy * qz - qw * qx)},
+                           {2.0f * (qx * qz - qw * qy), 2.0f * (qy * qz + qw * qx), 1.0f - 2.0f * (qx * qx + qy * qy)}};
+    float gs[3] = {0.0f, 0.0f, 0.0f};
+    float gR[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        // dL/dM_ij = 2 (G3 M)_ij with M_lj = R_lj s_j
+        const float gM = 2.0f * (G3[i][0] * R[0][j] + G3[i][1] * R[1][j] + G3[i][2] * R[2][j]) * s[j];
+        gs[j] += gM * R[i][j];
+        gR[i][j] = gM * s[j];
+      }
+    const float gqw = 2.0f * (-qz * gR[0][1] + qy * gR[0][2] + qz * gR[1][0] - qx * gR[1][2] - qy * gR[2][0] + qx * gR[2][1]);
+    const float gqx = 2.0f * (qy * gR[0][1] + qz * gR[0][2] + qy * gR[1][0] - 2.0f * qx * gR[1][1] - qw * gR[1][2] +
+                              qz * gR[2][0] + qw * gR[2][1] - 2.0f * qx * gR[2][2]);
+    const float gqy = 2.0f * (-2.0f * qy * gR[0][0] + qx * gR[0][1] + qw * gR[0][2] + qx * gR[1][0] + qz * gR[1][2] -
+                              qw * gR[2][0] + qz * gR[2][1] - 2.0f * qy * gR[2][2]);
+    const float gqz = 2.0f * (-2.0f * qz * gR[0][0] - qw * gR[0][1] + qx * gR[0][2] + qw * gR[1][0] - 2.0f * qz * gR[1][1] +
+                              qy * gR[1][2] + qx * gR[2][0] + qy * gR[2][1]);
+    const float dq = gqw * qw + gqx * qx + gqy * qy + gqz * qz;
+    g_quats[k] = (gqw - qw * dq) * iqn;
+    g_quats[n + k] = (gqx - qx * dq) * iqn;
+    g_quats[2 * n + k] = (gqy - qy * dq) * iqn;
+    g_quats[3 * n + k] = (gqz - qz * dq) * iqn;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      g_log_scales[j * n + k] = gs[j] * s[j];
+      g_means[j * n + k] = gmu[j];
+    }
+    const float o = opacity[k];
+    g_logits[k] = go * o * (1.0f - o);
+#pragma unroll
+    for (int i = 0; i < 48; ++i) g_sh[(int64_t)i * n + k] = gsh[i];
+  }
+}
+
+}  // namespace
+}  // namespace potr
+
+extern "C" size_t potr_loss_workspace_size(int64_t total_pixels) {
+  (void)total_pixels;
+  return sizeof(double) * potr::kLossBlocks;
+}
+
+extern "C" potr_status potr_loss_grad(const potr_frame* frame, const float* d_images, const float* d_targets,
+                                      float lambda, double* d_loss, float* d_dL_dimages, void* d_ws, size_t ws_bytes,
+                                      potr_stream_t stream) {
+  using namespace potr;
+  if (!frame || !d_images || !d_targets || !d_dL_dimages || frame->total_pixels <= 0) return POTR_ERR_INVALID_ARGUMENT;
+  if (!(lambda >= 0.0f && lambda <= 1.0f)) return POTR_ERR_INVALID_ARGUMENT;
+  if (d_loss && (!d_ws || ws_bytes < sizeof(double) * kLossBlocks)) return POTR_ERR_INVALID_ARGUMENT;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t n_elems = 3 * frame->total_pixels;
+  double* block_sums = d_loss ? static_cast<double*>(d_ws) : nullptr;
+  loss_grad_kernel<<<kLossBlocks, 256, 0, s>>>(d_images, d_targets, n_elems, lambda, d_dL_dimages, block_sums);
+  POTR_CHECK_LAUNCH();
+  if (d_loss) {
+    loss_finish_kernel<<<1, 1, 0, s>>>(block_sums, kLossBlocks, n_elems, d_loss);
+    POTR_CHECK_LAUNCH();
+  }
+  return POTR_OK;
+}
+
+extern "C" size_t potr_render_backward_workspace_size(int64_t instance_capacity) {
+  return sizeof(float) * (size_t)potr::kGradQ * (size_t)(instance_capacity > 0 ? instance_capacity : 0);
+}
+
+extern "C" potr_status potr_render_backward(const potr_scene* scene, const potr_views* views, const potr_frame* frame,
+                                            const potr_raster_config* cfg, const uint32_t* d_vals,
+                                            const uint32_t* d_tile_ranges, const float* d_t_final,
+                                            const uint32_t* d_n_last, const float* d_dL_dimages,
+                                            int64_t instance_capacity, const potr_scene_grads* grads, void* d_ws,
+                                            size_t ws_bytes, potr_stream_t stream) {
+  using namespace potr;
+  if (!scene || !views || !frame || !valid_cfg(cfg) || !grads || !d_vals || !d_tile_ranges || !d_dL_dimages)
+    return POTR_ERR_INVALID_ARGUMENT;
+  if (!scene->means || !scene->log_scales || !scene->quats || !scene->sh || scene->n <= 0) return POTR_ERR_INVALID_ARGUMENT;
+  if (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logits || !grads->sh)
+    return POTR_ERR_INVALID_ARGUMENT;
+  if (!views->raster || !views->cov3d || !views->opacity || !views->touched || !views->offsets || !views->n_instances)
+    return POTR_ERR_INVALID_ARGUMENT;
+  if ((d_t_final == nullptr) != (d_n_last == nullptr)) return POTR_ERR_INVALID_ARGUMENT;
+  if (frame->total_tiles <= 0 || frame->total_tiles > 0x7fffffffll || !frame->cams || !frame->info)
+    return POTR_ERR_INVALID_ARGUMENT;
+  if (instance_capacity <= 0 || !d_ws || ws_bytes < potr_render_backward_workspace_size(instance_capacity))
+    return POTR_ERR_INVALID_ARGUMENT;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  float* inst_grad = static_cast<float*>(d_ws);
+  if (cudaMemsetAsync(inst_grad, 0, potr_render_backward_workspace_size(instance_capacity), s) != cudaSuccess)
+    return POTR_ERR_CUDA;
+  const size_t smem = bwd_smem_bytes();
+  const bool recompute = d_t_final == nullptr;
+  if (recompute) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(render_bwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return POTR_ERR_CUDA;
+    render_bwd_kernel<true><<<(unsigned)frame->total_tiles, kThreads, smem, s>>>(
+        reinterpret_cast<const float4*>(views->raster), d_vals, d_tile_ranges, frame->info, frame->n_views, *cfg,
+        nullptr, nullptr, d_dL_dimages, instance_capacity, inst_grad);
+  } else {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(render_bwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return POTR_ERR_CUDA;
+    render_bwd_kernel<false><<<(unsigned)frame->total_tiles, kThreads, smem, s>>>(
+        reinterpret_cast<const float4*>(views->raster), d_vals, d_tile_ranges, frame->info, frame->n_views, *cfg,
+        d_t_final, d_n_last, d_dL_dimages, instance_capacity, inst_grad);
+  }
+  POTR_CHECK_LAUNCH();
+  const int64_t n = scene->n;
+  int64_t g = (n + 127) / 128;
+  if (g > 152 * 64) g = 152 * 64;
+  preprocess_bwd_kernel<<<(unsigned)g, 128, 0, s>>>(
+      scene->means, scene->log_scales, scene->quats, scene->sh, views->cov3d, views->opacity, n, frame->cams,
+      frame->n_views, *cfg, views->touched, views->offsets, views->n_instances, instance_capacity, inst_grad,
+      grads->means, grads->log_scales, grads->quats, grads->opacity_logits, grads->sh);
+  POTR_CHECK_LAUNCH();
+  return POTR_OK;
+}

@@ -1,0 +1,181 @@
+// raster_common.cuh -- tile-kernel building blocks shared by the forward, removal and
+// backward passes (one CTA of 256 threads per (view, tile), one pixel per thread).
+#pragma once
+
+#include "potr_device.cuh"
+
+namespace potr {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit_wait() {
+  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+// Gather the raster records of list entries [first, first + cnt) into smem[0 .. cnt).
+template <int BATCH>
+__device__ __forceinline__ void stage_batch(float4* smem, const float4* __restrict__ raster,
+                                            const uint32_t* __restrict__ vals, uint32_t first, int cnt) {
+  for (int j = threadIdx.x; j < cnt; j += kThreads) {
+    const uint32_t vk = vals[first + j];
+    const float4* src = raster + (size_t)vk * 3;
+    cp_async16(smem + 3 * j + 0, src + 0);
+    cp_async16(smem + 3 * j + 1, src + 1);
+    cp_async16(smem + 3 * j + 2, src + 2);
+  }
+  cp_async_commit_wait();
+}
+
+struct TileCtx {
+  int64_t tile;
+  int view;
+  potr_view_info vi;
+  int px, py;
+  bool inside;
+  float fx, fy;
+  uint32_t s, e;
+  int tx, ty;
+};
+
+__device__ __forceinline__ TileCtx tile_ctx(const potr_view_info* __restrict__ info, int n_views,
+                                            const uint32_t* __restrict__ ranges, const potr_raster_config& cfg) {
+  TileCtx c;
+  c.tile = blockIdx.x;
+  c.view = view_of_tile(info, n_views, c.tile);
+  c.vi = info[c.view];
+  const int64_t local = c.tile - c.vi.tile_base;
+  c.ty = (int)(local / c.vi.tiles_x);
+  c.tx = (int)(local - (int64_t)c.ty * c.vi.tiles_x);
+  c.px = c.tx * cfg.tile_w + (int)(threadIdx.x % cfg.tile_w);
+  c.py = c.ty * cfg.tile_h + (int)(threadIdx.x / cfg.tile_w);
+  c.inside = c.px < c.vi.width && c.py < c.vi.height;
+  c.fx = (float)c.px + 0.5f;
+  c.fy = (float)c.py + 0.5f;
+  c.s = ranges[2 * c.tile];
+  c.e = ranges[2 * c.tile + 1];
+  return c;
+}
+
+// Bit w of the result is set when the splat of record (r0, r1) may pass the opacity
+// prefilter (log2 G >= r1.z) at some pixel centre of warp w's rows of this tile.  For each
+// pixel row y the exponent A u^2 + B u v + C v^2 (v = y - my fixed) is a concave parabola in
+// u = x - mx, maximised over the row's span of pixel centres; a pair whose warp bit is clear
+// therefore has alpha < alpha_min at every pixel of that warp and is skipped without changing
+// any decision.  The margin covers binary32 rounding of both evaluations.
+__device__ __forceinline__ uint32_t warp_mask(const float4& r0, const float4& r1, const TileCtx& c,
+                                              const potr_raster_config& cfg) {
+  const float A = r0.z, B = r0.w, C = r1.x, thr = r1.z;
+  if (!(thr < INFINITY)) return 0u;                             // o = 0: never passes
+  if (!(thr > -INFINITY) || !(A < 0.0f) || !(C < 0.0f)) return 0xffu;  // no bound: keep all
+  const float ux0 = ((float)(c.tx * cfg.tile_w) + 0.5f) - r0.x;
+  const float ux1 = ux0 + (float)(cfg.tile_w - 1);
+  const float k1 = -B / (2.0f * A);
+  const int rows_per_warp = 32 / cfg.tile_w;
+  const float vy0 = ((float)(c.ty * cfg.tile_h) + 0.5f) - r0.y;
+  uint32_t m = 0;
+  for (int r = 0; r < cfg.tile_h; ++r) {
+    const float v = vy0 + (float)r;
+    const float u = fminf(fmaxf(k1 * v, ux0), ux1);
+    const float t1 = A * u * u, t2 = B * u * v, t3 = C * v * v;
+    const float pmax = t1 + t2 + t3;
+    const float margin = 1e-4f * (fabsf(t1) + fabsf(t2) + fabsf(t3)) + 1e-3f;
+    if (pmax + margin >= thr) m |= 1u << (r / rows_per_warp);
+  }
+  return m;
+}
+
+// Gather a batch and compute every staged splat's warp mask.
+template <int BATCH>
+__device__ __forceinline__ void stage_batch_masked(float4* smem, uint8_t* wmask, const float4* __restrict__ raster,
+                                                   const uint32_t* __restrict__ vals, uint32_t first, int cnt,
+                                                   const TileCtx& c, const potr_raster_config& cfg) {
+  stage_batch<BATCH>(smem, raster, vals, first, cnt);
+  for (int j = threadIdx.x; j < cnt; j += kThreads) wmask[j] = (uint8_t)warp_mask(smem[3 * j], smem[3 * j + 1], c, cfg);
+}
+
+// Forward walk of the tile list (Section 3, Eqs. 2-4).  Returns colour, final T and n_last.
+template <int BATCH>
+__device__ __forceinline__ void forward_walk(float4* smem, uint8_t* wmask, const float4* __restrict__ raster,
+                                             const uint32_t* __restrict__ vals, const TileCtx& c,
+                                             const potr_raster_config& cfg, float (&C)[3], float& T,
+                                             uint32_t& last) {
+  C[0] = C[1] = C[2] = 0.0f;
+  T = 1.0f;
+  last = 0;
+  bool done = !c.inside;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t base = c.s; base < c.e; base += BATCH) {
+    if (__syncthreads_and(done)) break;  // also guards the shared-memory batch
+    const int cnt = (int)min((uint32_t)BATCH, c.e - base);
+    stage_batch_masked<BATCH>(smem, wmask, raster, vals, base, cnt, c, cfg);
+    __syncthreads();
+    for (int g = 0; g < cnt; g += 32) {
+      if (__all_sync(0xffffffffu, done)) break;
+      const int jl = g + lane;
+      uint32_t m = __ballot_sync(0xffffffffu, jl < cnt && ((wmask[jl] >> warp) & 1u));
+      while (m) {
+        const int j = g + __ffs(m) - 1;
+        m &= m - 1;
+        if (done) continue;
+        const float4 r0 = smem[3 * j];
+        const float4 r1 = smem[3 * j + 1];
+        const float p = pair_exponent(r0.z, r0.w, r1.x, __fsub_rn(c.fx, r0.x), __fsub_rn(c.fy, r0.y));
+        if (p < r1.z) continue;  // alpha < alpha_min certainly (prefilter with margin)
+        const float a = pair_alpha(r1.y, p, cfg.alpha_max);
+        if (a < cfg.alpha_min) continue;
+        const float Tn = trans_next(a, T);
+        if (Tn < cfg.t_min) {
+          done = true;
+          continue;
+        }
+        const float4 r2 = smem[3 * j + 2];
+        const float w = a * T;
+        C[0] = fmaf(w, r2.x, C[0]);
+        C[1] = fmaf(w, r2.y, C[1]);
+        C[2] = fmaf(w, r2.z, C[2]);
+        T = Tn;
+        last = base - c.s + (uint32_t)j + 1;
+      }
+    }
+  }
+}
+
+// Emission slot of the instance of record (r1, r2) that lies in tile (tx, ty).
+__device__ __forceinline__ uint32_t emission_slot(const float4& r1, const float4& r2, int tx, int ty) {
+  const uint32_t off = __float_as_uint(r1.w);
+  const uint32_t rw = __float_as_uint(r2.w);
+  const uint32_t x0 = rw & 0x7ffu, y0 = (rw >> 11) & 0x7ffu, w = rw >> 22;
+  return off + ((uint32_t)ty - y0) * w + ((uint32_t)tx - x0);
+}
+
+// Compensated (Kahan) binary32 summation: s + (-c) carries the sum to about binary64 accuracy
+// for the handful of tile partials one (view, splat) has; plain adds, so nothing is contracted.
+struct KahanSum {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+inline bool valid_cfg(const potr_raster_config* cfg) {
+  if (!cfg) return false;
+  if (cfg->tile_w * cfg->tile_h != kTilePixels) return false;
+  if (!((cfg->tile_w == 16 && cfg->tile_h == 16) || (cfg->tile_w == 8 && cfg->tile_h == 32) ||
+        (cfg->tile_w == 32 && cfg->tile_h == 8)))
+    return false;
+  return cfg->batch == 128 || cfg->batch == 256 || cfg->batch == 512;
+}
+
+}  // namespace
+}  // namespace potr

@@ -114,6 +114,35 @@ class RemovalEffectFrame:
                               self.inst_imp if importance is not None else None, dmse, importance, dsse_view,
                               images, stream)
 
+    def bind_scene(self, scene: dict):
+        """Point the frame at other parameter tensors of the same size (e.g. autograd inputs)."""
+        assert int(scene["means"].shape[-1]) == self.n
+        self.scene = scene
+        self.scene_c = scene_struct(scene)
+
+    def status_code(self) -> int:
+        """Device status of the last binning (synchronises)."""
+        return int(self.status[0].item())
+
+    def loss_grad(self, images, targets, lam: float, dL_dimages, loss=None, stream=None):
+        ws = None
+        if loss is not None:
+            ws = getattr(self, "_loss_ws", None)
+            if ws is None:
+                ws = self._loss_ws = torch.empty(B.potr_loss_workspace_size(self.total_pixels), dtype=torch.uint8,
+                                                 device=self.device)
+        B.potr_loss_grad(self.frame, images, targets, lam, loss, dL_dimages, ws, stream)
+
+    def render_backward(self, dL_dimages, grads: dict, t_final=None, n_last=None, stream=None):
+        """Parameter gradients (dict of tensors shaped like the scene, overwritten)."""
+        need = B.potr_render_backward_workspace_size(self.capacity)
+        ws = getattr(self, "_bwd_ws", None)
+        if ws is None or ws.numel() < need:
+            ws = self._bwd_ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        g = B.SceneGrads(*(grads[k].data_ptr() for k in SCENE_KEYS))
+        B.potr_render_backward(self.scene_c, self.views, self.frame, self.cfg, self.vals, self.ranges, t_final, n_last,
+                               dL_dimages, self.capacity, g, ws, stream)
+
     def pair_stats(self, stream=None) -> dict:
         """Exact pair counts of the forward and removal walks (see potr_pair_stats)."""
         counts = torch.zeros(5, dtype=torch.int64, device=self.device)

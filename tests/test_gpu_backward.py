@@ -1,0 +1,130 @@
+"""GPU backward (potr_loss_grad + potr_render_backward, and the autograd bridge) against the
+binary64 autograd gradient oracle (oracle/grad.py).
+
+Gradient tolerance, per parameter group: |gpu - oracle| <= 1e-3 |oracle| + 1e-4 max|oracle|.
+The GPU accumulates per-pixel terms in binary32 over tiles and views (relative rounding
+~1e-6 per term, amplified where terms of opposite sign cancel); the second term is the
+norm-wise floor for gradients that cancel to near zero.  The parity runs use the squared-error
+loss (lambda = 1): the L1 term's subgradient flips sign where |c - c_t| is below the 1e-5
+image tolerance, which is not a gradient error.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import build_frame, oracle_cfg, pack_targets
+from oracle import grad as G
+
+pytestmark = pytest.mark.gpu
+
+REL, FLOOR = 1e-3, 1e-4
+KEYS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+def _targets(scene, cams, cfg, seed, sigma=0.02):
+    ocfg = oracle_cfg(cfg)
+    out = []
+    for v, cam in enumerate(cams):
+        pv = oracle.prepare_view(scene, cam, ocfg)
+        img, *_ = oracle.render(pv, pv["vals"], pv["ranges"], cam, ocfg)
+        out.append((img + synth.target_noise(img.shape, sigma, seed, v)).astype(np.float32))
+    return out
+
+
+def _gpu_grads(fr, tg_flat, lam, store=True):
+    import torch
+
+    img = fr.image_buffer()
+    tf = fr.pixel_buffer() if store else None
+    nl = fr.pixel_buffer(torch.int32) if store else None
+    fr.render(img, tf, nl)
+    dL = torch.empty_like(img)
+    loss = torch.zeros(1, dtype=torch.float64, device=img.device)
+    fr.loss_grad(img, tg_flat, lam, dL, loss)
+    grads = {k: torch.empty_like(fr.scene[k]) for k in KEYS}
+    fr.render_backward(dL, grads, tf, nl)
+    torch.cuda.synchronize()
+    return float(loss.item()), {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}, dL, img
+
+
+def _check(got, want, what):
+    msgs = []
+    for k in KEYS:
+        g, o = got[k].reshape(-1), want[k].reshape(-1)
+        tol = REL * np.abs(o) + FLOOR * np.abs(o).max()
+        bad = np.abs(g - o) > tol
+        if bad.any():
+            i = int(np.argmax(np.abs(g - o) - tol))
+            msgs.append(f"{what}/{k}: {bad.sum()} of {bad.size} outside; worst got {g[i]!r} want {o[i]!r} "
+                        f"(max|o| {np.abs(o).max():.3e}, median rel {np.median(np.abs(g - o) / (np.abs(o) + 1e-30)):.2e})")
+    assert not msgs, "\n".join(msgs)
+
+
+@pytest.mark.parametrize("case", ["tiny16", "mixed8x32"])
+def test_backward_matches_gradient_oracle(case, tiny):
+    if case == "tiny16":
+        scene, cams, cfg = tiny.scene, tiny.cameras, dict(tile_w=16, tile_h=16, batch=256)
+    else:
+        scene = synth.uniform_cube_scene(3000, 88)
+        cams = [synth.look_at_camera((0.0, 0.3, -3.0), 120, 90), synth.look_at_camera((2.5, -0.2, -1.5), 72, 100)]
+        cfg = dict(tile_w=8, tile_h=32, batch=128)
+    tg = _targets(scene, cams, cfg, 17)
+    fr = build_frame(scene, cams, **cfg)
+    loss, grads, dL, img = _gpu_grads(fr, pack_targets(fr, tg), 1.0)
+    oloss, ograds, _ = G.loss_and_grad(scene, cams, oracle_cfg(cfg), tg, lam=1.0)
+    assert loss == pytest.approx(oloss, rel=1e-5)
+    _check(grads, ograds, case)
+
+
+def test_loss_grad_kernel_against_plain_formula(tiny):
+    import torch
+
+    cfg = dict(tile_w=16, tile_h=16, batch=256)
+    tg = _targets(tiny.scene, tiny.cameras, cfg, 5)
+    fr = build_frame(tiny.scene, tiny.cameras, **cfg)
+    tflat = pack_targets(fr, tg)
+    for lam in (0.0, 0.2, 1.0):
+        loss, _, dL, img = _gpu_grads(fr, tflat, lam)
+        r = (img - tflat).double()
+        want_loss = float(((1 - lam) * r.abs() + lam * r * r).mean())
+        want = ((1 - lam) * torch.sign(r) + 2 * lam * r) / r.numel()
+        assert loss == pytest.approx(want_loss, rel=1e-6)  # binary32 per-element terms, binary64 sum
+        assert torch.allclose(dL.double(), want, rtol=1e-6, atol=1e-12)
+
+
+def test_recompute_equals_store_and_is_deterministic(tiny):
+    sc = synth.uniform_cube_scene(3000, 88)
+    cams = [synth.look_at_camera((0.0, 0.3, -3.0), 120, 90), synth.look_at_camera((2.5, -0.2, -1.5), 72, 100)]
+    cfg = dict(tile_w=16, tile_h=16, batch=256)
+    tg = _targets(sc, cams, cfg, 3)
+    fr = build_frame(sc, cams, **cfg)
+    tflat = pack_targets(fr, tg)
+    _, g1, _, _ = _gpu_grads(fr, tflat, 0.2, store=True)
+    _, g2, _, _ = _gpu_grads(fr, tflat, 0.2, store=False)
+    _, g3, _, _ = _gpu_grads(fr, tflat, 0.2, store=True)
+    for k in KEYS:
+        assert np.array_equal(g1[k], g2[k]), k
+        assert np.array_equal(g1[k], g3[k]), k
+        assert np.count_nonzero(g1[k]) > 0
+
+
+def test_autograd_function_matches_c_path(tiny):
+    import torch
+
+    from paper_2601_14821_gb300.autograd import render
+
+    cfg = dict(tile_w=16, tile_h=16, batch=256)
+    tg = _targets(tiny.scene, tiny.cameras, cfg, 9)
+    fr = build_frame(tiny.scene, tiny.cameras, **cfg)
+    tflat = pack_targets(fr, tg)
+    _, want, _, _ = _gpu_grads(fr, tflat, 1.0)
+    params = {k: fr.scene[k].clone().requires_grad_(True) for k in KEYS}
+    for store in (True, False):
+        img = render(fr, params, store_transmittance=store)
+        loss = ((img - tflat) ** 2).mean()
+        gr = torch.autograd.grad(loss, [params[k] for k in KEYS])
+        for k, g in zip(KEYS, gr):
+            g = g.cpu().numpy().astype(np.float64)
+            w = want[k]
+            assert np.allclose(g, w, rtol=1e-5, atol=1e-7 * np.abs(w).max()), k
