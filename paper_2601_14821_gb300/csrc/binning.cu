@@ -15,11 +15,17 @@ namespace {
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanChunk = kScanThreads * kScanItems;  // items per block
-constexpr int kSortThreads = 256;
-constexpr int kSortRounds = 8;
-constexpr int kSortTile = kSortThreads * kSortRounds;  // items per block
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+constexpr int kOsThreads = 256;
+constexpr int kOsItems = 16;
+constexpr int kOsTile = kOsThreads * kOsItems;  // items per block and pass
+constexpr int kMaxPasses = 8;
+constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagInc = 2ull << 62, kCountMask = (1ull << 62) - 1;
+constexpr int kSpinLimit = 1 << 22;
+
+
 
 // -----------------------------------------------------------------------------------------
 // Block-wide exclusive scan of kScanChunk items.  Warp w owns items [w*256, w*256+256) with
@@ -118,102 +124,245 @@ __global__ void count_check_kernel(const uint64_t* __restrict__ total, int64_t c
   if (!ok) set_status(st, POTR_ERR_CAPACITY, (int64_t)t);
 }
 
+// One warp per 32 consecutive vk.  Their emission slots form one contiguous run (offsets are
+// the exclusive prefix of touched in vk order), so the lanes write consecutive slots: lane l
+// takes slots l, l + 32, ... of the run, finds the owning vk by a 5-step shuffle search over
+// the warp's exclusive counts, and derives the tile from the slot's rank in that vk's
+// row-major rectangle.  Stores are coalesced whatever the rectangle sizes.
+// It also counts the digits of every sort pass (ghist[pass][256]): the four depth digits are
+// shared by all instances of a vk (added once per vk, weighted by its count), the tile digits
+// are counted per instance with warp-aggregated shared-memory increments.
 __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ touched, const uint32_t* __restrict__ offsets,
                                                    const uint2* __restrict__ rect, const float* __restrict__ depth,
                                                    const potr_view_info* __restrict__ info, int64_t n, int64_t n_vk,
                                                    const uint64_t* __restrict__ m_eff, float4* __restrict__ raster,
-                                                   uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-  if (*m_eff == 0) return;
-  for (int64_t vk = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; vk < n_vk; vk += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t cnt = touched[vk];
-    if (cnt == 0) continue;
-    const uint32_t off = offsets[vk];
-    reinterpret_cast<float*>(raster + vk * 3 + 1)[3] = __uint_as_float(off);
-    const int v = (int)(vk / n);
-    const potr_view_info vi = info[v];
-    const uint2 r = rect[vk];
-    const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu, y1 = r.y >> 16;
-    const uint64_t lo = (uint64_t)__float_as_uint(depth[vk]);
-    uint32_t e = off;
-    for (uint32_t ty = y0; ty < y1; ++ty) {
-      const uint64_t row = (uint64_t)vi.tile_base + (uint64_t)ty * (uint64_t)vi.tiles_x;
-      for (uint32_t tx = x0; tx < x1; ++tx, ++e) {
-        keys[e] = ((row + tx) << 32) | lo;
-        vals[e] = (uint32_t)vk;
+                                                   uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, int passes,
+                                                   uint32_t* __restrict__ ghist) {
+  __shared__ uint32_t h[kMaxPasses][256];
+  for (int p = 0; p < kMaxPasses; ++p) h[p][threadIdx.x] = 0;
+  __syncthreads();
+  if (*m_eff == 0) return;  // uniform: nothing emitted, nothing counted
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  const int64_t warps_total = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t wv = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wv * 32 < n_vk; wv += warps_total) {
+    const int64_t vk = wv * 32 + lane;
+    uint32_t cnt = 0, off = 0, x0 = 0, y0 = 0, w = 1, lo = 0;
+    uint64_t row0 = 0, tiles_x = 0;
+    if (vk < n_vk) {
+      cnt = touched[vk];
+      if (cnt) {
+        off = offsets[vk];
+        reinterpret_cast<float*>(raster + vk * 3 + 1)[3] = __uint_as_float(off);
+        const potr_view_info vi = info[(int)(vk / n)];
+        const uint2 r = rect[vk];
+        x0 = r.x & 0xffffu;
+        y0 = r.x >> 16;
+        w = (r.y & 0xffffu) - x0;
+        tiles_x = (uint64_t)vi.tiles_x;
+        row0 = (uint64_t)vi.tile_base;
+        lo = __float_as_uint(depth[vk]);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) atomicAdd(&h[p][(lo >> (8 * p)) & 0xffu], cnt);
+      }
+    }
+    // exclusive prefix of cnt over the warp, total, and the run's first slot
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t excl = incl - cnt;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) continue;
+    const uint32_t first_lane = __ffs(__ballot_sync(0xffffffffu, cnt != 0)) - 1;
+    const uint32_t run0 = __shfl_sync(0xffffffffu, off, first_lane);
+    for (uint32_t e0 = 0; e0 < total; e0 += 32) {
+      const uint32_t e = e0 + lane;
+      // owner: the last lane whose exclusive count is <= e (lanes with cnt = 0 never win ties
+      // because the owner of e must have excl <= e < excl + cnt)
+      uint32_t owner = 0;
+#pragma unroll
+      for (int b = 16; b >= 1; b >>= 1) {
+        const uint32_t cand = owner + b;
+        const uint32_t ce = __shfl_sync(0xffffffffu, excl, cand & 31);
+        if (cand < 32 && ce <= e) owner = cand;
+      }
+      const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, owner);
+      const uint32_t o_x0 = __shfl_sync(0xffffffffu, x0, owner);
+      const uint32_t o_y0 = __shfl_sync(0xffffffffu, y0, owner);
+      const uint32_t o_w = __shfl_sync(0xffffffffu, w, owner);
+      const uint32_t o_lo = __shfl_sync(0xffffffffu, lo, owner);
+      const uint64_t o_row0 = __shfl_sync(0xffffffffu, row0, owner);
+      const uint64_t o_tx = __shfl_sync(0xffffffffu, tiles_x, owner);
+      uint64_t tile = 0;
+      if (e < total) {
+        const uint32_t li = e - o_excl;
+        const uint32_t dy = li / o_w, dx = li - dy * o_w;
+        tile = o_row0 + (uint64_t)(o_y0 + dy) * o_tx + (o_x0 + dx);
+        keys[run0 + e] = (tile << 32) | (uint64_t)o_lo;
+        vals[run0 + e] = (uint32_t)(wv * 32 + owner);
+      }
+      for (int p = 4; p < passes; ++p) {
+        const uint32_t d = (e < total) ? (uint32_t)(tile >> (8 * (p - 4))) & 0xffu : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (d < 256u && (peers & lt) == 0) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
       }
     }
   }
+  __syncthreads();
+  for (int p = 0; p < passes; ++p)
+    if (h[p][threadIdx.x]) atomicAdd(&ghist[p * 256 + threadIdx.x], h[p][threadIdx.x]);
 }
 
 // -----------------------------------------------------------------------------------------
-// Stable LSD radix sort, 8-bit digits.
+// Stable LSD radix sort, 8-bit digits, one kernel per pass ("onesweep": Adinets & Merrill,
+// 2022).  One read of the keys builds the digit histograms of every pass; then each pass
+// ranks 4096 items per block stably (per-warp match masks, warps in order), publishes its
+// per-digit counts, finds the counts of all earlier blocks by decoupled look-back over the
+// published words, and writes its items grouped by digit through shared memory so that the
+// global stores are contiguous runs.  Blocks take their item range from an atomic counter,
+// so every block a look-back waits on is already running; the wait is bounded and reports
+// POTR_ERR_TIMEOUT instead of hanging.
 // -----------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t* __restrict__ keys,
-                                                                  const uint64_t* __restrict__ m_eff, int shift,
-                                                                  int64_t n_tiles, uint32_t* __restrict__ hist) {
-  __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  const int64_t m = (int64_t)*m_eff;
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
-  for (int r = 0; r < kSortRounds; ++r) {
-    const int64_t i = base + r * kSortThreads + threadIdx.x;
-    if (i < m) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & 0xffu], 1u);
-  }
-  __syncthreads();
-  hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = h[threadIdx.x];  // digit-major
+size_t onesweep_smem_bytes() {
+  return sizeof(uint64_t) * kOsTile + sizeof(uint32_t) * kOsTile + sizeof(uint32_t) * (8 * 257 + 3 * 256);
 }
 
-__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const uint64_t* __restrict__ keys_in,
-                                                                     const uint32_t* __restrict__ vals_in,
-                                                                     const uint64_t* __restrict__ m_eff, int shift,
-                                                                     int64_t n_tiles, const uint32_t* __restrict__ hist_scan,
-                                                                     uint64_t* __restrict__ keys_out,
-                                                                     uint32_t* __restrict__ vals_out) {
-  __shared__ uint32_t dig_base[256];
-  __shared__ uint32_t warp_cnt[kSortThreads / 32][257];
+// Exclusive scan of one value per thread over a 256-thread block (returns this thread's prefix).
+__device__ __forceinline__ uint32_t block_exclusive_scan256(uint32_t x, uint32_t* tmp8) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t m = (int64_t)*m_eff;
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
-  if (base >= m) return;  // uniform per block
-  dig_base[threadIdx.x] = hist_scan[(int64_t)threadIdx.x * n_tiles + blockIdx.x];
+  uint32_t incl = x;
 #pragma unroll
-  for (int w = 0; w < kSortThreads / 32; ++w) warp_cnt[w][threadIdx.x] = 0;
-  if (threadIdx.x < kSortThreads / 32) warp_cnt[threadIdx.x][256] = 0;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) tmp8[warp] = incl;
   __syncthreads();
+  uint32_t wbase = 0;
+  for (int w = 0; w < warp; ++w) wbase += tmp8[w];
+  __syncthreads();
+  return wbase + incl - x;
+}
+
+__global__ void __launch_bounds__(256) digit_base_kernel(const uint32_t* __restrict__ ghist, int passes,
+                                                         uint32_t* __restrict__ gbase) {
+  __shared__ uint32_t tmp8[8];
+  for (int p = 0; p < passes; ++p) gbase[p * 256 + threadIdx.x] = block_exclusive_scan256(ghist[p * 256 + threadIdx.x], tmp8);
+}
+
+__global__ void __launch_bounds__(kOsThreads) onesweep_kernel(const uint64_t* __restrict__ keys_in,
+                                                              const uint32_t* __restrict__ vals_in,
+                                                              const uint64_t* __restrict__ m_eff, int shift,
+                                                              const uint32_t* __restrict__ gbase,
+                                                              uint32_t* __restrict__ tile_counter,
+                                                              unsigned long long* status,
+                                                              uint64_t* __restrict__ keys_out,
+                                                              uint32_t* __restrict__ vals_out,
+                                                              potr_device_status* __restrict__ st) {
+  extern __shared__ uint64_t os_smem[];
+  uint64_t* s_keys = os_smem;                                          // [kOsTile]
+  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + kOsTile);    // [kOsTile]
+  uint32_t* warp_cnt = s_vals + kOsTile;                               // [8][257]
+  uint32_t* blk_off = warp_cnt + 8 * 257;                              // [256]
+  uint32_t* dig_glob = blk_off + 256;                                  // [256]
+  uint32_t* tmp8 = dig_glob + 256;                                     // [8]
+  __shared__ uint32_t s_tile;
+  __shared__ int s_err;
+  if (threadIdx.x == 0) {
+    s_tile = atomicAdd(tile_counter, 1u);
+    s_err = 0;
+  }
+  for (int w = 0; w < 8; ++w) warp_cnt[w * 257 + threadIdx.x] = 0;
+  if (threadIdx.x < 8) warp_cnt[threadIdx.x * 257 + 256] = 0;
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const int64_t m = (int64_t)*m_eff;
+  const int64_t base = (int64_t)tile * kOsTile;
+  if (base >= m) return;  // uniform per block
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
-  for (int r = 0; r < kSortRounds; ++r) {
-    const int64_t i = base + r * kSortThreads + threadIdx.x;
+  uint64_t k[kOsItems];
+  uint32_t v[kOsItems], dg[kOsItems], lr[kOsItems];
+#pragma unroll
+  for (int r = 0; r < kOsItems; ++r) {
+    const int64_t i = base + warp * (kOsItems * 32) + r * 32 + lane;
     const bool valid = i < m;
-    uint64_t key = 0;
-    uint32_t val = 0, d = 256;
-    if (valid) {
-      key = keys_in[i];
-      val = vals_in[i];
-      d = (uint32_t)(key >> shift) & 0xffu;
-    }
+    k[r] = valid ? keys_in[i] : 0ull;
+    v[r] = valid ? vals_in[i] : 0u;
+    dg[r] = valid ? (uint32_t)(k[r] >> shift) & 0xffu : 256u;
+  }
+  // stable rank inside the warp: rounds in order, lanes in order
+  uint32_t* wc = warp_cnt + warp * 257;
+#pragma unroll
+  for (int r = 0; r < kOsItems; ++r) {
+    const uint32_t d = dg[r];
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const uint32_t rank = __popc(peers & lt);
-    if (rank == 0) warp_cnt[warp][d] = __popc(peers);
-    __syncthreads();
-    if (valid) {
-      uint32_t pos = dig_base[d] + rank;
-      for (int w = 0; w < warp; ++w) pos += warp_cnt[w][d];
-      keys_out[pos] = key;
-      vals_out[pos] = val;
-    }
-    __syncthreads();
-    {
-      uint32_t tot = 0;
-#pragma unroll
-      for (int w = 0; w < kSortThreads / 32; ++w) {
-        tot += warp_cnt[w][threadIdx.x];
-        warp_cnt[w][threadIdx.x] = 0;
-      }
-      dig_base[threadIdx.x] += tot;
-    }
-    __syncthreads();
+    const uint32_t c0 = wc[d];
+    __syncwarp();
+    if (rank == 0) wc[d] = c0 + __popc(peers);
+    __syncwarp();
+    lr[r] = c0 + rank;
   }
+  __syncthreads();
+  // per digit (one per thread): exclusive prefix over warps, block count
+  const uint32_t t = threadIdx.x;
+  uint32_t run = 0;
+  for (int w = 0; w < 8; ++w) {
+    const uint32_t c = warp_cnt[w * 257 + t];
+    warp_cnt[w * 257 + t] = run;
+    run += c;
+  }
+  volatile unsigned long long* vst = status;
+  const int64_t si = (int64_t)tile * 256 + t;
+  uint64_t excl = 0;
+  if (tile == 0) {
+    vst[si] = kFlagInc | run;
+  } else {
+    vst[si] = kFlagAgg | run;
+    int64_t p = (int64_t)tile - 1;
+    int spins = 0;
+    while (true) {
+      const unsigned long long x = vst[p * 256 + t];
+      const unsigned long long flag = x >> 62;
+      if (flag == 0) {
+        if (++spins > kSpinLimit) {
+          s_err = 1;
+          break;
+        }
+        continue;
+      }
+      excl += x & kCountMask;
+      if (flag == 2 || p == 0) break;
+      --p;
+    }
+    vst[si] = kFlagInc | (excl + run);
+  }
+  dig_glob[t] = gbase[t] + (uint32_t)excl;
+  blk_off[t] = block_exclusive_scan256(run, tmp8);
+  __syncthreads();
+  // items grouped by digit in shared memory
+#pragma unroll
+  for (int r = 0; r < kOsItems; ++r) {
+    if (dg[r] < 256u) {
+      const uint32_t pos = blk_off[dg[r]] + warp_cnt[warp * 257 + dg[r]] + lr[r];
+      s_keys[pos] = k[r];
+      s_vals[pos] = v[r];
+    }
+  }
+  __syncthreads();
+  const int nvalid = (int)min((int64_t)kOsTile, m - base);
+  for (int i = threadIdx.x; i < nvalid; i += kOsThreads) {
+    const uint64_t key = s_keys[i];
+    const uint32_t d = (uint32_t)(key >> shift) & 0xffu;
+    const uint32_t o = dig_glob[d] + ((uint32_t)i - blk_off[d]);
+    keys_out[o] = key;
+    vals_out[o] = s_vals[i];
+  }
+  if (threadIdx.x == 0 && s_err) set_status(st, POTR_ERR_TIMEOUT, 0);
 }
 
 __global__ void __launch_bounds__(256) tile_ranges_kernel(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ m_eff,
@@ -234,8 +383,8 @@ int bits_for(int64_t x) {  // bits needed to represent values in [0, x)
 }
 
 struct SortLayout {
-  int64_t n_vk, scan_words, tiles_cap, hist_n, hist_scan_words;
-  size_t off_scan, off_total, off_meff, off_keys_alt, off_vals_alt, off_hist, off_hist_scan, bytes;
+  int64_t n_vk, scan_words, tiles_cap;
+  size_t off_scan, off_total, off_meff, off_keys_alt, off_vals_alt, off_status, off_ghist, off_gbase, off_counter, bytes;
 };
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -244,17 +393,17 @@ SortLayout sort_layout(int64_t n, int32_t n_views, int64_t capacity) {
   SortLayout L{};
   L.n_vk = n * (int64_t)n_views;
   L.scan_words = scan_ws_words(L.n_vk > 0 ? L.n_vk : 1);
-  L.tiles_cap = ceil_div(capacity > 0 ? capacity : 1, kSortTile);
-  L.hist_n = 256 * L.tiles_cap;
-  L.hist_scan_words = scan_ws_words(L.hist_n);
+  L.tiles_cap = ceil_div(capacity > 0 ? capacity : 1, kOsTile);
   size_t o = 0;
   L.off_scan = o; o = align_up(o + sizeof(uint64_t) * L.scan_words);
   L.off_total = o; o = align_up(o + 2 * sizeof(uint64_t));
   L.off_meff = o; o = align_up(o + sizeof(uint64_t));
   L.off_keys_alt = o; o = align_up(o + sizeof(uint64_t) * (size_t)capacity);
   L.off_vals_alt = o; o = align_up(o + sizeof(uint32_t) * (size_t)capacity);
-  L.off_hist = o; o = align_up(o + sizeof(uint32_t) * (size_t)L.hist_n);
-  L.off_hist_scan = o; o = align_up(o + sizeof(uint64_t) * (size_t)L.hist_scan_words);
+  L.off_status = o; o = align_up(o + sizeof(unsigned long long) * 256 * (size_t)L.tiles_cap);
+  L.off_ghist = o; o = align_up(o + sizeof(uint32_t) * 256 * kMaxPasses);
+  L.off_gbase = o; o = align_up(o + sizeof(uint32_t) * 256 * kMaxPasses);
+  L.off_counter = o; o = align_up(o + sizeof(uint32_t) * kMaxPasses);
   L.bytes = o;
   return L;
 }
@@ -288,8 +437,10 @@ extern "C" potr_status potr_bin_sort(const potr_views* views, const potr_frame* 
   uint64_t* m_eff = reinterpret_cast<uint64_t*>(ws + L.off_meff);
   uint64_t* keys_alt = reinterpret_cast<uint64_t*>(ws + L.off_keys_alt);
   uint32_t* vals_alt = reinterpret_cast<uint32_t*>(ws + L.off_vals_alt);
-  uint32_t* hist = reinterpret_cast<uint32_t*>(ws + L.off_hist);
-  uint64_t* hist_scan_ws = reinterpret_cast<uint64_t*>(ws + L.off_hist_scan);
+  unsigned long long* status = reinterpret_cast<unsigned long long*>(ws + L.off_status);
+  uint32_t* ghist = reinterpret_cast<uint32_t*>(ws + L.off_ghist);
+  uint32_t* gbase = reinterpret_cast<uint32_t*>(ws + L.off_gbase);
+  uint32_t* counter = reinterpret_cast<uint32_t*>(ws + L.off_counter);
 
   if (scan_exclusive<uint32_t, uint32_t>(views->touched, views->offsets, L.n_vk, total, scan_ws, s) != cudaSuccess)
     return POTR_ERR_CUDA;
@@ -303,21 +454,26 @@ extern "C" potr_status potr_bin_sort(const potr_views* views, const potr_frame* 
   uint32_t* v_src = (passes & 1) ? vals_alt : d_vals;
   uint64_t* k_dst = (passes & 1) ? d_keys : keys_alt;
   uint32_t* v_dst = (passes & 1) ? d_vals : vals_alt;
+  if (passes > kMaxPasses) return POTR_ERR_UNSUPPORTED;
+  if (cudaMemsetAsync(ghist, 0, sizeof(uint32_t) * 256 * kMaxPasses, s) != cudaSuccess) return POTR_ERR_CUDA;
+  if (cudaMemsetAsync(counter, 0, sizeof(uint32_t) * kMaxPasses, s) != cudaSuccess) return POTR_ERR_CUDA;
   {
     const int64_t g = ceil_div(L.n_vk, 256);
-    emit_kernel<<<(unsigned)(g < 152 * 64 ? g : 152 * 64), 256, 0, s>>>(
+    emit_kernel<<<(unsigned)(g < 152 * 16 ? g : 152 * 16), 256, 0, s>>>(
         views->touched, views->offsets, reinterpret_cast<const uint2*>(views->rect), views->depth, frame->info, n, L.n_vk,
-        m_eff, reinterpret_cast<float4*>(views->raster), k_src, v_src);
+        m_eff, reinterpret_cast<float4*>(views->raster), k_src, v_src, passes, ghist);
+    POTR_CHECK_LAUNCH();
+    digit_base_kernel<<<1, 256, 0, s>>>(ghist, passes, gbase);
     POTR_CHECK_LAUNCH();
   }
+  const size_t os_smem = onesweep_smem_bytes();
+  if (cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem) != cudaSuccess)
+    return POTR_ERR_CUDA;
   for (int p = 0; p < passes; ++p) {
-    const int shift = 8 * p;
-    radix_hist_kernel<<<(unsigned)L.tiles_cap, kSortThreads, 0, s>>>(k_src, m_eff, shift, L.tiles_cap, hist);
-    POTR_CHECK_LAUNCH();
-    if (scan_exclusive<uint32_t, uint32_t>(hist, hist, L.hist_n, total + 1, hist_scan_ws, s) != cudaSuccess)
+    if (cudaMemsetAsync(status, 0, sizeof(unsigned long long) * 256 * (size_t)L.tiles_cap, s) != cudaSuccess)
       return POTR_ERR_CUDA;
-    radix_scatter_kernel<<<(unsigned)L.tiles_cap, kSortThreads, 0, s>>>(k_src, v_src, m_eff, shift, L.tiles_cap, hist,
-                                                                        k_dst, v_dst);
+    onesweep_kernel<<<(unsigned)L.tiles_cap, kOsThreads, os_smem, s>>>(k_src, v_src, m_eff, 8 * p, gbase + 256 * p,
+                                                                        counter + p, status, k_dst, v_dst, d_status);
     POTR_CHECK_LAUNCH();
     uint64_t* tk = k_src; k_src = k_dst; k_dst = tk;
     uint32_t* tv = v_src; v_src = v_dst; v_dst = tv;
