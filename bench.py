@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--views", type=int, default=0, help="use only the first V views (profiling cases)")
     ap.add_argument("--only-batched", action="store_true", help="time the batched frame only (profiling cases)")
+    ap.add_argument("--large", action="store_true",
+                    help="also time the 6M-splat, 300-view 1920x1080 workload (several minutes)")
+    ap.add_argument("--no-multiview", action="store_true", help="skip the 3M-splat, 200-view workload")
     return ap.parse_args()
 
 
@@ -317,6 +320,10 @@ def run_ours(args):
     # ---- fine-tuning step: 1M splats, 8 views 1280x720, L1 + squared-error loss (lambda 0.2)
     fwd_bwd = fwd_bwd_step_ms(args, dev, D)
 
+    # ---- many views of uneven resolution in view chunks, autotuned, eager and graph-replayed
+    multiview = None if args.no_multiview else multiview_config(args, dev, D, "batched", 16)
+    large = multiview_config(args, dev, D, "large", 8, fwd_bwd=True) if args.large else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         secs, _ = oracle_view_seconds(w, 0)
@@ -343,6 +350,8 @@ def run_ours(args):
             "pairs": pc,
             "fwd_bwd_ms_per_step": fwd_bwd["store"],
             "fwd_bwd": fwd_bwd,
+            "multiview": multiview,
+            "large": large,
             "roofline": {"kernel": "removal_kernel (memset + tile pass + per-splat reduce)", "bound": "alu",
                          "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / PEAK_FP32_TFLOPS, "traffic": None,
@@ -409,6 +418,104 @@ def fwd_bwd_step_ms(args, dev, D) -> dict:
         out[mode] = D.max_over_ranks(a.elapsed_time(b), dev) / args.steps
     out["per_pixel_bytes_stored"] = 8
     del fr
+    return out
+
+
+def multiview_config(args, dev, D, name: str, views_per_chunk: int, fwd_bwd: bool = False) -> dict:
+    """A many-view workload (``batched``: 3M splats, 200 views of mixed resolution; ``large``: 6M
+    splats, 300 views 1920x1080): the autotuner picks the tile shape and splat batch on the first
+    chunk, then whole passes over every view run chunk by chunk, eagerly and as one CUDA graph.
+    Steps: min(--steps, 3) per form (a pass is long)."""
+    import torch
+
+    import synth
+    from paper_2601_14821_gb300.batched import BatchedRemovalEffect, autotune
+    from paper_2601_14821_gb300.pipeline import RemovalEffectFrame, scene_to_device
+
+    w = synth.workload(name)
+    rec = synth.cameras_to_array(w.cameras)
+    scene_d = scene_to_device(w.scene, dev)
+    tuned = autotune(scene_d, rec, probe_views=views_per_chunk, steps=2, warmup=1, device=dev)
+    cfg = dict(tile_w=tuned["tile_w"], tile_h=tuned["tile_h"], batch=tuned["batch"])
+    # targets: render of the scene with 5 % of the splats dropped + N(0, 0.01) (seeded, on device)
+    keep = synth.target_drop_mask(w.scene.n, w.target_drop, w.seed)
+    tb = BatchedRemovalEffect(scene_to_device(w.scene.subset(keep), dev), rec, views_per_chunk, device=dev,
+                              with_importance=False, **cfg)
+    tb.plan()
+    targets = torch.empty(3 * tb.total_pixels, dtype=torch.float32, device=dev)
+    tb.render(targets)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(w.seed)
+    targets += w.target_noise * torch.randn(targets.shape, generator=gen, device=dev)
+    del tb
+    torch.cuda.empty_cache()
+    be = BatchedRemovalEffect(scene_d, rec, views_per_chunk, device=dev, **cfg)
+    n_inst = be.plan()
+    dmse = torch.zeros(be.n, dtype=torch.float64, device=dev)
+    imp = torch.zeros_like(dmse)
+    steps = max(1, min(args.steps, 3))
+    be.step(targets, dmse, imp)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    D.barrier()
+    a.record()
+    for _ in range(steps):
+        be.step(targets, dmse, imp)
+    b.record()
+    torch.cuda.synchronize()
+    eager_ms = D.max_over_ranks(a.elapsed_time(b), dev) / steps
+    graph_ms = None
+    try:
+        g = be.capture(targets, dmse, imp)
+        g.replay()
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(steps):
+            g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        graph_ms = D.max_over_ranks(a.elapsed_time(b), dev) / steps
+        del g
+    except Exception as exc:
+        graph_ms = f"capture failed: {exc}"
+    world = D.env_ranks()[2]
+    out = {"workload": name, "n_splats": be.n, "views_per_gpu": be.n_views, "views_per_chunk": views_per_chunk,
+           "instances": int(n_inst), "tuned": {k: tuned[k] for k in ("tile_w", "tile_h", "batch", "ms_per_view")},
+           "autotune_table": tuned["table"], "pass_ms": eager_ms,
+           "views_per_s": world * be.n_views / (eager_ms / 1e3),
+           "graph_pass_ms": graph_ms,
+           "graph_views_per_s": world * be.n_views / (graph_ms / 1e3) if isinstance(graph_ms, float) else None,
+           "steps": steps, "pool_gb": be.pool.nbytes() / 1e9}
+    del be
+    torch.cuda.empty_cache()
+    if fwd_bwd:
+        # one fine-tuning step on an 8-view minibatch of the workload
+        fr = RemovalEffectFrame(scene_d, rec[:8], device=dev, with_importance=False, **cfg)
+        fr.plan()
+        img = fr.image_buffer()
+        dL = torch.empty_like(img)
+        tgt = targets[: 3 * fr.total_pixels]
+        tf = fr.pixel_buffer()
+        nl = fr.pixel_buffer(torch.int32)
+        grads = {k: torch.empty_like(v) for k, v in scene_d.items()}
+
+        def st():
+            fr.preprocess()
+            fr.bin_sort()
+            fr.render(img, tf, nl)
+            fr.loss_grad(img, tgt, 0.2, dL)
+            fr.render_backward(dL, grads, tf, nl)
+
+        st()
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(steps):
+            st()
+        b.record()
+        torch.cuda.synchronize()
+        out["fwd_bwd_ms_per_step_8_views"] = D.max_over_ranks(a.elapsed_time(b), dev) / steps
+        del fr
+        torch.cuda.empty_cache()
     return out
 
 

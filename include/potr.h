@@ -162,6 +162,19 @@ POTR_API potr_status potr_view_layout(const potr_camera* h_cams, int32_t n_views
 POTR_API potr_status potr_preprocess(const potr_scene* scene, const potr_frame* frame, const potr_raster_config* cfg,
                             const potr_views* views, potr_stream_t stream);
 
+/* Workspace bytes of potr_tile_schedule. */
+POTR_API size_t potr_tile_schedule_workspace_size(void);
+
+/*
+ * Longest-list-first order of the frame's tiles (no counterpart in the paper: scheduling of
+ * the per-tile work of Section 3's compositing).  Tiles are bucketed by the bit length of their
+ * list length from d_tile_ranges; d_tile_order[0 .. total_tiles) receives the tiles of the
+ * longest bucket first and empty tiles last (order inside a bucket unspecified).  The word at
+ * d_tile_order[total_tiles] is left for the work counter of the tile kernels.
+ */
+POTR_API potr_status potr_tile_schedule(const potr_frame* frame, const uint32_t* d_tile_ranges,
+                                        uint32_t* d_tile_order, void* d_ws, size_t ws_bytes, potr_stream_t stream);
+
 /* Workspace bytes potr_bin_sort needs (scan partials, sort double buffers, histograms). */
 POTR_API size_t potr_bin_sort_workspace_size(int64_t n, int32_t n_views, int64_t total_tiles, int64_t instance_capacity);
 
@@ -187,11 +200,15 @@ POTR_API potr_status potr_bin_sort(const potr_views* views, const potr_frame* fr
  * c = sum T_k alpha_k c_k over a black background.  Outputs (device, per frame pixel):
  * d_images planar [3][H][W] per view at offset 3 * pixel_base; d_t_final the final
  * transmittance; d_n_last one past the tile-list position of the last composited splat
- * (0 if none).  Any output may be NULL.
+ * (0 if none).  Any output may be NULL.  d_tile_order (nullable, [total_tiles + 1]) is a tile
+ * order from potr_tile_schedule: with it a persistent grid takes tiles in that order (the last
+ * word is the work counter, reset by the call); without it one CTA renders each tile.  The
+ * order changes scheduling only, never a result.
  */
 POTR_API potr_status potr_render(const potr_views* views, const potr_frame* frame, const potr_raster_config* cfg,
-                        int64_t n, const uint32_t* d_vals, const uint32_t* d_tile_ranges, float* d_images,
-                        float* d_t_final, uint32_t* d_n_last, potr_stream_t stream);
+                                 int64_t n, const uint32_t* d_vals, const uint32_t* d_tile_ranges,
+                                 uint32_t* d_tile_order, float* d_images, float* d_t_final, uint32_t* d_n_last,
+                                 potr_stream_t stream);
 
 /*
  * Removal effect (Section IV-B).  For every pixel: the render above, then a back-to-front
@@ -209,11 +226,13 @@ POTR_API potr_status potr_render(const potr_views* views, const potr_frame* fram
  * With d_inst_imp / d_importance non-NULL the same is done for T_i alpha_i, giving
  * I_k += (sum_x T alpha) / (P_v n_views_total) (Section IV-A).  d_dsse_view (nullable,
  * [n_views][n] binary64) receives dSSE_k(v) itself.  d_images (nullable) receives the
- * render.  d_targets: planar [3][H][W] per view at offset 3 * pixel_base.
+ * render.  d_targets: planar [3][H][W] per view at offset 3 * pixel_base.  d_tile_order as in
+ * potr_render.
  */
 POTR_API potr_status potr_removal_effect(const potr_views* views, const potr_frame* frame, const potr_raster_config* cfg,
                                 int64_t n, const uint32_t* d_vals, const uint32_t* d_tile_ranges,
-                                const float* d_targets, int32_t n_views_total, int64_t instance_capacity,
+                                uint32_t* d_tile_order, const float* d_targets, int32_t n_views_total,
+                                int64_t instance_capacity,
                                 float* d_inst_dse,
                                 float* d_inst_imp, double* d_dmse, double* d_importance, double* d_dsse_view,
                                 float* d_images, potr_stream_t stream);
@@ -261,10 +280,12 @@ POTR_API size_t potr_render_backward_workspace_size(int64_t instance_capacity);
  * Transmittance: pass the forward render's d_t_final and d_n_last (stored), or NULL for both to
  * recompute them inside the kernel (no per-pixel storage).  The same inputs as potr_render plus
  * the scene; writes every plane of *grads.  d_ws: potr_render_backward_workspace_size bytes.
+ * d_tile_order as in potr_render.
  */
 POTR_API potr_status potr_render_backward(const potr_scene* scene, const potr_views* views, const potr_frame* frame,
                                           const potr_raster_config* cfg, const uint32_t* d_vals,
-                                          const uint32_t* d_tile_ranges, const float* d_t_final,
+                                          const uint32_t* d_tile_ranges, uint32_t* d_tile_order,
+                                          const float* d_t_final,
                                           const uint32_t* d_n_last, const float* d_dL_dimages,
                                           int64_t instance_capacity, const potr_scene_grads* grads, void* d_ws,
                                           size_t ws_bytes, potr_stream_t stream);

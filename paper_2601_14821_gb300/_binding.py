@@ -86,16 +86,18 @@ SIGNATURES = {
     "potr_bin_sort": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _I64, _P, _P, _P,
                              _P, _P, _SZ, _P]),
     "potr_render": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _P, _P, _P, _P, _P,
-                           _P]),
+                           _P, _P]),
     "potr_removal_effect": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _P, _P, _P,
-                                   _I32, _I64, _P, _P, _P, _P, _P, _P, _P]),
+                                   _P, _I32, _I64, _P, _P, _P, _P, _P, _P, _P]),
+    "potr_tile_schedule_workspace_size": (_SZ, []),
+    "potr_tile_schedule": (_I32, [C.POINTER(Frame), _P, _P, _P, _SZ, _P]),
     "potr_pair_stats": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _P, _P, _P, _P]),
     "potr_launch_count": (C.c_uint64, []),
     "potr_loss_workspace_size": (_SZ, [_I64]),
     "potr_loss_grad": (_I32, [C.POINTER(Frame), _P, _P, C.c_float, _P, _P, _P, _SZ, _P]),
     "potr_render_backward_workspace_size": (_SZ, [_I64]),
     "potr_render_backward": (_I32, [C.POINTER(Scene), C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _P,
-                                    _P, _P, _P, _P, _I64, C.POINTER(SceneGrads), _P, _SZ, _P]),
+                                    _P, _P, _P, _P, _P, _I64, C.POINTER(SceneGrads), _P, _SZ, _P]),
     "potr_bin_sort_static": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _I64, _P, _P,
                                     _P, _P, _P]),
 }
@@ -186,18 +188,27 @@ def potr_bin_sort(views: Views, frame: Frame, cfg: RasterConfig, n: int, capacit
 
 
 def potr_render(views: Views, frame: Frame, cfg: RasterConfig, n: int, vals, ranges, images=None, t_final=None,
-                n_last=None, stream=None):
+                n_last=None, stream=None, order=None):
     _check("potr_render", lib().potr_render(C.byref(views), C.byref(frame), C.byref(cfg), n, ptr(vals), ptr(ranges),
-                                            ptr(images), ptr(t_final), ptr(n_last), stream_handle(stream)))
+                                            ptr(order), ptr(images), ptr(t_final), ptr(n_last), stream_handle(stream)))
 
 
 def potr_removal_effect(views: Views, frame: Frame, cfg: RasterConfig, n: int, vals, ranges, targets,
                         n_views_total: int, capacity: int, inst_dse, inst_imp=None, dmse=None, importance=None,
-                        dsse_view=None, images=None, stream=None):
+                        dsse_view=None, images=None, stream=None, order=None):
     _check("potr_removal_effect",
            lib().potr_removal_effect(C.byref(views), C.byref(frame), C.byref(cfg), n, ptr(vals), ptr(ranges),
-                                     ptr(targets), n_views_total, capacity, ptr(inst_dse), ptr(inst_imp), ptr(dmse),
-                                     ptr(importance), ptr(dsse_view), ptr(images), stream_handle(stream)))
+                                     ptr(order), ptr(targets), n_views_total, capacity, ptr(inst_dse), ptr(inst_imp),
+                                     ptr(dmse), ptr(importance), ptr(dsse_view), ptr(images), stream_handle(stream)))
+
+
+def potr_tile_schedule_workspace_size() -> int:
+    return int(lib().potr_tile_schedule_workspace_size())
+
+
+def potr_tile_schedule(frame: Frame, ranges, order, ws, stream=None):
+    _check("potr_tile_schedule", lib().potr_tile_schedule(C.byref(frame), ptr(ranges), ptr(order), ptr(ws), ws.numel(),
+                                                          stream_handle(stream)))
 
 
 def potr_pair_stats(views: Views, frame: Frame, cfg: RasterConfig, n: int, vals, ranges, counts, stream=None):
@@ -232,8 +243,8 @@ def potr_render_backward_workspace_size(capacity: int) -> int:
 
 
 def potr_render_backward(scene: Scene, views: Views, frame: Frame, cfg: RasterConfig, vals, ranges, t_final, n_last,
-                         dL_dimages, capacity: int, grads: SceneGrads, ws, stream=None):
+                         dL_dimages, capacity: int, grads: SceneGrads, ws, stream=None, order=None):
     _check("potr_render_backward",
            lib().potr_render_backward(C.byref(scene), C.byref(views), C.byref(frame), C.byref(cfg), ptr(vals),
-                                      ptr(ranges), ptr(t_final), ptr(n_last), ptr(dL_dimages), capacity,
+                                      ptr(ranges), ptr(order), ptr(t_final), ptr(n_last), ptr(dL_dimages), capacity,
                                       C.byref(grads), ptr(ws), ws.numel(), stream_handle(stream)))

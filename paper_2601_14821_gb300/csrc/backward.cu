@@ -99,13 +99,16 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const float4* __re
                                                               potr_raster_config cfg, const float* __restrict__ t_final,
                                                               const uint32_t* __restrict__ n_last,
                                                               const float* __restrict__ dL_dimg, int64_t capacity,
-                                                              float* __restrict__ inst_grad) {
+                                                              float* __restrict__ inst_grad, TileQueue queue) {
   extern __shared__ float4 dyn[];
   float4* smem = dyn;                                                // [kBwdBatch][3]
   float* red = reinterpret_cast<float*>(dyn + 3 * kBwdBatch);        // [kGradQ][kWarps][kBwdBatch]
   uint8_t* wmask = reinterpret_cast<uint8_t*>(red + kGradQ * kWarps * kBwdBatch);
   __shared__ uint32_t max_last_w[kWarps];
-  const TileCtx c = tile_ctx(info, n_views, ranges, cfg);
+  __shared__ uint32_t s_slot;
+  int64_t tile;
+  for (bool first = true; next_tile(queue, &s_slot, first, tile); first = false) {
+  const TileCtx c = tile_ctx(info, n_views, ranges, cfg, tile);
   float T = 1.0f;
   uint32_t last = 0;
   if (RECOMPUTE) {
@@ -225,6 +228,7 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const float4* __re
     }
     top = lo;
   }
+  }  // tiles
 }
 
 // ---------------------------------------------------------------------------------------
@@ -506,7 +510,8 @@ extern "C" size_t potr_render_backward_workspace_size(int64_t instance_capacity)
 
 extern "C" potr_status potr_render_backward(const potr_scene* scene, const potr_views* views, const potr_frame* frame,
                                             const potr_raster_config* cfg, const uint32_t* d_vals,
-                                            const uint32_t* d_tile_ranges, const float* d_t_final,
+                                            const uint32_t* d_tile_ranges, uint32_t* d_tile_order,
+                                            const float* d_t_final,
                                             const uint32_t* d_n_last, const float* d_dL_dimages,
                                             int64_t instance_capacity, const potr_scene_grads* grads, void* d_ws,
                                             size_t ws_bytes, potr_stream_t stream) {
@@ -529,20 +534,25 @@ extern "C" potr_status potr_render_backward(const potr_scene* scene, const potr_
     return POTR_ERR_CUDA;
   const size_t smem = bwd_smem_bytes();
   const bool recompute = d_t_final == nullptr;
+  TileQueue q;
+  q.order = d_tile_order;
+  q.counter = d_tile_order ? d_tile_order + frame->total_tiles : nullptr;
+  q.total = (uint32_t)frame->total_tiles;
+  if (d_tile_order && cudaMemsetAsync(q.counter, 0, sizeof(uint32_t), s) != cudaSuccess) return POTR_ERR_CUDA;
   if (recompute) {
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(render_bwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return POTR_ERR_CUDA;
-    render_bwd_kernel<true><<<(unsigned)frame->total_tiles, kThreads, smem, s>>>(
+    render_bwd_kernel<true><<<tile_grid(render_bwd_kernel<true>, smem, q, frame->total_tiles), kThreads, smem, s>>>(
         reinterpret_cast<const float4*>(views->raster), d_vals, d_tile_ranges, frame->info, frame->n_views, *cfg,
-        nullptr, nullptr, d_dL_dimages, instance_capacity, inst_grad);
+        nullptr, nullptr, d_dL_dimages, instance_capacity, inst_grad, q);
   } else {
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(render_bwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return POTR_ERR_CUDA;
-    render_bwd_kernel<false><<<(unsigned)frame->total_tiles, kThreads, smem, s>>>(
+    render_bwd_kernel<false><<<tile_grid(render_bwd_kernel<false>, smem, q, frame->total_tiles), kThreads, smem, s>>>(
         reinterpret_cast<const float4*>(views->raster), d_vals, d_tile_ranges, frame->info, frame->n_views, *cfg,
-        d_t_final, d_n_last, d_dL_dimages, instance_capacity, inst_grad);
+        d_t_final, d_n_last, d_dL_dimages, instance_capacity, inst_grad, q);
   }
   POTR_CHECK_LAUNCH();
   const int64_t n = scene->n;

@@ -32,24 +32,29 @@ __global__ void __launch_bounds__(kThreads) render_kernel(const float4* __restri
                                                           const uint32_t* __restrict__ ranges,
                                                           const potr_view_info* __restrict__ info, int n_views,
                                                           potr_raster_config cfg, float* __restrict__ images,
-                                                          float* __restrict__ t_final, uint32_t* __restrict__ n_last) {
+                                                          float* __restrict__ t_final, uint32_t* __restrict__ n_last,
+                                                          TileQueue queue) {
   extern __shared__ float4 smem[];
   uint8_t* wmask = reinterpret_cast<uint8_t*>(smem + 3 * BATCH);
-  const TileCtx c = tile_ctx(info, n_views, ranges, cfg);
-  float C[3], T;
-  uint32_t last;
-  forward_walk<BATCH>(smem, wmask, raster, vals, c, cfg, C, T, last);
-  if (!c.inside) return;
-  const int64_t pix = c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
-  const int64_t plane = (int64_t)c.vi.width * c.vi.height;
-  if (images) {
-    float* im = images + 3 * c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
-    im[0] = C[0];
-    im[plane] = C[1];
-    im[2 * plane] = C[2];
+  __shared__ uint32_t s_slot;
+  int64_t tile;
+  for (bool first = true; next_tile(queue, &s_slot, first, tile); first = false) {
+    const TileCtx c = tile_ctx(info, n_views, ranges, cfg, tile);
+    float C[3], T;
+    uint32_t last;
+    forward_walk<BATCH>(smem, wmask, raster, vals, c, cfg, C, T, last);
+    if (!c.inside) continue;
+    const int64_t pix = c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
+    const int64_t plane = (int64_t)c.vi.width * c.vi.height;
+    if (images) {
+      float* im = images + 3 * c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
+      im[0] = C[0];
+      im[plane] = C[1];
+      im[2 * plane] = C[2];
+    }
+    if (t_final) t_final[pix] = T;
+    if (n_last) n_last[pix] = last;
   }
-  if (t_final) t_final[pix] = T;
-  if (n_last) n_last[pix] = last;
 }
 
 // Lanes l and l ^ 16 both receive the sum over all 32 lanes of v[l & 15] (fixed order):
@@ -83,14 +88,17 @@ __global__ void __launch_bounds__(kThreads) removal_kernel(const float4* __restr
                                                            const potr_view_info* __restrict__ info, int n_views,
                                                            potr_raster_config cfg, const float* __restrict__ targets,
                                                            float* __restrict__ images, float* __restrict__ inst_dse,
-                                                           float* __restrict__ inst_imp) {
+                                                           float* __restrict__ inst_imp, TileQueue queue) {
   extern __shared__ float4 dyn[];
   float4* smem = dyn;                                               // [BATCH][3] raster records
   float* red_d = reinterpret_cast<float*>(dyn + 3 * BATCH);         // [kWarps][BATCH] warp sums of dSE
   float* red_i = red_d + kWarps * BATCH;                            // [kWarps][BATCH] warp sums of T alpha
   uint8_t* wmask = reinterpret_cast<uint8_t*>(red_d + kWarps * BATCH * (IMP ? 2 : 1));  // [BATCH]
   __shared__ uint32_t max_last_w[kWarps];
-  const TileCtx c = tile_ctx(info, n_views, ranges, cfg);
+  __shared__ uint32_t s_slot;
+  int64_t tile;
+  for (bool first = true; next_tile(queue, &s_slot, first, tile); first = false) {
+  const TileCtx c = tile_ctx(info, n_views, ranges, cfg, tile);
   float C[3], T;
   uint32_t last;
   forward_walk<BATCH>(smem, wmask, raster, vals, c, cfg, C, T, last);
@@ -206,6 +214,7 @@ __global__ void __launch_bounds__(kThreads) removal_kernel(const float4* __restr
     }
     top = lo;
   }
+  }  // tiles
 }
 
 // Per splat k: dSSE_k(v) = sum over its emission slots (emission order), then
@@ -261,11 +270,11 @@ __global__ void __launch_bounds__(256) splat_reduce_kernel(const uint32_t* __res
 template <int BATCH>
 cudaError_t launch_render(const potr_views* views, const potr_frame* frame, const potr_raster_config& cfg,
                           const uint32_t* vals, const uint32_t* ranges, float* images, float* t_final,
-                          uint32_t* n_last, cudaStream_t s) {
+                          uint32_t* n_last, const TileQueue& q, cudaStream_t s) {
   const size_t smem = sizeof(float4) * 3 * BATCH + BATCH;
-  render_kernel<BATCH><<<(unsigned)frame->total_tiles, kThreads, smem, s>>>(
-      reinterpret_cast<const float4*>(views->raster), vals, ranges, frame->info, frame->n_views, cfg, images, t_final,
-      n_last);
+  const unsigned grid = tile_grid(render_kernel<BATCH>, smem, q, frame->total_tiles);
+  render_kernel<BATCH><<<grid, kThreads, smem, s>>>(reinterpret_cast<const float4*>(views->raster), vals, ranges,
+                                                    frame->info, frame->n_views, cfg, images, t_final, n_last, q);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -273,45 +282,58 @@ cudaError_t launch_render(const potr_views* views, const potr_frame* frame, cons
 template <int BATCH, bool IMP>
 cudaError_t launch_removal(const potr_views* views, const potr_frame* frame, const potr_raster_config& cfg,
                            const uint32_t* vals, const uint32_t* ranges, const float* targets, float* images,
-                           float* inst_dse, float* inst_imp, cudaStream_t s) {
+                           float* inst_dse, float* inst_imp, const TileQueue& q, cudaStream_t s) {
   constexpr size_t smem = removal_smem_bytes<BATCH, IMP>();
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(removal_kernel<BATCH, IMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  removal_kernel<BATCH, IMP><<<(unsigned)frame->total_tiles, kThreads, smem, s>>>(
-      reinterpret_cast<const float4*>(views->raster), vals, ranges, frame->info, frame->n_views, cfg, targets, images,
-      inst_dse, inst_imp);
+  const unsigned grid = tile_grid(removal_kernel<BATCH, IMP>, smem, q, frame->total_tiles);
+  removal_kernel<BATCH, IMP><<<grid, kThreads, smem, s>>>(reinterpret_cast<const float4*>(views->raster), vals, ranges,
+                                                          frame->info, frame->n_views, cfg, targets, images, inst_dse,
+                                                          inst_imp, q);
   note_launches(1);
   return cudaGetLastError();
 }
 
+// The work counter word after the order is reset before each persistent launch.
+cudaError_t make_queue(uint32_t* d_tile_order, int64_t total_tiles, TileQueue& q, cudaStream_t s) {
+  q.order = d_tile_order;
+  q.counter = d_tile_order ? d_tile_order + total_tiles : nullptr;
+  q.total = (uint32_t)total_tiles;
+  if (d_tile_order) return cudaMemsetAsync(q.counter, 0, sizeof(uint32_t), s);
+  return cudaSuccess;
+}
 
 }  // namespace
 }  // namespace potr
 
 extern "C" potr_status potr_render(const potr_views* views, const potr_frame* frame, const potr_raster_config* cfg,
-                                   int64_t n, const uint32_t* d_vals, const uint32_t* d_tile_ranges, float* d_images,
-                                   float* d_t_final, uint32_t* d_n_last, potr_stream_t stream) {
+                                   int64_t n, const uint32_t* d_vals, const uint32_t* d_tile_ranges,
+                                   uint32_t* d_tile_order, float* d_images, float* d_t_final, uint32_t* d_n_last,
+                                   potr_stream_t stream) {
   using namespace potr;
   if (!views || !frame || !valid_cfg(cfg) || !d_vals || !d_tile_ranges || !views->raster || !frame->info)
     return POTR_ERR_INVALID_ARGUMENT;
   if (n <= 0 || frame->n_views < 1 || frame->total_tiles <= 0 || frame->total_tiles > 0x7fffffffll)
     return POTR_ERR_INVALID_ARGUMENT;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  TileQueue q;
+  if (make_queue(d_tile_order, frame->total_tiles, q, s) != cudaSuccess) return POTR_ERR_CUDA;
   cudaError_t e;
   switch (cfg->batch) {
-    case 128: e = launch_render<128>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, s); break;
-    case 256: e = launch_render<256>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, s); break;
-    default: e = launch_render<512>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, s); break;
+    case 128: e = launch_render<128>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, q, s); break;
+    case 256: e = launch_render<256>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, q, s); break;
+    default: e = launch_render<512>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, q, s); break;
   }
   return e == cudaSuccess ? POTR_OK : POTR_ERR_CUDA;
 }
 
 extern "C" potr_status potr_removal_effect(const potr_views* views, const potr_frame* frame,
                                            const potr_raster_config* cfg, int64_t n, const uint32_t* d_vals,
-                                           const uint32_t* d_tile_ranges, const float* d_targets, int32_t n_views_total,
+                                           const uint32_t* d_tile_ranges, uint32_t* d_tile_order,
+                                           const float* d_targets, int32_t n_views_total,
                                            int64_t instance_capacity, float* d_inst_dse, float* d_inst_imp,
                                            double* d_dmse, double* d_importance, double* d_dsse_view, float* d_images,
                                            potr_stream_t stream) {
@@ -328,14 +350,16 @@ extern "C" potr_status potr_removal_effect(const potr_views* views, const potr_f
   if (d_inst_imp && cudaMemsetAsync(d_inst_imp, 0, sizeof(float) * (size_t)instance_capacity, s) != cudaSuccess)
     return POTR_ERR_CUDA;
   const bool imp = d_inst_imp != nullptr;
+  TileQueue q;
+  if (make_queue(d_tile_order, frame->total_tiles, q, s) != cudaSuccess) return POTR_ERR_CUDA;
   cudaError_t e;
   switch (cfg->batch * 2 + (imp ? 1 : 0)) {
-    case 256: e = launch_removal<128, false>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, s); break;
-    case 257: e = launch_removal<128, true>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, s); break;
-    case 512: e = launch_removal<256, false>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, s); break;
-    case 513: e = launch_removal<256, true>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, s); break;
-    case 1024: e = launch_removal<512, false>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, s); break;
-    default: e = launch_removal<512, true>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, s); break;
+    case 256: e = launch_removal<128, false>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, q, s); break;
+    case 257: e = launch_removal<128, true>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, q, s); break;
+    case 512: e = launch_removal<256, false>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, q, s); break;
+    case 513: e = launch_removal<256, true>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, q, s); break;
+    case 1024: e = launch_removal<512, false>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, q, s); break;
+    default: e = launch_removal<512, true>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, q, s); break;
   }
   if (e != cudaSuccess) return POTR_ERR_CUDA;
   if (d_dmse || d_importance || d_dsse_view) {
@@ -366,7 +390,7 @@ __global__ void __launch_bounds__(kThreads) pair_stats_kernel(const float4* __re
                                                               unsigned long long* __restrict__ counts) {
   extern __shared__ float4 smem[];
   __shared__ unsigned long long red[5][kWarps];
-  const TileCtx c = tile_ctx(info, n_views, ranges, cfg);
+  const TileCtx c = tile_ctx(info, n_views, ranges, cfg, blockIdx.x);
   float T = 1.0f;
   uint32_t n_ex = 0, n_pass = 0, n_comp = 0, last = 0, pass_at_last = 0;
   bool done = !c.inside;

@@ -45,9 +45,10 @@ struct TileCtx {
 };
 
 __device__ __forceinline__ TileCtx tile_ctx(const potr_view_info* __restrict__ info, int n_views,
-                                            const uint32_t* __restrict__ ranges, const potr_raster_config& cfg) {
+                                            const uint32_t* __restrict__ ranges, const potr_raster_config& cfg,
+                                            int64_t tile) {
   TileCtx c;
-  c.tile = blockIdx.x;
+  c.tile = tile;
   c.view = view_of_tile(info, n_views, c.tile);
   c.vi = info[c.view];
   const int64_t local = c.tile - c.vi.tile_base;
@@ -167,6 +168,43 @@ struct KahanSum {
   }
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
+
+// Tile scheduling.  Without an order every CTA renders the tile of its block index.  With an
+// order (a permutation of the frame's tiles, longest lists first, plus one work-counter word
+// after it) a persistent grid of CTAs takes the next entry from the counter until the order
+// is exhausted; only the processing order changes, never a result.
+struct TileQueue {
+  const uint32_t* order;  // nullable
+  uint32_t* counter;
+  uint32_t total;
+};
+
+__device__ __forceinline__ bool next_tile(const TileQueue& q, uint32_t* s_slot, bool first, int64_t& tile) {
+  if (!q.order) {
+    tile = blockIdx.x;
+    return first;
+  }
+  __syncthreads();  // the previous tile's reads of s_slot and shared memory are done
+  if (threadIdx.x == 0) *s_slot = atomicAdd(q.counter, 1u);
+  __syncthreads();
+  const uint32_t item = *s_slot;
+  if (item >= q.total) return false;
+  tile = q.order[item];
+  return true;
+}
+
+// Grid for a tile kernel: one CTA per tile, or as many CTAs as fit on the device at once.
+template <typename K>
+inline unsigned tile_grid(K kernel, size_t smem, const TileQueue& q, int64_t total_tiles) {
+  if (!q.order) return (unsigned)total_tiles;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kTilePixels, smem);
+  int64_t g = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  if (g > total_tiles) g = total_tiles;
+  return (unsigned)(g > 0 ? g : 1);
+}
 
 inline bool valid_cfg(const potr_raster_config* cfg) {
   if (!cfg) return false;

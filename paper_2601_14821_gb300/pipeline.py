@@ -27,11 +27,34 @@ def scene_struct(sc: dict) -> B.Scene:
                    sc["opacity_logits"].data_ptr(), sc["sh"].data_ptr(), int(sc["means"].shape[-1]))
 
 
+class BufferPool:
+    """Named device buffers shared by frames that run one after another on one stream (the view
+    chunks of a batched pass).  ``get`` returns a typed view of the named buffer, growing it when
+    a caller needs more; frames re-take their views (``rebind``) once every frame is planned, so
+    nothing is reallocated while steps run or a CUDA graph replays."""
+
+    def __init__(self, device):
+        self.device = torch.device(device)
+        self.store: dict[str, torch.Tensor] = {}
+
+    def get(self, name: str, numel: int, dtype) -> torch.Tensor:
+        esize = torch.empty(0, dtype=dtype).element_size()
+        nbytes = max(int(numel), 1) * esize
+        t = self.store.get(name)
+        if t is None or t.numel() < nbytes:
+            t = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.store[name] = t
+        return t[:nbytes].view(dtype)
+
+    def nbytes(self) -> int:
+        return sum(t.numel() for t in self.store.values())
+
+
 class RemovalEffectFrame:
     """All device buffers for one frame (scene x views) and the C calls over them."""
 
     def __init__(self, scene: dict, cams_rec: np.ndarray, device="cuda", capacity: int | None = None,
-                 with_importance: bool = True, **cfg):
+                 with_importance: bool = True, schedule: bool = True, pool: BufferPool | None = None, **cfg):
         self.device = torch.device(device)
         self.scene = scene
         self.scene_c = scene_struct(scene)
@@ -47,35 +70,44 @@ class RemovalEffectFrame:
         self.d_info = torch.from_numpy(info.copy()).to(dev)
         self.frame = B.Frame(self.d_cams.data_ptr(), self.d_info.data_ptr(), self.n_views, self.total_tiles,
                              self.total_pixels)
-        vn = self.n_views * self.n
-        i32 = torch.int32
+        self.pool = pool if pool is not None else BufferPool(dev)
         self.cov3d = torch.empty(6 * self.n, dtype=torch.float32, device=dev)
         self.opacity = torch.empty(self.n, dtype=torch.float32, device=dev)
-        self.raster = torch.empty(vn * 12, dtype=torch.float32, device=dev)
-        self.depth = torch.empty(vn, dtype=torch.float32, device=dev)
-        self.rect = torch.empty(2 * vn, dtype=i32, device=dev)
-        self.touched = torch.empty(vn, dtype=i32, device=dev)
-        self.offsets = torch.empty(vn, dtype=i32, device=dev)
-        self.n_instances = torch.zeros(1, dtype=i32, device=dev)
+        self.n_instances = torch.zeros(1, dtype=torch.int32, device=dev)
         self.status = torch.zeros(2, dtype=torch.int64, device=dev)
+        self.sched_ws = torch.empty(B.potr_tile_schedule_workspace_size(), dtype=torch.uint8, device=dev)
+        self.schedule = schedule
+        self.with_importance = with_importance
+        self.capacity = int(capacity) if capacity else 1
+        self.rebind()
+
+    # -------------------------------------------------------------------------------------
+    def rebind(self):
+        """(Re)take every pooled buffer at the current sizes and rebuild the C views."""
+        vn = self.n_views * self.n
+        i32, P = torch.int32, self.pool
+        self.raster = P.get("raster", vn * 12, torch.float32)
+        self.depth = P.get("depth", vn, torch.float32)
+        self.rect = P.get("rect", 2 * vn, i32)
+        self.touched = P.get("touched", vn, i32)
+        self.offsets = P.get("offsets", vn, i32)
+        self.ranges = P.get("ranges", 2 * self.total_tiles, i32)
+        # longest-list-first tile order for the persistent tile kernels (+1 work-counter word)
+        self.order = P.get("order", self.total_tiles + 1, i32) if self.schedule else None
         self.views = B.Views(self.cov3d.data_ptr(), self.opacity.data_ptr(), self.raster.data_ptr(),
                              self.depth.data_ptr(), self.rect.data_ptr(), self.touched.data_ptr(),
                              self.offsets.data_ptr(), self.n_instances.data_ptr())
-        self.ranges = torch.empty(2 * self.total_tiles, dtype=i32, device=dev)
-        self.with_importance = with_importance
-        self.capacity = 0
-        self._alloc(capacity if capacity else 1)
+        self._alloc(self.capacity)
 
-    # -------------------------------------------------------------------------------------
     def _alloc(self, capacity: int):
-        dev = self.device
+        P = self.pool
         self.capacity = int(capacity)
-        self.keys = torch.empty(self.capacity, dtype=torch.int64, device=dev)
-        self.vals = torch.empty(self.capacity, dtype=torch.int32, device=dev)
-        ws = B.potr_bin_sort_workspace_size(self.n, self.n_views, self.total_tiles, self.capacity)
-        self.ws = torch.empty(ws, dtype=torch.uint8, device=dev)
-        self.inst_dse = torch.empty(self.capacity, dtype=torch.float32, device=dev)
-        self.inst_imp = torch.empty(self.capacity, dtype=torch.float32, device=dev) if self.with_importance else None
+        self.keys = P.get("keys", self.capacity, torch.int64)
+        self.vals = P.get("vals", self.capacity, torch.int32)
+        self.ws = P.get("sort_ws", B.potr_bin_sort_workspace_size(self.n, self.n_views, self.total_tiles,
+                                                                   self.capacity), torch.uint8)
+        self.inst_dse = P.get("inst_dse", self.capacity, torch.float32)
+        self.inst_imp = P.get("inst_imp", self.capacity, torch.float32) if self.with_importance else None
 
     def plan(self, slack: float = 1.05) -> int:
         """Run preprocess + binning once, grow the instance capacity to fit, return the count."""
@@ -100,19 +132,23 @@ class RemovalEffectFrame:
         B.potr_preprocess(self.scene_c, self.frame, self.cfg, self.views, stream)
 
     def bin_sort(self, stream=None):
+        """Binning + sort, then (with scheduling on) the longest-list-first tile order."""
         self.status.zero_()
         B.potr_bin_sort(self.views, self.frame, self.cfg, self.n, self.capacity, self.keys, self.vals, self.ranges,
                         self.status, self.ws, stream)
+        if self.schedule:
+            B.potr_tile_schedule(self.frame, self.ranges, self.order, self.sched_ws, stream)
 
     def render(self, images=None, t_final=None, n_last=None, stream=None):
-        B.potr_render(self.views, self.frame, self.cfg, self.n, self.vals, self.ranges, images, t_final, n_last, stream)
+        B.potr_render(self.views, self.frame, self.cfg, self.n, self.vals, self.ranges, images, t_final, n_last, stream,
+                      order=self.order)
 
     def removal_effect(self, targets, dmse, importance=None, n_views_total=None, dsse_view=None, images=None,
                        stream=None):
         B.potr_removal_effect(self.views, self.frame, self.cfg, self.n, self.vals, self.ranges, targets,
                               int(n_views_total or self.n_views), self.capacity, self.inst_dse,
                               self.inst_imp if importance is not None else None, dmse, importance, dsse_view,
-                              images, stream)
+                              images, stream, order=self.order)
 
     def bind_scene(self, scene: dict):
         """Point the frame at other parameter tensors of the same size (e.g. autograd inputs)."""
@@ -135,13 +171,10 @@ class RemovalEffectFrame:
 
     def render_backward(self, dL_dimages, grads: dict, t_final=None, n_last=None, stream=None):
         """Parameter gradients (dict of tensors shaped like the scene, overwritten)."""
-        need = B.potr_render_backward_workspace_size(self.capacity)
-        ws = getattr(self, "_bwd_ws", None)
-        if ws is None or ws.numel() < need:
-            ws = self._bwd_ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        ws = self.pool.get("bwd_ws", B.potr_render_backward_workspace_size(self.capacity), torch.uint8)
         g = B.SceneGrads(*(grads[k].data_ptr() for k in SCENE_KEYS))
         B.potr_render_backward(self.scene_c, self.views, self.frame, self.cfg, self.vals, self.ranges, t_final, n_last,
-                               dL_dimages, self.capacity, g, ws, stream)
+                               dL_dimages, self.capacity, g, ws, stream, order=self.order)
 
     def pair_stats(self, stream=None) -> dict:
         """Exact pair counts of the forward and removal walks (see potr_pair_stats)."""

@@ -283,3 +283,27 @@ def test_single_splat_closed_form():
     img = view_slice(fr, res["image"], 0).astype(np.float64)
     want = np.sum(img * (img - 2.0 * (img - 0.25)))
     assert res["dsse_view"][0] == pytest.approx(want, rel=1e-5)
+
+
+def test_tile_schedule_is_a_longest_first_permutation_and_changes_no_bit():
+    import torch
+
+    from paper_2601_14821_gb300.pipeline import RemovalEffectFrame, scene_to_device
+
+    sc, cams = mixed_workload()
+    tg = _tiny_targets(sc, cams, CFG16, 31)
+    outs = []
+    for sched in (False, True):
+        fr = RemovalEffectFrame(scene_to_device(sc), synth.cameras_to_array(cams), schedule=sched, **CFG16)
+        fr.plan()
+        outs.append(frame_outputs(fr, pack_targets(fr, tg)))
+        if sched:
+            torch.cuda.synchronize()
+            order = fr.order.cpu().numpy().view(np.uint32)[: fr.total_tiles]
+            assert np.array_equal(np.sort(order), np.arange(fr.total_tiles, dtype=np.uint32))
+            r = fr.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+            lens = (r[:, 1] - r[:, 0])[order]
+            bucket = np.where(lens == 0, 0, np.floor(np.log2(np.maximum(lens, 1))).astype(np.int64) + 1)
+            assert np.all(np.diff(bucket) <= 0)
+    for k in ("image", "t_final", "n_last", "dmse", "importance", "dsse_view", "inst_dse"):
+        assert np.array_equal(outs[0][k], outs[1][k]), k
