@@ -319,6 +319,16 @@ POTR_API potr_status potr_bin_sort_static(const potr_views* views, const potr_fr
                                           uint64_t* d_keys, uint32_t* d_vals, uint32_t* d_tile_ranges,
                                           potr_device_status* d_status, potr_stream_t stream);
 
+/*
+ * Self-test of the library's bounded device waits (no counterpart in the paper).  The only
+ * device-side wait is the sort's decoupled look-back; this runs that wait against a predecessor
+ * whose counts are never published, so it must give up after spin_limit polls and write
+ * POTR_ERR_TIMEOUT to *d_status (the kernel returns normally; the context stays usable).
+ * d_ws: >= 4096 bytes of device scratch.
+ */
+POTR_API potr_status potr_selftest_wait_timeout(void* d_ws, size_t ws_bytes, int32_t spin_limit,
+                                                potr_device_status* d_status, potr_stream_t stream);
+
 /* Number of kernels the library has launched in this process (host-side counter). */
 POTR_API uint64_t potr_launch_count(void);
 

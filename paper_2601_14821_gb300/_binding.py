@@ -93,6 +93,7 @@ SIGNATURES = {
     "potr_tile_schedule": (_I32, [C.POINTER(Frame), _P, _P, _P, _SZ, _P]),
     "potr_pair_stats": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _P, _P, _P, _P]),
     "potr_launch_count": (C.c_uint64, []),
+    "potr_selftest_wait_timeout": (_I32, [_P, _SZ, _I32, _P, _P]),
     "potr_loss_workspace_size": (_SZ, [_I64]),
     "potr_loss_grad": (_I32, [C.POINTER(Frame), _P, _P, C.c_float, _P, _P, _P, _SZ, _P]),
     "potr_render_backward_workspace_size": (_SZ, [_I64]),
@@ -248,3 +249,8 @@ def potr_render_backward(scene: Scene, views: Views, frame: Frame, cfg: RasterCo
            lib().potr_render_backward(C.byref(scene), C.byref(views), C.byref(frame), C.byref(cfg), ptr(vals),
                                       ptr(ranges), ptr(order), ptr(t_final), ptr(n_last), ptr(dL_dimages), capacity,
                                       C.byref(grads), ptr(ws), ws.numel(), stream_handle(stream)))
+
+
+def potr_selftest_wait_timeout(ws, spin_limit: int, status, stream=None):
+    _check("potr_selftest_wait_timeout", lib().potr_selftest_wait_timeout(ptr(ws), ws.numel(), spin_limit,
+                                                                          ptr(status), stream_handle(stream)))

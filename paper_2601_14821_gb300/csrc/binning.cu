@@ -247,6 +247,43 @@ __device__ __forceinline__ uint32_t block_exclusive_scan256(uint32_t x, uint32_t
   return wbase + incl - x;
 }
 
+// Decoupled look-back for digit t of block `tile`: the sum of the counts published by blocks
+// 0 .. tile-1 (walking back until an inclusive prefix).  A word that stays unpublished for
+// spin_limit polls ends the wait: *err is set and the partial sum returned.
+__device__ __forceinline__ uint64_t lookback_prefix(volatile unsigned long long* vst, int64_t tile, uint32_t t,
+                                                    int spin_limit, int* err) {
+  uint64_t excl = 0;
+  int64_t p = tile - 1;
+  int spins = 0;
+  while (p >= 0) {
+    const unsigned long long x = vst[p * 256 + t];
+    const unsigned long long flag = x >> 62;
+    if (flag == 0) {
+      if (++spins > spin_limit) {
+        *err = 1;
+        break;
+      }
+      continue;
+    }
+    excl += x & kCountMask;
+    if (flag == 2) break;
+    --p;
+  }
+  return excl;
+}
+
+// Self-test of the bounded wait: block 1 looks back at block 0, whose words nobody publishes.
+__global__ void lookback_timeout_probe_kernel(unsigned long long* status, int spin_limit,
+                                              potr_device_status* __restrict__ st) {
+  __shared__ int s_err;
+  if (threadIdx.x == 0) s_err = 0;
+  __syncthreads();
+  volatile unsigned long long* vst = status;
+  const uint64_t got = lookback_prefix(vst, 1, threadIdx.x, spin_limit, &s_err);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_err && got == 0) set_status(st, POTR_ERR_TIMEOUT, 0);
+}
+
 __global__ void __launch_bounds__(256) digit_base_kernel(const uint32_t* __restrict__ ghist, int passes,
                                                          uint32_t* __restrict__ gbase) {
   __shared__ uint32_t tmp8[8];
@@ -323,22 +360,7 @@ __global__ void __launch_bounds__(kOsThreads) onesweep_kernel(const uint64_t* __
     vst[si] = kFlagInc | run;
   } else {
     vst[si] = kFlagAgg | run;
-    int64_t p = (int64_t)tile - 1;
-    int spins = 0;
-    while (true) {
-      const unsigned long long x = vst[p * 256 + t];
-      const unsigned long long flag = x >> 62;
-      if (flag == 0) {
-        if (++spins > kSpinLimit) {
-          s_err = 1;
-          break;
-        }
-        continue;
-      }
-      excl += x & kCountMask;
-      if (flag == 2 || p == 0) break;
-      --p;
-    }
+    excl = lookback_prefix(vst, tile, t, kSpinLimit, &s_err);
     vst[si] = kFlagInc | (excl + run);
   }
   dig_glob[t] = gbase[t] + (uint32_t)excl;
@@ -486,5 +508,18 @@ extern "C" potr_status potr_bin_sort(const potr_views* views, const potr_frame* 
                                                                                d_tile_ranges);
     POTR_CHECK_LAUNCH();
   }
+  return POTR_OK;
+}
+
+extern "C" potr_status potr_selftest_wait_timeout(void* d_ws, size_t ws_bytes, int32_t spin_limit,
+                                                  potr_device_status* d_status, potr_stream_t stream) {
+  using namespace potr;
+  if (!d_ws || !d_status || spin_limit < 1 || ws_bytes < 2 * 256 * sizeof(unsigned long long))
+    return POTR_ERR_INVALID_ARGUMENT;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned long long* status = static_cast<unsigned long long*>(d_ws);
+  if (cudaMemsetAsync(status, 0, 2 * 256 * sizeof(unsigned long long), s) != cudaSuccess) return POTR_ERR_CUDA;
+  lookback_timeout_probe_kernel<<<1, 256, 0, s>>>(status, spin_limit, d_status);
+  POTR_CHECK_LAUNCH();
   return POTR_OK;
 }

@@ -307,3 +307,21 @@ def test_tile_schedule_is_a_longest_first_permutation_and_changes_no_bit():
             assert np.all(np.diff(bucket) <= 0)
     for k in ("image", "t_final", "n_last", "dmse", "importance", "dsse_view", "inst_dse"):
         assert np.array_equal(outs[0][k], outs[1][k]), k
+
+
+def test_bounded_wait_times_out_and_reports():
+    """The sort's look-back gives up on a predecessor that never publishes: it writes
+    POTR_ERR_TIMEOUT to the status word and returns; the context keeps working."""
+    import torch
+
+    from paper_2601_14821_gb300 import _binding as B
+    from paper_2601_14821_gb300 import build
+
+    build.build()
+    ws = torch.empty(4096, dtype=torch.uint8, device="cuda")
+    status = torch.zeros(2, dtype=torch.int64, device="cuda")
+    B.potr_selftest_wait_timeout(ws, 1000, status)
+    torch.cuda.synchronize()
+    assert int(status[0].item()) == B.POTR_ERR_TIMEOUT
+    fr = build_frame(*mixed_workload(), **CFG16)  # the device is still usable afterwards
+    assert fr.instance_count() > 0
