@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--views", type=int, default=0, help="use only the first V views (profiling cases)")
     ap.add_argument("--only-batched", action="store_true", help="time the batched frame only (profiling cases)")
+    ap.add_argument("--only-fwdbwd", action="store_true", help="time the fine-tuning step only (profiling case)")
     ap.add_argument("--large", action="store_true",
                     help="also time the 6M-splat, 300-view 1920x1080 workload (several minutes)")
     ap.add_argument("--no-multiview", action="store_true", help="skip the 3M-splat, 200-view workload")
@@ -169,6 +170,11 @@ def run_ours(args):
     torch.cuda.set_device(local)
     D.init("nccl")
     dev = torch.device("cuda", local)
+    if args.only_fwdbwd:
+        out = fwd_bwd_step_ms(args, dev, D)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "fwd_bwd": out, "profiling_case": True}))
+        return
     w = synth.workload(WORKLOAD)
     if args.views:
         w.cameras = w.cameras[: args.views]

@@ -262,7 +262,9 @@ POTR_API potr_status potr_loss_grad(const potr_frame* frame, const float* d_imag
                                     float lambda, double* d_loss, float* d_dL_dimages, void* d_ws, size_t ws_bytes,
                                     potr_stream_t stream);
 
-/* Workspace bytes of potr_render_backward: 9 float partial gradients per instance slot. */
+/* Bytes of potr_render_backward's 9 float partial gradients per instance slot.  The workspace it
+ * needs is this plus 9 floats per (view, splat): potr_render_backward_workspace_size(capacity)
+ * + 36 * n_views * n bytes. */
 POTR_API size_t potr_render_backward_workspace_size(int64_t instance_capacity);
 
 /*

@@ -283,41 +283,94 @@ __device__ __forceinline__ void sh_weighted_grad(float x, float y, float z, cons
   gx += w[15] * -3.0f * c3a * (xx - yy);           gy += w[15] * 6.0f * c3a * x * y;
 }
 
+// Per (view, splat): the nine instance partials summed over the vk's emission slots (emission
+// order, compensated).  One warp per 32 consecutive vk, whose slots form one contiguous run:
+// the run is read coalesced into shared memory a chunk at a time and each lane adds the part of
+// its own segment that the chunk holds.  vk_grad[q][vk] receives the sums.
+constexpr int kSumChunk = 256;
+
+__global__ void __launch_bounds__(128) vk_grad_sum_kernel(const uint32_t* __restrict__ touched,
+                                                          const uint32_t* __restrict__ offsets,
+                                                          const uint32_t* __restrict__ n_inst, int64_t capacity,
+                                                          int64_t n_vk, const float* __restrict__ inst_grad,
+                                                          float* __restrict__ vk_grad) {
+  __shared__ float buf[4][kGradQ][kSumChunk];
+  const bool ok = (int64_t)*n_inst <= capacity;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t warps_total = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t wv = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wv * 32 < n_vk; wv += warps_total) {
+    const int64_t vk = wv * 32 + lane;
+    uint32_t cnt = 0, off = 0;
+    if (ok && vk < n_vk) {
+      cnt = touched[vk];
+      if (cnt) off = offsets[vk];
+    }
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t seg0 = incl - cnt, seg1 = incl;  // my segment inside the warp's run
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t first_lane = total ? __ffs(__ballot_sync(0xffffffffu, cnt != 0)) - 1 : 0;
+    const uint32_t run0 = __shfl_sync(0xffffffffu, off, first_lane);
+    KahanSum acc[kGradQ];
+    for (uint32_t c0 = 0; c0 < total; c0 += kSumChunk) {
+      const uint32_t cn = min((uint32_t)kSumChunk, total - c0);
+      for (uint32_t i = lane; i < cn; i += 32)
+#pragma unroll
+        for (int q = 0; q < kGradQ; ++q) buf[wib][q][i] = inst_grad[(int64_t)q * capacity + run0 + c0 + i];
+      __syncwarp();
+      const uint32_t a = max(seg0, c0), b = min(seg1, c0 + cn);
+      for (uint32_t i = a; i < b; ++i)
+#pragma unroll
+        for (int q = 0; q < kGradQ; ++q) acc[q].add(buf[wib][q][i - c0]);
+      __syncwarp();
+    }
+    if (vk < n_vk) {
+#pragma unroll
+      for (int q = 0; q < kGradQ; ++q) vk_grad[(int64_t)q * n_vk + vk] = (float)acc[q].value();
+    }
+  }
+}
+
 __global__ void __launch_bounds__(128) preprocess_bwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ sh, const float* __restrict__ cov3d, const float* __restrict__ opacity, int64_t n,
     const potr_camera* __restrict__ cams, int n_views, potr_raster_config cfg, const uint32_t* __restrict__ touched,
-    const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ n_inst, int64_t capacity,
-    const float* __restrict__ inst_grad, float* __restrict__ g_means, float* __restrict__ g_log_scales,
+    const float* __restrict__ vk_grad, float* __restrict__ g_means, float* __restrict__ g_log_scales,
     float* __restrict__ g_quats, float* __restrict__ g_logits, float* __restrict__ g_sh) {
-  const bool ok = (int64_t)*n_inst <= capacity;
   const float kA = -0.5f * kLog2e;
+  const int64_t n_vk = (int64_t)n_views * n;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     float gmu[3] = {0.0f, 0.0f, 0.0f};
     float G3[3][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
     float go = 0.0f;
-    float gsh[48];
+    float gsh[48], shc[48];
 #pragma unroll
     for (int i = 0; i < 48; ++i) gsh[i] = 0.0f;
+    bool have_sh = false;
     const float mu[3] = {means[k], means[n + k], means[2 * n + k]};
     const float Sg[3][3] = {{cov3d[k], cov3d[n + k], cov3d[2 * n + k]},
                             {cov3d[n + k], cov3d[3 * n + k], cov3d[4 * n + k]},
                             {cov3d[2 * n + k], cov3d[4 * n + k], cov3d[5 * n + k]}};
-    for (int v = 0; ok && v < n_views; ++v) {
+    for (int v = 0; v < n_views; ++v) {
       const int64_t vk = (int64_t)v * n + k;
-      const uint32_t cnt = touched[vk];
-      if (!cnt) continue;
-      const uint32_t off = offsets[vk];
+      if (!touched[vk]) continue;
       float gq[kGradQ];
       bool nz = false;
 #pragma unroll
       for (int q = 0; q < kGradQ; ++q) {
-        KahanSum ks;
-        for (uint32_t i = 0; i < cnt; ++i) ks.add(inst_grad[(int64_t)q * capacity + off + i]);
-        gq[q] = (float)ks.value();
+        gq[q] = vk_grad[(int64_t)q * n_vk + vk];
         nz |= gq[q] != 0.0f;
       }
       if (!nz) continue;
+      if (!have_sh) {
+#pragma unroll
+        for (int i = 0; i < 48; ++i) shc[i] = __ldg(sh + (int64_t)i * n + k);
+        have_sh = true;
+      }
       const potr_camera& cam = cams[v];
       const float* W = cam.w2c;
       // forward recomputation (values only)
@@ -411,7 +464,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(
       for (int ch = 0; ch < 3; ++ch) {
         float acc = 0.0f;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) acc = fmaf(sh[(int64_t)(i * 3 + ch) * n + k], Y[i], acc);
+        for (int i = 0; i < 16; ++i) acc = fmaf(shc[i * 3 + ch], Y[i], acc);
         gv[ch] = (acc + 0.5f > 0.0f) ? gq[6 + ch] : 0.0f;
       }
 #pragma unroll
@@ -420,7 +473,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
           gsh[i * 3 + ch] += gv[ch] * Y[i];
-          shc_w[i] += gv[ch] * sh[(int64_t)(i * 3 + ch) * n + k];
+          shc_w[i] += gv[ch] * shc[i * 3 + ch];
         }
       }
       float gdx, gdy, gdz;
@@ -508,6 +561,9 @@ extern "C" size_t potr_render_backward_workspace_size(int64_t instance_capacity)
   return sizeof(float) * (size_t)potr::kGradQ * (size_t)(instance_capacity > 0 ? instance_capacity : 0);
 }
 
+// Extra workspace for the per-(view, splat) sums: 9 floats per vk, after the instance partials.
+static size_t vk_grad_bytes(int64_t n_vk) { return sizeof(float) * (size_t)potr::kGradQ * (size_t)n_vk; }
+
 extern "C" potr_status potr_render_backward(const potr_scene* scene, const potr_views* views, const potr_frame* frame,
                                             const potr_raster_config* cfg, const uint32_t* d_vals,
                                             const uint32_t* d_tile_ranges, uint32_t* d_tile_order,
@@ -526,8 +582,9 @@ extern "C" potr_status potr_render_backward(const potr_scene* scene, const potr_
   if ((d_t_final == nullptr) != (d_n_last == nullptr)) return POTR_ERR_INVALID_ARGUMENT;
   if (frame->total_tiles <= 0 || frame->total_tiles > 0x7fffffffll || !frame->cams || !frame->info)
     return POTR_ERR_INVALID_ARGUMENT;
-  if (instance_capacity <= 0 || !d_ws || ws_bytes < potr_render_backward_workspace_size(instance_capacity))
-    return POTR_ERR_INVALID_ARGUMENT;
+  const int64_t n_vk = (int64_t)frame->n_views * scene->n;
+  const size_t inst_bytes = potr_render_backward_workspace_size(instance_capacity);
+  if (instance_capacity <= 0 || !d_ws || ws_bytes < inst_bytes + vk_grad_bytes(n_vk)) return POTR_ERR_INVALID_ARGUMENT;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   float* inst_grad = static_cast<float*>(d_ws);
   if (cudaMemsetAsync(inst_grad, 0, potr_render_backward_workspace_size(instance_capacity), s) != cudaSuccess)
@@ -556,12 +613,20 @@ extern "C" potr_status potr_render_backward(const potr_scene* scene, const potr_
   }
   POTR_CHECK_LAUNCH();
   const int64_t n = scene->n;
+  float* vk_grad = reinterpret_cast<float*>(static_cast<char*>(d_ws) + inst_bytes);
+  {
+    int64_t gw = (n_vk + 127) / 128;
+    if (gw > 152 * 32) gw = 152 * 32;
+    vk_grad_sum_kernel<<<(unsigned)gw, 128, 0, s>>>(views->touched, views->offsets, views->n_instances,
+                                                     instance_capacity, n_vk, inst_grad, vk_grad);
+    POTR_CHECK_LAUNCH();
+  }
   int64_t g = (n + 127) / 128;
   if (g > 152 * 64) g = 152 * 64;
   preprocess_bwd_kernel<<<(unsigned)g, 128, 0, s>>>(
       scene->means, scene->log_scales, scene->quats, scene->sh, views->cov3d, views->opacity, n, frame->cams,
-      frame->n_views, *cfg, views->touched, views->offsets, views->n_instances, instance_capacity, inst_grad,
-      grads->means, grads->log_scales, grads->quats, grads->opacity_logits, grads->sh);
+      frame->n_views, *cfg, views->touched, vk_grad, grads->means, grads->log_scales, grads->quats,
+      grads->opacity_logits, grads->sh);
   POTR_CHECK_LAUNCH();
   return POTR_OK;
 }

@@ -248,26 +248,40 @@ __device__ __forceinline__ uint32_t block_exclusive_scan256(uint32_t x, uint32_t
 }
 
 // Decoupled look-back for digit t of block `tile`: the sum of the counts published by blocks
-// 0 .. tile-1 (walking back until an inclusive prefix).  A word that stays unpublished for
-// spin_limit polls ends the wait: *err is set and the partial sum returned.
+// 0 .. tile-1 (walking back until an inclusive prefix).  Eight predecessors' words are loaded
+// at once (independent loads) and consumed nearest first; a word that is not yet published
+// restarts the window there.  After spin_limit such restarts the wait ends: *err is set and the
+// partial sum returned.
 __device__ __forceinline__ uint64_t lookback_prefix(volatile unsigned long long* vst, int64_t tile, uint32_t t,
                                                     int spin_limit, int* err) {
+  constexpr int kWin = 8;
   uint64_t excl = 0;
   int64_t p = tile - 1;
   int spins = 0;
   while (p >= 0) {
-    const unsigned long long x = vst[p * 256 + t];
-    const unsigned long long flag = x >> 62;
-    if (flag == 0) {
-      if (++spins > spin_limit) {
-        *err = 1;
-        break;
+    unsigned long long x[kWin];
+#pragma unroll
+    for (int i = 0; i < kWin; ++i) x[i] = (p - i >= 0) ? vst[(p - i) * 256 + t] : (kFlagInc | 0ull);
+    int used = 0;
+    bool done = false, stalled = false;
+#pragma unroll
+    for (int i = 0; i < kWin; ++i) {
+      if (done || stalled) continue;
+      const unsigned long long flag = x[i] >> 62;
+      if (flag == 0) {
+        stalled = true;
+        continue;
       }
-      continue;
+      excl += x[i] & kCountMask;
+      ++used;
+      if (flag == 2) done = true;
     }
-    excl += x & kCountMask;
-    if (flag == 2) break;
-    --p;
+    if (done) break;
+    p -= used;
+    if (stalled && ++spins > spin_limit) {
+      *err = 1;
+      break;
+    }
   }
   return excl;
 }
