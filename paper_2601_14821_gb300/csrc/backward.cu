@@ -24,7 +24,7 @@ namespace potr {
 namespace {
 
 constexpr int kGradQ = 9;     // per-pair gradients: mx, my, A, B, C, opacity, r, g, b
-constexpr int kBwdChunk = 8;  // splats per warp transpose-sum
+constexpr int kBwdChunk = 4;  // splats per warp transpose-sum
 constexpr int kBwdBatch = 128;
 constexpr float kLn2 = 0.69314718055994531f;
 
@@ -32,11 +32,12 @@ size_t bwd_smem_bytes() {
   return sizeof(float4) * 3 * kBwdBatch + sizeof(float) * kGradQ * kWarps * kBwdBatch + kBwdBatch;
 }
 
-// Lanes l, l^8, l^16, l^24 receive the sum over all 32 lanes of v[l & 7] (fixed order).
-__device__ __forceinline__ float warp_transpose_sum8(float (&v)[kBwdChunk]) {
+// Lanes l, l^4, l^8, ... receive the sum over all 32 lanes of v[l & 3] (fixed order): a
+// transpose-sum inside each 4-lane group, then exchanges between the groups.
+__device__ __forceinline__ float warp_transpose_sum4(float (&v)[kBwdChunk]) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int off = 4; off >= 1; off >>= 1) {
+  for (int off = 2; off >= 1; off >>= 1) {
     const bool upper = (lane & off) != 0;
 #pragma unroll
     for (int i = 0; i < off; ++i) {
@@ -46,6 +47,7 @@ __device__ __forceinline__ float warp_transpose_sum8(float (&v)[kBwdChunk]) {
     }
   }
   float r = v[0];
+  r += __shfl_xor_sync(0xffffffffu, r, 4);
   r += __shfl_xor_sync(0xffffffffu, r, 8);
   r += __shfl_xor_sync(0xffffffffu, r, 16);
   return r;
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const float4* __re
         if (__any_sync(0xffffffffu, any)) {
 #pragma unroll
           for (int q = 0; q < kGradQ; ++q) {
-            const float sq = warp_transpose_sum8(v[q]);
+            const float sq = warp_transpose_sum4(v[q]);
             if (lane < kBwdChunk && mypos >= 0) red[(q * kWarps + warp) * kBwdBatch + mypos] = sq;
           }
         }
