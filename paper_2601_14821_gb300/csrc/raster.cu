@@ -15,7 +15,7 @@
 // which equals the paper's P_i - P_{i+1} / (1 - alpha_i) + alpha_i / (1 - alpha_i) P_K because
 // P_K - P_{i+1} = S_{>i}; every term is a sum of non-negative numbers, so no prefix sums are
 // subtracted.  dSE_i = sum_ch PD_i (PD_i + 2 (c - c_t)).  Per (tile, splat) the 256 pixel
-// values are summed without atomics: 16 consecutive splats at a time, a warp transpose-sum
+// values are summed without atomics: 8 consecutive splats at a time, a warp transpose-sum
 // leaves lane l with its warp's total for splat l, the warp totals of a whole batch go to
 // shared memory, and after one barrier the 8 warp totals are added in warp order.  The order
 // is fixed, so the result does not depend on scheduling.
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(kThreads) render_kernel(const float4* __restri
                                                           potr_raster_config cfg, float* __restrict__ images,
                                                           float* __restrict__ t_final, uint32_t* __restrict__ n_last,
                                                           TileQueue queue) {
-  extern __shared__ float4 smem[];
+  extern __shared__ float4 smem[];  // one batch of records
   uint8_t* wmask = reinterpret_cast<uint8_t*>(smem + 3 * BATCH);
   __shared__ uint32_t s_slot;
   int64_t tile;
@@ -57,12 +57,12 @@ __global__ void __launch_bounds__(kThreads) render_kernel(const float4* __restri
   }
 }
 
-// Lanes l and l ^ 16 both receive the sum over all 32 lanes of v[l & 15] (fixed order):
-// a transpose-sum inside each 16-lane half, then one exchange between the halves.
-__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16]) {
+// Lanes l, l^8, l^16, l^24 receive the sum over all 32 lanes of v[l & 7] (fixed order): a
+// transpose-sum inside each 8-lane group, then exchanges between the groups.
+__device__ __forceinline__ float warp_transpose_sum8(float (&v)[8]) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int off = 8; off >= 1; off >>= 1) {
+  for (int off = 4; off >= 1; off >>= 1) {
     const bool upper = (lane & off) != 0;
 #pragma unroll
     for (int i = 0; i < off; ++i) {
@@ -71,14 +71,17 @@ __device__ __forceinline__ float warp_transpose_sum16(float (&v)[16]) {
       v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
     }
   }
-  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+  float r = v[0];
+  r += __shfl_xor_sync(0xffffffffu, r, 8);
+  r += __shfl_xor_sync(0xffffffffu, r, 16);
+  return r;
 }
 
-constexpr int kChunk = 16;  // splats per warp transpose-sum
+constexpr int kChunk = 8;  // splats per warp transpose-sum
 
 template <int BATCH, bool IMP>
 constexpr size_t removal_smem_bytes() {
-  return sizeof(float4) * 3 * BATCH + sizeof(float) * kWarps * BATCH * (IMP ? 2 : 1) + BATCH;
+  return sizeof(float4) * 6 * BATCH + sizeof(float) * kWarps * BATCH * (IMP ? 2 : 1) + BATCH;
 }
 
 template <int BATCH, bool IMP>
@@ -90,8 +93,8 @@ __global__ void __launch_bounds__(kThreads) removal_kernel(const float4* __restr
                                                            float* __restrict__ images, float* __restrict__ inst_dse,
                                                            float* __restrict__ inst_imp, TileQueue queue) {
   extern __shared__ float4 dyn[];
-  float4* smem = dyn;                                               // [BATCH][3] raster records
-  float* red_d = reinterpret_cast<float*>(dyn + 3 * BATCH);         // [kWarps][BATCH] warp sums of dSE
+  float4* smem = dyn;                                               // [2][BATCH][3] raster records
+  float* red_d = reinterpret_cast<float*>(dyn + 6 * BATCH);         // [kWarps][BATCH] warp sums of dSE
   float* red_i = red_d + kWarps * BATCH;                            // [kWarps][BATCH] warp sums of T alpha
   uint8_t* wmask = reinterpret_cast<uint8_t*>(red_d + kWarps * BATCH * (IMP ? 2 : 1));  // [BATCH]
   __shared__ uint32_t max_last_w[kWarps];
@@ -124,15 +127,40 @@ __global__ void __launch_bounds__(kThreads) removal_kernel(const float4* __restr
 
   // Back-to-front over list positions [0, max_last): T_i = T_{i+1} / (1 - alpha_i),
   // S = sum of T_j alpha_j c_j over the composited j > i.  Each warp visits only the splats
-  // of its warp mask, 16 at a time, highest position first.
+  // of its warp mask, 8 at a time, highest position first.
   float S[3] = {0.0f, 0.0f, 0.0f};
   float* my_d = red_d + warp * BATCH;
   float* my_i = red_i + warp * BATCH;
-  for (uint32_t top = max_last; top > 0;) {
+  // batch k covers positions [lo_k, hi_k), hi_0 = max_last, going down; double-buffered
+  const uint32_t nb = (max_last + BATCH - 1) / BATCH;
+  BatchStager<BATCH> st;
+  __syncthreads();  // the forward walk's last batch is no longer read
+  if (nb > 0) {
+    const uint32_t lo0 = max_last > (uint32_t)BATCH ? max_last - BATCH : 0u;
+    st.load(vals, c.s + lo0, (int)(max_last - lo0));
+    st.issue(smem, raster);
+  }
+  if (nb > 1) {
+    const uint32_t hi1 = max_last - BATCH, lo1 = hi1 > (uint32_t)BATCH ? hi1 - BATCH : 0u;
+    st.load(vals, c.s + lo1, (int)(hi1 - lo1));
+  }
+  for (uint32_t k = 0; k < nb; ++k) {
+    const uint32_t top = max_last - k * BATCH;
     const uint32_t lo = top > (uint32_t)BATCH ? top - BATCH : 0u;
     const int cnt = (int)(top - lo);
-    __syncthreads();  // previous batch (records and warp sums) fully consumed
-    stage_batch_masked<BATCH>(smem, wmask, raster, vals, c.s + lo, cnt, c, cfg);
+    const float4* buf = smem + 3 * BATCH * (k & 1);
+    if (k > 0) __syncthreads();  // batch k-1 (records, warp sums) fully consumed
+    if (k + 1 < nb) {
+      st.issue(smem + 3 * BATCH * ((k + 1) & 1), raster);
+      cp_async_wait<1>();
+      if (k + 2 < nb) {
+        const uint32_t hi2 = lo - BATCH, lo2 = hi2 > (uint32_t)BATCH ? hi2 - BATCH : 0u;
+        st.load(vals, c.s + lo2, (int)(hi2 - lo2));
+      }
+    } else {
+      cp_async_wait<0>();
+    }
+    compute_masks<BATCH>(buf, wmask, cnt, c, cfg);
     for (int j = lane; j < cnt; j += 32) {
       my_d[j] = 0.0f;
       if (IMP) my_i[j] = 0.0f;
@@ -157,13 +185,13 @@ __global__ void __launch_bounds__(kThreads) removal_kernel(const float4* __restr
             const int j = glo + b;
             if (lane == u) mypos = j;
             if (lo + (uint32_t)j < last) {
-              const float4 r0 = smem[3 * j];
-              const float4 r1 = smem[3 * j + 1];
+              const float4 r0 = buf[3 * j];
+              const float4 r1 = buf[3 * j + 1];
               const float p = pair_exponent(r0.z, r0.w, r1.x, __fsub_rn(c.fx, r0.x), __fsub_rn(c.fy, r0.y));
               if (p >= r1.z) {
                 const float a = pair_alpha(r1.y, p, cfg.alpha_max);
                 if (a >= cfg.alpha_min) {
-                  const float4 r2 = smem[3 * j + 2];
+                  const float4 r2 = buf[3 * j + 2];
                   const float rcp = __fdividef(1.0f, 1.0f - a);
                   T = T * rcp;                  // T_i = T_{i+1} / (1 - alpha_i)
                   const float w = a * T;        // T_i alpha_i
@@ -188,8 +216,8 @@ __global__ void __launch_bounds__(kThreads) removal_kernel(const float4* __restr
         }
         float sd = 0.0f, si = 0.0f;
         if (__any_sync(0xffffffffu, any)) {
-          sd = warp_transpose_sum16(d);
-          if (IMP) si = warp_transpose_sum16(im);
+          sd = warp_transpose_sum8(d);
+          if (IMP) si = warp_transpose_sum8(im);
         }
         if (lane < kChunk && mypos >= 0) {
           my_d[mypos] = sd;
@@ -207,12 +235,11 @@ __global__ void __launch_bounds__(kThreads) removal_kernel(const float4* __restr
         if (IMP) si += red_i[w * BATCH + j];
       }
       if (sd != 0.0f || (IMP && si != 0.0f)) {
-        const uint32_t slot = emission_slot(smem[3 * j + 1], smem[3 * j + 2], c.tx, c.ty);
+        const uint32_t slot = emission_slot(buf[3 * j + 1], buf[3 * j + 2], c.tx, c.ty);
         inst_dse[slot] = sd;
         if (IMP) inst_imp[slot] = si;
       }
     }
-    top = lo;
   }
   }  // tiles
 }

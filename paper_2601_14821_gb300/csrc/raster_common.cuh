@@ -33,6 +33,42 @@ __device__ __forceinline__ void stage_batch(float4* smem, const float4* __restri
   cp_async_commit_wait();
 }
 
+// Double-buffered batch staging: the gathers of one batch are in flight (cp.async, one commit
+// group per batch) while the CTA works on the other buffer, and every thread already holds the
+// list values (vk) of the batch after that in registers, so issuing never waits on a load.
+template <int BATCH>
+struct BatchStager {
+  static constexpr int kPer = (BATCH + kThreads - 1) / kThreads;
+  uint32_t vk[kPer];
+  int loaded;
+  __device__ __forceinline__ void load(const uint32_t* __restrict__ vals, uint32_t first, int cnt) {
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int j = threadIdx.x + r * kThreads;
+      vk[r] = j < cnt ? vals[first + j] : 0u;
+    }
+    loaded = cnt;
+  }
+  __device__ __forceinline__ void issue(float4* buf, const float4* __restrict__ raster) const {
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int j = threadIdx.x + r * kThreads;
+      if (j < loaded) {
+        const float4* src = raster + (size_t)vk[r] * 3;
+        cp_async16(buf + 3 * j + 0, src + 0);
+        cp_async16(buf + 3 * j + 1, src + 1);
+        cp_async16(buf + 3 * j + 2, src + 2);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+  }
+};
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
 struct TileCtx {
   int64_t tile;
   int view;
@@ -90,6 +126,17 @@ __device__ __forceinline__ uint32_t warp_mask(const float4& r0, const float4& r1
     if (pmax + margin >= thr) m |= 1u << (r / rows_per_warp);
   }
   return m;
+}
+
+// Warp masks of the entries this thread gathered (its own cp.async copies are complete).
+template <int BATCH>
+__device__ __forceinline__ void compute_masks(const float4* buf, uint8_t* wmask, int cnt, const TileCtx& c,
+                                              const potr_raster_config& cfg) {
+#pragma unroll
+  for (int r = 0; r < BatchStager<BATCH>::kPer; ++r) {
+    const int j = threadIdx.x + r * kThreads;
+    if (j < cnt) wmask[j] = (uint8_t)warp_mask(buf[3 * j], buf[3 * j + 1], c, cfg);
+  }
 }
 
 // Gather a batch and compute every staged splat's warp mask.
