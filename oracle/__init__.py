@@ -101,9 +101,12 @@ def lib():
             L.orc_exp2r_coeffs.argtypes = [vp]
             L.orc_activate.argtypes = [i64, vp, vp, vp, vp, vp]
             L.orc_sh_basis.argtypes = [C.c_double, C.c_double, C.c_double, vp]
-            L.orc_project.argtypes = [i64, vp, vp, vp, C.POINTER(Camera), C.POINTER(Config)] + [vp] * 9
+            L.orc_project.argtypes = [i64, vp, vp, vp, vp, C.POINTER(Camera), C.POINTER(Config)] + [vp] * 9
             L.orc_bin.restype = i64
-            L.orc_bin.argtypes = [i64, vp, vp, vp, C.c_int32, C.c_uint64, u32, i64, vp, vp, vp]
+            L.orc_bin.argtypes = [i64, vp, vp, vp, vp, vp, vp, C.POINTER(Config), C.c_int32, C.c_uint64, u32, i64,
+                                  vp, vp, vp]
+            L.orc_tile_hit.restype = C.c_int
+            L.orc_tile_hit.argtypes = [C.c_float] * 6 + [C.c_int] * 4 + [C.c_float]
             L.orc_tile_ranges.argtypes = [i64, vp, C.c_uint64, i64, vp]
             L.orc_render.argtypes = [C.POINTER(Camera), C.POINTER(Config), i64, vp, vp, vp, vp, vp, vp,
                                      i64, vp, vp, vp, vp, vp]
@@ -155,8 +158,11 @@ def activate(scene):
     return cov, op
 
 
-def project(scene, cov3d, cam, cfg: Config) -> dict:
+def project(scene, cov3d, cam, cfg: Config, opacity) -> dict:
+    """Projection of every splat into one view; the touched count is the number of tiles of the
+    3-sigma rectangle that pass the tile test (alpha_min reachable at some pixel centre)."""
     n = scene.n
+    opacity = _f32(opacity)
     means, sh = _f32(scene.means), _f32(scene.sh)
     out = dict(
         depth=np.empty(n, np.float32), mean2d=np.empty((2, n), np.float32),
@@ -165,10 +171,23 @@ def project(scene, cov3d, cam, cfg: Config) -> dict:
         rect=np.empty((4, n), np.int32), touched=np.empty(n, np.uint32), rgb=np.empty((3, n), np.float64),
     )
     ccam = make_camera(cam)
-    lib().orc_project(n, _p(means), _p(_f32(cov3d)), _p(sh), C.byref(ccam), C.byref(cfg),
+    lib().orc_project(n, _p(means), _p(_f32(cov3d)), _p(opacity), _p(sh), C.byref(ccam), C.byref(cfg),
                       *[_p(out[k]) for k in ("depth", "mean2d", "cov2d", "conic", "qcoef", "radius",
                                              "rect", "touched", "rgb")])
+    out["opacity"] = opacity
     return out
+
+
+CULL_MAX_TILES = 64  # rectangles with more tiles keep every tile
+
+
+def tile_hit(proj: dict, k: int, tx: int, ty: int, cfg: Config) -> bool:
+    """The binning tile test for splat k and tile (tx, ty): True when some pixel centre of
+    the tile can reach alpha >= alpha_min (conservative, binary32)."""
+    m, q = proj["mean2d"], proj["qcoef"]
+    return bool(lib().orc_tile_hit(float(m[0, k]), float(m[1, k]), float(q[0, k]), float(q[1, k]), float(q[2, k]),
+                                   float(proj["opacity"][k]), int(tx), int(ty), cfg.tile_w, cfg.tile_h,
+                                   float(cfg.alpha_min)))
 
 
 def tiles_of(cam, cfg: Config):
@@ -183,8 +202,9 @@ def bin_sort(proj: dict, cam, cfg: Config, tile_base: int = 0, val_base: int = 0
     keys = np.empty(max(m, 1), np.uint64)
     vals = np.empty(max(m, 1), np.uint32)
     emit = np.empty(max(m, 1), np.uint32)
-    got = lib().orc_bin(n, _p(proj["touched"]), _p(proj["rect"]), _p(proj["depth"]), tx, tile_base,
-                        val_base, m, _p(keys), _p(vals), _p(emit))
+    got = lib().orc_bin(n, _p(proj["touched"]), _p(proj["rect"]), _p(proj["depth"]), _p(proj["mean2d"]),
+                        _p(proj["qcoef"]), _p(proj["opacity"]), C.byref(cfg), tx, tile_base, val_base, m,
+                        _p(keys), _p(vals), _p(emit))
     assert got == m
     ranges = np.empty((tx * ty, 2), np.uint32)
     lib().orc_tile_ranges(m, _p(keys), tile_base, tx * ty, _p(ranges))
@@ -265,8 +285,7 @@ def pixel_lists(proj: dict, vals, ranges, cam, cfg: Config):
 def prepare_view(scene, cam, cfg: Config, act=None) -> dict:
     """Activation + projection + binning of one view; returns a dict of every stage's output."""
     cov, op = act if act is not None else activate(scene)
-    proj = project(scene, cov, cam, cfg)
-    proj["opacity"] = op
+    proj = project(scene, cov, cam, cfg, op)
     proj["cov3d"] = cov
     keys, vals, emit, ranges = bin_sort(proj, cam, cfg)
     proj.update(keys=keys, vals=vals, emit=emit, ranges=ranges)

@@ -33,6 +33,9 @@
  * (x + 0.5, y + 0.5), colour = max(0, SH + 0.5), alpha <= alpha_max, skip alpha < alpha_min,
  * stop before a splat that would take T below T_min, quaternions (w, x, y, z) normalised,
  * scale = exp(log-scale), opacity = sigmoid(logit), depth ties broken by splat index.
+ * Binning keeps a tile of the 3-sigma rectangle only when some pixel centre of it can reach
+ * alpha_min (orc_tile_hit; rectangles of more than 64 tiles keep every tile): pixels skip
+ * such splats anyway, so images and removal effects are those of whole-rectangle binning.
  */
 #include <math.h>
 #include <stdint.h>
@@ -100,6 +103,48 @@ void orc_exp2r_coeffs(float* out7) {
 }
 
 static const float kLog2e = 1.44269504088896340736f; /* log2(e) rounded to binary32 */
+
+/*
+ * Binning reading: a tile of a splat's 3-sigma rectangle receives the splat only if some pixel
+ * centre of the tile can reach alpha >= alpha_min.  With log2 G = A u^2 + B u v + C v^2
+ * (u = x - mx, v = y - my), the exponent's maximum over the rectangle of the tile's pixel
+ * centres is taken on its edges (on each edge a concave parabola, maximised at its clamped
+ * vertex) and at the splat centre when it lies inside; the tile is kept when
+ * o * exp2r(max + margin) >= alpha_min, the margin 1e-5 |terms| + 1e-4 covering, some ten
+ * times over, the binary32 rounding of this maximum and of a pixel's own exponent (a few units
+ * in the last place of the largest term) and the error of exp2r.  Every pixel whose alpha reaches alpha_min therefore lies in a kept tile, so no
+ * compositing decision changes.  Binary32, fixed operation order, no contraction.
+ */
+static float edge_max(float A, float B, float C, float u, float v) { return (A * u + B * v) * u + C * v * v; }
+
+int orc_tile_hit(float mx, float my, float A, float B, float C, float o, int tx, int ty, int tile_w, int tile_h,
+                 float alpha_min) {
+  if (!(A < 0.0f && C < 0.0f)) return 1;
+  float X0 = (float)(tx * tile_w) + 0.5f, X1 = X0 + (float)(tile_w - 1);
+  float Y0 = (float)(ty * tile_h) + 0.5f, Y1 = Y0 + (float)(tile_h - 1);
+  float ux0 = X0 - mx, ux1 = X1 - mx, vy0 = Y0 - my, vy1 = Y1 - my;
+  float ku = -B / (2.0f * A), kv = -B / (2.0f * C);
+  float u0 = fminf(fmaxf(ku * vy0, ux0), ux1);
+  float u1 = fminf(fmaxf(ku * vy1, ux0), ux1);
+  float v0 = fminf(fmaxf(kv * ux0, vy0), vy1);
+  float v1 = fminf(fmaxf(kv * ux1, vy0), vy1);
+  float pmax = fmaxf(fmaxf(edge_max(A, B, C, u0, vy0), edge_max(A, B, C, u1, vy1)),
+                     fmaxf(edge_max(A, B, C, ux0, v0), edge_max(A, B, C, ux1, v1)));
+  if (ux0 <= 0.0f && ux1 >= 0.0f && vy0 <= 0.0f && vy1 >= 0.0f) pmax = fmaxf(pmax, 0.0f);
+  float um = fmaxf(fabsf(ux0), fabsf(ux1)), vm = fmaxf(fabsf(vy0), fabsf(vy1));
+  float mag = (fabsf(A) * um * um + fabsf(B) * um * vm) + fabsf(C) * vm * vm;
+  float margin = 1e-5f * mag + 1e-4f;
+  return o * orc_exp2r(pmax + margin) >= alpha_min;
+}
+
+/* A rectangle of more than 64 tiles keeps every tile (the test is applied to smaller ones). */
+#define ORC_CULL_MAX_TILES 64
+
+static int tile_kept(int64_t area, float mx, float my, float A, float B, float C, float o, int tx, int ty,
+                     const orc_config* cfg) {
+  if (area > ORC_CULL_MAX_TILES) return 1;
+  return orc_tile_hit(mx, my, A, B, C, o, tx, ty, cfg->tile_w, cfg->tile_h, cfg->alpha_min);
+}
 
 /* ---------------------------------------------------------------------------------- */
 /* Section 3: activation of one splat (view independent).                             */
@@ -211,7 +256,7 @@ void orc_sh_basis(double x, double y, double z, double* Y /*16*/) {
  *   rgb[3n]        colour (binary64)
  * A culled splat has touched = 0 and its other outputs are zero.
  */
-void orc_project(int64_t n, const float* means, const float* cov3d, const float* sh, const orc_camera* cam, const orc_config* cfg, float* depth,
+void orc_project(int64_t n, const float* means, const float* cov3d, const float* opacity, const float* sh, const orc_camera* cam, const orc_config* cfg, float* depth,
                  float* mean2d, float* cov2d, float* conic, float* qcoef, float* radius,
                  int32_t* rect, uint32_t* touched, double* rgb) {
   const float* W = cam->w2c;
@@ -296,7 +341,14 @@ void orc_project(int64_t n, const float* means, const float* cov3d, const float*
     qcoef[2 * n + k] = cc2 * kA;
     radius[k] = r;
     rect[k] = x0; rect[n + k] = y0; rect[2 * n + k] = x1; rect[3 * n + k] = y1;
-    touched[k] = (uint32_t)((x1 - x0) * (y1 - y0));
+    {
+      uint32_t kept = 0;
+      const int64_t area = (int64_t)(x1 - x0) * (y1 - y0);
+      for (int ty = y0; ty < y1; ++ty)
+        for (int tx = x0; tx < x1; ++tx)
+          kept += (uint32_t)tile_kept(area, mx, my, qcoef[k], qcoef[n + k], qcoef[2 * n + k], opacity[k], tx, ty, cfg);
+      touched[k] = kept;
+    }
 
     /* colour along the direction camera centre -> splat centre */
     double d[3] = {(double)mu[0] - cc[0], (double)mu[1] - cc[1], (double)mu[2] - cc[2]};
@@ -356,6 +408,7 @@ static void merge_sort_pairs(uint64_t* key, uint32_t* val, uint32_t* idx, int64_
  * (outputs untouched).
  */
 int64_t orc_bin(int64_t n, const uint32_t* touched, const int32_t* rect, const float* depth,
+                const float* mean2d, const float* qcoef, const float* opacity, const orc_config* cfg,
                 int32_t tiles_x, uint64_t tile_base, uint32_t val_base, int64_t capacity,
                 uint64_t* keys, uint32_t* vals, uint32_t* emit_index) {
   int64_t m = 0;
@@ -366,8 +419,11 @@ int64_t orc_bin(int64_t n, const uint32_t* touched, const int32_t* rect, const f
     if (touched[k] == 0) continue;
     uint32_t dbits;
     memcpy(&dbits, &depth[k], 4);
+    const int64_t area = (int64_t)(rect[2 * n + k] - rect[k]) * (rect[3 * n + k] - rect[n + k]);
     for (int32_t ty = rect[n + k]; ty < rect[3 * n + k]; ++ty)
       for (int32_t tx = rect[k]; tx < rect[2 * n + k]; ++tx) {
+        if (!tile_kept(area, mean2d[k], mean2d[n + k], qcoef[k], qcoef[n + k], qcoef[2 * n + k], opacity[k], tx, ty, cfg))
+          continue;
         uint64_t tile = tile_base + (uint64_t)ty * (uint64_t)tiles_x + (uint64_t)tx;
         keys[e] = (tile << 32) | (uint64_t)dbits;
         vals[e] = val_base + (uint32_t)k;

@@ -113,7 +113,7 @@ def test_batched_workload_sampled_views_and_tiles():
     for v in picks:
         cam = w.cameras[v]
         tx, ty = oracle.tiles_of(cam, ocfg)
-        pv = oracle.project(w.scene, act[0], cam, ocfg)
+        pv = oracle.project(w.scene, act[0], cam, ocfg, act[1])
         lk, lvv, le, lr = oracle.bin_sort(pv, cam, ocfg)
         lens = lr[:, 1].astype(np.int64) - lr[:, 0]
         pick = np.unique(np.concatenate([np.argsort(lens)[-4:], rng.choice(tx * ty, 6, replace=False)]))
@@ -136,7 +136,7 @@ def test_batched_workload_sampled_views_and_tiles():
         fr.step(flat[3 * off: 3 * (off + fr.total_pixels)], dm, torch.zeros_like(dm), n_views_total=len(w.cameras))
         torch.cuda.synchronize()
         cam = w.cameras[v]
-        pv = oracle.project(w.scene, act[0], cam, ocfg)
+        pv = oracle.project(w.scene, act[0], cam, ocfg, act[1])
         pv["opacity"] = act[1]
         touched = fr.touched.cpu().numpy().view(np.uint32).reshape(-1, n)
         start = int(touched[:lv].astype(np.int64).sum())

@@ -28,7 +28,7 @@ def _oracle_views(scene, cams, cfg):
     out = []
     tile_base = 0
     for v, cam in enumerate(cams):
-        pv = oracle.project(scene, act[0], cam, ocfg)
+        pv = oracle.project(scene, act[0], cam, ocfg, act[1])
         pv["opacity"] = act[1]
         keys, vals, emit, ranges = oracle.bin_sort(pv, cam, ocfg, tile_base=tile_base, val_base=v * scene.n)
         pv.update(keys=keys, vals=vals, emit=emit, ranges=ranges, tile_base=tile_base)

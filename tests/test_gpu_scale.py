@@ -65,7 +65,7 @@ def test_fullsize_preprocess_and_sort_views(big):
     counts = touched.reshape(len(w.cameras), n).astype(np.int64).sum(axis=1)
     for v in VIEWS:
         cam = w.cameras[v]
-        pv = oracle.project(w.scene, act[0], cam, ocfg)
+        pv = oracle.project(w.scene, act[0], cam, ocfg, act[1])
         assert np.array_equal(touched[v * n:(v + 1) * n], pv["touched"])
         vis = pv["touched"] > 0
         assert np.array_equal(r["mx"][v * n:(v + 1) * n][vis].view(np.uint32), pv["mean2d"][0][vis].view(np.uint32))
@@ -86,7 +86,7 @@ def test_fullsize_sampled_tiles(big):
     rng = np.random.default_rng(5)
     for v in VIEWS:
         cam = w.cameras[v]
-        pv = oracle.project(w.scene, act[0], cam, ocfg)
+        pv = oracle.project(w.scene, act[0], cam, ocfg, act[1])
         pv["opacity"] = act[1]
         ok, ov, oe, orng = oracle.bin_sort(pv, cam, ocfg)
         tx, ty = oracle.tiles_of(cam, ocfg)

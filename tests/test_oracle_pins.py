@@ -107,7 +107,7 @@ def test_axis_aligned_splat_on_optical_axis():
     sigma = 0.05
     sc = _scene(np.zeros((3, 1)), np.full((3, 1), math.log(sigma)), np.array([[1.0], [0], [0], [0]]), np.zeros(1))
     cov, op = oracle.activate(sc)
-    pr = oracle.project(sc, cov, cam, CFG)
+    pr = oracle.project(sc, cov, cam, CFG, op)
     f = cam.fy
     expect = f * f * sigma * sigma / 9.0 + 0.3
     assert pr["cov2d"][0, 0] == pytest.approx(expect, rel=2e-6)
@@ -140,7 +140,7 @@ def _numeric_jacobian(cam, p):
 def test_projection_is_linearised_pinhole(tiny):
     sc, cam = tiny.scene, tiny.cameras[0]
     cov, op = oracle.activate(sc)
-    pr = oracle.project(sc, cov, cam, CFG)
+    pr = oracle.project(sc, cov, cam, CFG, op)
     vis = np.nonzero(pr["touched"])[0]
     assert vis.size > 500
     checked = 0
@@ -166,7 +166,7 @@ def test_colour_dc_only():
     sh[0, :, 0] = [1.0, -0.2, -3.0]
     sc = _scene(np.zeros((3, 1)), np.full((3, 1), -3.0), np.array([[1.0], [0], [0], [0]]), np.zeros(1), sh)
     cov, op = oracle.activate(sc)
-    pr = oracle.project(sc, cov, cam, CFG)
+    pr = oracle.project(sc, cov, cam, CFG, op)
     y0 = 0.5 / math.sqrt(math.pi)
     np.testing.assert_allclose(pr["rgb"][:, 0], [max(0, v * y0 + 0.5) for v in sh[0, :, 0].astype(np.float64)], rtol=1e-12)
 
@@ -174,7 +174,7 @@ def test_colour_dc_only():
 def test_rect_encloses_square_and_clamps(tiny):
     sc, cam = tiny.scene, tiny.cameras[0]
     cov, op = oracle.activate(sc)
-    pr = oracle.project(sc, cov, cam, CFG)
+    pr = oracle.project(sc, cov, cam, CFG, op)
     tx, ty = oracle.tiles_of(cam, CFG)
     for k in np.nonzero(pr["touched"])[0][:400]:
         mx, my, r = pr["mean2d"][0, k], pr["mean2d"][1, k], pr["radius"][k]
@@ -183,7 +183,8 @@ def test_rect_encloses_square_and_clamps(tiny):
         x0, y0, x1, y1 = pr["rect"][:, k]
         got = [(x, y) for y in range(y0, y1) for x in range(x0, x1)]
         assert sorted(got) == sorted(want)
-        assert pr["touched"][k] == len(got)
+        kept = [t for t in got if len(got) > oracle.CULL_MAX_TILES or oracle.tile_hit(pr, k, t[0], t[1], CFG)]
+        assert pr["touched"][k] == len(kept)
 
 
 def test_cull_behind_and_near():
@@ -191,7 +192,7 @@ def test_cull_behind_and_near():
     means = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 0.0], [-3.5, -2.9, 0.0]])  # behind, inside near, visible
     sc = _scene(means, np.full((3, 3), -3.0), np.tile([[1.0], [0], [0], [0]], (1, 3)), np.zeros(3))
     cov, op = oracle.activate(sc)
-    pr = oracle.project(sc, cov, cam, CFG)
+    pr = oracle.project(sc, cov, cam, CFG, op)
     assert list(pr["touched"][:2]) == [0, 0] and pr["touched"][2] > 0
 
 
@@ -209,10 +210,12 @@ def test_bin_sort_against_numpy_stable_sort(tiny):
         for k in range(sc.n):
             x0, y0, x1, y1 = v["rect"][:, k]
             dbits = int(np.float32(v["depth"][k]).view(np.uint32))
+            big = (x1 - x0) * (y1 - y0) > oracle.CULL_MAX_TILES
             for y in range(y0, y1):
                 for x in range(x0, x1):
-                    keys.append(((y * tx + x) << 32) | dbits)
-                    vals.append(k)
+                    if big or oracle.tile_hit(v, k, x, y, cfg):
+                        keys.append(((y * tx + x) << 32) | dbits)
+                        vals.append(k)
         keys = np.array(keys, np.uint64)
         order = np.argsort(keys, kind="stable")
         assert np.array_equal(v["keys"], keys[order])
@@ -225,6 +228,142 @@ def test_bin_sort_against_numpy_stable_sort(tiny):
                 assert tuple(v["ranges"][t]) == (idx[0], idx[-1] + 1)
             else:
                 assert v["ranges"][t][0] == v["ranges"][t][1]
+
+
+def _random_splats(rng, m, tile):
+    """Splats around one tile: centres within 1.5 tiles of it, 2D covariances of every
+    orientation and anisotropy (low-pass 0.3 added), opacities from 0.004 to 0.99."""
+    out = []
+    for _ in range(m):
+        mx = float(rng.uniform(-1.5, 2.5) * tile[0])
+        my = float(rng.uniform(-1.5, 2.5) * tile[1])
+        th = rng.uniform(0, np.pi)
+        s1, s2 = np.exp(rng.uniform(np.log(0.3), np.log(12.0), 2))
+        R = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+        S = R @ np.diag([s1 * s1, s2 * s2]) @ R.T + 0.3 * np.eye(2)
+        Q = np.linalg.inv(S)
+        kA = -0.5 * math.log2(math.e)
+        A, B, C = np.float32(Q[0, 0] * kA), np.float32(-Q[0, 1] * math.log2(math.e)), np.float32(Q[1, 1] * kA)
+        o = float(np.exp(rng.uniform(np.log(0.004), np.log(0.99))))
+        out.append((np.float32(mx), np.float32(my), A, B, C, np.float32(o)))
+    return out
+
+
+def _tile_alpha_max(sp, tile, step):
+    """Largest o 2^p over a lattice of the tile's pixel-centre rectangle (binary64)."""
+    mx, my, A, B, C, o = (float(x) for x in sp)
+    xs = np.arange(0.5, tile[0] - 0.5 + 1e-9, step)
+    ys = np.arange(0.5, tile[1] - 0.5 + 1e-9, step)
+    u = xs[None, :] - mx
+    v = ys[:, None] - my
+    p = A * u * u + B * u * v + C * v * v
+    return o * np.exp2(p.max())
+
+
+def test_tile_test_is_conservative_and_tight():
+    """Brute force over pixel centres: a tile that some pixel centre gives alpha >= alpha_min
+    is always kept; a kept tile comes within the test's margin of alpha_min somewhere on its
+    pixel-centre rectangle (sampled at 1/8 pixel, edges included)."""
+    rng = np.random.default_rng(11)
+    amin = float(CFG.alpha_min)
+    kept = dropped = near = 0
+    for tw, th in [(16, 16), (8, 32), (32, 8)]:
+        cfg = oracle.make_config(tile_w=tw, tile_h=th)
+        for sp in _random_splats(rng, 700, (tw, th)):
+            proj = dict(mean2d=np.array([[sp[0]], [sp[1]]], np.float32),
+                        qcoef=np.array([[sp[2]], [sp[3]], [sp[4]]], np.float32), opacity=np.array([sp[5]], np.float32))
+            hit = oracle.tile_hit(proj, 0, 0, 0, cfg)
+            on_pixels = _tile_alpha_max(sp, (tw, th), 1.0)
+            if on_pixels >= amin * (1 + 1e-6):
+                assert hit, sp
+            dense = _tile_alpha_max(sp, (tw, th), 0.125)
+            if hit:
+                kept += 1
+                assert dense >= amin * 2.0 ** -0.25, sp
+                near += dense < amin
+            else:
+                dropped += 1
+                assert dense < amin * 1.001, sp
+    assert kept > 300 and dropped > 300 and near < 0.03 * kept
+    # on the boundary: opacity set so that the sampled maximum is alpha_min x f
+    both = 0
+    for sp in _random_splats(rng, 1500, (16, 16)):
+        peak = _tile_alpha_max(sp, (16, 16), 0.125) / float(sp[5])
+        if not 1e-30 < peak:
+            continue
+        res = []
+        for f in (1.002, 0.95):
+            o = np.float32(amin * f / peak)
+            if not 0.0 < o < 1.0:
+                break
+            proj = dict(mean2d=np.array([[sp[0]], [sp[1]]], np.float32),
+                        qcoef=np.array([[sp[2]], [sp[3]], [sp[4]]], np.float32), opacity=np.array([o], np.float32))
+            res.append(oracle.tile_hit(proj, 0, 0, 0, CFG))
+        if len(res) == 2:
+            assert res[0]  # the continuous maximum passes alpha_min: kept
+            both += 1
+            dropped += not res[1]
+            near += res[1]
+    # the margin keeps only a sliver of tiles whose maximum is 5 % short of alpha_min
+    assert both > 300 and near < 0.05 * both
+
+
+def test_tile_test_agrees_with_rendered_alphas(tiny):
+    """Every (pixel, splat) pair the compositor takes lies in a kept tile, and nearly every
+    kept instance of the tiny view has a pixel whose alpha (in binary64) reaches alpha_min."""
+    sc, cam = tiny.scene, tiny.cameras[0]
+    v = oracle.prepare_view(sc, cam, CFG)
+    pix, ks, pos = oracle.pixel_lists(v, v["vals"], v["ranges"], cam, CFG)
+    tx, _ = oracle.tiles_of(cam, CFG)
+    tile_of_pix = (pix // cam.width // 16) * tx + (pix % cam.width) // 16
+    kept = set(zip((v["keys"] >> np.uint64(32)).astype(np.int64).tolist(), v["vals"].astype(np.int64).tolist()))
+    assert all((int(t), int(k)) in kept for t, k in zip(tile_of_pix, ks))
+    hit = 0
+    for t, k in list(kept)[:3000]:
+        x, y = t % tx, t // tx
+        sp = (v["mean2d"][0, k] - 16 * x, v["mean2d"][1, k] - 16 * y, *v["qcoef"][:, k], v["opacity"][k])
+        hit += _tile_alpha_max(sp, (16, 16), 1.0) >= CFG.alpha_min * 0.99
+    assert hit >= 0.97 * min(3000, len(kept))
+
+
+def _full_rect_lists(v, cam, cfg):
+    """Whole-rectangle binning written out with numpy: per tile, every splat whose 3-sigma
+    rectangle covers it, stably ordered by depth bits."""
+    tx, ty = oracle.tiles_of(cam, cfg)
+    keys, vals = [], []
+    for k in np.nonzero(v["rect"][2] > v["rect"][0])[0]:
+        x0, y0, x1, y1 = v["rect"][:, k]
+        d = int(np.float32(v["depth"][k]).view(np.uint32))
+        for y in range(y0, y1):
+            for x in range(x0, x1):
+                keys.append(((y * tx + x) << 32) | d)
+                vals.append(k)
+    keys = np.array(keys, np.uint64)
+    order = np.argsort(keys, kind="stable")
+    keys, vals = keys[order], np.array(vals, np.uint32)[order]
+    t = (keys >> np.uint64(32)).astype(np.int64)
+    ranges = np.zeros((tx * ty, 2), np.uint32)
+    ranges[:, 0] = np.searchsorted(t, np.arange(tx * ty), "left")
+    ranges[:, 1] = np.searchsorted(t, np.arange(tx * ty), "right")
+    return vals, ranges
+
+
+def test_culled_binning_renders_and_removes_like_whole_rectangles(tiny):
+    """Images, transmittances and per-splat removal effects from the culled lists equal those
+    from whole-rectangle lists bit for bit: culling only drops pairs the compositor skips."""
+    sc, cam = tiny.scene, tiny.cameras[0]
+    v = oracle.prepare_view(sc, cam, CFG)
+    fv, fr = _full_rect_lists(v, cam, CFG)
+    assert fv.size > v["vals"].size * 1.2
+    a = oracle.render(v, v["vals"], v["ranges"], cam, CFG)
+    b = oracle.render(v, fv, fr, cam, CFG)
+    for x, y in zip(a[:3], b[:3]):
+        assert np.array_equal(x, y)
+    tgt = (a[0] + synth.target_noise(a[0].shape, 0.02, 5, 0)).astype(np.float32)
+    da, ia = oracle.removal_effect(v, v["vals"], v["ranges"], cam, CFG, tgt)
+    db, ib = oracle.removal_effect(v, fv, fr, cam, CFG, tgt)
+    assert np.array_equal(da, db) and np.array_equal(ia, ib)
+    assert np.count_nonzero(da) > 500
 
 
 def test_depth_bits_order_matches_numeric_order():
@@ -397,7 +536,7 @@ def test_colour_direction_is_camera_to_splat():
     sh[3, 1, 0] = 1.0  # green also gets Y_1^1 = -c x
     sc = _scene(np.array([[1.0], [0.0], [0.0]]), np.full((3, 1), -3.0), np.array([[1.0], [0], [0], [0]]), np.zeros(1), sh)
     cov, op = oracle.activate(sc)
-    pr = oracle.project(sc, cov, cam, CFG)
+    pr = oracle.project(sc, cov, cam, CFG, op)
     c1 = math.sqrt(3 / (4 * math.pi))
     d = np.array([1.0, 0.0, 3.0]) / math.sqrt(10.0)
     assert pr["touched"][0] > 0
