@@ -116,19 +116,22 @@ typedef struct {
 
 /*
  * Per-(view, splat) buffers produced by potr_preprocess and potr_bin_sort (device, caller
- * owned).  raster holds 12 floats per vk, 16-byte aligned:
+ * owned).  raster holds 16 floats (64 bytes) per vk, 16-byte aligned:
  *   [0] mean x  [1] mean y  [2] A  [3] B  [4] C  [5] opacity  [6] prefilter  [7] offset bits
  *   [8] r       [9] g       [10] b [11] rectangle bits (x0 | y0 << 11 | width << 22)
- * where log2 G(dx, dy) = A dx^2 + B dx dy + C dy^2 and "offset" is the vk's first emission
- * slot (written by potr_bin_sort).
+ *   [12] kept-tile mask, low word  [13] high word  [14] 1 if every tile is kept  [15] 0
+ * where log2 G(dx, dy) = A dx^2 + B dx dy + C dy^2, "offset" is the vk's first emission
+ * slot (written by potr_bin_sort) and mask bit (ty - y0) width + (tx - x0) says whether
+ * tile (tx, ty) of the rectangle is kept (rectangles of at most 64 tiles; larger ones keep
+ * every tile).
  */
 typedef struct {
   float* cov3d;          /* [6][n] activated covariance (xx, xy, xz, yy, yz, zz) */
   float* opacity;        /* [n] */
-  float* raster;         /* [V * n][12] */
+  float* raster;         /* [V * n][16] */
   float* depth;          /* [V * n] camera-space z, the sort key's low word */
   uint32_t* rect;        /* [V * n][2] (x0 | y0 << 16, x1 | y1 << 16), tiles, half open */
-  uint32_t* touched;     /* [V * n] tiles covered, 0 when culled */
+  uint32_t* touched;     /* [V * n] kept tiles, 0 when culled */
   uint32_t* offsets;     /* [V * n] exclusive prefix sum of touched (emission slots) */
   uint32_t* n_instances; /* [1] total instances (potr_bin_sort) */
 } potr_views;
@@ -154,8 +157,13 @@ POTR_API potr_status potr_view_layout(const potr_camera* h_cams, int32_t n_views
  * every view of the frame, EWA projection (view transform, near cull, clamped Jacobian,
  * Sigma2D = J W Sigma W^T J^T + lowpass I, conic, radius ceil(3 sqrt(lambda_max))), pixel
  * centre, tile rectangle, depth and the SH colour max(0, sum_i L_i Y_i(d) + 0.5) along the
- * camera-to-splat direction d.  Writes views->cov3d, opacity, raster (all but the offset
- * word), depth, rect, touched.  Every quantity that decides the binning or the per-pixel
+ * camera-to-splat direction d.  A tile of the rectangle is kept only if some pixel centre in
+ * it can reach alpha >= alpha_min (the exponent's maximum over the tile's pixel-centre
+ * rectangle, on its edges or at the splat centre, plus a rounding margin of 1e-5 x the
+ * largest term magnitude + 1e-4, through the same exp2): such tiles hold no pair the
+ * compositor takes, so no output changes.  Rectangles of more than 64 tiles keep every tile.
+ * Writes views->cov3d, opacity, raster (all but the offset word), depth, rect, touched
+ * (kept tiles).  Every quantity that decides the binning or the per-pixel
  * alpha test is computed in binary32 with a fixed operation order (no contraction), with
  * exp taken by a reproducible exp2 (Cody-Waite reduction plus a degree-6 Taylor polynomial).
  */
@@ -175,22 +183,26 @@ POTR_API size_t potr_tile_schedule_workspace_size(void);
 POTR_API potr_status potr_tile_schedule(const potr_frame* frame, const uint32_t* d_tile_ranges,
                                         uint32_t* d_tile_order, void* d_ws, size_t ws_bytes, potr_stream_t stream);
 
-/* Workspace bytes potr_bin_sort needs (scan partials, sort double buffers, histograms). */
+/* Workspace bytes potr_bin_sort needs (scan partials, sort double buffers for the V * n depth
+ * keys and the instances, histograms): about 16 (V * n) + 8 instance_capacity bytes. */
 POTR_API size_t potr_bin_sort_workspace_size(int64_t n, int32_t n_views, int64_t total_tiles, int64_t instance_capacity);
 
 /*
- * Binning (Section 3, "ordering these layers according to the splats' approximate depth"):
- * exclusive scan of touched over vk -> views->offsets and *views->n_instances; one instance
- * per touched tile emitted in vk order and, within a rectangle, row-major, with key
- * (global tile << 32) | bits(depth) and value vk; a stable LSD radix sort of the keys
- * (8-bit digits over the significant bits); and per-global-tile [start, end) ranges into
- * d_tile_ranges[total_tiles][2] (empty tiles get [0, 0)).  The result equals a stable sort,
- * so equal keys keep emission order.  d_keys / d_vals hold instance_capacity entries.
- * If the instance count exceeds instance_capacity, d_status gets POTR_ERR_CAPACITY and the
- * required count, and every tile range is left empty.
+ * Binning (Section 3, "ordering these layers according to the splats' approximate depth").
+ * Defined result: one instance per kept tile, emitted in vk order and, within a rectangle,
+ * row-major, with key (global tile << 32) | bits(depth) and value vk, stably sorted by key;
+ * its emission slot is views->offsets[vk] (exclusive scan of touched over vk, also stored in
+ * record word 7) plus the tile's rank among the vk's kept tiles.  Outputs: d_tiles[i] = the
+ * global tile (the key's high word) and d_vals[i] = vk of sorted instance i, both
+ * instance_capacity entries; *views->n_instances; per-global-tile [start, end) ranges into
+ * d_tile_ranges[total_tiles][2] (empty tiles get [0, 0)).  Computed as a stable radix sort
+ * of the vk by depth bits, emission in that order, and a stable radix partition by tile,
+ * which yields the same order.  If the instance count exceeds instance_capacity, d_status
+ * gets POTR_ERR_CAPACITY and the required count, and every tile range is left empty.
+ * UNSUPPORTED if the frame has 2^32 or more tiles or V * n >= 2^32 - 1.
  */
 POTR_API potr_status potr_bin_sort(const potr_views* views, const potr_frame* frame, const potr_raster_config* cfg,
-                          int64_t n, int64_t instance_capacity, uint64_t* d_keys, uint32_t* d_vals,
+                          int64_t n, int64_t instance_capacity, uint32_t* d_tiles, uint32_t* d_vals,
                           uint32_t* d_tile_ranges, potr_device_status* d_status, void* d_ws, size_t ws_bytes,
                           potr_stream_t stream);
 
@@ -315,10 +327,10 @@ POTR_API potr_status potr_pair_stats(const potr_views* views, const potr_frame* 
  * that overlap on the GPU race, so serialise them.  It allocates nothing.
  */
 #define POTR_STATIC_MAX_INSTANCES 4194304LL
-#define POTR_STATIC_MAX_VIEW_SPLATS 16777216LL
+#define POTR_STATIC_MAX_VIEW_SPLATS 1048576LL
 POTR_API potr_status potr_bin_sort_static(const potr_views* views, const potr_frame* frame,
                                           const potr_raster_config* cfg, int64_t n, int64_t instance_capacity,
-                                          uint64_t* d_keys, uint32_t* d_vals, uint32_t* d_tile_ranges,
+                                          uint32_t* d_tiles, uint32_t* d_vals, uint32_t* d_tile_ranges,
                                           potr_device_status* d_status, potr_stream_t stream);
 
 /*

@@ -26,7 +26,7 @@ POTR_ERR_NUMERIC = 5
 POTR_ERR_UNSUPPORTED = 6
 POTR_ERR_TOO_LARGE = 7
 POTR_STATIC_MAX_INSTANCES = 4194304
-POTR_STATIC_MAX_VIEW_SPLATS = 16777216
+POTR_STATIC_MAX_VIEW_SPLATS = 1048576
 
 
 class PotrError(RuntimeError):
@@ -181,9 +181,9 @@ def potr_bin_sort_workspace_size(n: int, n_views: int, total_tiles: int, capacit
     return int(lib().potr_bin_sort_workspace_size(n, n_views, total_tiles, capacity))
 
 
-def potr_bin_sort(views: Views, frame: Frame, cfg: RasterConfig, n: int, capacity: int, keys, vals, ranges, status,
+def potr_bin_sort(views: Views, frame: Frame, cfg: RasterConfig, n: int, capacity: int, tiles, vals, ranges, status,
                   ws, stream=None):
-    _check("potr_bin_sort", lib().potr_bin_sort(C.byref(views), C.byref(frame), C.byref(cfg), n, capacity, ptr(keys),
+    _check("potr_bin_sort", lib().potr_bin_sort(C.byref(views), C.byref(frame), C.byref(cfg), n, capacity, ptr(tiles),
                                                 ptr(vals), ptr(ranges), ptr(status), ptr(ws), ws.numel(),
                                                 stream_handle(stream)))
 
@@ -221,11 +221,11 @@ def potr_launch_count() -> int:
     return int(lib().potr_launch_count())
 
 
-def potr_bin_sort_static(views: Views, frame: Frame, cfg: RasterConfig, n: int, capacity: int, keys, vals, ranges,
+def potr_bin_sort_static(views: Views, frame: Frame, cfg: RasterConfig, n: int, capacity: int, tiles, vals, ranges,
                          status, stream=None):
     """potr_bin_sort with the library's fixed scratch instead of a caller workspace."""
     _check("potr_bin_sort_static", lib().potr_bin_sort_static(C.byref(views), C.byref(frame), C.byref(cfg), n,
-                                                              capacity, ptr(keys), ptr(vals), ptr(ranges),
+                                                              capacity, ptr(tiles), ptr(vals), ptr(ranges),
                                                               ptr(status), stream_handle(stream)))
 
 

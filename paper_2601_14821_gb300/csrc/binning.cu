@@ -32,8 +32,8 @@ constexpr int kSpinLimit = 1 << 22;
 // lane l holding items l + 32 j (j = 0..7): loads and stores are coalesced.
 // -----------------------------------------------------------------------------------------
 template <typename Tin, typename Tacc, typename Tout>
-__global__ void __launch_bounds__(kScanThreads) scan_chunks_kernel(const Tin* in, Tout* out,
-                                                                   int64_t n, Tacc* __restrict__ chunk_sums) {
+__global__ void __launch_bounds__(kScanThreads) scan_chunks_kernel(const Tin* in, const uint32_t* __restrict__ gather,
+                                                                   Tout* out, int64_t n, Tacc* __restrict__ chunk_sums) {
   __shared__ Tacc warp_tot[kScanThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)warp * 256;
@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_chunks_kernel(const Tin* in
 #pragma unroll
   for (int j = 0; j < kScanItems; ++j) {
     const int64_t i = base + lane + 32 * j;
-    v[j] = (i < n) ? (Tacc)in[i] : (Tacc)0;
+    v[j] = (i < n) ? (Tacc)in[gather ? (int64_t)gather[i] : i] : (Tacc)0;
   }
   Tacc carry = 0;
 #pragma unroll
@@ -95,12 +95,14 @@ int64_t scan_ws_words(int64_t n) {
   return w + 1;
 }
 
-// Exclusive scan in[0..n) -> out, total (u64) -> *total.  ws: scan_ws_words(n) u64 words.
+// Exclusive scan of x_i = in[i] (or in[gather[i]]) for i in [0, n) -> out, total (u64) ->
+// *total.  ws: scan_ws_words(n) u64 words.
 template <typename Tin, typename Tout>
-cudaError_t scan_exclusive(const Tin* in, Tout* out, int64_t n, uint64_t* total, uint64_t* ws, cudaStream_t s) {
+cudaError_t scan_exclusive(const Tin* in, Tout* out, int64_t n, uint64_t* total, uint64_t* ws, cudaStream_t s,
+                           const uint32_t* gather = nullptr) {
   const int64_t nb = ceil_div(n, kScanChunk);
   uint64_t* sums = ws;
-  scan_chunks_kernel<Tin, uint64_t, Tout><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, sums);
+  scan_chunks_kernel<Tin, uint64_t, Tout><<<(unsigned)nb, kScanThreads, 0, s>>>(in, gather, out, n, sums);
   note_launches(2);  // this level's scan plus the store or the add below
   if (nb == 1) {
     store_total_kernel<<<1, 1, 0, s>>>(sums, total);
@@ -113,7 +115,7 @@ cudaError_t scan_exclusive(const Tin* in, Tout* out, int64_t n, uint64_t* total,
 }
 
 // -----------------------------------------------------------------------------------------
-// Instance count check and emission.
+// Instance count check, depth keys and emission.
 // -----------------------------------------------------------------------------------------
 __global__ void count_check_kernel(const uint64_t* __restrict__ total, int64_t capacity, uint32_t* __restrict__ n_inst,
                                    uint64_t* __restrict__ m_eff, potr_device_status* __restrict__ st) {
@@ -124,49 +126,75 @@ __global__ void count_check_kernel(const uint64_t* __restrict__ total, int64_t c
   if (!ok) set_status(st, POTR_ERR_CAPACITY, (int64_t)t);
 }
 
-// One warp per 32 consecutive vk.  Their emission slots form one contiguous run (offsets are
-// the exclusive prefix of touched in vk order), so the lanes write consecutive slots: lane l
-// takes slots l, l + 32, ... of the run, finds the owning vk by a 5-step shuffle search over
-// the warp's exclusive counts, and derives the tile from the slot's rank in that vk's
-// row-major rectangle.  Stores are coalesced whatever the rectangle sizes.
-// It also counts the digits of every sort pass (ghist[pass][256]): the four depth digits are
-// shared by all instances of a vk (added once per vk, weighted by its count), the tile digits
-// are counted per instance with warp-aggregated shared-memory increments.
-__global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ touched, const uint32_t* __restrict__ offsets,
-                                                   const uint2* __restrict__ rect, const float* __restrict__ depth,
+// Depth sort keys of every vk (bits of the camera-space depth, which order like the positive
+// floats they are; 0xffffffff for a vk without kept tiles, so it sorts last), the digit
+// histograms of the four depth passes, and the vk's first emission slot into record word 7.
+__global__ void __launch_bounds__(256) depth_key_kernel(const uint32_t* __restrict__ touched,
+                                                        const uint32_t* __restrict__ offsets,
+                                                        const float* __restrict__ depth, int64_t n_vk,
+                                                        float4* __restrict__ raster, uint32_t* __restrict__ keys,
+                                                        uint32_t* __restrict__ ghist) {
+  __shared__ uint32_t h[4][256];
+  for (int p = 0; p < 4; ++p) h[p][threadIdx.x] = 0;
+  __syncthreads();
+  for (int64_t vk = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; vk < n_vk; vk += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t key = 0xffffffffu;
+    if (touched[vk]) {
+      key = __float_as_uint(depth[vk]);
+      reinterpret_cast<float*>(raster + vk * kRec + 1)[3] = __uint_as_float(offsets[vk]);
+    }
+    keys[vk] = key;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) atomicAdd(&h[p][(key >> (8 * p)) & 0xffu], 1u);
+  }
+  __syncthreads();
+  for (int p = 0; p < 4; ++p)
+    if (h[p][threadIdx.x]) atomicAdd(&ghist[p * 256 + threadIdx.x], h[p][threadIdx.x]);
+}
+
+// Emission in depth order.  One warp per 32 consecutive entries of the depth-sorted vk order;
+// their emission slots form one contiguous run (eoff is the exclusive prefix of the kept-tile
+// counts in that order), so lane l takes slots l, l + 32, ... of the run, finds the owning
+// entry by a 5-step shuffle search over the warp's exclusive counts, and derives the tile
+// from the slot's rank among that vk's kept tiles (row-major in its rectangle, through the
+// kept-tile mask).  Stores are coalesced whatever the rectangle sizes.  Each instance gets key
+// = global tile and value = vk; a stable partition by tile then yields per-tile lists in
+// (depth, vk) order.  The tile digits of every partition pass are counted here
+// (warp-aggregated shared-memory increments).
+__global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ eoff,
+                                                   const uint32_t* __restrict__ touched, const uint2* __restrict__ rect,
                                                    const potr_view_info* __restrict__ info, int64_t n, int64_t n_vk,
-                                                   const uint64_t* __restrict__ m_eff, float4* __restrict__ raster,
-                                                   uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, int passes,
-                                                   uint32_t* __restrict__ ghist) {
+                                                   const uint64_t* __restrict__ m_eff,
+                                                   const float4* __restrict__ raster, uint32_t* __restrict__ keys,
+                                                   uint32_t* __restrict__ vals, int passes, uint32_t* __restrict__ ghist) {
   __shared__ uint32_t h[kMaxPasses][256];
-  for (int p = 0; p < kMaxPasses; ++p) h[p][threadIdx.x] = 0;
+  for (int p = 0; p < passes; ++p) h[p][threadIdx.x] = 0;
   __syncthreads();
   if (*m_eff == 0) return;  // uniform: nothing emitted, nothing counted
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   const int64_t warps_total = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t wv = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wv * 32 < n_vk; wv += warps_total) {
-    const int64_t vk = wv * 32 + lane;
-    uint32_t cnt = 0, off = 0, x0 = 0, y0 = 0, w = 1, lo = 0;
-    uint64_t row0 = 0, tiles_x = 0;
-    if (vk < n_vk) {
+    const int64_t i = wv * 32 + lane;
+    uint32_t vk = 0, cnt = 0, off = 0, x0 = 0, y0 = 0, w = 1, m_lo = 0, m_hi = 0, m_all = 1, tiles_x = 0, row0 = 0;
+    if (i < n_vk) {
+      vk = order[i];
+      off = eoff[i];
       cnt = touched[vk];
       if (cnt) {
-        off = offsets[vk];
-        reinterpret_cast<float*>(raster + vk * 3 + 1)[3] = __uint_as_float(off);
-        const potr_view_info vi = info[(int)(vk / n)];
+        const potr_view_info vi = info[(int)(vk / (uint64_t)n)];
         const uint2 r = rect[vk];
         x0 = r.x & 0xffffu;
         y0 = r.x >> 16;
         w = (r.y & 0xffffu) - x0;
-        tiles_x = (uint64_t)vi.tiles_x;
-        row0 = (uint64_t)vi.tile_base;
-        lo = __float_as_uint(depth[vk]);
-#pragma unroll
-        for (int p = 0; p < 4; ++p) atomicAdd(&h[p][(lo >> (8 * p)) & 0xffu], cnt);
+        tiles_x = (uint32_t)vi.tiles_x;
+        row0 = (uint32_t)vi.tile_base;
+        const float4 m = raster[(size_t)vk * kRec + 3];  // kept-tile mask
+        m_lo = __float_as_uint(m.x);
+        m_hi = __float_as_uint(m.y);
+        m_all = __float_as_uint(m.z);
       }
     }
-    // exclusive prefix of cnt over the warp, total, and the run's first slot
     uint32_t incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -190,22 +218,26 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
         if (cand < 32 && ce <= e) owner = cand;
       }
       const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, owner);
+      const uint32_t o_vk = __shfl_sync(0xffffffffu, vk, owner);
       const uint32_t o_x0 = __shfl_sync(0xffffffffu, x0, owner);
       const uint32_t o_y0 = __shfl_sync(0xffffffffu, y0, owner);
       const uint32_t o_w = __shfl_sync(0xffffffffu, w, owner);
-      const uint32_t o_lo = __shfl_sync(0xffffffffu, lo, owner);
-      const uint64_t o_row0 = __shfl_sync(0xffffffffu, row0, owner);
-      const uint64_t o_tx = __shfl_sync(0xffffffffu, tiles_x, owner);
-      uint64_t tile = 0;
+      const uint32_t o_row0 = __shfl_sync(0xffffffffu, row0, owner);
+      const uint32_t o_tx = __shfl_sync(0xffffffffu, tiles_x, owner);
+      const uint32_t o_mlo = __shfl_sync(0xffffffffu, m_lo, owner);
+      const uint32_t o_mhi = __shfl_sync(0xffffffffu, m_hi, owner);
+      const uint32_t o_all = __shfl_sync(0xffffffffu, m_all, owner);
+      uint32_t tile = 0;
       if (e < total) {
-        const uint32_t li = e - o_excl;
+        // the li-th kept tile of the owner's rectangle, row-major
+        const uint32_t li = o_all ? e - o_excl : select_bit64(((uint64_t)o_mhi << 32) | o_mlo, e - o_excl);
         const uint32_t dy = li / o_w, dx = li - dy * o_w;
-        tile = o_row0 + (uint64_t)(o_y0 + dy) * o_tx + (o_x0 + dx);
-        keys[run0 + e] = (tile << 32) | (uint64_t)o_lo;
-        vals[run0 + e] = (uint32_t)(wv * 32 + owner);
+        tile = o_row0 + (o_y0 + dy) * o_tx + (o_x0 + dx);
+        keys[run0 + e] = tile;
+        vals[run0 + e] = o_vk;
       }
-      for (int p = 4; p < passes; ++p) {
-        const uint32_t d = (e < total) ? (uint32_t)(tile >> (8 * (p - 4))) & 0xffu : 256u;
+      for (int p = 0; p < passes; ++p) {
+        const uint32_t d = (e < total) ? (tile >> (8 * p)) & 0xffu : 256u;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         if (d < 256u && (peers & lt) == 0) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
       }
@@ -226,9 +258,7 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
 // so every block a look-back waits on is already running; the wait is bounded and reports
 // POTR_ERR_TIMEOUT instead of hanging.
 // -----------------------------------------------------------------------------------------
-size_t onesweep_smem_bytes() {
-  return sizeof(uint64_t) * kOsTile + sizeof(uint32_t) * kOsTile + sizeof(uint32_t) * (8 * 257 + 3 * 256);
-}
+size_t onesweep_smem_bytes() { return sizeof(uint32_t) * 2 * kOsTile + sizeof(uint32_t) * (8 * 257 + 3 * 256); }
 
 // Exclusive scan of one value per thread over a 256-thread block (returns this thread's prefix).
 __device__ __forceinline__ uint32_t block_exclusive_scan256(uint32_t x, uint32_t* tmp8) {
@@ -304,18 +334,21 @@ __global__ void __launch_bounds__(256) digit_base_kernel(const uint32_t* __restr
   for (int p = 0; p < passes; ++p) gbase[p * 256 + threadIdx.x] = block_exclusive_scan256(ghist[p * 256 + threadIdx.x], tmp8);
 }
 
-__global__ void __launch_bounds__(kOsThreads) onesweep_kernel(const uint64_t* __restrict__ keys_in,
+// vals_in == nullptr: the value of item i is i itself.  The item count is *m_dev, or m_host
+// when m_dev is null.
+__global__ void __launch_bounds__(kOsThreads) onesweep_kernel(const uint32_t* __restrict__ keys_in,
                                                               const uint32_t* __restrict__ vals_in,
-                                                              const uint64_t* __restrict__ m_eff, int shift,
+                                                              const uint64_t* __restrict__ m_dev, int64_t m_host,
+                                                              int shift,
                                                               const uint32_t* __restrict__ gbase,
                                                               uint32_t* __restrict__ tile_counter,
                                                               unsigned long long* status,
-                                                              uint64_t* __restrict__ keys_out,
+                                                              uint32_t* __restrict__ keys_out,
                                                               uint32_t* __restrict__ vals_out,
                                                               potr_device_status* __restrict__ st) {
-  extern __shared__ uint64_t os_smem[];
-  uint64_t* s_keys = os_smem;                                          // [kOsTile]
-  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + kOsTile);    // [kOsTile]
+  extern __shared__ uint32_t os_smem[];
+  uint32_t* s_keys = os_smem;                                          // [kOsTile]
+  uint32_t* s_vals = s_keys + kOsTile;                                 // [kOsTile]
   uint32_t* warp_cnt = s_vals + kOsTile;                               // [8][257]
   uint32_t* blk_off = warp_cnt + 8 * 257;                              // [256]
   uint32_t* dig_glob = blk_off + 256;                                  // [256]
@@ -330,20 +363,19 @@ __global__ void __launch_bounds__(kOsThreads) onesweep_kernel(const uint64_t* __
   if (threadIdx.x < 8) warp_cnt[threadIdx.x * 257 + 256] = 0;
   __syncthreads();
   const uint32_t tile = s_tile;
-  const int64_t m = (int64_t)*m_eff;
+  const int64_t m = m_dev ? (int64_t)*m_dev : m_host;
   const int64_t base = (int64_t)tile * kOsTile;
   if (base >= m) return;  // uniform per block
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
-  uint64_t k[kOsItems];
-  uint32_t v[kOsItems], dg[kOsItems], lr[kOsItems];
+  uint32_t k[kOsItems], v[kOsItems], dg[kOsItems], lr[kOsItems];
 #pragma unroll
   for (int r = 0; r < kOsItems; ++r) {
     const int64_t i = base + warp * (kOsItems * 32) + r * 32 + lane;
     const bool valid = i < m;
-    k[r] = valid ? keys_in[i] : 0ull;
-    v[r] = valid ? vals_in[i] : 0u;
-    dg[r] = valid ? (uint32_t)(k[r] >> shift) & 0xffu : 256u;
+    k[r] = valid ? keys_in[i] : 0u;
+    v[r] = valid ? (vals_in ? vals_in[i] : (uint32_t)i) : 0u;
+    dg[r] = valid ? (k[r] >> shift) & 0xffu : 256u;
   }
   // stable rank inside the warp: rounds in order, lanes in order
   uint32_t* wc = warp_cnt + warp * 257;
@@ -392,8 +424,8 @@ __global__ void __launch_bounds__(kOsThreads) onesweep_kernel(const uint64_t* __
   __syncthreads();
   const int nvalid = (int)min((int64_t)kOsTile, m - base);
   for (int i = threadIdx.x; i < nvalid; i += kOsThreads) {
-    const uint64_t key = s_keys[i];
-    const uint32_t d = (uint32_t)(key >> shift) & 0xffu;
+    const uint32_t key = s_keys[i];
+    const uint32_t d = (key >> shift) & 0xffu;
     const uint32_t o = dig_glob[d] + ((uint32_t)i - blk_off[d]);
     keys_out[o] = key;
     vals_out[o] = s_vals[i];
@@ -401,14 +433,14 @@ __global__ void __launch_bounds__(kOsThreads) onesweep_kernel(const uint64_t* __
   if (threadIdx.x == 0 && s_err) set_status(st, POTR_ERR_TIMEOUT, 0);
 }
 
-__global__ void __launch_bounds__(256) tile_ranges_kernel(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ m_eff,
+__global__ void __launch_bounds__(256) tile_ranges_kernel(const uint32_t* __restrict__ tiles, const uint64_t* __restrict__ m_eff,
                                                           int64_t total_tiles, uint32_t* __restrict__ ranges) {
   const int64_t m = (int64_t)*m_eff;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t t = keys[i] >> 32;
+    const uint32_t t = tiles[i];
     if (t >= (uint64_t)total_tiles) continue;
-    if (i == 0 || (keys[i - 1] >> 32) != t) ranges[2 * t] = (uint32_t)i;
-    if (i == m - 1 || (keys[i + 1] >> 32) != t) ranges[2 * t + 1] = (uint32_t)(i + 1);
+    if (i == 0 || tiles[i - 1] != t) ranges[2 * t] = (uint32_t)i;
+    if (i == m - 1 || tiles[i + 1] != t) ranges[2 * t + 1] = (uint32_t)(i + 1);
   }
 }
 
@@ -419,8 +451,9 @@ int bits_for(int64_t x) {  // bits needed to represent values in [0, x)
 }
 
 struct SortLayout {
-  int64_t n_vk, scan_words, tiles_cap;
-  size_t off_scan, off_total, off_meff, off_keys_alt, off_vals_alt, off_status, off_ghist, off_gbase, off_counter, bytes;
+  int64_t n_vk, scan_words, blocks_vk, blocks_inst, blocks_max;
+  size_t off_scan, off_total, off_meff, off_dk0, off_dv0, off_dk1, off_dv1, off_keys_alt, off_vals_alt, off_status,
+      off_ghist, off_gbase, off_counter, bytes;
 };
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -429,19 +462,39 @@ SortLayout sort_layout(int64_t n, int32_t n_views, int64_t capacity) {
   SortLayout L{};
   L.n_vk = n * (int64_t)n_views;
   L.scan_words = scan_ws_words(L.n_vk > 0 ? L.n_vk : 1);
-  L.tiles_cap = ceil_div(capacity > 0 ? capacity : 1, kOsTile);
+  L.blocks_vk = ceil_div(L.n_vk > 0 ? L.n_vk : 1, kOsTile);
+  L.blocks_inst = ceil_div(capacity > 0 ? capacity : 1, kOsTile);
+  L.blocks_max = L.blocks_vk > L.blocks_inst ? L.blocks_vk : L.blocks_inst;
+  const size_t vk_words = sizeof(uint32_t) * (size_t)L.n_vk;
   size_t o = 0;
   L.off_scan = o; o = align_up(o + sizeof(uint64_t) * L.scan_words);
   L.off_total = o; o = align_up(o + 2 * sizeof(uint64_t));
   L.off_meff = o; o = align_up(o + sizeof(uint64_t));
-  L.off_keys_alt = o; o = align_up(o + sizeof(uint64_t) * (size_t)capacity);
+  L.off_dk0 = o; o = align_up(o + vk_words);
+  L.off_dv0 = o; o = align_up(o + vk_words);
+  L.off_dk1 = o; o = align_up(o + vk_words);
+  L.off_dv1 = o; o = align_up(o + vk_words);
+  L.off_keys_alt = o; o = align_up(o + sizeof(uint32_t) * (size_t)capacity);
   L.off_vals_alt = o; o = align_up(o + sizeof(uint32_t) * (size_t)capacity);
-  L.off_status = o; o = align_up(o + sizeof(unsigned long long) * 256 * (size_t)L.tiles_cap);
+  L.off_status = o; o = align_up(o + sizeof(unsigned long long) * 256 * (size_t)L.blocks_max);
   L.off_ghist = o; o = align_up(o + sizeof(uint32_t) * 256 * kMaxPasses);
   L.off_gbase = o; o = align_up(o + sizeof(uint32_t) * 256 * kMaxPasses);
   L.off_counter = o; o = align_up(o + sizeof(uint32_t) * kMaxPasses);
   L.bytes = o;
   return L;
+}
+
+// One onesweep pass over m items (count in device memory at m_dev, or m_host).
+cudaError_t onesweep_pass(const uint32_t* k_in, const uint32_t* v_in, const uint64_t* m_dev, int64_t m_host,
+                          int64_t blocks, int shift, const uint32_t* gbase, uint32_t* counter,
+                          unsigned long long* status, uint32_t* k_out, uint32_t* v_out, potr_device_status* st,
+                          cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(unsigned long long) * 256 * (size_t)blocks, s);
+  if (e != cudaSuccess) return e;
+  onesweep_kernel<<<(unsigned)blocks, kOsThreads, onesweep_smem_bytes(), s>>>(k_in, v_in, m_dev, m_host, shift, gbase,
+                                                                            counter, status, k_out, v_out, st);
+  note_launches(1);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -454,16 +507,27 @@ extern "C" size_t potr_bin_sort_workspace_size(int64_t n, int32_t n_views, int64
   return potr::sort_layout(n, n_views, instance_capacity).bytes;
 }
 
+// Binning in four steps, every one integer work and bit-exact:
+//   1. exclusive scan of the kept-tile counts in vk order -> offsets (emission slots of the
+//      vk-order definition, kept in record word 7) and the instance total;
+//   2. a stable LSD radix sort (4 x 8-bit passes) of the vk by depth bits: ties keep vk order;
+//   3. emission in that depth order (slots from a second scan of the counts, in depth order),
+//      key = global tile, value = vk;
+//   4. a stable LSD radix sort of the instances by tile (8-bit passes over its significant
+//      bits).  Per tile the instances keep step 3's order, (depth bits, vk), which is the
+//      order of a stable sort of (tile, depth) keys emitted in vk order.
 extern "C" potr_status potr_bin_sort(const potr_views* views, const potr_frame* frame, const potr_raster_config* cfg,
-                                     int64_t n, int64_t instance_capacity, uint64_t* d_keys, uint32_t* d_vals,
+                                     int64_t n, int64_t instance_capacity, uint32_t* d_tiles, uint32_t* d_vals,
                                      uint32_t* d_tile_ranges, potr_device_status* d_status, void* d_ws, size_t ws_bytes,
                                      potr_stream_t stream) {
   using namespace potr;
-  if (!views || !frame || !cfg || !d_keys || !d_vals || !d_tile_ranges || !d_ws) return POTR_ERR_INVALID_ARGUMENT;
+  if (!views || !frame || !cfg || !d_tiles || !d_vals || !d_tile_ranges || !d_ws) return POTR_ERR_INVALID_ARGUMENT;
   if (n <= 0 || frame->n_views < 1 || frame->total_tiles <= 0 || !frame->info) return POTR_ERR_INVALID_ARGUMENT;
   if (instance_capacity <= 0 || instance_capacity > (int64_t)0xffffffffll) return POTR_ERR_INVALID_ARGUMENT;
   if (!views->touched || !views->offsets || !views->rect || !views->depth || !views->raster || !views->n_instances)
     return POTR_ERR_INVALID_ARGUMENT;
+  if (frame->total_tiles > (int64_t)0xffffffffll || n * (int64_t)frame->n_views >= (int64_t)0xffffffffll)
+    return POTR_ERR_UNSUPPORTED;
   const SortLayout L = sort_layout(n, frame->n_views, instance_capacity);
   if (ws_bytes < L.bytes) return POTR_ERR_INVALID_ARGUMENT;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -471,54 +535,81 @@ extern "C" potr_status potr_bin_sort(const potr_views* views, const potr_frame* 
   uint64_t* scan_ws = reinterpret_cast<uint64_t*>(ws + L.off_scan);
   uint64_t* total = reinterpret_cast<uint64_t*>(ws + L.off_total);
   uint64_t* m_eff = reinterpret_cast<uint64_t*>(ws + L.off_meff);
-  uint64_t* keys_alt = reinterpret_cast<uint64_t*>(ws + L.off_keys_alt);
+  uint32_t* dk0 = reinterpret_cast<uint32_t*>(ws + L.off_dk0);
+  uint32_t* dv0 = reinterpret_cast<uint32_t*>(ws + L.off_dv0);
+  uint32_t* dk1 = reinterpret_cast<uint32_t*>(ws + L.off_dk1);
+  uint32_t* dv1 = reinterpret_cast<uint32_t*>(ws + L.off_dv1);
+  uint32_t* keys_alt = reinterpret_cast<uint32_t*>(ws + L.off_keys_alt);
   uint32_t* vals_alt = reinterpret_cast<uint32_t*>(ws + L.off_vals_alt);
   unsigned long long* status = reinterpret_cast<unsigned long long*>(ws + L.off_status);
   uint32_t* ghist = reinterpret_cast<uint32_t*>(ws + L.off_ghist);
   uint32_t* gbase = reinterpret_cast<uint32_t*>(ws + L.off_gbase);
   uint32_t* counter = reinterpret_cast<uint32_t*>(ws + L.off_counter);
+  const int tile_passes = (bits_for(frame->total_tiles) + 7) / 8;
+  if (4 + tile_passes > kMaxPasses) return POTR_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)onesweep_smem_bytes()) !=
+      cudaSuccess)
+    return POTR_ERR_CUDA;
 
+  // 1. slots in vk order, instance total, capacity check
   if (scan_exclusive<uint32_t, uint32_t>(views->touched, views->offsets, L.n_vk, total, scan_ws, s) != cudaSuccess)
     return POTR_ERR_CUDA;
   count_check_kernel<<<1, 1, 0, s>>>(total, instance_capacity, views->n_instances, m_eff, d_status);
   POTR_CHECK_LAUNCH();
-
-  const int key_bits = 32 + bits_for(frame->total_tiles);
-  const int passes = (key_bits + 7) / 8;
-  // emit into the buffer that makes the last pass land in d_keys / d_vals
-  uint64_t* k_src = (passes & 1) ? keys_alt : d_keys;
-  uint32_t* v_src = (passes & 1) ? vals_alt : d_vals;
-  uint64_t* k_dst = (passes & 1) ? d_keys : keys_alt;
-  uint32_t* v_dst = (passes & 1) ? d_vals : vals_alt;
-  if (passes > kMaxPasses) return POTR_ERR_UNSUPPORTED;
   if (cudaMemsetAsync(ghist, 0, sizeof(uint32_t) * 256 * kMaxPasses, s) != cudaSuccess) return POTR_ERR_CUDA;
   if (cudaMemsetAsync(counter, 0, sizeof(uint32_t) * kMaxPasses, s) != cudaSuccess) return POTR_ERR_CUDA;
+
+  // 2. vk by depth: keys dk0 (values implicit) -> dk1/dv1 -> dk0/dv0 -> dk1/dv1 -> dk0/dv0
+  {
+    const int64_t g = ceil_div(L.n_vk, 256);
+    depth_key_kernel<<<(unsigned)(g < 152 * 8 ? g : 152 * 8), 256, 0, s>>>(
+        views->touched, views->offsets, views->depth, L.n_vk, reinterpret_cast<float4*>(views->raster), dk0, ghist);
+    POTR_CHECK_LAUNCH();
+    digit_base_kernel<<<1, 256, 0, s>>>(ghist, 4, gbase);
+    POTR_CHECK_LAUNCH();
+  }
+  uint32_t *ka = dk0, *va = nullptr, *kb = dk1, *vb = dv1;
+  for (int p = 0; p < 4; ++p) {
+    if (onesweep_pass(ka, va, nullptr, L.n_vk, L.blocks_vk, 8 * p, gbase + 256 * p, counter + p, status, kb, vb,
+                      d_status, s) != cudaSuccess)
+      return POTR_ERR_CUDA;
+    uint32_t* t = ka; ka = kb; kb = t;
+    va = vb;
+    vb = (vb == dv1) ? dv0 : dv1;
+  }
+  const uint32_t* order = va;  // dv0: vk in (depth bits, vk) order
+
+  // 3. slots in depth order (dv1 is free now), emission
+  if (scan_exclusive<uint32_t, uint32_t>(views->touched, dv1, L.n_vk, total + 1, scan_ws, s, order) != cudaSuccess)
+    return POTR_ERR_CUDA;
+  // emit where the last tile pass lands in d_tiles / d_vals
+  uint32_t* k_src = (tile_passes & 1) ? keys_alt : d_tiles;
+  uint32_t* v_src = (tile_passes & 1) ? vals_alt : d_vals;
+  uint32_t* k_dst = (tile_passes & 1) ? d_tiles : keys_alt;
+  uint32_t* v_dst = (tile_passes & 1) ? d_vals : vals_alt;
   {
     const int64_t g = ceil_div(L.n_vk, 256);
     emit_kernel<<<(unsigned)(g < 152 * 16 ? g : 152 * 16), 256, 0, s>>>(
-        views->touched, views->offsets, reinterpret_cast<const uint2*>(views->rect), views->depth, frame->info, n, L.n_vk,
-        m_eff, reinterpret_cast<float4*>(views->raster), k_src, v_src, passes, ghist);
+        order, dv1, views->touched, reinterpret_cast<const uint2*>(views->rect), frame->info, n, L.n_vk, m_eff,
+        reinterpret_cast<const float4*>(views->raster), k_src, v_src, tile_passes, ghist + 256 * 4);
     POTR_CHECK_LAUNCH();
-    digit_base_kernel<<<1, 256, 0, s>>>(ghist, passes, gbase);
+    digit_base_kernel<<<1, 256, 0, s>>>(ghist + 256 * 4, tile_passes, gbase + 256 * 4);
     POTR_CHECK_LAUNCH();
   }
-  const size_t os_smem = onesweep_smem_bytes();
-  if (cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem) != cudaSuccess)
-    return POTR_ERR_CUDA;
-  for (int p = 0; p < passes; ++p) {
-    if (cudaMemsetAsync(status, 0, sizeof(unsigned long long) * 256 * (size_t)L.tiles_cap, s) != cudaSuccess)
+
+  // 4. instances by tile
+  for (int p = 0; p < tile_passes; ++p) {
+    if (onesweep_pass(k_src, v_src, m_eff, 0, L.blocks_inst, 8 * p, gbase + 256 * (4 + p), counter + 4 + p, status,
+                      k_dst, v_dst, d_status, s) != cudaSuccess)
       return POTR_ERR_CUDA;
-    onesweep_kernel<<<(unsigned)L.tiles_cap, kOsThreads, os_smem, s>>>(k_src, v_src, m_eff, 8 * p, gbase + 256 * p,
-                                                                        counter + p, status, k_dst, v_dst, d_status);
-    POTR_CHECK_LAUNCH();
-    uint64_t* tk = k_src; k_src = k_dst; k_dst = tk;
+    uint32_t* tk = k_src; k_src = k_dst; k_dst = tk;
     uint32_t* tv = v_src; v_src = v_dst; v_dst = tv;
   }
   if (cudaMemsetAsync(d_tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)frame->total_tiles, s) != cudaSuccess)
     return POTR_ERR_CUDA;
   {
     const int64_t g = ceil_div(instance_capacity, 256);
-    tile_ranges_kernel<<<(unsigned)(g < 152 * 64 ? g : 152 * 64), 256, 0, s>>>(d_keys, m_eff, frame->total_tiles,
+    tile_ranges_kernel<<<(unsigned)(g < 152 * 64 ? g : 152 * 64), 256, 0, s>>>(d_tiles, m_eff, frame->total_tiles,
                                                                                d_tile_ranges);
     POTR_CHECK_LAUNCH();
   }

@@ -50,7 +50,7 @@ potr_status scratch_for_current_device(void** out) {
 
 extern "C" potr_status potr_bin_sort_static(const potr_views* views, const potr_frame* frame,
                                             const potr_raster_config* cfg, int64_t n, int64_t instance_capacity,
-                                            uint64_t* d_keys, uint32_t* d_vals, uint32_t* d_tile_ranges,
+                                            uint32_t* d_tiles, uint32_t* d_vals, uint32_t* d_tile_ranges,
                                             potr_device_status* d_status, potr_stream_t stream) {
   if (!views || !frame || !cfg || n <= 0 || frame->n_views < 1 || instance_capacity <= 0)
     return POTR_ERR_INVALID_ARGUMENT;
@@ -62,6 +62,6 @@ extern "C" potr_status potr_bin_sort_static(const potr_views* views, const potr_
   void* scratch = nullptr;
   const potr_status st = scratch_for_current_device(&scratch);
   if (st != POTR_OK) return st;
-  return potr_bin_sort(views, frame, cfg, n, instance_capacity, d_keys, d_vals, d_tile_ranges, d_status, scratch,
+  return potr_bin_sort(views, frame, cfg, n, instance_capacity, d_tiles, d_vals, d_tile_ranges, d_status, scratch,
                        kStaticScratchBytes, stream);
 }

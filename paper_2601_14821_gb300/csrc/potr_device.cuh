@@ -14,7 +14,8 @@
 namespace potr {
 
 constexpr int kTilePixels = 256;  // tile_w * tile_h
-constexpr int kRecFloats = 12;    // raster record: 3 x float4
+constexpr int kRec = 4;           // raster record: 4 x float4 (64 bytes) per (view, splat)
+constexpr int kCullMaxTiles = 64;  // rectangles with more tiles keep every tile
 constexpr float kLog2e = 1.44269504088896340736f;
 
 // ---------------------------------------------------------------------------------------
@@ -70,6 +71,70 @@ __device__ __forceinline__ float pair_alpha(float o, float p, float alpha_max) {
 
 // Transmittance after compositing a splat of opacity a: T (1 - a) as fma(-a, T, T).
 __device__ __forceinline__ float trans_next(float a, float T) { return __fmaf_rn(-a, T, T); }
+
+// Binning tile test: can some pixel centre of tile (tx, ty) reach alpha >= alpha_min?  The
+// exponent log2 G = A u^2 + B u v + C v^2 (u = x - mx, v = y - my) is maximised over the
+// rectangle of the tile's pixel centres: on each edge it is a concave parabola, largest at
+// its vertex clamped to the edge, and the splat centre counts when it lies inside.  The tile
+// is kept when o * exp2r(max + margin) >= alpha_min, the margin 1e-5 |terms| + 1e-4 covering
+// the binary32 rounding of this maximum and of any pixel's own exponent and the error of
+// exp2r, so every pixel that takes the splat lies in a kept tile.  Fixed operation order.
+__device__ __forceinline__ float tile_edge_exponent(float A, float B, float C, float u, float v) {
+  return __fadd_rn(__fmul_rn(__fadd_rn(__fmul_rn(A, u), __fmul_rn(B, v)), u), __fmul_rn(__fmul_rn(C, v), v));
+}
+
+// The per-splat part: the parabola vertices along the two edge directions, u = ku v and
+// v = kv u (only meaningful when A < 0 and C < 0; otherwise every tile is kept).
+__device__ __forceinline__ float tile_ku(float A, float B) { return __fdiv_rn(-B, __fmul_rn(2.0f, A)); }
+
+// The per-tile part, for a splat with A < 0 and C < 0 and its ku = tile_ku(A, B), kv = tile_ku(C, B).
+__device__ __forceinline__ bool tile_hit_concave(float mx, float my, float A, float B, float C, float o, float ku,
+                                                 float kv, int tx, int ty, int tile_w, int tile_h, float alpha_min) {
+  const float X0 = __fadd_rn((float)(tx * tile_w), 0.5f), X1 = __fadd_rn(X0, (float)(tile_w - 1));
+  const float Y0 = __fadd_rn((float)(ty * tile_h), 0.5f), Y1 = __fadd_rn(Y0, (float)(tile_h - 1));
+  const float ux0 = __fsub_rn(X0, mx), ux1 = __fsub_rn(X1, mx);
+  const float vy0 = __fsub_rn(Y0, my), vy1 = __fsub_rn(Y1, my);
+  const float u0 = fminf(fmaxf(__fmul_rn(ku, vy0), ux0), ux1);
+  const float u1 = fminf(fmaxf(__fmul_rn(ku, vy1), ux0), ux1);
+  const float v0 = fminf(fmaxf(__fmul_rn(kv, ux0), vy0), vy1);
+  const float v1 = fminf(fmaxf(__fmul_rn(kv, ux1), vy0), vy1);
+  float pmax = fmaxf(fmaxf(tile_edge_exponent(A, B, C, u0, vy0), tile_edge_exponent(A, B, C, u1, vy1)),
+                     fmaxf(tile_edge_exponent(A, B, C, ux0, v0), tile_edge_exponent(A, B, C, ux1, v1)));
+  if (ux0 <= 0.0f && ux1 >= 0.0f && vy0 <= 0.0f && vy1 >= 0.0f) pmax = fmaxf(pmax, 0.0f);
+  const float um = fmaxf(fabsf(ux0), fabsf(ux1)), vm = fmaxf(fabsf(vy0), fabsf(vy1));
+  const float mag = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(fabsf(A), um), um), __fmul_rn(__fmul_rn(fabsf(B), um), vm)),
+                              __fmul_rn(__fmul_rn(fabsf(C), vm), vm));
+  const float margin = __fadd_rn(__fmul_rn(1e-5f, mag), 1e-4f);
+  return __fmul_rn(o, exp2r(__fadd_rn(pmax, margin))) >= alpha_min;
+}
+
+__device__ __forceinline__ bool tile_hit(float mx, float my, float A, float B, float C, float o, int tx, int ty,
+                                         int tile_w, int tile_h, float alpha_min) {
+  if (!(A < 0.0f && C < 0.0f)) return true;
+  return tile_hit_concave(mx, my, A, B, C, o, tile_ku(A, B), tile_ku(C, B), tx, ty, tile_w, tile_h, alpha_min);
+}
+
+// Position of the r-th set bit (r counted from 0) of a 64-bit word that has more than r.
+__device__ __forceinline__ uint32_t select_bit64(uint64_t m, uint32_t r) {
+  uint32_t pos = 0;
+  uint32_t w = (uint32_t)m;
+  uint32_t c = (uint32_t)__popc(w);
+  if (r >= c) {
+    r -= c;
+    w = (uint32_t)(m >> 32);
+    pos = 32;
+  }
+#pragma unroll
+  for (int half = 16; half >= 1; half >>= 1) {
+    c = (uint32_t)__popc(w & ((1u << half) - 1u));
+    if (r >= c) {
+      r -= c;
+      w >>= half;
+      pos += half;
+    }
+  }
+  return pos;
+}
 
 // Rectangle packing of the raster record word 11: x0 (11 bits) | y0 (11 bits) | w (10 bits).
 __device__ __forceinline__ uint32_t pack_rect_word(uint32_t x0, uint32_t y0, uint32_t w) {

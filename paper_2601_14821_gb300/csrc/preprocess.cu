@@ -190,13 +190,94 @@ __global__ void __launch_bounds__(256) project_kernel(const float* __restrict__ 
         rgb[ch] = fmaxf(acc + 0.5f, 0.0f);
       }
       const uint32_t rw = pack_rect_word((uint32_t)x0, (uint32_t)y0, (uint32_t)(x1 - x0));
-      float4* rec = raster + vk * 3;
+      float4* rec = raster + vk * kRec;
       rec[0] = make_float4(mx, my, __fmul_rn(ca, kA), __fmul_rn(cb, -kLog2e));
       rec[1] = make_float4(__fmul_rn(cc, kA), o, pthr, 0.0f);
       rec[2] = make_float4(rgb[0], rgb[1], rgb[2], __uint_as_float(rw));
       depth_out[vk] = t[2];
       rect_out[vk] = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
-      touched_out[vk] = (uint32_t)((x1 - x0) * (y1 - y0));
+      touched_out[vk] = (uint32_t)((x1 - x0) * (y1 - y0));  // candidates; tile_mask_kernel keeps some
+    }
+  }
+}
+
+// Kept tiles of every (view, splat) rectangle of at most kCullMaxTiles tiles.  One warp per 32
+// consecutive vk: their candidate tiles (rectangle cells, row-major) are dealt to the lanes 32
+// at a time, each lane runs tile_hit for one candidate (owner found by a shuffle search over
+// the warp's exclusive candidate counts), and every owner collects its bits from the ballot.
+// Writes record word 12..14 (mask, all-kept flag) and touched = number of kept tiles.
+__global__ void __launch_bounds__(256) tile_mask_kernel(const uint2* __restrict__ rect, int64_t n_vk,
+                                                        potr_raster_config cfg, float4* __restrict__ raster,
+                                                        uint32_t* __restrict__ touched) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps_total = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t wv = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wv * 32 < n_vk; wv += warps_total) {
+    const int64_t vk = wv * 32 + lane;
+    uint32_t area = 0, cand = 0, x0 = 0, y0 = 0, w = 1;
+    float mx = 0.0f, my = 0.0f, qa = 0.0f, qb = 0.0f, qc = 0.0f, o = 0.0f, ku = 0.0f, kv = 0.0f;
+    bool concave = false;
+    if (vk < n_vk) {
+      area = touched[vk];
+      if (area) {
+        const uint2 r = rect[vk];
+        x0 = r.x & 0xffffu;
+        y0 = r.x >> 16;
+        w = (r.y & 0xffffu) - x0;
+        if (area <= (uint32_t)kCullMaxTiles) {
+          cand = area;
+          const float4 r0 = raster[vk * kRec], r1 = raster[vk * kRec + 1];
+          mx = r0.x; my = r0.y; qa = r0.z; qb = r0.w; qc = r1.x; o = r1.y;
+          concave = qa < 0.0f && qc < 0.0f;
+          if (concave) {
+            ku = tile_ku(qa, qb);
+            kv = tile_ku(qc, qb);
+          }
+        }
+      }
+    }
+    uint32_t incl = cand;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, s);
+      if (lane >= s) incl += y;
+    }
+    const uint32_t excl = incl - cand;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    uint64_t mask = 0;
+    for (uint32_t e0 = 0; e0 < total; e0 += 32) {
+      const uint32_t e = e0 + lane;
+      uint32_t owner = 0;
+#pragma unroll
+      for (int b = 16; b >= 1; b >>= 1) {
+        const uint32_t c = owner + b;
+        const uint32_t ce = __shfl_sync(0xffffffffu, excl, c & 31);
+        if (c < 32 && ce <= e) owner = c;
+      }
+      const uint32_t li = e - __shfl_sync(0xffffffffu, excl, owner);
+      const uint32_t ow = __shfl_sync(0xffffffffu, w, owner);
+      const int tx = (int)(__shfl_sync(0xffffffffu, x0, owner) + li % ow);
+      const int ty = (int)(__shfl_sync(0xffffffffu, y0, owner) + li / ow);
+      const float omx = __shfl_sync(0xffffffffu, mx, owner), omy = __shfl_sync(0xffffffffu, my, owner);
+      const float oa = __shfl_sync(0xffffffffu, qa, owner), ob = __shfl_sync(0xffffffffu, qb, owner);
+      const float oc = __shfl_sync(0xffffffffu, qc, owner), oo = __shfl_sync(0xffffffffu, o, owner);
+      const float oku = __shfl_sync(0xffffffffu, ku, owner), okv = __shfl_sync(0xffffffffu, kv, owner);
+      const bool oconc = __shfl_sync(0xffffffffu, concave ? 1u : 0u, owner) != 0u;
+      const bool hit = e < total && (!oconc || tile_hit_concave(omx, omy, oa, ob, oc, oo, oku, okv, tx, ty, cfg.tile_w,
+                                                                cfg.tile_h, cfg.alpha_min));
+      const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+      // this lane's candidates [excl, excl + cand) overlapping [e0, e0 + 32)
+      const uint32_t lo = max(excl, e0), hi = min(excl + cand, e0 + 32u);
+      if (lo < hi) {
+        const uint32_t len = hi - lo;
+        const uint32_t bits = (bal >> (lo - e0)) & (len == 32u ? 0xffffffffu : ((1u << len) - 1u));
+        mask |= (uint64_t)bits << (lo - excl);
+      }
+    }
+    if (vk < n_vk && area) {
+      const bool all = area > (uint32_t)kCullMaxTiles;
+      raster[vk * kRec + 3] = make_float4(__uint_as_float((uint32_t)mask), __uint_as_float((uint32_t)(mask >> 32)),
+                                          __uint_as_float(all ? 1u : 0u), 0.0f);
+      touched[vk] = all ? area : (uint32_t)__popcll(mask);
     }
   }
 }
@@ -255,6 +336,10 @@ extern "C" potr_status potr_preprocess(const potr_scene* scene, const potr_frame
   potr::project_kernel<<<potr::grid_for(n, 256, 152 * 16), 256, 0, s>>>(
       scene->means, views->cov3d, views->opacity, scene->sh, n, frame->cams, frame->info, frame->n_views, *cfg,
       reinterpret_cast<float4*>(views->raster), views->depth, reinterpret_cast<uint2*>(views->rect), views->touched);
+  POTR_CHECK_LAUNCH();
+  const int64_t n_vk = n * frame->n_views;
+  potr::tile_mask_kernel<<<potr::grid_for(n_vk, 256, 152 * 16), 256, 0, s>>>(
+      reinterpret_cast<const uint2*>(views->rect), n_vk, *cfg, reinterpret_cast<float4*>(views->raster), views->touched);
   POTR_CHECK_LAUNCH();
   return POTR_OK;
 }

@@ -19,16 +19,17 @@ __device__ __forceinline__ void cp_async_commit_wait() {
   asm volatile("cp.async.wait_group 0;\n" ::);
 }
 
-// Gather the raster records of list entries [first, first + cnt) into smem[0 .. cnt).
+// Gather the first three float4 of the raster records of list entries [first, first + cnt)
+// into smem (record stride kRec); the fourth (the tile mask) is not needed when compositing.
 template <int BATCH>
 __device__ __forceinline__ void stage_batch(float4* smem, const float4* __restrict__ raster,
                                             const uint32_t* __restrict__ vals, uint32_t first, int cnt) {
   for (int j = threadIdx.x; j < cnt; j += kThreads) {
     const uint32_t vk = vals[first + j];
-    const float4* src = raster + (size_t)vk * 3;
-    cp_async16(smem + 3 * j + 0, src + 0);
-    cp_async16(smem + 3 * j + 1, src + 1);
-    cp_async16(smem + 3 * j + 2, src + 2);
+    const float4* src = raster + (size_t)vk * kRec;
+    cp_async16(smem + kRec * j + 0, src + 0);
+    cp_async16(smem + kRec * j + 1, src + 1);
+    cp_async16(smem + kRec * j + 2, src + 2);
   }
   cp_async_commit_wait();
 }
@@ -36,6 +37,7 @@ __device__ __forceinline__ void stage_batch(float4* smem, const float4* __restri
 // Double-buffered batch staging: the gathers of one batch are in flight (cp.async, one commit
 // group per batch) while the CTA works on the other buffer, and every thread already holds the
 // list values (vk) of the batch after that in registers, so issuing never waits on a load.
+// Whole records (all kRec float4, tile mask included) are copied.
 template <int BATCH>
 struct BatchStager {
   static constexpr int kPer = (BATCH + kThreads - 1) / kThreads;
@@ -54,10 +56,11 @@ struct BatchStager {
     for (int r = 0; r < kPer; ++r) {
       const int j = threadIdx.x + r * kThreads;
       if (j < loaded) {
-        const float4* src = raster + (size_t)vk[r] * 3;
-        cp_async16(buf + 3 * j + 0, src + 0);
-        cp_async16(buf + 3 * j + 1, src + 1);
-        cp_async16(buf + 3 * j + 2, src + 2);
+        const float4* src = raster + (size_t)vk[r] * kRec;
+        cp_async16(buf + kRec * j + 0, src + 0);
+        cp_async16(buf + kRec * j + 1, src + 1);
+        cp_async16(buf + kRec * j + 2, src + 2);
+        cp_async16(buf + kRec * j + 3, src + 3);
       }
     }
     asm volatile("cp.async.commit_group;\n" ::);
@@ -135,7 +138,7 @@ __device__ __forceinline__ void compute_masks(const float4* buf, uint8_t* wmask,
 #pragma unroll
   for (int r = 0; r < BatchStager<BATCH>::kPer; ++r) {
     const int j = threadIdx.x + r * kThreads;
-    if (j < cnt) wmask[j] = (uint8_t)warp_mask(buf[3 * j], buf[3 * j + 1], c, cfg);
+    if (j < cnt) wmask[j] = (uint8_t)warp_mask(buf[kRec * j], buf[kRec * j + 1], c, cfg);
   }
 }
 
@@ -145,7 +148,7 @@ __device__ __forceinline__ void stage_batch_masked(float4* smem, uint8_t* wmask,
                                                    const uint32_t* __restrict__ vals, uint32_t first, int cnt,
                                                    const TileCtx& c, const potr_raster_config& cfg) {
   stage_batch<BATCH>(smem, raster, vals, first, cnt);
-  for (int j = threadIdx.x; j < cnt; j += kThreads) wmask[j] = (uint8_t)warp_mask(smem[3 * j], smem[3 * j + 1], c, cfg);
+  for (int j = threadIdx.x; j < cnt; j += kThreads) wmask[j] = (uint8_t)warp_mask(smem[kRec * j], smem[kRec * j + 1], c, cfg);
 }
 
 // Forward walk of the tile list (Section 3, Eqs. 2-4).  Returns colour, final T and n_last.
@@ -172,8 +175,8 @@ __device__ __forceinline__ void forward_walk(float4* smem, uint8_t* wmask, const
         const int j = g + __ffs(m) - 1;
         m &= m - 1;
         if (done) continue;
-        const float4 r0 = smem[3 * j];
-        const float4 r1 = smem[3 * j + 1];
+        const float4 r0 = smem[kRec * j];
+        const float4 r1 = smem[kRec * j + 1];
         const float p = pair_exponent(r0.z, r0.w, r1.x, __fsub_rn(c.fx, r0.x), __fsub_rn(c.fy, r0.y));
         if (p < r1.z) continue;  // alpha < alpha_min certainly (prefilter with margin)
         const float a = pair_alpha(r1.y, p, cfg.alpha_max);
@@ -183,7 +186,7 @@ __device__ __forceinline__ void forward_walk(float4* smem, uint8_t* wmask, const
           done = true;
           continue;
         }
-        const float4 r2 = smem[3 * j + 2];
+        const float4 r2 = smem[kRec * j + 2];
         const float w = a * T;
         C[0] = fmaf(w, r2.x, C[0]);
         C[1] = fmaf(w, r2.y, C[1]);
@@ -195,12 +198,18 @@ __device__ __forceinline__ void forward_walk(float4* smem, uint8_t* wmask, const
   }
 }
 
-// Emission slot of the instance of record (r1, r2) that lies in tile (tx, ty).
-__device__ __forceinline__ uint32_t emission_slot(const float4& r1, const float4& r2, int tx, int ty) {
-  const uint32_t off = __float_as_uint(r1.w);
-  const uint32_t rw = __float_as_uint(r2.w);
+// Emission slot of the instance of record r (kRec float4) that lies in tile (tx, ty): the
+// splat's first slot plus the number of its kept tiles before (tx, ty) in row-major order of
+// its rectangle (record word 15 flags a rectangle that keeps every tile).
+__device__ __forceinline__ uint32_t emission_slot(const float4* r, int tx, int ty) {
+  const uint32_t off = __float_as_uint(r[1].w);
+  const uint32_t rw = __float_as_uint(r[2].w);
   const uint32_t x0 = rw & 0x7ffu, y0 = (rw >> 11) & 0x7ffu, w = rw >> 22;
-  return off + ((uint32_t)ty - y0) * w + ((uint32_t)tx - x0);
+  const uint32_t pos = ((uint32_t)ty - y0) * w + ((uint32_t)tx - x0);
+  const float4 m = r[3];
+  if (__float_as_uint(m.z)) return off + pos;
+  const uint64_t mask = ((uint64_t)__float_as_uint(m.y) << 32) | __float_as_uint(m.x);
+  return off + (uint32_t)__popcll(mask & ((1ull << pos) - 1ull));
 }
 
 // Compensated (Kahan) binary32 summation: s + (-c) carries the sum to about binary64 accuracy

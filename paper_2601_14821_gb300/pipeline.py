@@ -86,7 +86,7 @@ class RemovalEffectFrame:
         """(Re)take every pooled buffer at the current sizes and rebuild the C views."""
         vn = self.n_views * self.n
         i32, P = torch.int32, self.pool
-        self.raster = P.get("raster", vn * 12, torch.float32)
+        self.raster = P.get("raster", vn * 16, torch.float32)
         self.depth = P.get("depth", vn, torch.float32)
         self.rect = P.get("rect", 2 * vn, i32)
         self.touched = P.get("touched", vn, i32)
@@ -102,7 +102,7 @@ class RemovalEffectFrame:
     def _alloc(self, capacity: int):
         P = self.pool
         self.capacity = int(capacity)
-        self.keys = P.get("keys", self.capacity, torch.int64)
+        self.tiles = P.get("tiles", self.capacity, torch.int32)  # sorted instances' global tiles
         self.vals = P.get("vals", self.capacity, torch.int32)
         self.ws = P.get("sort_ws", B.potr_bin_sort_workspace_size(self.n, self.n_views, self.total_tiles,
                                                                    self.capacity), torch.uint8)
@@ -134,7 +134,7 @@ class RemovalEffectFrame:
     def bin_sort(self, stream=None):
         """Binning + sort, then (with scheduling on) the longest-list-first tile order."""
         self.status.zero_()
-        B.potr_bin_sort(self.views, self.frame, self.cfg, self.n, self.capacity, self.keys, self.vals, self.ranges,
+        B.potr_bin_sort(self.views, self.frame, self.cfg, self.n, self.capacity, self.tiles, self.vals, self.ranges,
                         self.status, self.ws, stream)
         if self.schedule:
             B.potr_tile_schedule(self.frame, self.ranges, self.order, self.sched_ws, stream)

@@ -6,7 +6,8 @@ import numpy as np
 import oracle
 import synth
 
-RASTER_FIELDS = ("mx", "my", "A", "B", "C", "o", "pthr", "offset", "r", "g", "b", "rectw")
+RASTER_FIELDS = ("mx", "my", "A", "B", "C", "o", "pthr", "offset", "r", "g", "b", "rectw", "mask_lo", "mask_hi",
+                 "all_tiles", "pad")
 
 
 def oracle_cfg(cfg: dict):
@@ -28,10 +29,11 @@ def build_frame(scene, cams, **cfg):
 
 
 def unpack_raster(fr) -> dict:
-    r = fr.raster.cpu().numpy().reshape(-1, 12)
+    r = fr.raster.cpu().numpy().reshape(-1, 16)
     out = {k: r[:, i] for i, k in enumerate(RASTER_FIELDS)}
-    out["offset"] = r[:, 7].view(np.uint32)
-    out["rectw"] = r[:, 11].view(np.uint32)
+    for k in ("offset", "rectw", "mask_lo", "mask_hi", "all_tiles"):
+        out[k] = r[:, RASTER_FIELDS.index(k)].view(np.uint32)
+    out["mask"] = out["mask_lo"].astype(np.uint64) | (out["mask_hi"].astype(np.uint64) << np.uint64(32))
     return out
 
 

@@ -55,4 +55,4 @@ def test_host_only_layout_and_status_strings(libpotr):
     with pytest.raises(B.PotrError):
         B.potr_view_layout(synth.cameras_to_array(cams), B.make_config(tile_w=16, tile_h=8))
     ws = B.potr_bin_sort_workspace_size(1000, 2, tt, 100_000)
-    assert ws >= 12 * 100_000
+    assert ws >= 8 * 100_000 + 16 * 2000

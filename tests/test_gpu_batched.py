@@ -142,9 +142,9 @@ def test_batched_workload_sampled_views_and_tiles():
         start = int(touched[:lv].astype(np.int64).sum())
         tb = int(fr.info_np[lv]["tile_base"])
         ok, ov, oe, orng = oracle.bin_sort(pv, cam, ocfg, tile_base=tb, val_base=lv * n)
-        keys = fr.keys[start:start + ok.size].cpu().numpy().view(np.uint64)
+        tiles = fr.tiles[start:start + ok.size].cpu().numpy().view(np.uint32)
         vals = fr.vals[start:start + ok.size].cpu().numpy().view(np.uint32)
-        assert np.array_equal(keys, ok) and np.array_equal(vals, ov)
+        assert np.array_equal(tiles.astype(np.uint64), ok >> np.uint64(32)) and np.array_equal(vals, ov)
         lk, lvv, le, lr = oracle.bin_sort(pv, cam, ocfg)
         pick, mask = masks[v]
         d, i, idse, iimp = oracle.removal_effect(pv, lvv, lr, cam, ocfg, tg[v], tile_mask=mask, per_instance=True)

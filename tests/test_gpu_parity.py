@@ -112,6 +112,19 @@ def _check_preprocess(fr, scene, ovs):
         assert np.array_equal(rw >> 22, pv["rect"][2][vis] - pv["rect"][0][vis])
         for i, key in enumerate("rgb"):
             assert np.max(np.abs(g[key] - pv["rgb"][i][vis])) < 2e-6, key
+        # kept-tile mask: the oracle's binned (tile, splat) pairs, as rectangle bit positions
+        tx_n = int(fr.info_np[v]["tiles_x"])
+        k = (pv["vals"].astype(np.int64) - v * n)
+        t = (pv["keys"] >> np.uint64(32)).astype(np.int64) - pv["tile_base"]
+        w = (pv["rect"][2] - pv["rect"][0]).astype(np.int64)
+        area = w * (pv["rect"][3] - pv["rect"][1])
+        pos = (t // tx_n - pv["rect"][1][k]) * w[k] + (t % tx_n - pv["rect"][0][k])
+        small = area[k] <= oracle.CULL_MAX_TILES
+        want = np.zeros(n, np.uint64)
+        np.bitwise_or.at(want, k[small], np.left_shift(np.uint64(1), pos[small].astype(np.uint64)))
+        big = area > oracle.CULL_MAX_TILES
+        assert np.array_equal(g["all_tiles"], big[vis].astype(np.uint32))
+        assert np.array_equal(g["mask"][~big[vis]], want[vis][~big[vis]])
 
 
 def test_preprocess_bit_exact(tiny, tiny_run):
@@ -121,13 +134,13 @@ def test_preprocess_bit_exact(tiny, tiny_run):
 
 def _check_binning(fr, ovs):
     m = fr.instance_count()
-    keys = fr.keys[:m].cpu().numpy().view(np.uint64)
+    tiles = fr.tiles[:m].cpu().numpy().view(np.uint32)
     vals = fr.vals[:m].cpu().numpy().view(np.uint32)
     ranges = fr.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2)
     okeys = np.concatenate([pv["keys"] for pv in ovs])
     ovals = np.concatenate([pv["vals"] for pv in ovs])
     assert m == okeys.size
-    assert np.array_equal(keys, okeys)
+    assert np.array_equal(tiles.astype(np.uint64), okeys >> np.uint64(32))
     assert np.array_equal(vals, ovals)
     start = 0
     for pv in ovs:

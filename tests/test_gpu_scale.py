@@ -50,15 +50,15 @@ def big():
     res = frame_outputs(fr, pack_targets(fr, tg), images=False)
     r = unpack_raster(fr)
     m = fr.instance_count()
-    keys = fr.keys[:m].cpu().numpy().view(np.uint64)
+    tiles = fr.tiles[:m].cpu().numpy().view(np.uint32)
     vals = fr.vals[:m].cpu().numpy().view(np.uint32)
     touched = fr.touched.cpu().numpy().view(np.uint32)
     torch.cuda.synchronize()
-    return w, fr, tg, res, r, keys, vals, touched
+    return w, fr, tg, res, r, tiles, vals, touched
 
 
 def test_fullsize_preprocess_and_sort_views(big):
-    w, fr, tg, res, r, keys, vals, touched = big
+    w, fr, tg, res, r, tiles, vals, touched = big
     ocfg = oracle_cfg(CFG)
     act = oracle.activate(w.scene)
     n = w.scene.n
@@ -73,12 +73,12 @@ def test_fullsize_preprocess_and_sort_views(big):
         tb = int(fr.info_np[v]["tile_base"])
         ok, ov, oe, orng = oracle.bin_sort(pv, cam, ocfg, tile_base=tb, val_base=v * n)
         s0 = int(counts[:v].sum())
-        assert np.array_equal(keys[s0:s0 + ok.size], ok)
+        assert np.array_equal(tiles[s0:s0 + ok.size].astype(np.uint64), ok >> np.uint64(32))
         assert np.array_equal(vals[s0:s0 + ok.size], ov)
 
 
 def test_fullsize_sampled_tiles(big):
-    w, fr, tg, res, r, keys, vals, touched = big
+    w, fr, tg, res, r, tiles, vals, touched = big
     ocfg = oracle_cfg(CFG)
     act = oracle.activate(w.scene)
     n = w.scene.n

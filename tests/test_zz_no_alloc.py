@@ -27,9 +27,9 @@ def _frame(scene, cams):
     return fr
 
 
-def _sorted_outputs(fr, keys, vals, ranges):
+def _sorted_outputs(fr, tiles, vals, ranges):
     m = fr.instance_count()
-    return (keys[:m].cpu().numpy().view(np.uint64), vals[:m].cpu().numpy().view(np.uint32),
+    return (tiles[:m].cpu().numpy().view(np.uint32), vals[:m].cpu().numpy().view(np.uint32),
             ranges.cpu().numpy().view(np.uint32))
 
 
@@ -46,17 +46,17 @@ def test_static_scratch_sort_matches_workspace_sort_twice(which):
         scene = synth.uniform_cube_scene(5000, 77)
         cams = [synth.look_at_camera((0.0, 0.3, -3.0), 200, 150), synth.look_at_camera((2.5, -0.2, -1.5), 96, 160)]
     fr = _frame(scene, cams)
-    want = _sorted_outputs(fr, fr.keys, fr.vals, fr.ranges)
+    want = _sorted_outputs(fr, fr.tiles, fr.vals, fr.ranges)
     assert want[0].size > 1000
     for call in range(2):
-        keys = torch.full_like(fr.keys, -1)
+        tiles = torch.full_like(fr.tiles, -1)
         vals = torch.full_like(fr.vals, -1)
         ranges = torch.full_like(fr.ranges, -1)
         status = torch.zeros(2, dtype=torch.int64, device=fr.device)
-        B.potr_bin_sort_static(fr.views, fr.frame, fr.cfg, fr.n, fr.capacity, keys, vals, ranges, status)
+        B.potr_bin_sort_static(fr.views, fr.frame, fr.cfg, fr.n, fr.capacity, tiles, vals, ranges, status)
         torch.cuda.synchronize()
         assert status.tolist() == [0, 0], call
-        got = _sorted_outputs(fr, keys, vals, ranges)
+        got = _sorted_outputs(fr, tiles, vals, ranges)
         for g, e in zip(got, want):
             assert np.array_equal(g, e), call
 
@@ -70,6 +70,6 @@ def test_static_scratch_sort_rejects_oversize():
     fr = _frame(w.scene, w.cameras)
     status = torch.zeros(2, dtype=torch.int64, device=fr.device)
     with pytest.raises(B.PotrError) as e:
-        B.potr_bin_sort_static(fr.views, fr.frame, fr.cfg, fr.n, B.POTR_STATIC_MAX_INSTANCES + 1, fr.keys, fr.vals,
+        B.potr_bin_sort_static(fr.views, fr.frame, fr.cfg, fr.n, B.POTR_STATIC_MAX_INSTANCES + 1, fr.tiles, fr.vals,
                                fr.ranges, status)
     assert e.value.status == B.POTR_ERR_TOO_LARGE
