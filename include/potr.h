@@ -119,7 +119,8 @@ typedef struct {
  * owned).  raster holds 16 floats (64 bytes) per vk, 16-byte aligned:
  *   [0] mean x  [1] mean y  [2] A  [3] B  [4] C  [5] opacity  [6] prefilter  [7] offset bits
  *   [8] r       [9] g       [10] b [11] rectangle bits (x0 | y0 << 11 | width << 22)
- *   [12] kept-tile mask, low word  [13] high word  [14] 1 if every tile is kept  [15] 0
+ *   [12] kept-tile mask, low word  [13] high word  [14] rectangle bits (as [11])
+ *   [15] kept tiles | (1 << 31 if every tile is kept)
  * where log2 G(dx, dy) = A dx^2 + B dx dy + C dy^2, "offset" is the vk's first emission
  * slot (written by potr_bin_sort) and mask bit (ty - y0) width + (tx - x0) says whether
  * tile (tx, ty) of the rectangle is kept (rectangles of at most 64 tiles; larger ones keep

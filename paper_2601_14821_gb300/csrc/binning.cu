@@ -162,7 +162,6 @@ __global__ void __launch_bounds__(256) depth_key_kernel(const uint32_t* __restri
 // (depth, vk) order.  The tile digits of every partition pass are counted here
 // (warp-aggregated shared-memory increments).
 __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ eoff,
-                                                   const uint32_t* __restrict__ touched, const uint2* __restrict__ rect,
                                                    const potr_view_info* __restrict__ info, int64_t n, int64_t n_vk,
                                                    const uint64_t* __restrict__ m_eff,
                                                    const float4* __restrict__ raster, uint32_t* __restrict__ keys,
@@ -180,19 +179,20 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
     if (i < n_vk) {
       vk = order[i];
       off = eoff[i];
-      cnt = touched[vk];
+      // record words 12..15: kept-tile mask, rectangle word, kept count | all-kept << 31
+      const float4 m = raster[(size_t)vk * kRec + 3];
+      cnt = __float_as_uint(m.w) & 0x7fffffffu;
       if (cnt) {
         const potr_view_info vi = info[(int)(vk / (uint64_t)n)];
-        const uint2 r = rect[vk];
-        x0 = r.x & 0xffffu;
-        y0 = r.x >> 16;
-        w = (r.y & 0xffffu) - x0;
+        const uint32_t rw = __float_as_uint(m.z);
+        x0 = rw & 0x7ffu;
+        y0 = (rw >> 11) & 0x7ffu;
+        w = rw >> 22;
         tiles_x = (uint32_t)vi.tiles_x;
         row0 = (uint32_t)vi.tile_base;
-        const float4 m = raster[(size_t)vk * kRec + 3];  // kept-tile mask
         m_lo = __float_as_uint(m.x);
         m_hi = __float_as_uint(m.y);
-        m_all = __float_as_uint(m.z);
+        m_all = __float_as_uint(m.w) >> 31;
       }
     }
     uint32_t incl = cnt;
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(256) digit_base_kernel(const uint32_t* __restr
 
 // vals_in == nullptr: the value of item i is i itself.  The item count is *m_dev, or m_host
 // when m_dev is null.
-__global__ void __launch_bounds__(kOsThreads) onesweep_kernel(const uint32_t* __restrict__ keys_in,
+__global__ void __launch_bounds__(kOsThreads, 4) onesweep_kernel(const uint32_t* __restrict__ keys_in,
                                                               const uint32_t* __restrict__ vals_in,
                                                               const uint64_t* __restrict__ m_dev, int64_t m_host,
                                                               int shift,
@@ -368,20 +368,18 @@ __global__ void __launch_bounds__(kOsThreads) onesweep_kernel(const uint32_t* __
   if (base >= m) return;  // uniform per block
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
-  uint32_t k[kOsItems], v[kOsItems], dg[kOsItems], lr[kOsItems];
+  // Keys (and ranks) stay in registers; values are loaded only when they are scattered, and
+  // digits are recomputed from the keys, so that four blocks fit on an SM.
+  const int64_t ibase = base + warp * (kOsItems * 32) + lane;  // item r is ibase + 32 r
+  const int nv = (int)min((int64_t)kOsItems, (m - ibase + 31) / 32);  // items r < nv are valid
+  uint32_t k[kOsItems], lr[kOsItems];
 #pragma unroll
-  for (int r = 0; r < kOsItems; ++r) {
-    const int64_t i = base + warp * (kOsItems * 32) + r * 32 + lane;
-    const bool valid = i < m;
-    k[r] = valid ? keys_in[i] : 0u;
-    v[r] = valid ? (vals_in ? vals_in[i] : (uint32_t)i) : 0u;
-    dg[r] = valid ? (k[r] >> shift) & 0xffu : 256u;
-  }
+  for (int r = 0; r < kOsItems; ++r) k[r] = r < nv ? keys_in[ibase + 32 * r] : 0u;
   // stable rank inside the warp: rounds in order, lanes in order
   uint32_t* wc = warp_cnt + warp * 257;
 #pragma unroll
   for (int r = 0; r < kOsItems; ++r) {
-    const uint32_t d = dg[r];
+    const uint32_t d = r < nv ? (k[r] >> shift) & 0xffu : 256u;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const uint32_t rank = __popc(peers & lt);
     const uint32_t c0 = wc[d];
@@ -412,15 +410,19 @@ __global__ void __launch_bounds__(kOsThreads) onesweep_kernel(const uint32_t* __
   dig_glob[t] = gbase[t] + (uint32_t)excl;
   blk_off[t] = block_exclusive_scan256(run, tmp8);
   __syncthreads();
-  // items grouped by digit in shared memory
+  // items grouped by digit in shared memory: keys, then the values (loaded now)
 #pragma unroll
   for (int r = 0; r < kOsItems; ++r) {
-    if (dg[r] < 256u) {
-      const uint32_t pos = blk_off[dg[r]] + warp_cnt[warp * 257 + dg[r]] + lr[r];
+    if (r < nv) {
+      const uint32_t d = (k[r] >> shift) & 0xffu;
+      const uint32_t pos = blk_off[d] + warp_cnt[warp * 257 + d] + lr[r];
       s_keys[pos] = k[r];
-      s_vals[pos] = v[r];
+      lr[r] = pos;
     }
   }
+#pragma unroll
+  for (int r = 0; r < kOsItems; ++r)
+    if (r < nv) s_vals[lr[r]] = vals_in ? vals_in[ibase + 32 * r] : (uint32_t)(ibase + 32 * r);
   __syncthreads();
   const int nvalid = (int)min((int64_t)kOsTile, m - base);
   for (int i = threadIdx.x; i < nvalid; i += kOsThreads) {
@@ -548,7 +550,9 @@ extern "C" potr_status potr_bin_sort(const potr_views* views, const potr_frame* 
   const int tile_passes = (bits_for(frame->total_tiles) + 7) / 8;
   if (4 + tile_passes > kMaxPasses) return POTR_ERR_UNSUPPORTED;
   if (cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)onesweep_smem_bytes()) !=
-      cudaSuccess)
+          cudaSuccess ||
+      cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
     return POTR_ERR_CUDA;
 
   // 1. slots in vk order, instance total, capacity check
@@ -590,7 +594,7 @@ extern "C" potr_status potr_bin_sort(const potr_views* views, const potr_frame* 
   {
     const int64_t g = ceil_div(L.n_vk, 256);
     emit_kernel<<<(unsigned)(g < 152 * 16 ? g : 152 * 16), 256, 0, s>>>(
-        order, dv1, views->touched, reinterpret_cast<const uint2*>(views->rect), frame->info, n, L.n_vk, m_eff,
+        order, dv1, frame->info, n, L.n_vk, m_eff,
         reinterpret_cast<const float4*>(views->raster), k_src, v_src, tile_passes, ghist + 256 * 4);
     POTR_CHECK_LAUNCH();
     digit_base_kernel<<<1, 256, 0, s>>>(ghist + 256 * 4, tile_passes, gbase + 256 * 4);

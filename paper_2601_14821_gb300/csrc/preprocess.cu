@@ -205,7 +205,9 @@ __global__ void __launch_bounds__(256) project_kernel(const float* __restrict__ 
 // consecutive vk: their candidate tiles (rectangle cells, row-major) are dealt to the lanes 32
 // at a time, each lane runs tile_hit for one candidate (owner found by a shuffle search over
 // the warp's exclusive candidate counts), and every owner collects its bits from the ballot.
-// Writes record word 12..14 (mask, all-kept flag) and touched = number of kept tiles.
+// Writes record words 12..15 of every vk -- mask low, mask high, the rectangle word (as word
+// 11) and the kept count | all-kept flag << 31 (0 for a culled vk) -- and touched = the kept
+// count, so that the emission reads one 16-byte word per vk.
 __global__ void __launch_bounds__(256) tile_mask_kernel(const uint2* __restrict__ rect, int64_t n_vk,
                                                         potr_raster_config cfg, float4* __restrict__ raster,
                                                         uint32_t* __restrict__ touched) {
@@ -273,11 +275,13 @@ __global__ void __launch_bounds__(256) tile_mask_kernel(const uint2* __restrict_
         mask |= (uint64_t)bits << (lo - excl);
       }
     }
-    if (vk < n_vk && area) {
+    if (vk < n_vk) {
       const bool all = area > (uint32_t)kCullMaxTiles;
+      const uint32_t kept = all ? area : (uint32_t)__popcll(mask);
+      const uint32_t rw = area ? pack_rect_word(x0, y0, w) : 0u;
       raster[vk * kRec + 3] = make_float4(__uint_as_float((uint32_t)mask), __uint_as_float((uint32_t)(mask >> 32)),
-                                          __uint_as_float(all ? 1u : 0u), 0.0f);
-      touched[vk] = all ? area : (uint32_t)__popcll(mask);
+                                          __uint_as_float(rw), __uint_as_float(kept | (all ? 0x80000000u : 0u)));
+      if (area) touched[vk] = kept;
     }
   }
 }

@@ -200,14 +200,14 @@ __device__ __forceinline__ void forward_walk(float4* smem, uint8_t* wmask, const
 
 // Emission slot of the instance of record r (kRec float4) that lies in tile (tx, ty): the
 // splat's first slot plus the number of its kept tiles before (tx, ty) in row-major order of
-// its rectangle (record word 15 flags a rectangle that keeps every tile).
+// its rectangle (bit 31 of record word 15 flags a rectangle that keeps every tile).
 __device__ __forceinline__ uint32_t emission_slot(const float4* r, int tx, int ty) {
   const uint32_t off = __float_as_uint(r[1].w);
   const uint32_t rw = __float_as_uint(r[2].w);
   const uint32_t x0 = rw & 0x7ffu, y0 = (rw >> 11) & 0x7ffu, w = rw >> 22;
   const uint32_t pos = ((uint32_t)ty - y0) * w + ((uint32_t)tx - x0);
   const float4 m = r[3];
-  if (__float_as_uint(m.z)) return off + pos;
+  if (__float_as_uint(m.w) >> 31) return off + pos;
   const uint64_t mask = ((uint64_t)__float_as_uint(m.y) << 32) | __float_as_uint(m.x);
   return off + (uint32_t)__popcll(mask & ((1ull << pos) - 1ull));
 }

@@ -7,7 +7,7 @@ import oracle
 import synth
 
 RASTER_FIELDS = ("mx", "my", "A", "B", "C", "o", "pthr", "offset", "r", "g", "b", "rectw", "mask_lo", "mask_hi",
-                 "all_tiles", "pad")
+                 "rectw2", "kept")
 
 
 def oracle_cfg(cfg: dict):
@@ -31,8 +31,10 @@ def build_frame(scene, cams, **cfg):
 def unpack_raster(fr) -> dict:
     r = fr.raster.cpu().numpy().reshape(-1, 16)
     out = {k: r[:, i] for i, k in enumerate(RASTER_FIELDS)}
-    for k in ("offset", "rectw", "mask_lo", "mask_hi", "all_tiles"):
+    for k in ("offset", "rectw", "mask_lo", "mask_hi", "rectw2", "kept"):
         out[k] = r[:, RASTER_FIELDS.index(k)].view(np.uint32)
+    out["all_tiles"] = out["kept"] >> np.uint32(31)
+    out["kept"] = out["kept"] & np.uint32(0x7FFFFFFF)
     out["mask"] = out["mask_lo"].astype(np.uint64) | (out["mask_hi"].astype(np.uint64) << np.uint64(32))
     return out
 

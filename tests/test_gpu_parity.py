@@ -125,6 +125,7 @@ def _check_preprocess(fr, scene, ovs):
         big = area > oracle.CULL_MAX_TILES
         assert np.array_equal(g["all_tiles"], big[vis].astype(np.uint32))
         assert np.array_equal(g["mask"][~big[vis]], want[vis][~big[vis]])
+        assert np.array_equal(g["rectw2"], rw) and np.array_equal(g["kept"], pv["touched"][vis])
 
 
 def test_preprocess_bit_exact(tiny, tiny_run):
