@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
       if (e < total) {
         // the li-th kept tile of the owner's rectangle, row-major
         const uint32_t li = o_all ? e - o_excl : select_bit64(((uint64_t)o_mhi << 32) | o_mlo, e - o_excl);
-        const uint32_t dy = li / o_w, dx = li - dy * o_w;
+        const uint32_t dy = o_all ? li / o_w : small_div(li, o_w), dx = li - dy * o_w;  // masked: li < 64
         tile = o_row0 + (o_y0 + dy) * o_tx + (o_x0 + dx);
         keys[run0 + e] = tile;
         vals[run0 + e] = o_vk;

@@ -88,8 +88,14 @@ __device__ __forceinline__ float tile_edge_exponent(float A, float B, float C, f
 __device__ __forceinline__ float tile_ku(float A, float B) { return __fdiv_rn(-B, __fmul_rn(2.0f, A)); }
 
 // The per-tile part, for a splat with A < 0 and C < 0 and its ku = tile_ku(A, B), kv = tile_ku(C, B).
+// pthr is the record's prefilter log2(alpha_min / o) - 0.01 (log2f, error a few units in the
+// last place): with y the margin-raised maximum, y < pthr means o 2^y < alpha_min 2^-0.0099
+// and y >= pthr + 0.02 means o 2^y >= alpha_min 2^0.0099, so in both cases the decision of
+// o * exp2r(y) >= alpha_min is known (exp2r is within 4e-7 of 2^y) without evaluating it;
+// only the band between takes exp2r.  The result is the same as evaluating it always.
 __device__ __forceinline__ bool tile_hit_concave(float mx, float my, float A, float B, float C, float o, float ku,
-                                                 float kv, int tx, int ty, int tile_w, int tile_h, float alpha_min) {
+                                                 float kv, float pthr, int tx, int ty, int tile_w, int tile_h,
+                                                 float alpha_min) {
   const float X0 = __fadd_rn((float)(tx * tile_w), 0.5f), X1 = __fadd_rn(X0, (float)(tile_w - 1));
   const float Y0 = __fadd_rn((float)(ty * tile_h), 0.5f), Y1 = __fadd_rn(Y0, (float)(tile_h - 1));
   const float ux0 = __fsub_rn(X0, mx), ux1 = __fsub_rn(X1, mx);
@@ -105,13 +111,17 @@ __device__ __forceinline__ bool tile_hit_concave(float mx, float my, float A, fl
   const float mag = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(fabsf(A), um), um), __fmul_rn(__fmul_rn(fabsf(B), um), vm)),
                               __fmul_rn(__fmul_rn(fabsf(C), vm), vm));
   const float margin = __fadd_rn(__fmul_rn(1e-5f, mag), 1e-4f);
-  return __fmul_rn(o, exp2r(__fadd_rn(pmax, margin))) >= alpha_min;
+  const float y = __fadd_rn(pmax, margin);
+  if (y < pthr) return false;
+  if (y >= pthr + 0.02f) return true;
+  return __fmul_rn(o, exp2r(y)) >= alpha_min;
 }
 
-__device__ __forceinline__ bool tile_hit(float mx, float my, float A, float B, float C, float o, int tx, int ty,
-                                         int tile_w, int tile_h, float alpha_min) {
-  if (!(A < 0.0f && C < 0.0f)) return true;
-  return tile_hit_concave(mx, my, A, B, C, o, tile_ku(A, B), tile_ku(C, B), tx, ty, tile_w, tile_h, alpha_min);
+// q = li / w for li < 2^12 and 1 <= w < 2^12: (li + 1/2) / w lies at least 1/(2w) away from
+// an integer, far more than the few units in the last place of the approximate division, so
+// truncating it gives the exact quotient.
+__device__ __forceinline__ uint32_t small_div(uint32_t li, uint32_t w) {
+  return (uint32_t)__fdividef((float)li + 0.5f, (float)w);
 }
 
 // Position of the r-th set bit (r counted from 0) of a 64-bit word that has more than r.

@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) project_kernel(const float* __restrict__ 
 
 // Kept tiles of every (view, splat) rectangle of at most kCullMaxTiles tiles.  One warp per 32
 // consecutive vk: their candidate tiles (rectangle cells, row-major) are dealt to the lanes 32
-// at a time, each lane runs tile_hit for one candidate (owner found by a shuffle search over
+// at a time, each lane runs the tile test for one candidate (owner found by a shuffle search over
 // the warp's exclusive candidate counts), and every owner collects its bits from the ballot.
 // Writes record words 12..15 of every vk -- mask low, mask high, the rectangle word (as word
 // 11) and the kept count | all-kept flag << 31 (0 for a culled vk) -- and touched = the kept
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(256) tile_mask_kernel(const uint2* __restrict_
   for (int64_t wv = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wv * 32 < n_vk; wv += warps_total) {
     const int64_t vk = wv * 32 + lane;
     uint32_t area = 0, cand = 0, x0 = 0, y0 = 0, w = 1;
-    float mx = 0.0f, my = 0.0f, qa = 0.0f, qb = 0.0f, qc = 0.0f, o = 0.0f, ku = 0.0f, kv = 0.0f;
+    float mx = 0.0f, my = 0.0f, qa = 0.0f, qb = 0.0f, qc = 0.0f, o = 0.0f, ku = 0.0f, kv = 0.0f, pthr = 0.0f;
     bool concave = false;
     if (vk < n_vk) {
       area = touched[vk];
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(256) tile_mask_kernel(const uint2* __restrict_
         if (area <= (uint32_t)kCullMaxTiles) {
           cand = area;
           const float4 r0 = raster[vk * kRec], r1 = raster[vk * kRec + 1];
-          mx = r0.x; my = r0.y; qa = r0.z; qb = r0.w; qc = r1.x; o = r1.y;
+          mx = r0.x; my = r0.y; qa = r0.z; qb = r0.w; qc = r1.x; o = r1.y; pthr = r1.z;
           concave = qa < 0.0f && qc < 0.0f;
           if (concave) {
             ku = tile_ku(qa, qb);
@@ -257,15 +257,17 @@ __global__ void __launch_bounds__(256) tile_mask_kernel(const uint2* __restrict_
       }
       const uint32_t li = e - __shfl_sync(0xffffffffu, excl, owner);
       const uint32_t ow = __shfl_sync(0xffffffffu, w, owner);
-      const int tx = (int)(__shfl_sync(0xffffffffu, x0, owner) + li % ow);
-      const int ty = (int)(__shfl_sync(0xffffffffu, y0, owner) + li / ow);
+      const uint32_t dy = small_div(li, ow);  // li < 64
+      const int tx = (int)(__shfl_sync(0xffffffffu, x0, owner) + (li - dy * ow));
+      const int ty = (int)(__shfl_sync(0xffffffffu, y0, owner) + dy);
       const float omx = __shfl_sync(0xffffffffu, mx, owner), omy = __shfl_sync(0xffffffffu, my, owner);
       const float oa = __shfl_sync(0xffffffffu, qa, owner), ob = __shfl_sync(0xffffffffu, qb, owner);
       const float oc = __shfl_sync(0xffffffffu, qc, owner), oo = __shfl_sync(0xffffffffu, o, owner);
       const float oku = __shfl_sync(0xffffffffu, ku, owner), okv = __shfl_sync(0xffffffffu, kv, owner);
+      const float opt = __shfl_sync(0xffffffffu, pthr, owner);
       const bool oconc = __shfl_sync(0xffffffffu, concave ? 1u : 0u, owner) != 0u;
-      const bool hit = e < total && (!oconc || tile_hit_concave(omx, omy, oa, ob, oc, oo, oku, okv, tx, ty, cfg.tile_w,
-                                                                cfg.tile_h, cfg.alpha_min));
+      const bool hit = e < total && (!oconc || tile_hit_concave(omx, omy, oa, ob, oc, oo, oku, okv, opt, tx, ty,
+                                                                cfg.tile_w, cfg.tile_h, cfg.alpha_min));
       const uint32_t bal = __ballot_sync(0xffffffffu, hit);
       // this lane's candidates [excl, excl + cand) overlapping [e0, e0 + 32)
       const uint32_t lo = max(excl, e0), hi = min(excl + cand, e0 + 32u);
