@@ -248,6 +248,8 @@ __global__ void __launch_bounds__(kThreads) removal_kernel(const float4* __restr
 // dmse[k] += dSSE_k(v) * scale_d[v] with scale_d[v] = 1 / (3 P_v N), views in order; the
 // importance likewise with scale_i[v] = 1 / (P_v N).  The per-view scales are computed once
 // per view (binary64), so the loop has no division.
+constexpr int kReduceChunk = 4096;  // partials staged per block and round
+
 __global__ void __launch_bounds__(256) splat_reduce_kernel(const uint32_t* __restrict__ touched,
                                                            const uint32_t* __restrict__ offsets,
                                                            const uint32_t* __restrict__ n_inst, int64_t capacity,
@@ -256,8 +258,19 @@ __global__ void __launch_bounds__(256) splat_reduce_kernel(const uint32_t* __res
                                                            const potr_view_info* __restrict__ info, double n_total,
                                                            double* __restrict__ dmse, double* __restrict__ importance,
                                                            double* __restrict__ dsse_view) {
+  // One block per 256 consecutive splats.  For one view their emission slots form one
+  // contiguous range (offsets are the exclusive prefix in vk order), which the block stages
+  // through shared memory with coalesced loads; each thread then adds its own slots, in slot
+  // order, from there.
   __shared__ double scale_d[64], scale_i[64];
+  __shared__ float s_d[kReduceChunk], s_i[kReduceChunk];
+  __shared__ uint32_t s_lo, s_hi;
   if ((int64_t)*n_inst > capacity) return;
+  const int64_t k0 = (int64_t)blockIdx.x * blockDim.x;
+  const int64_t k = k0 + threadIdx.x;
+  const int64_t k_last = min(k0 + (int64_t)blockDim.x, n) - 1;
+  double acc_d = (dmse && k < n) ? dmse[k] : 0.0;
+  double acc_i = (importance && k < n) ? importance[k] : 0.0;
   for (int v0 = 0; v0 < n_views; v0 += 64) {
     const int nv = min(64, n_views - v0);
     __syncthreads();
@@ -266,31 +279,42 @@ __global__ void __launch_bounds__(256) splat_reduce_kernel(const uint32_t* __res
       scale_d[threadIdx.x] = 1.0 / (3.0 * P * n_total);
       scale_i[threadIdx.x] = 1.0 / (P * n_total);
     }
-    __syncthreads();
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-      double acc_d = dmse ? dmse[k] : 0.0;
-      double acc_i = importance ? importance[k] : 0.0;
-      for (int vv = 0; vv < nv; ++vv) {
-        const int64_t vk = (int64_t)(v0 + vv) * n + k;
-        const uint32_t cnt = touched[vk];
-        double sd = 0.0, si = 0.0;
-        if (cnt) {
-          const uint32_t off = offsets[vk];
-          KahanSum kd, ki;
-          for (uint32_t i = 0; i < cnt; ++i) kd.add(inst_dse[off + i]);
-          sd = kd.value();
-          if (inst_imp) {
-            for (uint32_t i = 0; i < cnt; ++i) ki.add(inst_imp[off + i]);
-            si = ki.value();
-          }
-        }
-        acc_d += sd * scale_d[vv];
-        acc_i += si * scale_i[vv];
-        if (dsse_view) dsse_view[vk] = sd;
+    for (int vv = 0; vv < nv; ++vv) {
+      const int64_t row = (int64_t)(v0 + vv) * n;
+      uint32_t cnt = 0, off = 0;
+      if (k < n) {
+        cnt = touched[row + k];
+        off = offsets[row + k];
       }
-      if (dmse) dmse[k] = acc_d;
-      if (importance) importance[k] = acc_i;
+      if (threadIdx.x == 0) s_lo = offsets[row + k0];
+      if (k == k_last) s_hi = off + cnt;
+      __syncthreads();
+      const uint32_t lo = s_lo, hi = s_hi;
+      KahanSum kd, ki;
+      for (uint32_t c0 = lo; c0 < hi; c0 += kReduceChunk) {
+        const uint32_t m = min((uint32_t)kReduceChunk, hi - c0);
+        for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+          s_d[i] = inst_dse[c0 + i];
+          if (inst_imp) s_i[i] = inst_imp[c0 + i];
+        }
+        __syncthreads();
+        const uint32_t a = max(off, c0), b = min(off + cnt, c0 + m);
+        for (uint32_t i = a; i < b; ++i) {
+          kd.add(s_d[i - c0]);
+          if (inst_imp) ki.add(s_i[i - c0]);
+        }
+        __syncthreads();
+      }
+      const double sd = cnt ? (double)kd.value() : 0.0;
+      const double si = (cnt && inst_imp) ? (double)ki.value() : 0.0;
+      acc_d += sd * scale_d[vv];
+      acc_i += si * scale_i[vv];
+      if (dsse_view && k < n) dsse_view[row + k] = sd;
     }
+  }
+  if (k < n) {
+    if (dmse) dmse[k] = acc_d;
+    if (importance) importance[k] = acc_i;
   }
 }
 
@@ -390,8 +414,7 @@ extern "C" potr_status potr_removal_effect(const potr_views* views, const potr_f
   }
   if (e != cudaSuccess) return POTR_ERR_CUDA;
   if (d_dmse || d_importance || d_dsse_view) {
-    int64_t g = (n + 255) / 256;
-    if (g > 152 * 32) g = 152 * 32;
+    const int64_t g = (n + 255) / 256;  // one block per 256 splats
     splat_reduce_kernel<<<(unsigned)g, 256, 0, s>>>(views->touched, views->offsets, views->n_instances,
                                                      instance_capacity, d_inst_dse, d_inst_imp, n, frame->n_views,
                                                      frame->info, (double)n_views_total, d_dmse, d_importance,
