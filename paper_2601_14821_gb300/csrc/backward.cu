@@ -29,7 +29,7 @@ constexpr int kBwdBatch = 128;
 constexpr float kLn2 = 0.69314718055994531f;
 
 size_t bwd_smem_bytes() {
-  return sizeof(float4) * 2 * kRec * kBwdBatch + sizeof(float) * kGradQ * kWarps * kBwdBatch + kBwdBatch;
+  return sizeof(float4) * 2 * kSRec * kBwdBatch + sizeof(float) * kGradQ * kWarps * kBwdBatch + kBwdBatch;
 }
 
 // Lanes l, l^4, l^8, ... receive the sum over all 32 lanes of v[l & 3] (fixed order): a
@@ -94,7 +94,7 @@ __global__ void loss_finish_kernel(const double* __restrict__ block_sums, int nb
 // K9: back-to-front adjoint of the compositing
 // ---------------------------------------------------------------------------------------
 template <bool RECOMPUTE>
-__global__ void __launch_bounds__(kThreads) render_bwd_kernel(const float4* __restrict__ raster,
+__global__ void __launch_bounds__(kThreads, 4) render_bwd_kernel(const float4* __restrict__ raster,
                                                               const uint32_t* __restrict__ vals,
                                                               const uint32_t* __restrict__ ranges,
                                                               const potr_view_info* __restrict__ info, int n_views,
@@ -103,8 +103,8 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const float4* __re
                                                               const float* __restrict__ dL_dimg, int64_t capacity,
                                                               float* __restrict__ inst_grad, TileQueue queue) {
   extern __shared__ float4 dyn[];
-  float4* smem = dyn;                                                // [2][kBwdBatch][kRec]
-  float* red = reinterpret_cast<float*>(dyn + 2 * kRec * kBwdBatch);        // [kGradQ][kWarps][kBwdBatch]
+  float4* smem = dyn;                                                // [2][kBwdBatch][kSRec]
+  float* red = reinterpret_cast<float*>(dyn + 2 * kSRec * kBwdBatch);        // [kGradQ][kWarps][kBwdBatch]
   uint8_t* wmask = reinterpret_cast<uint8_t*>(red + kGradQ * kWarps * kBwdBatch);
   __shared__ uint32_t max_last_w[kWarps];
   __shared__ uint32_t s_slot;
@@ -154,10 +154,10 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const float4* __re
     const uint32_t top = max_last - k * B;
     const uint32_t lo = top > B ? top - B : 0u;
     const int cnt = (int)(top - lo);
-    const float4* buf = smem + kRec * B * (k & 1);
+    const float4* buf = smem + kSRec * B * (k & 1);
     if (k > 0) __syncthreads();  // batch k-1 fully consumed
     if (k + 1 < nb) {
-      st.issue(smem + kRec * B * ((k + 1) & 1), raster);
+      st.issue(smem + kSRec * B * ((k + 1) & 1), raster);
       cp_async_wait<1>();
       if (k + 2 < nb) {
         const uint32_t hi2 = lo - B, lo2 = hi2 > B ? hi2 - B : 0u;
@@ -189,8 +189,8 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const float4* __re
             const int j = glo + b;
             if (lane == u) mypos = j;
             if (lo + (uint32_t)j < last) {
-              const float4 r0 = buf[kRec * j];
-              const float4 r1 = buf[kRec * j + 1];
+              const float4 r0 = buf[kSRec * j];
+              const float4 r1 = buf[kSRec * j + 1];
               const float dx = __fsub_rn(c.fx, r0.x), dy = __fsub_rn(c.fy, r0.y);
               const float p = pair_exponent(r0.z, r0.w, r1.x, dx, dy);
               if (p >= r1.z) {
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const float4* __re
                 const float ao = __fmul_rn(r1.y, G);
                 const float a = fminf(cfg.alpha_max, ao);
                 if (a >= cfg.alpha_min) {
-                  const float4 r2 = buf[kRec * j + 2];
+                  const float4 r2 = buf[kSRec * j + 2];
                   const float rcp = __fdividef(1.0f, 1.0f - a);
                   T = T * rcp;            // T_i
                   const float w = a * T;  // T_i alpha_i
@@ -248,7 +248,8 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const float4* __re
         nz |= t != 0.0f;
       }
       if (nz) {
-        const uint32_t slot = emission_slot(buf + kRec * j, c.tx, c.ty);
+        const float4 m = raster[(size_t)vals[c.s + lo + j] * kRec + 3];  // mask word (L2)
+        const uint32_t slot = emission_slot(buf + kSRec * j, m, c.tx, c.ty);
 #pragma unroll
         for (int q = 0; q < kGradQ; ++q) inst_grad[(int64_t)q * capacity + slot] = sq[q];
       }

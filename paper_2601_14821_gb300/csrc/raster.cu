@@ -27,7 +27,7 @@ namespace potr {
 namespace {
 
 template <int BATCH>
-__global__ void __launch_bounds__(kThreads) render_kernel(const float4* __restrict__ raster,
+__global__ void __launch_bounds__(kThreads, 6) render_kernel(const float4* __restrict__ raster,
                                                           const uint32_t* __restrict__ vals,
                                                           const uint32_t* __restrict__ ranges,
                                                           const potr_view_info* __restrict__ info, int n_views,
@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(kThreads) render_kernel(const float4* __restri
                                                           float* __restrict__ t_final, uint32_t* __restrict__ n_last,
                                                           TileQueue queue) {
   extern __shared__ float4 smem[];  // one batch of records
-  uint8_t* wmask = reinterpret_cast<uint8_t*>(smem + kRec * BATCH);
+  uint8_t* wmask = reinterpret_cast<uint8_t*>(smem + kSRec * BATCH);
   __shared__ uint32_t s_slot;
   int64_t tile;
   for (bool first = true; next_tile(queue, &s_slot, first, tile); first = false) {
@@ -81,11 +81,11 @@ constexpr int kChunk = 8;  // splats per warp transpose-sum
 
 template <int BATCH, bool IMP>
 constexpr size_t removal_smem_bytes() {
-  return sizeof(float4) * 2 * kRec * BATCH + sizeof(float) * kWarps * BATCH * (IMP ? 2 : 1) + BATCH;
+  return sizeof(float4) * 2 * kSRec * BATCH + sizeof(float) * kWarps * BATCH * (IMP ? 2 : 1) + BATCH;
 }
 
 template <int BATCH, bool IMP>
-__global__ void __launch_bounds__(kThreads) removal_kernel(const float4* __restrict__ raster,
+__global__ void __launch_bounds__(kThreads, 5) removal_kernel(const float4* __restrict__ raster,
                                                            const uint32_t* __restrict__ vals,
                                                            const uint32_t* __restrict__ ranges,
                                                            const potr_view_info* __restrict__ info, int n_views,
@@ -93,8 +93,8 @@ __global__ void __launch_bounds__(kThreads) removal_kernel(const float4* __restr
                                                            float* __restrict__ images, float* __restrict__ inst_dse,
                                                            float* __restrict__ inst_imp, TileQueue queue) {
   extern __shared__ float4 dyn[];
-  float4* smem = dyn;                                               // [2][BATCH][kRec] raster records
-  float* red_d = reinterpret_cast<float*>(dyn + 2 * kRec * BATCH);  // [kWarps][BATCH] warp sums of dSE
+  float4* smem = dyn;                                               // [2][BATCH][kSRec] raster records
+  float* red_d = reinterpret_cast<float*>(dyn + 2 * kSRec * BATCH);  // [kWarps][BATCH] warp sums of dSE
   float* red_i = red_d + kWarps * BATCH;                            // [kWarps][BATCH] warp sums of T alpha
   uint8_t* wmask = reinterpret_cast<uint8_t*>(red_d + kWarps * BATCH * (IMP ? 2 : 1));  // [BATCH]
   __shared__ uint32_t max_last_w[kWarps];
@@ -148,10 +148,10 @@ __global__ void __launch_bounds__(kThreads) removal_kernel(const float4* __restr
     const uint32_t top = max_last - k * BATCH;
     const uint32_t lo = top > (uint32_t)BATCH ? top - BATCH : 0u;
     const int cnt = (int)(top - lo);
-    const float4* buf = smem + kRec * BATCH * (k & 1);
+    const float4* buf = smem + kSRec * BATCH * (k & 1);
     if (k > 0) __syncthreads();  // batch k-1 (records, warp sums) fully consumed
     if (k + 1 < nb) {
-      st.issue(smem + kRec * BATCH * ((k + 1) & 1), raster);
+      st.issue(smem + kSRec * BATCH * ((k + 1) & 1), raster);
       cp_async_wait<1>();
       if (k + 2 < nb) {
         const uint32_t hi2 = lo - BATCH, lo2 = hi2 > (uint32_t)BATCH ? hi2 - BATCH : 0u;
@@ -185,13 +185,13 @@ __global__ void __launch_bounds__(kThreads) removal_kernel(const float4* __restr
             const int j = glo + b;
             if (lane == u) mypos = j;
             if (lo + (uint32_t)j < last) {
-              const float4 r0 = buf[kRec * j];
-              const float4 r1 = buf[kRec * j + 1];
+              const float4 r0 = buf[kSRec * j];
+              const float4 r1 = buf[kSRec * j + 1];
               const float p = pair_exponent(r0.z, r0.w, r1.x, __fsub_rn(c.fx, r0.x), __fsub_rn(c.fy, r0.y));
               if (p >= r1.z) {
                 const float a = pair_alpha(r1.y, p, cfg.alpha_max);
                 if (a >= cfg.alpha_min) {
-                  const float4 r2 = buf[kRec * j + 2];
+                  const float4 r2 = buf[kSRec * j + 2];
                   const float rcp = __fdividef(1.0f, 1.0f - a);
                   T = T * rcp;                  // T_i = T_{i+1} / (1 - alpha_i)
                   const float w = a * T;        // T_i alpha_i
@@ -235,7 +235,8 @@ __global__ void __launch_bounds__(kThreads) removal_kernel(const float4* __restr
         if (IMP) si += red_i[w * BATCH + j];
       }
       if (sd != 0.0f || (IMP && si != 0.0f)) {
-        const uint32_t slot = emission_slot(buf + kRec * j, c.tx, c.ty);
+        const float4 m = raster[(size_t)vals[c.s + lo + j] * kRec + 3];  // mask word (L2)
+        const uint32_t slot = emission_slot(buf + kSRec * j, m, c.tx, c.ty);
         inst_dse[slot] = sd;
         if (IMP) inst_imp[slot] = si;
       }
@@ -322,7 +323,7 @@ template <int BATCH>
 cudaError_t launch_render(const potr_views* views, const potr_frame* frame, const potr_raster_config& cfg,
                           const uint32_t* vals, const uint32_t* ranges, float* images, float* t_final,
                           uint32_t* n_last, const TileQueue& q, cudaStream_t s) {
-  const size_t smem = sizeof(float4) * kRec * BATCH + BATCH;
+  const size_t smem = sizeof(float4) * kSRec * BATCH + BATCH;
   const unsigned grid = tile_grid(render_kernel<BATCH>, smem, q, frame->total_tiles);
   render_kernel<BATCH><<<grid, kThreads, smem, s>>>(reinterpret_cast<const float4*>(views->raster), vals, ranges,
                                                     frame->info, frame->n_views, cfg, images, t_final, n_last, q);
@@ -451,8 +452,8 @@ __global__ void __launch_bounds__(kThreads) pair_stats_kernel(const float4* __re
     __syncthreads();
     if (done) continue;
     for (int j = 0; j < cnt; ++j) {
-      const float4 r0 = smem[kRec * j];
-      const float4 r1 = smem[kRec * j + 1];
+      const float4 r0 = smem[kSRec * j];
+      const float4 r1 = smem[kSRec * j + 1];
       ++n_ex;
       const float p = pair_exponent(r0.z, r0.w, r1.x, __fsub_rn(c.fx, r0.x), __fsub_rn(c.fy, r0.y));
       if (p < r1.z) continue;
@@ -504,7 +505,7 @@ extern "C" potr_status potr_pair_stats(const potr_views* views, const potr_frame
   if (n <= 0 || frame->total_tiles <= 0 || frame->total_tiles > 0x7fffffffll) return POTR_ERR_INVALID_ARGUMENT;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaMemsetAsync(d_counts, 0, 5 * sizeof(uint64_t), s) != cudaSuccess) return POTR_ERR_CUDA;
-  pair_stats_kernel<256><<<(unsigned)frame->total_tiles, kThreads, sizeof(float4) * kRec * 256, s>>>(
+  pair_stats_kernel<256><<<(unsigned)frame->total_tiles, kThreads, sizeof(float4) * kSRec * 256, s>>>(
       reinterpret_cast<const float4*>(views->raster), d_vals, d_tile_ranges, frame->info, frame->n_views, *cfg,
       reinterpret_cast<unsigned long long*>(d_counts));
   POTR_CHECK_LAUNCH();

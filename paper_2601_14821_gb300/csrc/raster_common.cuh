@@ -9,6 +9,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+constexpr int kSRec = 3;  // float4 per record in shared memory: the first three of the kRec
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
@@ -20,16 +21,17 @@ __device__ __forceinline__ void cp_async_commit_wait() {
 }
 
 // Gather the first three float4 of the raster records of list entries [first, first + cnt)
-// into smem (record stride kRec); the fourth (the tile mask) is not needed when compositing.
+// into smem (record stride kSRec); the fourth (the tile mask) is read from global memory only
+// where an emission slot is needed.
 template <int BATCH>
 __device__ __forceinline__ void stage_batch(float4* smem, const float4* __restrict__ raster,
                                             const uint32_t* __restrict__ vals, uint32_t first, int cnt) {
   for (int j = threadIdx.x; j < cnt; j += kThreads) {
     const uint32_t vk = vals[first + j];
     const float4* src = raster + (size_t)vk * kRec;
-    cp_async16(smem + kRec * j + 0, src + 0);
-    cp_async16(smem + kRec * j + 1, src + 1);
-    cp_async16(smem + kRec * j + 2, src + 2);
+    cp_async16(smem + kSRec * j + 0, src + 0);
+    cp_async16(smem + kSRec * j + 1, src + 1);
+    cp_async16(smem + kSRec * j + 2, src + 2);
   }
   cp_async_commit_wait();
 }
@@ -37,7 +39,6 @@ __device__ __forceinline__ void stage_batch(float4* smem, const float4* __restri
 // Double-buffered batch staging: the gathers of one batch are in flight (cp.async, one commit
 // group per batch) while the CTA works on the other buffer, and every thread already holds the
 // list values (vk) of the batch after that in registers, so issuing never waits on a load.
-// Whole records (all kRec float4, tile mask included) are copied.
 template <int BATCH>
 struct BatchStager {
   static constexpr int kPer = (BATCH + kThreads - 1) / kThreads;
@@ -57,10 +58,9 @@ struct BatchStager {
       const int j = threadIdx.x + r * kThreads;
       if (j < loaded) {
         const float4* src = raster + (size_t)vk[r] * kRec;
-        cp_async16(buf + kRec * j + 0, src + 0);
-        cp_async16(buf + kRec * j + 1, src + 1);
-        cp_async16(buf + kRec * j + 2, src + 2);
-        cp_async16(buf + kRec * j + 3, src + 3);
+        cp_async16(buf + kSRec * j + 0, src + 0);
+        cp_async16(buf + kSRec * j + 1, src + 1);
+        cp_async16(buf + kSRec * j + 2, src + 2);
       }
     }
     asm volatile("cp.async.commit_group;\n" ::);
@@ -138,7 +138,7 @@ __device__ __forceinline__ void compute_masks(const float4* buf, uint8_t* wmask,
 #pragma unroll
   for (int r = 0; r < BatchStager<BATCH>::kPer; ++r) {
     const int j = threadIdx.x + r * kThreads;
-    if (j < cnt) wmask[j] = (uint8_t)warp_mask(buf[kRec * j], buf[kRec * j + 1], c, cfg);
+    if (j < cnt) wmask[j] = (uint8_t)warp_mask(buf[kSRec * j], buf[kSRec * j + 1], c, cfg);
   }
 }
 
@@ -148,7 +148,7 @@ __device__ __forceinline__ void stage_batch_masked(float4* smem, uint8_t* wmask,
                                                    const uint32_t* __restrict__ vals, uint32_t first, int cnt,
                                                    const TileCtx& c, const potr_raster_config& cfg) {
   stage_batch<BATCH>(smem, raster, vals, first, cnt);
-  for (int j = threadIdx.x; j < cnt; j += kThreads) wmask[j] = (uint8_t)warp_mask(smem[kRec * j], smem[kRec * j + 1], c, cfg);
+  for (int j = threadIdx.x; j < cnt; j += kThreads) wmask[j] = (uint8_t)warp_mask(smem[kSRec * j], smem[kSRec * j + 1], c, cfg);
 }
 
 // Forward walk of the tile list (Section 3, Eqs. 2-4).  Returns colour, final T and n_last.
@@ -175,8 +175,8 @@ __device__ __forceinline__ void forward_walk(float4* smem, uint8_t* wmask, const
         const int j = g + __ffs(m) - 1;
         m &= m - 1;
         if (done) continue;
-        const float4 r0 = smem[kRec * j];
-        const float4 r1 = smem[kRec * j + 1];
+        const float4 r0 = smem[kSRec * j];
+        const float4 r1 = smem[kSRec * j + 1];
         const float p = pair_exponent(r0.z, r0.w, r1.x, __fsub_rn(c.fx, r0.x), __fsub_rn(c.fy, r0.y));
         if (p < r1.z) continue;  // alpha < alpha_min certainly (prefilter with margin)
         const float a = pair_alpha(r1.y, p, cfg.alpha_max);
@@ -186,7 +186,7 @@ __device__ __forceinline__ void forward_walk(float4* smem, uint8_t* wmask, const
           done = true;
           continue;
         }
-        const float4 r2 = smem[kRec * j + 2];
+        const float4 r2 = smem[kSRec * j + 2];
         const float w = a * T;
         C[0] = fmaf(w, r2.x, C[0]);
         C[1] = fmaf(w, r2.y, C[1]);
@@ -198,15 +198,15 @@ __device__ __forceinline__ void forward_walk(float4* smem, uint8_t* wmask, const
   }
 }
 
-// Emission slot of the instance of record r (kRec float4) that lies in tile (tx, ty): the
-// splat's first slot plus the number of its kept tiles before (tx, ty) in row-major order of
-// its rectangle (bit 31 of record word 15 flags a rectangle that keeps every tile).
-__device__ __forceinline__ uint32_t emission_slot(const float4* r, int tx, int ty) {
+// Emission slot of the instance in tile (tx, ty) of the splat whose staged record is r (r[1].w:
+// first slot, r[2].w: rectangle word) and whose record word 12..15 is m: the first slot plus the
+// number of its kept tiles before (tx, ty) in row-major order of its rectangle (bit 31 of m.w
+// flags a rectangle that keeps every tile).
+__device__ __forceinline__ uint32_t emission_slot(const float4* r, const float4& m, int tx, int ty) {
   const uint32_t off = __float_as_uint(r[1].w);
   const uint32_t rw = __float_as_uint(r[2].w);
   const uint32_t x0 = rw & 0x7ffu, y0 = (rw >> 11) & 0x7ffu, w = rw >> 22;
   const uint32_t pos = ((uint32_t)ty - y0) * w + ((uint32_t)tx - x0);
-  const float4 m = r[3];
   if (__float_as_uint(m.w) >> 31) return off + pos;
   const uint64_t mask = ((uint64_t)__float_as_uint(m.y) << 32) | __float_as_uint(m.x);
   return off + (uint32_t)__popcll(mask & ((1ull << pos) - 1ull));
