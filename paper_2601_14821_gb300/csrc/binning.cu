@@ -284,7 +284,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan256(uint32_t x, uint32_t
 // partial sum returned.
 __device__ __forceinline__ uint64_t lookback_prefix(volatile unsigned long long* vst, int64_t tile, uint32_t t,
                                                     int spin_limit, int* err) {
-  constexpr int kWin = 8;
+  constexpr int kWin = 4;
   uint64_t excl = 0;
   int64_t p = tile - 1;
   int spins = 0;
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(256) digit_base_kernel(const uint32_t* __restr
 
 // vals_in == nullptr: the value of item i is i itself.  The item count is *m_dev, or m_host
 // when m_dev is null.
-__global__ void __launch_bounds__(kOsThreads, 4) onesweep_kernel(const uint32_t* __restrict__ keys_in,
+__global__ void __launch_bounds__(kOsThreads, 5) onesweep_kernel(const uint32_t* __restrict__ keys_in,
                                                               const uint32_t* __restrict__ vals_in,
                                                               const uint64_t* __restrict__ m_dev, int64_t m_host,
                                                               int shift,
