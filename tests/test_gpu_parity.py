@@ -218,6 +218,23 @@ def test_mixed_views_every_tile_shape(tile):
     _check_removal(fr, sc, cams, cfg, ovs, res, tg)
 
 
+def test_frame_over_65536_tiles_takes_three_tile_passes():
+    """Nine 1920x1080 views (73,440 global tiles: 17 tile bits, three partition passes, the odd
+    count that lands the result through the alternate buffer); binning, render and removal
+    effect against the oracle."""
+    sc = synth.uniform_cube_scene(4000, 91)
+    cams = synth.ring_cameras(9, 3.0, 0.2, (1920, 1080))
+    cfg = dict(tile_w=16, tile_h=16, batch=256)
+    fr = build_frame(sc, cams, **cfg)
+    assert fr.total_tiles > 65536
+    tg = _tiny_targets(sc, cams, cfg, 91)
+    res = frame_outputs(fr, pack_targets(fr, tg))
+    act, ovs = _oracle_views(sc, cams, cfg)
+    _check_binning(fr, ovs)
+    _check_render(fr, sc, cams, cfg, ovs, res)
+    _check_removal(fr, sc, cams, cfg, ovs, res, tg)
+
+
 def test_batch_size_and_view_chunking_do_not_change_bits():
     sc, cams = mixed_workload()
     outs = []
