@@ -344,6 +344,37 @@ POTR_API potr_status potr_bin_sort_static(const potr_views* views, const potr_fr
 POTR_API potr_status potr_selftest_wait_timeout(void* d_ws, size_t ws_bytes, int32_t spin_limit,
                                                 potr_device_status* d_status, potr_stream_t stream);
 
+/* Workspace bytes of potr_prune_select for n splats (about 16 n). */
+POTR_API size_t potr_prune_workspace_size(int64_t n);
+
+/*
+ * One iteration of the pruning controller (Section IV-C, "Iterative pruning": the pruning
+ * approximation, the budget and mapping-function equations).  Candidates are the splats with
+ * d_alive[k] != 0 and d_dmse[k] < dmse_max.  Budget B = floor(sum of q_k over candidates /
+ * remaining_iterations) with q_k = floor(d_importance[k] * 2^40) (importance counted in integer
+ * units of 2^-40, so the budget test is exact; q_k = 0 when the importance is not >= 0).  The
+ * removal set S is the shortest prefix of the candidates in ascending (m(d_dmse[k] / dmse_max),
+ * k) order whose q-sum reaches B (empty when B = 0), with m(x) = x for x >= 0 and
+ * (sqrt(1 - 2 a x) - 1) / a for x < 0, in binary64 IEEE arithmetic in that order.  Effect:
+ * d_alive[k] = 0 for k in S; *d_removed (device, nullable) = |S|.
+ * Inputs (device): d_dmse, d_importance [n] binary64 (potr_removal_effect's outputs);
+ * d_alive [n] uint8, in/out.  d_ws: potr_prune_workspace_size(n) bytes.  n <= 2^32 - 1,
+ * remaining_iterations >= 1, dmse_max > 0, a > 0, else INVALID_ARGUMENT.  Asynchronous; no
+ * host synchronisation, graph-capturable.
+ */
+POTR_API potr_status potr_prune_select(int64_t n, const double* d_dmse, const double* d_importance,
+                                       uint8_t* d_alive, double dmse_max, double a, int32_t remaining_iterations,
+                                       unsigned long long* d_removed, void* d_ws, size_t ws_bytes,
+                                       potr_stream_t stream);
+
+/*
+ * Removes the pruned splats from the scene: d_opacity_logits[k] = -infinity where d_alive[k]
+ * == 0 (opacity 0 after activation: the splat keeps no tile and composites nowhere, so its
+ * removal effect and importance are 0 from then on).  Device arrays of n entries.
+ */
+POTR_API potr_status potr_prune_apply(int64_t n, const uint8_t* d_alive, float* d_opacity_logits,
+                                      potr_stream_t stream);
+
 /* Number of kernels the library has launched in this process (host-side counter). */
 POTR_API uint64_t potr_launch_count(void);
 

@@ -101,6 +101,9 @@ SIGNATURES = {
                                     _P, _P, _P, _P, _P, _I64, C.POINTER(SceneGrads), _P, _SZ, _P]),
     "potr_bin_sort_static": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _I64, _P, _P,
                                     _P, _P, _P]),
+    "potr_prune_workspace_size": (_SZ, [_I64]),
+    "potr_prune_select": (_I32, [_I64, _P, _P, _P, C.c_double, C.c_double, _I32, _P, _P, _SZ, _P]),
+    "potr_prune_apply": (_I32, [_I64, _P, _P, _P]),
 }
 
 
@@ -254,3 +257,18 @@ def potr_render_backward(scene: Scene, views: Views, frame: Frame, cfg: RasterCo
 def potr_selftest_wait_timeout(ws, spin_limit: int, status, stream=None):
     _check("potr_selftest_wait_timeout", lib().potr_selftest_wait_timeout(ptr(ws), ws.numel(), spin_limit,
                                                                           ptr(status), stream_handle(stream)))
+
+
+def potr_prune_workspace_size(n: int) -> int:
+    return int(lib().potr_prune_workspace_size(n))
+
+
+def potr_prune_select(n: int, dmse, importance, alive, dmse_max: float, a: float, remaining: int, removed, ws,
+                      stream=None):
+    _check("potr_prune_select", lib().potr_prune_select(n, ptr(dmse), ptr(importance), ptr(alive), float(dmse_max),
+                                                        float(a), int(remaining), ptr(removed), ptr(ws), ws.numel(),
+                                                        stream_handle(stream)))
+
+
+def potr_prune_apply(n: int, alive, opacity_logits, stream=None):
+    _check("potr_prune_apply", lib().potr_prune_apply(n, ptr(alive), ptr(opacity_logits), stream_handle(stream)))
