@@ -326,6 +326,9 @@ def run_ours(args):
     # ---- fine-tuning step: 1M splats, 8 views 1280x720, L1 + squared-error loss (lambda 0.2)
     fwd_bwd = fwd_bwd_step_ms(args, dev, D)
 
+    # ---- iterative pruning (Section IV-C): 48 iterations over the 16 views of the scene
+    pruning = prune_run(args, dev, D)
+
     # ---- many views of uneven resolution in view chunks, autotuned, eager and graph-replayed
     multiview = None if args.no_multiview else multiview_config(args, dev, D, "batched", 16)
     large = multiview_config(args, dev, D, "large", 8, fwd_bwd=True) if args.large else None
@@ -356,6 +359,7 @@ def run_ours(args):
             "pairs": pc,
             "fwd_bwd_ms_per_step": fwd_bwd["store"],
             "fwd_bwd": fwd_bwd,
+            "pruning": pruning,
             "multiview": multiview,
             "large": large,
             "roofline": {"kernel": "removal_kernel (memset + tile pass + per-splat reduce)", "bound": "alu",
@@ -425,6 +429,67 @@ def fwd_bwd_step_ms(args, dev, D) -> dict:
     out["per_pixel_bytes_stored"] = 8
     del fr
     return out
+
+
+def prune_run(args, dev, D, q: float = 0.5, iterations: int = 48) -> dict:
+    """The whole iterative pruning of the scene workload: each iteration recomputes dMSE_k and
+    I_k over the 16 views (preprocess, bin + sort, removal effect) and the controller removes a
+    budget's worth of the splats below dMSE_MAX = 10^(-8.8 - 2q).  Targets are the render of the
+    unpruned scene.  Device-timed; the controller's share is timed with events around it."""
+    import torch
+
+    import synth
+    from paper_2601_14821_gb300.batched import BatchedRemovalEffect
+    from paper_2601_14821_gb300.pipeline import scene_to_device
+    from paper_2601_14821_gb300.prune import PruneController
+
+    w = synth.workload("scene")
+    scene_d = scene_to_device(w.scene, dev)
+    be = BatchedRemovalEffect(scene_d, synth.cameras_to_array(w.cameras), views_per_chunk=16, device=dev, **CFG)
+    inst0 = be.plan()
+    targets = torch.empty(3 * be.total_pixels, dtype=torch.float32, device=dev)
+    be.render(targets)
+    ctrl = PruneController(w.scene.n, device=dev, iterations=iterations, q=q)
+    n = w.scene.n
+    dmse = torch.zeros(n, dtype=torch.float64, device=dev)
+    imp = torch.zeros_like(dmse)
+    logits = scene_d["opacity_logits"]
+    # first launches of the controller's kernels outside the timed region (on a scratch mask)
+    warm = PruneController(n, device=dev, iterations=iterations, q=q)
+    warm.select(dmse, imp)
+    removed = torch.zeros(iterations, dtype=torch.int64, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(iterations)]
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(iterations + 1)]
+    torch.cuda.synchronize()
+    D.barrier()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for it in range(iterations):
+        starts[it].record()
+        dmse.zero_()
+        imp.zero_()
+        be.step(targets, dmse, imp)
+        ev[it][0].record()
+        ctrl.select(dmse, imp)
+        ctrl.apply(logits)
+        ev[it][1].record()
+        removed[it : it + 1].copy_(ctrl.removed)
+    starts[iterations].record()
+    b.record()
+    torch.cuda.synchronize()
+    total_ms = D.max_over_ranks(a.elapsed_time(b), dev)
+    per_it = [starts[i].elapsed_time(starts[i + 1]) for i in range(iterations)]
+    counts = [int(x) for x in n - np.cumsum(removed.cpu().numpy())]
+    ctrl_ms = sum(x.elapsed_time(y) for x, y in ev) / iterations
+    be.frames[0].preprocess()
+    be.frames[0].bin_sort()
+    torch.cuda.synchronize()
+    return {"workload": "scene: 1M splats, 16 views 1280x720, targets = render of the unpruned scene",
+            "q": q, "dmse_max": ctrl.dmse_max, "iterations": iterations,
+            "ms_per_iteration": total_ms / iterations, "controller_ms_per_iteration": ctrl_ms,
+            "iteration_ms": [round(x, 3) for x in per_it[:3] + per_it[-2:]],
+            "splats_before": n, "splats_after": counts[-1], "alive_after_iteration": counts[:8] + counts[-2:],
+            "instances_before": int(inst0), "instances_after": be.frames[0].instance_count()}
 
 
 def multiview_config(args, dev, D, name: str, views_per_chunk: int, fwd_bwd: bool = False) -> dict:
