@@ -238,7 +238,9 @@ POTR_API potr_status potr_render(const potr_views* views, const potr_frame* fram
  * so that calls over consecutive view chunks compose (zero d_dmse before the first call).
  * With d_inst_imp / d_importance non-NULL the same is done for T_i alpha_i, giving
  * I_k += (sum_x T alpha) / (P_v n_views_total) (Section IV-A).  d_dsse_view (nullable,
- * [n_views][n] binary64) receives dSSE_k(v) itself.  d_images (nullable) receives the
+ * [n_views][n] binary64) receives dSSE_k(v) itself, and d_imp_view (nullable, [n_views][n]
+ * binary64, needs d_inst_imp) the per-view importance I_k(v) = (sum_x T alpha) / P_v (the
+ * weights of the SH energy compaction).  d_images (nullable) receives the
  * render.  d_targets: planar [3][H][W] per view at offset 3 * pixel_base.  d_tile_order as in
  * potr_render.
  */
@@ -248,7 +250,7 @@ POTR_API potr_status potr_removal_effect(const potr_views* views, const potr_fra
                                 int64_t instance_capacity,
                                 float* d_inst_dse,
                                 float* d_inst_imp, double* d_dmse, double* d_importance, double* d_dsse_view,
-                                float* d_images, potr_stream_t stream);
+                                double* d_imp_view, float* d_images, potr_stream_t stream);
 
 /* Gradients of a scene's parameters: the same SoA planes as potr_scene (device, overwritten). */
 typedef struct {
@@ -374,6 +376,29 @@ POTR_API potr_status potr_prune_select(int64_t n, const double* d_dmse, const do
  */
 POTR_API potr_status potr_prune_apply(int64_t n, const uint8_t* d_alive, float* d_opacity_logits,
                                       potr_stream_t stream);
+
+/*
+ * Spherical-harmonics energy compaction (Section IV-D: the per-splat linear system, the
+ * ridge-regression closed form with the Tikhonov matrix that spares the DC coefficient, and the
+ * importance, colour-model, sparsity and two-pass modifications).  For every splat k of the
+ * scene and every view s of the frame with w_s = d_imp_view[s * n + k] > 0 (I_k(s) from
+ * potr_removal_effect): rows w_s Y(d_s) of the real SH basis at the direction camera -> splat and
+ * colours w_s C(d_s), C = sum_i L_i Y_i(d_s) the splat's linear SH colour (before the +0.5 offset
+ * and the clamp) in YCoCg (Y = R/4 + G/2 + B/4, Co = R/2 - B/2, Cg = -R/4 + G/2 - B/4).  Columns
+ * are kept in index order unless |cosine| with a kept preceding column exceeds alpha (or the
+ * column is all zero); the DC column is always kept.  Pass 1 solves, per YCoCg channel, the
+ * ridge system over the kept columns with lambda (Y) or 3 lambda (Co, Cg) on the AC
+ * coefficients only; pass 2 repeats it per channel without the AC coefficients x of pass 1 with
+ * floor(1/2 + x sf) == 0 (quantised to zero).  A splat no view sees keeps its coefficients.
+ * Binary64 throughout.  Outputs (device, nullable): d_sh_out [16][3][n] float, the compacted
+ * coefficients back in RGB (must not alias scene->sh); d_sh_ycocg [16][3][n] binary64, in YCoCg;
+ * d_kept [4][n] bit masks of the kept columns (after the cosine test, then per channel after
+ * pass 2; all 0 for an unseen splat).  Paper values: lambda = 10^-q, alpha = sigmoid(3q),
+ * sf = 1 + 100 q.
+ */
+POTR_API potr_status potr_sh_compact(const potr_scene* scene, const potr_frame* frame, const double* d_imp_view,
+                                     double lambda, double alpha, double sf, float* d_sh_out, double* d_sh_ycocg,
+                                     uint32_t* d_kept, potr_stream_t stream);
 
 /* Number of kernels the library has launched in this process (host-side counter). */
 POTR_API uint64_t potr_launch_count(void);

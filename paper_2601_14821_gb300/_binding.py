@@ -88,7 +88,7 @@ SIGNATURES = {
     "potr_render": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _P, _P, _P, _P, _P,
                            _P, _P]),
     "potr_removal_effect": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _P, _P, _P,
-                                   _P, _I32, _I64, _P, _P, _P, _P, _P, _P, _P]),
+                                   _P, _I32, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
     "potr_tile_schedule_workspace_size": (_SZ, []),
     "potr_tile_schedule": (_I32, [C.POINTER(Frame), _P, _P, _P, _SZ, _P]),
     "potr_pair_stats": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _P, _P, _P, _P]),
@@ -104,6 +104,8 @@ SIGNATURES = {
     "potr_prune_workspace_size": (_SZ, [_I64]),
     "potr_prune_select": (_I32, [_I64, _P, _P, _P, C.c_double, C.c_double, _I32, _P, _P, _SZ, _P]),
     "potr_prune_apply": (_I32, [_I64, _P, _P, _P]),
+    "potr_sh_compact": (_I32, [C.POINTER(Scene), C.POINTER(Frame), _P, C.c_double, C.c_double, C.c_double, _P, _P,
+                               _P, _P]),
 }
 
 
@@ -199,11 +201,12 @@ def potr_render(views: Views, frame: Frame, cfg: RasterConfig, n: int, vals, ran
 
 def potr_removal_effect(views: Views, frame: Frame, cfg: RasterConfig, n: int, vals, ranges, targets,
                         n_views_total: int, capacity: int, inst_dse, inst_imp=None, dmse=None, importance=None,
-                        dsse_view=None, images=None, stream=None, order=None):
+                        dsse_view=None, images=None, stream=None, order=None, imp_view=None):
     _check("potr_removal_effect",
            lib().potr_removal_effect(C.byref(views), C.byref(frame), C.byref(cfg), n, ptr(vals), ptr(ranges),
                                      ptr(order), ptr(targets), n_views_total, capacity, ptr(inst_dse), ptr(inst_imp),
-                                     ptr(dmse), ptr(importance), ptr(dsse_view), ptr(images), stream_handle(stream)))
+                                     ptr(dmse), ptr(importance), ptr(dsse_view), ptr(imp_view), ptr(images),
+                                     stream_handle(stream)))
 
 
 def potr_tile_schedule_workspace_size() -> int:
@@ -272,3 +275,10 @@ def potr_prune_select(n: int, dmse, importance, alive, dmse_max: float, a: float
 
 def potr_prune_apply(n: int, alive, opacity_logits, stream=None):
     _check("potr_prune_apply", lib().potr_prune_apply(n, ptr(alive), ptr(opacity_logits), stream_handle(stream)))
+
+
+def potr_sh_compact(scene: Scene, frame: Frame, imp_view, lam: float, alpha: float, sf: float, sh_out=None,
+                    sh_ycocg=None, kept=None, stream=None):
+    _check("potr_sh_compact", lib().potr_sh_compact(C.byref(scene), C.byref(frame), ptr(imp_view), float(lam),
+                                                    float(alpha), float(sf), ptr(sh_out), ptr(sh_ycocg), ptr(kept),
+                                                    stream_handle(stream)))

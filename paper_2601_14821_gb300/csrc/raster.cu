@@ -258,12 +258,13 @@ __global__ void __launch_bounds__(256) splat_reduce_kernel(const uint32_t* __res
                                                            const float* __restrict__ inst_imp, int64_t n, int n_views,
                                                            const potr_view_info* __restrict__ info, double n_total,
                                                            double* __restrict__ dmse, double* __restrict__ importance,
-                                                           double* __restrict__ dsse_view) {
+                                                           double* __restrict__ dsse_view,
+                                                           double* __restrict__ imp_view) {
   // One block per 256 consecutive splats.  For one view their emission slots form one
   // contiguous range (offsets are the exclusive prefix in vk order), which the block stages
   // through shared memory with coalesced loads; each thread then adds its own slots, in slot
   // order, from there.
-  __shared__ double scale_d[64], scale_i[64];
+  __shared__ double scale_d[64], scale_i[64], inv_p[64];
   __shared__ float s_d[kReduceChunk], s_i[kReduceChunk];
   __shared__ uint32_t s_lo, s_hi;
   if ((int64_t)*n_inst > capacity) return;
@@ -279,6 +280,7 @@ __global__ void __launch_bounds__(256) splat_reduce_kernel(const uint32_t* __res
       const double P = (double)info[v0 + threadIdx.x].width * (double)info[v0 + threadIdx.x].height;
       scale_d[threadIdx.x] = 1.0 / (3.0 * P * n_total);
       scale_i[threadIdx.x] = 1.0 / (P * n_total);
+      inv_p[threadIdx.x] = 1.0 / P;
     }
     for (int vv = 0; vv < nv; ++vv) {
       const int64_t row = (int64_t)(v0 + vv) * n;
@@ -311,6 +313,7 @@ __global__ void __launch_bounds__(256) splat_reduce_kernel(const uint32_t* __res
       acc_d += sd * scale_d[vv];
       acc_i += si * scale_i[vv];
       if (dsse_view && k < n) dsse_view[row + k] = sd;
+      if (imp_view && k < n) imp_view[row + k] = si * inv_p[vv];
     }
   }
   if (k < n) {
@@ -387,7 +390,8 @@ extern "C" potr_status potr_removal_effect(const potr_views* views, const potr_f
                                            const uint32_t* d_tile_ranges, uint32_t* d_tile_order,
                                            const float* d_targets, int32_t n_views_total,
                                            int64_t instance_capacity, float* d_inst_dse, float* d_inst_imp,
-                                           double* d_dmse, double* d_importance, double* d_dsse_view, float* d_images,
+                                           double* d_dmse, double* d_importance, double* d_dsse_view,
+                                           double* d_imp_view, float* d_images,
                                            potr_stream_t stream) {
   using namespace potr;
   if (!views || !frame || !valid_cfg(cfg) || !d_vals || !d_tile_ranges || !d_targets || !d_inst_dse)
@@ -396,7 +400,7 @@ extern "C" potr_status potr_removal_effect(const potr_views* views, const potr_f
     return POTR_ERR_INVALID_ARGUMENT;
   if (n <= 0 || frame->n_views < 1 || n_views_total < 1 || instance_capacity <= 0) return POTR_ERR_INVALID_ARGUMENT;
   if (frame->total_tiles <= 0 || frame->total_tiles > 0x7fffffffll) return POTR_ERR_INVALID_ARGUMENT;
-  if (d_importance && !d_inst_imp) return POTR_ERR_INVALID_ARGUMENT;
+  if ((d_importance || d_imp_view) && !d_inst_imp) return POTR_ERR_INVALID_ARGUMENT;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaMemsetAsync(d_inst_dse, 0, sizeof(float) * (size_t)instance_capacity, s) != cudaSuccess) return POTR_ERR_CUDA;
   if (d_inst_imp && cudaMemsetAsync(d_inst_imp, 0, sizeof(float) * (size_t)instance_capacity, s) != cudaSuccess)
@@ -414,12 +418,12 @@ extern "C" potr_status potr_removal_effect(const potr_views* views, const potr_f
     default: e = launch_removal<512, true>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, q, s); break;
   }
   if (e != cudaSuccess) return POTR_ERR_CUDA;
-  if (d_dmse || d_importance || d_dsse_view) {
+  if (d_dmse || d_importance || d_dsse_view || d_imp_view) {
     const int64_t g = (n + 255) / 256;  // one block per 256 splats
     splat_reduce_kernel<<<(unsigned)g, 256, 0, s>>>(views->touched, views->offsets, views->n_instances,
                                                      instance_capacity, d_inst_dse, d_inst_imp, n, frame->n_views,
                                                      frame->info, (double)n_views_total, d_dmse, d_importance,
-                                                     d_dsse_view);
+                                                     d_dsse_view, d_imp_view);
     note_launches(1);
     if (cudaGetLastError() != cudaSuccess) return POTR_ERR_CUDA;
   }
