@@ -484,12 +484,61 @@ def prune_run(args, dev, D, q: float = 0.5, iterations: int = 48) -> dict:
     be.frames[0].preprocess()
     be.frames[0].bin_sort()
     torch.cuda.synchronize()
+    sh = sh_compaction_run(args, dev, D, be.frames[0], targets, q)
     return {"workload": "scene: 1M splats, 16 views 1280x720, targets = render of the unpruned scene",
             "q": q, "dmse_max": ctrl.dmse_max, "iterations": iterations,
             "ms_per_iteration": total_ms / iterations, "controller_ms_per_iteration": ctrl_ms,
             "iteration_ms": [round(x, 3) for x in per_it[:3] + per_it[-2:]],
             "splats_before": n, "splats_after": counts[-1], "alive_after_iteration": counts[:8] + counts[-2:],
-            "instances_before": int(inst0), "instances_after": be.frames[0].instance_count()}
+            "instances_before": int(inst0), "instances_after": be.frames[0].instance_count(),
+            "sh_compaction": sh}
+
+
+def sh_compaction_run(args, dev, D, frame, targets, q: float) -> dict:
+    """SH energy compaction (Section IV-D) of the pruned scene over the frame's 16 views: per-view
+    importances from one removal pass, then the compaction of every splat (binary64), timed with
+    CUDA events; the oracle's per-splat time on a 300-splat sample for context."""
+    import time
+
+    import torch
+
+    import synth
+    from oracle import sh_compact as oshc
+    from paper_2601_14821_gb300.sh_compact import compact, params
+
+    n, V = frame.n, frame.n_views
+    imp_view = torch.zeros(V * n, dtype=torch.float64, device=dev)
+    dmse = torch.zeros(n, dtype=torch.float64, device=dev)
+    frame.removal_effect(targets, dmse, None, imp_view=imp_view)
+    p = params(q)
+    compact(frame, imp_view, p=p)  # first launch outside the timed region
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    a.record()
+    for _ in range(reps):
+        rgb, ycocg, kept = compact(frame, imp_view, p=p)
+    b.record()
+    torch.cuda.synchronize()
+    ms = D.max_over_ranks(a.elapsed_time(b), dev) / reps
+    kept_np = kept.cpu().numpy().view(np.uint32)
+    seen = kept_np[0] != 0
+    ac_kept = [np.array([bin(int(x)).count("1") - 1 for x in kept_np[c + 1][seen]]) for c in range(3)]
+    out = {"splats": n, "views": V, "ms": ms, "splats_per_s": n / (ms / 1e3), "lambda": p["lam"],
+           "alpha": p["alpha"], "sf": p["sf"], "splats_seen": int(seen.sum()),
+           "mean_ac_kept_per_channel": [float(x.mean()) if x.size else 0.0 for x in ac_kept]}
+    if D.env_ranks()[0] == 0 and not args.no_cpu_baseline:
+        w = synth.workload("scene")
+        iv = imp_view.cpu().numpy().reshape(V, n)
+        centres = np.array([oshc.camera_centre(c) for c in w.cameras])
+        sample = np.nonzero(seen)[0][:300]
+        t0 = time.perf_counter()
+        for k in sample:
+            oshc.compact_splat(w.scene.sh[:, :, k], w.scene.means[:, k], centres, iv[:, k], p["lam"], p["alpha"],
+                               p["sf"])
+        dt = time.perf_counter() - t0
+        out["oracle_splats_per_s_1_core"] = len(sample) / dt
+    return out
 
 
 def multiview_config(args, dev, D, name: str, views_per_chunk: int, fwd_bwd: bool = False) -> dict:

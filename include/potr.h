@@ -381,8 +381,9 @@ POTR_API potr_status potr_prune_apply(int64_t n, const uint8_t* d_alive, float* 
  * Spherical-harmonics energy compaction (Section IV-D: the per-splat linear system, the
  * ridge-regression closed form with the Tikhonov matrix that spares the DC coefficient, and the
  * importance, colour-model, sparsity and two-pass modifications).  For every splat k of the
- * scene and every view s of the frame with w_s = d_imp_view[s * n + k] > 0 (I_k(s) from
- * potr_removal_effect): rows w_s Y(d_s) of the real SH basis at the direction camera -> splat and
+ * scene and every view s of the frame with I_k(s) = d_imp_view[s * n + k] > 0 (from
+ * potr_removal_effect), weighted relative to each other, w_s = I_k(s) / max_s' I_k(s'): rows
+ * w_s Y(d_s) of the real SH basis at the direction camera -> splat and
  * colours w_s C(d_s), C = sum_i L_i Y_i(d_s) the splat's linear SH colour (before the +0.5 offset
  * and the clamp) in YCoCg (Y = R/4 + G/2 + B/4, Co = R/2 - B/2, Cg = -R/4 + G/2 - B/4).  Columns
  * are kept in index order unless |cosine| with a kept preceding column exceeds alpha (or the

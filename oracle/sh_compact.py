@@ -8,7 +8,7 @@ lighting coefficients (Section IV-D, linear-system equation; Y holds the real SH
 view directions).  The compacted coefficients are the ridge-regression solution
 L' = (Y^T Y + Gamma^T Gamma)^-1 Y^T C (closed-form equation), Gamma = sqrt(lambda) diag(0, 1, ...,
 1) (the DC coefficient is not regularised), with the section's four modifications:
-  * importance: every row of Y and C is multiplied by I_k(s), the splat's importance in view s;
+  * importance: every row of Y and C is multiplied by the splat's importance in view s;
   * colour model: C is taken to YCoCg (Y = R/4 + G/2 + B/4, Co = R/2 - B/2, Cg = -R/4 + G/2 - B/4)
     and solved per channel with lambda_Y = lambda, lambda_Co = lambda_Cg = 3 lambda;
   * sparsity: column i of Y is zeroed (L'_i = 0) if a preceding column is sufficiently parallel,
@@ -26,7 +26,12 @@ Readings (where the paper is silent):
     == 0 with SF_SH = 1 + 100 q (quantisation equation, hyper-parameter table); decided per
     YCoCg channel, so the second pass may keep different coefficients per channel;
   * lambda = 10^-q, alpha = sigmoid(3q) (hyper-parameter table);
-  * a splat no view sees (all importances 0) keeps its coefficients.
+  * a splat no view sees (all importances 0) keeps its coefficients;
+  * the importance weights a splat's views against each other: the row weights are
+    w_s = I_k(s) / max_s' I_k(s'), so that lambda means the same for a splat of any size.  Taken
+    literally (w_s = I_k(s), a fraction of the image, ~1e-4 per view), the data term would be
+    ~1e-8 of lambda = 10^-q and every AC coefficient would vanish, against the section's claim of
+    virtually no quality loss.
 Everything is binary64.
 """
 from __future__ import annotations
@@ -73,6 +78,7 @@ def compact_splat(L_rgb, mean, centres, weights, lam, alpha, sf):
     w = np.asarray(weights, np.float64)
     if not np.any(w > 0):
         return L_rgb @ RGB_TO_YCOCG.T, None, None, None, None
+    w = np.where(w > 0, w, 0.0) / np.max(w)
     rows, cols = [], []
     for c, ws in zip(centres, w):
         if ws <= 0:

@@ -1,7 +1,8 @@
 // sh_compact.cu -- spherical-harmonics energy compaction of POTR (Section IV-D), one warp per
 // splat, binary64.
 //
-// For splat k and the frame's views s with importance w_s = I_k(s) > 0, the rows w_s Y(d_s)
+// For splat k and the frame's views s with importance I_k(s) > 0, weighted relative to each
+// other (w_s = I_k(s) / max_s' I_k(s')), the rows w_s Y(d_s)
 // (real SH basis at the direction camera -> splat) and the colours w_s C(d_s) (its current
 // linear SH colour, taken to YCoCg) give the weighted Gram matrix G = Y~^T Y~ and the right-hand
 // sides b = Y~^T C~ (lanes build them 32 views at a time through shared memory).  Columns are
@@ -102,12 +103,18 @@ __global__ void __launch_bounds__(32 * kShWarps) sh_compact_kernel(int64_t n, co
     const double mx = means[k], my = means[n + k], mz = means[2 * n + k];
     for (int e = lane; e < 256; e += 32) (&w.G[0][0])[e] = 0.0;
     for (int e = lane; e < 48; e += 32) (&w.b[0][0])[e] = 0.0;
+    double wmax = 0.0;  // the views are weighted relative to the most important one
+    for (int v = lane; v < n_views; v += 32) {
+      const double x = imp_view[(int64_t)v * n + k];
+      if (x > wmax) wmax = x;
+    }
+    for (int o = 16; o >= 1; o >>= 1) wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
     __syncwarp();
     for (int v0 = 0; v0 < n_views; v0 += 32) {
       const int v = v0 + lane;
       double wt = 0.0;
       if (v < n_views) wt = imp_view[(int64_t)v * n + k];
-      if (!(wt > 0.0)) wt = 0.0;
+      wt = wt > 0.0 ? wt / wmax : 0.0;
       double* row = w.rows[lane];
       if (wt > 0.0) {
         const float* W = cams[v].w2c;

@@ -67,7 +67,7 @@ def test_compaction_matches_oracle(run, case):
     from paper_2601_14821_gb300.sh_compact import compact, params
 
     sc, cams, fr, imp_view, iv = run
-    p = params(0.5) if case.startswith("paper") else {"lam": 1e-9, "alpha": 0.9, "sf": 51.0}
+    p = params(0.5) if case.startswith("paper") else {"lam": 1e-4, "alpha": 0.9, "sf": 51.0}
     rgb, ycocg, kept = compact(fr, imp_view, p=p)
     rgb, ycocg, kept = rgb.cpu().numpy(), ycocg.cpu().numpy(), kept.cpu().numpy().view(np.uint32)
     centres = np.array([oshc.camera_centre(c) for c in cams])
