@@ -401,6 +401,20 @@ POTR_API potr_status potr_sh_compact(const potr_scene* scene, const potr_frame* 
                                      double lambda, double alpha, double sf, float* d_sh_out, double* d_sh_ycocg,
                                      uint32_t* d_kept, potr_stream_t stream);
 
+/*
+ * One Adam step over every parameter plane of a scene (the optimiser of the fine-tuning loop,
+ * Section IV-F: the original 3DGS training routine; Kingma & Ba 2015 in PyTorch's form):
+ *   m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2,
+ *   p <- p - (lr / (1 - b1^step)) m / (sqrt(v) / sqrt(1 - b2^step) + eps)   (p unchanged if m = 0).
+ * params / m / v: device planes in the potr_scene layout, updated in place; grads: the
+ * gradients (e.g. from potr_render_backward).  lr[6] (host): means, log_scales, quats,
+ * opacity_logits, SH DC (planes 0-2 of sh), SH rest (planes 3-47).  step >= 1, 0 <= beta < 1,
+ * eps >= 0, else INVALID_ARGUMENT.
+ */
+POTR_API potr_status potr_adam_step(const potr_scene_grads* params, const potr_scene_grads* grads,
+                                    const potr_scene_grads* m, const potr_scene_grads* v, int64_t n, int64_t step,
+                                    const float* lr, float beta1, float beta2, float eps, potr_stream_t stream);
+
 /* Number of kernels the library has launched in this process (host-side counter). */
 POTR_API uint64_t potr_launch_count(void);
 

@@ -106,6 +106,9 @@ SIGNATURES = {
     "potr_prune_apply": (_I32, [_I64, _P, _P, _P]),
     "potr_sh_compact": (_I32, [C.POINTER(Scene), C.POINTER(Frame), _P, C.c_double, C.c_double, C.c_double, _P, _P,
                                _P, _P]),
+    "potr_adam_step": (_I32, [C.POINTER(SceneGrads), C.POINTER(SceneGrads), C.POINTER(SceneGrads),
+                              C.POINTER(SceneGrads), _I64, _I64, C.POINTER(C.c_float), C.c_float, C.c_float, C.c_float,
+                              _P]),
 }
 
 
@@ -282,3 +285,17 @@ def potr_sh_compact(scene: Scene, frame: Frame, imp_view, lam: float, alpha: flo
     _check("potr_sh_compact", lib().potr_sh_compact(C.byref(scene), C.byref(frame), ptr(imp_view), float(lam),
                                                     float(alpha), float(sf), ptr(sh_out), ptr(sh_ycocg), ptr(kept),
                                                     stream_handle(stream)))
+
+
+def grads_struct(d: dict) -> SceneGrads:
+    """SceneGrads view of a dict of parameter-shaped device tensors."""
+    return SceneGrads(d["means"].data_ptr(), d["log_scales"].data_ptr(), d["quats"].data_ptr(),
+                      d["opacity_logits"].data_ptr(), d["sh"].data_ptr())
+
+
+def potr_adam_step(params: dict, grads: dict, m: dict, v: dict, n: int, step: int, lr, beta1=0.9, beta2=0.999,
+                   eps=1e-15, stream=None):
+    lrs = (C.c_float * 6)(*[float(x) for x in lr])
+    _check("potr_adam_step", lib().potr_adam_step(C.byref(grads_struct(params)), C.byref(grads_struct(grads)),
+                                                  C.byref(grads_struct(m)), C.byref(grads_struct(v)), n, int(step),
+                                                  lrs, float(beta1), float(beta2), float(eps), stream_handle(stream)))

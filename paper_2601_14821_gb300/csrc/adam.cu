@@ -1,0 +1,87 @@
+// adam.cu -- fused Adam step over all parameter planes of a scene (the optimiser of the
+// fine-tuning loop: the original 3DGS training routine, Section IV-F).  One thread per scalar,
+// six learning-rate groups (means, log-scales, quaternions, opacity logits, SH DC, SH rest):
+//   m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2,
+//   p <- p - (lr / (1 - b1^t)) m / (sqrt(v) / sqrt(1 - b2^t) + eps)     (Kingma & Ba 2015)
+// A parameter whose gradient is 0 and whose moments are 0 does not move (an infinite opacity
+// logit of a pruned splat stays infinite).
+#include "potr_device.cuh"
+
+namespace potr {
+namespace {
+
+struct AdamGroup {
+  float* p;
+  const float* g;
+  float* m;
+  float* v;
+  int64_t count;
+  float step_size;  // lr / (1 - b1^t)
+};
+
+struct AdamGroups {
+  AdamGroup g[6];
+};
+
+__global__ void __launch_bounds__(256) adam_kernel(AdamGroups groups, float b1, float b2, float inv_sqrt_bc2,
+                                                   float eps) {
+  for (int gi = 0; gi < 6; ++gi) {
+    const AdamGroup& G = groups.g[gi];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < G.count; i += (int64_t)gridDim.x * blockDim.x) {
+      const float g = G.g[i];
+      const float m = b1 * G.m[i] + (1.0f - b1) * g;
+      const float v = b2 * G.v[i] + (1.0f - b2) * g * g;
+      G.m[i] = m;
+      G.v[i] = v;
+      if (m != 0.0f) G.p[i] -= G.step_size * m / (sqrtf(v) * inv_sqrt_bc2 + eps);
+    }
+  }
+}
+
+}  // namespace
+}  // namespace potr
+
+extern "C" potr_status potr_adam_step(const potr_scene_grads* params, const potr_scene_grads* grads,
+                                      const potr_scene_grads* m, const potr_scene_grads* v, int64_t n, int64_t step,
+                                      const float* lr, float beta1, float beta2, float eps, potr_stream_t stream) {
+  using namespace potr;
+  if (!params || !grads || !m || !v || !lr || n <= 0 || step < 1) return POTR_ERR_INVALID_ARGUMENT;
+  if (!(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps >= 0.0f))
+    return POTR_ERR_INVALID_ARGUMENT;
+  const potr_scene_grads* s4[4] = {params, grads, m, v};
+  for (const potr_scene_grads* s : s4)
+    if (!s->means || !s->log_scales || !s->quats || !s->opacity_logits || !s->sh) return POTR_ERR_INVALID_ARGUMENT;
+  const double bc1 = 1.0 - pow((double)beta1, (double)step);
+  const double bc2 = 1.0 - pow((double)beta2, (double)step);
+  // groups: means, log-scales, quaternions, opacity logits, SH DC (planes 0..2), SH rest (3..47)
+  auto groups_of = [n](const potr_scene_grads* s, float** out) {
+    out[0] = s->means;
+    out[1] = s->log_scales;
+    out[2] = s->quats;
+    out[3] = s->opacity_logits;
+    out[4] = s->sh;
+    out[5] = s->sh + 3 * n;
+  };
+  float *P[6], *Gr[6], *M[6], *V[6];
+  groups_of(params, P);
+  groups_of(grads, Gr);
+  groups_of(m, M);
+  groups_of(v, V);
+  const int64_t cnt[6] = {3 * n, 3 * n, 4 * n, n, 3 * n, 45 * n};
+  AdamGroups G;
+  for (int i = 0; i < 6; ++i) {
+    G.g[i].p = P[i];
+    G.g[i].g = Gr[i];
+    G.g[i].m = M[i];
+    G.g[i].v = V[i];
+    G.g[i].count = cnt[i];
+    G.g[i].step_size = (float)((double)lr[i] / bc1);
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int64_t blocks = (59 * n / 6 + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  adam_kernel<<<(unsigned)blocks, 256, 0, s>>>(G, beta1, beta2, (float)(1.0 / sqrt(bc2)), eps);
+  POTR_CHECK_LAUNCH();
+  return POTR_OK;
+}
