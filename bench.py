@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--large", action="store_true",
                     help="also time the 6M-splat, 300-view 1920x1080 workload (several minutes)")
     ap.add_argument("--no-multiview", action="store_true", help="skip the 3M-splat, 200-view workload")
+    ap.add_argument("--profile-timed", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     return ap.parse_args()
 
 
@@ -208,6 +210,8 @@ def run_ours(args):
     l0 = B.potr_launch_count()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
+    if args.profile_timed:
+        torch.cuda.profiler.start()
     t_start.record()
     for i in range(K):
         ev[i][0].record()
@@ -219,6 +223,8 @@ def run_ours(args):
         ev[i][3].record()
     t_end.record()
     torch.cuda.synchronize()
+    if args.profile_timed:
+        torch.cuda.profiler.stop()
     D.barrier()
     launches = B.potr_launch_count() - l0
     clk = clocks.stop()
@@ -428,7 +434,35 @@ def fwd_bwd_step_ms(args, dev, D) -> dict:
         out[mode] = D.max_over_ranks(a.elapsed_time(b), dev) / args.steps
     out["per_pixel_bytes_stored"] = 8
     del fr
+    out["finetune"] = finetune_run(args, dev, D, w, scene_d, cams_rec, img, targets)
     return out
+
+
+def finetune_run(args, dev, D, w, scene_d, cams_rec, img, targets, iterations: int = 100) -> dict:
+    """The fine-tuning loop (Section IV-F) on the gradient workload: one training view per
+    iteration (seeded random order), forward, loss gradient, backward and the fused Adam step
+    with the 3DGS learning rates; device-timed over ``iterations`` iterations after a warm-up."""
+    import torch
+
+    from paper_2601_14821_gb300.finetune import FineTuner
+
+    V = len(w.cameras)
+    per_view = [targets[3 * v * w.cameras[0].pixels: 3 * (v + 1) * w.cameras[0].pixels] for v in range(V)]
+    params = {k: t.clone() for k, t in scene_d.items()}
+    ft = FineTuner(params, cams_rec, per_view, lam=0.2, extent=4.0, device=dev, check_every=0, **CFG)
+    ft.run(V, order=list(range(V)))
+    first = float(ft.loss.item())
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    ft.run(iterations, seed=1)
+    b.record()
+    torch.cuda.synchronize()
+    ft.ensure_capacity()
+    ms = D.max_over_ranks(a.elapsed_time(b), dev) / iterations
+    return {"workload": "grad: 1M splats, 8 views 1280x720, one view per iteration", "iterations": iterations,
+            "ms_per_iteration": ms, "loss_first_view0": first, "loss_last": float(ft.loss.item()),
+            "lr": ft.lr}
 
 
 def prune_run(args, dev, D, q: float = 0.5, iterations: int = 48) -> dict:
