@@ -42,6 +42,10 @@ FLOP_COMPOSITE = 9       # T (1 - alpha), w = alpha T, three colour FMAs (compos
 FLOP_REMOVAL = 26        # T recovery, ratio, PD and dSE over 3 channels, suffix update (composited pairs)
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 PEAK_FP32_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+# DRAM bytes (read + written) of one removal-kernel launch per view of the scene workload: an
+# ncu capture of the 4-view case measured 246.7 MB (dram__bytes_read.sum + dram__bytes_write.sum);
+# the traffic grows with the views (records gathered per tile), so a 16-view launch moves 16 x this.
+REMOVAL_DRAM_BYTES_PER_VIEW = 246.7e6 / 4
 
 
 def parse():
@@ -370,7 +374,8 @@ def run_ours(args):
             "large": large,
             "roofline": {"kernel": "removal_kernel (memset + tile pass + per-splat reduce)", "bound": "alu",
                          "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / PEAK_FP32_TFLOPS, "traffic": None,
+                         "frac": achieved / PEAK_FP32_TFLOPS,
+                         "traffic": REMOVAL_DRAM_BYTES_PER_VIEW * n_views,
                          "flops_per_launch": flops},
             "e2e": {"value": e2e_vps, "unit": "views/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
