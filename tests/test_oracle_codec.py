@@ -1,0 +1,104 @@
+"""Pins of the codec oracle (Section IV-E) against facts fixed outside it."""
+import math
+
+import numpy as np
+
+import synth
+from oracle import codec
+
+
+def test_quantiser_rounds_half_up():
+    x = np.array([0.0, 0.49, 0.5, -0.5, -0.51, 1.5, 2.4999]) / 10.0
+    assert list(codec.quantise(x, 10.0)) == [0, 0, 1, 0, -1, 2, 2]
+
+
+def test_two_splats_hand_worked_stream():
+    """Splats at opposite corners of the unit cube, one eye 1000 away: tolerance 1.4e-4 q x 1000
+    = 0.07 (q = 0.5), so each ends in the corner cell of depth 4 (centre sqrt(3)/2^5 = 0.054 away;
+    depth 3 gives 0.108).  Root: children 0 and 7 (0x81); then three single-child nodes (0x01 or
+    0x80) and a leaf (0x00) per splat."""
+    means = np.array([[0.0, 1.0], [0.0, 1.0], [0.0, 1.0]], np.float32)
+    eyes = [np.array([0.5, 0.5, 1000.0])]
+    p = codec.params(0.5)
+    occ, order, depth, corner, S = codec.build_octree(means, eyes, p)
+    assert occ == bytes([0x81, 0x01, 0x01, 0x01, 0x00, 0x80, 0x80, 0x80, 0x00])
+    assert list(order) == [0, 1] and list(depth) == [4, 4]
+    pos, dep = codec.decode_positions(occ, corner, S)
+    np.testing.assert_allclose(pos[:, 0], [1 / 32] * 3)
+    np.testing.assert_allclose(pos[:, 1], [1 - 1 / 32] * 3)
+
+
+def test_round_trip_honours_the_precision_criterion_and_the_quantisers():
+    sc = synth.uniform_cube_scene(3000, 9)
+    eyes = [np.array([3.0, 0.2, 0.0]), np.array([-2.0, 0.0, 2.5]), np.array([0.0, 3.0, -0.5])]
+    p = codec.params(0.5)
+    e = codec.encode(sc, eyes, p=p)
+    d = codec.decode(e["compressed"])
+    o = e["order"]
+    mu = sc.means[:, o].astype(np.float64)
+    tol = codec.tolerance(mu, eyes, p["beta"], p["gamma"])
+    err = np.linalg.norm(d["means"] - mu, axis=0)
+    assert np.all(err < tol) and np.array_equal(d["depths"], e["depth"][o])
+    assert np.max(np.abs(d["log_scales"] - sc.log_scales[:, o])) <= 0.5 / p["sf_scale"] + 1e-12
+    assert np.max(np.abs(d["sh"] - sc.sh[:, :, o])) <= 0.5 / p["sf_sh"] + 1e-9
+    op = 1.0 / (1.0 + np.exp(-sc.opacity_logits[o].astype(np.float64)))
+    assert np.max(np.abs(d["opacity"] - op)) <= 0.75 / p["sf_opacity"] + 1e-12
+    q = sc.quats[:, o].astype(np.float64)
+    q = q / np.linalg.norm(q, axis=0)
+    q = np.where(q[0] < 0, -q, q)
+    assert np.max(np.abs(d["quats"][1:] - q[1:])) <= 0.5 / p["sf_rotation"] + 1e-12
+    assert len(e["compressed"]) < len(e["raw"])
+
+
+def _sorted_formulation(means, eyes, p):
+    """The same octree from the splats sorted by cell code: a splat's leaf is the first depth at
+    or below the point where its cell holds no other splat (one more than the longest common
+    cell prefix with its neighbours) that passes the precision test."""
+    corner, S = codec.root_cube(means)
+    X = codec.cells(means, corner, S)
+    n = X.shape[1]
+    code = np.zeros(n, dtype=object)
+    for k in range(n):
+        c = 0
+        for b in range(codec.DEPTH - 1, -1, -1):
+            c = (c << 3) | ((int(X[0, k]) >> b & 1) << 2) | ((int(X[1, k]) >> b & 1) << 1) | (int(X[2, k]) >> b & 1)
+        code[k] = c
+    order = sorted(range(n), key=lambda k: (code[k], k))
+
+    def lcp(a, b):
+        for d in range(codec.DEPTH):
+            s = 3 * (codec.DEPTH - 1 - d)
+            if (a >> s) != (b >> s):
+                return d
+        return codec.DEPTH
+
+    tol = codec.tolerance(means, eyes, p["beta"], p["gamma"])
+    mu = np.asarray(means, np.float64)
+    depth = np.zeros(n, np.int64)
+    for i, k in enumerate(order):
+        l = max(lcp(code[order[i - 1]], code[k]) if i > 0 else -1,
+                lcp(code[order[i + 1]], code[k]) if i + 1 < n else -1)
+        d = min(l + 1, codec.DEPTH)
+        while d < codec.DEPTH:
+            cell = [int(X[a, k]) >> (codec.DEPTH - d) for a in range(3)]
+            c = codec.centre(corner, S, cell, d)
+            if math.sqrt((mu[0, k] - c[0]) ** 2 + (mu[1, k] - c[1]) ** 2 + (mu[2, k] - c[2]) ** 2) < tol[k]:
+                break
+            d += 1
+        depth[k] = d
+    return np.array(order), depth
+
+
+def test_splitting_equals_the_sorted_formulation():
+    rng = np.random.default_rng(2)
+    eyes = [np.array([2.0, 0.1, 0.3]), np.array([0.0, -2.5, 1.0])]
+    p = codec.params(0.7)
+    for n in (1, 2, 17, 400):
+        means = rng.uniform(-1, 1, (3, n)).astype(np.float32)
+        if n > 10:
+            means[:, 5] = means[:, 3]  # two splats in one cell: split to the depth limit
+        occ, order, depth, corner, S = codec.build_octree(means, eyes, p)
+        o2, d2 = _sorted_formulation(means, eyes, p)
+        assert np.array_equal(order, o2) and np.array_equal(depth, d2), n
+        if n > 10:
+            assert depth[5] == codec.DEPTH and depth[3] == codec.DEPTH
