@@ -415,6 +415,37 @@ POTR_API potr_status potr_adam_step(const potr_scene_grads* params, const potr_s
                                     const potr_scene_grads* m, const potr_scene_grads* v, int64_t n, int64_t step,
                                     const float* lr, float beta1, float beta2, float eps, potr_stream_t stream);
 
+/* Scale factors and precision parameters of the codec (Section IV-E, hyper-parameter table:
+ * SF_scale = 1 + 4000q, SF_rotation = 1 + 400q, SF_opacity = 1 + 200q, SF_SH = 1 + 100q,
+ * beta = 1.4e-4 q, gamma = 5 10^(-3-5q)). */
+typedef struct {
+  double sf_scale, sf_rotation, sf_opacity, sf_sh, beta, gamma;
+} potr_codec_params;
+
+/* Workspace bytes of potr_codec_encode for n splats (about 130 n). */
+POTR_API size_t potr_codec_workspace_size(int64_t n);
+
+/*
+ * The encoder's device part (Section IV-E, quantisation equation and the octree precision
+ * criterion ||mu - mu^|| < max(gamma, beta min_s ||mu - mu_s||)).  Root cube: corner = per-axis
+ * minimum of the positions, edge = the largest per-axis range (1 if all coincide); depth limit
+ * 21; child octant c = (x bit << 2) | (y bit << 1) | z bit.  A cell is split while it holds
+ * several splats or its single splat is not within the tolerance of the cell centre (binary64).
+ * Outputs (device): d_nodes [<= 22 n] the node bytes in depth-first order -- an internal node
+ * its child octant mask, a leaf 0, a leaf at depth 21 its splat count - 1 -- and *d_n_nodes
+ * their number; d_order [n] the splats in that leaf order (ties by index); d_attrs [55][n]
+ * int32, in that order, property after property: floor(1/2 + x SF) of the 3 log-scales, of x,
+ * y, z of the normalised quaternion made to have w >= 0, of sigmoid(opacity logit), and of the
+ * 48 SH values (coefficient-major; planes 0-2, the DC, as differences from the previous splat);
+ * d_cube (nullable) [4] binary64: corner x, y, z and edge.  d_eyes [n_eyes][3] binary64: the
+ * camera centres.  d_status as potr_bin_sort (bounded waits).  UNSUPPORTED if 22 n >= 2^31.
+ */
+POTR_API potr_status potr_codec_encode(const potr_scene* scene, const double* d_eyes, int32_t n_eyes,
+                                       const potr_codec_params* params, uint8_t* d_nodes, uint32_t* d_n_nodes,
+                                       uint32_t* d_order, int32_t* d_attrs, double* d_cube,
+                                       potr_device_status* d_status, void* d_ws, size_t ws_bytes,
+                                       potr_stream_t stream);
+
 /* Number of kernels the library has launched in this process (host-side counter). */
 POTR_API uint64_t potr_launch_count(void);
 

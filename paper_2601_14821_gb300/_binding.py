@@ -71,6 +71,11 @@ class SceneGrads(C.Structure):
                 ("opacity_logits", C.c_void_p), ("sh", C.c_void_p)]
 
 
+class CodecParams(C.Structure):
+    _fields_ = [("sf_scale", C.c_double), ("sf_rotation", C.c_double), ("sf_opacity", C.c_double),
+                ("sf_sh", C.c_double), ("beta", C.c_double), ("gamma", C.c_double)]
+
+
 class DeviceStatus(C.Structure):
     _fields_ = [("code", C.c_int32), ("reserved", C.c_int32), ("required_instances", C.c_int64)]
 
@@ -106,6 +111,9 @@ SIGNATURES = {
     "potr_prune_apply": (_I32, [_I64, _P, _P, _P]),
     "potr_sh_compact": (_I32, [C.POINTER(Scene), C.POINTER(Frame), _P, C.c_double, C.c_double, C.c_double, _P, _P,
                                _P, _P]),
+    "potr_codec_workspace_size": (_SZ, [_I64]),
+    "potr_codec_encode": (_I32, [C.POINTER(Scene), _P, _I32, C.POINTER(CodecParams), _P, _P, _P, _P, _P, _P, _P, _SZ,
+                                 _P]),
     "potr_adam_step": (_I32, [C.POINTER(SceneGrads), C.POINTER(SceneGrads), C.POINTER(SceneGrads),
                               C.POINTER(SceneGrads), _I64, _I64, C.POINTER(C.c_float), C.c_float, C.c_float, C.c_float,
                               _P]),
@@ -299,3 +307,14 @@ def potr_adam_step(params: dict, grads: dict, m: dict, v: dict, n: int, step: in
     _check("potr_adam_step", lib().potr_adam_step(C.byref(grads_struct(params)), C.byref(grads_struct(grads)),
                                                   C.byref(grads_struct(m)), C.byref(grads_struct(v)), n, int(step),
                                                   lrs, float(beta1), float(beta2), float(eps), stream_handle(stream)))
+
+
+def potr_codec_workspace_size(n: int) -> int:
+    return int(lib().potr_codec_workspace_size(n))
+
+
+def potr_codec_encode(scene: Scene, eyes, n_eyes: int, params: CodecParams, nodes, n_nodes, order, attrs, cube,
+                      status, ws, stream=None):
+    _check("potr_codec_encode", lib().potr_codec_encode(C.byref(scene), ptr(eyes), int(n_eyes), C.byref(params),
+                                                        ptr(nodes), ptr(n_nodes), ptr(order), ptr(attrs), ptr(cube),
+                                                        ptr(status), ptr(ws), ws.numel(), stream_handle(stream)))

@@ -7,112 +7,19 @@
 // inter-block waiting), the sort ranks items stably inside a block with warp match masks, so
 // its result equals std::stable_sort of the keys.  All kernels are HBM-bound; they read the
 // instance count from device memory so that a whole frame can be captured in a CUDA graph.
-#include "potr_device.cuh"
+#include "radix.cuh"
+#include "scan.cuh"
 
 namespace potr {
 namespace {
 
-constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
-constexpr int kScanChunk = kScanThreads * kScanItems;  // items per block
-
-int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
-
-constexpr int kOsThreads = 256;
-constexpr int kOsItems = 16;
-constexpr int kOsTile = kOsThreads * kOsItems;  // items per block and pass
-constexpr int kMaxPasses = 8;
-constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagInc = 2ull << 62, kCountMask = (1ull << 62) - 1;
-constexpr int kSpinLimit = 1 << 22;
 
 
 
-// -----------------------------------------------------------------------------------------
-// Block-wide exclusive scan of kScanChunk items.  Warp w owns items [w*256, w*256+256) with
-// lane l holding items l + 32 j (j = 0..7): loads and stores are coalesced.
-// -----------------------------------------------------------------------------------------
-template <typename Tin, typename Tacc, typename Tout>
-__global__ void __launch_bounds__(kScanThreads) scan_chunks_kernel(const Tin* in, const uint32_t* __restrict__ gather,
-                                                                   Tout* out, int64_t n, Tacc* __restrict__ chunk_sums) {
-  __shared__ Tacc warp_tot[kScanThreads / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)warp * 256;
-  Tacc v[kScanItems];
-#pragma unroll
-  for (int j = 0; j < kScanItems; ++j) {
-    const int64_t i = base + lane + 32 * j;
-    v[j] = (i < n) ? (Tacc)in[gather ? (int64_t)gather[i] : i] : (Tacc)0;
-  }
-  Tacc carry = 0;
-#pragma unroll
-  for (int j = 0; j < kScanItems; ++j) {
-    Tacc x = v[j];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const Tacc y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    const Tacc row_total = __shfl_sync(0xffffffffu, x, 31);
-    v[j] = carry + x - v[j];  // exclusive within the warp's 256 items
-    carry += row_total;
-  }
-  if (lane == 0) warp_tot[warp] = carry;
-  __syncthreads();
-  Tacc wbase = 0, btot = 0;
-#pragma unroll
-  for (int w = 0; w < kScanThreads / 32; ++w) {
-    const Tacc t = warp_tot[w];
-    if (w < warp) wbase += t;
-    btot += t;
-  }
-#pragma unroll
-  for (int j = 0; j < kScanItems; ++j) {
-    const int64_t i = base + lane + 32 * j;
-    if (i < n) out[i] = (Tout)(v[j] + wbase);
-  }
-  if (threadIdx.x == 0) chunk_sums[blockIdx.x] = btot;
-}
 
-template <typename Tout>
-__global__ void __launch_bounds__(256) add_chunk_base_kernel(Tout* out, int64_t n,
-                                                             const uint64_t* __restrict__ chunk_base) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) out[i] = (Tout)((uint64_t)out[i] + chunk_base[i / kScanChunk]);
-}
 
-__global__ void store_total_kernel(const uint64_t* __restrict__ chunk_sums, uint64_t* __restrict__ total) {
-  *total = chunk_sums[0];
-}
 
-// Workspace for an exclusive scan of n items: one u64 per chunk at each level.
-int64_t scan_ws_words(int64_t n) {
-  int64_t w = 0;
-  int64_t m = n;
-  do {
-    m = ceil_div(m, kScanChunk);
-    w += m;
-  } while (m > 1);
-  return w + 1;
-}
 
-// Exclusive scan of x_i = in[i] (or in[gather[i]]) for i in [0, n) -> out, total (u64) ->
-// *total.  ws: scan_ws_words(n) u64 words.
-template <typename Tin, typename Tout>
-cudaError_t scan_exclusive(const Tin* in, Tout* out, int64_t n, uint64_t* total, uint64_t* ws, cudaStream_t s,
-                           const uint32_t* gather = nullptr) {
-  const int64_t nb = ceil_div(n, kScanChunk);
-  uint64_t* sums = ws;
-  scan_chunks_kernel<Tin, uint64_t, Tout><<<(unsigned)nb, kScanThreads, 0, s>>>(in, gather, out, n, sums);
-  note_launches(2);  // this level's scan plus the store or the add below
-  if (nb == 1) {
-    store_total_kernel<<<1, 1, 0, s>>>(sums, total);
-  } else {
-    cudaError_t e = scan_exclusive<uint64_t, uint64_t>(sums, sums, nb, total, ws + nb, s);
-    if (e != cudaSuccess) return e;
-    add_chunk_base_kernel<Tout><<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(out, n, sums);
-  }
-  return cudaGetLastError();
-}
 
 // -----------------------------------------------------------------------------------------
 // Instance count check, depth keys and emission.
@@ -248,74 +155,6 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
     if (h[p][threadIdx.x]) atomicAdd(&ghist[p * 256 + threadIdx.x], h[p][threadIdx.x]);
 }
 
-// -----------------------------------------------------------------------------------------
-// Stable LSD radix sort, 8-bit digits, one kernel per pass ("onesweep": Adinets & Merrill,
-// 2022).  One read of the keys builds the digit histograms of every pass; then each pass
-// ranks 4096 items per block stably (per-warp match masks, warps in order), publishes its
-// per-digit counts, finds the counts of all earlier blocks by decoupled look-back over the
-// published words, and writes its items grouped by digit through shared memory so that the
-// global stores are contiguous runs.  Blocks take their item range from an atomic counter,
-// so every block a look-back waits on is already running; the wait is bounded and reports
-// POTR_ERR_TIMEOUT instead of hanging.
-// -----------------------------------------------------------------------------------------
-size_t onesweep_smem_bytes() { return sizeof(uint32_t) * 2 * kOsTile + sizeof(uint32_t) * (8 * 257 + 3 * 256); }
-
-// Exclusive scan of one value per thread over a 256-thread block (returns this thread's prefix).
-__device__ __forceinline__ uint32_t block_exclusive_scan256(uint32_t x, uint32_t* tmp8) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t incl = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) tmp8[warp] = incl;
-  __syncthreads();
-  uint32_t wbase = 0;
-  for (int w = 0; w < warp; ++w) wbase += tmp8[w];
-  __syncthreads();
-  return wbase + incl - x;
-}
-
-// Decoupled look-back for digit t of block `tile`: the sum of the counts published by blocks
-// 0 .. tile-1 (walking back until an inclusive prefix).  Eight predecessors' words are loaded
-// at once (independent loads) and consumed nearest first; a word that is not yet published
-// restarts the window there.  After spin_limit such restarts the wait ends: *err is set and the
-// partial sum returned.
-__device__ __forceinline__ uint64_t lookback_prefix(volatile unsigned long long* vst, int64_t tile, uint32_t t,
-                                                    int spin_limit, int* err) {
-  constexpr int kWin = 4;
-  uint64_t excl = 0;
-  int64_t p = tile - 1;
-  int spins = 0;
-  while (p >= 0) {
-    unsigned long long x[kWin];
-#pragma unroll
-    for (int i = 0; i < kWin; ++i) x[i] = (p - i >= 0) ? vst[(p - i) * 256 + t] : (kFlagInc | 0ull);
-    int used = 0;
-    bool done = false, stalled = false;
-#pragma unroll
-    for (int i = 0; i < kWin; ++i) {
-      if (done || stalled) continue;
-      const unsigned long long flag = x[i] >> 62;
-      if (flag == 0) {
-        stalled = true;
-        continue;
-      }
-      excl += x[i] & kCountMask;
-      ++used;
-      if (flag == 2) done = true;
-    }
-    if (done) break;
-    p -= used;
-    if (stalled && ++spins > spin_limit) {
-      *err = 1;
-      break;
-    }
-  }
-  return excl;
-}
-
 // Self-test of the bounded wait: block 1 looks back at block 0, whose words nobody publishes.
 __global__ void lookback_timeout_probe_kernel(unsigned long long* status, int spin_limit,
                                               potr_device_status* __restrict__ st) {
@@ -326,113 +165,6 @@ __global__ void lookback_timeout_probe_kernel(unsigned long long* status, int sp
   const uint64_t got = lookback_prefix(vst, 1, threadIdx.x, spin_limit, &s_err);
   __syncthreads();
   if (threadIdx.x == 0 && s_err && got == 0) set_status(st, POTR_ERR_TIMEOUT, 0);
-}
-
-__global__ void __launch_bounds__(256) digit_base_kernel(const uint32_t* __restrict__ ghist, int passes,
-                                                         uint32_t* __restrict__ gbase) {
-  __shared__ uint32_t tmp8[8];
-  for (int p = 0; p < passes; ++p) gbase[p * 256 + threadIdx.x] = block_exclusive_scan256(ghist[p * 256 + threadIdx.x], tmp8);
-}
-
-// vals_in == nullptr: the value of item i is i itself.  The item count is *m_dev, or m_host
-// when m_dev is null.
-__global__ void __launch_bounds__(kOsThreads, 5) onesweep_kernel(const uint32_t* __restrict__ keys_in,
-                                                              const uint32_t* __restrict__ vals_in,
-                                                              const uint64_t* __restrict__ m_dev, int64_t m_host,
-                                                              int shift,
-                                                              const uint32_t* __restrict__ gbase,
-                                                              uint32_t* __restrict__ tile_counter,
-                                                              unsigned long long* status,
-                                                              uint32_t* __restrict__ keys_out,
-                                                              uint32_t* __restrict__ vals_out,
-                                                              potr_device_status* __restrict__ st) {
-  extern __shared__ uint32_t os_smem[];
-  uint32_t* s_keys = os_smem;                                          // [kOsTile]
-  uint32_t* s_vals = s_keys + kOsTile;                                 // [kOsTile]
-  uint32_t* warp_cnt = s_vals + kOsTile;                               // [8][257]
-  uint32_t* blk_off = warp_cnt + 8 * 257;                              // [256]
-  uint32_t* dig_glob = blk_off + 256;                                  // [256]
-  uint32_t* tmp8 = dig_glob + 256;                                     // [8]
-  __shared__ uint32_t s_tile;
-  __shared__ int s_err;
-  if (threadIdx.x == 0) {
-    s_tile = atomicAdd(tile_counter, 1u);
-    s_err = 0;
-  }
-  for (int w = 0; w < 8; ++w) warp_cnt[w * 257 + threadIdx.x] = 0;
-  if (threadIdx.x < 8) warp_cnt[threadIdx.x * 257 + 256] = 0;
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  const int64_t m = m_dev ? (int64_t)*m_dev : m_host;
-  const int64_t base = (int64_t)tile * kOsTile;
-  if (base >= m) return;  // uniform per block
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t lt = (1u << lane) - 1u;
-  // Keys (and ranks) stay in registers; values are loaded only when they are scattered, and
-  // digits are recomputed from the keys, so that four blocks fit on an SM.
-  const int64_t ibase = base + warp * (kOsItems * 32) + lane;  // item r is ibase + 32 r
-  const int nv = (int)min((int64_t)kOsItems, (m - ibase + 31) / 32);  // items r < nv are valid
-  uint32_t k[kOsItems], lr[kOsItems];
-#pragma unroll
-  for (int r = 0; r < kOsItems; ++r) k[r] = r < nv ? keys_in[ibase + 32 * r] : 0u;
-  // stable rank inside the warp: rounds in order, lanes in order
-  uint32_t* wc = warp_cnt + warp * 257;
-#pragma unroll
-  for (int r = 0; r < kOsItems; ++r) {
-    const uint32_t d = r < nv ? (k[r] >> shift) & 0xffu : 256u;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t rank = __popc(peers & lt);
-    const uint32_t c0 = wc[d];
-    __syncwarp();
-    if (rank == 0) wc[d] = c0 + __popc(peers);
-    __syncwarp();
-    lr[r] = c0 + rank;
-  }
-  __syncthreads();
-  // per digit (one per thread): exclusive prefix over warps, block count
-  const uint32_t t = threadIdx.x;
-  uint32_t run = 0;
-  for (int w = 0; w < 8; ++w) {
-    const uint32_t c = warp_cnt[w * 257 + t];
-    warp_cnt[w * 257 + t] = run;
-    run += c;
-  }
-  volatile unsigned long long* vst = status;
-  const int64_t si = (int64_t)tile * 256 + t;
-  uint64_t excl = 0;
-  if (tile == 0) {
-    vst[si] = kFlagInc | run;
-  } else {
-    vst[si] = kFlagAgg | run;
-    excl = lookback_prefix(vst, tile, t, kSpinLimit, &s_err);
-    vst[si] = kFlagInc | (excl + run);
-  }
-  dig_glob[t] = gbase[t] + (uint32_t)excl;
-  blk_off[t] = block_exclusive_scan256(run, tmp8);
-  __syncthreads();
-  // items grouped by digit in shared memory: keys, then the values (loaded now)
-#pragma unroll
-  for (int r = 0; r < kOsItems; ++r) {
-    if (r < nv) {
-      const uint32_t d = (k[r] >> shift) & 0xffu;
-      const uint32_t pos = blk_off[d] + warp_cnt[warp * 257 + d] + lr[r];
-      s_keys[pos] = k[r];
-      lr[r] = pos;
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < kOsItems; ++r)
-    if (r < nv) s_vals[lr[r]] = vals_in ? vals_in[ibase + 32 * r] : (uint32_t)(ibase + 32 * r);
-  __syncthreads();
-  const int nvalid = (int)min((int64_t)kOsTile, m - base);
-  for (int i = threadIdx.x; i < nvalid; i += kOsThreads) {
-    const uint32_t key = s_keys[i];
-    const uint32_t d = (key >> shift) & 0xffu;
-    const uint32_t o = dig_glob[d] + ((uint32_t)i - blk_off[d]);
-    keys_out[o] = key;
-    vals_out[o] = s_vals[i];
-  }
-  if (threadIdx.x == 0 && s_err) set_status(st, POTR_ERR_TIMEOUT, 0);
 }
 
 __global__ void __launch_bounds__(256) tile_ranges_kernel(const uint32_t* __restrict__ tiles, const uint64_t* __restrict__ m_eff,
@@ -484,19 +216,6 @@ SortLayout sort_layout(int64_t n, int32_t n_views, int64_t capacity) {
   L.off_counter = o; o = align_up(o + sizeof(uint32_t) * kMaxPasses);
   L.bytes = o;
   return L;
-}
-
-// One onesweep pass over m items (count in device memory at m_dev, or m_host).
-cudaError_t onesweep_pass(const uint32_t* k_in, const uint32_t* v_in, const uint64_t* m_dev, int64_t m_host,
-                          int64_t blocks, int shift, const uint32_t* gbase, uint32_t* counter,
-                          unsigned long long* status, uint32_t* k_out, uint32_t* v_out, potr_device_status* st,
-                          cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(unsigned long long) * 256 * (size_t)blocks, s);
-  if (e != cudaSuccess) return e;
-  onesweep_kernel<<<(unsigned)blocks, kOsThreads, onesweep_smem_bytes(), s>>>(k_in, v_in, m_dev, m_host, shift, gbase,
-                                                                            counter, status, k_out, v_out, st);
-  note_launches(1);
-  return cudaGetLastError();
 }
 
 }  // namespace
