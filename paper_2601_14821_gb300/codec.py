@@ -55,10 +55,10 @@ class Encoder:
         return head + struct.pack("<I", m) + nodes + body
 
 
-def encode(scene: dict, eyes, q: float = 0.5, p: dict | None = None) -> dict:
+def encode(scene: dict, eyes, q: float = 0.5, p: dict | None = None, level: int = 6) -> dict:
     """Encode a scene: returns the raw and the zlib-compressed bitstream and the leaf order."""
     p = p or params(q)
     enc = Encoder(int(scene["means"].shape[-1]), scene["means"].device)
     enc.run(scene, eyes, p)
     raw = enc.stream(p)
-    return {"raw": raw, "compressed": zlib.compress(raw, 9), "order": enc.order.cpu().numpy()}
+    return {"raw": raw, "compressed": zlib.compress(raw, level), "order": enc.order.cpu().numpy()}
