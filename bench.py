@@ -3,14 +3,18 @@
 A step is one pass of the whole path over one frame: activation + EWA projection of 1M
 splats into 16 views of 1280x720, tile binning + radix sort of every (tile, splat) instance,
 and the removal-effect pass with the per-splat dMSE_k / I_k reduction.  Inputs (the 236 MB of
-splat parameters, the 768 MB of per-view raster records, ~1 GB of sort keys) are larger than
+splat parameters, the 1 GB of per-view raster records, 0.45 GB of instances) are larger than
 the 129 MB L2, so no L2 flush is needed between steps.
 
 Printed (one JSON line on rank 0): the device-timed throughput of the batched frame
 (``value``, views/s), the same frame replayed as a CUDA graph, the one-view-per-launch form,
 Gblend/s (evaluated pixel-splat pairs per second of the removal kernel), the roofline of the
 removal kernel (FP32 ALU), the end-to-end number through host buffers, the clocks seen
-during the timed region, and the CPU oracle timed on a bounded sample.
+during the timed region, and the CPU oracle timed on a bounded sample.  Beside them: the
+fine-tuning forward + backward step and the Adam fine-tuning loop (``fwd_bwd``), the whole
+iterative pruning of the scene with the SH energy compaction and the encoder of the pruned
+scene (``pruning``), and many views of mixed resolution in view chunks (``multiview``; the
+6M-splat, 300-view workload with ``--large``).
 
 ``--impl reference`` times the CPU oracle itself on the same workload (one view per step).
 """
@@ -360,7 +364,7 @@ def run_ours(args):
                        "n_splats": int(frame.n), "views_per_gpu": n_views, "resolution": "1280x720",
                        "tile": f"{CFG['tile_w']}x{CFG['tile_h']}", "splat_batch": CFG["batch"],
                        "form": "batched frame (all views in one launch per stage)", "instances": int(n_inst),
-                       "l2": "inputs larger than L2 (236 MB parameters, 768 MB raster records, ~1 GB keys)",
+                       "l2": "inputs larger than L2 (236 MB parameters, 1 GB raster records, 0.45 GB instances)",
                        "parallelism": f"views replicated per GPU x{world}"},
             "stage_ms": {"preprocess": stage_ms[0], "bin_sort": stage_ms[1], "removal_effect": stage_ms[2]},
             "graph_views_per_s": graph_vps,

@@ -1,7 +1,8 @@
-// binning.cu -- tile binning of the projected splats: exclusive scan of per-(view, splat)
-// tile counts, emission of one (global tile, depth) key per touched tile, a stable LSD radix
-// sort of the 64-bit keys, and per-tile [start, end) ranges (paper Section 3: splats are
-// alpha-composited as layers ordered by approximate depth).
+// binning.cu -- tile binning of the projected splats (paper Section 3: splats are
+// alpha-composited as layers ordered by approximate depth): exclusive scan of the per-(view,
+// splat) kept-tile counts, a stable radix sort of the (view, splat) pairs by depth, emission of
+// one (global tile, vk) instance per kept tile in that depth order, a stable radix partition of
+// the instances by tile, and per-tile [start, end) ranges.
 //
 // Everything is integer work and bit-exact: the scan is a two-level reduce-then-scan (no
 // inter-block waiting), the sort ranks items stably inside a block with warp match masks, so
