@@ -207,3 +207,65 @@ class RemovalEffectFrame:
         vi = self.info_np[v]
         h, w, pb = int(vi["height"]), int(vi["width"]), int(vi["pixel_base"])
         return flat[pb: pb + h * w].view(h, w)
+
+
+class HostPipeline:
+    """Removal-effect steps whose inputs arrive in pinned host memory and whose results go back
+    to it, with the transfers overlapped with compute: the parameters and targets of step i + 1
+    are copied to the device (on a copy stream) while step i computes, and step i's dMSE_k /
+    I_k are copied back while step i + 1 computes.  Device inputs and outputs are double
+    buffered; events order every copy against the compute that uses or produces its buffer."""
+
+    def __init__(self, frame: RemovalEffectFrame):
+        self.frame = frame
+        dev = frame.device
+        self.compute = torch.cuda.current_stream(dev)
+        self.copy = torch.cuda.Stream(device=dev)
+        self.scenes = [{k: torch.empty_like(t) for k, t in frame.scene.items()} for _ in range(2)]
+        self.targets = [torch.empty(3 * frame.total_pixels, dtype=torch.float32, device=dev) for _ in range(2)]
+        self.dmse = [torch.zeros(frame.n, dtype=torch.float64, device=dev) for _ in range(2)]
+        self.imp = [torch.zeros(frame.n, dtype=torch.float64, device=dev) for _ in range(2)]
+        self.inputs_ready = [torch.cuda.Event() for _ in range(2)]
+        self.done = [torch.cuda.Event() for _ in range(2)]
+        self.read = [torch.cuda.Event() for _ in range(2)]
+        self.i = 0   # steps run
+        self.up = 0  # input sets uploaded
+
+    def upload(self, host_scene: dict, host_targets: torch.Tensor):
+        """Queue the copy of the inputs of the next step not yet uploaded (pinned host tensors)."""
+        s = self.up % 2
+        self.up += 1
+        with torch.cuda.stream(self.copy):
+            self.copy.wait_event(self.done[s])  # the step that last read this set has finished
+            for k, t in host_scene.items():
+                self.scenes[s][k].copy_(t, non_blocking=True)
+            self.targets[s].copy_(host_targets, non_blocking=True)
+            self.inputs_ready[s].record(self.copy)
+
+    def step(self, host_dmse: torch.Tensor, host_imp: torch.Tensor):
+        """Run the step on the uploaded inputs and queue the copy of its results to the host."""
+        if self.i >= self.up:
+            raise RuntimeError("upload the step's inputs first")
+        s = self.i % 2
+        f = self.frame
+        self.compute.wait_event(self.inputs_ready[s])
+        self.compute.wait_event(self.read[s])  # the results of two steps ago have left this set
+        f.bind_scene(self.scenes[s])
+        self.dmse[s].zero_()
+        self.imp[s].zero_()
+        f.step(self.targets[s], self.dmse[s], self.imp[s])
+        self.done[s].record(self.compute)
+        with torch.cuda.stream(self.copy):
+            self.copy.wait_event(self.done[s])
+            host_dmse.copy_(self.dmse[s], non_blocking=True)
+            host_imp.copy_(self.imp[s], non_blocking=True)
+            self.read[s].record(self.copy)
+        self.i += 1
+
+    def join(self):
+        """Make the compute stream wait for every queued copy (no host synchronisation)."""
+        self.compute.wait_stream(self.copy)
+
+    def finish(self):
+        self.join()
+        self.compute.synchronize()
