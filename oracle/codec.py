@@ -25,8 +25,9 @@ Readings (the section is silent on them):
     positions map to integer cells at the depth limit 21, X = floor((mu - corner) / S 2^21)
     clamped to [0, 2^21 - 1] (binary64), and a splat's cell at depth d is X >> (21 - d);
   * splitting stops at depth 21 even if several splats share the leaf (they are written in
-    index order); such a leaf's byte is its splat count - 1 (the decoder knows a depth-21 node
-    cannot split), so the stream alone gives every leaf and its multiplicity;
+    index order); that leaf writes 0 like every leaf, and a table after the node bytes lists
+    each such leaf as (its ordinal among the leaves, splat count - 1), so every node byte is a
+    plain child mask and the stream can be parsed in parallel;
   * the precision test uses binary64 with the operations in the written order; the leaf centre
     is corner + (cell + 1/2) S / 2^d per axis;
   * scale = the stored log-scales; opacity = sigmoid(logit) in [0, 1]; rotation = the
@@ -34,7 +35,8 @@ Readings (the section is silent on them):
     coefficients, DC (planes 0-2) as differences of consecutive splats' quantised values in
     stream order (the first against 0);
   * stream: little-endian; header (magic 'POTR', version, n, corner (3 x f64), S (f64), the
-    four SF (f64)); the occupancy bytes; then property after property over the splats in
+    four SF (f64)); the number of node bytes (u32) and the node bytes; the number of shared
+    leaves (u32) and their (ordinal, count - 1) pairs (u32); then property after property over the splats in
     stream order, each quantised value as int32: 3 log-scales, 3 rotation components, opacity,
     48 SH values (coefficient-major, channel inside); entropy coding: zlib level 9 (the paper
     uses zstd, which this image does not have).
@@ -97,7 +99,9 @@ def build_octree(means, eyes, p):
     n = mu.shape[1]
     occ = []
     order = []
+    dups = []
     depth = np.zeros(n, np.int64)
+    leaves = [0]
 
     def visit(d, cell, members):
         must_split = len(members) > 1
@@ -107,8 +111,10 @@ def build_octree(means, eyes, p):
             dist = math.sqrt((mu[0, k] - c[0]) ** 2 + (mu[1, k] - c[1]) ** 2 + (mu[2, k] - c[2]) ** 2)
             must_split = not (dist < tol[k])
         if not must_split or d == DEPTH:
-            assert len(members) <= 256
-            occ.append(len(members) - 1 if d == DEPTH else 0)  # a leaf
+            occ.append(0)  # a leaf
+            if len(members) > 1:
+                dups.append((leaves[0], len(members) - 1))
+            leaves[0] += 1
             for k in sorted(members):
                 order.append(k)
                 depth[k] = d
@@ -123,7 +129,7 @@ def build_octree(means, eyes, p):
             visit(d + 1, (2 * cell[0] + (c >> 2 & 1), 2 * cell[1] + (c >> 1 & 1), 2 * cell[2] + (c & 1)), kids[c])
 
     visit(0, (0, 0, 0), list(range(n)))
-    return bytes(occ), np.array(order, np.int64), depth, corner, S
+    return bytes(occ), np.array(order, np.int64), depth, corner, S, dups
 
 
 def quantised_attributes(scene, order, p):
@@ -141,34 +147,39 @@ def quantised_attributes(scene, order, p):
     return out
 
 
-def serialise(n, corner, S, p, occ: bytes, attrs: dict) -> bytes:
+def serialise(n, corner, S, p, occ: bytes, dups, attrs: dict) -> bytes:
     head = MAGIC + struct.pack("<II", VERSION, n) + struct.pack("<4d", *corner, S)
     head += struct.pack("<4d", p["sf_scale"], p["sf_rotation"], p["sf_opacity"], p["sf_sh"])
+    table = struct.pack("<I", len(dups)) + b"".join(struct.pack("<II", o, c) for o, c in dups)
     body = b"".join(attrs[k].astype("<i4").tobytes() for k in ("scale", "rotation", "opacity", "sh"))
-    return head + struct.pack("<I", len(occ)) + occ + body
+    return head + struct.pack("<I", len(occ)) + occ + table + body
 
 
 def encode(scene, eyes, q: float = 0.5, p: dict | None = None) -> dict:
     p = p or params(q)
-    occ, order, depth, corner, S = build_octree(scene.means, eyes, p)
+    occ, order, depth, corner, S, dups = build_octree(scene.means, eyes, p)
     attrs = quantised_attributes(scene, order, p)
-    raw = serialise(scene.n, corner, S, p, occ, attrs)
+    raw = serialise(scene.n, corner, S, p, occ, dups, attrs)
     return {"raw": raw, "compressed": zlib.compress(raw, 9), "occupancy": occ, "order": order, "depth": depth,
-            "corner": corner, "S": S, "attrs": attrs}
+            "corner": corner, "S": S, "attrs": attrs, "dups": dups}
 
 
-def decode_positions(occ: bytes, corner, S):
-    """Leaf centres (one per splat, in stream order) and leaf depths from the node bytes."""
+def decode_positions(occ: bytes, corner, S, dups=()):
+    """Leaf centres (one per splat, in stream order) and leaf depths from the node bytes and
+    the shared-leaf table."""
+    extra = dict(dups)
     out, depths = [], []
     pos = [0]
+    leaf = [0]
 
     def visit(d, cell):
         b = occ[pos[0]]
         pos[0] += 1
-        if d == DEPTH or b == 0:
-            for _ in range(b + 1 if d == DEPTH else 1):
+        if b == 0:
+            for _ in range(1 + extra.get(leaf[0], 0)):
                 out.append(centre(corner, S, cell, d))
                 depths.append(d)
+            leaf[0] += 1
             return
         for c in range(8):
             if b >> c & 1:
@@ -187,9 +198,11 @@ def decode(stream: bytes) -> dict:
     sf_scale, sf_rot, sf_op, sf_sh = struct.unpack_from("<4d", raw, 44)
     (n_occ,) = struct.unpack_from("<I", raw, 76)
     occ = raw[80:80 + n_occ]
+    (n_dup,) = struct.unpack_from("<I", raw, 80 + n_occ)
+    dups = [struct.unpack_from("<II", raw, 84 + n_occ + 8 * i) for i in range(n_dup)]
     corner = np.array([c0, c1, c2])
-    pos, depths = decode_positions(occ, corner, S)
-    body = np.frombuffer(raw[80 + n_occ:], "<i4").astype(np.int64)
+    pos, depths = decode_positions(occ, corner, S, dups)
+    body = np.frombuffer(raw[84 + n_occ + 8 * n_dup:], "<i4").astype(np.int64)
     off = 0
 
     def take(rows):

@@ -20,12 +20,45 @@ def test_two_splats_hand_worked_stream():
     means = np.array([[0.0, 1.0], [0.0, 1.0], [0.0, 1.0]], np.float32)
     eyes = [np.array([0.5, 0.5, 1000.0])]
     p = codec.params(0.5)
-    occ, order, depth, corner, S = codec.build_octree(means, eyes, p)
-    assert occ == bytes([0x81, 0x01, 0x01, 0x01, 0x00, 0x80, 0x80, 0x80, 0x00])
+    occ, order, depth, corner, S, dups = codec.build_octree(means, eyes, p)
+    assert not dups and occ == bytes([0x81, 0x01, 0x01, 0x01, 0x00, 0x80, 0x80, 0x80, 0x00])
     assert list(order) == [0, 1] and list(depth) == [4, 4]
     pos, dep = codec.decode_positions(occ, corner, S)
     np.testing.assert_allclose(pos[:, 0], [1 / 32] * 3)
     np.testing.assert_allclose(pos[:, 1], [1 - 1 / 32] * 3)
+
+
+def test_coincident_splats_share_a_depth_limit_leaf_listed_in_the_table():
+    """Splats 0 and 1 coincide at the cube's corner (0,0,0), splat 2 sits at (1,1,1): the root has
+    children 0 and 7; splats 0 and 1 split down to depth 21 (20 single-child bytes 0x01, then a
+    leaf), and that leaf -- the first in depth-first order -- holds one extra splat, so the table
+    reads (0, 1); splat 2 ends at depth 4 as in the two-splat stream.  The serialised stream
+    carries the node count, the nodes, the table size and the pair, little-endian."""
+    means = np.array([[0.0, 0.0, 1.0], [0.0, 0.0, 1.0], [0.0, 0.0, 1.0]], np.float32)
+    eyes = [np.array([0.5, 0.5, 1000.0])]
+    p = codec.params(0.5)
+    occ, order, depth, corner, S, dups = codec.build_octree(means, eyes, p)
+    want = bytes([0x81] + [0x01] * 20 + [0x00] + [0x80] * 3 + [0x00])
+    assert occ == want and dups == [(0, 1)]
+    assert list(order) == [0, 1, 2] and list(depth) == [21, 21, 4]
+    pos, dep = codec.decode_positions(occ, corner, S, dups)
+    np.testing.assert_allclose(pos[:, 0], [0.5 / 2 ** 21] * 3)
+    np.testing.assert_allclose(pos[:, 1], pos[:, 0])
+    np.testing.assert_allclose(pos[:, 2], [1 - 1 / 32] * 3)
+    assert list(dep) == [21, 21, 4]
+
+    class Sc:
+        n = 3
+    sc = Sc()
+    sc.means = means
+    sc.log_scales = np.zeros((3, 3), np.float32)
+    sc.quats = np.tile(np.array([[1.0], [0.0], [0.0], [0.0]], np.float32), (1, 3))
+    sc.opacity_logits = np.zeros(3, np.float32)
+    sc.sh = np.zeros((16, 3, 3), np.float32)
+    raw = codec.encode(sc, eyes, p=p)["raw"]
+    assert raw[76:80] == (len(want)).to_bytes(4, "little") and raw[80:80 + len(want)] == want
+    assert raw[80 + len(want):80 + len(want) + 12] == bytes([1, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0])
+    assert len(raw) == 80 + len(want) + 12 + 4 * 55 * 3
 
 
 def test_round_trip_honours_the_precision_criterion_and_the_quantisers():
@@ -97,8 +130,10 @@ def test_splitting_equals_the_sorted_formulation():
         means = rng.uniform(-1, 1, (3, n)).astype(np.float32)
         if n > 10:
             means[:, 5] = means[:, 3]  # two splats in one cell: split to the depth limit
-        occ, order, depth, corner, S = codec.build_octree(means, eyes, p)
+        occ, order, depth, corner, S, dups = codec.build_octree(means, eyes, p)
         o2, d2 = _sorted_formulation(means, eyes, p)
         assert np.array_equal(order, o2) and np.array_equal(depth, d2), n
         if n > 10:
-            assert depth[5] == codec.DEPTH and depth[3] == codec.DEPTH
+            assert depth[5] == codec.DEPTH and depth[3] == codec.DEPTH and len(dups) == 1 and dups[0][1] == 1
+            pos, dep = codec.decode_positions(occ, corner, S, dups)
+            assert pos.shape[1] == n
