@@ -34,6 +34,9 @@ Readings (the section is silent on them):
     normalised quaternion with w >= 0 (sign flipped otherwise), x, y, z stored; SH: 48
     coefficients, DC (planes 0-2) as differences of consecutive splats' quantised values in
     stream order (the first against 0);
+  * decoding to a scene: the opacity logit is log(o / (1 - o)) of the dequantised opacity
+    clamped to [1e-6, 1 - 1e-6] (the off-centre reconstruction can exceed 1), and the
+    quaternion's real part is sqrt(max(0, 1 - x^2 - y^2 - z^2));
   * stream: little-endian; header (magic 'POTR', version, n, corner (3 x f64), S (f64), the
     four SF (f64)); the number of node bytes (u32) and the node bytes; the number of shared
     leaves (u32) and their (ordinal, count - 1) pairs (u32); then property after property over the splats in
@@ -216,5 +219,8 @@ def decode(stream: bytes) -> dict:
     sh[:3] = np.cumsum(sh[:3], axis=1)
     xyz = rot / sf_rot
     w = np.sqrt(np.maximum(0.0, 1.0 - (xyz ** 2).sum(axis=0)))
+    opacity = (op[0] + 0.25) / sf_op
+    oc = np.clip(opacity, 1e-6, 1.0 - 1e-6)
     return {"means": pos, "depths": depths, "log_scales": scale / sf_scale, "quats": np.vstack([w, xyz]),
-            "opacity": (op[0] + 0.25) / sf_op, "sh": (sh / sf_sh).reshape(16, 3, n)}
+            "opacity": opacity, "opacity_logits": np.log(oc / (1.0 - oc)), "sh": (sh / sf_sh).reshape(16, 3, n),
+            "n_nodes": n_occ, "n_dups": n_dup}

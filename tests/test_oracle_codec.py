@@ -76,6 +76,8 @@ def test_round_trip_honours_the_precision_criterion_and_the_quantisers():
     assert np.max(np.abs(d["sh"] - sc.sh[:, :, o])) <= 0.5 / p["sf_sh"] + 1e-9
     op = 1.0 / (1.0 + np.exp(-sc.opacity_logits[o].astype(np.float64)))
     assert np.max(np.abs(d["opacity"] - op)) <= 0.75 / p["sf_opacity"] + 1e-12
+    sig = 1.0 / (1.0 + np.exp(-d["opacity_logits"]))
+    assert np.max(np.abs(sig - np.clip(d["opacity"], 1e-6, 1 - 1e-6))) < 1e-12
     q = sc.quats[:, o].astype(np.float64)
     q = q / np.linalg.norm(q, axis=0)
     q = np.where(q[0] < 0, -q, q)
@@ -137,3 +139,48 @@ def test_splitting_equals_the_sorted_formulation():
             assert depth[5] == codec.DEPTH and depth[3] == codec.DEPTH and len(dups) == 1 and dups[0][1] == 1
             pos, dep = codec.decode_positions(occ, corner, S, dups)
             assert pos.shape[1] == n
+
+
+def _parallel_parse(occ: bytes, corner, S, dups):
+    """Leaf centres from the node bytes without recursion: e_i = sum_{j<i} (c_j - 1) (c_j the
+    children of node j) counts the pending subtrees when node i is met; node i's parent is the
+    last j < i with e_j <= e_i, and it is that parent's child number e_j + c_j - 1 - e_i."""
+    c = [bin(b).count("1") for b in occ]
+    e = np.concatenate([[0], np.cumsum(np.array(c) - 1)])
+    assert e[-1] == -1 and np.all(e[:-1] >= 0)
+    m = len(occ)
+    par, octant = [0] * m, [0] * m
+    for i in range(1, m):
+        j = max(j for j in range(i) if e[j] <= e[i])
+        r = e[j] + c[j] - 1 - e[i]
+        bits = [k for k in range(8) if occ[j] >> k & 1]
+        par[i], octant[i] = j, bits[r]
+    extra = dict(dups)
+    out, ordinal = [], 0
+    for i in range(m):
+        if occ[i]:
+            continue
+        cell, d, k = [0, 0, 0], 0, i
+        while k:
+            o = octant[k]
+            cell = [cell[0] | (o >> 2 & 1) << d, cell[1] | (o >> 1 & 1) << d, cell[2] | (o & 1) << d]
+            d += 1
+            k = par[k]
+        out += [codec.centre(corner, S, cell, d)] * (1 + extra.get(ordinal, 0))
+        ordinal += 1
+    return np.array(out).T
+
+
+def test_parallel_parse_formulation_equals_the_recursive_decode():
+    rng = np.random.default_rng(5)
+    eyes = [np.array([2.0, 0.1, 0.3])]
+    for n, q in ((1, 0.5), (2, 0.5), (40, 0.2), (300, 0.9)):
+        means = rng.uniform(-1, 1, (3, n)).astype(np.float32)
+        if n > 10:
+            means[:, 9] = means[:, 4]
+            means[:, 21] = means[:, 4]
+            means[:, 30] = means[:, 12]
+        occ, order, depth, corner, S, dups = codec.build_octree(means, eyes, codec.params(q))
+        want, _ = codec.decode_positions(occ, corner, S, dups)
+        got = _parallel_parse(occ, corner, S, dups)
+        assert np.array_equal(got, want), n
