@@ -553,7 +553,7 @@ def codec_run(args, dev, D, scene_d, alive, sh_rgb, cams, q: float) -> dict:
 
     from oracle import codec as ocodec
     from oracle.sh_compact import camera_centre
-    from paper_2601_14821_gb300.codec import Encoder, params
+    from paper_2601_14821_gb300.codec import Decoder, Encoder, params
 
     keep = torch.nonzero(alive, as_tuple=False).flatten()
     sub = {k: t[..., keep].contiguous() for k, t in scene_d.items() if k != "sh"}
@@ -578,9 +578,26 @@ def codec_run(args, dev, D, scene_d, alive, sh_rgb, cams, q: float) -> dict:
     packed = zlib.compress(raw, 6)
     host_ms = (time.perf_counter() - t0) * 1e3
     n = int(keep.numel())
+    m, n_dups = enc.sizes()
+    # the decoder on the encoder's device outputs (the decode half of a fine-tuning cycle)
+    dec = Decoder(m, n, dev)
+    cube = enc.cube.tolist()
+    dec.run(enc.nodes, enc.dups, n_dups, enc.attrs, cube, p)
+    torch.cuda.synchronize()
+    dec.check()
+    a.record()
+    for _ in range(reps):
+        dec.run(enc.nodes, enc.dups, n_dups, enc.attrs, cube, p)
+    b.record()
+    torch.cuda.synchronize()
+    dec_ms = D.max_over_ranks(a.elapsed_time(b), dev) / reps
+    t0 = time.perf_counter()
+    zlib.decompress(packed)
+    unzip_ms = (time.perf_counter() - t0) * 1e3
     out = {"splats": n, "device_ms": ms, "device_splats_per_s": n / (ms / 1e3), "host_stream_and_zlib_ms": host_ms,
+           "decode_device_ms": dec_ms, "decode_device_splats_per_s": n / (dec_ms / 1e3), "host_unzip_ms": unzip_ms,
            "raw_bytes": len(raw), "compressed_bytes": len(packed), "bytes_per_splat": len(packed) / n,
-           "node_bytes": int(enc.n_nodes.item()), "q": q}
+           "node_bytes": m, "shared_leaves": n_dups, "q": q}
     if D.env_ranks()[0] == 0 and not args.no_cpu_baseline:
         import synth
 

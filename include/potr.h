@@ -47,7 +47,8 @@ enum {
   POTR_ERR_TIMEOUT = 4,  /* device: a bounded wait ran out */
   POTR_ERR_NUMERIC = 5,
   POTR_ERR_UNSUPPORTED = 6,
-  POTR_ERR_TOO_LARGE = 7 /* a size exceeds potr_bin_sort_static's fixed scratch */
+  POTR_ERR_TOO_LARGE = 7, /* a size exceeds potr_bin_sort_static's fixed scratch */
+  POTR_ERR_CORRUPT = 8    /* device: a malformed codec stream (potr_codec_decode) */
 };
 
 /* Device-side status word; zero it before the calls that may write it. */
@@ -422,7 +423,7 @@ typedef struct {
   double sf_scale, sf_rotation, sf_opacity, sf_sh, beta, gamma;
 } potr_codec_params;
 
-/* Workspace bytes of potr_codec_encode for n splats (about 130 n). */
+/* Workspace bytes of potr_codec_encode for n splats (about 150 n). */
 POTR_API size_t potr_codec_workspace_size(int64_t n);
 
 /*
@@ -432,8 +433,10 @@ POTR_API size_t potr_codec_workspace_size(int64_t n);
  * 21; child octant c = (x bit << 2) | (y bit << 1) | z bit.  A cell is split while it holds
  * several splats or its single splat is not within the tolerance of the cell centre (binary64).
  * Outputs (device): d_nodes [<= 22 n] the node bytes in depth-first order -- an internal node
- * its child octant mask, a leaf 0, a leaf at depth 21 its splat count - 1 -- and *d_n_nodes
- * their number; d_order [n] the splats in that leaf order (ties by index); d_attrs [55][n]
+ * its child octant mask, every leaf 0 -- and *d_n_nodes their number; d_dups [n] (room for n/2
+ * pairs) the leaves that hold several (coincident) splats, which only a depth-21 leaf can, as
+ * (leaf ordinal in depth-first order, splat count - 1) pairs in ascending ordinal, and
+ * *d_n_dups their number; d_order [n] the splats in that leaf order (ties by index); d_attrs [55][n]
  * int32, in that order, property after property: floor(1/2 + x SF) of the 3 log-scales, of x,
  * y, z of the normalised quaternion made to have w >= 0, of sigmoid(opacity logit), and of the
  * 48 SH values (coefficient-major; planes 0-2, the DC, as differences from the previous splat);
@@ -442,7 +445,33 @@ POTR_API size_t potr_codec_workspace_size(int64_t n);
  */
 POTR_API potr_status potr_codec_encode(const potr_scene* scene, const double* d_eyes, int32_t n_eyes,
                                        const potr_codec_params* params, uint8_t* d_nodes, uint32_t* d_n_nodes,
-                                       uint32_t* d_order, int32_t* d_attrs, double* d_cube,
+                                       uint32_t* d_dups, uint32_t* d_n_dups, uint32_t* d_order, int32_t* d_attrs,
+                                       double* d_cube, potr_device_status* d_status, void* d_ws, size_t ws_bytes,
+                                       potr_stream_t stream);
+
+/* Workspace bytes of potr_codec_decode for a stream of n_nodes node bytes and n splats
+ * (about 22 n_nodes + 26 n). */
+POTR_API size_t potr_codec_decode_workspace_size(int64_t n_nodes, int64_t n);
+
+/*
+ * The decoder's device part: the inverse of potr_codec_encode (Section IV-E; dequantisation
+ * x~ = x^ / SF, opacity x~ = (x^ + 1/4) / SF).  Inputs (device): d_nodes [n_nodes] the node
+ * bytes, d_dups [2 n_dups] the shared-leaf pairs, d_attrs [55][n] the quantised attributes in
+ * stream order; (host) cube [4] corner x, y, z and edge, params (only the four SF are used).
+ * Output: the scene in stream order, written to the planes of *out (device, float32): means =
+ * the centres of the splats' leaf cells, corner + (cell + 1/2) edge / 2^depth in binary64;
+ * log-scales; quaternion (w, x, y, z) with w = sqrt(max(0, 1 - x^2 - y^2 - z^2)); opacity
+ * logit log(o / (1 - o)) of the dequantised opacity clamped to [1e-6, 1 - 1e-6]; the 48 SH
+ * values, DC as running sums of the stored differences.  A malformed stream (a node sequence
+ * that is not one complete tree of depth <= 21, table entries out of order or out of range,
+ * leaf and splat counts that disagree with n) writes POTR_ERR_CORRUPT to *d_status (nullable)
+ * and leaves the affected outputs unspecified; nothing is read or written out of bounds.
+ * INVALID_ARGUMENT for null pointers, n_nodes <= 0, n <= 0, n_dups outside [0, n/2], a scale
+ * factor or edge <= 0, or a short workspace; UNSUPPORTED if n_nodes >= 2^31 or 55 n >= 2^31.
+ */
+POTR_API potr_status potr_codec_decode(const uint8_t* d_nodes, int64_t n_nodes, const uint32_t* d_dups,
+                                       int64_t n_dups, const int32_t* d_attrs, int64_t n, const double* cube,
+                                       const potr_codec_params* params, const potr_scene_grads* out,
                                        potr_device_status* d_status, void* d_ws, size_t ws_bytes,
                                        potr_stream_t stream);
 

@@ -25,6 +25,7 @@ POTR_ERR_TIMEOUT = 4
 POTR_ERR_NUMERIC = 5
 POTR_ERR_UNSUPPORTED = 6
 POTR_ERR_TOO_LARGE = 7
+POTR_ERR_CORRUPT = 8
 POTR_STATIC_MAX_INSTANCES = 4194304
 POTR_STATIC_MAX_VIEW_SPLATS = 1048576
 
@@ -112,8 +113,11 @@ SIGNATURES = {
     "potr_sh_compact": (_I32, [C.POINTER(Scene), C.POINTER(Frame), _P, C.c_double, C.c_double, C.c_double, _P, _P,
                                _P, _P]),
     "potr_codec_workspace_size": (_SZ, [_I64]),
-    "potr_codec_encode": (_I32, [C.POINTER(Scene), _P, _I32, C.POINTER(CodecParams), _P, _P, _P, _P, _P, _P, _P, _SZ,
-                                 _P]),
+    "potr_codec_encode": (_I32, [C.POINTER(Scene), _P, _I32, C.POINTER(CodecParams), _P, _P, _P, _P, _P, _P, _P, _P,
+                                 _P, _SZ, _P]),
+    "potr_codec_decode_workspace_size": (_SZ, [_I64, _I64]),
+    "potr_codec_decode": (_I32, [_P, _I64, _P, _I64, _P, _I64, C.POINTER(C.c_double), C.POINTER(CodecParams),
+                                 C.POINTER(SceneGrads), _P, _P, _SZ, _P]),
     "potr_adam_step": (_I32, [C.POINTER(SceneGrads), C.POINTER(SceneGrads), C.POINTER(SceneGrads),
                               C.POINTER(SceneGrads), _I64, _I64, C.POINTER(C.c_float), C.c_float, C.c_float, C.c_float,
                               _P]),
@@ -313,8 +317,22 @@ def potr_codec_workspace_size(n: int) -> int:
     return int(lib().potr_codec_workspace_size(n))
 
 
-def potr_codec_encode(scene: Scene, eyes, n_eyes: int, params: CodecParams, nodes, n_nodes, order, attrs, cube,
-                      status, ws, stream=None):
+def potr_codec_encode(scene: Scene, eyes, n_eyes: int, params: CodecParams, nodes, n_nodes, dups, n_dups, order,
+                      attrs, cube, status, ws, stream=None):
     _check("potr_codec_encode", lib().potr_codec_encode(C.byref(scene), ptr(eyes), int(n_eyes), C.byref(params),
-                                                        ptr(nodes), ptr(n_nodes), ptr(order), ptr(attrs), ptr(cube),
+                                                        ptr(nodes), ptr(n_nodes), ptr(dups), ptr(n_dups), ptr(order),
+                                                        ptr(attrs), ptr(cube), ptr(status), ptr(ws), ws.numel(),
+                                                        stream_handle(stream)))
+
+
+def potr_codec_decode_workspace_size(n_nodes: int, n: int) -> int:
+    return int(lib().potr_codec_decode_workspace_size(n_nodes, n))
+
+
+def potr_codec_decode(nodes, n_nodes: int, dups, n_dups: int, attrs, n: int, cube, params: CodecParams, out: dict,
+                      status, ws, stream=None):
+    """cube: four host floats (corner x, y, z, edge); out: dict of scene-shaped device tensors."""
+    cb = (C.c_double * 4)(*[float(x) for x in cube])
+    _check("potr_codec_decode", lib().potr_codec_decode(ptr(nodes), int(n_nodes), ptr(dups), int(n_dups), ptr(attrs),
+                                                        int(n), cb, C.byref(params), C.byref(grads_struct(out)),
                                                         ptr(status), ptr(ws), ws.numel(), stream_handle(stream)))

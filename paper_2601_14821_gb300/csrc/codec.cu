@@ -14,21 +14,15 @@
 // children's octants: each splat sets its own nodes' bits, and the one bit it adds to the node
 // at depth L_i it shares with earlier splats goes to the node created by the last splat j < i
 // with L_j < L_i (found by a backward search inside blocks of 1024 splats and a per-level
-// running maximum over blocks).  Leaves write 0; a leaf at depth D writes its splat count - 1.
+// running maximum over blocks).  Every leaf writes 0; a depth-D leaf that holds several
+// (coincident) splats goes into a table of (leaf ordinal, count - 1) pairs, compacted with one
+// scan of packed (leaf, shared-leaf) flags.
+#include "codec_common.cuh"
 #include "radix.cuh"
 #include "scan.cuh"
 
 namespace potr {
 namespace {
-
-constexpr int kDepth = 21;
-constexpr int kChunkCodec = 1024;  // splats per block of the backward search
-constexpr int kLevels = kDepth + 1;
-
-struct Cube {
-  double corner[3];
-  double S;
-};
 
 __device__ __forceinline__ double atomic_min_d(double* a, double v) {
   unsigned long long* p = reinterpret_cast<unsigned long long*>(a);
@@ -189,11 +183,10 @@ __global__ void __launch_bounds__(256) codec_depth_kernel(int64_t n, const uint3
     int d = min(max(L, R) + 1, kDepth);
     const uint32_t X = compact3(code >> 2), Y = compact3(code >> 1), Z = compact3(code);
     for (; d < kDepth; ++d) {
-      const double w = __ddiv_rn(c.S, (double)(1u << d));
       const int sh = kDepth - d;  // cell at depth d = full-depth cell >> (D - d)
-      const double px = __dadd_rn(c.corner[0], __dmul_rn(__dadd_rn((double)(X >> sh), 0.5), w));
-      const double py = __dadd_rn(c.corner[1], __dmul_rn(__dadd_rn((double)(Y >> sh), 0.5), w));
-      const double pz = __dadd_rn(c.corner[2], __dmul_rn(__dadd_rn((double)(Z >> sh), 0.5), w));
+      const double px = cell_centre(c.corner[0], c.S, X >> sh, d);
+      const double py = cell_centre(c.corner[1], c.S, Y >> sh, d);
+      const double pz = cell_centre(c.corner[2], c.S, Z >> sh, d);
       const double ddx = __dsub_rn(mx, px), ddy = __dsub_rn(my, py), ddz = __dsub_rn(mz, pz);
       const double dist = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz)));
       if (dist < t) break;
@@ -225,20 +218,8 @@ __global__ void __launch_bounds__(256) codec_chunk_last_kernel(int64_t n, const 
   }
 }
 
-// Exclusive running maximum over blocks, per level (one thread per level).
-__global__ void codec_chunk_prefix_kernel(int64_t n_chunks, int* __restrict__ last) {
-  const int t = threadIdx.x;
-  if (t >= kLevels) return;
-  int run = -1;
-  for (int64_t c = 0; c < n_chunks; ++c) {
-    const int x = last[c * kLevels + t];
-    last[c * kLevels + t] = run;
-    run = max(run, x);
-  }
-}
-
-// Node bytes: every splat sets the octant bits of its own internal nodes, its leaf byte, and the
-// bit it adds to the node at depth L_i created by an earlier splat.
+// Node bytes: every splat sets the octant bits of its own internal nodes (its leaf stays 0) and
+// the bit it adds to the node at depth L_i created by an earlier splat.
 __global__ void __launch_bounds__(256) codec_nodes_kernel(int64_t n, const uint32_t* __restrict__ lo,
                                                           const uint32_t* __restrict__ hi, const int8_t* __restrict__ L,
                                                           const int8_t* __restrict__ D, const uint32_t* __restrict__ off,
@@ -251,13 +232,6 @@ __global__ void __launch_bounds__(256) codec_nodes_kernel(int64_t n, const uint3
     const uint64_t code = code_at(lo, hi, i);
     const uint32_t o = off[i];
     for (int d = li + 1; d < di; ++d) atomicOr(&node[o + (d - li - 1)], 1u << digit_at(code, d));
-    uint32_t leaf = 0;
-    if (di == kDepth) {  // splats sharing this depth-limit cell follow it
-      int64_t j = i + 1;
-      while (j < n && L[j] == kDepth) ++j;
-      leaf = (uint32_t)(j - i - 1);
-    }
-    node[o + (di - 1 - li)] = leaf;
     if (li >= 0) {
       // the node at depth li on this path: created by the last j < i with L_j < li
       int64_t j = i - 1;
@@ -268,6 +242,38 @@ __global__ void __launch_bounds__(256) codec_nodes_kernel(int64_t n, const uint3
       atomicOr(&node[id], 1u << digit_at(code, li));
     }
   }
+}
+
+// Per sorted position: bit 0 -- it opens a leaf (it shares no depth-limit cell with its
+// predecessor); bit 32 -- that leaf is at the depth limit and the next splat shares it.
+__global__ void __launch_bounds__(256) codec_leaf_flags_kernel(int64_t n, const int8_t* __restrict__ L,
+                                                               const int8_t* __restrict__ D,
+                                                               uint64_t* __restrict__ flags) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const bool opens = L[i] != kDepth;
+    const bool shared = opens && D[i] == kDepth && i + 1 < n && L[i + 1] == kDepth;
+    flags[i] = (uint64_t)opens | ((uint64_t)shared << 32);
+  }
+}
+
+// The shared-leaf table: (leaf ordinal, splat count - 1) at the slot the packed scan gives.
+__global__ void __launch_bounds__(256) codec_dups_kernel(int64_t n, const int8_t* __restrict__ L,
+                                                         const uint64_t* __restrict__ flags,
+                                                         const uint64_t* __restrict__ excl,
+                                                         uint32_t* __restrict__ dups) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!(flags[i] >> 32)) continue;
+    int64_t j = i + 1;
+    while (j < n && L[j] == kDepth) ++j;
+    const uint64_t e = excl[i];
+    const uint32_t slot = (uint32_t)(e >> 32);
+    dups[2 * (size_t)slot] = (uint32_t)e;
+    dups[2 * (size_t)slot + 1] = (uint32_t)(j - i - 1);
+  }
+}
+
+__global__ void store_high_word_kernel(const uint64_t* __restrict__ total, uint32_t* __restrict__ out) {
+  *out = (uint32_t)(*total >> 32);
 }
 
 __global__ void __launch_bounds__(256) pack_bytes_kernel(const uint32_t* __restrict__ total, const uint32_t* __restrict__ node,
@@ -312,7 +318,7 @@ size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct CodecLayout {
   size_t mm, cube, lo, hi, lo2, hi2, v, v2, tol, L, D, cnt, off, scan, total, chunk, node, status, ghist, gbase,
-      counter, bytes;
+      counter, flags, fscan, bytes;
   int64_t blocks, n_chunks;
 };
 
@@ -344,13 +350,15 @@ CodecLayout codec_layout(int64_t n) {
   L.cnt = o; o = al(o + 4 * (size_t)n);
   L.off = o; o = al(o + 4 * (size_t)n);
   L.scan = o; o = al(o + 8 * (size_t)scan_words_for(n));
-  L.total = o; o = al(o + 8);
+  L.total = o; o = al(o + 16);
   L.chunk = o; o = al(o + 4 * (size_t)L.n_chunks * kLevels);
   L.node = o; o = al(o + 4 * (size_t)n * (kDepth + 1));
   L.status = o; o = al(o + 8 * 256 * (size_t)L.blocks);
   L.ghist = o; o = al(o + 4 * 256 * 8);
   L.gbase = o; o = al(o + 4 * 256 * 8);
   L.counter = o; o = al(o + 4 * 8);
+  L.flags = o; o = al(o + 8 * (size_t)n);
+  L.fscan = o; o = al(o + 8 * (size_t)n);
   L.bytes = o;
   return L;
 }
@@ -365,11 +373,12 @@ extern "C" size_t potr_codec_workspace_size(int64_t n) {
 
 extern "C" potr_status potr_codec_encode(const potr_scene* scene, const double* d_eyes, int32_t n_eyes,
                                          const potr_codec_params* params, uint8_t* d_nodes, uint32_t* d_n_nodes,
-                                         uint32_t* d_order, int32_t* d_attrs, double* d_cube,
+                                         uint32_t* d_dups, uint32_t* d_n_dups, uint32_t* d_order, int32_t* d_attrs, double* d_cube,
                                          potr_device_status* d_status, void* d_ws, size_t ws_bytes,
                                          potr_stream_t stream) {
   using namespace potr;
-  if (!scene || !d_eyes || n_eyes < 1 || !params || !d_nodes || !d_n_nodes || !d_order || !d_attrs || !d_ws)
+  if (!scene || !d_eyes || n_eyes < 1 || !params || !d_nodes || !d_n_nodes || !d_dups || !d_n_dups || !d_order ||
+      !d_attrs || !d_ws)
     return POTR_ERR_INVALID_ARGUMENT;
   if (!scene->means || !scene->log_scales || !scene->quats || !scene->opacity_logits || !scene->sh)
     return POTR_ERR_INVALID_ARGUMENT;
@@ -395,6 +404,7 @@ extern "C" potr_status potr_codec_encode(const potr_scene* scene, const double* 
   uint32_t* ghist = reinterpret_cast<uint32_t*>(ws + L.ghist);
   uint32_t* gbase = reinterpret_cast<uint32_t*>(ws + L.gbase);
   uint32_t* counter = reinterpret_cast<uint32_t*>(ws + L.counter);
+  uint64_t *flags = reinterpret_cast<uint64_t*>(ws + L.flags), *fscan = reinterpret_cast<uint64_t*>(ws + L.fscan);
   const int g = (int)(cdiv(n, 256) < 152 * 16 ? cdiv(n, 256) : 152 * 16);
   if (cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)onesweep_smem_bytes()) !=
       cudaSuccess)
@@ -457,10 +467,18 @@ extern "C" potr_status potr_codec_encode(const potr_scene* scene, const double* 
     if (scan_exclusive<uint32_t, uint32_t>(cnt, off, n, total, scan_ws, s) != cudaSuccess) return POTR_ERR_CUDA;
     codec_chunk_last_kernel<<<(unsigned)L.n_chunks, 256, 0, s>>>(n, Ls, chunk);
     POTR_CHECK_LAUNCH();
-    codec_chunk_prefix_kernel<<<1, 32, 0, s>>>(L.n_chunks, chunk);
+    prefix_max_columns_kernel<<<kLevels, 256, 0, s>>>(L.n_chunks, kLevels, chunk);
     POTR_CHECK_LAUNCH();
     if (cudaMemsetAsync(node, 0, 4 * (size_t)n * (kDepth + 1), s) != cudaSuccess) return POTR_ERR_CUDA;
     codec_nodes_kernel<<<g, 256, 0, s>>>(n, ls, hs, Ls, Ds, off, chunk, node);
+    POTR_CHECK_LAUNCH();
+    // the shared-leaf table
+    codec_leaf_flags_kernel<<<g, 256, 0, s>>>(n, Ls, Ds, flags);
+    POTR_CHECK_LAUNCH();
+    if (scan_exclusive<uint64_t, uint64_t>(flags, fscan, n, total + 1, scan_ws, s) != cudaSuccess) return POTR_ERR_CUDA;
+    codec_dups_kernel<<<g, 256, 0, s>>>(n, Ls, flags, fscan, d_dups);
+    POTR_CHECK_LAUNCH();
+    store_high_word_kernel<<<1, 1, 0, s>>>(total + 1, d_n_dups);
     POTR_CHECK_LAUNCH();
   }
   if (cudaMemcpyAsync(d_n_nodes, total, 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return POTR_ERR_CUDA;

@@ -528,6 +528,7 @@ extern "C" const char* potr_status_string(potr_status status) {
     case POTR_ERR_NUMERIC: return "non-finite input";
     case POTR_ERR_UNSUPPORTED: return "unsupported configuration";
     case POTR_ERR_TOO_LARGE: return "size exceeds the fixed scratch of potr_bin_sort_static";
+    case POTR_ERR_CORRUPT: return "malformed codec stream";
     default: return "unknown status";
   }
 }

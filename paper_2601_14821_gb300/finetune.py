@@ -81,3 +81,25 @@ class FineTuner:
         for it in range(iterations):
             self.step(int(views[it % len(views)]))
         return float(self.loss.item())
+
+
+def potr_ft(scene: dict, cams_rec: np.ndarray, targets: list, eyes, q: float = 0.5, cycles: int = 2,
+            iterations: int = 500, lam: float = 0.2, extent: float = 1.0, seed: int = 0, **cfg) -> dict:
+    """POTR-FT (Section IV-F): ``cycles`` rounds of decode -> fine-tune -> encode, every step on the
+    device (the codec's zlib stage is lossless and is applied once, to the final bitstream).  The
+    scene must hold only live splats (compact a pruned scene first).  Returns the final
+    bitstream (raw and compressed), the fine-tuned scene before its last encoding, and the loss
+    after each cycle's fine-tuning."""
+    from .codec import encode, params, roundtrip
+
+    p = params(q)
+    losses = []
+    for c in range(cycles):
+        decoded, _ = roundtrip(scene, eyes, p=p)
+        ft = FineTuner(decoded, cams_rec, targets, lam=lam, extent=extent, device=scene["means"].device, **cfg)
+        losses.append(ft.run(iterations, seed=seed + c))
+        scene = ft.scene
+    out = encode(scene, eyes, p=p)
+    out["scene"] = scene
+    out["losses"] = losses
+    return out
