@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--views", type=int, default=0, help="use only the first V views (profiling cases)")
     ap.add_argument("--only-batched", action="store_true", help="time the batched frame only (profiling cases)")
     ap.add_argument("--only-fwdbwd", action="store_true", help="time the fine-tuning step only (profiling case)")
+    ap.add_argument("--only-pruning", action="store_true",
+                    help="run the pruning, SH compaction, codec and POTR-FT section only (profiling case)")
     ap.add_argument("--large", action="store_true",
                     help="also time the 6M-splat, 300-view 1920x1080 workload (several minutes)")
     ap.add_argument("--no-multiview", action="store_true", help="skip the 3M-splat, 200-view workload")
@@ -184,6 +186,11 @@ def run_ours(args):
         out = fwd_bwd_step_ms(args, dev, D)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "fwd_bwd": out, "profiling_case": True}))
+        return
+    if args.only_pruning:
+        out = prune_run(args, dev, D)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "pruning": out, "profiling_case": True}))
         return
     w = synth.workload(WORKLOAD)
     if args.views:
@@ -533,13 +540,14 @@ def prune_run(args, dev, D, q: float = 0.5, iterations: int = 48) -> dict:
     torch.cuda.synchronize()
     sh = sh_compaction_run(args, dev, D, be.frames[0], targets, q)
     enc = codec_run(args, dev, D, scene_d, ctrl.alive, sh.pop("_sh_rgb"), w.cameras, q)
+    ft = potr_ft_run(args, dev, D, enc.pop("_scene"), w.cameras, targets, q)
     return {"workload": "scene: 1M splats, 16 views 1280x720, targets = render of the unpruned scene",
             "q": q, "dmse_max": ctrl.dmse_max, "iterations": iterations,
             "ms_per_iteration": total_ms / iterations, "controller_ms_per_iteration": ctrl_ms,
             "iteration_ms": [round(x, 3) for x in per_it[:3] + per_it[-2:]],
             "splats_before": n, "splats_after": counts[-1], "alive_after_iteration": counts[:8] + counts[-2:],
             "instances_before": int(inst0), "instances_after": be.frames[0].instance_count(),
-            "sh_compaction": sh, "codec": enc}
+            "sh_compaction": sh, "codec": enc, "potr_ft": ft}
 
 
 def codec_run(args, dev, D, scene_d, alive, sh_rgb, cams, q: float) -> dict:
@@ -607,7 +615,49 @@ def codec_run(args, dev, D, scene_d, alive, sh_rgb, cams, q: float) -> dict:
         t0 = time.perf_counter()
         ocodec.encode(sample, eyes, p=ocodec.params(q))
         out["oracle_splats_per_s_1_core"] = sample.n / (time.perf_counter() - t0)
+    out["_scene"] = sub
     return out
+
+
+def potr_ft_run(args, dev, D, scene, cams, targets, q: float, cycles: int = 2, iterations: int = 500) -> dict:
+    """POTR-FT (Section IV-F) on the pruned, compacted scene: R_FT = 2 cycles of encode -> decode ->
+    500 fine-tuning iterations (one of the 16 views each, against the unpruned render), then the
+    final encoding; every step on the device.  Reports the wall time of the whole run and the
+    PSNR of the decoded scene before and after, over the 16 views."""
+    import time
+
+    import torch
+
+    import synth
+    from oracle.sh_compact import camera_centre
+    from paper_2601_14821_gb300.batched import BatchedRemovalEffect
+    from paper_2601_14821_gb300.codec import decode, roundtrip
+    from paper_2601_14821_gb300.finetune import potr_ft
+
+    rec = synth.cameras_to_array(cams)
+    eyes = np.array([camera_centre(c) for c in cams])
+    P = cams[0].pixels
+    per_view = [targets[3 * v * P: 3 * (v + 1) * P] for v in range(len(cams))]
+
+    def psnr(sc):
+        be = BatchedRemovalEffect(sc, rec, views_per_chunk=16, device=dev, **CFG)
+        be.plan()
+        img = torch.empty(3 * be.total_pixels, dtype=torch.float32, device=dev)
+        be.render(img)
+        mse = float(torch.mean((img - targets) ** 2).item())
+        return 10.0 * np.log10(1.0 / mse)
+
+    before, _ = roundtrip(scene, eyes, q=q)
+    psnr0 = psnr(before)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = potr_ft(scene, rec, per_view, eyes, q=q, cycles=cycles, iterations=iterations, extent=4.0, **CFG)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    psnr1 = psnr(decode(out["compressed"]))
+    return {"cycles": cycles, "iterations_per_cycle": iterations, "wall_s": wall,
+            "ms_per_iteration_incl_codec": wall * 1e3 / (cycles * iterations), "psnr_decoded_before": psnr0,
+            "psnr_decoded_after": psnr1, "loss_per_cycle": out["losses"], "compressed_bytes": len(out["compressed"])}
 
 
 def sh_compaction_run(args, dev, D, frame, targets, q: float) -> dict:
