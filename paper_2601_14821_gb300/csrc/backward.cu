@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kThreads, 4) render_bwd_kernel(const float4* _
   uint32_t last = 0;
   if (RECOMPUTE) {
     float C[3];
-    forward_walk<kBwdBatch>(smem, wmask, raster, vals, c, cfg, C, T, last);
+    forward_walk<kBwdBatch>(smem, wmask, nullptr, 0u, raster, vals, c, cfg, C, T, last);
   } else if (c.inside) {
     const int64_t pix = c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
     T = t_final[pix];

@@ -34,15 +34,15 @@ __global__ void __launch_bounds__(kThreads, 6) render_kernel(const float4* __res
                                                           potr_raster_config cfg, float* __restrict__ images,
                                                           float* __restrict__ t_final, uint32_t* __restrict__ n_last,
                                                           TileQueue queue) {
-  extern __shared__ float4 smem[];  // one batch of records
-  uint8_t* wmask = reinterpret_cast<uint8_t*>(smem + kSRec * BATCH);
+  extern __shared__ float4 smem[];  // two batches of records
+  uint8_t* wmask = reinterpret_cast<uint8_t*>(smem + 2 * kSRec * BATCH);
   __shared__ uint32_t s_slot;
   int64_t tile;
   for (bool first = true; next_tile(queue, &s_slot, first, tile); first = false) {
     const TileCtx c = tile_ctx(info, n_views, ranges, cfg, tile);
     float C[3], T;
     uint32_t last;
-    forward_walk<BATCH>(smem, wmask, raster, vals, c, cfg, C, T, last);
+    forward_walk<BATCH>(smem, wmask, nullptr, 0u, raster, vals, c, cfg, C, T, last);
     if (!c.inside) continue;
     const int64_t pix = c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
     const int64_t plane = (int64_t)c.vi.width * c.vi.height;
@@ -77,11 +77,12 @@ __device__ __forceinline__ float warp_transpose_sum8(float (&v)[8]) {
   return r;
 }
 
-constexpr int kChunk = 8;  // splats per warp transpose-sum
+constexpr int kChunk = 8;           // splats per warp transpose-sum
+constexpr uint32_t kMaskCache = 2048;  // list positions whose warp masks the back walk reuses
 
 template <int BATCH, bool IMP>
 constexpr size_t removal_smem_bytes() {
-  return sizeof(float4) * 2 * kSRec * BATCH + sizeof(float) * kWarps * BATCH * (IMP ? 2 : 1) + BATCH;
+  return sizeof(float4) * 2 * kSRec * BATCH + sizeof(float) * kWarps * BATCH * (IMP ? 2 : 1) + BATCH + kMaskCache;
 }
 
 template <int BATCH, bool IMP>
@@ -97,6 +98,7 @@ __global__ void __launch_bounds__(kThreads, 5) removal_kernel(const float4* __re
   float* red_d = reinterpret_cast<float*>(dyn + 2 * kSRec * BATCH);  // [kWarps][BATCH] warp sums of dSE
   float* red_i = red_d + kWarps * BATCH;                            // [kWarps][BATCH] warp sums of T alpha
   uint8_t* wmask = reinterpret_cast<uint8_t*>(red_d + kWarps * BATCH * (IMP ? 2 : 1));  // [BATCH]
+  uint8_t* mcache = wmask + BATCH;  // [kMaskCache] warp masks of the first list positions
   __shared__ uint32_t max_last_w[kWarps];
   __shared__ uint32_t s_slot;
   int64_t tile;
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(kThreads, 5) removal_kernel(const float4* __re
   const TileCtx c = tile_ctx(info, n_views, ranges, cfg, tile);
   float C[3], T;
   uint32_t last;
-  forward_walk<BATCH>(smem, wmask, raster, vals, c, cfg, C, T, last);
+  forward_walk<BATCH>(smem, wmask, mcache, kMaskCache, raster, vals, c, cfg, C, T, last);
 
   float e2[3] = {0.0f, 0.0f, 0.0f};  // 2 (c - c_t)
   if (c.inside) {
@@ -160,7 +162,8 @@ __global__ void __launch_bounds__(kThreads, 5) removal_kernel(const float4* __re
     } else {
       cp_async_wait<0>();
     }
-    compute_masks<BATCH>(buf, wmask, cnt, c, cfg);
+    const uint8_t* bm = top <= kMaskCache ? mcache + lo : wmask;  // the forward walk's masks
+    if (top > kMaskCache) compute_masks<BATCH>(buf, wmask, cnt, c, cfg);
     for (int j = lane; j < cnt; j += 32) {
       my_d[j] = 0.0f;
       if (IMP) my_i[j] = 0.0f;
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(kThreads, 5) removal_kernel(const float4* __re
       const int glo = ghi > 32 ? ghi - 32 : 0;
       if (lo + (uint32_t)glo >= warp_last) continue;  // warp-uniform: nothing composited here
       const int jl = glo + lane;
-      uint32_t m = __ballot_sync(0xffffffffu, jl < ghi && lo + (uint32_t)jl < warp_last && ((wmask[jl] >> warp) & 1u));
+      uint32_t m = __ballot_sync(0xffffffffu, jl < ghi && lo + (uint32_t)jl < warp_last && ((bm[jl] >> warp) & 1u));
       while (m) {
         float d[kChunk], im[kChunk];
         int mypos = -1;
@@ -326,7 +329,11 @@ template <int BATCH>
 cudaError_t launch_render(const potr_views* views, const potr_frame* frame, const potr_raster_config& cfg,
                           const uint32_t* vals, const uint32_t* ranges, float* images, float* t_final,
                           uint32_t* n_last, const TileQueue& q, cudaStream_t s) {
-  const size_t smem = sizeof(float4) * kSRec * BATCH + BATCH;
+  const size_t smem = sizeof(float4) * 2 * kSRec * BATCH + BATCH;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(render_kernel<BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   const unsigned grid = tile_grid(render_kernel<BATCH>, smem, q, frame->total_tiles);
   render_kernel<BATCH><<<grid, kThreads, smem, s>>>(reinterpret_cast<const float4*>(views->raster), vals, ranges,
                                                     frame->info, frame->n_views, cfg, images, t_final, n_last, q);
@@ -344,6 +351,10 @@ cudaError_t launch_removal(const potr_views* views, const potr_frame* frame, con
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
+  // five CTAs of about 43 KB each only fit with the largest shared-memory carveout
+  cudaError_t ce = cudaFuncSetAttribute(removal_kernel<BATCH, IMP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        (int)cudaSharedmemCarveoutMaxShared);
+  if (ce != cudaSuccess) return ce;
   const unsigned grid = tile_grid(removal_kernel<BATCH, IMP>, smem, q, frame->total_tiles);
   removal_kernel<BATCH, IMP><<<grid, kThreads, smem, s>>>(reinterpret_cast<const float4*>(views->raster), vals, ranges,
                                                           frame->info, frame->n_views, cfg, targets, images, inst_dse,

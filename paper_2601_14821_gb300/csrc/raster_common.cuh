@@ -142,41 +142,54 @@ __device__ __forceinline__ void compute_masks(const float4* buf, uint8_t* wmask,
   }
 }
 
-// Gather a batch and compute every staged splat's warp mask.
-template <int BATCH>
-__device__ __forceinline__ void stage_batch_masked(float4* smem, uint8_t* wmask, const float4* __restrict__ raster,
-                                                   const uint32_t* __restrict__ vals, uint32_t first, int cnt,
-                                                   const TileCtx& c, const potr_raster_config& cfg) {
-  stage_batch<BATCH>(smem, raster, vals, first, cnt);
-  for (int j = threadIdx.x; j < cnt; j += kThreads) wmask[j] = (uint8_t)warp_mask(smem[kSRec * j], smem[kSRec * j + 1], c, cfg);
-}
-
 // Forward walk of the tile list (Section 3, Eqs. 2-4).  Returns colour, final T and n_last.
+// smem holds two batches of records ([2][BATCH][kSRec]): the gathers of batch k + 1 are in
+// flight while the CTA composites batch k.  Warp masks go to wmask, or, for list positions below
+// mcap (a multiple of BATCH), to mcache[position], where a later back-to-front walk of the same
+// list finds them instead of recomputing them (mcache may be null with mcap = 0).
 template <int BATCH>
-__device__ __forceinline__ void forward_walk(float4* smem, uint8_t* wmask, const float4* __restrict__ raster,
-                                             const uint32_t* __restrict__ vals, const TileCtx& c,
-                                             const potr_raster_config& cfg, float (&C)[3], float& T,
+__device__ __forceinline__ void forward_walk(float4* smem, uint8_t* wmask, uint8_t* mcache, uint32_t mcap,
+                                             const float4* __restrict__ raster, const uint32_t* __restrict__ vals,
+                                             const TileCtx& c, const potr_raster_config& cfg, float (&C)[3], float& T,
                                              uint32_t& last) {
   C[0] = C[1] = C[2] = 0.0f;
   T = 1.0f;
   last = 0;
   bool done = !c.inside;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (uint32_t base = c.s; base < c.e; base += BATCH) {
-    if (__syncthreads_and(done)) break;  // also guards the shared-memory batch
-    const int cnt = (int)min((uint32_t)BATCH, c.e - base);
-    stage_batch_masked<BATCH>(smem, wmask, raster, vals, base, cnt, c, cfg);
+  const uint32_t len = c.e - c.s;
+  const uint32_t nb = (len + BATCH - 1) / BATCH;
+  BatchStager<BATCH> st;
+  if (nb > 0) {
+    st.load(vals, c.s, (int)min((uint32_t)BATCH, len));
+    st.issue(smem, raster);
+  }
+  if (nb > 1) st.load(vals, c.s + BATCH, (int)min((uint32_t)BATCH, len - BATCH));
+  for (uint32_t k = 0; k < nb; ++k) {
+    if (__syncthreads_and(done)) break;  // also: batch k - 1 (and its buffer) fully consumed
+    const uint32_t pos0 = k * BATCH;
+    const int cnt = (int)min((uint32_t)BATCH, len - pos0);
+    const float4* buf = smem + kSRec * BATCH * (k & 1);
+    if (k + 1 < nb) {
+      st.issue(smem + kSRec * BATCH * ((k + 1) & 1), raster);
+      cp_async_wait<1>();
+      if (k + 2 < nb) st.load(vals, c.s + pos0 + 2 * BATCH, (int)min((uint32_t)BATCH, len - pos0 - 2 * BATCH));
+    } else {
+      cp_async_wait<0>();
+    }
+    uint8_t* bm = pos0 + BATCH <= mcap ? mcache + pos0 : wmask;
+    compute_masks<BATCH>(buf, bm, cnt, c, cfg);
     __syncthreads();
     for (int g = 0; g < cnt; g += 32) {
       if (__all_sync(0xffffffffu, done)) break;
       const int jl = g + lane;
-      uint32_t m = __ballot_sync(0xffffffffu, jl < cnt && ((wmask[jl] >> warp) & 1u));
+      uint32_t m = __ballot_sync(0xffffffffu, jl < cnt && ((bm[jl] >> warp) & 1u));
       while (m) {
         const int j = g + __ffs(m) - 1;
         m &= m - 1;
         if (done) continue;
-        const float4 r0 = smem[kSRec * j];
-        const float4 r1 = smem[kSRec * j + 1];
+        const float4 r0 = buf[kSRec * j];
+        const float4 r1 = buf[kSRec * j + 1];
         const float p = pair_exponent(r0.z, r0.w, r1.x, __fsub_rn(c.fx, r0.x), __fsub_rn(c.fy, r0.y));
         if (p < r1.z) continue;  // alpha < alpha_min certainly (prefilter with margin)
         const float a = pair_alpha(r1.y, p, cfg.alpha_max);
@@ -186,16 +199,17 @@ __device__ __forceinline__ void forward_walk(float4* smem, uint8_t* wmask, const
           done = true;
           continue;
         }
-        const float4 r2 = smem[kSRec * j + 2];
+        const float4 r2 = buf[kSRec * j + 2];
         const float w = a * T;
         C[0] = fmaf(w, r2.x, C[0]);
         C[1] = fmaf(w, r2.y, C[1]);
         C[2] = fmaf(w, r2.z, C[2]);
         T = Tn;
-        last = base - c.s + (uint32_t)j + 1;
+        last = pos0 + (uint32_t)j + 1;
       }
     }
   }
+  cp_async_wait<0>();  // after an early exit the next batch may still be landing
 }
 
 // Emission slot of the instance in tile (tx, ty) of the splat whose staged record is r (r[1].w:
