@@ -10,6 +10,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kSRec = 3;  // float4 per record in shared memory: the first three of the kRec
+constexpr int kWarpW = 8, kWarpH = 4;  // pixel block of one warp
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
@@ -93,8 +94,12 @@ __device__ __forceinline__ TileCtx tile_ctx(const potr_view_info* __restrict__ i
   const int64_t local = c.tile - c.vi.tile_base;
   c.ty = (int)(local / c.vi.tiles_x);
   c.tx = (int)(local - (int64_t)c.ty * c.vi.tiles_x);
-  c.px = c.tx * cfg.tile_w + (int)(threadIdx.x % cfg.tile_w);
-  c.py = c.ty * cfg.tile_h + (int)(threadIdx.x / cfg.tile_w);
+  // warp w covers the 8 x 4 pixel block (w mod (tile_w / 8), w div (tile_w / 8)) of the tile,
+  // lane l its pixel (l mod 8, l div 8): compact blocks meet fewer splats only in part than
+  // rows of the tile would
+  const int lane = (int)(threadIdx.x & 31), warp = (int)(threadIdx.x >> 5), bx_n = cfg.tile_w / kWarpW;
+  c.px = c.tx * cfg.tile_w + (warp % bx_n) * kWarpW + (lane % kWarpW);
+  c.py = c.ty * cfg.tile_h + (warp / bx_n) * kWarpH + (lane / kWarpW);
   c.inside = c.px < c.vi.width && c.py < c.vi.height;
   c.fx = (float)c.px + 0.5f;
   c.fy = (float)c.py + 0.5f;
@@ -104,29 +109,32 @@ __device__ __forceinline__ TileCtx tile_ctx(const potr_view_info* __restrict__ i
 }
 
 // Bit w of the result is set when the splat of record (r0, r1) may pass the opacity
-// prefilter (log2 G >= r1.z) at some pixel centre of warp w's rows of this tile.  For each
-// pixel row y the exponent A u^2 + B u v + C v^2 (v = y - my fixed) is a concave parabola in
-// u = x - mx, maximised over the row's span of pixel centres; a pair whose warp bit is clear
-// therefore has alpha < alpha_min at every pixel of that warp and is skipped without changing
-// any decision.  The margin covers binary32 rounding of both evaluations.
+// prefilter (log2 G >= r1.z) at some pixel centre of warp w's 8 x 4 block of this tile.  For
+// each pixel row y the exponent A u^2 + B u v + C v^2 (v = y - my fixed) is a concave parabola
+// in u = x - mx, maximised over each block's 8-pixel span of the row; a pair whose warp bit is
+// clear therefore has alpha < alpha_min at every pixel of that warp and is skipped without
+// changing any decision.  The margin covers binary32 rounding of both evaluations.
 __device__ __forceinline__ uint32_t warp_mask(const float4& r0, const float4& r1, const TileCtx& c,
                                               const potr_raster_config& cfg) {
   const float A = r0.z, B = r0.w, C = r1.x, thr = r1.z;
   if (!(thr < INFINITY)) return 0u;                             // o = 0: never passes
   if (!(thr > -INFINITY) || !(A < 0.0f) || !(C < 0.0f)) return 0xffu;  // no bound: keep all
   const float ux0 = ((float)(c.tx * cfg.tile_w) + 0.5f) - r0.x;
-  const float ux1 = ux0 + (float)(cfg.tile_w - 1);
   const float k1 = -B / (2.0f * A);
-  const int rows_per_warp = 32 / cfg.tile_w;
+  const int bx_n = cfg.tile_w / kWarpW;
   const float vy0 = ((float)(c.ty * cfg.tile_h) + 0.5f) - r0.y;
   uint32_t m = 0;
   for (int r = 0; r < cfg.tile_h; ++r) {
     const float v = vy0 + (float)r;
-    const float u = fminf(fmaxf(k1 * v, ux0), ux1);
-    const float t1 = A * u * u, t2 = B * u * v, t3 = C * v * v;
-    const float pmax = t1 + t2 + t3;
-    const float margin = 1e-4f * (fabsf(t1) + fabsf(t2) + fabsf(t3)) + 1e-3f;
-    if (pmax + margin >= thr) m |= 1u << (r / rows_per_warp);
+    const float us = k1 * v, bv = B * v, t3 = C * v * v;
+    for (int xb = 0; xb < bx_n; ++xb) {
+      const float lo = ux0 + (float)(kWarpW * xb);
+      const float u = fminf(fmaxf(us, lo), lo + (float)(kWarpW - 1));
+      const float t1 = A * u * u, t2 = bv * u;
+      const float pmax = t1 + t2 + t3;
+      const float margin = 1e-4f * (fabsf(t1) + fabsf(t2) + fabsf(t3)) + 1e-3f;
+      if (pmax + margin >= thr) m |= 1u << ((r / kWarpH) * bx_n + xb);
+    }
   }
   return m;
 }
