@@ -67,8 +67,10 @@ __global__ void __launch_bounds__(256) depth_key_kernel(const uint32_t* __restri
 // from the slot's rank among that vk's kept tiles (row-major in its rectangle, through the
 // kept-tile mask).  Stores are coalesced whatever the rectangle sizes.  Each instance gets key
 // = global tile and value = vk; a stable partition by tile then yields per-tile lists in
-// (depth, vk) order.  The tile digits of every partition pass are counted here
-// (warp-aggregated shared-memory increments).
+// (depth, vk) order.  An entry's fields travel packed: its first tile (the rectangle's corner),
+// and rectangle width | all-kept flag << 11 | view tiles_x << 12.  The tile digits of every
+// partition pass are counted here in shared memory: one add per warp when the warp's 32 keys
+// share the digit (the usual case above the lowest byte), else one add per lane.
 __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ eoff,
                                                    const potr_view_info* __restrict__ info, int64_t n, int64_t n_vk,
                                                    const uint64_t* __restrict__ m_eff,
@@ -79,11 +81,10 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
   __syncthreads();
   if (*m_eff == 0) return;  // uniform: nothing emitted, nothing counted
   const int lane = threadIdx.x & 31;
-  const uint32_t lt = (1u << lane) - 1u;
   const int64_t warps_total = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t wv = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wv * 32 < n_vk; wv += warps_total) {
     const int64_t i = wv * 32 + lane;
-    uint32_t vk = 0, cnt = 0, off = 0, x0 = 0, y0 = 0, w = 1, m_lo = 0, m_hi = 0, m_all = 1, tiles_x = 0, row0 = 0;
+    uint32_t vk = 0, cnt = 0, off = 0, corner = 0, pk = 1u, m_lo = 0, m_hi = 0;
     if (i < n_vk) {
       vk = order[i];
       off = eoff[i];
@@ -91,16 +92,13 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
       const float4 m = raster[(size_t)vk * kRec + 3];
       cnt = __float_as_uint(m.w) & 0x7fffffffu;
       if (cnt) {
-        const potr_view_info vi = info[(int)(vk / (uint64_t)n)];
+        const potr_view_info& vi = info[(int)(vk / (uint64_t)n)];
         const uint32_t rw = __float_as_uint(m.z);
-        x0 = rw & 0x7ffu;
-        y0 = (rw >> 11) & 0x7ffu;
-        w = rw >> 22;
-        tiles_x = (uint32_t)vi.tiles_x;
-        row0 = (uint32_t)vi.tile_base;
+        const uint32_t tiles_x = (uint32_t)vi.tiles_x;
+        corner = (uint32_t)vi.tile_base + ((rw >> 11) & 0x7ffu) * tiles_x + (rw & 0x7ffu);
+        pk = (rw >> 22) | ((__float_as_uint(m.w) >> 31) << 11) | (tiles_x << 12);
         m_lo = __float_as_uint(m.x);
         m_hi = __float_as_uint(m.y);
-        m_all = __float_as_uint(m.w) >> 31;
       }
     }
     uint32_t incl = cnt;
@@ -127,27 +125,29 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
       }
       const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, owner);
       const uint32_t o_vk = __shfl_sync(0xffffffffu, vk, owner);
-      const uint32_t o_x0 = __shfl_sync(0xffffffffu, x0, owner);
-      const uint32_t o_y0 = __shfl_sync(0xffffffffu, y0, owner);
-      const uint32_t o_w = __shfl_sync(0xffffffffu, w, owner);
-      const uint32_t o_row0 = __shfl_sync(0xffffffffu, row0, owner);
-      const uint32_t o_tx = __shfl_sync(0xffffffffu, tiles_x, owner);
+      const uint32_t o_corner = __shfl_sync(0xffffffffu, corner, owner);
+      const uint32_t o_pk = __shfl_sync(0xffffffffu, pk, owner);
       const uint32_t o_mlo = __shfl_sync(0xffffffffu, m_lo, owner);
       const uint32_t o_mhi = __shfl_sync(0xffffffffu, m_hi, owner);
-      const uint32_t o_all = __shfl_sync(0xffffffffu, m_all, owner);
       uint32_t tile = 0;
       if (e < total) {
         // the li-th kept tile of the owner's rectangle, row-major
-        const uint32_t li = o_all ? e - o_excl : select_bit64(((uint64_t)o_mhi << 32) | o_mlo, e - o_excl);
-        const uint32_t dy = o_all ? li / o_w : small_div(li, o_w), dx = li - dy * o_w;  // masked: li < 64
-        tile = o_row0 + (o_y0 + dy) * o_tx + (o_x0 + dx);
+        const uint32_t w = o_pk & 0x7ffu, all = (o_pk >> 11) & 1u, tiles_x = o_pk >> 12;
+        const uint32_t li = all ? e - o_excl : select_bit64(((uint64_t)o_mhi << 32) | o_mlo, e - o_excl);
+        const uint32_t dy = all ? li / w : small_div(li, w), dx = li - dy * w;  // masked: li < 64
+        tile = o_corner + dy * tiles_x + dx;
         keys[run0 + e] = tile;
         vals[run0 + e] = o_vk;
       }
+      const uint32_t n_valid = min(32u, total - e0);  // lanes 0 .. n_valid - 1 hold keys
       for (int p = 0; p < passes; ++p) {
-        const uint32_t d = (e < total) ? (tile >> (8 * p)) & 0xffu : 256u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (d < 256u && (peers & lt) == 0) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
+        const uint32_t d = (tile >> (8 * p)) & 0xffu;
+        const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+        if (__all_sync(0xffffffffu, e >= total || d == d0)) {
+          if (lane == 0) atomicAdd(&h[p][d0], n_valid);
+        } else if (e < total) {
+          atomicAdd(&h[p][d], 1u);
+        }
       }
     }
   }
@@ -314,8 +314,8 @@ extern "C" potr_status potr_bin_sort(const potr_views* views, const potr_frame* 
   {
     const int64_t g = ceil_div(L.n_vk, 256);
     emit_kernel<<<(unsigned)(g < 152 * 16 ? g : 152 * 16), 256, 0, s>>>(
-        order, dv1, frame->info, n, L.n_vk, m_eff,
-        reinterpret_cast<const float4*>(views->raster), k_src, v_src, tile_passes, ghist + 256 * 4);
+        order, dv1, frame->info, n, L.n_vk, m_eff, reinterpret_cast<const float4*>(views->raster), k_src, v_src,
+        tile_passes, ghist + 256 * 4);
     POTR_CHECK_LAUNCH();
     digit_base_kernel<<<1, 256, 0, s>>>(ghist + 256 * 4, tile_passes, gbase + 256 * 4);
     POTR_CHECK_LAUNCH();

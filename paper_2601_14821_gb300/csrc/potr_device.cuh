@@ -162,6 +162,20 @@ __device__ __forceinline__ int view_of_tile(const potr_view_info* info, int n_vi
   return lo;
 }
 
+// Lanes whose values d agree in their low NBITS bits (every lane of the warp takes part): one
+// ballot per bit, the lane keeping the lanes that agree with it on that bit.
+template <int NBITS>
+__device__ __forceinline__ uint32_t match_low_bits(uint32_t d) {
+  uint32_t peers = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < NBITS; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+}
+
 __device__ __forceinline__ void set_status(potr_device_status* st, int32_t code, int64_t required) {
   if (st) {
     atomicCAS(&st->code, 0, code);

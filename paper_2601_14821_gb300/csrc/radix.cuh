@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kOsThreads, 5) onesweep_kernel(const uint32_t*
 #pragma unroll
   for (int r = 0; r < kOsItems; ++r) {
     const uint32_t d = r < nv ? (k[r] >> shift) & 0xffu : 256u;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t peers = match_low_bits<9>(d);  // d <= 256
     const uint32_t rank = __popc(peers & lt);
     const uint32_t c0 = wc[d];
     __syncwarp();
