@@ -47,9 +47,10 @@ FLOP_REMOVAL = 26        # T recovery, ratio, PD and dSE over 3 channels, suffix
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 PEAK_FP32_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 # DRAM bytes (read + written) of one removal-kernel launch per view of the scene workload: an
-# ncu capture of the 4-view case measured 246.7 MB (dram__bytes_read.sum + dram__bytes_write.sum);
-# the traffic grows with the views (records gathered per tile), so a 16-view launch moves 16 x this.
-REMOVAL_DRAM_BYTES_PER_VIEW = 246.7e6 / 4
+# ncu capture of the 4-view case measured 255.5 MB (dram__bytes_read.sum 209.6 MB +
+# dram__bytes_write.sum 45.8 MB); the traffic grows with the views (records gathered per tile),
+# so a 16-view launch moves 16 x this.
+REMOVAL_DRAM_BYTES_PER_VIEW = 255.45e6 / 4
 
 
 def parse():

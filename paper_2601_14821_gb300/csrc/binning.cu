@@ -168,14 +168,33 @@ __global__ void lookback_timeout_probe_kernel(unsigned long long* status, int sp
   if (threadIdx.x == 0 && s_err && got == 0) set_status(st, POTR_ERR_TIMEOUT, 0);
 }
 
+// Per tile [first, end) of its instances in the sorted keys.  Each thread takes four consecutive
+// keys (one 16-byte load when the array is 16-byte aligned) and the key after them.
 __global__ void __launch_bounds__(256) tile_ranges_kernel(const uint32_t* __restrict__ tiles, const uint64_t* __restrict__ m_eff,
                                                           int64_t total_tiles, uint32_t* __restrict__ ranges) {
   const int64_t m = (int64_t)*m_eff;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t t = tiles[i];
-    if (t >= (uint64_t)total_tiles) continue;
-    if (i == 0 || tiles[i - 1] != t) ranges[2 * t] = (uint32_t)i;
-    if (i == m - 1 || tiles[i + 1] != t) ranges[2 * t + 1] = (uint32_t)(i + 1);
+  const bool vec = (reinterpret_cast<uintptr_t>(tiles) & 15u) == 0;
+  for (int64_t i0 = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); i0 < m;
+       i0 += 4 * (int64_t)gridDim.x * blockDim.x) {
+    uint32_t t[5];
+    if (vec && i0 + 4 <= m) {
+      const uint4 q = *reinterpret_cast<const uint4*>(tiles + i0);
+      t[0] = q.x; t[1] = q.y; t[2] = q.z; t[3] = q.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) t[j] = i0 + j < m ? tiles[i0 + j] : 0xffffffffu;
+    }
+    t[4] = i0 + 4 < m ? tiles[i0 + 4] : 0xffffffffu;
+    uint32_t prev = i0 > 0 ? tiles[i0 - 1] : 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t i = i0 + j;
+      if (i < m && t[j] < (uint64_t)total_tiles) {
+        if (i == 0 || prev != t[j]) ranges[2 * t[j]] = (uint32_t)i;
+        if (i == m - 1 || t[j + 1] != t[j]) ranges[2 * t[j] + 1] = (uint32_t)(i + 1);
+      }
+      prev = t[j];
+    }
   }
 }
 
@@ -332,7 +351,7 @@ extern "C" potr_status potr_bin_sort(const potr_views* views, const potr_frame* 
   if (cudaMemsetAsync(d_tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)frame->total_tiles, s) != cudaSuccess)
     return POTR_ERR_CUDA;
   {
-    const int64_t g = ceil_div(instance_capacity, 256);
+    const int64_t g = ceil_div(instance_capacity, 4 * 256);
     tile_ranges_kernel<<<(unsigned)(g < 152 * 64 ? g : 152 * 64), 256, 0, s>>>(d_tiles, m_eff, frame->total_tiles,
                                                                                d_tile_ranges);
     POTR_CHECK_LAUNCH();

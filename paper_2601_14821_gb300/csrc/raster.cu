@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 5) removal_kernel(const float4* __re
 // dmse[k] += dSSE_k(v) * scale_d[v] with scale_d[v] = 1 / (3 P_v N), views in order; the
 // importance likewise with scale_i[v] = 1 / (P_v N).  The per-view scales are computed once
 // per view (binary64), so the loop has no division.
-constexpr int kReduceChunk = 4096;  // partials staged per block and round
+constexpr int kReduceChunk = 512;  // partials staged per warp and round
 
 __global__ void __launch_bounds__(256) splat_reduce_kernel(const uint32_t* __restrict__ touched,
                                                            const uint32_t* __restrict__ offsets,
@@ -263,17 +263,20 @@ __global__ void __launch_bounds__(256) splat_reduce_kernel(const uint32_t* __res
                                                            double* __restrict__ dmse, double* __restrict__ importance,
                                                            double* __restrict__ dsse_view,
                                                            double* __restrict__ imp_view) {
-  // One block per 256 consecutive splats.  For one view their emission slots form one
-  // contiguous range (offsets are the exclusive prefix in vk order), which the block stages
-  // through shared memory with coalesced loads; each thread then adds its own slots, in slot
-  // order, from there.
+  // One warp per 32 consecutive splats.  For one view their emission slots form one contiguous
+  // range (offsets are the exclusive prefix in vk order), which the warp stages through its own
+  // shared memory with coalesced loads; each lane then adds its own slots, in slot order, from
+  // there.  Warps synchronise only among their own lanes.
   __shared__ double scale_d[64], scale_i[64], inv_p[64];
-  __shared__ float s_d[kReduceChunk], s_i[kReduceChunk];
-  __shared__ uint32_t s_lo, s_hi;
+  __shared__ float s_d[kWarps][kReduceChunk], s_i[kWarps][kReduceChunk];
   if ((int64_t)*n_inst > capacity) return;
-  const int64_t k0 = (int64_t)blockIdx.x * blockDim.x;
-  const int64_t k = k0 + threadIdx.x;
-  const int64_t k_last = min(k0 + (int64_t)blockDim.x, n) - 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t k0 = ((int64_t)blockIdx.x * kWarps + warp) * 32;
+  const int64_t k = k0 + lane;
+  const bool active = k0 < n;  // warp-uniform
+  const int last_lane = active ? (int)(min(k0 + 32, n) - 1 - k0) : 0;
+  float* wd = s_d[warp];
+  float* wi = s_i[warp];
   double acc_d = (dmse && k < n) ? dmse[k] : 0.0;
   double acc_i = (importance && k < n) ? importance[k] : 0.0;
   for (int v0 = 0; v0 < n_views; v0 += 64) {
@@ -285,6 +288,8 @@ __global__ void __launch_bounds__(256) splat_reduce_kernel(const uint32_t* __res
       scale_i[threadIdx.x] = 1.0 / (P * n_total);
       inv_p[threadIdx.x] = 1.0 / P;
     }
+    __syncthreads();
+    if (!active) continue;
     for (int vv = 0; vv < nv; ++vv) {
       const int64_t row = (int64_t)(v0 + vv) * n;
       uint32_t cnt = 0, off = 0;
@@ -292,24 +297,22 @@ __global__ void __launch_bounds__(256) splat_reduce_kernel(const uint32_t* __res
         cnt = touched[row + k];
         off = offsets[row + k];
       }
-      if (threadIdx.x == 0) s_lo = offsets[row + k0];
-      if (k == k_last) s_hi = off + cnt;
-      __syncthreads();
-      const uint32_t lo = s_lo, hi = s_hi;
+      const uint32_t lo = __shfl_sync(0xffffffffu, off, 0);
+      const uint32_t hi = __shfl_sync(0xffffffffu, off + cnt, last_lane);
       KahanSum kd, ki;
       for (uint32_t c0 = lo; c0 < hi; c0 += kReduceChunk) {
         const uint32_t m = min((uint32_t)kReduceChunk, hi - c0);
-        for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
-          s_d[i] = inst_dse[c0 + i];
-          if (inst_imp) s_i[i] = inst_imp[c0 + i];
+        for (uint32_t i = lane; i < m; i += 32) {
+          wd[i] = inst_dse[c0 + i];
+          if (inst_imp) wi[i] = inst_imp[c0 + i];
         }
-        __syncthreads();
+        __syncwarp();
         const uint32_t a = max(off, c0), b = min(off + cnt, c0 + m);
         for (uint32_t i = a; i < b; ++i) {
-          kd.add(s_d[i - c0]);
-          if (inst_imp) ki.add(s_i[i - c0]);
+          kd.add(wd[i - c0]);
+          if (inst_imp) ki.add(wi[i - c0]);
         }
-        __syncthreads();
+        __syncwarp();
       }
       const double sd = cnt ? (double)kd.value() : 0.0;
       const double si = (cnt && inst_imp) ? (double)ki.value() : 0.0;
@@ -430,7 +433,7 @@ extern "C" potr_status potr_removal_effect(const potr_views* views, const potr_f
   }
   if (e != cudaSuccess) return POTR_ERR_CUDA;
   if (d_dmse || d_importance || d_dsse_view || d_imp_view) {
-    const int64_t g = (n + 255) / 256;  // one block per 256 splats
+    const int64_t g = (n + 255) / 256;  // one block per 256 splats (a warp per 32)
     splat_reduce_kernel<<<(unsigned)g, 256, 0, s>>>(views->touched, views->offsets, views->n_instances,
                                                      instance_capacity, d_inst_dse, d_inst_imp, n, frame->n_views,
                                                      frame->info, (double)n_views_total, d_dmse, d_importance,
