@@ -86,7 +86,7 @@ constexpr size_t removal_smem_bytes() {
 }
 
 template <int BATCH, bool IMP>
-__global__ void __launch_bounds__(kThreads, 5) removal_kernel(const float4* __restrict__ raster,
+__global__ void __launch_bounds__(kThreads, BATCH <= 128 ? 6 : 5) removal_kernel(const float4* __restrict__ raster,
                                                            const uint32_t* __restrict__ vals,
                                                            const uint32_t* __restrict__ ranges,
                                                            const potr_view_info* __restrict__ info, int n_views,
