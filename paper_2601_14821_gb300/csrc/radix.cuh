@@ -17,12 +17,12 @@ constexpr int kSpinLimit = 1 << 22;
 // -----------------------------------------------------------------------------------------
 // Stable LSD radix sort, 8-bit digits, one kernel per pass ("onesweep": Adinets & Merrill,
 // 2022).  One read of the keys builds the digit histograms of every pass; then each pass
-// ranks 4096 items per block stably (per-warp match masks, warps in order), publishes its
-// per-digit counts, finds the counts of all earlier blocks by decoupled look-back over the
-// published words, and writes its items grouped by digit through shared memory so that the
-// global stores are contiguous runs.  Blocks take their item range from an atomic counter,
-// so every block a look-back waits on is already running; the wait is bounded and reports
-// POTR_ERR_TIMEOUT instead of hanging.
+// ranks 4096 items per block stably (per-warp equal-digit masks from ballots, warps in
+// order), publishes its per-digit counts, finds the counts of all earlier blocks by decoupled
+// look-back over the published words, and writes its items grouped by digit through shared
+// memory so that the global stores are contiguous runs.  Blocks take their item range from an
+// atomic counter, so every block a look-back waits on is already running; the wait is bounded
+// and reports POTR_ERR_TIMEOUT instead of hanging.
 // -----------------------------------------------------------------------------------------
 size_t onesweep_smem_bytes() { return sizeof(uint32_t) * 2 * kOsTile + sizeof(uint32_t) * (8 * 257 + 3 * 256); }
 
