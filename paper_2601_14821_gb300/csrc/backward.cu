@@ -28,8 +28,11 @@ constexpr int kBwdChunk = 4;  // splats per warp transpose-sum
 constexpr int kBwdBatch = 128;
 constexpr float kLn2 = 0.69314718055994531f;
 
+constexpr uint32_t kBwdMaskCache = 2048;  // list positions whose warp masks the back walk reuses
+
 size_t bwd_smem_bytes() {
-  return sizeof(float4) * 2 * kSRec * kBwdBatch + sizeof(float) * kGradQ * kWarps * kBwdBatch + kBwdBatch;
+  return sizeof(float4) * 2 * kSRec * kBwdBatch + sizeof(float) * kGradQ * kWarps * kBwdBatch + kBwdBatch +
+         kBwdMaskCache;
 }
 
 // Lanes l, l^4, l^8, ... receive the sum over all 32 lanes of v[l & 3] (fixed order): a
@@ -101,11 +104,14 @@ __global__ void __launch_bounds__(kThreads, 4) render_bwd_kernel(const float4* _
                                                               potr_raster_config cfg, const float* __restrict__ t_final,
                                                               const uint32_t* __restrict__ n_last,
                                                               const float* __restrict__ dL_dimg, int64_t capacity,
-                                                              float* __restrict__ inst_grad, TileQueue queue) {
+                                                              float* __restrict__ inst_grad,
+                                                              const uint8_t* __restrict__ gmask, TileQueue queue) {
   extern __shared__ float4 dyn[];
   float4* smem = dyn;                                                // [2][kBwdBatch][kSRec]
   float* red = reinterpret_cast<float*>(dyn + 2 * kSRec * kBwdBatch);        // [kGradQ][kWarps][kBwdBatch]
   uint8_t* wmask = reinterpret_cast<uint8_t*>(red + kGradQ * kWarps * kBwdBatch);
+  uint8_t* mcache = wmask + kBwdBatch;  // [kBwdMaskCache] the recomputing forward walk's warp masks
+  const bool stored_masks = !RECOMPUTE && gmask != nullptr;
   __shared__ uint32_t max_last_w[kWarps];
   __shared__ uint32_t s_slot;
   int64_t tile;
@@ -115,7 +121,7 @@ __global__ void __launch_bounds__(kThreads, 4) render_bwd_kernel(const float4* _
   uint32_t last = 0;
   if (RECOMPUTE) {
     float C[3];
-    forward_walk<kBwdBatch>(smem, wmask, nullptr, 0u, raster, vals, c, cfg, C, T, last);
+    forward_walk<kBwdBatch>(smem, wmask, mcache, kBwdMaskCache, raster, vals, c, cfg, C, T, last);
   } else if (c.inside) {
     const int64_t pix = c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
     T = t_final[pix];
@@ -140,10 +146,12 @@ __global__ void __launch_bounds__(kThreads, 4) render_bwd_kernel(const float4* _
   constexpr uint32_t B = kBwdBatch;
   const uint32_t nb = (max_last + B - 1) / B;
   BatchStager<kBwdBatch> st;
+  uint32_t mk_cur[BatchStager<kBwdBatch>::kPer], mk_nxt[BatchStager<kBwdBatch>::kPer];  // stored masks
   __syncthreads();  // the forward walk's last batch is no longer read
   if (nb > 0) {
     const uint32_t lo0 = max_last > B ? max_last - B : 0u;
     st.load(vals, c.s + lo0, (int)(max_last - lo0));
+    if (stored_masks) st.load_masks(gmask + c.s, lo0, (int)(max_last - lo0), mk_cur);
     st.issue(smem, raster);
   }
   if (nb > 1) {
@@ -157,6 +165,10 @@ __global__ void __launch_bounds__(kThreads, 4) render_bwd_kernel(const float4* _
     const float4* buf = smem + kSRec * B * (k & 1);
     if (k > 0) __syncthreads();  // batch k-1 fully consumed
     if (k + 1 < nb) {
+      if (stored_masks) {
+        const uint32_t lo1 = lo > B ? lo - B : 0u;
+        st.load_masks(gmask + c.s, lo1, (int)(lo - lo1), mk_nxt);  // in flight during batch k
+      }
       st.issue(smem + kSRec * B * ((k + 1) & 1), raster);
       cp_async_wait<1>();
       if (k + 2 < nb) {
@@ -166,7 +178,21 @@ __global__ void __launch_bounds__(kThreads, 4) render_bwd_kernel(const float4* _
     } else {
       cp_async_wait<0>();
     }
-    compute_masks<kBwdBatch>(buf, wmask, cnt, c, cfg);
+    // this batch's warp masks: stored by the render pass, cached by the forward walk above, or
+    // computed here
+    const uint8_t* bm = wmask;
+    if (stored_masks) {
+#pragma unroll
+      for (int r = 0; r < BatchStager<kBwdBatch>::kPer; ++r) {
+        const int j = threadIdx.x + r * kThreads;
+        if (j < cnt) wmask[j] = (uint8_t)mk_cur[r];
+        mk_cur[r] = mk_nxt[r];
+      }
+    } else if (RECOMPUTE && top <= kBwdMaskCache) {
+      bm = mcache + lo;
+    } else {
+      compute_masks<kBwdBatch>(buf, wmask, cnt, c, cfg);
+    }
     for (int q = 0; q < kGradQ; ++q)
       for (int j = lane; j < cnt; j += 32) red[(q * kWarps + warp) * kBwdBatch + j] = 0.0f;
     __syncthreads();
@@ -174,7 +200,7 @@ __global__ void __launch_bounds__(kThreads, 4) render_bwd_kernel(const float4* _
       const int glo = ghi > 32 ? ghi - 32 : 0;
       if (lo + (uint32_t)glo >= warp_last) continue;
       const int jl = glo + lane;
-      uint32_t m = __ballot_sync(0xffffffffu, jl < ghi && lo + (uint32_t)jl < warp_last && ((wmask[jl] >> warp) & 1u));
+      uint32_t m = __ballot_sync(0xffffffffu, jl < ghi && lo + (uint32_t)jl < warp_last && ((bm[jl] >> warp) & 1u));
       while (m) {
         float v[kGradQ][kBwdChunk];
         int mypos = -1;
@@ -314,9 +340,9 @@ __device__ __forceinline__ void sh_weighted_grad(float x, float y, float z, cons
 // order, compensated).  One warp per 32 consecutive vk, whose slots form one contiguous run:
 // the run is read coalesced into shared memory a chunk at a time and each lane adds the part of
 // its own segment that the chunk holds.  vk_grad[q][vk] receives the sums.
-constexpr int kSumChunk = 256;
+constexpr int kSumChunk = 128;  // a warp's run is usually shorter (about 32 x 3.5 slots)
 
-__global__ void __launch_bounds__(128) vk_grad_sum_kernel(const uint32_t* __restrict__ touched,
+__global__ void __launch_bounds__(128, 8) vk_grad_sum_kernel(const uint32_t* __restrict__ touched,
                                                           const uint32_t* __restrict__ offsets,
                                                           const uint32_t* __restrict__ n_inst, int64_t capacity,
                                                           int64_t n_vk, const float* __restrict__ inst_grad,
@@ -595,7 +621,8 @@ extern "C" potr_status potr_render_backward(const potr_scene* scene, const potr_
                                             const potr_raster_config* cfg, const uint32_t* d_vals,
                                             const uint32_t* d_tile_ranges, uint32_t* d_tile_order,
                                             const float* d_t_final,
-                                            const uint32_t* d_n_last, const float* d_dL_dimages,
+                                            const uint32_t* d_n_last, const uint8_t* d_warp_masks,
+                                            const float* d_dL_dimages,
                                             int64_t instance_capacity, const potr_scene_grads* grads, void* d_ws,
                                             size_t ws_bytes, potr_stream_t stream) {
   using namespace potr;
@@ -629,14 +656,14 @@ extern "C" potr_status potr_render_backward(const potr_scene* scene, const potr_
       return POTR_ERR_CUDA;
     render_bwd_kernel<true><<<tile_grid(render_bwd_kernel<true>, smem, q, frame->total_tiles), kThreads, smem, s>>>(
         reinterpret_cast<const float4*>(views->raster), d_vals, d_tile_ranges, frame->info, frame->n_views, *cfg,
-        nullptr, nullptr, d_dL_dimages, instance_capacity, inst_grad, q);
+        nullptr, nullptr, d_dL_dimages, instance_capacity, inst_grad, nullptr, q);
   } else {
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(render_bwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return POTR_ERR_CUDA;
     render_bwd_kernel<false><<<tile_grid(render_bwd_kernel<false>, smem, q, frame->total_tiles), kThreads, smem, s>>>(
         reinterpret_cast<const float4*>(views->raster), d_vals, d_tile_ranges, frame->info, frame->n_views, *cfg,
-        d_t_final, d_n_last, d_dL_dimages, instance_capacity, inst_grad, q);
+        d_t_final, d_n_last, d_dL_dimages, instance_capacity, inst_grad, d_warp_masks, q);
   }
   POTR_CHECK_LAUNCH();
   const int64_t n = scene->n;

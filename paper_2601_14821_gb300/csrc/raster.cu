@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kThreads, 6) render_kernel(const float4* __res
                                                           const potr_view_info* __restrict__ info, int n_views,
                                                           potr_raster_config cfg, float* __restrict__ images,
                                                           float* __restrict__ t_final, uint32_t* __restrict__ n_last,
-                                                          TileQueue queue) {
+                                                          uint8_t* __restrict__ gmask, TileQueue queue) {
   extern __shared__ float4 smem[];  // two batches of records
   uint8_t* wmask = reinterpret_cast<uint8_t*>(smem + 2 * kSRec * BATCH);
   __shared__ uint32_t s_slot;
@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(kThreads, 6) render_kernel(const float4* __res
     const TileCtx c = tile_ctx(info, n_views, ranges, cfg, tile);
     float C[3], T;
     uint32_t last;
-    forward_walk<BATCH>(smem, wmask, nullptr, 0u, raster, vals, c, cfg, C, T, last);
+    forward_walk<BATCH>(smem, wmask, nullptr, 0u, raster, vals, c, cfg, C, T, last, gmask ? gmask + c.s : nullptr);
     if (!c.inside) continue;
     const int64_t pix = c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
     const int64_t plane = (int64_t)c.vi.width * c.vi.height;
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(256) splat_reduce_kernel(const uint32_t* __res
 template <int BATCH>
 cudaError_t launch_render(const potr_views* views, const potr_frame* frame, const potr_raster_config& cfg,
                           const uint32_t* vals, const uint32_t* ranges, float* images, float* t_final,
-                          uint32_t* n_last, const TileQueue& q, cudaStream_t s) {
+                          uint32_t* n_last, uint8_t* gmask, const TileQueue& q, cudaStream_t s) {
   const size_t smem = sizeof(float4) * 2 * kSRec * BATCH + BATCH;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(render_kernel<BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -339,7 +339,8 @@ cudaError_t launch_render(const potr_views* views, const potr_frame* frame, cons
   }
   const unsigned grid = tile_grid(render_kernel<BATCH>, smem, q, frame->total_tiles);
   render_kernel<BATCH><<<grid, kThreads, smem, s>>>(reinterpret_cast<const float4*>(views->raster), vals, ranges,
-                                                    frame->info, frame->n_views, cfg, images, t_final, n_last, q);
+                                                    frame->info, frame->n_views, cfg, images, t_final, n_last, gmask,
+                                                    q);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -381,7 +382,7 @@ cudaError_t make_queue(uint32_t* d_tile_order, int64_t total_tiles, TileQueue& q
 extern "C" potr_status potr_render(const potr_views* views, const potr_frame* frame, const potr_raster_config* cfg,
                                    int64_t n, const uint32_t* d_vals, const uint32_t* d_tile_ranges,
                                    uint32_t* d_tile_order, float* d_images, float* d_t_final, uint32_t* d_n_last,
-                                   potr_stream_t stream) {
+                                   uint8_t* d_warp_masks, potr_stream_t stream) {
   using namespace potr;
   if (!views || !frame || !valid_cfg(cfg) || !d_vals || !d_tile_ranges || !views->raster || !frame->info)
     return POTR_ERR_INVALID_ARGUMENT;
@@ -392,9 +393,9 @@ extern "C" potr_status potr_render(const potr_views* views, const potr_frame* fr
   if (make_queue(d_tile_order, frame->total_tiles, q, s) != cudaSuccess) return POTR_ERR_CUDA;
   cudaError_t e;
   switch (cfg->batch) {
-    case 128: e = launch_render<128>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, q, s); break;
-    case 256: e = launch_render<256>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, q, s); break;
-    default: e = launch_render<512>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, q, s); break;
+    case 128: e = launch_render<128>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, d_warp_masks, q, s); break;
+    case 256: e = launch_render<256>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, d_warp_masks, q, s); break;
+    default: e = launch_render<512>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, d_warp_masks, q, s); break;
   }
   return e == cudaSuccess ? POTR_OK : POTR_ERR_CUDA;
 }

@@ -53,6 +53,15 @@ struct BatchStager {
     }
     loaded = cnt;
   }
+  // With stored warp masks: their bytes for the same entries (gmask: the list's, from first).
+  __device__ __forceinline__ void load_masks(const uint8_t* __restrict__ gmask, uint32_t first, int cnt,
+                                             uint32_t (&mk)[kPer]) const {
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int j = threadIdx.x + r * kThreads;
+      mk[r] = j < cnt ? gmask[first + j] : 0u;
+    }
+  }
   __device__ __forceinline__ void issue(float4* buf, const float4* __restrict__ raster) const {
 #pragma unroll
     for (int r = 0; r < kPer; ++r) {
@@ -139,14 +148,19 @@ __device__ __forceinline__ uint32_t warp_mask(const float4& r0, const float4& r1
   return m;
 }
 
-// Warp masks of the entries this thread gathered (its own cp.async copies are complete).
+// Warp masks of the entries this thread gathered (its own cp.async copies are complete), also
+// written to gout[j] when gout is not null.
 template <int BATCH>
 __device__ __forceinline__ void compute_masks(const float4* buf, uint8_t* wmask, int cnt, const TileCtx& c,
-                                              const potr_raster_config& cfg) {
+                                              const potr_raster_config& cfg, uint8_t* gout = nullptr) {
 #pragma unroll
   for (int r = 0; r < BatchStager<BATCH>::kPer; ++r) {
     const int j = threadIdx.x + r * kThreads;
-    if (j < cnt) wmask[j] = (uint8_t)warp_mask(buf[kSRec * j], buf[kSRec * j + 1], c, cfg);
+    if (j < cnt) {
+      const uint8_t mk = (uint8_t)warp_mask(buf[kSRec * j], buf[kSRec * j + 1], c, cfg);
+      wmask[j] = mk;
+      if (gout) gout[j] = mk;
+    }
   }
 }
 
@@ -154,12 +168,13 @@ __device__ __forceinline__ void compute_masks(const float4* buf, uint8_t* wmask,
 // smem holds two batches of records ([2][BATCH][kSRec]): the gathers of batch k + 1 are in
 // flight while the CTA composites batch k.  Warp masks go to wmask, or, for list positions below
 // mcap (a multiple of BATCH), to mcache[position], where a later back-to-front walk of the same
-// list finds them instead of recomputing them (mcache may be null with mcap = 0).
+// list finds them instead of recomputing them (mcache may be null with mcap = 0); with gmask not
+// null they are also written to gmask[position] (device memory, this tile's list).
 template <int BATCH>
 __device__ __forceinline__ void forward_walk(float4* smem, uint8_t* wmask, uint8_t* mcache, uint32_t mcap,
                                              const float4* __restrict__ raster, const uint32_t* __restrict__ vals,
                                              const TileCtx& c, const potr_raster_config& cfg, float (&C)[3], float& T,
-                                             uint32_t& last) {
+                                             uint32_t& last, uint8_t* gmask = nullptr) {
   C[0] = C[1] = C[2] = 0.0f;
   T = 1.0f;
   last = 0;
@@ -186,7 +201,7 @@ __device__ __forceinline__ void forward_walk(float4* smem, uint8_t* wmask, uint8
       cp_async_wait<0>();
     }
     uint8_t* bm = pos0 + BATCH <= mcap ? mcache + pos0 : wmask;
-    compute_masks<BATCH>(buf, bm, cnt, c, cfg);
+    compute_masks<BATCH>(buf, bm, cnt, c, cfg, gmask ? gmask + pos0 : nullptr);
     __syncthreads();
     for (int g = 0; g < cnt; g += 32) {
       if (__all_sync(0xffffffffu, done)) break;

@@ -108,6 +108,7 @@ class RemovalEffectFrame:
                                                                    self.capacity), torch.uint8)
         self.inst_dse = P.get("inst_dse", self.capacity, torch.float32)
         self.inst_imp = P.get("inst_imp", self.capacity, torch.float32) if self.with_importance else None
+        self.warp_masks = P.get("warp_masks", self.capacity, torch.uint8)  # render -> stored-T backward
 
     def plan(self, slack: float = 1.05) -> int:
         """Run preprocess + binning once, grow the instance capacity to fit, return the count."""
@@ -133,6 +134,7 @@ class RemovalEffectFrame:
 
     def bin_sort(self, stream=None):
         """Binning + sort, then (with scheduling on) the longest-list-first tile order."""
+        self._sort_gen = getattr(self, "_sort_gen", 0) + 1
         self.status.zero_()
         B.potr_bin_sort(self.views, self.frame, self.cfg, self.n, self.capacity, self.tiles, self.vals, self.ranges,
                         self.status, self.ws, stream)
@@ -140,8 +142,12 @@ class RemovalEffectFrame:
             B.potr_tile_schedule(self.frame, self.ranges, self.order, self.sched_ws, stream)
 
     def render(self, images=None, t_final=None, n_last=None, stream=None):
+        masks = None
+        if t_final is not None:  # a backward pass with stored transmittance may follow: keep the warp masks
+            masks = self.warp_masks
+            self.pool.masks_owner = (id(self), getattr(self, "_sort_gen", 0))
         B.potr_render(self.views, self.frame, self.cfg, self.n, self.vals, self.ranges, images, t_final, n_last, stream,
-                      order=self.order)
+                      order=self.order, warp_masks=masks)
 
     def removal_effect(self, targets, dmse, importance=None, n_views_total=None, dsse_view=None, images=None,
                        stream=None, imp_view=None):
@@ -175,8 +181,11 @@ class RemovalEffectFrame:
         ws = self.pool.get("bwd_ws", B.potr_render_backward_workspace_size(self.capacity)
                            + 36 * self.n_views * self.n, torch.uint8)
         g = B.SceneGrads(*(grads[k].data_ptr() for k in SCENE_KEYS))
+        masks = None
+        if t_final is not None and getattr(self.pool, "masks_owner", None) == (id(self), getattr(self, "_sort_gen", 0)):
+            masks = self.warp_masks
         B.potr_render_backward(self.scene_c, self.views, self.frame, self.cfg, self.vals, self.ranges, t_final, n_last,
-                               dL_dimages, self.capacity, g, ws, stream, order=self.order)
+                               dL_dimages, self.capacity, g, ws, stream, order=self.order, warp_masks=masks)
 
     def pair_stats(self, stream=None) -> dict:
         """Exact pair counts of the forward and removal walks (see potr_pair_stats)."""
