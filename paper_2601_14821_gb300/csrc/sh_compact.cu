@@ -10,7 +10,8 @@
 // norm is 0); the DC column is always kept.  Pass 1 solves the ridge system (G_AA + lambda_c D)
 // x = b_A per YCoCg channel (lambda_Co = lambda_Cg = 3 lambda, D = 1 except on the DC), pass 2
 // re-solves each channel without the AC coefficients that pass 1 leaves quantising to zero
-// (floor(1/2 + x SF) == 0).  The factorisations are Cholesky decompositions by lane 0.
+// (floor(1/2 + x SF) == 0).  The factorisations are Cholesky decompositions, one channel per
+// lane (lanes 0-2, in parallel); the cosine test is lane 0's.
 #include "potr_device.cuh"
 
 namespace potr {
@@ -19,12 +20,17 @@ namespace {
 constexpr int kShWarps = 4;  // splats per block
 
 struct ShWarpMem {
-  double rows[32][20];  // per view of the chunk: w Y (0..15), w C in YCoCg (16..18)
+  union {
+    double rows[32][20];  // Gram phase: per view of the chunk, w Y (0..15), w C in YCoCg (16..18)
+    double M[3][16][16];  // solve phase: one Cholesky factor per channel
+  };
   double G[16][16];
   double b[16][3];
-  double M[16][16];
   double first[3][16];
   double second[3][16];
+  double Lc[3][16];  // the splat's current coefficients (RGB)
+  int cols[16];
+  int m;
 };
 
 // Real SH basis of degree <= 3 (Condon-Shortley phase), index l(l+1)+m, unit direction, binary64.
@@ -49,10 +55,10 @@ __device__ __forceinline__ void sh_basis16_f64(double x, double y, double z, dou
 }
 
 // Ridge solve over the kept columns `cols` (m of them, cols[0] = 0 the DC) for channel ch:
-// (G_AA + lam D) x = b_A with Cholesky (lane 0).  x is written for every column (0 outside).
+// (G_AA + lam D) x = b_A with Cholesky in L.  x is written for every column (0 outside).
 // Returns false if the matrix is not numerically positive definite.
-__device__ bool ridge_solve(ShWarpMem& w, const int* cols, int m, int ch, double lam, double* x) {
-  double (*L)[16] = w.M;
+__device__ bool ridge_solve(const ShWarpMem& w, const int* cols, int m, int ch, double lam, double* x,
+                            double (*L)[16]) {
   for (int i = 0; i < m; ++i)
     for (int j = 0; j <= i; ++j) L[i][j] = w.G[cols[i]][cols[j]] + ((i == j && cols[i] != 0) ? lam : 0.0);
   for (int j = 0; j < m; ++j) {
@@ -94,12 +100,8 @@ __global__ void __launch_bounds__(32 * kShWarps) sh_compact_kernel(int64_t n, co
   ShWarpMem& w = mem[wib];
   const int64_t warps_total = (int64_t)gridDim.x * kShWarps;
   for (int64_t k = (int64_t)blockIdx.x * kShWarps + wib; k < n; k += warps_total) {
-    // current coefficients (RGB) and position
-    double Lc[3][16];  // only lane-uniform use below; every lane loads all 48 (L1-cached)
-#pragma unroll
-    for (int i = 0; i < 16; ++i)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) Lc[c][i] = (double)sh[(int64_t)(i * 3 + c) * n + k];
+    // current coefficients (RGB, in shared memory) and position
+    for (int e = lane; e < 48; e += 32) w.Lc[e % 3][e / 3] = (double)sh[(int64_t)e * n + k];
     const double mx = means[k], my = means[n + k], mz = means[2 * n + k];
     for (int e = lane; e < 256; e += 32) (&w.G[0][0])[e] = 0.0;
     for (int e = lane; e < 48; e += 32) (&w.b[0][0])[e] = 0.0;
@@ -130,9 +132,9 @@ __global__ void __launch_bounds__(32 * kShWarps) sh_compact_kernel(int64_t n, co
         double rgb[3] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          rgb[0] += Lc[0][i] * Y[i];
-          rgb[1] += Lc[1][i] * Y[i];
-          rgb[2] += Lc[2][i] * Y[i];
+          rgb[0] += w.Lc[0][i] * Y[i];
+          rgb[1] += w.Lc[1][i] * Y[i];
+          rgb[2] += w.Lc[2][i] * Y[i];
         }
 #pragma unroll
         for (int i = 0; i < 16; ++i) row[i] = wt * Y[i];
@@ -170,46 +172,56 @@ __global__ void __launch_bounds__(32 * kShWarps) sh_compact_kernel(int64_t n, co
     if (lane == 0) {
       for (int i = 0; i < 16; ++i)
         for (int j = 0; j < i; ++j) w.G[i][j] = w.G[j][i];
-      uint32_t keep = 0, k1 = 0, k2 = 0, k3 = 0;
-      bool ok = w.G[0][0] > 0.0;  // some view sees the splat
-      if (ok) {
-        int cols[16], m = 1;
-        cols[0] = 0;
+      int m = 1;
+      w.cols[0] = 0;
+      if (w.G[0][0] > 0.0) {  // some view sees the splat
         for (int i = 1; i < 16; ++i) {
           if (!(w.G[i][i] > 0.0)) continue;
           bool par = false;
           for (int q = 0; q < m && !par; ++q) {
-            const int j = cols[q];
+            const int j = w.cols[q];
             par = fabs(w.G[i][j]) / sqrt(w.G[i][i] * w.G[j][j]) > alpha;
           }
-          if (!par) cols[m++] = i;
-        }
-        for (int q = 0; q < m; ++q) keep |= 1u << cols[q];
-        const double lams[3] = {lam, 3.0 * lam, 3.0 * lam};
-        for (int ch = 0; ch < 3 && ok; ++ch) ok = ridge_solve(w, cols, m, ch, lams[ch], w.first[ch]);
-        uint32_t* kk[3] = {&k1, &k2, &k3};
-        for (int ch = 0; ch < 3 && ok; ++ch) {
-          int c2[16], m2 = 1;
-          c2[0] = 0;
-          for (int q = 1; q < m; ++q)
-            if (floor(__dadd_rn(0.5, __dmul_rn(w.first[ch][cols[q]], sf))) != 0.0) c2[m2++] = cols[q];
-          for (int q = 0; q < m2; ++q) *kk[ch] |= 1u << c2[q];
-          ok = ridge_solve(w, c2, m2, ch, lams[ch], w.second[ch]);
+          if (!par) w.cols[m++] = i;
         }
       }
+      w.m = m;
+    }
+    __syncwarp();
+    // pass 1 then pass 2, channel `lane` on lanes 0-2
+    const bool seen = w.G[0][0] > 0.0;
+    const int m = w.m;
+    const double lam_c = lane == 0 ? lam : 3.0 * lam;
+    bool ok_lane = true;
+    uint32_t kbits = 0;
+    if (seen && lane < 3) ok_lane = ridge_solve(w, w.cols, m, lane, lam_c, w.first[lane], w.M[lane]);
+    bool ok = seen && __all_sync(0xffffffffu, ok_lane);
+    if (ok && lane < 3) {
+      int c2[16], m2 = 1;
+      c2[0] = 0;
+      for (int q = 1; q < m; ++q)
+        if (floor(__dadd_rn(0.5, __dmul_rn(w.first[lane][w.cols[q]], sf))) != 0.0) c2[m2++] = w.cols[q];
+      for (int q = 0; q < m2; ++q) kbits |= 1u << c2[q];
+      ok_lane = ridge_solve(w, c2, m2, lane, lam_c, w.second[lane], w.M[lane]);
+    }
+    ok = ok && __all_sync(0xffffffffu, ok_lane);
+    const uint32_t k1 = __shfl_sync(0xffffffffu, kbits, 0), k2 = __shfl_sync(0xffffffffu, kbits, 1),
+                   k3 = __shfl_sync(0xffffffffu, kbits, 2);
+    if (lane == 0) {
+      uint32_t keep = 0;
+      for (int q = 0; q < m; ++q) keep |= 1u << w.cols[q];
       if (!ok) {  // unseen (or not positive definite): keep the coefficients
         for (int i = 0; i < 16; ++i) {
-          w.second[0][i] = 0.25 * Lc[0][i] + 0.5 * Lc[1][i] + 0.25 * Lc[2][i];
-          w.second[1][i] = 0.5 * Lc[0][i] - 0.5 * Lc[2][i];
-          w.second[2][i] = -0.25 * Lc[0][i] + 0.5 * Lc[1][i] - 0.25 * Lc[2][i];
+          w.second[0][i] = 0.25 * w.Lc[0][i] + 0.5 * w.Lc[1][i] + 0.25 * w.Lc[2][i];
+          w.second[1][i] = 0.5 * w.Lc[0][i] - 0.5 * w.Lc[2][i];
+          w.second[2][i] = -0.25 * w.Lc[0][i] + 0.5 * w.Lc[1][i] - 0.25 * w.Lc[2][i];
         }
-        keep = k1 = k2 = k3 = 0;
       }
       if (kept_out) {
-        kept_out[k] = keep;
-        kept_out[n + k] = k1;
-        kept_out[2 * n + k] = k2;
-        kept_out[3 * n + k] = k3;
+        kept_out[k] = ok ? keep : 0u;
+        kept_out[n + k] = ok ? k1 : 0u;
+        kept_out[2 * n + k] = ok ? k2 : 0u;
+        kept_out[3 * n + k] = ok ? k3 : 0u;
       }
     }
     __syncwarp();

@@ -128,3 +128,35 @@ def test_autograd_function_matches_c_path(tiny):
             g = g.cpu().numpy().astype(np.float64)
             w = want[k]
             assert np.allclose(g, w, rtol=1e-5, atol=1e-7 * np.abs(w).max()), k
+
+
+@pytest.mark.parametrize("cfg", [dict(tile_w=16, tile_h=16, batch=256), dict(tile_w=32, tile_h=8, batch=128)])
+def test_stored_warp_masks_give_identical_gradients(cfg):
+    """The backward pass with the render's stored warp masks, with masks recomputed per batch,
+    and with the whole forward walk recomputed produce the same bits (the masks are the same
+    function of the records; only where they are computed changes)."""
+    import torch
+
+    scene = synth.uniform_cube_scene(6000, 91)
+    cams = [synth.look_at_camera((0.0, 0.3, -3.0), 160, 120), synth.look_at_camera((2.5, -0.2, -1.5), 96, 130)]
+    fr = build_frame(scene, cams, **cfg)
+    tg = pack_targets(fr, _targets(scene, cams, cfg, 5))
+    img, tf, nl = fr.image_buffer(), fr.pixel_buffer(), fr.pixel_buffer(torch.int32)
+    fr.render(img, tf, nl)
+    dL = torch.empty_like(img)
+    fr.loss_grad(img, tg, 0.2, dL)
+    out = []
+    for mode in ("stored masks", "masks recomputed", "forward recomputed"):
+        grads = {k: torch.empty_like(fr.scene[k]) for k in KEYS}
+        if mode == "masks recomputed":
+            fr.pool.masks_owner = None  # the frame no longer offers the render's masks
+        if mode == "forward recomputed":
+            fr.render_backward(dL, grads)
+        else:
+            fr.render_backward(dL, grads, tf, nl)
+        torch.cuda.synchronize()
+        out.append({k: v.cpu().numpy() for k, v in grads.items()})
+    for k in KEYS:
+        assert np.array_equal(out[0][k], out[1][k]), k
+        assert np.array_equal(out[0][k], out[2][k]), k
+    assert any(np.abs(out[0][k]).max() > 0 for k in KEYS)
