@@ -84,13 +84,15 @@ class FineTuner:
 
 
 def potr_ft(scene: dict, cams_rec: np.ndarray, targets: list, eyes, q: float = 0.5, cycles: int = 2,
-            iterations: int = 500, lam: float = 0.2, extent: float = 1.0, seed: int = 0, **cfg) -> dict:
+            iterations: int = 500, lam: float = 0.2, extent: float = 1.0, seed: int = 0, compress: bool = True,
+            **cfg) -> dict:
     """POTR-FT (Section IV-F): ``cycles`` rounds of decode -> fine-tune -> encode, every step on the
-    device (the codec's zlib stage is lossless and is applied once, to the final bitstream).  The
-    scene must hold only live splats (compact a pruned scene first).  Returns the final
-    bitstream (raw and compressed), the fine-tuned scene before its last encoding, and the loss
-    after each cycle's fine-tuning."""
-    from .codec import encode, params, roundtrip
+    device (the codec's zlib stage is lossless and is applied once, to the final bitstream, on the
+    host; ``compress=False`` leaves it to the caller).  The scene must hold only live splats
+    (compact a pruned scene first).  Returns the final bitstream (raw, and compressed unless
+    ``compress`` is False), the fine-tuned scene before its last encoding, and the loss after
+    each cycle's fine-tuning."""
+    from .codec import Encoder, encode, params, roundtrip
 
     p = params(q)
     losses = []
@@ -99,7 +101,12 @@ def potr_ft(scene: dict, cams_rec: np.ndarray, targets: list, eyes, q: float = 0
         ft = FineTuner(decoded, cams_rec, targets, lam=lam, extent=extent, device=scene["means"].device, **cfg)
         losses.append(ft.run(iterations, seed=seed + c))
         scene = ft.scene
-    out = encode(scene, eyes, p=p)
+    if compress:
+        out = encode(scene, eyes, p=p)
+    else:
+        enc = Encoder(int(scene["means"].shape[-1]), scene["means"].device)
+        enc.run(scene, eyes, p)
+        out = {"raw": enc.stream(p), "order": enc.order.cpu().numpy()}
     out["scene"] = scene
     out["losses"] = losses
     return out
