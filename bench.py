@@ -3,7 +3,7 @@
 A step is one pass of the whole path over one frame: activation + EWA projection of 1M
 splats into 16 views of 1280x720, tile binning + radix sort of every (tile, splat) instance,
 and the removal-effect pass with the per-splat dMSE_k / I_k reduction.  Inputs (the 236 MB of
-splat parameters, the 1 GB of per-view raster records, 0.45 GB of instances) are larger than
+splat parameters, the 0.77 GB of per-view raster records, 0.45 GB of instances) are larger than
 the 129 MB L2, so no L2 flush is needed between steps.
 
 Printed (one JSON line on rank 0): the device-timed throughput of the batched frame
@@ -47,10 +47,10 @@ FLOP_REMOVAL = 26        # T recovery, ratio, PD and dSE over 3 channels, suffix
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 PEAK_FP32_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 # DRAM bytes (read + written) of one removal-kernel launch per view of the scene workload: an
-# ncu capture of the 4-view case measured 255.5 MB (dram__bytes_read.sum 209.6 MB +
-# dram__bytes_write.sum 45.8 MB); the traffic grows with the views (records gathered per tile),
+# ncu capture of the 4-view case measured 440.1 MB (dram__bytes_read.sum 386.4 MB +
+# dram__bytes_write.sum 53.7 MB); the traffic grows with the views (records gathered per tile),
 # so a 16-view launch moves 16 x this.
-REMOVAL_DRAM_BYTES_PER_VIEW = 255.45e6 / 4
+REMOVAL_DRAM_BYTES_PER_VIEW = 440.12e6 / 4
 
 
 def parse():
@@ -376,7 +376,7 @@ def run_ours(args):
                        "n_splats": int(frame.n), "views_per_gpu": n_views, "resolution": "1280x720",
                        "tile": f"{CFG['tile_w']}x{CFG['tile_h']}", "splat_batch": CFG["batch"],
                        "form": "batched frame (all views in one launch per stage)", "instances": int(n_inst),
-                       "l2": "inputs larger than L2 (236 MB parameters, 1 GB raster records, 0.45 GB instances)",
+                       "l2": "inputs larger than L2 (236 MB parameters, 0.77 GB raster records, 0.45 GB instances)",
                        "parallelism": f"views replicated per GPU x{world}"},
             "stage_ms": {"preprocess": stage_ms[0], "bin_sort": stage_ms[1], "removal_effect": stage_ms[2]},
             "graph_views_per_s": graph_vps,

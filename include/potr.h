@@ -117,25 +117,28 @@ typedef struct {
 
 /*
  * Per-(view, splat) buffers produced by potr_preprocess and potr_bin_sort (device, caller
- * owned).  raster holds 16 floats (64 bytes) per vk, 16-byte aligned:
- *   [0] mean x  [1] mean y  [2] A  [3] B  [4] C  [5] opacity  [6] prefilter  [7] offset bits
+ * owned).  raster holds 12 floats (48 bytes) per vk, 16-byte aligned (written for the vk with
+ * kept tiles):
+ *   [0] mean x  [1] mean y  [2] A  [3] B  [4] C  [5] opacity  [6] prefilter  [7] 0
  *   [8] r       [9] g       [10] b [11] rectangle bits (x0 | y0 << 11 | width << 22)
- *   [12] kept-tile mask, low word  [13] high word  [14] rectangle bits (as [11])
- *   [15] kept tiles | (1 << 31 if every tile is kept)
- * where log2 G(dx, dy) = A dx^2 + B dx dy + C dy^2, "offset" is the vk's first emission
- * slot (written by potr_bin_sort) and mask bit (ty - y0) width + (tx - x0) says whether
- * tile (tx, ty) of the rectangle is kept (rectangles of at most 64 tiles; larger ones keep
- * every tile).
+ * where log2 G(dx, dy) = A dx^2 + B dx dy + C dy^2.  cull holds 4 words per vk, 16-byte
+ * aligned (written for every vk):
+ *   [0] kept-tile mask, low word  [1] high word  [2] rectangle bits (as raster [11])
+ *   [3] kept tiles | (1 << 31 if every tile is kept)
+ * where mask bit (ty - y0) width + (tx - x0) says whether tile (tx, ty) of the rectangle is
+ * kept (rectangles of at most 64 tiles; larger ones keep every tile).  A vk's emission slots
+ * start at offsets[vk] (written by potr_bin_sort).
  */
 typedef struct {
   float* cov3d;          /* [6][n] activated covariance (xx, xy, xz, yy, yz, zz) */
   float* opacity;        /* [n] */
-  float* raster;         /* [V * n][16] */
+  float* raster;         /* [V * n][12] */
   float* depth;          /* [V * n] camera-space z, the sort key's low word */
   uint32_t* rect;        /* [V * n][2] (x0 | y0 << 16, x1 | y1 << 16), tiles, half open */
   uint32_t* touched;     /* [V * n] kept tiles, 0 when culled */
   uint32_t* offsets;     /* [V * n] exclusive prefix sum of touched (emission slots) */
   uint32_t* n_instances; /* [1] total instances (potr_bin_sort) */
+  uint32_t* cull;        /* [V * n][4] kept-tile mask, rectangle, kept count (see above) */
 } potr_views;
 
 /* Text for a status code (static string). */
@@ -193,8 +196,8 @@ POTR_API size_t potr_bin_sort_workspace_size(int64_t n, int32_t n_views, int64_t
  * Binning (Section 3, "ordering these layers according to the splats' approximate depth").
  * Defined result: one instance per kept tile, emitted in vk order and, within a rectangle,
  * row-major, with key (global tile << 32) | bits(depth) and value vk, stably sorted by key;
- * its emission slot is views->offsets[vk] (exclusive scan of touched over vk, also stored in
- * record word 7) plus the tile's rank among the vk's kept tiles.  Outputs: d_tiles[i] = the
+ * its emission slot is views->offsets[vk] (exclusive scan of touched over vk) plus the tile's
+ * rank among the vk's kept tiles.  Outputs: d_tiles[i] = the
  * global tile (the key's high word) and d_vals[i] = vk of sorted instance i, both
  * instance_capacity entries; *views->n_instances; per-global-tile [start, end) ranges into
  * d_tile_ranges[total_tiles][2] (empty tiles get [0, 0)).  Computed as a stable radix sort

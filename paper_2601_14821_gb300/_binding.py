@@ -64,7 +64,7 @@ class Frame(C.Structure):
 class Views(C.Structure):
     _fields_ = [("cov3d", C.c_void_p), ("opacity", C.c_void_p), ("raster", C.c_void_p), ("depth", C.c_void_p),
                 ("rect", C.c_void_p), ("touched", C.c_void_p), ("offsets", C.c_void_p),
-                ("n_instances", C.c_void_p)]
+                ("n_instances", C.c_void_p), ("cull", C.c_void_p)]
 
 
 class SceneGrads(C.Structure):

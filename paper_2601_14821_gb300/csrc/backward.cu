@@ -105,7 +105,9 @@ __global__ void __launch_bounds__(kThreads, 4) render_bwd_kernel(const float4* _
                                                               const uint32_t* __restrict__ n_last,
                                                               const float* __restrict__ dL_dimg, int64_t capacity,
                                                               float* __restrict__ inst_grad,
-                                                              const uint8_t* __restrict__ gmask, TileQueue queue) {
+                                                              const uint8_t* __restrict__ gmask,
+                                                              const uint4* __restrict__ cull,
+                                                              const uint32_t* __restrict__ offsets, TileQueue queue) {
   extern __shared__ float4 dyn[];
   float4* smem = dyn;                                                // [2][kBwdBatch][kSRec]
   float* red = reinterpret_cast<float*>(dyn + 2 * kSRec * kBwdBatch);        // [kGradQ][kWarps][kBwdBatch]
@@ -274,8 +276,8 @@ __global__ void __launch_bounds__(kThreads, 4) render_bwd_kernel(const float4* _
         nz |= t != 0.0f;
       }
       if (nz) {
-        const float4 m = raster[(size_t)vals[c.s + lo + j] * kRec + 3];  // mask word (L2)
-        const uint32_t slot = emission_slot(buf + kSRec * j, m, c.tx, c.ty);
+        const uint32_t vk = vals[c.s + lo + j];
+        const uint32_t slot = emission_slot(offsets[vk], cull[vk], c.tx, c.ty);  // L2
 #pragma unroll
         for (int q = 0; q < kGradQ; ++q) inst_grad[(int64_t)q * capacity + slot] = sq[q];
       }
@@ -631,7 +633,8 @@ extern "C" potr_status potr_render_backward(const potr_scene* scene, const potr_
   if (!scene->means || !scene->log_scales || !scene->quats || !scene->sh || scene->n <= 0) return POTR_ERR_INVALID_ARGUMENT;
   if (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logits || !grads->sh)
     return POTR_ERR_INVALID_ARGUMENT;
-  if (!views->raster || !views->cov3d || !views->opacity || !views->touched || !views->offsets || !views->n_instances)
+  if (!views->raster || !views->cov3d || !views->opacity || !views->touched || !views->offsets || !views->n_instances ||
+      !views->cull)
     return POTR_ERR_INVALID_ARGUMENT;
   if ((d_t_final == nullptr) != (d_n_last == nullptr)) return POTR_ERR_INVALID_ARGUMENT;
   if (frame->total_tiles <= 0 || frame->total_tiles > 0x7fffffffll || !frame->cams || !frame->info)
@@ -656,14 +659,16 @@ extern "C" potr_status potr_render_backward(const potr_scene* scene, const potr_
       return POTR_ERR_CUDA;
     render_bwd_kernel<true><<<tile_grid(render_bwd_kernel<true>, smem, q, frame->total_tiles), kThreads, smem, s>>>(
         reinterpret_cast<const float4*>(views->raster), d_vals, d_tile_ranges, frame->info, frame->n_views, *cfg,
-        nullptr, nullptr, d_dL_dimages, instance_capacity, inst_grad, nullptr, q);
+        nullptr, nullptr, d_dL_dimages, instance_capacity, inst_grad, nullptr,
+        reinterpret_cast<const uint4*>(views->cull), views->offsets, q);
   } else {
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(render_bwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return POTR_ERR_CUDA;
     render_bwd_kernel<false><<<tile_grid(render_bwd_kernel<false>, smem, q, frame->total_tiles), kThreads, smem, s>>>(
         reinterpret_cast<const float4*>(views->raster), d_vals, d_tile_ranges, frame->info, frame->n_views, *cfg,
-        d_t_final, d_n_last, d_dL_dimages, instance_capacity, inst_grad, d_warp_masks, q);
+        d_t_final, d_n_last, d_dL_dimages, instance_capacity, inst_grad, d_warp_masks,
+        reinterpret_cast<const uint4*>(views->cull), views->offsets, q);
   }
   POTR_CHECK_LAUNCH();
   const int64_t n = scene->n;

@@ -35,22 +35,16 @@ __global__ void count_check_kernel(const uint64_t* __restrict__ total, int64_t c
 }
 
 // Depth sort keys of every vk (bits of the camera-space depth, which order like the positive
-// floats they are; 0xffffffff for a vk without kept tiles, so it sorts last), the digit
-// histograms of the four depth passes, and the vk's first emission slot into record word 7.
+// floats they are; 0xffffffff for a vk without kept tiles, so it sorts last) and the digit
+// histograms of the four depth passes.
 __global__ void __launch_bounds__(256) depth_key_kernel(const uint32_t* __restrict__ touched,
-                                                        const uint32_t* __restrict__ offsets,
                                                         const float* __restrict__ depth, int64_t n_vk,
-                                                        float4* __restrict__ raster, uint32_t* __restrict__ keys,
-                                                        uint32_t* __restrict__ ghist) {
+                                                        uint32_t* __restrict__ keys, uint32_t* __restrict__ ghist) {
   __shared__ uint32_t h[4][256];
   for (int p = 0; p < 4; ++p) h[p][threadIdx.x] = 0;
   __syncthreads();
   for (int64_t vk = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; vk < n_vk; vk += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t key = 0xffffffffu;
-    if (touched[vk]) {
-      key = __float_as_uint(depth[vk]);
-      reinterpret_cast<float*>(raster + vk * kRec + 1)[3] = __uint_as_float(offsets[vk]);
-    }
+    const uint32_t key = touched[vk] ? __float_as_uint(depth[vk]) : 0xffffffffu;
     keys[vk] = key;
 #pragma unroll
     for (int p = 0; p < 4; ++p) atomicAdd(&h[p][(key >> (8 * p)) & 0xffu], 1u);
@@ -74,7 +68,7 @@ __global__ void __launch_bounds__(256) depth_key_kernel(const uint32_t* __restri
 __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ eoff,
                                                    const potr_view_info* __restrict__ info, int64_t n, int64_t n_vk,
                                                    const uint64_t* __restrict__ m_eff,
-                                                   const float4* __restrict__ raster, uint32_t* __restrict__ keys,
+                                                   const uint4* __restrict__ cull, uint32_t* __restrict__ keys,
                                                    uint32_t* __restrict__ vals, int passes, uint32_t* __restrict__ ghist) {
   __shared__ uint32_t h[kMaxPasses][256];
   for (int p = 0; p < passes; ++p) h[p][threadIdx.x] = 0;
@@ -88,17 +82,17 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
     if (i < n_vk) {
       vk = order[i];
       off = eoff[i];
-      // record words 12..15: kept-tile mask, rectangle word, kept count | all-kept << 31
-      const float4 m = raster[(size_t)vk * kRec + 3];
-      cnt = __float_as_uint(m.w) & 0x7fffffffu;
+      // culling word: kept-tile mask, rectangle word, kept count | all-kept << 31
+      const uint4 m = cull[vk];
+      cnt = m.w & 0x7fffffffu;
       if (cnt) {
         const potr_view_info& vi = info[(int)(vk / (uint64_t)n)];
-        const uint32_t rw = __float_as_uint(m.z);
+        const uint32_t rw = m.z;
         const uint32_t tiles_x = (uint32_t)vi.tiles_x;
         corner = (uint32_t)vi.tile_base + ((rw >> 11) & 0x7ffu) * tiles_x + (rw & 0x7ffu);
-        pk = (rw >> 22) | ((__float_as_uint(m.w) >> 31) << 11) | (tiles_x << 12);
-        m_lo = __float_as_uint(m.x);
-        m_hi = __float_as_uint(m.y);
+        pk = (rw >> 22) | ((m.w >> 31) << 11) | (tiles_x << 12);
+        m_lo = m.x;
+        m_hi = m.y;
       }
     }
     uint32_t incl = cnt;
@@ -250,7 +244,7 @@ extern "C" size_t potr_bin_sort_workspace_size(int64_t n, int32_t n_views, int64
 
 // Binning in four steps, every one integer work and bit-exact:
 //   1. exclusive scan of the kept-tile counts in vk order -> offsets (emission slots of the
-//      vk-order definition, kept in record word 7) and the instance total;
+//      vk-order definition, in views->offsets) and the instance total;
 //   2. a stable LSD radix sort (4 x 8-bit passes) of the vk by depth bits: ties keep vk order;
 //   3. emission in that depth order (slots from a second scan of the counts, in depth order),
 //      key = global tile, value = vk;
@@ -265,7 +259,8 @@ extern "C" potr_status potr_bin_sort(const potr_views* views, const potr_frame* 
   if (!views || !frame || !cfg || !d_tiles || !d_vals || !d_tile_ranges || !d_ws) return POTR_ERR_INVALID_ARGUMENT;
   if (n <= 0 || frame->n_views < 1 || frame->total_tiles <= 0 || !frame->info) return POTR_ERR_INVALID_ARGUMENT;
   if (instance_capacity <= 0 || instance_capacity > (int64_t)0xffffffffll) return POTR_ERR_INVALID_ARGUMENT;
-  if (!views->touched || !views->offsets || !views->rect || !views->depth || !views->raster || !views->n_instances)
+  if (!views->touched || !views->offsets || !views->rect || !views->depth || !views->raster || !views->n_instances ||
+      !views->cull)
     return POTR_ERR_INVALID_ARGUMENT;
   if (frame->total_tiles > (int64_t)0xffffffffll || n * (int64_t)frame->n_views >= (int64_t)0xffffffffll)
     return POTR_ERR_UNSUPPORTED;
@@ -306,7 +301,7 @@ extern "C" potr_status potr_bin_sort(const potr_views* views, const potr_frame* 
   {
     const int64_t g = ceil_div(L.n_vk, 256);
     depth_key_kernel<<<(unsigned)(g < 152 * 8 ? g : 152 * 8), 256, 0, s>>>(
-        views->touched, views->offsets, views->depth, L.n_vk, reinterpret_cast<float4*>(views->raster), dk0, ghist);
+        views->touched, views->depth, L.n_vk, dk0, ghist);
     POTR_CHECK_LAUNCH();
     digit_base_kernel<<<1, 256, 0, s>>>(ghist, 4, gbase);
     POTR_CHECK_LAUNCH();
@@ -333,7 +328,7 @@ extern "C" potr_status potr_bin_sort(const potr_views* views, const potr_frame* 
   {
     const int64_t g = ceil_div(L.n_vk, 256);
     emit_kernel<<<(unsigned)(g < 152 * 16 ? g : 152 * 16), 256, 0, s>>>(
-        order, dv1, frame->info, n, L.n_vk, m_eff, reinterpret_cast<const float4*>(views->raster), k_src, v_src,
+        order, dv1, frame->info, n, L.n_vk, m_eff, reinterpret_cast<const uint4*>(views->cull), k_src, v_src,
         tile_passes, ghist + 256 * 4);
     POTR_CHECK_LAUNCH();
     digit_base_kernel<<<1, 256, 0, s>>>(ghist + 256 * 4, tile_passes, gbase + 256 * 4);

@@ -14,7 +14,7 @@
 namespace potr {
 
 constexpr int kTilePixels = 256;  // tile_w * tile_h
-constexpr int kRec = 4;           // raster record: 4 x float4 (64 bytes) per (view, splat)
+constexpr int kRec = 3;           // raster record: 3 x float4 (48 bytes) per (view, splat)
 constexpr int kCullMaxTiles = 64;  // rectangles with more tiles keep every tile
 constexpr float kLog2e = 1.44269504088896340736f;
 

@@ -8,7 +8,7 @@
 //                     centre, covariance, opacity and (on first visibility) its 48 SH
 //                     coefficients are read once and kept in registers for all views.
 // Both are HBM-bound: 32 B read / 28 B written per splat for activation; 40 B read per splat
-// plus 192 B of SH per splat visible in the frame, and 64 B written per visible (view, splat).
+// plus 192 B of SH per splat visible in the frame, and 48 B written per visible (view, splat).
 #include "potr_device.cuh"
 
 namespace potr {
@@ -205,12 +205,13 @@ __global__ void __launch_bounds__(256) project_kernel(const float* __restrict__ 
 // consecutive vk: their candidate tiles (rectangle cells, row-major) are dealt to the lanes 32
 // at a time, each lane runs the tile test for one candidate (owner found by a shuffle search over
 // the warp's exclusive candidate counts), and every owner collects its bits from the ballot.
-// Writes record words 12..15 of every vk -- mask low, mask high, the rectangle word (as word
-// 11) and the kept count | all-kept flag << 31 (0 for a culled vk) -- and touched = the kept
-// count, so that the emission reads one 16-byte word per vk.
+// Writes the culling word of every vk -- mask low, mask high, the rectangle word (as record
+// word 11) and the kept count | all-kept flag << 31 (0 for a culled vk) -- to its own 16-byte
+// array (coalesced whole-sector stores, not a partial rewrite of the record), and touched = the
+// kept count, so that the emission reads one 16-byte word per vk.
 __global__ void __launch_bounds__(256) tile_mask_kernel(const uint2* __restrict__ rect, int64_t n_vk,
-                                                        potr_raster_config cfg, float4* __restrict__ raster,
-                                                        uint32_t* __restrict__ touched) {
+                                                        potr_raster_config cfg, const float4* __restrict__ raster,
+                                                        uint4* __restrict__ cull, uint32_t* __restrict__ touched) {
   const int lane = threadIdx.x & 31;
   const int64_t warps_total = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t wv = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wv * 32 < n_vk; wv += warps_total) {
@@ -281,8 +282,7 @@ __global__ void __launch_bounds__(256) tile_mask_kernel(const uint2* __restrict_
       const bool all = area > (uint32_t)kCullMaxTiles;
       const uint32_t kept = all ? area : (uint32_t)__popcll(mask);
       const uint32_t rw = area ? pack_rect_word(x0, y0, w) : 0u;
-      raster[vk * kRec + 3] = make_float4(__uint_as_float((uint32_t)mask), __uint_as_float((uint32_t)(mask >> 32)),
-                                          __uint_as_float(rw), __uint_as_float(kept | (all ? 0x80000000u : 0u)));
+      cull[vk] = make_uint4((uint32_t)mask, (uint32_t)(mask >> 32), rw, kept | (all ? 0x80000000u : 0u));
       if (area) touched[vk] = kept;
     }
   }
@@ -329,9 +329,11 @@ extern "C" potr_status potr_preprocess(const potr_scene* scene, const potr_frame
   if (scene->n <= 0 || frame->n_views < 1 || !frame->cams || !frame->info) return POTR_ERR_INVALID_ARGUMENT;
   if (!scene->means || !scene->log_scales || !scene->quats || !scene->opacity_logits || !scene->sh)
     return POTR_ERR_INVALID_ARGUMENT;
-  if (!views->cov3d || !views->opacity || !views->raster || !views->depth || !views->rect || !views->touched)
+  if (!views->cov3d || !views->opacity || !views->raster || !views->depth || !views->rect || !views->touched ||
+      !views->cull)
     return POTR_ERR_INVALID_ARGUMENT;
-  if ((reinterpret_cast<uintptr_t>(views->raster) & 15) != 0) return POTR_ERR_INVALID_ARGUMENT;
+  if ((reinterpret_cast<uintptr_t>(views->raster) & 15) != 0 || (reinterpret_cast<uintptr_t>(views->cull) & 15) != 0)
+    return POTR_ERR_INVALID_ARGUMENT;
   if ((int64_t)frame->n_views * scene->n >= (int64_t)UINT32_MAX) return POTR_ERR_UNSUPPORTED;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int64_t n = scene->n;
@@ -345,7 +347,8 @@ extern "C" potr_status potr_preprocess(const potr_scene* scene, const potr_frame
   POTR_CHECK_LAUNCH();
   const int64_t n_vk = n * frame->n_views;
   potr::tile_mask_kernel<<<potr::grid_for(n_vk, 256, 152 * 16), 256, 0, s>>>(
-      reinterpret_cast<const uint2*>(views->rect), n_vk, *cfg, reinterpret_cast<float4*>(views->raster), views->touched);
+      reinterpret_cast<const uint2*>(views->rect), n_vk, *cfg, reinterpret_cast<const float4*>(views->raster),
+      reinterpret_cast<uint4*>(views->cull), views->touched);
   POTR_CHECK_LAUNCH();
   return POTR_OK;
 }

@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(kThreads, BATCH <= 128 ? 6 : 5) removal_kernel
                                                            const potr_view_info* __restrict__ info, int n_views,
                                                            potr_raster_config cfg, const float* __restrict__ targets,
                                                            float* __restrict__ images, float* __restrict__ inst_dse,
-                                                           float* __restrict__ inst_imp, TileQueue queue) {
+                                                           float* __restrict__ inst_imp, const uint4* __restrict__ cull,
+                                                           const uint32_t* __restrict__ offsets, TileQueue queue) {
   extern __shared__ float4 dyn[];
   float4* smem = dyn;                                               // [2][BATCH][kSRec] raster records
   float* red_d = reinterpret_cast<float*>(dyn + 2 * kSRec * BATCH);  // [kWarps][BATCH] warp sums of dSE
@@ -238,8 +239,8 @@ __global__ void __launch_bounds__(kThreads, BATCH <= 128 ? 6 : 5) removal_kernel
         if (IMP) si += red_i[w * BATCH + j];
       }
       if (sd != 0.0f || (IMP && si != 0.0f)) {
-        const float4 m = raster[(size_t)vals[c.s + lo + j] * kRec + 3];  // mask word (L2)
-        const uint32_t slot = emission_slot(buf + kSRec * j, m, c.tx, c.ty);
+        const uint32_t vk = vals[c.s + lo + j];
+        const uint32_t slot = emission_slot(offsets[vk], cull[vk], c.tx, c.ty);  // L2
         inst_dse[slot] = sd;
         if (IMP) inst_imp[slot] = si;
       }
@@ -362,7 +363,8 @@ cudaError_t launch_removal(const potr_views* views, const potr_frame* frame, con
   const unsigned grid = tile_grid(removal_kernel<BATCH, IMP>, smem, q, frame->total_tiles);
   removal_kernel<BATCH, IMP><<<grid, kThreads, smem, s>>>(reinterpret_cast<const float4*>(views->raster), vals, ranges,
                                                           frame->info, frame->n_views, cfg, targets, images, inst_dse,
-                                                          inst_imp, q);
+                                                          inst_imp, reinterpret_cast<const uint4*>(views->cull),
+                                                          views->offsets, q);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -411,7 +413,7 @@ extern "C" potr_status potr_removal_effect(const potr_views* views, const potr_f
   using namespace potr;
   if (!views || !frame || !valid_cfg(cfg) || !d_vals || !d_tile_ranges || !d_targets || !d_inst_dse)
     return POTR_ERR_INVALID_ARGUMENT;
-  if (!views->raster || !views->touched || !views->offsets || !views->n_instances || !frame->info)
+  if (!views->raster || !views->touched || !views->offsets || !views->n_instances || !views->cull || !frame->info)
     return POTR_ERR_INVALID_ARGUMENT;
   if (n <= 0 || frame->n_views < 1 || n_views_total < 1 || instance_capacity <= 0) return POTR_ERR_INVALID_ARGUMENT;
   if (frame->total_tiles <= 0 || frame->total_tiles > 0x7fffffffll) return POTR_ERR_INVALID_ARGUMENT;

@@ -9,7 +9,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kSRec = 3;  // float4 per record in shared memory: the first three of the kRec
+constexpr int kSRec = 3;  // float4 per record in shared memory: the whole record
 constexpr int kWarpW = 8, kWarpH = 4;  // pixel block of one warp
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -235,17 +235,16 @@ __device__ __forceinline__ void forward_walk(float4* smem, uint8_t* wmask, uint8
   cp_async_wait<0>();  // after an early exit the next batch may still be landing
 }
 
-// Emission slot of the instance in tile (tx, ty) of the splat whose staged record is r (r[1].w:
-// first slot, r[2].w: rectangle word) and whose record word 12..15 is m: the first slot plus the
-// number of its kept tiles before (tx, ty) in row-major order of its rectangle (bit 31 of m.w
-// flags a rectangle that keeps every tile).
-__device__ __forceinline__ uint32_t emission_slot(const float4* r, const float4& m, int tx, int ty) {
-  const uint32_t off = __float_as_uint(r[1].w);
-  const uint32_t rw = __float_as_uint(r[2].w);
+// Emission slot of the instance in tile (tx, ty) of the splat whose first emission slot is off
+// and whose culling word is m (kept-tile mask low / high, rectangle word, kept count | all-kept
+// << 31): the first slot plus the number of its kept tiles before (tx, ty) in row-major order
+// of its rectangle.
+__device__ __forceinline__ uint32_t emission_slot(uint32_t off, const uint4& m, int tx, int ty) {
+  const uint32_t rw = m.z;
   const uint32_t x0 = rw & 0x7ffu, y0 = (rw >> 11) & 0x7ffu, w = rw >> 22;
   const uint32_t pos = ((uint32_t)ty - y0) * w + ((uint32_t)tx - x0);
-  if (__float_as_uint(m.w) >> 31) return off + pos;
-  const uint64_t mask = ((uint64_t)__float_as_uint(m.y) << 32) | __float_as_uint(m.x);
+  if (m.w >> 31) return off + pos;
+  const uint64_t mask = ((uint64_t)m.y << 32) | m.x;
   return off + (uint32_t)__popcll(mask & ((1ull << pos) - 1ull));
 }
 

@@ -86,7 +86,8 @@ class RemovalEffectFrame:
         """(Re)take every pooled buffer at the current sizes and rebuild the C views."""
         vn = self.n_views * self.n
         i32, P = torch.int32, self.pool
-        self.raster = P.get("raster", vn * 16, torch.float32)
+        self.raster = P.get("raster", vn * 12, torch.float32)
+        self.cull = P.get("cull", vn * 4, i32)
         self.depth = P.get("depth", vn, torch.float32)
         self.rect = P.get("rect", 2 * vn, i32)
         self.touched = P.get("touched", vn, i32)
@@ -96,7 +97,7 @@ class RemovalEffectFrame:
         self.order = P.get("order", self.total_tiles + 1, i32) if self.schedule else None
         self.views = B.Views(self.cov3d.data_ptr(), self.opacity.data_ptr(), self.raster.data_ptr(),
                              self.depth.data_ptr(), self.rect.data_ptr(), self.touched.data_ptr(),
-                             self.offsets.data_ptr(), self.n_instances.data_ptr())
+                             self.offsets.data_ptr(), self.n_instances.data_ptr(), self.cull.data_ptr())
         self._alloc(self.capacity)
 
     def _alloc(self, capacity: int):

@@ -6,8 +6,8 @@ import numpy as np
 import oracle
 import synth
 
-RASTER_FIELDS = ("mx", "my", "A", "B", "C", "o", "pthr", "offset", "r", "g", "b", "rectw", "mask_lo", "mask_hi",
-                 "rectw2", "kept")
+RASTER_FIELDS = ("mx", "my", "A", "B", "C", "o", "pthr", "zero", "r", "g", "b", "rectw")
+CULL_FIELDS = ("mask_lo", "mask_hi", "rectw2", "kept")
 
 
 def oracle_cfg(cfg: dict):
@@ -29,10 +29,12 @@ def build_frame(scene, cams, **cfg):
 
 
 def unpack_raster(fr) -> dict:
-    r = fr.raster.cpu().numpy().reshape(-1, 16)
+    r = fr.raster.cpu().numpy().reshape(-1, 12)
+    cu = fr.cull.cpu().numpy().view(np.uint32).reshape(-1, 4)
     out = {k: r[:, i] for i, k in enumerate(RASTER_FIELDS)}
-    for k in ("offset", "rectw", "mask_lo", "mask_hi", "rectw2", "kept"):
-        out[k] = r[:, RASTER_FIELDS.index(k)].view(np.uint32)
+    out["rectw"] = out["rectw"].view(np.uint32)
+    for i, k in enumerate(CULL_FIELDS):
+        out[k] = cu[:, i]
     out["all_tiles"] = out["kept"] >> np.uint32(31)
     out["kept"] = out["kept"] & np.uint32(0x7FFFFFFF)
     out["mask"] = out["mask_lo"].astype(np.uint64) | (out["mask_hi"].astype(np.uint64) << np.uint64(32))
