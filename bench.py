@@ -36,7 +36,7 @@ import numpy as np  # noqa: E402
 
 METRIC = "removal-effect views/s & Gblend/s (batched vs per-view); fwd+bwd ms/step"
 WORKLOAD = "scene"
-CFG = dict(tile_w=16, tile_h=16, batch=256)
+CFG = dict(tile_w=16, tile_h=16, batch=128)
 # Algorithmic FP32 work per pair (FMA = 2 FLOP), counted from the kernel's operation spec.
 # Only pairs whose opacity reaches the prefilter count (the rest provably have alpha < alpha_min
 # and are skipped without evaluation), once in the front-to-back walk and once back to front:
@@ -47,10 +47,10 @@ FLOP_REMOVAL = 26        # T recovery, ratio, PD and dSE over 3 channels, suffix
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 PEAK_FP32_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 # DRAM bytes (read + written) of one removal-kernel launch per view of the scene workload: an
-# ncu capture of the 4-view case measured 440.1 MB (dram__bytes_read.sum 386.4 MB +
-# dram__bytes_write.sum 53.7 MB); the traffic grows with the views (records gathered per tile),
-# so a 16-view launch moves 16 x this.
-REMOVAL_DRAM_BYTES_PER_VIEW = 440.12e6 / 4
+# ncu capture of the 4-view case (128-splat batches) measured 467.5 MB (dram__bytes_read.sum
+# 406.3 MB + dram__bytes_write.sum 61.2 MB); the traffic grows with the views (records gathered
+# per tile), so a 16-view launch moves 16 x this.
+REMOVAL_DRAM_BYTES_PER_VIEW = 467.51e6 / 4
 
 
 def parse():

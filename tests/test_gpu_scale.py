@@ -1,5 +1,5 @@
 """Parity at full size: the 1M-splat, 16-view 1280x720 workload in the launch configuration
-the benchmark times (all 16 views in one frame, 16x16 tiles, 256-splat batches).
+the benchmark times (all 16 views in one frame, 16x16 tiles, 128-splat batches).
 
 The oracle cannot redo the whole frame in seconds, so it checks sampled outputs it can
 compute one by one: preprocess and the complete binning/sort of two views (bit-exact), and
@@ -16,7 +16,7 @@ from gpu_util import (assert_close_abs_rel, assert_close_rel, build_frame, frame
 
 pytestmark = pytest.mark.gpu
 
-CFG = dict(tile_w=16, tile_h=16, batch=256)
+CFG = dict(tile_w=16, tile_h=16, batch=128)
 VIEWS = (0, 11)
 
 
