@@ -371,13 +371,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "scene: 1M splats (70% unit ball, 30% shell 2-10), 16 views 1280x720 on a ring "
-                                   "of radius 4, targets = render with 5% of splats dropped + N(0, 0.01)",
-                       "n_splats": int(frame.n), "views_per_gpu": n_views, "resolution": "1280x720",
-                       "tile": f"{CFG['tile_w']}x{CFG['tile_h']}", "splat_batch": CFG["batch"],
-                       "form": "batched frame (all views in one launch per stage)", "instances": int(n_inst),
-                       "l2": "inputs larger than L2 (236 MB parameters, 0.77 GB raster records, 0.45 GB instances)",
-                       "parallelism": f"views replicated per GPU x{world}"},
+            "config": scene_config(int(frame.n), n_views, world),
+            "form": "batched frame (all views in one launch per stage)", "instances": int(n_inst),
             "stage_ms": {"preprocess": stage_ms[0], "bin_sort": stage_ms[1], "removal_effect": stage_ms[2]},
             "graph_views_per_s": graph_vps,
             "per_view_views_per_s": per_view_vps,
@@ -814,6 +809,16 @@ def multiview_config(args, dev, D, name: str, views_per_chunk: int, fwd_bwd: boo
     return out
 
 
+def scene_config(n_splats: int, n_views: int, world: int) -> dict:
+    """The timed workload, named the same way on both arms."""
+    return {"workload": "scene: 1M splats (70% unit ball, 30% shell 2-10), 16 views 1280x720 on a ring "
+                        "of radius 4, targets = render with 5% of splats dropped + N(0, 0.01)",
+            "n_splats": int(n_splats), "views_per_gpu": int(n_views), "resolution": "1280x720",
+            "tile": f"{CFG['tile_w']}x{CFG['tile_h']}", "splat_batch": CFG["batch"],
+            "l2": "inputs larger than L2 (236 MB parameters, 0.77 GB raster records, 0.45 GB instances)",
+            "parallelism": f"views replicated per GPU x{world}"}
+
+
 # ------------------------------------------------------------------------------------------
 # reference arm: the CPU oracle as it stands
 # ------------------------------------------------------------------------------------------
@@ -836,9 +841,9 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "scene: 1M splats, 16 views 1280x720 (one whole view per step)"},
+            "config": scene_config(w.scene.n, n_views, int(os.environ.get("WORLD_SIZE", "1"))),
             "cpu_baseline": {"value": value, "unit": "views/s", "cores": 1, "kind": "oracle",
-                             "sample": "one whole view per step, views 0.. in order"},
+                             "sample": "one whole view of the workload per step, views 0.. in order"},
             "e2e": {"value": value, "unit": "views/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
