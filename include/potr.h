@@ -425,6 +425,22 @@ POTR_API potr_status potr_adam_step(const potr_scene_grads* params, const potr_s
                                     const potr_scene_grads* m, const potr_scene_grads* v, int64_t n, int64_t step,
                                     const float* lr, float beta1, float beta2, float eps, potr_stream_t stream);
 
+/* The per-step factors potr_adam_step uses, for steps first_step .. first_step + count - 1 (host):
+ * out[i][0..5] = lr[g] / (1 - beta1^t) of the six groups, out[i][6] = 1 / sqrt(1 - beta2^t),
+ * t = first_step + i, computed in binary64 and rounded to float.  first_step >= 1. */
+POTR_API potr_status potr_adam_schedule(int64_t first_step, int64_t count, const float* lr, float beta1,
+                                        float beta2, float* out);
+
+/* potr_adam_step with t taken from the device: the update of step t = *d_step + 1 uses row
+ * *d_step of d_sched ([n_sched][7], device, from potr_adam_schedule with first_step 1), then
+ * *d_step is incremented on the device; a step past the table changes nothing but the counter.
+ * Gives the same bits as potr_adam_step(step = t) and needs no host argument that changes from
+ * step to step, so a fine-tuning iteration can be captured in a CUDA graph. */
+POTR_API potr_status potr_adam_step_scheduled(const potr_scene_grads* params, const potr_scene_grads* grads,
+                                              const potr_scene_grads* m, const potr_scene_grads* v, int64_t n,
+                                              const float* d_sched, int64_t n_sched, uint32_t* d_step, float beta1,
+                                              float beta2, float eps, potr_stream_t stream);
+
 /* Scale factors and precision parameters of the codec (Section IV-E, hyper-parameter table:
  * SF_scale = 1 + 4000q, SF_rotation = 1 + 400q, SF_opacity = 1 + 200q, SF_SH = 1 + 100q,
  * beta = 1.4e-4 q, gamma = 5 10^(-3-5q)). */

@@ -121,6 +121,10 @@ SIGNATURES = {
     "potr_adam_step": (_I32, [C.POINTER(SceneGrads), C.POINTER(SceneGrads), C.POINTER(SceneGrads),
                               C.POINTER(SceneGrads), _I64, _I64, C.POINTER(C.c_float), C.c_float, C.c_float, C.c_float,
                               _P]),
+    "potr_adam_schedule": (_I32, [_I64, _I64, C.POINTER(C.c_float), C.c_float, C.c_float, _P]),
+    "potr_adam_step_scheduled": (_I32, [C.POINTER(SceneGrads), C.POINTER(SceneGrads), C.POINTER(SceneGrads),
+                                        C.POINTER(SceneGrads), _I64, _P, _I64, _P, C.c_float, C.c_float, C.c_float,
+                                        _P]),
 }
 
 
@@ -313,6 +317,26 @@ def potr_adam_step(params: dict, grads: dict, m: dict, v: dict, n: int, step: in
     _check("potr_adam_step", lib().potr_adam_step(C.byref(grads_struct(params)), C.byref(grads_struct(grads)),
                                                   C.byref(grads_struct(m)), C.byref(grads_struct(v)), n, int(step),
                                                   lrs, float(beta1), float(beta2), float(eps), stream_handle(stream)))
+
+
+def potr_adam_schedule(first_step: int, count: int, lr, beta1=0.9, beta2=0.999):
+    """Host table [count][7] (float32) of the per-step factors."""
+    import numpy as np
+
+    out = np.zeros((int(count), 7), np.float32)
+    lrs = (C.c_float * 6)(*[float(x) for x in lr])
+    _check("potr_adam_schedule", lib().potr_adam_schedule(int(first_step), int(count), lrs, float(beta1),
+                                                          float(beta2), out.ctypes.data))
+    return out
+
+
+def potr_adam_step_scheduled(params: dict, grads: dict, m: dict, v: dict, n: int, sched, n_sched: int, step_counter,
+                             beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+    _check("potr_adam_step_scheduled",
+           lib().potr_adam_step_scheduled(C.byref(grads_struct(params)), C.byref(grads_struct(grads)),
+                                          C.byref(grads_struct(m)), C.byref(grads_struct(v)), n, ptr(sched),
+                                          int(n_sched), ptr(step_counter), float(beta1), float(beta2), float(eps),
+                                          stream_handle(stream)))
 
 
 def potr_codec_workspace_size(n: int) -> int:

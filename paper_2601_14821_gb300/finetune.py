@@ -20,10 +20,16 @@ LR_3DGS = (1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3, 2.5e-3 / 20.0)  # means, log_scales
 
 
 class FineTuner:
-    """Adam fine-tuning of a scene (dict of device tensors, updated in place) on its views."""
+    """Adam fine-tuning of a scene (dict of device tensors, updated in place) on its views.
+
+    Adam takes its step count from a device counter and its per-step factors from a table
+    (potr_adam_step_scheduled), so with ``graphs`` each view's whole iteration -- preprocess,
+    binning, render, loss gradient, backward, Adam -- is captured once in a CUDA graph (after one
+    eager iteration of that view) and replayed; re-planning a view's capacity drops its graph.
+    Both forms issue the same kernels and give the same bits."""
 
     def __init__(self, scene: dict, cams_rec: np.ndarray, targets: list, lam: float = 0.2, extent: float = 1.0,
-                 lr=None, device="cuda", check_every: int = 25, **cfg):
+                 lr=None, device="cuda", check_every: int = 25, graphs: bool = True, **cfg):
         self.scene = scene
         self.device = torch.device(device)
         cams_rec = np.ascontiguousarray(cams_rec, np.float32).reshape(-1, 18)
@@ -44,6 +50,11 @@ class FineTuner:
         self.t = 0
         self.check_every = int(check_every)
         self._bufs = {}
+        self.step_counter = torch.zeros(1, dtype=torch.int32, device=self.device)  # Adam steps done
+        self.sched, self.sched_rows = None, 0
+        self.use_graphs = bool(graphs)
+        self._graphs = [None] * len(self.frames)
+        self._warm = [False] * len(self.frames)
 
     def _buffers(self, fr):
         key = fr.total_pixels
@@ -51,27 +62,56 @@ class FineTuner:
             self._bufs[key] = (fr.image_buffer(), fr.pixel_buffer(), fr.pixel_buffer(torch.int32), fr.image_buffer())
         return self._bufs[key]
 
-    def step(self, view: int, stream=None):
-        """One iteration on one view: forward, loss gradient, backward, Adam."""
+    def _ensure_schedule(self, steps: int):
+        """A device table of Adam's per-step factors covering ``steps`` steps (regrowing it drops
+        the captured graphs, which hold its address)."""
+        if steps <= self.sched_rows:
+            return
+        rows = max(steps, 2 * self.sched_rows, 1024)
+        table = B.potr_adam_schedule(1, rows, self.lr)
+        self.sched = torch.from_numpy(table.reshape(-1)).to(self.device)
+        self.sched_rows = rows
+        self._graphs = [None] * len(self.frames)
+
+    def _iteration(self, view: int):
+        """The device work of one iteration on the current stream (no host synchronisation)."""
         fr = self.frames[view]
         img, tf, nl, dL = self._buffers(fr)
-        fr.preprocess(stream)
-        fr.bin_sort(stream)
+        fr.preprocess()
+        fr.bin_sort()
+        fr.render(img, tf, nl)
+        self.loss.zero_()
+        fr.loss_grad(img, self.targets[view], self.lam, dL, self.loss)
+        fr.render_backward(dL, self.grads, tf, nl)
+        B.potr_adam_step_scheduled(self.scene, self.grads, self.m, self.v, self.n, self.sched, self.sched_rows,
+                                   self.step_counter)
+
+    def step(self, view: int):
+        """One iteration on one view: forward, loss gradient, backward, Adam."""
         self.t += 1
+        self._ensure_schedule(self.t)
         if self.check_every and self.t % self.check_every == 0:
             self.ensure_capacity()
-        fr.render(img, tf, nl, stream)
-        self.loss.zero_()
-        fr.loss_grad(img, self.targets[view], self.lam, dL, self.loss, stream)
-        fr.render_backward(dL, self.grads, tf, nl, stream)
-        B.potr_adam_step(self.scene, self.grads, self.m, self.v, self.n, self.t, self.lr, stream=stream)
+        g = self._graphs[view]
+        if g is not None:
+            g.replay()
+            return
+        self._iteration(view)
+        if self.use_graphs and self._warm[view]:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):  # records only; the next iteration of this view replays it
+                self._iteration(view)
+            self._graphs[view] = g
+        self._warm[view] = True
 
     def ensure_capacity(self):
         """Re-plan every frame whose instances outgrew its capacity (the parameters move)."""
-        for f in self.frames:
+        for v, f in enumerate(self.frames):
             code, _ = f.status.tolist()
             if code == B.POTR_ERR_CAPACITY:
                 f.plan(1.2)
+                self._graphs[v] = None
+                self._warm[v] = False
 
     def run(self, iterations: int, order=None, seed: int = 0):
         """``iterations`` steps over the views (a seeded random view per step, as 3DGS draws
