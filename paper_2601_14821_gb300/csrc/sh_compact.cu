@@ -11,7 +11,9 @@
 // x = b_A per YCoCg channel (lambda_Co = lambda_Cg = 3 lambda, D = 1 except on the DC), pass 2
 // re-solves each channel without the AC coefficients that pass 1 leaves quantising to zero
 // (floor(1/2 + x SF) == 0).  The factorisations are Cholesky decompositions, one channel per
-// lane (lanes 0-2, in parallel); the cosine test is lane 0's.
+// group of 8 lanes (three groups in parallel; inside a group the rows below the diagonal are
+// dealt to the lanes, column by column); the cosine test compares a column with every kept
+// one at once, one kept column per lane.
 #include "potr_device.cuh"
 
 namespace potr {
@@ -30,7 +32,6 @@ struct ShWarpMem {
   double second[3][16];
   double Lc[3][16];  // the splat's current coefficients (RGB)
   int cols[16];
-  int m;
 };
 
 // Real SH basis of degree <= 3 (Condon-Shortley phase), index l(l+1)+m, unit direction, binary64.
@@ -55,36 +56,52 @@ __device__ __forceinline__ void sh_basis16_f64(double x, double y, double z, dou
 }
 
 // Ridge solve over the kept columns `cols` (m of them, cols[0] = 0 the DC) for channel ch:
-// (G_AA + lam D) x = b_A with Cholesky in L.  x is written for every column (0 outside).
-// Returns false if the matrix is not numerically positive definite.
-__device__ bool ridge_solve(const ShWarpMem& w, const int* cols, int m, int ch, double lam, double* x,
-                            double (*L)[16]) {
-  for (int i = 0; i < m; ++i)
+// (G_AA + lam D) x = b_A with Cholesky in L, by the 8 lanes of one group (sub-lane sl, group mask
+// gmask, first lane gbase); row i of L belongs to sub-lane i mod 8, and each entry is formed with
+// the same operations in the same order as a one-lane factorisation.  x is written for every
+// column (0 outside).  Returns false (on every lane of the group) if the matrix is not
+// numerically positive definite.
+__device__ bool ridge_solve_group(const ShWarpMem& w, const int* cols, int m, int ch, double lam, double* x,
+                                  double (*L)[16], int sl, int gbase, unsigned gmask) {
+  for (int i = sl; i < m; i += 8)
     for (int j = 0; j <= i; ++j) L[i][j] = w.G[cols[i]][cols[j]] + ((i == j && cols[i] != 0) ? lam : 0.0);
+  __syncwarp(gmask);
   for (int j = 0; j < m; ++j) {
-    double s = L[j][j];
-    for (int p = 0; p < j; ++p) s -= L[j][p] * L[j][p];
-    if (!(s > 0.0)) return false;
-    const double d = sqrt(s);
-    L[j][j] = d;
-    for (int i = j + 1; i < m; ++i) {
+    const int owner = j & 7;
+    int okj = 1;
+    if (sl == owner) {
+      double s = L[j][j];
+      for (int p = 0; p < j; ++p) s -= L[j][p] * L[j][p];
+      okj = s > 0.0;
+      if (okj) L[j][j] = sqrt(s);
+    }
+    okj = __shfl_sync(gmask, okj, gbase + owner);
+    if (!okj) return false;
+    __syncwarp(gmask);
+    const double d = L[j][j];
+    for (int i = sl; i < m; i += 8) {
+      if (i <= j) continue;
       double t = L[i][j];
       for (int p = 0; p < j; ++p) t -= L[i][p] * L[j][p];
       L[i][j] = t / d;
     }
+    __syncwarp(gmask);
   }
-  double y[16];
-  for (int i = 0; i < m; ++i) {
-    double t = w.b[cols[i]][ch];
-    for (int p = 0; p < i; ++p) t -= L[i][p] * y[p];
-    y[i] = t / L[i][i];
+  if (sl == 0) {
+    double y[16];
+    for (int i = 0; i < m; ++i) {
+      double t = w.b[cols[i]][ch];
+      for (int p = 0; p < i; ++p) t -= L[i][p] * y[p];
+      y[i] = t / L[i][i];
+    }
+    for (int i = 0; i < 16; ++i) x[i] = 0.0;
+    for (int i = m - 1; i >= 0; --i) {
+      double t = y[i];
+      for (int p = i + 1; p < m; ++p) t -= L[p][i] * x[cols[p]];
+      x[cols[i]] = t / L[i][i];
+    }
   }
-  for (int i = 0; i < 16; ++i) x[i] = 0.0;
-  for (int i = m - 1; i >= 0; --i) {
-    double t = y[i];
-    for (int p = i + 1; p < m; ++p) t -= L[p][i] * x[cols[p]];
-    x[cols[i]] = t / L[i][i];
-  }
+  __syncwarp(gmask);
   return true;
 }
 
@@ -112,12 +129,15 @@ __global__ void __launch_bounds__(32 * kShWarps) sh_compact_kernel(int64_t n, co
     }
     for (int o = 16; o >= 1; o >>= 1) wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
     __syncwarp();
-    for (int v0 = 0; v0 < n_views; v0 += 32) {
+    // an unseen splat (wmax 0) skips the Gram phase: G stays 0 and its coefficients are kept
+    for (int v0 = 0; wmax > 0.0 && v0 < n_views; v0 += 32) {
       const int v = v0 + lane;
       double wt = 0.0;
       if (v < n_views) wt = imp_view[(int64_t)v * n + k];
       wt = wt > 0.0 ? wt / wmax : 0.0;
-      double* row = w.rows[lane];
+      // the rows of the views with a weight, packed in view order (zero rows add nothing)
+      const uint32_t has = __ballot_sync(0xffffffffu, wt > 0.0);
+      double* row = w.rows[__popc(has & ((1u << lane) - 1u))];
       if (wt > 0.0) {
         const float* W = cams[v].w2c;
         double c[3];
@@ -141,12 +161,9 @@ __global__ void __launch_bounds__(32 * kShWarps) sh_compact_kernel(int64_t n, co
         row[16] = wt * (0.25 * rgb[0] + 0.5 * rgb[1] + 0.25 * rgb[2]);   // Y
         row[17] = wt * (0.5 * rgb[0] - 0.5 * rgb[2]);                    // Co
         row[18] = wt * (-0.25 * rgb[0] + 0.5 * rgb[1] - 0.25 * rgb[2]);  // Cg
-      } else {
-#pragma unroll
-        for (int i = 0; i < 19; ++i) row[i] = 0.0;
       }
       __syncwarp();
-      const int nr = min(32, n_views - v0);
+      const int nr = __popc(has);
       // G (upper triangle incl. diagonal, 136 entries) and b (48 entries), lanes over entries
       for (int e = lane; e < 136 + 48; e += 32) {
         int i, j;
@@ -169,44 +186,49 @@ __global__ void __launch_bounds__(32 * kShWarps) sh_compact_kernel(int64_t n, co
       }
       __syncwarp();
     }
-    if (lane == 0) {
-      for (int i = 0; i < 16; ++i)
-        for (int j = 0; j < i; ++j) w.G[i][j] = w.G[j][i];
-      int m = 1;
-      w.cols[0] = 0;
-      if (w.G[0][0] > 0.0) {  // some view sees the splat
-        for (int i = 1; i < 16; ++i) {
-          if (!(w.G[i][i] > 0.0)) continue;
-          bool par = false;
-          for (int q = 0; q < m && !par; ++q) {
-            const int j = w.cols[q];
-            par = fabs(w.G[i][j]) / sqrt(w.G[i][i] * w.G[j][j]) > alpha;
-          }
-          if (!par) w.cols[m++] = i;
+    for (int e = lane; e < 256; e += 32) {  // G's lower triangle from the upper one
+      const int i = e >> 4, j = e & 15;
+      if (j < i) w.G[i][j] = w.G[j][i];
+    }
+    if (lane == 0) w.cols[0] = 0;
+    __syncwarp();
+    const bool seen = w.G[0][0] > 0.0;  // some view sees the splat
+    int m = 1;
+    if (seen) {
+      for (int i = 1; i < 16; ++i) {  // column i against every kept column, one per lane
+        const double gii = w.G[i][i];
+        if (!(gii > 0.0)) continue;
+        bool par = false;
+        if (lane < m) {
+          const int j = w.cols[lane];
+          par = fabs(w.G[i][j]) / sqrt(gii * w.G[j][j]) > alpha;
+        }
+        if (!__any_sync(0xffffffffu, par)) {
+          if (lane == 0) w.cols[m] = i;
+          ++m;
+          __syncwarp();
         }
       }
-      w.m = m;
     }
-    __syncwarp();
-    // pass 1 then pass 2, channel `lane` on lanes 0-2
-    const bool seen = w.G[0][0] > 0.0;
-    const int m = w.m;
-    const double lam_c = lane == 0 ? lam : 3.0 * lam;
-    bool ok_lane = true;
+    // pass 1 then pass 2, channel `grp` on the 8 lanes of group grp (0-2)
+    const int grp = lane >> 3, sl = lane & 7, gbase = grp * 8;
+    const unsigned gmask = 0xffu << gbase;
+    const double lam_c = grp == 0 ? lam : 3.0 * lam;
+    bool ok_g = true;
     uint32_t kbits = 0;
-    if (seen && lane < 3) ok_lane = ridge_solve(w, w.cols, m, lane, lam_c, w.first[lane], w.M[lane]);
-    bool ok = seen && __all_sync(0xffffffffu, ok_lane);
-    if (ok && lane < 3) {
+    if (seen && grp < 3) ok_g = ridge_solve_group(w, w.cols, m, grp, lam_c, w.first[grp], w.M[grp], sl, gbase, gmask);
+    bool ok = seen && __all_sync(0xffffffffu, ok_g);
+    if (ok && grp < 3) {
       int c2[16], m2 = 1;
       c2[0] = 0;
       for (int q = 1; q < m; ++q)
-        if (floor(__dadd_rn(0.5, __dmul_rn(w.first[lane][w.cols[q]], sf))) != 0.0) c2[m2++] = w.cols[q];
+        if (floor(__dadd_rn(0.5, __dmul_rn(w.first[grp][w.cols[q]], sf))) != 0.0) c2[m2++] = w.cols[q];
       for (int q = 0; q < m2; ++q) kbits |= 1u << c2[q];
-      ok_lane = ridge_solve(w, c2, m2, lane, lam_c, w.second[lane], w.M[lane]);
+      ok_g = ridge_solve_group(w, c2, m2, grp, lam_c, w.second[grp], w.M[grp], sl, gbase, gmask);
     }
-    ok = ok && __all_sync(0xffffffffu, ok_lane);
-    const uint32_t k1 = __shfl_sync(0xffffffffu, kbits, 0), k2 = __shfl_sync(0xffffffffu, kbits, 1),
-                   k3 = __shfl_sync(0xffffffffu, kbits, 2);
+    ok = ok && __all_sync(0xffffffffu, ok_g);
+    const uint32_t k1 = __shfl_sync(0xffffffffu, kbits, 0), k2 = __shfl_sync(0xffffffffu, kbits, 8),
+                   k3 = __shfl_sync(0xffffffffu, kbits, 16);
     if (lane == 0) {
       uint32_t keep = 0;
       for (int q = 0; q < m; ++q) keep |= 1u << w.cols[q];
