@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(128, 8) vk_grad_sum_kernel(const uint32_t* __r
   }
 }
 
-__global__ void __launch_bounds__(128) preprocess_bwd_kernel(
+__global__ void __launch_bounds__(128, 3) preprocess_bwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ sh, const float* __restrict__ cov3d, const float* __restrict__ opacity, int64_t n,
     const potr_camera* __restrict__ cams, int n_views, potr_raster_config cfg, const uint32_t* __restrict__ touched,
