@@ -11,9 +11,10 @@
 //                         per-pair gradients are summed per (tile, splat) without atomics (warp
 //                         transpose-sums in a fixed order, then warps in order) into per-instance
 //                         slots.  T_i comes either from the stored final transmittance of the
-//                         forward render or, with none stored, from re-running the forward walk.
-//   preprocess_bwd_kernel per splat: the instance slots summed in emission order per view, then
-//                         the adjoint of the projection (conic inverse, Sigma2D = T Sigma T^T,
+//                         forward render (whose per-entry warp masks are then read, not
+//                         recomputed) or, with none stored, from re-running the forward walk.
+//   vk_grad_sum_kernel    per (view, splat): its instance slots summed in emission order.
+//   preprocess_bwd_kernel per splat: the adjoint of the projection (conic inverse, Sigma2D = T Sigma T^T,
 //                         clamped Jacobian, pinhole centre, SH colour and its direction) and of
 //                         the activation (Sigma = M M^T, M = R diag(exp(log_scale)), quaternion
 //                         normalisation, sigmoid), accumulated over views in view order.

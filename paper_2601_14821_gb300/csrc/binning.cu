@@ -5,22 +5,14 @@
 // the instances by tile, and per-tile [start, end) ranges.
 //
 // Everything is integer work and bit-exact: the scan is a two-level reduce-then-scan (no
-// inter-block waiting), the sort ranks items stably inside a block with warp match masks, so
-// its result equals std::stable_sort of the keys.  All kernels are HBM-bound; they read the
-// instance count from device memory so that a whole frame can be captured in a CUDA graph.
+// inter-block waiting), the sort ranks items stably inside a block with per-warp equal-digit
+// masks, so its result equals std::stable_sort of the keys.  The kernels read the instance
+// count from device memory so that a whole frame can be captured in a CUDA graph.
 #include "radix.cuh"
 #include "scan.cuh"
 
 namespace potr {
 namespace {
-
-
-
-
-
-
-
-
 
 // -----------------------------------------------------------------------------------------
 // Instance count check, depth keys and emission.
