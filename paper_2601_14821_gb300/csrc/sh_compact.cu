@@ -57,10 +57,11 @@ __device__ __forceinline__ void sh_basis16_f64(double x, double y, double z, dou
 
 // Ridge solve over the kept columns `cols` (m of them, cols[0] = 0 the DC) for channel ch:
 // (G_AA + lam D) x = b_A with Cholesky in L, by the 8 lanes of one group (sub-lane sl, group mask
-// gmask, first lane gbase); row i of L belongs to sub-lane i mod 8, and each entry is formed with
-// the same operations in the same order as a one-lane factorisation.  x is written for every
-// column (0 outside).  Returns false (on every lane of the group) if the matrix is not
-// numerically positive definite.
+// gmask, first lane gbase); row i of L belongs to sub-lane i mod 8.  Binary64 divisions are long
+// sequences on this part, so each diagonal entry's reciprocal is formed once (kept in the
+// upper triangle, L[i][i+..] is unused) and the off-diagonal entries and the substitutions
+// multiply by it.  x is written for every column (0 outside).  Returns false (on every lane of
+// the group) if the matrix is not numerically positive definite.
 __device__ bool ridge_solve_group(const ShWarpMem& w, const int* cols, int m, int ch, double lam, double* x,
                                   double (*L)[16], int sl, int gbase, unsigned gmask) {
   for (int i = sl; i < m; i += 8)
@@ -77,28 +78,31 @@ __device__ bool ridge_solve_group(const ShWarpMem& w, const int* cols, int m, in
     }
     okj = __shfl_sync(gmask, okj, gbase + owner);
     if (!okj) return false;
+    if (sl == owner && j + 1 < 16) L[j][j + 1] = 1.0 / L[j][j];  // the reciprocal, once
     __syncwarp(gmask);
-    const double d = L[j][j];
+    const double inv_d = j + 1 < 16 ? L[j][j + 1] : 1.0 / L[j][j];
     for (int i = sl; i < m; i += 8) {
       if (i <= j) continue;
       double t = L[i][j];
       for (int p = 0; p < j; ++p) t -= L[i][p] * L[j][p];
-      L[i][j] = t / d;
+      L[i][j] = t * inv_d;
     }
     __syncwarp(gmask);
   }
   if (sl == 0) {
     double y[16];
     for (int i = 0; i < m; ++i) {
+      const double inv = i + 1 < 16 ? L[i][i + 1] : 1.0 / L[i][i];
       double t = w.b[cols[i]][ch];
       for (int p = 0; p < i; ++p) t -= L[i][p] * y[p];
-      y[i] = t / L[i][i];
+      y[i] = t * inv;
     }
     for (int i = 0; i < 16; ++i) x[i] = 0.0;
     for (int i = m - 1; i >= 0; --i) {
+      const double inv = i + 1 < 16 ? L[i][i + 1] : 1.0 / L[i][i];
       double t = y[i];
       for (int p = i + 1; p < m; ++p) t -= L[p][i] * x[cols[p]];
-      x[cols[i]] = t / L[i][i];
+      x[cols[i]] = t * inv;
     }
   }
   __syncwarp(gmask);
