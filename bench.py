@@ -555,14 +555,14 @@ def codec_run(args, dev, D, scene_d, alive, sh_rgb, cams, q: float) -> dict:
 
     import torch
 
-    from oracle import codec as ocodec
-    from oracle.sh_compact import camera_centre
+    import synth
     from paper_2601_14821_gb300.codec import Decoder, Encoder, params
+    from paper_2601_14821_gb300.compress import camera_centres
 
     keep = torch.nonzero(alive, as_tuple=False).flatten()
     sub = {k: t[..., keep].contiguous() for k, t in scene_d.items() if k != "sh"}
     sub["sh"] = sh_rgb[..., keep].contiguous()
-    eyes = np.array([camera_centre(c) for c in cams])
+    eyes = camera_centres(synth.cameras_to_array(cams))
     p = params(q)
     enc = Encoder(int(keep.numel()), dev)
     enc.run(sub, eyes, p)  # first launches outside the timed region
@@ -603,7 +603,7 @@ def codec_run(args, dev, D, scene_d, alive, sh_rgb, cams, q: float) -> dict:
            "raw_bytes": len(raw), "compressed_bytes": len(packed), "bytes_per_splat": len(packed) / n,
            "node_bytes": m, "shared_leaves": n_dups, "q": q}
     if D.env_ranks()[0] == 0 and not args.no_cpu_baseline:
-        import synth
+        from oracle import codec as ocodec
 
         w = synth.workload("scene")
         k = keep.cpu().numpy()[:20000]
@@ -626,13 +626,13 @@ def potr_ft_run(args, dev, D, scene, cams, targets, q: float, cycles: int = 2, i
     import torch
 
     import synth
-    from oracle.sh_compact import camera_centre
     from paper_2601_14821_gb300.batched import BatchedRemovalEffect
     from paper_2601_14821_gb300.codec import decode, roundtrip
+    from paper_2601_14821_gb300.compress import camera_centres
     from paper_2601_14821_gb300.finetune import potr_ft
 
     rec = synth.cameras_to_array(cams)
-    eyes = np.array([camera_centre(c) for c in cams])
+    eyes = camera_centres(rec)
     P = cams[0].pixels
     per_view = [targets[3 * v * P: 3 * (v + 1) * P] for v in range(len(cams))]
 
@@ -673,7 +673,6 @@ def sh_compaction_run(args, dev, D, frame, targets, q: float) -> dict:
     import torch
 
     import synth
-    from oracle import sh_compact as oshc
     from paper_2601_14821_gb300.sh_compact import compact, params
 
     n, V = frame.n, frame.n_views
@@ -698,6 +697,8 @@ def sh_compaction_run(args, dev, D, frame, targets, q: float) -> dict:
            "alpha": p["alpha"], "sf": p["sf"], "splats_seen": int(seen.sum()),
            "mean_ac_kept_per_channel": [float(x.mean()) if x.size else 0.0 for x in ac_kept]}
     if D.env_ranks()[0] == 0 and not args.no_cpu_baseline:
+        from oracle import sh_compact as oshc
+
         w = synth.workload("scene")
         iv = imp_view.cpu().numpy().reshape(V, n)
         centres = np.array([oshc.camera_centre(c) for c in w.cameras])

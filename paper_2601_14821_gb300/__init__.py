@@ -12,6 +12,7 @@ that own the torch device buffers:
 * ``sh_compact``-- SH energy compaction (Section IV-D);
 * ``codec``     -- encoder and decoder of the bitstream (Section IV-E);
 * ``finetune``  -- the fine-tuning loop and the POTR-FT cycle (Section IV-F);
+* ``compress``  -- the four chained: pruning, SH compaction, encoding (or POTR-FT) in one call;
 * ``dist``      -- one process per GPU, ordered cross-rank sums.
 
 Build with ``build.build()``; there is no CPU fallback.

@@ -1,4 +1,5 @@
-"""Host-side logic that needs no GPU: the library's Adam factor table and the bitstream parser."""
+"""Host-side logic that needs no GPU: the library's Adam factor table, the bitstream parser and
+the camera and image-layout helpers of the compression driver."""
 import struct
 import zlib
 
@@ -65,3 +66,34 @@ def test_stream_parser_rejects_damaged_streams():
         parse(raw[:-4])
     assert zlib.decompress(zlib.compress(raw)) == raw
     assert struct.unpack_from("<I", raw, 4)[0] == ocodec.VERSION
+
+
+def test_camera_centres_recover_the_look_at_positions():
+    """The eye of a look-at camera is the position it was built at (the world point the
+    world-to-camera map sends to the origin)."""
+    import synth
+    from paper_2601_14821_gb300.compress import camera_centres
+
+    rng = np.random.default_rng(5)
+    pos = rng.normal(0, 3, (7, 3))
+    pos[0] = (0.0, 0.0, 4.0)
+    cams = [synth.look_at_camera(p, 64 + 8 * i, 48) for i, p in enumerate(pos)]
+    got = camera_centres(synth.cameras_to_array(cams))
+    assert got.shape == (7, 3) and got.dtype == np.float64
+    assert np.allclose(got, pos, rtol=0, atol=1e-5 * (1 + np.abs(pos)))
+
+
+def test_view_images_follow_the_packed_layout():
+    """View v's block starts at 3 * (pixels of views 0..v-1) and holds 3 * width * height floats."""
+    import torch
+
+    import synth
+    from paper_2601_14821_gb300.compress import view_images
+
+    sizes = [(16, 8), (5, 3), (32, 32)]
+    cams = [synth.look_at_camera((0.0, 0.0, 3.0), w, h) for w, h in sizes]
+    total = sum(3 * w * h for w, h in sizes)
+    buf = torch.arange(total, dtype=torch.float32)
+    parts = view_images(synth.cameras_to_array(cams), buf)
+    assert [p.numel() for p in parts] == [3 * w * h for w, h in sizes]
+    assert torch.equal(torch.cat(parts), buf) and parts[1][0].item() == 3 * 16 * 8
