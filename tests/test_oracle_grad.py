@@ -36,7 +36,10 @@ def _same_order(a, b):
     return np.array_equal(a[1], b[1]) and np.array_equal(a[0] >> np.uint64(32), b[0] >> np.uint64(32))
 
 
-def test_autograd_gradient_equals_finite_differences():
+def _smooth_setup(offset=None):
+    """200 splats seen by a 64x64 and a 48x64 view, with no threshold, stop or clamp that a small
+    perturbation can switch; targets are the render plus noise, or minus ``offset`` (a residual
+    of one sign everywhere)."""
     cfg = oracle.make_config(alpha_min=0.0, t_min=0.0, alpha_max=1.0 - 1e-6)
     sc = synth.uniform_cube_scene(200, 31)
     cams = [synth.look_at_camera((0, 0, -3), 64, 64), synth.look_at_camera((2.0, 0.5, -2.2), 48, 64)]
@@ -44,29 +47,64 @@ def test_autograd_gradient_equals_finite_differences():
     for v, c in enumerate(cams):
         pv = oracle.prepare_view(sc, c, cfg)
         im, *_ = oracle.render(pv, pv["vals"], pv["ranges"], c, cfg)
-        tg.append((im + synth.target_noise(im.shape, 0.05, 5, v)).astype(np.float32))
-    _, grad, _ = G.loss_and_grad(sc, cams, cfg, tg, lam=1.0)
-    _, keys0 = G.oracle_loss(sc, cams, cfg, tg, lam=1.0)
-    rng = np.random.default_rng(0)
+        if offset is None:
+            tg.append((im + synth.target_noise(im.shape, 0.05, 5, v)).astype(np.float32))
+        else:
+            tg.append(im - offset)
+    return cfg, sc, cams, tg
+
+
+def _finite_difference_check(cfg, sc, cams, tg, lam, samples, need, seed=0, noise_scale=1.0):
+    # The C oracle's binary32 alphas put a noise floor on the difference quotient proportional to
+    # |dL/dc|: about 2 |r| ~ 0.1 for squared error on 0.05 noise, the unit of noise_scale.
+    _, grad, _ = G.loss_and_grad(sc, cams, cfg, tg, lam=lam)
+    _, keys0 = G.oracle_loss(sc, cams, cfg, tg, lam=lam)
+    rng = np.random.default_rng(seed)
     checked = {}
     for key in G.PARAM_KEYS:
         arr = getattr(sc, key)
         step = 2e-4 if key == "means" else 1e-3
-        for _ in range(25):
+        for _ in range(samples):
             idx = tuple(int(rng.integers(0, s)) for s in arr.shape)
             x0 = arr[idx]
             h = np.float32(step * max(1.0, abs(float(x0))))
             xp, xm = np.float32(x0 + h), np.float32(x0 - h)
             arr[idx] = xp
-            lp, kp = G.oracle_loss(sc, cams, cfg, tg, lam=1.0)
+            lp, kp = G.oracle_loss(sc, cams, cfg, tg, lam=lam)
             arr[idx] = xm
-            lm, km = G.oracle_loss(sc, cams, cfg, tg, lam=1.0)
+            lm, km = G.oracle_loss(sc, cams, cfg, tg, lam=lam)
             arr[idx] = x0
             if not all(_same_order(a, c) and _same_order(b, c) for a, b, c in zip(kp, km, keys0)):
                 continue
             fd = (lp - lm) / (float(xp) - float(xm))
             an = grad[key][idx]
-            noise = 5e-9 * (1e-3 / step)
+            noise = 5e-9 * (1e-3 / step) * noise_scale
             assert abs(fd - an) <= 2e-3 * abs(an) + noise, (key, idx, fd, an)
             checked[key] = checked.get(key, 0) + 1
-    assert all(checked.get(k, 0) >= 15 for k in G.PARAM_KEYS), checked
+    assert all(checked.get(k, 0) >= need for k in G.PARAM_KEYS), checked
+
+
+def test_autograd_gradient_equals_finite_differences():
+    _finite_difference_check(*_smooth_setup(), lam=1.0, samples=25, need=15)
+
+
+def test_mixed_loss_gradient_equals_finite_differences():
+    """lambda = 0.2 (both terms): targets 0.5 below the render keep every residual positive, so
+    the L1 term is smooth under the perturbations and its weight 1 - lambda is exercised.
+    |dL/dc| = (1 - lambda) + 2 lambda r = 1.0, ten times the squared-error setup's, and so is the
+    finite-difference noise floor."""
+    _finite_difference_check(*_smooth_setup(offset=0.5), lam=0.2, samples=10, need=6, seed=1, noise_scale=10.0)
+
+
+@pytest.mark.parametrize("delta", [0.25, -0.125])
+def test_loss_closed_form_for_a_constant_residual(delta):
+    """With every target delta below the render, each of the 3 x (64 x 64 + 48 x 64) residuals is
+    delta and the loss is (1 - lambda) |delta| + lambda delta^2 for any lambda: pins the weights
+    of the two terms and the mean over channels, pixels and views of unequal sizes."""
+    cfg, sc, cams, tg = _smooth_setup(offset=delta)
+    for lam in (0.0, 0.2, 1.0):
+        want = (1.0 - lam) * abs(delta) + lam * delta * delta
+        L, _ = G.oracle_loss(sc, cams, cfg, tg, lam=lam)
+        assert L == pytest.approx(want, abs=1e-12)
+        Lg, _, _ = G.loss_and_grad(sc, cams, cfg, tg, lam=lam)
+        assert Lg == pytest.approx(want, abs=2e-5)  # binary64 alphas against the C oracle's binary32
