@@ -21,8 +21,8 @@ __device__ __forceinline__ void cp_async_commit_wait() {
   asm volatile("cp.async.wait_group 0;\n" ::);
 }
 
-// Gather the first three float4 of the raster records of list entries [first, first + cnt)
-// into smem (record stride kSRec); the fourth (the tile mask) is read from global memory only
+// Gather the raster records (three float4 each) of list entries [first, first + cnt) into smem
+// (record stride kSRec) and wait for them; the culling words are read from global memory only
 // where an emission slot is needed.
 template <int BATCH>
 __device__ __forceinline__ void stage_batch(float4* smem, const float4* __restrict__ raster,
