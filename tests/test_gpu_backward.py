@@ -93,6 +93,25 @@ def test_loss_grad_kernel_against_plain_formula(tiny):
         assert torch.allclose(dL.double(), want, rtol=1e-6, atol=1e-12)
 
 
+def test_zero_residual_gives_zero_gradients(tiny):
+    """Targets equal to the device's own render: every residual is 0, where the L1 term's
+    subgradient is taken as 0, so the loss, dL/dc and every parameter gradient are exactly 0 (in
+    both the stored-transmittance and the recompute form)."""
+    import torch
+
+    cfg = dict(tile_w=16, tile_h=16, batch=256)
+    fr = build_frame(tiny.scene, tiny.cameras, **cfg)
+    img = fr.image_buffer()
+    fr.render(img)
+    torch.cuda.synchronize()
+    for store in (True, False):
+        loss, grads, dL, again = _gpu_grads(fr, img.clone(), 0.2, store=store)
+        assert torch.equal(again, img)  # the render is reproducible, so the residual is exactly 0
+        assert loss == 0.0 and int(torch.count_nonzero(dL)) == 0
+        for k in KEYS:
+            assert np.count_nonzero(grads[k]) == 0, (store, k)
+
+
 def test_recompute_equals_store_and_is_deterministic(tiny):
     sc = synth.uniform_cube_scene(3000, 88)
     cams = [synth.look_at_camera((0.0, 0.3, -3.0), 120, 90), synth.look_at_camera((2.5, -0.2, -1.5), 72, 100)]

@@ -8,7 +8,10 @@
   (lambda = 1: the L1 term has a kink at c = c_t that finite differences cross), and only
   perturbations that leave every tile list and depth order unchanged.  Step h = 1e-3
   (2e-4 for means, whose truncation error is larger for sub-pixel splats); tolerance
-  2e-3 relative plus the finite-difference noise floor of the binary32 decisions.
+  2e-3 relative plus the finite-difference noise floor of the binary32 decisions.  Again at
+  lambda = 0.2 with every residual kept positive, so that the L1 term's weight enters.
+* The loss in closed form when every residual is delta: (1 - lambda) |delta| + lambda delta^2.
+* A zero residual (targets equal to the render) gives a loss and gradients of exactly 0.
 """
 import numpy as np
 import pytest
@@ -108,3 +111,20 @@ def test_loss_closed_form_for_a_constant_residual(delta):
         assert L == pytest.approx(want, abs=1e-12)
         Lg, _, _ = G.loss_and_grad(sc, cams, cfg, tg, lam=lam)
         assert Lg == pytest.approx(want, abs=2e-5)  # binary64 alphas against the C oracle's binary32
+
+
+def test_zero_residual_gives_zero_gradient(tiny):
+    """Targets equal to the oracle's own binary64 render: every residual is exactly 0, where the
+    L1 term's subgradient is 0 (sign 0 = 0), so the loss and every gradient are exactly 0."""
+    cfg = oracle.make_config()
+    first = []
+    for cam in tiny.cameras:
+        v = oracle.prepare_view(tiny.scene, cam, cfg)
+        img, *_ = oracle.render(v, v["vals"], v["ranges"], cam, cfg)
+        first.append(np.zeros_like(img))
+    _, _, imgs = G.loss_and_grad(tiny.scene, tiny.cameras, cfg, first)
+    for lam in (0.0, 0.2):
+        L, g, _ = G.loss_and_grad(tiny.scene, tiny.cameras, cfg, [np.asarray(i, np.float64) for i in imgs], lam=lam)
+        assert L == 0.0
+        for k in G.PARAM_KEYS:
+            assert np.count_nonzero(g[k]) == 0, (lam, k)
