@@ -218,6 +218,26 @@ def test_mixed_views_every_tile_shape(tile):
     _check_removal(fr, sc, cams, cfg, ovs, res, tg)
 
 
+def test_coincident_splats_keep_emission_order():
+    """Splat 2j + 1 at splat 2j's position (equal depths, so equal (tile, depth) keys wherever
+    both touch a tile): the device sort must keep such ties in emission order, as the oracle's
+    stable sort does; binning bit-exact, render and removal effect within tolerance."""
+    sc0, cams = mixed_workload()
+    means = sc0.means.copy()
+    means[:, 1::2] = means[:, 0:means.shape[1] - 1:2]
+    sc = synth.Scene(means, sc0.log_scales, sc0.quats, sc0.opacity_logits, sc0.sh)
+    cfg = dict(tile_w=16, tile_h=16, batch=128)
+    fr = build_frame(sc, cams, **cfg)
+    tg = _tiny_targets(sc, cams, cfg, 4243)
+    res = frame_outputs(fr, pack_targets(fr, tg))
+    act, ovs = _oracle_views(sc, cams, cfg)
+    keys = np.concatenate([pv["keys"] for pv in ovs])
+    assert np.count_nonzero(np.diff(keys.astype(np.int64)) == 0) > 1000
+    _check_binning(fr, ovs)
+    _check_render(fr, sc, cams, cfg, ovs, res)
+    _check_removal(fr, sc, cams, cfg, ovs, res, tg)
+
+
 def test_frame_over_65536_tiles_takes_three_tile_passes():
     """Nine 1920x1080 views (73,440 global tiles: 17 tile bits, three partition passes, the odd
     count that lands the result through the alternate buffer); binning, render and removal

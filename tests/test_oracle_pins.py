@@ -201,7 +201,26 @@ def test_cull_behind_and_near():
 # ------------------------------------------------------------------------------------------
 
 def test_bin_sort_against_numpy_stable_sort(tiny):
-    sc, cam = tiny.scene, tiny.cameras[0]
+    _check_bin_sort(tiny.scene, tiny.cameras[0])
+
+
+def test_bin_sort_keeps_emission_order_for_equal_keys(tiny):
+    """Splat 2j + 1 a copy of splat 2j's position (its own shape and opacity): the pair has the
+    same depth, so wherever both touch a tile their keys are equal and a stable sort keeps them in
+    emission order (k ascending)."""
+    sc = tiny.scene
+    means = sc.means.copy()
+    means[:, 1::2] = means[:, 0:means.shape[1] - 1:2]
+    dup = synth.Scene(means, sc.log_scales, sc.quats, sc.opacity_logits, sc.sh)
+    ties = _check_bin_sort(dup, tiny.cameras[0])
+    assert ties > 100
+
+
+def _check_bin_sort(sc, cam):
+    """The oracle's keys, values, emission indices and tile ranges against numpy's stable argsort
+    of keys emitted by enumeration, for the three tile shapes; returns the number of equal
+    adjacent keys seen."""
+    ties = 0
     for tw, th in [(16, 16), (8, 32), (32, 8)]:
         cfg = oracle.make_config(tile_w=tw, tile_h=th)
         v = oracle.prepare_view(sc, cam, cfg)
@@ -218,6 +237,7 @@ def test_bin_sort_against_numpy_stable_sort(tiny):
                         vals.append(k)
         keys = np.array(keys, np.uint64)
         order = np.argsort(keys, kind="stable")
+        ties += int(np.count_nonzero(np.diff(keys[order].astype(np.int64)) == 0))
         assert np.array_equal(v["keys"], keys[order])
         assert np.array_equal(v["vals"], np.array(vals, np.uint32)[order])
         assert np.array_equal(v["emit"], order.astype(np.uint32))
@@ -228,6 +248,7 @@ def test_bin_sort_against_numpy_stable_sort(tiny):
                 assert tuple(v["ranges"][t]) == (idx[0], idx[-1] + 1)
             else:
                 assert v["ranges"][t][0] == v["ranges"][t][1]
+    return ties
 
 
 def _random_splats(rng, m, tile):
@@ -375,6 +396,29 @@ def test_depth_bits_order_matches_numeric_order():
 # compositing and removal effect on hand-built splats (closed forms)
 # ------------------------------------------------------------------------------------------
 
+def test_jacobian_clamp_freezes_the_footprint_beyond_the_limit():
+    """The Jacobian is taken at the camera-space point with x / z clamped to 1.3 times the half
+    field of view: an isotropic splat at a fixed depth has one 2D covariance for every position
+    beyond that limit, and a smaller one inside it (the footprint of the plain linearisation grows
+    with (x / z)^2)."""
+    cam = synth.look_at_camera((0.0, 0.0, -3.0), 128, 96)
+    W = cam.w2c.reshape(3, 4).astype(np.float64)
+    lim = 1.3 * 0.5 * cam.width / cam.fx
+    z = 3.0
+    ratios = [0.5 * lim, 1.5 * lim, 2.0 * lim, 3.0 * lim]
+    cam_pts = np.array([[r * z, 0.0, z] for r in ratios])
+    world = (W[:, :3].T @ (cam_pts.T - W[:, 3:4]))  # x_c = R x + t  ->  x = R^T (x_c - t)
+    n = len(ratios)
+    sc = _scene(world, np.full((3, n), math.log(3.0)), np.tile([[1.0], [0], [0], [0]], n), np.full(n, 4.0))
+    cov, op = oracle.activate(sc)
+    pr = oracle.project(sc, cov, cam, CFG, op)
+    assert np.all(pr["touched"] > 0)
+    c2 = pr["cov2d"].astype(np.float64)
+    for j in (2, 3):
+        np.testing.assert_allclose(c2[:, j], c2[:, 1], rtol=1e-5, atol=1e-3)
+    assert c2[0, 0] < 0.9 * c2[0, 1]
+
+
 def _flat_view(opac, rgb, depth, w=16, h=16):
     """Splats whose exponent is 0 everywhere (alpha = opacity exactly), all in one tile."""
     n = len(opac)
@@ -437,6 +481,21 @@ def test_alpha_clamp_and_threshold_and_termination():
     cfg2 = oracle.make_config(t_min=0.006)
     img2, t32b, _, nl2 = oracle.render(v, vals, ranges, cam, cfg2)
     assert nl2[0, 0] == 1 and t32b[0, 0] == np.float32(1.0) - np.float32(0.99)  # stops before the last splat
+
+
+def test_termination_ends_the_pixel():
+    """T_min ends the walk at the first splat that would take T below it: 0.99 then 0.98 leave
+    T = 2e-4; 0.9 would leave 2e-5 < 1e-4, so the pixel stops there, and a fainter splat after it
+    (0.1, which would leave 1.8e-4) is not composited either."""
+    v, vals, ranges, cam = _flat_view([0.99, 0.98, 0.9, 0.1], [[1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1]],
+                                      [1.0, 2.0, 3.0, 4.0])
+    img, t32, t64, nl = oracle.render(v, vals, ranges, cam, oracle.make_config(t_min=1e-4))
+    a0, a1 = float(np.float32(0.99)), float(np.float32(0.98))
+    np.testing.assert_allclose(img[:, 0, 0], [a0, (1 - a0) * a1, 0.0], rtol=1e-14, atol=0)
+    assert nl[0, 0] == 2 and t32[0, 0] >= np.float32(1e-4)
+    tgt = np.zeros(img.shape, np.float32)
+    d, imp = oracle.removal_effect(v, vals, ranges, cam, oracle.make_config(t_min=1e-4), tgt)
+    assert d[2] == 0.0 and d[3] == 0.0 and imp[2] == 0.0 and imp[3] == 0.0
 
 
 # ------------------------------------------------------------------------------------------
