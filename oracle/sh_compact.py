@@ -70,6 +70,20 @@ def _ridge(G, b, active, lam):
     return x
 
 
+def cosine_kept(G, alpha):
+    """The sparsity step of Section IV-D on the weighted Gram matrix G: columns in index order,
+    the DC column always kept, a column with zero norm dropped, and any other dropped when its
+    |cosine| with a column already kept exceeds alpha."""
+    kept = [0]
+    for i in range(1, G.shape[0]):
+        if G[i, i] <= 0.0:
+            continue
+        if any(abs(G[i, j]) / math.sqrt(G[i, i] * G[j, j]) > alpha for j in kept):
+            continue
+        kept.append(i)
+    return kept
+
+
 def compact_splat(L_rgb, mean, centres, weights, lam, alpha, sf):
     """One splat.  L_rgb [16][3], mean [3], centres [N][3], weights [N] (I_k(s)).
     Returns (L' in YCoCg [16][3], kept columns after the cosine test, per-channel columns of
@@ -91,13 +105,7 @@ def compact_splat(L_rgb, mean, centres, weights, lam, alpha, sf):
     Cw = np.array(cols) @ RGB_TO_YCOCG.T  # weighted YCoCg colours
     G = Yw.T @ Yw
     b = Yw.T @ Cw
-    kept = [0]
-    for i in range(1, 16):
-        if G[i, i] <= 0.0:
-            continue
-        if any(abs(G[i, j]) / math.sqrt(G[i, i] * G[j, j]) > alpha for j in kept):
-            continue
-        kept.append(i)
+    kept = cosine_kept(G, alpha)
     lams = (lam, 3.0 * lam, 3.0 * lam)
     first = np.stack([_ridge(G, b[:, ch], kept, lams[ch]) for ch in range(3)], axis=1)
     second = np.zeros((16, 3))

@@ -82,7 +82,30 @@ def test_round_trip_honours_the_precision_criterion_and_the_quantisers():
     q = q / np.linalg.norm(q, axis=0)
     q = np.where(q[0] < 0, -q, q)
     assert np.max(np.abs(d["quats"][1:] - q[1:])) <= 0.5 / p["sf_rotation"] + 1e-12
+    # the real part is rebuilt so that the quaternion has unit norm (where |xyz~| <= 1), and it
+    # is within sqrt(|w~^2 - w^2|) <= sqrt(2 delta + 3 delta^2) of the original, delta = the
+    # norm of the xyz rounding error
+    xyz = d["quats"][1:]
+    inside = (xyz ** 2).sum(axis=0) <= 1.0
+    assert inside.mean() > 0.9 and np.all(d["quats"][0, ~inside] == 0.0)  # rounding past 1: w = 0
+    assert np.max(np.abs(np.linalg.norm(d["quats"][:, inside], axis=0) - 1.0)) < 1e-12
+    delta = math.sqrt(3.0) * 0.5 / p["sf_rotation"]
+    assert np.max(np.abs(d["quats"][0] - q[0])) <= math.sqrt(2.0 * delta + 3.0 * delta * delta)
     assert len(e["compressed"]) < len(e["raw"])
+
+
+def test_nearest_eye_sets_the_tolerance():
+    """The precision criterion takes the distance to the nearest eye: an eye farther from every
+    splat than the others changes no byte of the stream, and an eye among the splats refines the
+    octree."""
+    sc = synth.uniform_cube_scene(2000, 12)
+    eyes = [np.array([3.0, 0.2, 0.0]), np.array([-2.0, 0.0, 2.5])]
+    p = codec.params(0.5)
+    base = codec.encode(sc, eyes, p=p)
+    far = codec.encode(sc, eyes + [np.array([60.0, -45.0, 80.0])], p=p)
+    assert far["raw"] == base["raw"]
+    near = codec.encode(sc, eyes + [sc.means.astype(np.float64).mean(axis=1)], p=p)
+    assert len(near["occupancy"]) > len(base["occupancy"])
 
 
 def _sorted_formulation(means, eyes, p):

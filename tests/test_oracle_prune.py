@@ -44,6 +44,17 @@ def test_hand_worked_iteration():
     assert not removed[1]
 
 
+def test_threshold_is_strict_and_bad_importances_count_zero():
+    """Candidates have dMSE_k strictly below dMSE_MAX (a splat exactly at it stays); an importance
+    that is negative or NaN adds nothing to the budget."""
+    removed, budget, total, order = prune.select([1.0, 0.5, 0.999999], [0.3, 0.2, 0.1], [True] * 3, 1.0, 1)
+    assert order == [1, 2] and not removed[0]
+    q = prune.quantize_importance(np.array([-1e-3, np.nan, 0.25, 0.0, -0.0]))
+    assert q.tolist() == [0, 0, 2 ** 38, 0, 0]
+    removed, budget, *_ = prune.select([0.1, 0.2], [-0.5, 0.25], [True, True], 1.0, 1)
+    assert budget == 2 ** 38 and removed.tolist() == [True, True]
+
+
 def _numpy_select(dmse, imp, alive, dmax, remaining, a=prune.A_DEFAULT):
     """The same rule through numpy: lexsort on (m, index), cumulative sum, searchsorted."""
     q = np.floor(np.asarray(imp) * 2.0 ** 40).astype(np.int64)

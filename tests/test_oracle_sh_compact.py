@@ -113,3 +113,20 @@ def test_unseen_splat_keeps_its_coefficients():
     Lp, kept, *_ = shc.compact_splat(L, m, c, np.zeros(5), 0.3, 0.8, 51.0)
     assert kept is None
     np.testing.assert_allclose(Lp @ shc.YCOCG_TO_RGB.T, L, rtol=0, atol=1e-15)
+
+
+def test_cosine_test_compares_with_kept_columns_only():
+    """Columns 1, 2, 3 at 0, 20 and 40 degrees in one plane, the rest orthonormal, alpha = 0.9:
+    column 2 goes (cos 20 = 0.94 with column 1); column 3 stays, since its cosine with the kept
+    column 1 is cos 40 = 0.77 and the dropped column 2 no longer counts; a zero column goes."""
+    V = np.zeros((16, 16))
+    V[0, 0] = 1.0
+    for col, deg in ((1, 0.0), (2, 20.0), (3, 40.0)):
+        V[1, col], V[2, col] = math.cos(math.radians(deg)), math.sin(math.radians(deg))
+    for col in range(4, 15):
+        V[col - 1, col] = 1.0
+    # column 15 stays zero
+    G = V.T @ V
+    assert shc.cosine_kept(G, 0.9) == [0, 1, 3] + list(range(4, 15))
+    assert shc.cosine_kept(G, 0.95) == list(range(15))  # 0.94 < 0.95: nothing parallel enough
+    assert shc.cosine_kept(G, 0.7) == [0, 1] + list(range(4, 15))  # cos 40 = 0.77 > 0.7 too
