@@ -56,3 +56,24 @@ def test_host_only_layout_and_status_strings(libpotr):
         B.potr_view_layout(synth.cameras_to_array(cams), B.make_config(tile_w=16, tile_h=8))
     ws = B.potr_bin_sort_workspace_size(1000, 2, tt, 100_000)
     assert ws >= 8 * 100_000 + 16 * 2000
+
+
+def test_every_entry_point_rejects_null_arguments_on_the_host(libpotr):
+    """Every call that returns a status, given null pointers and zero sizes, answers
+    POTR_ERR_INVALID_ARGUMENT from its host-side checks, before any device work (only null
+    pointers are passed, so nothing could be launched on a device even if a check were missing)."""
+    import ctypes as C
+
+    from paper_2601_14821_gb300 import _binding as B
+
+    floats = (C.c_float, C.c_double)
+    checked = []
+    for name, (res, args) in sorted(B.SIGNATURES.items()):
+        if res is not B._I32 or name == "potr_version":
+            continue
+        vals = [0.0 if a in floats else (None if a is B._P or issubclass(a, C._Pointer) else 0) for a in args]
+        assert getattr(B.lib(), name)(*vals) == B.POTR_ERR_INVALID_ARGUMENT, name
+        checked.append(name)
+    for required in ("potr_preprocess", "potr_bin_sort", "potr_render", "potr_removal_effect",
+                     "potr_render_backward", "potr_sh_compact", "potr_codec_encode", "potr_codec_decode"):
+        assert required in checked
