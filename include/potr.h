@@ -380,8 +380,8 @@ POTR_API potr_status potr_prune_select(int64_t n, const double* d_dmse, const do
                                        potr_stream_t stream);
 
 /*
- * Removes the pruned splats from the scene: d_opacity_logits[k] = -infinity where d_alive[k]
- * == 0 (opacity 0 after activation: the splat keeps no tile and composites nowhere, so its
+ * Removes the pruned splats from the scene (Section IV-C: the splats of the removal set S leave
+ * it): d_opacity_logits[k] = -infinity where d_alive[k] == 0 (opacity 0 after activation: the splat keeps no tile and composites nowhere, so its
  * removal effect and importance are 0 from then on).  Device arrays of n entries.
  */
 POTR_API potr_status potr_prune_apply(int64_t n, const uint8_t* d_alive, float* d_opacity_logits,
@@ -425,13 +425,15 @@ POTR_API potr_status potr_adam_step(const potr_scene_grads* params, const potr_s
                                     const potr_scene_grads* m, const potr_scene_grads* v, int64_t n, int64_t step,
                                     const float* lr, float beta1, float beta2, float eps, potr_stream_t stream);
 
-/* The per-step factors potr_adam_step uses, for steps first_step .. first_step + count - 1 (host):
+/* The per-step factors potr_adam_step uses (Adam's bias corrections, Kingma & Ba 2015; the
+ * optimiser of Section IV-F's fine-tuning), for steps first_step .. first_step + count - 1 (host):
  * out[i][0..5] = lr[g] / (1 - beta1^t) of the six groups, out[i][6] = 1 / sqrt(1 - beta2^t),
  * t = first_step + i, computed in binary64 and rounded to float.  first_step >= 1. */
 POTR_API potr_status potr_adam_schedule(int64_t first_step, int64_t count, const float* lr, float beta1,
                                         float beta2, float* out);
 
-/* potr_adam_step with t taken from the device: the update of step t = *d_step + 1 uses row
+/* potr_adam_step (Section IV-F's fine-tuning optimiser) with t taken from the device: the
+ * update of step t = *d_step + 1 uses row
  * *d_step of d_sched ([n_sched][7], device, from potr_adam_schedule with first_step 1), then
  * *d_step is incremented on the device; a step past the table changes nothing but the counter.
  * Gives the same bits as potr_adam_step(step = t) and needs no host argument that changes from
