@@ -433,9 +433,8 @@ POTR_API potr_status potr_adam_schedule(int64_t first_step, int64_t count, const
                                         float beta2, float* out);
 
 /* potr_adam_step (Section IV-F's fine-tuning optimiser) with t taken from the device: the
- * update of step t = *d_step + 1 uses row
- * *d_step of d_sched ([n_sched][7], device, from potr_adam_schedule with first_step 1), then
- * *d_step is incremented on the device; a step past the table changes nothing but the counter.
+ * update of step t = *d_step + 1 uses row *d_step of d_sched ([n_sched][7], device, from
+ * potr_adam_schedule with first_step 1), then *d_step is incremented on the device; a step past the table changes nothing but the counter.
  * Gives the same bits as potr_adam_step(step = t) and needs no host argument that changes from
  * step to step, so a fine-tuning iteration can be captured in a CUDA graph. */
 POTR_API potr_status potr_adam_step_scheduled(const potr_scene_grads* params, const potr_scene_grads* grads,
