@@ -1,5 +1,5 @@
-"""Host-side logic that needs no GPU: the library's Adam factor table, the bitstream parser and
-the camera and image-layout helpers of the compression driver."""
+"""Host-side logic that needs no GPU: the library's Adam factor table, the bitstream parser, the
+camera and image-layout helpers of the compression driver and the autotuner's cache."""
 import struct
 import zlib
 
@@ -97,3 +97,29 @@ def test_view_images_follow_the_packed_layout():
     parts = view_images(synth.cameras_to_array(cams), buf)
     assert [p.numel() for p in parts] == [3 * w * h for w, h in sizes]
     assert torch.equal(torch.cat(parts), buf) and parts[1][0].item() == 3 * 16 * 8
+
+
+def test_autotune_answers_from_its_cache_file(tmp_path, monkeypatch):
+    """The autotuner's key is the GPU model, the splat count rounded down to a power of two and the
+    set of view resolutions; a key found in the cache file is answered before any device work."""
+    import json
+
+    import torch
+
+    import synth
+    from paper_2601_14821_gb300 import batched
+
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a: "GPU-under-test")
+    monkeypatch.setattr(batched, "_CACHE", {})
+    cams = synth.cameras_to_array([synth.look_at_camera((0.0, 0.0, -3.0), 1280, 720),
+                                   synth.look_at_camera((1.0, 0.0, -3.0), 640, 480),
+                                   synth.look_at_camera((2.0, 0.0, -3.0), 1280, 720)])
+    scene = {"means": torch.zeros(3, 3000)}
+    key = batched._signature(scene, cams)
+    assert key == "GPU-under-test|n~2048|[(640, 480), (1280, 720)]"
+    assert batched._signature({"means": torch.zeros(3, 4095)}, cams) == key
+    assert batched._signature({"means": torch.zeros(3, 4096)}, cams) != key
+    entry = {"tile_w": 8, "tile_h": 32, "batch": 128, "ms_per_view": 1.25, "table": []}
+    path = tmp_path / "tune.json"
+    path.write_text(json.dumps({key: entry}))
+    assert batched.autotune(scene, cams, device="cpu", cache_path=str(path)) == entry
