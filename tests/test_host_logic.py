@@ -1,5 +1,6 @@
 """Host-side logic that needs no GPU: the library's Adam factor table, the bitstream parser, the
-camera and image-layout helpers of the compression driver and the autotuner's cache."""
+camera and image-layout helpers of the compression driver, the autotuner's cache and the buffer
+pool that view chunks share."""
 import struct
 import zlib
 
@@ -123,3 +124,25 @@ def test_autotune_answers_from_its_cache_file(tmp_path, monkeypatch):
     path = tmp_path / "tune.json"
     path.write_text(json.dumps({key: entry}))
     assert batched.autotune(scene, cams, device="cpu", cache_path=str(path)) == entry
+
+
+def test_buffer_pool_shares_and_grows_named_buffers():
+    """A name is one buffer: typed views of it share storage, a larger request replaces it, a
+    smaller one reuses it, and every view starts 16-byte aligned (potr_preprocess rejects raster
+    and culling arrays that are not)."""
+    import torch
+
+    from paper_2601_14821_gb300.pipeline import BufferPool
+
+    pool = BufferPool("cpu")
+    a = pool.get("raster", 12, torch.float32)
+    b = pool.get("raster", 6, torch.int64)
+    assert a.numel() == 12 and b.numel() == 6 and a.data_ptr() == b.data_ptr()
+    big = pool.get("raster", 1000, torch.float32)
+    assert big.numel() == 1000 and pool.nbytes() == 4000
+    small = pool.get("raster", 3, torch.int32)
+    assert small.data_ptr() == big.data_ptr()
+    other = pool.get("cull", 0, torch.int32)  # at least one element
+    assert other.numel() == 1 and pool.nbytes() == 4004
+    for t in (a, big, other):
+        assert t.data_ptr() % 16 == 0
