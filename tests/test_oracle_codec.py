@@ -207,3 +207,20 @@ def test_parallel_parse_formulation_equals_the_recursive_decode():
         want, _ = codec.decode_positions(occ, corner, S, dups)
         got = _parallel_parse(occ, corner, S, dups)
         assert np.array_equal(got, want), n
+
+
+def test_single_splat_closed_form():
+    """One splat: the root cube has its corner at the splat and edge 1, so the splat lies at the
+    corner of every cell on its path (child 0 each time) and its leaf is the first depth d at
+    which the cell centre, 0.5 sqrt(3) 2^-d away, is within the tolerance max(gamma, beta |mu - eye|)."""
+    sc = synth.uniform_cube_scene(1, 3)
+    eye = np.array([3.0, 0.2, 0.0])
+    p = codec.params(0.5)
+    mu = sc.means[:, 0].astype(np.float64)
+    tol = max(p["gamma"], p["beta"] * float(np.linalg.norm(mu - eye)))
+    d = next(k for k in range(codec.DEPTH + 1) if 0.5 * math.sqrt(3.0) * 2.0 ** -k < tol)
+    e = codec.encode(sc, [eye], p=p)
+    assert e["S"] == 1.0 and np.array_equal(e["corner"], mu)
+    assert e["occupancy"] == bytes([1] * d + [0]) and e["depth"].tolist() == [d]
+    dec = codec.decode(e["compressed"])
+    np.testing.assert_allclose(dec["means"][:, 0], mu + 0.5 * 2.0 ** -d, rtol=0, atol=1e-15)
