@@ -53,7 +53,9 @@ def test_stream_parser_reads_the_oracle_layout():
     assert [tuple(x) for x in np.frombuffer(e["raw"][a:b], "<u4").reshape(-1, 2)] == [tuple(d) for d in e["dups"]]
     a, b = h["attrs"]
     assert (b - a) == 4 * 55 * 40
-    assert h["p"]["sf_sh"] == ocodec.params(0.5)["sf_sh"]
+    want = ocodec.params(0.5)
+    for k in ("sf_scale", "sf_rotation", "sf_opacity", "sf_sh"):  # four distinct values, so an order swap shows
+        assert h["p"][k] == want[k], k
     np.testing.assert_array_equal(h["cube"], (*e["corner"], e["S"]))
 
 
