@@ -77,3 +77,17 @@ def test_every_entry_point_rejects_null_arguments_on_the_host(libpotr):
     for required in ("potr_preprocess", "potr_bin_sort", "potr_render", "potr_removal_effect",
                      "potr_render_backward", "potr_sh_compact", "potr_codec_encode", "potr_codec_decode"):
         assert required in checked
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libpotr.so every call raises at once (there is no CPU fallback to take over)."""
+    import numpy as np
+
+    from paper_2601_14821_gb300 import _binding as B
+
+    monkeypatch.setattr(B, "_lib", None)
+    monkeypatch.setattr(B, "LIB_PATH", str(tmp_path / "libpotr.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        B.lib()
+    with pytest.raises(RuntimeError, match="not built"):
+        B.potr_view_layout(np.zeros((1, 18), np.float32), B.make_config())
