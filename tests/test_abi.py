@@ -1,4 +1,5 @@
-"""The C-ABI library loads without a GPU and exports every entry point include/potr.h declares."""
+"""The C-ABI library loads without a GPU, exports every entry point include/potr.h declares and
+rejects null arguments on the host; without the library every call fails loudly."""
 import ctypes
 import os
 import re
