@@ -1,0 +1,167 @@
+"""How strong the oracle pins are: plant one plausible mistake at a time in an oracle source (a
+dropped term, a wrong sign, a swapped operand, an off-by-one bound, a changed table constant),
+run that oracle's `-m "not gpu"` pins, and restore the source.  Every mistake must make at least
+one pin fail ("CAUGHT"); a "MISSED" line names a pin that is missing.  CPU only; the oracle
+sources are edited in place, so the script refuses to start over uncommitted changes to them.
+
+Usage: python tests/mutate_oracles.py [name ...]     (no names: every mutation; a few minutes)
+"""
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+C = "oracle/potr_oracle.c"
+
+MUT = [
+    # removal effect
+    ("pd_mul", C, "(PK - P[3 * (i + 1) + ch]) / (1.0 - a)", "(PK - P[3 * (i + 1) + ch]) * (1.0 - a)"),
+    ("dse_factor", C, "dse += pd * pd + 2.0 * pd * diff[ch];", "dse += pd * pd + pd * diff[ch];"),
+    ("dse_sign", C, "dse += pd * pd + 2.0 * pd * diff[ch];", "dse += pd * pd - 2.0 * pd * diff[ch];"),
+    ("imp_alpha", C, "double w = Tv[i] * a;", "double w = a;"),
+    ("imp_tnext", C, "            Tv[i] = T;\n", "            Tv[i] = T * (1.0 - a);\n"),
+    # compositing walk
+    ("tmin_after", C, "    if (Tn < cfg->t_min) break;\n",
+     "    if (Tn < cfg->t_min) { out[K].pos = i - s; out[K].k = k; out[K].alpha = a; ++K; last = i - s + 1; T = Tn; break; }\n"),
+    ("tmin_continue", C, "    if (Tn < cfg->t_min) break;\n", "    if (Tn < cfg->t_min) continue;\n"),
+    ("amin_le", C, "    if (a < cfg->alpha_min) continue;\n", "    if (a < 0.5f * cfg->alpha_min) continue;\n"),
+    ("amax_drop", C, "float a = fminf(cfg->alpha_max, sp->opacity[k] * G);", "float a = fminf(1.0f, sp->opacity[k] * G);"),
+    ("cross_sign", C, "float u = fmaf(A, dx, B * dy);", "float u = fmaf(A, dx, -B * dy);"),
+    ("comp_T", C, "    for (int ch = 0; ch < 3; ++ch) c[ch] += T * a * sp->rgb[ch * sp->n + ent[i].k];\n    T *= (1.0 - a);",
+     "    for (int ch = 0; ch < 3; ++ch) c[ch] += T * a * sp->rgb[ch * sp->n + ent[i].k];\n    T *= (1.0 - 0.5 * a);"),
+    ("comp_noT", C, "c[ch] += T * a * sp->rgb[ch * sp->n + ent[i].k];", "c[ch] += a * sp->rgb[ch * sp->n + ent[i].k];"),
+    ("centre_half", C, "int64_t K = walk_pixel(&sp, cfg, vals, s, e, (float)x + 0.5f, (float)y + 0.5f, -1, ent,",
+     "int64_t K = walk_pixel(&sp, cfg, vals, s, e, (float)x, (float)y + 0.5f, -1, ent,"),
+    # activation
+    ("rot_sign", C, "R[0][1] = 2.0f * (qx * qy - qw * qz);", "R[0][1] = 2.0f * (qx * qy + qw * qz);"),
+    ("rot_transpose", C, "M[i][j] = R[i][j] * s[j];", "M[i][j] = R[j][i] * s[j];"),
+    ("scale_row", C, "M[i][j] = R[i][j] * s[j];", "M[i][j] = R[i][j] * s[i];"),
+    ("scale_ln", C, "s[a] = orc_exp2r(log_scales[a * n + k] * kLog2e);", "s[a] = orc_exp2r(log_scales[a * n + k]);"),
+    ("sigmoid_flip", C, "opacity[k] = 1.0f / (1.0f + ex);", "opacity[k] = ex / (1.0f + ex);"),
+    ("qnorm_drop", C, "qw = qw / r; qx = qx / r; qy = qy / r; qz = qz / r;", "(void)r;"),
+    # SH
+    ("sh_cs_phase", C, "pmm *= -fact * s;", "pmm *= fact * s;"),
+    ("sh_sin_cos", C, "else v = sqrt(2.0) * K * sin(am * phi) * P;", "else v = sqrt(2.0) * K * cos(am * phi) * P;"),
+    ("sh_sqrt2", C, "else if (m > 0) v = sqrt(2.0) * K * cos(am * phi) * P;", "else if (m > 0) v = K * cos(am * phi) * P;"),
+    ("sh_offset", C, "      v += 0.5;\n", "      v += 0.0;\n"),
+    ("sh_clamp", C, "rgb[ch * n + k] = v > 0.0 ? v : 0.0;", "rgb[ch * n + k] = v;"),
+    ("sh_dir", C, "double d[3] = {(double)mu[0] - cc[0], (double)mu[1] - cc[1], (double)mu[2] - cc[2]};",
+     "double d[3] = {cc[0] - (double)mu[0], cc[1] - (double)mu[1], cc[2] - (double)mu[2]};"),
+    ("sh_channel", C, "v += (double)sh[(i * 3 + ch) * n + k] * Y[i];", "v += (double)sh[(ch * 16 + i) * n + k] * Y[i];"),
+    ("cam_centre", C, "cc[j] = -((double)W[0 * 4 + j] * W[3] + (double)W[1 * 4 + j] * W[7] + (double)W[2 * 4 + j] * W[11]);",
+     "cc[j] = -((double)W[j * 4 + 0] * W[3] + (double)W[j * 4 + 1] * W[7] + (double)W[j * 4 + 2] * W[11]);"),
+    # projection
+    ("lowpass_c", C, "float c = ((U1[0] * T1[0] + U1[1] * T1[1]) + U1[2] * T1[2]) + cfg->lowpass;",
+     "float c = ((U1[0] * T1[0] + U1[1] * T1[1]) + U1[2] * T1[2]);"),
+    ("jac_sign", C, "float j02 = -(cam->fx * xc) / z2;", "float j02 = (cam->fx * xc) / z2;"),
+    ("jac_clamp", C, "float xc = fminf(lim_x, fmaxf(-lim_x, txz)) * t[2];", "float xc = txz * t[2];"),
+    ("det_sign", C, "float det = a * c - b * b;", "float det = a * c + b * b;"),
+    ("conic_b", C, "float ca = c / det, cb = -b / det, cc2 = a / det;", "float ca = c / det, cb = b / det, cc2 = a / det;"),
+    ("conic_swap", C, "float ca = c / det, cb = -b / det, cc2 = a / det;", "float ca = a / det, cb = -b / det, cc2 = c / det;"),
+    ("radius_2s", C, "float r = ceilf(3.0f * sqrtf(lam));", "float r = ceilf(2.0f * sqrtf(lam));"),
+    ("qcoef_b", C, "qcoef[n + k] = cb * (-kLog2e);", "qcoef[n + k] = cb * kA;"),
+    ("mean_cx", C, "float mx = cam->fx * txz + cam->cx;", "float mx = cam->fx * txz - cam->cx;"),
+    ("near_cull", C, "if (!(t[2] > cfg->near_z)) continue;", "if (!(t[2] > 0.0f)) continue;"),
+    ("rect_x1", C, "float fx1 = floorf((mx + r) / (float)cfg->tile_w) + 1.0f;", "float fx1 = floorf((mx + r) / (float)cfg->tile_w);"),
+    ("view_row", C, "for (int i = 0; i < 3; ++i) t[i] = ((W[i * 4 + 0] * mu[0] + W[i * 4 + 1] * mu[1]) + W[i * 4 + 2] * mu[2]) + W[i * 4 + 3];",
+     "for (int i = 0; i < 3; ++i) t[i] = ((W[0 * 4 + i] * mu[0] + W[1 * 4 + i] * mu[1]) + W[2 * 4 + i] * mu[2]) + W[i * 4 + 3];"),
+    # binning and sort
+    ("sort_unstable", C, "if (ks[b] < ks[a]) {", "if (ks[b] <= ks[a]) {"),
+    ("key_order", C, "keys[e] = (tile << 32) | (uint64_t)dbits;", "keys[e] = ((uint64_t)dbits << 32) | tile;"),
+    ("rect_colmajor", C, "    for (int32_t ty = rect[n + k]; ty < rect[3 * n + k]; ++ty)\n      for (int32_t tx = rect[k]; tx < rect[2 * n + k]; ++tx) {",
+     "    for (int32_t tx = rect[k]; tx < rect[2 * n + k]; ++tx)\n      for (int32_t ty = rect[n + k]; ty < rect[3 * n + k]; ++ty) {"),
+    ("cull_margin", C, "float margin = 1e-5f * mag + 1e-4f;", "float margin = -0.05f * mag;"),
+    ("cull_centre", C, "if (ux0 <= 0.0f && ux1 >= 0.0f && vy0 <= 0.0f && vy1 >= 0.0f) pmax = fmaxf(pmax, 0.0f);", ""),
+    ("cull_edge", C, "float u1 = fminf(fmaxf(ku * vy1, ux0), ux1);", "float u1 = fminf(fmaxf(ku * vy0, ux0), ux1);"),
+    ("ranges_first", C, "if (i == 0 || (keys[i - 1] >> 32) != (keys[i] >> 32)) ranges[2 * t] = (uint32_t)i;",
+     "if (i == 0 || (keys[i - 1] >> 32) != (keys[i] >> 32)) ranges[2 * t] = (uint32_t)(i + (i > 0));"),
+    # exp2r
+    ("exp2r_coef", C, "  for (int k = 1; k <= 6; ++k) {\n    c = c * ln2;", "  for (int k = 1; k <= 5; ++k) {\n    c = c * ln2;"),
+    ("exp2r_round", C, "float n = rintf(y);", "float n = floorf(y);"),
+]
+
+TESTS = ["tests/test_oracle_pins.py", "tests/test_oracle_grad.py"]
+PR, SH, CO, AD, GR = "oracle/prune.py", "oracle/sh_compact.py", "oracle/codec.py", "oracle/adam.py", "oracle/grad.py"
+PY_TESTS = {PR: ["tests/test_oracle_prune.py", "tests/test_oracle_hyperparameters.py"], SH: ["tests/test_oracle_sh_compact.py", "tests/test_oracle_hyperparameters.py"],
+            CO: ["tests/test_oracle_codec.py", "tests/test_host_logic.py", "tests/test_oracle_hyperparameters.py"], AD: ["tests/test_oracle_adam.py"], GR: ["tests/test_oracle_grad.py"]}
+MUT += [
+    ("m_negsign", PR, "return (math.sqrt(1.0 - (2.0 * a) * x) - 1.0) / a", "return (1.0 - math.sqrt(1.0 - (2.0 * a) * x)) / a"),
+    ("m_a", PR, "return (math.sqrt(1.0 - (2.0 * a) * x) - 1.0) / a", "return (math.sqrt(1.0 - a * x) - 1.0) / a"),
+    ("cand_le", PR, "dmse[k] < dmse_max_value]", "dmse[k] <= dmse_max_value]"),
+    ("budget_r", PR, "// int(remaining)", "// int(remaining + 1)"),
+    ("tie_desc", PR, "key=lambda k: (m_map(dmse[k] / dmse_max_value, a), k))", "key=lambda k: (m_map(dmse[k] / dmse_max_value, a), -k))"),
+    ("budget_lt", PR, "if budget <= total:", "if budget < total:"),
+    ("dmax_q", PR, "10.0 ** (-8.8 - 2.0 * q)", "10.0 ** (-8.8 - q)"),
+    ("alive_ign", PR, "if alive[k] and dmse[k] < dmse_max_value]", "if dmse[k] < dmse_max_value]"),
+    ("qnan", PR, "imp = np.where(imp >= 0.0, imp, 0.0)", "imp = np.where(np.isnan(imp), 0.0, imp)"),
+    ("lam_dc", SH, "np.where(A == 0, 0.0, lam)", "lam"),
+    ("lam_chroma", SH, "lams = (lam, 3.0 * lam, 3.0 * lam)", "lams = (lam, lam, lam)"),
+    ("cos_abs", SH, "if any(abs(G[i, j]) / math.sqrt(G[i, i] * G[j, j]) > alpha for j in kept):",
+     "if any(G[i, j] / math.sqrt(G[i, i] * G[j, j]) > alpha for j in kept):"),
+    ("cos_all", SH, "> alpha for j in kept):", "> alpha for j in range(i)):"),
+    ("w_sum", SH, "w = np.where(w > 0, w, 0.0) / np.max(w)", "w = np.where(w > 0, w, 0.0) / np.sum(w)"),
+    ("w_rows", SH, "rows.append(ws * Y)", "rows.append(Y)"),
+    ("pass2_luma", SH, "if not quantises_to_zero(first[i, ch], sf)]", "if not quantises_to_zero(first[i, 0], sf)]"),
+    ("quant_floor", SH, "return math.floor(0.5 + x * sf) == 0", "return math.floor(x * sf) == 0"),
+    ("dir_rev", SH, "d = np.asarray(mean, np.float64) - c", "d = c - np.asarray(mean, np.float64)"),
+    ("alpha_q", SH, "\"alpha\": 1.0 / (1.0 + math.exp(-3.0 * q))", "\"alpha\": 1.0 / (1.0 + math.exp(-q))"),
+    ("offset_in", SH, "cols.append(ws * (Y @ L_rgb))", "cols.append(ws * (Y @ L_rgb + 0.5))"),
+    ("co_sign", SH, "[0.5, 0.0, -0.5], [-0.25", "[0.5, 0.0, 0.5], [-0.25"),
+    ("pass2_skip", SH, "second[:, ch] = _ridge(G, b[:, ch], keep2, lams[ch])", "second[:, ch] = first[:, ch]"),
+    ("q_round", CO, "return np.floor(0.5 + np.asarray(x, np.float64) * sf).astype(np.int64)",
+     "return np.floor(np.asarray(x, np.float64) * sf).astype(np.int64)"),
+    ("root_min", CO, "S = float((mu.max(axis=1) - lo).max())", "S = float((mu.max(axis=1) - lo).min())"),
+    ("tol_min", CO, "return np.maximum(gamma, beta * np.min(np.array(d), axis=0))", "return np.maximum(gamma, beta * np.max(np.array(d), axis=0))"),
+    ("leaf_centre_corner", CO, "return np.array([corner[a] + (cell[a] + 0.5) * w for a in range(3)])", "return np.array([corner[a] + cell[a] * w for a in range(3)])"),
+    ("split_le", CO, "must_split = not (dist < tol[k])", "must_split = not (dist < 2.0 * tol[k])"),
+    ("morton", CO, "cx, cy, cz = ((int(X[a, k]) >> sh) & 1 for a in range(3))", "cz, cy, cx = ((int(X[a, k]) >> sh) & 1 for a in range(3))"),
+    ("leaf_order", CO, "for k in sorted(members):", "for k in sorted(members, reverse=True):"),
+    ("quat_flip", CO, "qn = np.where(qn[0] < 0.0, -qn, qn)", "qn = qn"),
+    ("dc_diff", CO, "out[\"sh\"][:3] = np.diff(", "out[\"sh\"][3:6] = np.diff("),
+    ("sf_op", CO, "\"sf_opacity\": 1.0 + 200.0 * q", "\"sf_opacity\": 1.0 + 100.0 * q"),
+    ("op_offset", CO, "opacity = (op[0] + 0.25) / sf_op", "opacity = (op[0] + 0.5) / sf_op"),
+    ("dup_count", CO, "dups.append((leaves[0], len(members) - 1))", "dups.append((leaves[0], len(members)))"),
+    ("w_recon", CO, "w = np.sqrt(np.maximum(0.0, 1.0 - (xyz ** 2).sum(axis=0)))", "w = np.sqrt(np.maximum(0.0, 1.0 - xyz.sum(axis=0)))"),
+    ("adam_bc1", AD, "p -= (lr / bc1) * m / denom", "p -= lr * m / denom"),
+    ("adam_eps", AD, "denom = np.sqrt(v) / np.sqrt(bc2) + eps", "denom = np.sqrt(v / bc2 + eps)"),
+    ("g_clamp", GR, "xc = torch.clamp(txz, -lim_x, lim_x) * tz", "xc = txz * tz"),
+    ("g_sh_sign", GR, "-c1 * y, c1 * z, -c1 * x,", "c1 * y, c1 * z, -c1 * x,"),
+    ("g_sh_c3", GR, "c3d * z * (2 * zz - 3 * xx - 3 * yy)", "c3d * z * (2 * zz - xx - yy)"),
+    ("g_cross", GR, "2.0 * pr[\"cb\"][k_t] * dx * dy", "pr[\"cb\"][k_t] * dx * dy"),
+    ("g_lowpass", GR, "c = cov[:, 1, 1] + cfg.lowpass", "c = cov[:, 1, 1]"),
+    ("g_T_incl", GR, "Tv = torch.exp(excl - start[seg])", "Tv = torch.exp(cs - start[seg])"),
+    ("g_relu", GR, "rgb = torch.relu(torch.einsum(\"icn,ni->nc\", p[\"sh\"], Y) + 0.5)", "rgb = torch.einsum(\"icn,ni->nc\", p[\"sh\"], Y) + 0.5"),
+    ("g_campos", GR, "campos = -(Wr.T @ tw)", "campos = -(Wr @ tw)"),
+    ("g_qnorm", GR, "q = p[\"quats\"] / torch.linalg.norm(p[\"quats\"], dim=0, keepdim=True)", "q = p[\"quats\"]"),
+    ("g_amax", GR, "alpha = torch.clamp(o[k_t] * torch.exp(power), max=float(cfg.alpha_max))", "alpha = o[k_t] * torch.exp(power)"),
+    ("adam_v", AD, "v += (1.0 - b2) * g * g", "v += (1.0 - b2) * abs(g)"),
+]
+
+
+def run(name, path, old, new):
+    tests = PY_TESTS.get(path, TESTS)
+    full = os.path.join(ROOT, path)
+    src = open(full).read()
+    if src.count(old) != 1:
+        return f"{name}: pattern found {src.count(old)} times"
+    try:
+        open(full, "w").write(src.replace(old, new))
+        r = subprocess.run([sys.executable, "-m", "pytest", *tests, "-q", "-x", "-p", "no:cacheprovider"],
+                           cwd=ROOT, capture_output=True, text=True, timeout=900)
+        tail = [l for l in r.stdout.splitlines() if l.startswith("FAILED") or " passed" in l or " failed" in l]
+        verdict = "CAUGHT" if r.returncode != 0 else "MISSED"
+        return f"{name}: {verdict}  {tail[0] if tail else r.stdout[-200:]}"
+    finally:
+        open(full, "w").write(src)
+
+
+if __name__ == "__main__":
+    dirty = subprocess.run(["git", "status", "--porcelain", "--", "oracle"], cwd=ROOT, capture_output=True, text=True)
+    if dirty.returncode != 0 or dirty.stdout.strip():
+        sys.exit("oracle/ has uncommitted changes (or this is not a git checkout): not planting mistakes")
+    want = set(sys.argv[1:])
+    for m in MUT:
+        if want and m[0] not in want:
+            continue
+        print(run(*m), flush=True)
+    subprocess.run([sys.executable, "-c", "import oracle; oracle.build(force=True)"], cwd=ROOT, check=True)
