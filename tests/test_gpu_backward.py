@@ -93,6 +93,23 @@ def test_loss_grad_kernel_against_plain_formula(tiny):
         assert torch.allclose(dL.double(), want, rtol=1e-6, atol=1e-12)
 
 
+def test_backward_matches_gradient_oracle_at_the_clamps():
+    """The clamp scene (splats beyond the Jacobian clamp, alpha clamped to alpha_max, colour
+    clamped at 0): the device masks the same three clamps as the binary64 autograd oracle, so the
+    gradients agree within the parity tolerance."""
+    from scenes import clamp_scene
+
+    cam = synth.look_at_camera((0.0, 0.0, -3.0), 64, 64)
+    sc, _ = clamp_scene(cam)
+    cfg = dict(tile_w=16, tile_h=16, batch=256)
+    tg = _targets(sc, [cam], cfg, 23)
+    fr = build_frame(sc, [cam], **cfg)
+    loss, grads, _, _ = _gpu_grads(fr, pack_targets(fr, tg), 1.0)
+    oloss, ograds, _ = G.loss_and_grad(sc, [cam], oracle_cfg(cfg), tg, lam=1.0)
+    assert loss == pytest.approx(oloss, rel=1e-5)
+    _check(grads, ograds, "clamps")
+
+
 def test_zero_residual_gives_zero_gradients(tiny):
     """Targets equal to the device's own render: every residual is 0, where the L1 term's
     subgradient is taken as 0, so the loss, dL/dc and every parameter gradient are exactly 0 (in

@@ -134,25 +134,13 @@ def test_binary64_forward_matches_c_oracle_at_the_clamps():
     """A scene that reaches every clamp of the forward: large splats beyond the Jacobian clamp
     whose footprints reach into the image, opaque splats (alpha clamped to alpha_max) and splats
     whose colour clamps at 0.  The binary64 forward still reproduces the C oracle's image."""
+    from scenes import clamp_scene
+
     cfg = oracle.make_config()
     cam = synth.look_at_camera((0.0, 0.0, -3.0), 64, 64)
-    base = synth.uniform_cube_scene(300, 41)
+    sc, m = clamp_scene(cam)
     W = cam.w2c.reshape(3, 4).astype(np.float64)
     lim = 1.3 * 0.5 * cam.width / cam.fx
-    pts = np.array([[s * r * 3.0, 0.2 * j, 3.0] for j, (s, r) in enumerate([(1, 1.5), (-1, 1.6), (1, 1.75)])])
-    far = W[:, :3].T @ (pts.T - W[:, 3:4])
-    m = far.shape[1]
-    sh_far = np.zeros((16, 3, m), np.float32)
-    sh_far[0] = 0.8
-    sc = synth.Scene(
-        np.concatenate([base.means, far.astype(np.float32)], axis=1),
-        np.concatenate([base.log_scales, np.full((3, m), 0.2, np.float32)], axis=1),
-        np.concatenate([base.quats, np.tile(np.array([[1.0], [0.0], [0.0], [0.0]], np.float32), m)], axis=1),
-        np.concatenate([base.opacity_logits, np.full(m, 2.0, np.float32)]),
-        np.concatenate([base.sh, sh_far], axis=2),
-    )
-    sc.opacity_logits[:40] = 8.0        # o = 0.9997: alpha clamped to alpha_max at the centre
-    sc.sh[0, 0, 40:80] = -3.0           # red below 0: clamped
     act = oracle.activate(sc)
     v = oracle.prepare_view(sc, cam, cfg, act)
     n = sc.n
