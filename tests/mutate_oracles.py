@@ -75,6 +75,27 @@ MUT = [
     ("cull_edge", C, "float u1 = fminf(fmaxf(ku * vy1, ux0), ux1);", "float u1 = fminf(fmaxf(ku * vy0, ux0), ux1);"),
     ("ranges_first", C, "if (i == 0 || (keys[i - 1] >> 32) != (keys[i] >> 32)) ranges[2 * t] = (uint32_t)i;",
      "if (i == 0 || (keys[i - 1] >> 32) != (keys[i] >> 32)) ranges[2 * t] = (uint32_t)(i + (i > 0));"),
+    # second batch
+    ("qnorm_term", C, "float n2 = ((qw * qw + qx * qx) + qy * qy) + qz * qz;", "float n2 = (qw * qw + qx * qx) + qy * qy;"),
+    ("rot_diag", C, "R[2][2] = 1.0f - 2.0f * (qx * qx + qy * qy);", "R[2][2] = 1.0f - 2.0f * (qx * qx + qz * qz);"),
+    ("cov_index", C, "jj[6] = {0, 1, 2, 1, 2, 2};", "jj[6] = {0, 1, 2, 1, 2, 1};"),
+    ("sh_norm", C, "factorial(l - am) / factorial(l + am)", "factorial(l + am) / factorial(l - am)"),
+    ("legendre_rec", C, "(ll + m - 1.0) * pmm", "(ll + m) * pmm"),
+    ("sh_phi", C, "double phi = atan2(y, x);", "double phi = atan2(x, y);"),
+    ("proj_row", C, "T0[j] = j00 * W[0 * 4 + j] + j02 * W[2 * 4 + j];", "T0[j] = j00 * W[1 * 4 + j] + j02 * W[2 * 4 + j];"),
+    ("eig_disc", C, "float disc = fmaxf(0.1f, mid * mid - det);", "float disc = fmaxf(0.1f, mid * mid + det);"),
+    ("eig_minus", C, "float lam = mid + sqrtf(disc);", "float lam = mid - sqrtf(disc);"),
+    ("my_fx", C, "float my = cam->fy * tyz + cam->cy;", "float my = cam->fx * tyz + cam->cy;"),
+    ("jy_fx", C, "float j11 = cam->fy / t[2];", "float j11 = cam->fx / t[2];"),
+    ("rect_y_tw", C, "float fy0 = floorf((my - r) / (float)cfg->tile_h);", "float fy0 = floorf((my - r) / (float)cfg->tile_w);"),
+    ("resid_sign", C, "diff[ch] = P[3 * K + ch] - (double)target[(int64_t)ch * H * W + pix];",
+     "diff[ch] = (double)target[(int64_t)ch * H * W + pix] - P[3 * K + ch];"),
+    ("tile_transpose", C, "uint64_t tile = tile_base + (uint64_t)ty * (uint64_t)tiles_x + (uint64_t)tx;",
+     "uint64_t tile = tile_base + (uint64_t)tx * (uint64_t)tiles_x + (uint64_t)ty;"),
+    ("ranges_last", C, "ranges[2 * t + 1] = (uint32_t)(i + 1);", "ranges[2 * t + 1] = (uint32_t)i;"),
+    ("tile_ku", C, "float ku = -B / (2.0f * A), kv = -B / (2.0f * C);", "float ku = -B / A, kv = -B / (2.0f * C);"),
+    ("brute_sign", C, "acc += d1 * d1 - d0 * d0;", "acc += d0 * d0 - d1 * d1;"),
+    ("exp2r_hiclamp", C, "if (y > 125.0f) y = 125.0f;", "if (y > 100.0f) y = 100.0f;"),
     # exp2r
     ("exp2r_coef", C, "  for (int k = 1; k <= 6; ++k) {\n    c = c * ln2;", "  for (int k = 1; k <= 5; ++k) {\n    c = c * ln2;"),
     ("exp2r_round", C, "float n = rintf(y);", "float n = floorf(y);"),
@@ -124,6 +145,8 @@ MUT += [
     ("w_recon", CO, "w = np.sqrt(np.maximum(0.0, 1.0 - (xyz ** 2).sum(axis=0)))", "w = np.sqrt(np.maximum(0.0, 1.0 - xyz.sum(axis=0)))"),
     ("adam_bc1", AD, "p -= (lr / bc1) * m / denom", "p -= lr * m / denom"),
     ("adam_eps", AD, "denom = np.sqrt(v) / np.sqrt(bc2) + eps", "denom = np.sqrt(v / bc2 + eps)"),
+    ("qbits", PR, "Q_BITS = 40", "Q_BITS = 30"),
+    ("cell_clip", CO, "return np.clip(X, 0, (1 << DEPTH) - 1).astype(np.int64)", "return np.clip(X, 0, (1 << DEPTH)).astype(np.int64)"),
     ("g_clamp", GR, "xc = torch.clamp(txz, -lim_x, lim_x) * tz", "xc = txz * tz"),
     ("g_sh_sign", GR, "-c1 * y, c1 * z, -c1 * x,", "c1 * y, c1 * z, -c1 * x,"),
     ("g_sh_c3", GR, "c3d * z * (2 * zz - 3 * xx - 3 * yy)", "c3d * z * (2 * zz - xx - yy)"),

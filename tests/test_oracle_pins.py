@@ -171,19 +171,24 @@ def test_colour_dc_only():
     np.testing.assert_allclose(pr["rgb"][:, 0], [max(0, v * y0 + 0.5) for v in sh[0, :, 0].astype(np.float64)], rtol=1e-12)
 
 
-def test_rect_encloses_square_and_clamps(tiny):
+@pytest.mark.parametrize("tile", [(16, 16), (8, 32), (32, 8)])
+def test_rect_encloses_square_and_clamps(tiny, tile):
+    """The tile rectangle is every tile of the view that meets the square of half-side r around the
+    centre, by enumeration, for the three tile shapes (width and height used on their own axes)."""
     sc, cam = tiny.scene, tiny.cameras[0]
+    tw, th = tile
+    cfg = oracle.make_config(tile_w=tw, tile_h=th)
     cov, op = oracle.activate(sc)
-    pr = oracle.project(sc, cov, cam, CFG, op)
-    tx, ty = oracle.tiles_of(cam, CFG)
+    pr = oracle.project(sc, cov, cam, cfg, op)
+    tx, ty = oracle.tiles_of(cam, cfg)
     for k in np.nonzero(pr["touched"])[0][:400]:
         mx, my, r = pr["mean2d"][0, k], pr["mean2d"][1, k], pr["radius"][k]
         want = [(x, y) for y in range(ty) for x in range(tx)
-                if x * 16 <= mx + r and (x + 1) * 16 > mx - r and y * 16 <= my + r and (y + 1) * 16 > my - r]
+                if x * tw <= mx + r and (x + 1) * tw > mx - r and y * th <= my + r and (y + 1) * th > my - r]
         x0, y0, x1, y1 = pr["rect"][:, k]
         got = [(x, y) for y in range(y0, y1) for x in range(x0, x1)]
         assert sorted(got) == sorted(want)
-        kept = [t for t in got if len(got) > oracle.CULL_MAX_TILES or oracle.tile_hit(pr, k, t[0], t[1], CFG)]
+        kept = [t for t in got if len(got) > oracle.CULL_MAX_TILES or oracle.tile_hit(pr, k, t[0], t[1], cfg)]
         assert pr["touched"][k] == len(kept)
 
 
@@ -417,6 +422,33 @@ def test_jacobian_clamp_freezes_the_footprint_beyond_the_limit():
     for j in (2, 3):
         np.testing.assert_allclose(c2[:, j], c2[:, 1], rtol=1e-5, atol=1e-3)
     assert c2[0, 0] < 0.9 * c2[0, 1]
+
+
+def test_projection_with_unequal_focal_lengths():
+    """A camera with fx = 1.6 fy and an off-centre principal point: centres and 2D covariances
+    still follow the finite-difference linearisation of its pinhole map (fx on x, fy on y)."""
+    sc = synth.uniform_cube_scene(400, 17)
+    base = synth.look_at_camera((0.3, -0.2, -3.0), 160, 90)
+    cam = synth.Camera(base.w2c, 1.6 * base.fy, base.fy, 0.45 * base.width, 0.55 * base.height, base.width,
+                       base.height)
+    cov, op = oracle.activate(sc)
+    pr = oracle.project(sc, cov, cam, CFG, op)
+    W = cam.w2c.reshape(3, 4).astype(np.float64)
+    checked = 0
+    for k in np.nonzero(pr["touched"])[0]:
+        mu = sc.means[:, k].astype(np.float64)
+        c = W[:, :3] @ mu + W[:, 3]
+        if abs(c[0] / c[2]) > 1.3 * 0.5 * cam.width / cam.fx or abs(c[1] / c[2]) > 1.3 * 0.5 * cam.height / cam.fy:
+            continue
+        m2, J = _numeric_jacobian(cam, mu)
+        S = np.array([[cov[0, k], cov[1, k], cov[2, k]], [cov[1, k], cov[3, k], cov[4, k]],
+                      [cov[2, k], cov[4, k], cov[5, k]]], np.float64)
+        ref = J @ S @ J.T + 0.3 * np.eye(2)
+        got = np.array([[pr["cov2d"][0, k], pr["cov2d"][1, k]], [pr["cov2d"][1, k], pr["cov2d"][2, k]]])
+        assert np.max(np.abs(got - ref)) < 1e-4 * np.max(np.abs(ref)) + 1e-6
+        assert np.max(np.abs(pr["mean2d"][:, k] - m2)) < 1e-4
+        checked += 1
+    assert checked > 100
 
 
 def _flat_view(opac, rgb, depth, w=16, h=16):
