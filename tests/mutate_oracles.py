@@ -147,6 +147,19 @@ MUT += [
     ("adam_eps", AD, "denom = np.sqrt(v) / np.sqrt(bc2) + eps", "denom = np.sqrt(v / bc2 + eps)"),
     ("qbits", PR, "Q_BITS = 40", "Q_BITS = 30"),
     ("cell_clip", CO, "return np.clip(X, 0, (1 << DEPTH) - 1).astype(np.int64)", "return np.clip(X, 0, (1 << DEPTH)).astype(np.int64)"),
+    # third batch
+    ("inst_index", C, "if (inst_dse) inst_dse[s + ent[i].pos] += dse;", "if (inst_dse) inst_dse[s + (uint32_t)i] += dse;"),
+    ("nlast_off", C, "    last = i - s + 1;\n", "    last = i - s;\n"),
+    ("pass2_dc", SH, "keep2 = [0] + [i for i in kept[1:] if not quantises_to_zero(first[i, ch], sf)]",
+     "keep2 = [i for i in kept if not quantises_to_zero(first[i, ch], sf)] or [0]"),
+    ("unseen_zero", SH, "return L_rgb @ RGB_TO_YCOCG.T, None, None, None, None", "return np.zeros((16, 3)), None, None, None, None"),
+    ("sh_chmajor", CO, "sh = np.asarray(scene.sh, np.float64).reshape(48, -1)[:, order]",
+     "sh = np.asarray(scene.sh, np.float64).transpose(1, 0, 2).reshape(48, -1)[:, order]"),
+    ("rot_store_w", CO, "\"rotation\": quantise(qn[1:], p[\"sf_rotation\"])", "\"rotation\": quantise(qn[:3], p[\"sf_rotation\"])"),
+    ("op_logit", CO, "op = 1.0 / (1.0 + np.exp(-np.asarray(scene.opacity_logits, np.float64)[order]))",
+     "op = np.asarray(scene.opacity_logits, np.float64)[order]"),
+    ("header_sf", CO, "head += struct.pack(\"<4d\", p[\"sf_scale\"], p[\"sf_rotation\"], p[\"sf_opacity\"], p[\"sf_sh\"])",
+     "head += struct.pack(\"<4d\", p[\"sf_rotation\"], p[\"sf_scale\"], p[\"sf_opacity\"], p[\"sf_sh\"])"),
     ("g_clamp", GR, "xc = torch.clamp(txz, -lim_x, lim_x) * tz", "xc = txz * tz"),
     ("g_sh_sign", GR, "-c1 * y, c1 * z, -c1 * x,", "c1 * y, c1 * z, -c1 * x,"),
     ("g_sh_c3", GR, "c3d * z * (2 * zz - 3 * xx - 3 * yy)", "c3d * z * (2 * zz - xx - yy)"),

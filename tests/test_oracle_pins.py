@@ -557,6 +557,22 @@ def test_removal_effect_equals_definition_bruteforce(tiny, tiny_view):
     assert nz > 50
 
 
+def test_per_instance_partials_add_up_per_splat(tiny, tiny_view):
+    """The per-(tile, splat) partials sit at the splat's own list position: adding them up over
+    each splat's instances (through the sorted values) gives its dSSE and its importance sum."""
+    v, img, t32, t64, nl, tgt = tiny_view
+    cam = tiny.cameras[0]
+    d, imp, idse, iimp = oracle.removal_effect(v, v["vals"], v["ranges"], cam, CFG, tgt, per_instance=True)
+    n = tiny.scene.n
+    by_splat_d = np.zeros(n)
+    by_splat_i = np.zeros(n)
+    np.add.at(by_splat_d, v["vals"].astype(np.int64), idse)
+    np.add.at(by_splat_i, v["vals"].astype(np.int64), iimp)
+    assert np.count_nonzero(d) > 100
+    np.testing.assert_allclose(by_splat_d, d, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(by_splat_i, imp, rtol=1e-9, atol=1e-12)
+
+
 def test_removal_effect_pd_squared_when_target_is_render(tiny, tiny_view):
     v, img, t32, t64, nl, tgt = tiny_view
     d, _ = oracle.removal_effect(v, v["vals"], v["ranges"], tiny.cameras[0], CFG, img.astype(np.float32))
