@@ -160,6 +160,12 @@ MUT += [
      "op = np.asarray(scene.opacity_logits, np.float64)[order]"),
     ("header_sf", CO, "head += struct.pack(\"<4d\", p[\"sf_scale\"], p[\"sf_rotation\"], p[\"sf_opacity\"], p[\"sf_sh\"])",
      "head += struct.pack(\"<4d\", p[\"sf_rotation\"], p[\"sf_scale\"], p[\"sf_opacity\"], p[\"sf_sh\"])"),
+    # fourth batch
+    ("kA_scale", C, "const float kA = -0.5f * kLog2e;", "const float kA = -kLog2e;"),
+    ("cull_nomargin", C, "float margin = 1e-5f * mag + 1e-4f;", "float margin = 0.0f;"),
+    ("cull_max32", C, "#define ORC_CULL_MAX_TILES 64", "#define ORC_CULL_MAX_TILES 32"),
+    ("exclude_break", C, "    if ((int64_t)k == exclude) continue;\n", "    if ((int64_t)k == exclude) break;\n"),
+    ("near_ge", C, "if (!(t[2] > cfg->near_z)) continue;", "if (!(t[2] >= cfg->near_z)) continue;"),
     ("g_clamp", GR, "xc = torch.clamp(txz, -lim_x, lim_x) * tz", "xc = txz * tz"),
     ("g_sh_sign", GR, "-c1 * y, c1 * z, -c1 * x,", "c1 * y, c1 * z, -c1 * x,"),
     ("g_sh_c3", GR, "c3d * z * (2 * zz - 3 * xx - 3 * yy)", "c3d * z * (2 * zz - xx - yy)"),

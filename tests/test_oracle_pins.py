@@ -201,6 +201,37 @@ def test_cull_behind_and_near():
     assert list(pr["touched"][:2]) == [0, 0] and pr["touched"][2] > 0
 
 
+def test_near_plane_is_exclusive():
+    """A splat is culled when its camera-space z <= near_z: exactly on the plane it goes, one
+    binary32 step beyond it stays (identity world-to-camera map, so z is the stored mean)."""
+    near = np.float32(CFG.near_z)
+    cam = synth.Camera(np.array([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0], np.float32), 40.0, 40.0, 32.0, 32.0, 64, 64)
+    zs = [near, np.nextafter(near, np.float32(1.0))]
+    means = np.array([[0.0, 0.0], [0.0, 0.0], zs], np.float32)
+    sc = _scene(means, np.full((3, 2), -3.0), np.tile([[1.0], [0], [0], [0]], (1, 2)), np.zeros(2))
+    cov, op = oracle.activate(sc)
+    pr = oracle.project(sc, cov, cam, CFG, op)
+    assert pr["touched"][0] == 0 and pr["touched"][1] > 0
+
+
+def test_cull_limit_is_64_tiles():
+    """A needle-shaped splat along the image diagonal: with a rectangle of 33 to 64 tiles its
+    off-diagonal corner tiles are dropped by the tile test; with more than 64 tiles every tile is
+    kept."""
+    cam = synth.look_at_camera((0.0, 0.0, -3.0), 256, 256)
+    c, s_ = math.cos(math.pi / 8), math.sin(math.pi / 8)  # 45 degrees about z
+    means = np.zeros((3, 2))
+    log_scales = np.array([[math.log(0.226), math.log(0.4)], [math.log(0.02)] * 2, [math.log(0.02)] * 2])
+    quats = np.array([[c, c], [0, 0], [0, 0], [s_, s_]])
+    sc = _scene(means, log_scales, quats, np.full(2, 3.0))
+    cov, op = oracle.activate(sc)
+    pr = oracle.project(sc, cov, cam, CFG, op)
+    x0, y0, x1, y1 = pr["rect"]
+    area = (x1 - x0) * (y1 - y0)
+    assert 32 < area[0] <= oracle.CULL_MAX_TILES and 0 < pr["touched"][0] < area[0]
+    assert area[1] > oracle.CULL_MAX_TILES and pr["touched"][1] == area[1]
+
+
 # ------------------------------------------------------------------------------------------
 # binning and sort
 # ------------------------------------------------------------------------------------------
@@ -332,6 +363,13 @@ def test_tile_test_is_conservative_and_tight():
             near += res[1]
     # the margin keeps only a sliver of tiles whose maximum is 5 % short of alpha_min
     assert both > 300 and near < 0.05 * both
+    # a splat centred on a pixel centre (exponent 0 there): 3e-5 short of alpha_min is inside the
+    # margin (kept), 1 % short is not (dropped)
+    for f, want in ((1.0 - 3e-5, True), (0.99, False)):
+        proj = dict(mean2d=np.array([[7.5], [7.5]], np.float32),
+                    qcoef=np.array([[-0.05], [0.0], [-0.05]], np.float32),
+                    opacity=np.array([np.float32(amin * f)], np.float32))
+        assert oracle.tile_hit(proj, 0, 0, 0, CFG) == want, f
 
 
 def test_tile_test_agrees_with_rendered_alphas(tiny):
