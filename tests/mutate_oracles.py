@@ -166,6 +166,14 @@ MUT += [
     ("cull_max32", C, "#define ORC_CULL_MAX_TILES 64", "#define ORC_CULL_MAX_TILES 32"),
     ("exclude_break", C, "    if ((int64_t)k == exclude) continue;\n", "    if ((int64_t)k == exclude) break;\n"),
     ("near_ge", C, "if (!(t[2] > cfg->near_z)) continue;", "if (!(t[2] >= cfg->near_z)) continue;"),
+    # fifth batch
+    ("run_remaining", PR, "select(d, i, alive, dmse_max_value, iterations - it, a)", "select(d, i, alive, dmse_max_value, iterations, a)"),
+    ("cos_one_minus", SH, "kept = cosine_kept(G, alpha)", "kept = cosine_kept(G, 1.0 - alpha)"),
+    ("pass2_lam_luma", SH, "second[:, ch] = _ridge(G, b[:, ch], keep2, lams[ch])", "second[:, ch] = _ridge(G, b[:, ch], keep2, lams[0])"),
+    ("dup_range", CO, "for _ in range(1 + extra.get(leaf[0], 0)):", "for _ in range(max(1, extra.get(leaf[0], 0))):"),
+    ("tol_sq", CO, "return np.maximum(gamma, beta * np.min(np.array(d), axis=0))", "return np.maximum(gamma, beta * np.min(np.array(d), axis=0) ** 2)"),
+    ("g_power_half", GR, "power = -0.5 * (", "power = -1.0 * ("),
+    ("adam_bc2", AD, "bc2 = 1.0 - b2 ** t", "bc2 = 1.0 - b2 ** (t + 1)"),
     ("g_clamp", GR, "xc = torch.clamp(txz, -lim_x, lim_x) * tz", "xc = txz * tz"),
     ("g_sh_sign", GR, "-c1 * y, c1 * z, -c1 * x,", "c1 * y, c1 * z, -c1 * x,"),
     ("g_sh_c3", GR, "c3d * z * (2 * zz - 3 * xx - 3 * yy)", "c3d * z * (2 * zz - xx - yy)"),
