@@ -96,6 +96,12 @@ MUT = [
     ("tile_ku", C, "float ku = -B / (2.0f * A), kv = -B / (2.0f * C);", "float ku = -B / A, kv = -B / (2.0f * C);"),
     ("brute_sign", C, "acc += d1 * d1 - d0 * d0;", "acc += d0 * d0 - d1 * d1;"),
     ("exp2r_hiclamp", C, "if (y > 125.0f) y = 125.0f;", "if (y > 100.0f) y = 100.0f;"),
+    # sixth batch
+    ("p_dy_dx", C, "float p = fmaf(u, dx, v * dy);", "float p = fmaf(u, dx, v * dx);"),
+    ("v_C_dx", C, "float v = C * dy;", "float v = C * dx;"),
+    ("ranges_nobase", C, "int64_t t = (int64_t)((keys[i] >> 32) - tile_base);", "int64_t t = (int64_t)(keys[i] >> 32);"),
+    ("vals_nobase", C, "vals[e] = val_base + (uint32_t)k;", "vals[e] = (uint32_t)k;"),
+    ("t64_single", C, "if (t_final64) t_final64[pix] = T64;", "if (t_final64) t_final64[pix] = (double)T32;"),
     # exp2r
     ("exp2r_coef", C, "  for (int k = 1; k <= 6; ++k) {\n    c = c * ln2;", "  for (int k = 1; k <= 5; ++k) {\n    c = c * ln2;"),
     ("exp2r_round", C, "float n = rintf(y);", "float n = floorf(y);"),

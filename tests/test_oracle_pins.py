@@ -252,6 +252,21 @@ def test_bin_sort_keeps_emission_order_for_equal_keys(tiny):
     assert ties > 100
 
 
+def test_bin_sort_with_frame_bases(tiny):
+    """A view inside a multi-view frame: with tile base B and value base V its keys carry global
+    tiles t + B, its values are V + k, and its ranges (indexed by the view's own tiles), order and
+    emission indices are those of the view alone."""
+    sc, cam = tiny.scene, tiny.cameras[0]
+    v = oracle.prepare_view(sc, cam, CFG)
+    B, V = 123_457, 3 * sc.n
+    keys, vals, emit, ranges = oracle.bin_sort(v, cam, CFG, tile_base=B, val_base=V)
+    assert v["keys"].size > 1000
+    assert np.array_equal(keys >> np.uint64(32), (v["keys"] >> np.uint64(32)) + np.uint64(B))
+    assert np.array_equal(keys & np.uint64(0xFFFFFFFF), v["keys"] & np.uint64(0xFFFFFFFF))
+    assert np.array_equal(vals, v["vals"] + np.uint32(V))
+    assert np.array_equal(emit, v["emit"]) and np.array_equal(ranges, v["ranges"])
+
+
 def _check_bin_sort(sc, cam):
     """The oracle's keys, values, emission indices and tile ranges against numpy's stable argsort
     of keys emitted by enumeration, for the three tile shapes; returns the number of equal
