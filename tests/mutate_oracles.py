@@ -108,9 +108,11 @@ MUT = [
 ]
 
 TESTS = ["tests/test_oracle_pins.py", "tests/test_oracle_grad.py"]
-PR, SH, CO, AD, GR = "oracle/prune.py", "oracle/sh_compact.py", "oracle/codec.py", "oracle/adam.py", "oracle/grad.py"
+PR, SH, CO, AD, GR, OI = ("oracle/prune.py", "oracle/sh_compact.py", "oracle/codec.py", "oracle/adam.py",
+                          "oracle/grad.py", "oracle/__init__.py")
 PY_TESTS = {PR: ["tests/test_oracle_prune.py", "tests/test_oracle_hyperparameters.py"], SH: ["tests/test_oracle_sh_compact.py", "tests/test_oracle_hyperparameters.py"],
-            CO: ["tests/test_oracle_codec.py", "tests/test_host_logic.py", "tests/test_oracle_hyperparameters.py"], AD: ["tests/test_oracle_adam.py"], GR: ["tests/test_oracle_grad.py"]}
+            CO: ["tests/test_oracle_codec.py", "tests/test_host_logic.py", "tests/test_oracle_hyperparameters.py"], AD: ["tests/test_oracle_adam.py"], GR: ["tests/test_oracle_grad.py"],
+            OI: ["tests/test_oracle_pins.py"]}
 MUT += [
     ("m_negsign", PR, "return (math.sqrt(1.0 - (2.0 * a) * x) - 1.0) / a", "return (1.0 - math.sqrt(1.0 - (2.0 * a) * x)) / a"),
     ("m_a", PR, "return (math.sqrt(1.0 - (2.0 * a) * x) - 1.0) / a", "return (math.sqrt(1.0 - a * x) - 1.0) / a"),
@@ -180,6 +182,9 @@ MUT += [
     ("tol_sq", CO, "return np.maximum(gamma, beta * np.min(np.array(d), axis=0))", "return np.maximum(gamma, beta * np.min(np.array(d), axis=0) ** 2)"),
     ("g_power_half", GR, "power = -0.5 * (", "power = -1.0 * ("),
     ("adam_bc2", AD, "bc2 = 1.0 - b2 ** t", "bc2 = 1.0 - b2 ** (t + 1)"),
+    ("dmse_3P", OI, "out += d / (3.0 * cam.pixels) / n_views", "out += d / float(cam.pixels) / n_views"),
+    ("imp_P", OI, "imp += i / float(cam.pixels) / n_views", "imp += i / n_views"),
+    ("dmse_N", OI, "out += d / (3.0 * cam.pixels) / n_views", "out += d / (3.0 * cam.pixels)"),
     ("g_clamp", GR, "xc = torch.clamp(txz, -lim_x, lim_x) * tz", "xc = txz * tz"),
     ("g_sh_sign", GR, "-c1 * y, c1 * z, -c1 * x,", "c1 * y, c1 * z, -c1 * x,"),
     ("g_sh_c3", GR, "c3d * z * (2 * zz - 3 * xx - 3 * yy)", "c3d * z * (2 * zz - xx - yy)"),

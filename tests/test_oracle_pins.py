@@ -610,6 +610,39 @@ def test_removal_effect_equals_definition_bruteforce(tiny, tiny_view):
     assert nz > 50
 
 
+def test_dmse_is_the_change_in_mean_squared_error(tiny):
+    """dMSE_k is the change, when splat k alone is removed, of the mean squared error averaged over
+    the views (np.mean over each view's 3 x H x W values, then over views; two views of different
+    sizes; T_min = 0 so that the removal is exact), and the importances add up to the mean
+    coverage 1 - T_final averaged the same way."""
+    sc = tiny.scene
+    cams = [tiny.cameras[0], synth.look_at_camera((1.5, 0.4, -2.6), 96, 64)]
+    cfg0 = oracle.make_config(t_min=0.0)
+    tgts, imgs, cover = [], [], []
+    for v, cam in enumerate(cams):
+        pv = oracle.prepare_view(sc, cam, cfg0)
+        img, t32, t64, nl = oracle.render(pv, pv["vals"], pv["ranges"], cam, cfg0)
+        tgts.append((img + synth.target_noise(img.shape, 0.02, 7, v)).astype(np.float32))
+        imgs.append(img)
+        cover.append(np.mean(1.0 - t64))
+    d, imp = oracle.dmse(sc, cams, cfg0, tgts)
+    assert imp.sum() == pytest.approx(np.mean(cover), rel=1e-12)
+    checked = 0
+    for k in np.argsort(-np.abs(d))[:12]:
+        keep = np.ones(sc.n, bool)
+        keep[k] = False
+        sub = sc.subset(keep)
+        change = []
+        for cam, img, tgt in zip(cams, imgs, tgts):
+            pv = oracle.prepare_view(sub, cam, cfg0)
+            img_k, *_ = oracle.render(pv, pv["vals"], pv["ranges"], cam, cfg0)
+            t = tgt.astype(np.float64)
+            change.append(np.mean((img_k - t) ** 2) - np.mean((img - t) ** 2))
+        assert d[k] == pytest.approx(np.mean(change), rel=1e-9, abs=1e-15), k
+        checked += 1
+    assert checked == 12 and np.abs(d).max() > 0
+
+
 def test_per_instance_partials_add_up_per_splat(tiny, tiny_view):
     """The per-(tile, splat) partials sit at the splat's own list position: adding them up over
     each splat's instances (through the sorted values) gives its dSSE and its importance sum."""
