@@ -104,7 +104,7 @@ def lib():
             L.orc_project.argtypes = [i64, vp, vp, vp, vp, C.POINTER(Camera), C.POINTER(Config)] + [vp] * 9
             L.orc_bin.restype = i64
             L.orc_bin.argtypes = [i64, vp, vp, vp, vp, vp, vp, C.POINTER(Config), C.c_int32, C.c_uint64, u32, i64,
-                                  vp, vp, vp]
+                                  vp, vp, vp, C.c_int32]
             L.orc_tile_hit.restype = C.c_int
             L.orc_tile_hit.argtypes = [C.c_float] * 6 + [C.c_int] * 4 + [C.c_float]
             L.orc_tile_ranges.argtypes = [i64, vp, C.c_uint64, i64, vp]
@@ -194,17 +194,24 @@ def tiles_of(cam, cfg: Config):
     return (cam.width + cfg.tile_w - 1) // cfg.tile_w, (cam.height + cfg.tile_h - 1) // cfg.tile_h
 
 
-def bin_sort(proj: dict, cam, cfg: Config, tile_base: int = 0, val_base: int = 0):
-    """Emit and stably sort the (tile, depth) keys; returns keys, vals, emit_index, ranges."""
+def bin_sort(proj: dict, cam, cfg: Config, tile_base: int = 0, val_base: int = 0, whole_rect: bool = False):
+    """Emit and stably sort the (tile, depth) keys; returns keys, vals, emit_index, ranges.
+
+    ``whole_rect``: bin every tile of each splat's 3-sigma rectangle (the paper's footprint
+    binning, no tile test) instead of only the tiles where alpha_min is reachable."""
     n = proj["depth"].size
     tx, ty = tiles_of(cam, cfg)
-    m = int(proj["touched"].astype(np.int64).sum())
+    if whole_rect:
+        r = proj["rect"].astype(np.int64)
+        m = int(((r[2] - r[0]) * (r[3] - r[1])).sum())
+    else:
+        m = int(proj["touched"].astype(np.int64).sum())
     keys = np.empty(max(m, 1), np.uint64)
     vals = np.empty(max(m, 1), np.uint32)
     emit = np.empty(max(m, 1), np.uint32)
     got = lib().orc_bin(n, _p(proj["touched"]), _p(proj["rect"]), _p(proj["depth"]), _p(proj["mean2d"]),
                         _p(proj["qcoef"]), _p(proj["opacity"]), C.byref(cfg), tx, tile_base, val_base, m,
-                        _p(keys), _p(vals), _p(emit))
+                        _p(keys), _p(vals), _p(emit), int(bool(whole_rect)))
     assert got == m
     ranges = np.empty((tx * ty, 2), np.uint32)
     lib().orc_tile_ranges(m, _p(keys), tile_base, tx * ty, _p(ranges))
@@ -266,7 +273,7 @@ def pixel_lists(proj: dict, vals, ranges, cam, cfg: Config):
     ccam = make_camera(cam)
     vals = np.ascontiguousarray(vals, np.uint32)
     ranges = np.ascontiguousarray(ranges, np.uint32)
-    cap = max(1, int(vals.size) * cfg.tile_w * cfg.tile_h)
+    cap = max(1, min(int(vals.size) * cfg.tile_w * cfg.tile_h, 1 << 26))
     while True:
         pix = np.empty(cap, np.int64)
         k = np.empty(cap, np.uint32)

@@ -170,3 +170,84 @@ def oracle_loss(scene, cams, cfg, targets, lam: float = LAMBDA) -> tuple[float, 
         n_elems += 3 * cam.pixels
         keys.append((v["keys"].copy(), v["vals"].copy()))
     return total / n_elems, keys
+
+
+def _param_keys_of(p):
+    return [p[k] for k in PARAM_KEYS]
+
+
+def loss_grad_magnitude(scene, cams, cfg, targets, lam: float = LAMBDA) -> dict:
+    """Per parameter element, a bound B_p >= sum over pixels of |that pixel's contribution to
+    dL/dp|: the scale against which a binary32 accumulation of the gradient over pixels is
+    rounded.  For each composited (pixel, splat) entry of each view:
+
+      * the adjoint of alpha, dL/dalpha = sum_ch g_ch (T c_ch - S_>,ch / (1 - alpha)) (S_> the
+        suffix sum of T alpha c over the later entries of the pixel, g = dL/dc), is taken as the
+        sum of the magnitudes of its two parts, M = sum_ch |g_ch| (T c_ch + S_>,ch / (1 - alpha));
+      * the screen quantities s_j of the splat (centre mx, my, conic ca, cb, cc, opacity o,
+        colour r, g, b) receive M |d alpha / d s_j| (geometry, opacity) or |g_ch| T alpha (colour),
+        summed over the entries of the splat in the view;
+      * each parameter element p of splat k then gets sum_j |d s_j(k) / d p| times that sum, added
+        over views.
+    Every step replaces a sum by the sum of magnitudes, so B_p >= |dL/dp|.  Returns
+    {param: B as numpy binary64 of the parameter's shape}."""
+    p = to_params(scene)
+    sigma, o = activate(p)
+    n_elems = sum(3 * c.pixels for c in cams)
+    act = oracle.activate(scene)
+    n = scene.n
+    out = {k: np.zeros(np.shape(getattr(scene, k)), np.float64) for k in PARAM_KEYS}
+    names = ("mx", "my", "ca", "cb", "cc")
+    for cam, tgt in zip(cams, targets):
+        v = oracle.prepare_view(scene, cam, cfg, act)
+        pix, k, _ = oracle.pixel_lists(v, v["vals"], v["ranges"], cam, cfg)
+        pr = project(p, sigma, cam, cfg)
+        if pix.size == 0:
+            continue
+        H, W = cam.height, cam.width
+        k_t = torch.from_numpy(k.astype(np.int64))
+        pix_t = torch.from_numpy(pix.astype(np.int64))
+        leaves = [pr[nm][k_t].detach().clone().requires_grad_(True) for nm in names]
+        o_e = o[k_t].detach().clone().requires_grad_(True)
+        mx, my, ca, cb, cc = leaves
+        px = (pix_t % W).to(torch.float64) + 0.5
+        py = (pix_t // W).to(torch.float64) + 0.5
+        dx, dy = px - mx, py - my
+        expo = -0.5 * (ca * dx * dx + 2.0 * cb * dx * dy + cc * dy * dy)
+        alpha = torch.clamp(o_e * torch.exp(expo), max=float(cfg.alpha_max))
+        dalpha = torch.autograd.grad(alpha.sum(), leaves + [o_e])  # per entry (each alpha has its own leaves)
+        alpha = alpha.detach()
+        la = torch.log1p(-alpha)
+        excl = torch.cumsum(la, 0) - la
+        first = np.ones(pix.size, bool)
+        first[1:] = pix[1:] != pix[:-1]
+        seg = torch.from_numpy(np.cumsum(first) - 1)
+        starts = torch.from_numpy(np.nonzero(first)[0])
+        Tv = torch.exp(excl - excl[starts][seg])
+        rgb_e = pr["rgb"][k_t].detach()
+        contrib = (Tv * alpha)[:, None] * rgb_e  # [E, 3]
+        img = torch.zeros(3, H * W, dtype=torch.float64).index_add(1, pix_t, contrib.T)
+        r = img - torch.from_numpy(np.asarray(tgt, np.float64).reshape(3, -1))
+        gc = ((1.0 - lam) * torch.sign(r) + 2.0 * lam * r) / n_elems  # [3, P]
+        # suffix sums of later entries of the same pixel: segment total minus the inclusive prefix
+        cum = torch.cumsum(contrib, 0)
+        ends = torch.from_numpy(np.append(np.nonzero(first)[0][1:], pix.size) - 1)
+        seg_total = cum[ends][seg]
+        s_after = seg_total - cum
+        s_after = torch.clamp(s_after, min=0.0)  # rounding of the difference
+        gabs = gc.abs()[:, pix_t].T  # [E, 3]
+        M = (gabs * (Tv[:, None] * rgb_e + s_after / (1.0 - alpha)[:, None])).sum(1)
+        G = torch.zeros(n, 9, dtype=torch.float64)
+        for j in range(6):
+            G[:, j].index_add_(0, k_t, M * dalpha[j].abs())
+        for ch in range(3):
+            G[:, 6 + ch].index_add_(0, k_t, gabs[:, ch] * Tv * alpha)
+        screen = [pr[nm] for nm in names] + [o] + [pr["rgb"][:, ch] for ch in range(3)]
+        for j, s in enumerate(screen):
+            if float(G[:, j].abs().max()) == 0.0:
+                continue
+            gr = torch.autograd.grad(s.sum(), _param_keys_of(p), retain_graph=True, allow_unused=True)
+            for key, g in zip(PARAM_KEYS, gr):
+                if g is not None:
+                    out[key] += (g.abs() * G[:, j]).numpy()  # the splat index is the last axis
+    return out

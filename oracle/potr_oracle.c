@@ -405,24 +405,28 @@ static void merge_sort_pairs(uint64_t* key, uint32_t* val, uint32_t* idx, int64_
  * with key (tile_base + ty * tiles_x + tx) << 32 | bits(depth_k) and value val_base + k,
  * then sorts stably by key.  emit_index[pos] is the emission index of the instance now at
  * sorted position pos.  Returns the number of instances M, or -M when M > capacity
- * (outputs untouched).
+ * (outputs untouched).  With whole_rect = 0 only the tiles passing the tile test are
+ * emitted (touched[k] of them); with whole_rect != 0 every tile of the 3-sigma rectangle
+ * of every projected splat is, as the paper's renderer bins a footprint (no tile test).
  */
 int64_t orc_bin(int64_t n, const uint32_t* touched, const int32_t* rect, const float* depth,
                 const float* mean2d, const float* qcoef, const float* opacity, const orc_config* cfg,
                 int32_t tiles_x, uint64_t tile_base, uint32_t val_base, int64_t capacity,
-                uint64_t* keys, uint32_t* vals, uint32_t* emit_index) {
+                uint64_t* keys, uint32_t* vals, uint32_t* emit_index, int32_t whole_rect) {
   int64_t m = 0;
-  for (int64_t k = 0; k < n; ++k) m += touched[k];
+  for (int64_t k = 0; k < n; ++k)
+    m += whole_rect ? (int64_t)(rect[2 * n + k] - rect[k]) * (rect[3 * n + k] - rect[n + k]) : (int64_t)touched[k];
   if (m > capacity) return -m;
   int64_t e = 0;
   for (int64_t k = 0; k < n; ++k) {
-    if (touched[k] == 0) continue;
+    if (!whole_rect && touched[k] == 0) continue;
     uint32_t dbits;
     memcpy(&dbits, &depth[k], 4);
     const int64_t area = (int64_t)(rect[2 * n + k] - rect[k]) * (rect[3 * n + k] - rect[n + k]);
     for (int32_t ty = rect[n + k]; ty < rect[3 * n + k]; ++ty)
       for (int32_t tx = rect[k]; tx < rect[2 * n + k]; ++tx) {
-        if (!tile_kept(area, mean2d[k], mean2d[n + k], qcoef[k], qcoef[n + k], qcoef[2 * n + k], opacity[k], tx, ty, cfg))
+        if (!whole_rect &&
+            !tile_kept(area, mean2d[k], mean2d[n + k], qcoef[k], qcoef[n + k], qcoef[2 * n + k], opacity[k], tx, ty, cfg))
           continue;
         uint64_t tile = tile_base + (uint64_t)ty * (uint64_t)tiles_x + (uint64_t)tx;
         keys[e] = (tile << 32) | (uint64_t)dbits;

@@ -109,3 +109,76 @@ def assert_close_abs_rel(got, want, rel, atol, what=""):
         i = np.argmax(np.abs(got - want) - tol)
         raise AssertionError(f"{what}: {bad.sum()} of {bad.size} outside tolerance; worst at {i}"
                              f" got {got.flat[i]!r} want {want.flat[i]!r}")
+
+
+def check_against_whole_rect(fr, res, scene, cams, cfg, views, targets=None, act=None):
+    """The device's (tile-culled) lists of the given views against the paper's plain footprint
+    binning -- every tile of each splat's 3-sigma rectangle, no tile test -- as the oracle bins
+    with its tile test switched off:
+
+      * each tile's device list is an order-preserving subsequence of the whole-rectangle list;
+      * it holds every (tile, splat) pair that the oracle's per-pixel walk of the
+        whole-rectangle lists composites;
+      * the device image equals the oracle's whole-rectangle render (image tolerance), the final
+        transmittance bit for bit, and each pixel's last composited splat (n_last mapped through
+        its list) is the same splat;
+      * with targets, the per-view removal effects dSSE_k(v) equal the oracle's from the
+        whole-rectangle lists (removal-effect tolerance).
+    Returns the number of (tile, splat) pairs the culling dropped."""
+    ocfg = oracle_cfg(cfg)
+    n = scene.n
+    if act is None:
+        act = oracle.activate(scene)
+    m = fr.instance_count()
+    dvals = fr.vals[:m].cpu().numpy().view(np.uint32).astype(np.int64)
+    dranges = fr.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+    dropped = 0
+    for v in views:
+        cam = cams[v]
+        tw, th = cfg["tile_w"], cfg["tile_h"]
+        tx, ty = oracle.tiles_of(cam, ocfg)
+        pv = oracle.project(scene, act[0], cam, ocfg, act[1])
+        pv["opacity"] = act[1]
+        _, wv, _, wr = oracle.bin_sort(pv, cam, ocfg, whole_rect=True)
+        wr = wr.astype(np.int64)
+        tb = int(fr.info_np[v]["tile_base"])
+        # (tile, splat) keys of both binnings, in list order
+        wt = np.repeat(np.arange(tx * ty), wr[:, 1] - wr[:, 0])
+        wkey = wt * n + wv.astype(np.int64)
+        dr = dranges[tb:tb + tx * ty]
+        dlen = np.maximum(dr[:, 1] - dr[:, 0], 0)
+        didx = np.concatenate([np.arange(dr[t, 0], dr[t, 1]) for t in range(tx * ty) if dlen[t] > 0]
+                              or [np.zeros(0, np.int64)])
+        dt = np.repeat(np.arange(tx * ty), dlen)
+        dk = dvals[didx] - v * n
+        assert np.all((dk >= 0) & (dk < n)), f"view {v}: values outside the view"
+        dkey = dt * n + dk
+        order = np.argsort(wkey, kind="stable")
+        at = np.searchsorted(wkey[order], dkey)
+        assert np.all(at < wkey.size) and np.array_equal(wkey[order][np.minimum(at, wkey.size - 1)], dkey), \
+            f"view {v}: a device pair is not in the whole-rectangle binning"
+        wpos = order[at]  # position of each device pair in the whole-rectangle sorted list
+        same = dt[1:] == dt[:-1]
+        assert np.all(np.diff(wpos)[same] > 0), f"view {v}: device order differs from the whole-rectangle order"
+        dropped += int(wkey.size - dkey.size)
+        # every composited (tile, splat) pair of the whole-rectangle walk is in the device lists
+        pix, ck, cpos = oracle.pixel_lists(pv, wv, wr.astype(np.uint32), cam, ocfg)
+        ctile = (pix // cam.width) // th * tx + (pix % cam.width) // tw
+        ckey = np.unique(ctile * n + ck.astype(np.int64))
+        assert np.all(np.isin(ckey, dkey)), f"view {v}: a composited pair was culled"
+        # render: image, T_final and the last composited splat of every pixel
+        img, t32, t64, nl = oracle.render(pv, wv, wr.astype(np.uint32), cam, ocfg)
+        assert_close_rel(view_slice(fr, res["image"], v), img, 1e-5, 1e-3, f"image view {v} (whole rectangles)")
+        assert np.array_equal(view_slice(fr, res["t_final"], v, 1).view(np.uint32), t32.view(np.uint32))
+        gnl = view_slice(fr, res["n_last"], v, 1).astype(np.int64)
+        ys, xs = np.mgrid[0:cam.height, 0:cam.width]
+        tile = (ys // th) * tx + xs // tw
+        gl = np.where(gnl > 0, dvals[np.clip(dr[tile, 0] + gnl - 1, 0, max(m - 1, 0))] - v * n, -1)
+        wl = np.where(nl > 0, wv.astype(np.int64)[np.clip(wr[tile, 0] + nl.astype(np.int64) - 1, 0,
+                                                          max(wv.size - 1, 0))], -1)
+        assert np.array_equal(gl, wl), f"view {v}: last composited splat differs"
+        if targets is not None:
+            d, i = oracle.removal_effect(pv, wv, wr.astype(np.uint32), cam, ocfg, targets[v])
+            assert_close_abs_rel(res["dsse_view"][v * n:(v + 1) * n], d, 1e-4, 1e-7,
+                                 f"dSSE view {v} (whole rectangles)")
+    return dropped

@@ -196,6 +196,13 @@ MUT += [
     ("g_qnorm", GR, "q = p[\"quats\"] / torch.linalg.norm(p[\"quats\"], dim=0, keepdim=True)", "q = p[\"quats\"]"),
     ("g_amax", GR, "alpha = torch.clamp(o[k_t] * torch.exp(power), max=float(cfg.alpha_max))", "alpha = o[k_t] * torch.exp(power)"),
     ("adam_v", AD, "v += (1.0 - b2) * g * g", "v += (1.0 - b2) * abs(g)"),
+    # the gradient magnitude bound
+    ("gm_suffix_sign", GR, "(Tv[:, None] * rgb_e + s_after / (1.0 - alpha)[:, None])",
+     "(Tv[:, None] * rgb_e - s_after / (1.0 - alpha)[:, None])"),
+    ("gm_suffix_drop", GR, "s_after / (1.0 - alpha)[:, None])", "0.0 * s_after)"),
+    ("gm_colour_T", GR, "gabs[:, ch] * Tv * alpha", "gabs[:, ch] * alpha"),
+    ("gm_jac_abs", GR, "out[key] += (g.abs() * G[:, j]).numpy()", "out[key] += (g * G[:, j]).numpy()"),
+    ("gm_resid_abs", GR, "gabs = gc.abs()[:, pix_t].T", "gabs = gc[:, pix_t].T"),
 ]
 
 

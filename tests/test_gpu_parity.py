@@ -13,8 +13,8 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import (assert_close_abs_rel, assert_close_rel, build_frame, frame_outputs, oracle_cfg,
-                      pack_targets, unpack_raster, view_slice)
+from gpu_util import (assert_close_abs_rel, assert_close_rel, build_frame, check_against_whole_rect, frame_outputs,
+                      oracle_cfg, pack_targets, unpack_raster, view_slice)
 
 pytestmark = pytest.mark.gpu
 
@@ -216,6 +216,26 @@ def test_mixed_views_every_tile_shape(tile):
     _check_binning(fr, ovs)
     _check_render(fr, sc, cams, cfg, ovs, res)
     _check_removal(fr, sc, cams, cfg, ovs, res, tg)
+
+
+def test_culled_lists_against_whole_rectangle_binning_tiny(tiny, tiny_run):
+    """The device's tile lists against the paper's footprint binning (every 3-sigma rectangle
+    tile, the oracle's tile test off): order-preserving subsequences holding every composited
+    pair, with the same image, transmittance, last composited splat and removal effects."""
+    fr, tg, res, act, ovs = tiny_run
+    dropped = check_against_whole_rect(fr, res, tiny.scene, tiny.cameras, CFG16, [0], tg, act)
+    assert dropped > 0.1 * fr.instance_count()
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 32), (32, 8)])
+def test_culled_lists_against_whole_rectangle_binning_mixed(tile):
+    sc, cams = mixed_workload()
+    cfg = dict(tile_w=tile[0], tile_h=tile[1], batch=128)
+    fr = build_frame(sc, cams, **cfg)
+    tg = _tiny_targets(sc, cams, cfg, 4244)
+    res = frame_outputs(fr, pack_targets(fr, tg))
+    dropped = check_against_whole_rect(fr, res, sc, cams, cfg, range(len(cams)), tg)
+    assert dropped > 0
 
 
 def test_coincident_splats_keep_emission_order():

@@ -11,8 +11,8 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import (assert_close_abs_rel, assert_close_rel, build_frame, frame_outputs, oracle_cfg, unpack_raster,
-                      view_slice)
+from gpu_util import (assert_close_abs_rel, assert_close_rel, build_frame, check_against_whole_rect, frame_outputs,
+                      oracle_cfg, unpack_raster, view_slice)
 
 pytestmark = pytest.mark.gpu
 
@@ -113,3 +113,14 @@ def test_fullsize_sampled_tiles(big):
         assert_close_abs_rel(res["inst_dse"][slots], idse[sel], 1e-4, 1e-7, f"tile partials view {v}")
         assert_close_abs_rel(res["inst_imp"][slots], iimp[sel], 1e-4, 1e-7, f"tile importance view {v}")
         assert np.count_nonzero(idse[sel]) > 1000
+
+
+def test_fullsize_culled_lists_against_whole_rectangle_binning(big):
+    """Views 0 and 11 of the frame: every tile's device list is an order-preserving subsequence
+    of the paper's footprint binning (all 3-sigma rectangle tiles, computed by the oracle with its
+    tile test off) and holds every pair the oracle's walk of those lists composites; image,
+    transmittance, last composited splat and per-view removal effects equal the oracle's from the
+    whole-rectangle lists."""
+    w, fr, tg, res, r, tiles, vals, touched = big
+    dropped = check_against_whole_rect(fr, res, w.scene, w.cameras, CFG, VIEWS, tg)
+    assert dropped > 0.2 * fr.instance_count() * len(VIEWS) / len(w.cameras)

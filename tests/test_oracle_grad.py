@@ -156,3 +156,69 @@ def test_binary64_forward_matches_c_oracle_at_the_clamps():
     assert np.max(np.abs(img - img2)) > 0.05  # the splats beyond the clamp show in the image
     _, _, imgs = G.loss_and_grad(sc, [cam], cfg, [np.zeros_like(img)])
     assert np.max(np.abs(imgs[0] - img)) < 1e-5
+
+
+# ------------------------------------------------------------------------------------------
+# the per-element magnitude bound used as the device gradients' rounding scale
+# ------------------------------------------------------------------------------------------
+
+def test_gradient_magnitude_bounds_every_gradient_element():
+    """B_p (sum over entries of magnitudes, loss_grad_magnitude) is at least |dL/dp| for every
+    element, for the squared-error loss and at lambda = 0.2, and is reached with equality by some
+    elements (a sum of terms of one sign)."""
+    sc = synth.uniform_cube_scene(200, 88)
+    cam = synth.look_at_camera((0.0, 0.3, -3.0), 64, 64)
+    cfg = oracle.make_config()
+    v = oracle.prepare_view(sc, cam, cfg)
+    img, *_ = oracle.render(v, v["vals"], v["ranges"], cam, cfg)
+    tg = [(img + synth.target_noise(img.shape, 0.02, 3, 0)).astype(np.float32)]
+    for lam in (1.0, 0.2):
+        _, g, _ = G.loss_and_grad(sc, [cam], cfg, tg, lam=lam)
+        B = G.loss_grad_magnitude(sc, [cam], cfg, tg, lam=lam)
+        for k in G.PARAM_KEYS:
+            assert np.all(B[k] >= np.abs(g[k]) * (1.0 - 1e-12)), k
+            assert np.count_nonzero(B[k]) > 0.5 * B[k].size, k
+        # an SH coefficient of a splat seen in one view gets its gradient only through the colour
+        assert np.max(np.abs(g["sh"]) / np.maximum(B["sh"], 1e-300)) > 1.0 - 1e-9
+
+
+def _two_splats_one_pixel():
+    """A 1 x 1 image and two splats on the optical axis (front at z = 2, back at z = 3) wide
+    enough that the pixel centre sees both at their peaks (G = 1, alpha = o)."""
+    cam = synth.look_at_camera((0.0, 0.0, -3.0), 1, 1)
+    means = np.array([[0.0, 0.0], [0.0, 0.0], [-1.0, 0.0]], np.float32)
+    sh = np.zeros((16, 3, 2), np.float32)
+    sh[0, :, 0] = [0.9, 0.2, -0.3]
+    sh[0, :, 1] = [-0.1, 0.6, 0.4]
+    sc = synth.Scene(means, np.full((3, 2), -1.0, np.float32), np.array([[1.0, 1.0], [0, 0], [0, 0], [0, 0]], np.float32),
+                     np.array([0.3, -0.2], np.float32), sh)
+    return sc, cam
+
+
+def test_gradient_magnitude_closed_form_two_splats():
+    """Two splats composited at one pixel (front 0, back 1, alpha_i = o_i, T_0 = 1, T_1 = 1 - a0,
+    c = a0 c0 + (1 - a0) a1 c1, g = dL/dc = 2 (c - c_t) / 3):
+      dL/dlogit_0 = a0 (1 - o0) sum_ch g (c0 - a1 c1)   and its bound  a0 (1 - o0) sum_ch |g| (c0 + a1 c1),
+      dL/dlogit_1 = a1 (1 - o1) (1 - a0) sum_ch g c1     bound the same in |g|,
+      dL/dDC_0,ch = g_ch a0 Y_0                          bound |g_ch| a0 Y_0.
+    The suffix of the front splat's alpha adjoint enters the bound with a plus sign."""
+    sc, cam = _two_splats_one_pixel()
+    cfg = oracle.make_config()
+    tg = [np.full((3, 1, 1), 0.2, np.float32)]
+    _, g, imgs = G.loss_and_grad(sc, [cam], cfg, tg, lam=1.0)
+    B = G.loss_grad_magnitude(sc, [cam], cfg, tg, lam=1.0)
+    o = 1.0 / (1.0 + np.exp(-sc.opacity_logits.astype(np.float64)))
+    a0, a1 = o
+    Y0 = 0.5 / np.sqrt(np.pi)
+    c0 = np.maximum(sc.sh[0, :, 0].astype(np.float64) * Y0 + 0.5, 0.0)
+    c1 = np.maximum(sc.sh[0, :, 1].astype(np.float64) * Y0 + 0.5, 0.0)
+    c = a0 * c0 + (1.0 - a0) * a1 * c1
+    assert np.allclose(imgs[0].reshape(3), c, rtol=1e-6)
+    gc = 2.0 * (c - 0.2) / 3.0
+    assert g["opacity_logits"][0] == pytest.approx(a0 * (1 - a0) * np.sum(gc * (c0 - a1 * c1)), rel=1e-6)
+    assert B["opacity_logits"][0] == pytest.approx(a0 * (1 - a0) * np.sum(np.abs(gc) * (c0 + a1 * c1)), rel=1e-6)
+    want1 = a1 * (1 - a1) * (1 - a0) * np.sum(np.abs(gc) * c1)
+    assert B["opacity_logits"][1] == pytest.approx(want1, rel=1e-6)
+    assert abs(g["opacity_logits"][1]) == pytest.approx(want1, rel=1e-6)
+    assert np.allclose(B["sh"][0, :, 0], np.abs(gc) * a0 * Y0, rtol=1e-6)
+    assert np.allclose(np.abs(g["sh"][0, :, 0]), B["sh"][0, :, 0], rtol=1e-9)

@@ -445,6 +445,27 @@ def test_culled_binning_renders_and_removes_like_whole_rectangles(tiny):
     assert np.count_nonzero(da) > 500
 
 
+def test_whole_rectangle_binning_against_numpy_enumeration(tiny):
+    """The oracle's binning with the tile test switched off (whole_rect) equals the numpy
+    enumeration of every 3-sigma rectangle tile stably sorted by (tile, depth bits), for the
+    three tile shapes; it holds the culled binning's lists as order-preserving subsequences."""
+    sc, cam = tiny.scene, tiny.cameras[0]
+    for tw, th in [(16, 16), (8, 32), (32, 8)]:
+        cfg = oracle.make_config(tile_w=tw, tile_h=th)
+        v = oracle.prepare_view(sc, cam, cfg)
+        keys, vals, emit, ranges = oracle.bin_sort(v, cam, cfg, whole_rect=True)
+        fv, fr = _full_rect_lists(v, cam, cfg)
+        assert np.array_equal(vals, fv)
+        empty = fr[:, 1] == fr[:, 0]  # the oracle writes (0, 0) for an empty tile
+        assert np.array_equal(ranges[~empty], fr[~empty]) and np.all(ranges[empty] == 0)
+        assert vals.size > 1.2 * v["vals"].size
+        for t in range(ranges.shape[0]):
+            whole = list(vals[ranges[t, 0]:ranges[t, 1]])
+            culled = list(v["vals"][v["ranges"][t, 0]:v["ranges"][t, 1]])
+            it = iter(whole)
+            assert all(k in it for k in culled)  # subsequence test: consumes `it` in order
+
+
 def test_depth_bits_order_matches_numeric_order():
     d = np.sort(np.random.default_rng(1).uniform(0.2, 1e4, 100_000).astype(np.float32))
     assert np.all(np.diff(d.view(np.uint32).astype(np.int64)) >= 0)
