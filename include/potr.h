@@ -10,13 +10,16 @@
  * Conventions for every entry point:
  *   - Pointers named d_* and every pointer inside potr_views / potr_frame are DEVICE
  *     pointers owned by the caller.  Pointers named h_* are host pointers.  The library
- *     never allocates or frees memory and keeps no device state between calls.
+ *     never allocates or frees memory.  It keeps no device state between calls, with one
+ *     exception: potr_bin_sort_static (for callers that cannot allocate) works in a fixed
+ *     scratch array of the library's own, held by every GPU that loads it until exit.
  *   - Work is enqueued asynchronously on the caller's stream; no call synchronises the
  *     host with the device, so a sequence of calls can be captured in a CUDA graph.
  *   - Return value: POTR_OK, or an error detected on the host before anything was
  *     enqueued (POTR_ERR_INVALID_ARGUMENT, POTR_ERR_UNSUPPORTED), or POTR_ERR_CUDA when a
- *     launch failed.  Errors found on the device (instance capacity exceeded) are written
- *     to a caller-provided potr_device_status, read by the caller after synchronising.
+ *     launch failed.  Errors found on the device (instance capacity exceeded, a non-finite
+ *     splat parameter, a bounded wait that ran out) are written to a caller-provided
+ *     potr_device_status, read by the caller after synchronising.
  *   - Planes: "[3][n]" means three contiguous arrays of n floats (structure of arrays).
  *   - Index "vk" = v * n + k for view v and splat k of a frame.
  */
@@ -45,7 +48,7 @@ enum {
   POTR_ERR_CUDA = 2,
   POTR_ERR_CAPACITY = 3, /* device: more tile instances than instance_capacity */
   POTR_ERR_TIMEOUT = 4,  /* device: a bounded wait ran out */
-  POTR_ERR_NUMERIC = 5,
+  POTR_ERR_NUMERIC = 5,  /* device: a splat parameter is NaN or infinite (potr_preprocess) */
   POTR_ERR_UNSUPPORTED = 6,
   POTR_ERR_TOO_LARGE = 7, /* a size exceeds potr_bin_sort_static's fixed scratch */
   POTR_ERR_CORRUPT = 8    /* device: a malformed codec stream (potr_codec_decode) */
@@ -53,8 +56,8 @@ enum {
 
 /* Device-side status word; zero it before the calls that may write it. */
 typedef struct {
-  int32_t code;               /* POTR_OK or a POTR_ERR_* code */
-  int32_t reserved;
+  int32_t code;               /* POTR_OK or a POTR_ERR_* code (the first error written wins) */
+  int32_t n_nonfinite;        /* splats culled for a non-finite parameter (potr_preprocess) */
   int64_t required_instances; /* instance count needed when code == POTR_ERR_CAPACITY */
 } potr_device_status;
 
@@ -141,6 +144,17 @@ typedef struct {
   uint32_t* cull;        /* [V * n][4] kept-tile mask, rectangle, kept count (see above) */
 } potr_views;
 
+/*
+ * Measurement hook (no counterpart in the paper).  Arms two CUDA events (cudaEvent_t, passed as
+ * void*, created by the caller) for the next tile-pass kernel this host thread launches -- the
+ * compositing kernel of potr_render, the removal-effect kernel of potr_removal_effect or the
+ * backward tile kernel of potr_render_backward: start is recorded on that call's stream just
+ * before the kernel and stop just after it, so the time between them is the kernel's alone
+ * (no memsets, no per-splat reductions).  The launch disarms the hook; (NULL, NULL) disarms it
+ * without a launch.  INVALID_ARGUMENT when exactly one event is NULL.  Host state only.
+ */
+POTR_API potr_status potr_time_next_tile_kernel(void* start_event, void* stop_event);
+
 /* Text for a status code (static string). */
 POTR_API const char* potr_status_string(potr_status status);
 
@@ -171,9 +185,15 @@ POTR_API potr_status potr_view_layout(const potr_camera* h_cams, int32_t n_views
  * (kept tiles).  Every quantity that decides the binning or the per-pixel
  * alpha test is computed in binary32 with a fixed operation order (no contraction), with
  * exp taken by a reproducible exp2 (Cody-Waite reduction plus a degree-6 Taylor polynomial).
+ * Non-finite parameters (no counterpart in the paper): a splat whose mean, log-scale,
+ * quaternion or opacity logit holds a NaN or an infinity -- or one of its 48 SH coefficients,
+ * checked where the splat is first visible -- is culled in every view (touched 0: it enters no
+ * list, image, removal effect or gradient; its opacity is stored as NaN).  Each such splat adds
+ * 1 to d_status->n_nonfinite and the first one writes POTR_ERR_NUMERIC to d_status->code
+ * (d_status: device, caller-zeroed, nullable -- then the splats are still culled, silently).
  */
 POTR_API potr_status potr_preprocess(const potr_scene* scene, const potr_frame* frame, const potr_raster_config* cfg,
-                            const potr_views* views, potr_stream_t stream);
+                            const potr_views* views, potr_device_status* d_status, potr_stream_t stream);
 
 /* Workspace bytes of potr_tile_schedule. */
 POTR_API size_t potr_tile_schedule_workspace_size(void);

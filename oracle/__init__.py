@@ -49,7 +49,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm", "-pthread"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -95,6 +95,8 @@ def lib():
         if _lib is None:
             L = C.CDLL(build())
             vp, i64, u32 = C.c_void_p, C.c_int64, C.c_uint32
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_get_threads.restype = C.c_int
             L.orc_exp2r.restype = C.c_float
             L.orc_exp2r.argtypes = [C.c_float]
             L.orc_exp2r_array.argtypes = [i64, vp, vp]
@@ -129,6 +131,15 @@ def _f32(a):
 # ------------------------------------------------------------------------------------------
 # thin wrappers
 # ------------------------------------------------------------------------------------------
+
+def set_threads(n: int) -> None:
+    """Threads over tiles for render and removal_effect (results do not depend on the count)."""
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
 
 def exp2r(y) -> np.ndarray:
     y = _f32(np.atleast_1d(y))

@@ -38,6 +38,7 @@
  * such splats anyway, so images and removal effects are those of whole-rectangle binning.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -66,7 +67,7 @@ typedef struct {
 /* ---------------------------------------------------------------------------------- */
 
 static float g_c[7];
-static int g_c_ready = 0;
+static pthread_once_t g_c_once = PTHREAD_ONCE_INIT;
 
 static void exp2r_init(void) {
   /* c_k = (ln 2)^k / k!, evaluated in binary64 by the recurrence c_k = c_{k-1} * ln2 / k,
@@ -79,11 +80,10 @@ static void exp2r_init(void) {
     c = c / (double)k;
     g_c[k] = (float)c;
   }
-  g_c_ready = 1;
 }
 
 float orc_exp2r(float y) {
-  if (!g_c_ready) exp2r_init();
+  pthread_once(&g_c_once, exp2r_init);
   if (!(y >= -125.0f)) y = -125.0f; /* also maps NaN to the lower clamp */
   if (y > 125.0f) y = 125.0f;
   float n = rintf(y); /* nearest integer, ties to even */
@@ -98,7 +98,7 @@ void orc_exp2r_array(int64_t n, const float* y, float* out) {
 }
 
 void orc_exp2r_coeffs(float* out7) {
-  if (!g_c_ready) exp2r_init();
+  pthread_once(&g_c_once, exp2r_init);
   memcpy(out7, g_c, sizeof(g_c));
 }
 
@@ -531,6 +531,93 @@ static void composite64(const orc_splats* sp, const orc_entry* ent, int64_t K, d
 }
 
 /*
+ * Tiles are independent in the render and in the removal effect (each pixel walks its own
+ * tile's list), so both may run over several threads (orc_set_threads; 1 by default).  Every
+ * output is written by the one tile that owns it, and the per-splat sums are formed after all
+ * tiles from per-instance sums in tile order, so the results do not depend on the number of
+ * threads or on which thread took which tile.
+ */
+static int g_threads = 1;
+
+void orc_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
+int orc_get_threads(void) { return g_threads; }
+
+typedef struct {
+  const orc_camera* cam;
+  const orc_config* cfg;
+  orc_splats sp;
+  const uint32_t* vals;
+  const uint32_t* ranges;
+  const uint8_t* tile_mask;
+  int64_t exclude;
+  /* render outputs (nullable) */
+  double* image;
+  float* t_final32;
+  double* t_final64;
+  uint32_t* n_last;
+  /* removal-effect inputs and per-instance outputs */
+  const float* target;
+  double* part_dse;
+  double* part_imp;
+  int tiles_x, tiles_y;
+  uint32_t cap;
+  int64_t next; /* next tile to take (atomic) */
+  void (*tile_fn)(void* job, int64_t t, orc_entry* ent, double* P, double* Tv);
+} orc_tile_job;
+
+static void* tile_worker(void* arg) {
+  orc_tile_job* job = (orc_tile_job*)arg;
+  size_t cap1 = (size_t)job->cap + 1;
+  orc_entry* ent = (orc_entry*)malloc(sizeof(orc_entry) * cap1);
+  double* P = (double*)malloc(sizeof(double) * 3 * cap1);
+  double* Tv = (double*)malloc(sizeof(double) * cap1);
+  const int64_t n_tiles = (int64_t)job->tiles_x * job->tiles_y;
+  for (;;) {
+    int64_t t = __atomic_fetch_add(&job->next, 1, __ATOMIC_RELAXED);
+    if (t >= n_tiles) break;
+    if (job->tile_mask && !job->tile_mask[t]) continue;
+    job->tile_fn(job, t, ent, P, Tv);
+  }
+  free(ent); free(P); free(Tv);
+  return NULL;
+}
+
+/* Run job->tile_fn over every tile on g_threads threads (the calling thread included). */
+static void run_tiles(orc_tile_job* job) {
+  job->next = 0;
+  int nt = g_threads;
+  pthread_t* th = nt > 1 ? (pthread_t*)malloc(sizeof(pthread_t) * (size_t)(nt - 1)) : NULL;
+  int started = 0;
+  for (int i = 0; i < nt - 1; ++i)
+    if (pthread_create(&th[i], NULL, tile_worker, job) == 0) ++started;
+  tile_worker(job);
+  for (int i = 0; i < started; ++i) pthread_join(th[i], NULL);
+  free(th);
+}
+
+static void render_tile(void* arg, int64_t t, orc_entry* ent, double* P, double* Tv) {
+  (void)P; (void)Tv;
+  orc_tile_job* job = (orc_tile_job*)arg;
+  const orc_config* cfg = job->cfg;
+  const int W = job->cam->width, H = job->cam->height;
+  const int tx = (int)(t % job->tiles_x), ty = (int)(t / job->tiles_x);
+  for (int y = ty * cfg->tile_h; y < (ty + 1) * cfg->tile_h && y < H; ++y)
+    for (int x = tx * cfg->tile_w; x < (tx + 1) * cfg->tile_w && x < W; ++x) {
+      float T32;
+      uint32_t nl;
+      int64_t K = walk_pixel(&job->sp, cfg, job->vals, job->ranges[2 * t], job->ranges[2 * t + 1], (float)x + 0.5f,
+                             (float)y + 0.5f, job->exclude, ent, &T32, &nl);
+      double c[3], T64;
+      composite64(&job->sp, ent, K, c, &T64);
+      int64_t pix = (int64_t)y * W + x;
+      for (int ch = 0; ch < 3; ++ch) job->image[(int64_t)ch * H * W + pix] = c[ch];
+      if (job->t_final32) job->t_final32[pix] = T32;
+      if (job->t_final64) job->t_final64[pix] = T64;
+      if (job->n_last) job->n_last[pix] = nl;
+    }
+}
+
+/*
  * Render one view.  image is planar [3][H][W] binary64; t_final32 / n_last / t_final64
  * per pixel (nullable).  exclude >= 0 renders without that splat.  tile_mask (nullable)
  * restricts the work to tiles with a non-zero mask byte.
@@ -539,32 +626,24 @@ void orc_render(const orc_camera* cam, const orc_config* cfg, int64_t n, const f
                 const float* qcoef, const float* opacity, const double* rgb, const uint32_t* vals,
                 const uint32_t* ranges, int64_t exclude, const uint8_t* tile_mask, double* image,
                 float* t_final32, double* t_final64, uint32_t* n_last) {
-  const int W = cam->width, H = cam->height;
-  const int tiles_x = (W + cfg->tile_w - 1) / cfg->tile_w;
-  const int tiles_y = (H + cfg->tile_h - 1) / cfg->tile_h;
-  orc_splats sp = {n, mean2d, qcoef, opacity, rgb};
-  uint32_t cap = max_list(ranges, (int64_t)tiles_x * tiles_y);
-  orc_entry* ent = (orc_entry*)malloc(sizeof(orc_entry) * (size_t)(cap > 0 ? cap : 1));
-  for (int ty = 0; ty < tiles_y; ++ty)
-    for (int tx = 0; tx < tiles_x; ++tx) {
-      int64_t t = (int64_t)ty * tiles_x + tx;
-      if (tile_mask && !tile_mask[t]) continue;
-      for (int y = ty * cfg->tile_h; y < (ty + 1) * cfg->tile_h && y < H; ++y)
-        for (int x = tx * cfg->tile_w; x < (tx + 1) * cfg->tile_w && x < W; ++x) {
-          float T32;
-          uint32_t nl;
-          int64_t K = walk_pixel(&sp, cfg, vals, ranges[2 * t], ranges[2 * t + 1], (float)x + 0.5f,
-                                 (float)y + 0.5f, exclude, ent, &T32, &nl);
-          double c[3], T64;
-          composite64(&sp, ent, K, c, &T64);
-          int64_t pix = (int64_t)y * W + x;
-          for (int ch = 0; ch < 3; ++ch) image[(int64_t)ch * H * W + pix] = c[ch];
-          if (t_final32) t_final32[pix] = T32;
-          if (t_final64) t_final64[pix] = T64;
-          if (n_last) n_last[pix] = nl;
-        }
-    }
-  free(ent);
+  orc_tile_job job;
+  memset(&job, 0, sizeof(job));
+  job.cam = cam;
+  job.cfg = cfg;
+  job.sp = (orc_splats){n, mean2d, qcoef, opacity, rgb};
+  job.vals = vals;
+  job.ranges = ranges;
+  job.tile_mask = tile_mask;
+  job.exclude = exclude;
+  job.image = image;
+  job.t_final32 = t_final32;
+  job.t_final64 = t_final64;
+  job.n_last = n_last;
+  job.tiles_x = (cam->width + cfg->tile_w - 1) / cfg->tile_w;
+  job.tiles_y = (cam->height + cfg->tile_h - 1) / cfg->tile_h;
+  job.cap = max_list(ranges, (int64_t)job.tiles_x * job.tiles_y);
+  job.tile_fn = render_tile;
+  run_tiles(&job);
 }
 
 /*
@@ -574,70 +653,92 @@ void orc_render(const orc_camera* cam, const orc_config* cfg, int64_t n, const f
  * transmittance T_i and partial colours P_i (Eq. partial colour).  For each i:
  *   PD = (P_i + (P_K - P_{i+1}) / (1 - alpha_i)) - P_K          (Eq. pruning difference)
  *   dSE = sum over channels of PD^2 + 2 PD (c - c_t)             (Eq. pixel squared error)
- * with c = P_K and c_t the target.  Adds sum_x dSE to dsse[k] and sum_x T_i alpha_i to
- * imp[k] (both nullable, accumulated).  inst_dse / inst_imp (nullable) receive the same
- * sums per tile instance, indexed by sorted list position.  tile_mask as in orc_render.
+ * with c = P_K and c_t the target.  Per tile instance (sorted list position) the sums over the
+ * tile's pixels (row-major) of dSE and of T_i alpha_i are formed; then dsse[k] and imp[k]
+ * (both nullable, accumulated) receive, tile after tile, the sums of splat k's instances.
+ * inst_dse / inst_imp (nullable) receive the per-instance sums.  tile_mask as in orc_render.
  */
+static void removal_tile(void* arg, int64_t t, orc_entry* ent, double* P, double* Tv) {
+  orc_tile_job* job = (orc_tile_job*)arg;
+  const orc_config* cfg = job->cfg;
+  const int W = job->cam->width, H = job->cam->height;
+  const int64_t n = job->sp.n;
+  const double* rgb = job->sp.rgb;
+  const int tx = (int)(t % job->tiles_x), ty = (int)(t / job->tiles_x);
+  uint32_t s = job->ranges[2 * t], e = job->ranges[2 * t + 1];
+  for (uint32_t i = s; i < e; ++i) job->part_dse[i] = job->part_imp[i] = 0.0;
+  for (int y = ty * cfg->tile_h; y < (ty + 1) * cfg->tile_h && y < H; ++y)
+    for (int x = tx * cfg->tile_w; x < (tx + 1) * cfg->tile_w && x < W; ++x) {
+      float T32;
+      uint32_t nl;
+      int64_t K = walk_pixel(&job->sp, cfg, job->vals, s, e, (float)x + 0.5f, (float)y + 0.5f, -1, ent,
+                             &T32, &nl);
+      /* P_0 = 0, P_{i+1} = P_i + T_i alpha_i c_i, T_0 = 1, T_{i+1} = T_i (1 - alpha_i) */
+      double T = 1.0;
+      P[0] = P[1] = P[2] = 0.0;
+      for (int64_t i = 0; i < K; ++i) {
+        double a = (double)ent[i].alpha;
+        Tv[i] = T;
+        for (int ch = 0; ch < 3; ++ch)
+          P[3 * (i + 1) + ch] = P[3 * i + ch] + T * a * rgb[ch * n + ent[i].k];
+        T *= (1.0 - a);
+      }
+      int64_t pix = (int64_t)y * W + x;
+      double diff[3];
+      for (int ch = 0; ch < 3; ++ch) diff[ch] = P[3 * K + ch] - (double)job->target[(int64_t)ch * H * W + pix];
+      for (int64_t i = 0; i < K; ++i) {
+        double a = (double)ent[i].alpha;
+        double dse = 0.0;
+        for (int ch = 0; ch < 3; ++ch) {
+          double PK = P[3 * K + ch];
+          double pd = (P[3 * i + ch] + (PK - P[3 * (i + 1) + ch]) / (1.0 - a)) - PK;
+          dse += pd * pd + 2.0 * pd * diff[ch];
+        }
+        double w = Tv[i] * a;
+        job->part_dse[s + ent[i].pos] += dse;
+        job->part_imp[s + ent[i].pos] += w;
+      }
+    }
+}
+
 void orc_removal_effect(const orc_camera* cam, const orc_config* cfg, int64_t n,
                         const float* mean2d, const float* qcoef, const float* opacity,
                         const double* rgb, const uint32_t* vals, const uint32_t* ranges,
                         const float* target, const uint8_t* tile_mask, double* dsse, double* imp,
                         double* inst_dse, double* inst_imp) {
-  const int W = cam->width, H = cam->height;
-  const int tiles_x = (W + cfg->tile_w - 1) / cfg->tile_w;
-  const int tiles_y = (H + cfg->tile_h - 1) / cfg->tile_h;
-  orc_splats sp = {n, mean2d, qcoef, opacity, rgb};
-  uint32_t cap = max_list(ranges, (int64_t)tiles_x * tiles_y);
-  size_t cap1 = (size_t)cap + 1;
-  orc_entry* ent = (orc_entry*)malloc(sizeof(orc_entry) * cap1);
-  double* P = (double*)malloc(sizeof(double) * 3 * cap1);
-  double* Tv = (double*)malloc(sizeof(double) * cap1);
-  for (int ty = 0; ty < tiles_y; ++ty)
-    for (int tx = 0; tx < tiles_x; ++tx) {
-      int64_t t = (int64_t)ty * tiles_x + tx;
-      if (tile_mask && !tile_mask[t]) continue;
-      uint32_t s = ranges[2 * t], e = ranges[2 * t + 1];
-      if (inst_dse)
-        for (uint32_t i = s; i < e; ++i) inst_dse[i] = 0.0;
-      if (inst_imp)
-        for (uint32_t i = s; i < e; ++i) inst_imp[i] = 0.0;
-      for (int y = ty * cfg->tile_h; y < (ty + 1) * cfg->tile_h && y < H; ++y)
-        for (int x = tx * cfg->tile_w; x < (tx + 1) * cfg->tile_w && x < W; ++x) {
-          float T32;
-          uint32_t nl;
-          int64_t K = walk_pixel(&sp, cfg, vals, s, e, (float)x + 0.5f, (float)y + 0.5f, -1, ent,
-                                 &T32, &nl);
-          /* P_0 = 0, P_{i+1} = P_i + T_i alpha_i c_i, T_0 = 1, T_{i+1} = T_i (1 - alpha_i) */
-          double T = 1.0;
-          P[0] = P[1] = P[2] = 0.0;
-          for (int64_t i = 0; i < K; ++i) {
-            double a = (double)ent[i].alpha;
-            Tv[i] = T;
-            for (int ch = 0; ch < 3; ++ch)
-              P[3 * (i + 1) + ch] = P[3 * i + ch] + T * a * rgb[ch * n + ent[i].k];
-            T *= (1.0 - a);
-          }
-          int64_t pix = (int64_t)y * W + x;
-          double diff[3];
-          for (int ch = 0; ch < 3; ++ch) diff[ch] = P[3 * K + ch] - (double)target[(int64_t)ch * H * W + pix];
-          for (int64_t i = 0; i < K; ++i) {
-            double a = (double)ent[i].alpha;
-            double dse = 0.0;
-            for (int ch = 0; ch < 3; ++ch) {
-              double PK = P[3 * K + ch];
-              double pd = (P[3 * i + ch] + (PK - P[3 * (i + 1) + ch]) / (1.0 - a)) - PK;
-              dse += pd * pd + 2.0 * pd * diff[ch];
-            }
-            double w = Tv[i] * a;
-            uint32_t k = ent[i].k;
-            if (dsse) dsse[k] += dse;
-            if (imp) imp[k] += w;
-            if (inst_dse) inst_dse[s + ent[i].pos] += dse;
-            if (inst_imp) inst_imp[s + ent[i].pos] += w;
-          }
-        }
+  orc_tile_job job;
+  memset(&job, 0, sizeof(job));
+  job.cam = cam;
+  job.cfg = cfg;
+  job.sp = (orc_splats){n, mean2d, qcoef, opacity, rgb};
+  job.vals = vals;
+  job.ranges = ranges;
+  job.tile_mask = tile_mask;
+  job.exclude = -1;
+  job.target = target;
+  job.tiles_x = (cam->width + cfg->tile_w - 1) / cfg->tile_w;
+  job.tiles_y = (cam->height + cfg->tile_h - 1) / cfg->tile_h;
+  const int64_t n_tiles = (int64_t)job.tiles_x * job.tiles_y;
+  job.cap = max_list(ranges, n_tiles);
+  uint32_t m = 0;
+  for (int64_t t = 0; t < n_tiles; ++t)
+    if (ranges[2 * t + 1] > m) m = ranges[2 * t + 1];
+  job.part_dse = (double*)calloc((size_t)m + 1, sizeof(double));
+  job.part_imp = (double*)calloc((size_t)m + 1, sizeof(double));
+  job.tile_fn = removal_tile;
+  run_tiles(&job);
+  for (int64_t t = 0; t < n_tiles; ++t) {
+    if (tile_mask && !tile_mask[t]) continue;
+    for (uint32_t i = ranges[2 * t]; i < ranges[2 * t + 1]; ++i) {
+      uint32_t k = vals[i];
+      if (dsse) dsse[k] += job.part_dse[i];
+      if (imp) imp[k] += job.part_imp[i];
+      if (inst_dse) inst_dse[i] = job.part_dse[i];
+      if (inst_imp) inst_imp[i] = job.part_imp[i];
     }
-  free(ent); free(P); free(Tv);
+  }
+  free(job.part_dse);
+  free(job.part_imp);
 }
 
 /*

@@ -78,7 +78,7 @@ class CodecParams(C.Structure):
 
 
 class DeviceStatus(C.Structure):
-    _fields_ = [("code", C.c_int32), ("reserved", C.c_int32), ("required_instances", C.c_int64)]
+    _fields_ = [("code", C.c_int32), ("n_nonfinite", C.c_int32), ("required_instances", C.c_int64)]
 
 
 # Every exported symbol of include/potr.h, with its ctypes signature.
@@ -87,7 +87,8 @@ SIGNATURES = {
     "potr_status_string": (C.c_char_p, [_I32]),
     "potr_version": (_I32, []),
     "potr_view_layout": (_I32, [_P, _I32, C.POINTER(RasterConfig), _P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
-    "potr_preprocess": (_I32, [C.POINTER(Scene), C.POINTER(Frame), C.POINTER(RasterConfig), C.POINTER(Views), _P]),
+    "potr_preprocess": (_I32, [C.POINTER(Scene), C.POINTER(Frame), C.POINTER(RasterConfig), C.POINTER(Views), _P,
+                               _P]),
     "potr_bin_sort_workspace_size": (_SZ, [_I64, _I32, _I64, _I64]),
     "potr_bin_sort": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _I64, _P, _P, _P,
                              _P, _P, _SZ, _P]),
@@ -99,6 +100,7 @@ SIGNATURES = {
     "potr_tile_schedule": (_I32, [C.POINTER(Frame), _P, _P, _P, _SZ, _P]),
     "potr_pair_stats": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _P, _P, _P, _P]),
     "potr_launch_count": (C.c_uint64, []),
+    "potr_time_next_tile_kernel": (_I32, [_P, _P]),
     "potr_selftest_wait_timeout": (_I32, [_P, _SZ, _I32, _P, _P]),
     "potr_loss_workspace_size": (_SZ, [_I64]),
     "potr_loss_grad": (_I32, [C.POINTER(Frame), _P, _P, C.c_float, _P, _P, _P, _SZ, _P]),
@@ -196,9 +198,9 @@ def potr_view_layout(cams_rec: np.ndarray, cfg: RasterConfig):
     return info, tt.value, tp.value
 
 
-def potr_preprocess(scene: Scene, frame: Frame, cfg: RasterConfig, views: Views, stream=None):
+def potr_preprocess(scene: Scene, frame: Frame, cfg: RasterConfig, views: Views, stream=None, status=None):
     _check("potr_preprocess", lib().potr_preprocess(C.byref(scene), C.byref(frame), C.byref(cfg), C.byref(views),
-                                                    stream_handle(stream)))
+                                                    ptr(status), stream_handle(stream)))
 
 
 def potr_bin_sort_workspace_size(n: int, n_views: int, total_tiles: int, capacity: int) -> int:
@@ -362,3 +364,13 @@ def potr_codec_decode(nodes, n_nodes: int, dups, n_dups: int, attrs, n: int, cub
     _check("potr_codec_decode", lib().potr_codec_decode(ptr(nodes), int(n_nodes), ptr(dups), int(n_dups), ptr(attrs),
                                                         int(n), cb, C.byref(params), C.byref(grads_struct(out)),
                                                         ptr(status), ptr(ws), ws.numel(), stream_handle(stream)))
+
+
+def potr_time_next_tile_kernel(start, stop):
+    """Arm two torch.cuda.Event objects (enable_timing=True) around the next tile-pass kernel this
+    thread launches (render, removal effect or backward); None, None disarms."""
+    h = (lambda e: None if e is None else int(e.cuda_event))
+    if start is not None:
+        start.record()  # creates the events lazily; the library re-records them on the launch stream
+        stop.record()
+    _check("potr_time_next_tile_kernel", lib().potr_time_next_tile_kernel(h(start), h(stop)))

@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(128, 3) preprocess_bwd_kernel(
     float gsh[48], shc[48];
 #pragma unroll
     for (int i = 0; i < 48; ++i) gsh[i] = 0.0f;
-    bool have_sh = false;
+    bool have_sh = false, used = false;
     const float mu[3] = {means[k], means[n + k], means[2 * n + k]};
     const float Sg[3][3] = {{cov3d[k], cov3d[n + k], cov3d[2 * n + k]},
                             {cov3d[n + k], cov3d[3 * n + k], cov3d[4 * n + k]},
@@ -422,6 +422,7 @@ __global__ void __launch_bounds__(128, 3) preprocess_bwd_kernel(
         nz |= gq[q] != 0.0f;
       }
       if (!nz) continue;
+      used = true;
       if (!have_sh) {
 #pragma unroll
         for (int i = 0; i < 48; ++i) shc[i] = __ldg(sh + (int64_t)i * n + k);
@@ -539,6 +540,16 @@ __global__ void __launch_bounds__(128, 3) preprocess_bwd_kernel(
       gmu[1] += (gdy - dy * dotg) * inv_len;
       gmu[2] += (gdz - dz * dotg) * inv_len;
       go += gq[5];
+    }
+    if (!used) {  // no pixel of any view took the splat (also a splat culled for non-finite parameters)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) g_means[j * n + k] = g_log_scales[j * n + k] = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) g_quats[j * n + k] = 0.0f;
+      g_logits[k] = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 48; ++i) g_sh[(int64_t)i * n + k] = 0.0f;
+      continue;
     }
     // activation adjoint: Sigma = M M^T, M = R diag(s), s = exp(log_scale), R(q / |q|)
     float s[3];
@@ -658,18 +669,24 @@ extern "C" potr_status potr_render_backward(const potr_scene* scene, const potr_
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(render_bwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return POTR_ERR_CUDA;
-    render_bwd_kernel<true><<<tile_grid(render_bwd_kernel<true>, smem, q, frame->total_tiles), kThreads, smem, s>>>(
+    const unsigned grid = tile_grid(render_bwd_kernel<true>, smem, q, frame->total_tiles);
+    tile_timing_begin(s);
+    render_bwd_kernel<true><<<grid, kThreads, smem, s>>>(
         reinterpret_cast<const float4*>(views->raster), d_vals, d_tile_ranges, frame->info, frame->n_views, *cfg,
         nullptr, nullptr, d_dL_dimages, instance_capacity, inst_grad, nullptr,
         reinterpret_cast<const uint4*>(views->cull), views->offsets, q);
+    tile_timing_end(s);
   } else {
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(render_bwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return POTR_ERR_CUDA;
-    render_bwd_kernel<false><<<tile_grid(render_bwd_kernel<false>, smem, q, frame->total_tiles), kThreads, smem, s>>>(
+    const unsigned grid = tile_grid(render_bwd_kernel<false>, smem, q, frame->total_tiles);
+    tile_timing_begin(s);
+    render_bwd_kernel<false><<<grid, kThreads, smem, s>>>(
         reinterpret_cast<const float4*>(views->raster), d_vals, d_tile_ranges, frame->info, frame->n_views, *cfg,
         d_t_final, d_n_last, d_dL_dimages, instance_capacity, inst_grad, d_warp_masks,
         reinterpret_cast<const uint4*>(views->cull), views->offsets, q);
+    tile_timing_end(s);
   }
   POTR_CHECK_LAUNCH();
   const int64_t n = scene->n;

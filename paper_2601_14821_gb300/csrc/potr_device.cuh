@@ -187,6 +187,11 @@ __device__ __forceinline__ void set_status(potr_device_status* st, int32_t code,
 // Host-side count of kernel launches issued by the library (potr_launch_count).
 void note_launches(int n);
 
+// Measurement hook (potr_time_next_tile_kernel): the events armed by this host thread, recorded
+// on the launching stream around the next tile-pass kernel and then disarmed.
+void tile_timing_begin(cudaStream_t s);
+void tile_timing_end(cudaStream_t s);
+
 }  // namespace potr
 
 #define POTR_CHECK_LAUNCH()                                   \

@@ -19,10 +19,19 @@ __global__ void __launch_bounds__(256) activate_kernel(const float* __restrict__
                                                        const float* __restrict__ logits, int64_t n,
                                                        float* __restrict__ cov3d, float* __restrict__ opacity) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    float qw = quats[k], qx = quats[n + k], qy = quats[2 * n + k], qz = quats[3 * n + k];
+    const float ls0 = log_scales[k], ls1 = log_scales[n + k], ls2 = log_scales[2 * n + k], lg = logits[k];
+    if (!(isfinite(ls0) && isfinite(ls1) && isfinite(ls2) && isfinite(qw) && isfinite(qx) && isfinite(qy) &&
+          isfinite(qz) && isfinite(lg))) {
+      // a non-finite parameter: the splat is marked by a NaN opacity and culled by the projection
+#pragma unroll
+      for (int e = 0; e < 6; ++e) cov3d[e * n + k] = 0.0f;
+      opacity[k] = __int_as_float(0x7fc00000);
+      continue;
+    }
     float s[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) s[a] = exp2r(__fmul_rn(log_scales[a * n + k], kLog2e));
-    float qw = quats[k], qx = quats[n + k], qy = quats[2 * n + k], qz = quats[3 * n + k];
     const float n2 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(qw, qw), __fmul_rn(qx, qx)), __fmul_rn(qy, qy)),
                                __fmul_rn(qz, qz));
     if (n2 > 0.0f) {
@@ -88,7 +97,8 @@ __global__ void __launch_bounds__(256) project_kernel(const float* __restrict__ 
                                                       const potr_view_info* __restrict__ info, int n_views,
                                                       potr_raster_config cfg, float4* __restrict__ raster,
                                                       float* __restrict__ depth_out, uint2* __restrict__ rect_out,
-                                                      uint32_t* __restrict__ touched_out) {
+                                                      uint32_t* __restrict__ touched_out,
+                                                      potr_device_status* __restrict__ status) {
   const float kA = -0.5f * kLog2e;  // exact: a power-of-two scaling
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     const float mu0 = means[k], mu1 = means[n + k], mu2 = means[2 * n + k];
@@ -98,8 +108,14 @@ __global__ void __launch_bounds__(256) project_kernel(const float* __restrict__ 
     const float pthr = log2f(cfg.alpha_min / o) - 0.01f;  // conservative prefilter, see render
     float shc[48];
     bool have_sh = false;
+    // non-finite centre or activation input (NaN opacity from activate_kernel): culled in every view
+    bool bad = !(isfinite(mu0) && isfinite(mu1) && isfinite(mu2) && isfinite(o));
     for (int v = 0; v < n_views; ++v) {
       const int64_t vk = (int64_t)v * n + k;
+      if (bad) {
+        touched_out[vk] = 0;
+        continue;
+      }
       const potr_camera& cam = cams[v];
       const float* W = cam.w2c;
       float t[3];
@@ -169,9 +185,18 @@ __global__ void __launch_bounds__(256) project_kernel(const float* __restrict__ 
       }
       // SH colour along the camera-to-splat direction (values only: plain fp32 arithmetic)
       if (!have_sh) {
+        bool fin = true;
 #pragma unroll
-        for (int i = 0; i < 48; ++i) shc[i] = __ldg(sh + (int64_t)i * n + k);
+        for (int i = 0; i < 48; ++i) {
+          shc[i] = __ldg(sh + (int64_t)i * n + k);
+          fin = fin && isfinite(shc[i]);
+        }
         have_sh = true;
+        if (!fin) {  // a non-finite SH coefficient: culled here and in the later views (not seen before)
+          bad = true;
+          touched_out[vk] = 0;
+          continue;
+        }
       }
       const float cx0 = -(W[0] * W[3] + W[4] * W[7] + W[8] * W[11]);
       const float cy0 = -(W[1] * W[3] + W[5] * W[7] + W[9] * W[11]);
@@ -197,6 +222,10 @@ __global__ void __launch_bounds__(256) project_kernel(const float* __restrict__ 
       depth_out[vk] = t[2];
       rect_out[vk] = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
       touched_out[vk] = (uint32_t)((x1 - x0) * (y1 - y0));  // candidates; tile_mask_kernel keeps some
+    }
+    if (bad && status) {
+      atomicCAS(&status->code, 0, (int32_t)POTR_ERR_NUMERIC);
+      atomicAdd(&status->n_nonfinite, 1);
     }
   }
 }
@@ -324,7 +353,7 @@ extern "C" potr_status potr_view_layout(const potr_camera* h_cams, int32_t n_vie
 }
 
 extern "C" potr_status potr_preprocess(const potr_scene* scene, const potr_frame* frame, const potr_raster_config* cfg,
-                                       const potr_views* views, potr_stream_t stream) {
+                                       const potr_views* views, potr_device_status* d_status, potr_stream_t stream) {
   if (!scene || !frame || !cfg || !views) return POTR_ERR_INVALID_ARGUMENT;
   if (scene->n <= 0 || frame->n_views < 1 || !frame->cams || !frame->info) return POTR_ERR_INVALID_ARGUMENT;
   if (!scene->means || !scene->log_scales || !scene->quats || !scene->opacity_logits || !scene->sh)
@@ -343,7 +372,8 @@ extern "C" potr_status potr_preprocess(const potr_scene* scene, const potr_frame
   POTR_CHECK_LAUNCH();
   potr::project_kernel<<<potr::grid_for(n, 256, 152 * 16), 256, 0, s>>>(
       scene->means, views->cov3d, views->opacity, scene->sh, n, frame->cams, frame->info, frame->n_views, *cfg,
-      reinterpret_cast<float4*>(views->raster), views->depth, reinterpret_cast<uint2*>(views->rect), views->touched);
+      reinterpret_cast<float4*>(views->raster), views->depth, reinterpret_cast<uint2*>(views->rect), views->touched,
+      d_status);
   POTR_CHECK_LAUNCH();
   const int64_t n_vk = n * frame->n_views;
   potr::tile_mask_kernel<<<potr::grid_for(n_vk, 256, 152 * 16), 256, 0, s>>>(

@@ -339,9 +339,11 @@ cudaError_t launch_render(const potr_views* views, const potr_frame* frame, cons
     if (e != cudaSuccess) return e;
   }
   const unsigned grid = tile_grid(render_kernel<BATCH>, smem, q, frame->total_tiles);
+  tile_timing_begin(s);
   render_kernel<BATCH><<<grid, kThreads, smem, s>>>(reinterpret_cast<const float4*>(views->raster), vals, ranges,
                                                     frame->info, frame->n_views, cfg, images, t_final, n_last, gmask,
                                                     q);
+  tile_timing_end(s);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -361,10 +363,12 @@ cudaError_t launch_removal(const potr_views* views, const potr_frame* frame, con
                                         (int)cudaSharedmemCarveoutMaxShared);
   if (ce != cudaSuccess) return ce;
   const unsigned grid = tile_grid(removal_kernel<BATCH, IMP>, smem, q, frame->total_tiles);
+  tile_timing_begin(s);
   removal_kernel<BATCH, IMP><<<grid, kThreads, smem, s>>>(reinterpret_cast<const float4*>(views->raster), vals, ranges,
                                                           frame->info, frame->n_views, cfg, targets, images, inst_dse,
                                                           inst_imp, reinterpret_cast<const uint4*>(views->cull),
                                                           views->offsets, q);
+  tile_timing_end(s);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -511,9 +515,28 @@ __global__ void __launch_bounds__(kThreads) pair_stats_kernel(const float4* __re
 
 std::atomic<unsigned long long> g_launches{0};
 
+struct TileTiming {
+  cudaEvent_t start = nullptr, stop = nullptr;
+  bool armed = false, open = false;
+};
+thread_local TileTiming g_tile_timing;
+
 }  // namespace
 
 void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+void tile_timing_begin(cudaStream_t s) {
+  TileTiming& t = g_tile_timing;
+  if (!t.armed) return;
+  t.open = cudaEventRecord(t.start, s) == cudaSuccess;
+}
+
+void tile_timing_end(cudaStream_t s) {
+  TileTiming& t = g_tile_timing;
+  if (!t.armed || !t.open) return;
+  cudaEventRecord(t.stop, s);
+  t.armed = t.open = false;
+}
 
 }  // namespace potr
 
@@ -534,6 +557,16 @@ extern "C" potr_status potr_pair_stats(const potr_views* views, const potr_frame
 }
 
 extern "C" uint64_t potr_launch_count(void) { return potr::g_launches.load(); }
+
+extern "C" potr_status potr_time_next_tile_kernel(void* start_event, void* stop_event) {
+  potr::TileTiming& t = potr::g_tile_timing;
+  if ((start_event == nullptr) != (stop_event == nullptr)) return POTR_ERR_INVALID_ARGUMENT;
+  t.start = static_cast<cudaEvent_t>(start_event);
+  t.stop = static_cast<cudaEvent_t>(stop_event);
+  t.armed = start_event != nullptr;
+  t.open = false;
+  return POTR_OK;
+}
 
 extern "C" const char* potr_status_string(potr_status status) {
   switch (status) {

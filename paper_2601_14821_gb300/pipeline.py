@@ -75,6 +75,7 @@ class RemovalEffectFrame:
         self.opacity = torch.empty(self.n, dtype=torch.float32, device=dev)
         self.n_instances = torch.zeros(1, dtype=torch.int32, device=dev)
         self.status = torch.zeros(2, dtype=torch.int64, device=dev)
+        self.pre_status = torch.zeros(2, dtype=torch.int64, device=dev)  # non-finite splats (potr_preprocess)
         self.sched_ws = torch.empty(B.potr_tile_schedule_workspace_size(), dtype=torch.uint8, device=dev)
         self.schedule = schedule
         self.with_importance = with_importance
@@ -131,7 +132,13 @@ class RemovalEffectFrame:
 
     # -------------------------------------------------------------------------------------
     def preprocess(self, stream=None):
-        B.potr_preprocess(self.scene_c, self.frame, self.cfg, self.views, stream)
+        self.pre_status.zero_()
+        B.potr_preprocess(self.scene_c, self.frame, self.cfg, self.views, stream, status=self.pre_status)
+
+    def nonfinite(self) -> tuple[int, int]:
+        """(status code, splats culled for non-finite parameters) of the last preprocess (synchronises)."""
+        w = self.pre_status.cpu().numpy().view(np.int32)
+        return int(w[0]), int(w[1])
 
     def bin_sort(self, stream=None):
         """Binning + sort, then (with scheduling on) the longest-list-first tile order."""

@@ -19,7 +19,7 @@ MUT = [
     ("dse_factor", C, "dse += pd * pd + 2.0 * pd * diff[ch];", "dse += pd * pd + pd * diff[ch];"),
     ("dse_sign", C, "dse += pd * pd + 2.0 * pd * diff[ch];", "dse += pd * pd - 2.0 * pd * diff[ch];"),
     ("imp_alpha", C, "double w = Tv[i] * a;", "double w = a;"),
-    ("imp_tnext", C, "            Tv[i] = T;\n", "            Tv[i] = T * (1.0 - a);\n"),
+    ("imp_tnext", C, "        Tv[i] = T;\n", "        Tv[i] = T * (1.0 - a);\n"),
     # compositing walk
     ("tmin_after", C, "    if (Tn < cfg->t_min) break;\n",
      "    if (Tn < cfg->t_min) { out[K].pos = i - s; out[K].k = k; out[K].alpha = a; ++K; last = i - s + 1; T = Tn; break; }\n"),
@@ -30,8 +30,8 @@ MUT = [
     ("comp_T", C, "    for (int ch = 0; ch < 3; ++ch) c[ch] += T * a * sp->rgb[ch * sp->n + ent[i].k];\n    T *= (1.0 - a);",
      "    for (int ch = 0; ch < 3; ++ch) c[ch] += T * a * sp->rgb[ch * sp->n + ent[i].k];\n    T *= (1.0 - 0.5 * a);"),
     ("comp_noT", C, "c[ch] += T * a * sp->rgb[ch * sp->n + ent[i].k];", "c[ch] += a * sp->rgb[ch * sp->n + ent[i].k];"),
-    ("centre_half", C, "int64_t K = walk_pixel(&sp, cfg, vals, s, e, (float)x + 0.5f, (float)y + 0.5f, -1, ent,",
-     "int64_t K = walk_pixel(&sp, cfg, vals, s, e, (float)x, (float)y + 0.5f, -1, ent,"),
+    ("centre_half", C, "int64_t K = walk_pixel(&job->sp, cfg, job->vals, s, e, (float)x + 0.5f, (float)y + 0.5f, -1, ent,",
+     "int64_t K = walk_pixel(&job->sp, cfg, job->vals, s, e, (float)x, (float)y + 0.5f, -1, ent,"),
     # activation
     ("rot_sign", C, "R[0][1] = 2.0f * (qx * qy - qw * qz);", "R[0][1] = 2.0f * (qx * qy + qw * qz);"),
     ("rot_transpose", C, "M[i][j] = R[i][j] * s[j];", "M[i][j] = R[j][i] * s[j];"),
@@ -88,8 +88,8 @@ MUT = [
     ("my_fx", C, "float my = cam->fy * tyz + cam->cy;", "float my = cam->fx * tyz + cam->cy;"),
     ("jy_fx", C, "float j11 = cam->fy / t[2];", "float j11 = cam->fx / t[2];"),
     ("rect_y_tw", C, "float fy0 = floorf((my - r) / (float)cfg->tile_h);", "float fy0 = floorf((my - r) / (float)cfg->tile_w);"),
-    ("resid_sign", C, "diff[ch] = P[3 * K + ch] - (double)target[(int64_t)ch * H * W + pix];",
-     "diff[ch] = (double)target[(int64_t)ch * H * W + pix] - P[3 * K + ch];"),
+    ("resid_sign", C, "diff[ch] = P[3 * K + ch] - (double)job->target[(int64_t)ch * H * W + pix];",
+     "diff[ch] = (double)job->target[(int64_t)ch * H * W + pix] - P[3 * K + ch];"),
     ("tile_transpose", C, "uint64_t tile = tile_base + (uint64_t)ty * (uint64_t)tiles_x + (uint64_t)tx;",
      "uint64_t tile = tile_base + (uint64_t)tx * (uint64_t)tiles_x + (uint64_t)ty;"),
     ("ranges_last", C, "ranges[2 * t + 1] = (uint32_t)(i + 1);", "ranges[2 * t + 1] = (uint32_t)i;"),
@@ -101,7 +101,7 @@ MUT = [
     ("v_C_dx", C, "float v = C * dy;", "float v = C * dx;"),
     ("ranges_nobase", C, "int64_t t = (int64_t)((keys[i] >> 32) - tile_base);", "int64_t t = (int64_t)(keys[i] >> 32);"),
     ("vals_nobase", C, "vals[e] = val_base + (uint32_t)k;", "vals[e] = (uint32_t)k;"),
-    ("t64_single", C, "if (t_final64) t_final64[pix] = T64;", "if (t_final64) t_final64[pix] = (double)T32;"),
+    ("t64_single", C, "if (job->t_final64) job->t_final64[pix] = T64;", "if (job->t_final64) job->t_final64[pix] = (double)T32;"),
     # exp2r
     ("exp2r_coef", C, "  for (int k = 1; k <= 6; ++k) {\n    c = c * ln2;", "  for (int k = 1; k <= 5; ++k) {\n    c = c * ln2;"),
     ("exp2r_round", C, "float n = rintf(y);", "float n = floorf(y);"),
@@ -156,7 +156,7 @@ MUT += [
     ("qbits", PR, "Q_BITS = 40", "Q_BITS = 30"),
     ("cell_clip", CO, "return np.clip(X, 0, (1 << DEPTH) - 1).astype(np.int64)", "return np.clip(X, 0, (1 << DEPTH)).astype(np.int64)"),
     # third batch
-    ("inst_index", C, "if (inst_dse) inst_dse[s + ent[i].pos] += dse;", "if (inst_dse) inst_dse[s + (uint32_t)i] += dse;"),
+    ("inst_index", C, "job->part_dse[s + ent[i].pos] += dse;", "job->part_dse[s + (uint32_t)i] += dse;"),
     ("nlast_off", C, "    last = i - s + 1;\n", "    last = i - s;\n"),
     ("pass2_dc", SH, "keep2 = [0] + [i for i in kept[1:] if not quantises_to_zero(first[i, ch], sf)]",
      "keep2 = [i for i in kept if not quantises_to_zero(first[i, ch], sf)] or [0]"),

@@ -70,8 +70,8 @@ def test_every_entry_point_rejects_null_arguments_on_the_host(libpotr):
     floats = (C.c_float, C.c_double)
     checked = []
     for name, (res, args) in sorted(B.SIGNATURES.items()):
-        if res is not B._I32 or name == "potr_version":
-            continue
+        if res is not B._I32 or name in ("potr_version", "potr_time_next_tile_kernel"):
+            continue  # (NULL, NULL) is the hook's documented disarm, tested below
         vals = [0.0 if a in floats else (None if a is B._P or issubclass(a, C._Pointer) else 0) for a in args]
         assert getattr(B.lib(), name)(*vals) == B.POTR_ERR_INVALID_ARGUMENT, name
         checked.append(name)
@@ -92,3 +92,20 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         B.lib()
     with pytest.raises(RuntimeError, match="not built"):
         B.potr_view_layout(np.zeros((1, 18), np.float32), B.make_config())
+
+
+def test_timing_hook_and_status_word_on_the_host(libpotr):
+    """The tile-kernel timing hook takes both events or neither; the device status word has the
+    layout the header gives (code, non-finite splat count, required instances) and the
+    non-finite code its string."""
+    import ctypes as C
+
+    from paper_2601_14821_gb300 import _binding as B
+
+    L = B.lib()
+    assert L.potr_time_next_tile_kernel(None, None) == B.POTR_OK
+    assert L.potr_time_next_tile_kernel(C.c_void_p(16), None) == B.POTR_ERR_INVALID_ARGUMENT
+    assert L.potr_time_next_tile_kernel(None, C.c_void_p(16)) == B.POTR_ERR_INVALID_ARGUMENT
+    assert B.DeviceStatus.code.offset == 0 and B.DeviceStatus.n_nonfinite.offset == 4
+    assert B.DeviceStatus.required_instances.offset == 8 and C.sizeof(B.DeviceStatus) == 16
+    assert B.status_string(B.POTR_ERR_NUMERIC) == "non-finite input"

@@ -1,12 +1,20 @@
 """GPU backward (potr_loss_grad + potr_render_backward, and the autograd bridge) against the
 binary64 autograd gradient oracle (oracle/grad.py).
 
-Gradient tolerance, per parameter group: |gpu - oracle| <= 1e-3 |oracle| + 1e-4 max|oracle|.
-The GPU accumulates per-pixel terms in binary32 over tiles and views (relative rounding
-~1e-6 per term, amplified where terms of opposite sign cancel); the second term is the
-norm-wise floor for gradients that cancel to near zero.  The parity runs use the squared-error
-loss (lambda = 1): the L1 term's subgradient flips sign where |c - c_t| is below the 1e-5
-image tolerance, which is not a gradient error.
+Gradient tolerance, per parameter element p:
+    |gpu - oracle| <= 1e-4 |oracle| + KAPPA 2^-24 B_p
+where B_p (oracle.grad.loss_grad_magnitude) bounds the sum over pixels and composited entries of
+the magnitudes of the terms that make up dL/dp (the alpha adjoint's two parts taken with a plus
+sign).  The device forms each term in binary32 and adds them over pixels, tiles and views in
+binary32: each term carries a relative error of a few units in the last place times the depth of
+its chain -- the transmittance T_i is recovered by dividing the final T by (1 - alpha_j) back to
+front, one rounding per composited splat behind i, and the suffix sums S_> add one rounding per
+splat -- so the error of a sum is bounded by (chain depth) 2^-24 B_p.  KAPPA = 4096 covers chains
+of up to ~2000 composited splats per pixel, far more than any test scene reaches; relative to
+B_p this is 2.4e-4, the cancellation-aware form of the 1e-4 relative target.
+The L1 term's subgradient sign(c - c_t) is discontinuous where the residual vanishes: pixels
+whose residual is within 1e-4 of zero (ten times the image tolerance) have their target moved
+to c + 1e-3 before either side runs, so both paths take the same sign; nothing else changes.
 """
 import numpy as np
 import pytest
@@ -18,17 +26,22 @@ from oracle import grad as G
 
 pytestmark = pytest.mark.gpu
 
-REL, FLOOR = 1e-3, 1e-4
+REL, KAPPA = 1e-4, 4096.0
 KEYS = ("means", "log_scales", "quats", "opacity_logits", "sh")
 
 
 def _targets(scene, cams, cfg, seed, sigma=0.02):
+    """Oracle render + N(0, sigma) noise; residuals within 1e-4 of zero moved to -1e-3 (so the
+    L1 subgradient's sign is the same on both sides)."""
     ocfg = oracle_cfg(cfg)
     out = []
     for v, cam in enumerate(cams):
         pv = oracle.prepare_view(scene, cam, ocfg)
         img, *_ = oracle.render(pv, pv["vals"], pv["ranges"], cam, ocfg)
-        out.append((img + synth.target_noise(img.shape, sigma, seed, v)).astype(np.float32))
+        tg = (img + synth.target_noise(img.shape, sigma, seed, v)).astype(np.float32)
+        near = np.abs(img - tg) < 1e-4
+        tg[near] = (img[near] + 1e-3).astype(np.float32)
+        out.append(tg)
     return out
 
 
@@ -48,33 +61,47 @@ def _gpu_grads(fr, tg_flat, lam, store=True):
     return float(loss.item()), {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}, dL, img
 
 
-def _check(got, want, what):
+def _check(got, want, mag, what):
+    """Per element: |gpu - oracle| <= REL |oracle| + KAPPA 2^-24 B (B: the oracle's magnitude
+    bound of the element's terms).  Prints the largest error relative to 2^-24 B per group."""
     msgs = []
+    eps = 2.0 ** -24
     for k in KEYS:
-        g, o = got[k].reshape(-1), want[k].reshape(-1)
-        tol = REL * np.abs(o) + FLOOR * np.abs(o).max()
-        bad = np.abs(g - o) > tol
+        g, o, b = got[k].reshape(-1), want[k].reshape(-1), mag[k].reshape(-1)
+        err = np.abs(g - o)
+        tol = REL * np.abs(o) + KAPPA * eps * b
+        bad = err > tol
+        seen = b > 0
+        worst = float(np.max(err[seen] / (eps * b[seen]))) if seen.any() else 0.0
+        print(f"{what}/{k}: max |gpu - oracle| / (2^-24 B) = {worst:.1f}; "
+              f"max rel (where |o| > 1e-3 B) = {np.max((err / np.maximum(np.abs(o), 1e-300))[np.abs(o) > 1e-3 * b], initial=0):.2e}")
+        assert np.all(np.isfinite(g)), f"{what}/{k}: non-finite gradient"
         if bad.any():
-            i = int(np.argmax(np.abs(g - o) - tol))
-            msgs.append(f"{what}/{k}: {bad.sum()} of {bad.size} outside; worst got {g[i]!r} want {o[i]!r} "
-                        f"(max|o| {np.abs(o).max():.3e}, median rel {np.median(np.abs(g - o) / (np.abs(o) + 1e-30)):.2e})")
+            i = int(np.argmax(err - tol))
+            msgs.append(f"{what}/{k}: {bad.sum()} of {bad.size} outside; worst got {g[i]!r} want {o[i]!r} B {b[i]!r}")
     assert not msgs, "\n".join(msgs)
 
 
-@pytest.mark.parametrize("case", ["tiny16", "mixed8x32"])
-def test_backward_matches_gradient_oracle(case, tiny):
+def _grad_case(case, tiny):
     if case == "tiny16":
-        scene, cams, cfg = tiny.scene, tiny.cameras, dict(tile_w=16, tile_h=16, batch=256)
-    else:
-        scene = synth.uniform_cube_scene(3000, 88)
-        cams = [synth.look_at_camera((0.0, 0.3, -3.0), 120, 90), synth.look_at_camera((2.5, -0.2, -1.5), 72, 100)]
-        cfg = dict(tile_w=8, tile_h=32, batch=128)
+        return tiny.scene, tiny.cameras, dict(tile_w=16, tile_h=16, batch=256)
+    scene = synth.uniform_cube_scene(3000, 88)
+    cams = [synth.look_at_camera((0.0, 0.3, -3.0), 120, 90), synth.look_at_camera((2.5, -0.2, -1.5), 72, 100)]
+    return scene, cams, dict(tile_w=8, tile_h=32, batch=128)
+
+
+@pytest.mark.parametrize("lam", [1.0, 0.2])
+@pytest.mark.parametrize("case", ["tiny16", "mixed8x32"])
+def test_backward_matches_gradient_oracle(case, lam, tiny):
+    """Squared-error loss (lambda = 1) and the fine-tuning loss with its L1 term (lambda = 0.2)."""
+    scene, cams, cfg = _grad_case(case, tiny)
     tg = _targets(scene, cams, cfg, 17)
     fr = build_frame(scene, cams, **cfg)
-    loss, grads, dL, img = _gpu_grads(fr, pack_targets(fr, tg), 1.0)
-    oloss, ograds, _ = G.loss_and_grad(scene, cams, oracle_cfg(cfg), tg, lam=1.0)
+    loss, grads, dL, img = _gpu_grads(fr, pack_targets(fr, tg), lam)
+    oloss, ograds, _ = G.loss_and_grad(scene, cams, oracle_cfg(cfg), tg, lam=lam)
+    mag = G.loss_grad_magnitude(scene, cams, oracle_cfg(cfg), tg, lam=lam)
     assert loss == pytest.approx(oloss, rel=1e-5)
-    _check(grads, ograds, case)
+    _check(grads, ograds, mag, f"{case} lambda {lam}")
 
 
 def test_loss_grad_kernel_against_plain_formula(tiny):
@@ -104,10 +131,12 @@ def test_backward_matches_gradient_oracle_at_the_clamps():
     cfg = dict(tile_w=16, tile_h=16, batch=256)
     tg = _targets(sc, [cam], cfg, 23)
     fr = build_frame(sc, [cam], **cfg)
-    loss, grads, _, _ = _gpu_grads(fr, pack_targets(fr, tg), 1.0)
-    oloss, ograds, _ = G.loss_and_grad(sc, [cam], oracle_cfg(cfg), tg, lam=1.0)
-    assert loss == pytest.approx(oloss, rel=1e-5)
-    _check(grads, ograds, "clamps")
+    for lam in (1.0, 0.2):
+        loss, grads, _, _ = _gpu_grads(fr, pack_targets(fr, tg), lam)
+        oloss, ograds, _ = G.loss_and_grad(sc, [cam], oracle_cfg(cfg), tg, lam=lam)
+        mag = G.loss_grad_magnitude(sc, [cam], oracle_cfg(cfg), tg, lam=lam)
+        assert loss == pytest.approx(oloss, rel=1e-5)
+        _check(grads, ograds, mag, f"clamps lambda {lam}")
 
 
 def test_zero_residual_gives_zero_gradients(tiny):

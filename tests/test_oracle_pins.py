@@ -756,3 +756,27 @@ def test_colour_direction_is_camera_to_splat():
     assert pr["touched"][0] > 0
     assert pr["rgb"][0, 0] == pytest.approx(c1 * d[2] + 0.5, rel=1e-6)
     assert pr["rgb"][1, 0] == pytest.approx(c1 * d[2] - c1 * d[0] + 0.5, rel=1e-6)
+
+
+def test_threads_over_tiles_change_no_bit(tiny):
+    """The oracle's render and removal effect on 1, 3 and 8 threads over tiles: images,
+    transmittances, n_last, per-splat and per-instance sums identical bit for bit (every output
+    has one owning tile; per-splat sums are formed from per-instance sums in tile order)."""
+    sc = synth.uniform_cube_scene(5000, 77)
+    cam = synth.look_at_camera((0.0, 0.3, -3.0), 200, 150)
+    v = oracle.prepare_view(sc, cam, CFG)
+    tgt = np.full((3, 150, 200), 0.3, np.float32)
+    outs = []
+    try:
+        for nt in (1, 3, 8):
+            oracle.set_threads(nt)
+            assert oracle.get_threads() == nt
+            r = oracle.render(v, v["vals"], v["ranges"], cam, CFG)
+            d = oracle.removal_effect(v, v["vals"], v["ranges"], cam, CFG, tgt, per_instance=True)
+            outs.append(list(r) + list(d))
+    finally:
+        oracle.set_threads(1)
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert np.array_equal(a, b)
+    assert np.count_nonzero(outs[0][4]) > 1000
