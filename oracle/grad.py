@@ -172,51 +172,126 @@ def oracle_loss(scene, cams, cfg, targets, lam: float = LAMBDA) -> tuple[float, 
     return total / n_elems, keys
 
 
-def _param_keys_of(p):
-    return [p[k] for k in PARAM_KEYS]
+def _abs_vjp(outputs, inputs, b_out):
+    """For a per-splat map out = f(in) (splat i's outputs depend on splat i's inputs only) and
+    nonnegative weights b_out [n, m]: sum_c |d out_c / d in| b_out_c, per input element.  One
+    vector-Jacobian product per output component, with a one-hot upstream over all splats."""
+    res = [torch.zeros_like(x) for x in inputs]
+    for c in range(outputs.shape[1]):
+        if float(b_out[:, c].max()) == 0.0:
+            continue
+        gr = torch.autograd.grad(outputs[:, c].sum(), inputs, retain_graph=True, allow_unused=True)
+        for r, g in zip(res, gr):
+            if g is not None:
+                r += g.abs() * b_out[:, c:c + 1]
+    return res
+
+
+def _leaf(x):
+    return x.detach().clone().requires_grad_(True)
 
 
 def loss_grad_magnitude(scene, cams, cfg, targets, lam: float = LAMBDA) -> dict:
-    """Per parameter element, a bound B_p >= sum over pixels of |that pixel's contribution to
-    dL/dp|: the scale against which a binary32 accumulation of the gradient over pixels is
-    rounded.  For each composited (pixel, splat) entry of each view:
+    """Per parameter element, a bound B_p >= |dL/dp| that also bounds every term the gradient is
+    formed from: the scale against which a binary32 evaluation of the gradient is rounded.
 
+    Per composited (pixel, splat) entry of each view:
       * the adjoint of alpha, dL/dalpha = sum_ch g_ch (T c_ch - S_>,ch / (1 - alpha)) (S_> the
-        suffix sum of T alpha c over the later entries of the pixel, g = dL/dc), is taken as the
+        suffix sum of T alpha c over the later entries of the pixel, g = dL/dc), enters as the
         sum of the magnitudes of its two parts, M = sum_ch |g_ch| (T c_ch + S_>,ch / (1 - alpha));
-      * the screen quantities s_j of the splat (centre mx, my, conic ca, cb, cc, opacity o,
-        colour r, g, b) receive M |d alpha / d s_j| (geometry, opacity) or |g_ch| T alpha (colour),
-        summed over the entries of the splat in the view;
-      * each parameter element p of splat k then gets sum_j |d s_j(k) / d p| times that sum, added
-        over views.
-    Every step replaces a sum by the sum of magnitudes, so B_p >= |dL/dp|.  Returns
-    {param: B as numpy binary64 of the parameter's shape}."""
-    p = to_params(scene)
-    sigma, o = activate(p)
+      * through alpha = o exp(power), power = -(ca dx^2 + 2 cb dx dy + cc dy^2) / 2 (no term where
+        alpha is clamped to alpha_max): the centre gets M alpha (|ca dx| + |cb dy|) and
+        M alpha (|cb dx| + |cc dy|), the conic M alpha (dx^2 / 2, |dx dy|, dy^2 / 2), the opacity
+        M exp(power); the colour |g_ch| T alpha -- summed over the splat's entries in the view.
+    Then back through the forward's elementary stages, each a per-splat map, with absolute values
+    at every stage: conic <- 2D covariance <- (Jacobian, Sigma); Jacobian and centre <- camera-
+    space mean <- mean; colour <- (SH coefficients, basis); basis <- direction <- mean;
+    Sigma <- M M^T <- (R, scales); R <- normalised quaternion <- quaternion; scale <- log-scale;
+    opacity <- logit.  Returns {param: B as numpy binary64 of the parameter's shape}."""
     n_elems = sum(3 * c.pixels for c in cams)
     act = oracle.activate(scene)
     n = scene.n
-    out = {k: np.zeros(np.shape(getattr(scene, k)), np.float64) for k in PARAM_KEYS}
-    names = ("mx", "my", "ca", "cb", "cc")
+    P = {k: torch.tensor(np.asarray(getattr(scene, k), np.float64)) for k in PARAM_KEYS}
+    # 3D stages (view independent)
+    ls = _leaf(P["log_scales"].T)                                   # [n, 3]
+    s3 = torch.exp(ls)
+    qv = _leaf(P["quats"].T)                                        # [n, 4]
+    qh = qv / torch.linalg.norm(qv, dim=1, keepdim=True)
+    qh_l = _leaf(qh)
+    w, x, y, z = qh_l[:, 0], qh_l[:, 1], qh_l[:, 2], qh_l[:, 3]
+    R = torch.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                     2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                     2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], 1)  # [n, 9]
+    R_l, s_l = _leaf(R), _leaf(s3)
+    M = (R_l.view(n, 3, 3) * s_l[:, None, :]).reshape(n, 9)
+    M_l = _leaf(M)
+    Mm = M_l.view(n, 3, 3)
+    Sg = Mm @ Mm.transpose(1, 2)
+    iu = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    Sig6 = torch.stack([Sg[:, i, j] for i, j in iu], 1)             # [n, 6]
+    lg = _leaf(P["opacity_logits"][:, None])
+    o1 = torch.sigmoid(lg)
+    o = o1[:, 0].detach()
+    B_sig = torch.zeros(n, 6, dtype=torch.float64)
+    B_o = torch.zeros(n, 1, dtype=torch.float64)
+    B_mu = torch.zeros(n, 3, dtype=torch.float64)
+    B_sh = torch.zeros(n, 48, dtype=torch.float64)
+    mu_l = _leaf(P["means"].T)                                       # [n, 3]
+    sh_l = _leaf(P["sh"].permute(2, 0, 1).reshape(n, 48))            # [n, 16 * 3], index 3 i + ch
+    sig_l = _leaf(Sig6)
     for cam, tgt in zip(cams, targets):
         v = oracle.prepare_view(scene, cam, cfg, act)
         pix, k, _ = oracle.pixel_lists(v, v["vals"], v["ranges"], cam, cfg)
-        pr = project(p, sigma, cam, cfg)
         if pix.size == 0:
             continue
+        # ---- view stages
+        w2c = torch.tensor(np.asarray(cam.w2c, np.float64).reshape(3, 4))
+        Wr, tw = w2c[:, :3], w2c[:, 3]
+        t = mu_l @ Wr.T + tw
+        t_l = _leaf(t)
+        tx, ty, tz = t_l[:, 0], t_l[:, 1], t_l[:, 2]
+        lim_x, lim_y = 1.3 * (0.5 * cam.width / cam.fx), 1.3 * (0.5 * cam.height / cam.fy)
+        xc = torch.clamp(tx / tz, -lim_x, lim_x) * tz
+        yc = torch.clamp(ty / tz, -lim_y, lim_y) * tz
+        Jm = torch.stack([cam.fx / tz, -cam.fx * xc / (tz * tz), cam.fy / tz, -cam.fy * yc / (tz * tz)], 1)
+        mxy = torch.stack([cam.fx * tx / tz + cam.cx, cam.fy * ty / tz + cam.cy], 1)
+        J_l = _leaf(Jm)
+        j00, j02, j11, j12 = J_l[:, 0], J_l[:, 1], J_l[:, 2], J_l[:, 3]
+        T0 = torch.stack([j00 * Wr[0, 0] + j02 * Wr[2, 0], j00 * Wr[0, 1] + j02 * Wr[2, 1], j00 * Wr[0, 2] + j02 * Wr[2, 2]], 1)
+        T1 = torch.stack([j11 * Wr[1, 0] + j12 * Wr[2, 0], j11 * Wr[1, 1] + j12 * Wr[2, 1], j11 * Wr[1, 2] + j12 * Wr[2, 2]], 1)
+        S = torch.zeros(n, 3, 3, dtype=torch.float64)
+        for c_, (i, j) in enumerate(iu):
+            S = S.index_put((torch.arange(n), torch.full((n,), i), torch.full((n,), j)), sig_l[:, c_])
+            if i != j:
+                S = S.index_put((torch.arange(n), torch.full((n,), j), torch.full((n,), i)), sig_l[:, c_])
+        a = torch.einsum("ni,nij,nj->n", T0, S, T0) + cfg.lowpass
+        b = torch.einsum("ni,nij,nj->n", T0, S, T1)
+        c = torch.einsum("ni,nij,nj->n", T1, S, T1) + cfg.lowpass
+        cov = torch.stack([a, b, c], 1)
+        cov_l = _leaf(cov)
+        det = cov_l[:, 0] * cov_l[:, 2] - cov_l[:, 1] * cov_l[:, 1]
+        conic = torch.stack([cov_l[:, 2] / det, -cov_l[:, 1] / det, cov_l[:, 0] / det], 1)
+        campos = -(Wr.T @ tw)
+        dvec = mu_l - campos
+        dn = dvec / torch.linalg.norm(dvec, dim=1, keepdim=True)
+        d_l = _leaf(dn)
+        Y = _sh_basis(d_l)                                           # [n, 16]
+        Y_l = _leaf(Y)
+        lin = torch.einsum("nic,ni->nc", sh_l.view(n, 16, 3), Y_l) + 0.5
+        rgb = torch.relu(lin)
+        # ---- entry magnitudes -> G [n, 9] (mx, my, ca, cb, cc, o, r, g, b)
+        pr = {"mx": mxy[:, 0].detach(), "my": mxy[:, 1].detach(), "ca": conic[:, 0].detach(),
+              "cb": conic[:, 1].detach(), "cc": conic[:, 2].detach(), "rgb": rgb.detach()}
         H, W = cam.height, cam.width
         k_t = torch.from_numpy(k.astype(np.int64))
         pix_t = torch.from_numpy(pix.astype(np.int64))
-        leaves = [pr[nm][k_t].detach().clone().requires_grad_(True) for nm in names]
-        o_e = o[k_t].detach().clone().requires_grad_(True)
-        mx, my, ca, cb, cc = leaves
-        px = (pix_t % W).to(torch.float64) + 0.5
-        py = (pix_t // W).to(torch.float64) + 0.5
-        dx, dy = px - mx, py - my
-        expo = -0.5 * (ca * dx * dx + 2.0 * cb * dx * dy + cc * dy * dy)
-        alpha = torch.clamp(o_e * torch.exp(expo), max=float(cfg.alpha_max))
-        dalpha = torch.autograd.grad(alpha.sum(), leaves + [o_e])  # per entry (each alpha has its own leaves)
-        alpha = alpha.detach()
+        dx = (pix_t % W).to(torch.float64) + 0.5 - pr["mx"][k_t]
+        dy = (pix_t // W).to(torch.float64) + 0.5 - pr["my"][k_t]
+        ca, cb, cc = pr["ca"][k_t], pr["cb"][k_t], pr["cc"][k_t]
+        G_e = torch.exp(-0.5 * (ca * dx * dx + 2.0 * cb * dx * dy + cc * dy * dy))
+        a_raw = o[k_t] * G_e
+        alpha = torch.clamp(a_raw, max=float(cfg.alpha_max))
+        free = (a_raw <= float(cfg.alpha_max)).to(torch.float64)  # no gradient through a clamped alpha
         la = torch.log1p(-alpha)
         excl = torch.cumsum(la, 0) - la
         first = np.ones(pix.size, bool)
@@ -224,30 +299,46 @@ def loss_grad_magnitude(scene, cams, cfg, targets, lam: float = LAMBDA) -> dict:
         seg = torch.from_numpy(np.cumsum(first) - 1)
         starts = torch.from_numpy(np.nonzero(first)[0])
         Tv = torch.exp(excl - excl[starts][seg])
-        rgb_e = pr["rgb"][k_t].detach()
-        contrib = (Tv * alpha)[:, None] * rgb_e  # [E, 3]
+        rgb_e = pr["rgb"][k_t]
+        contrib = (Tv * alpha)[:, None] * rgb_e
         img = torch.zeros(3, H * W, dtype=torch.float64).index_add(1, pix_t, contrib.T)
         r = img - torch.from_numpy(np.asarray(tgt, np.float64).reshape(3, -1))
-        gc = ((1.0 - lam) * torch.sign(r) + 2.0 * lam * r) / n_elems  # [3, P]
-        # suffix sums of later entries of the same pixel: segment total minus the inclusive prefix
+        gc = ((1.0 - lam) * torch.sign(r) + 2.0 * lam * r) / n_elems
         cum = torch.cumsum(contrib, 0)
         ends = torch.from_numpy(np.append(np.nonzero(first)[0][1:], pix.size) - 1)
-        seg_total = cum[ends][seg]
-        s_after = seg_total - cum
-        s_after = torch.clamp(s_after, min=0.0)  # rounding of the difference
-        gabs = gc.abs()[:, pix_t].T  # [E, 3]
-        M = (gabs * (Tv[:, None] * rgb_e + s_after / (1.0 - alpha)[:, None])).sum(1)
+        s_after = torch.clamp(cum[ends][seg] - cum, min=0.0)
+        gabs = gc.abs()[:, pix_t].T
+        Mag = (gabs * (Tv[:, None] * rgb_e + s_after / (1.0 - alpha)[:, None])).sum(1)
+        am = Mag * alpha * free
         G = torch.zeros(n, 9, dtype=torch.float64)
-        for j in range(6):
-            G[:, j].index_add_(0, k_t, M * dalpha[j].abs())
+        G[:, 0].index_add_(0, k_t, am * ((ca * dx).abs() + (cb * dy).abs()))
+        G[:, 1].index_add_(0, k_t, am * ((cb * dx).abs() + (cc * dy).abs()))
+        G[:, 2].index_add_(0, k_t, am * 0.5 * dx * dx)
+        G[:, 3].index_add_(0, k_t, am * (dx * dy).abs())
+        G[:, 4].index_add_(0, k_t, am * 0.5 * dy * dy)
+        G[:, 5].index_add_(0, k_t, Mag * G_e * free)
         for ch in range(3):
             G[:, 6 + ch].index_add_(0, k_t, gabs[:, ch] * Tv * alpha)
-        screen = [pr[nm] for nm in names] + [o] + [pr["rgb"][:, ch] for ch in range(3)]
-        for j, s in enumerate(screen):
-            if float(G[:, j].abs().max()) == 0.0:
-                continue
-            gr = torch.autograd.grad(s.sum(), _param_keys_of(p), retain_graph=True, allow_unused=True)
-            for key, g in zip(PARAM_KEYS, gr):
-                if g is not None:
-                    out[key] += (g.abs() * G[:, j]).numpy()  # the splat index is the last axis
-    return out
+        # ---- back through the view stages
+        (B_cov,) = _abs_vjp(conic, [cov_l], G[:, 2:5])
+        B_J, B_s6 = _abs_vjp(cov, [J_l, sig_l], B_cov)
+        (B_t1,) = _abs_vjp(mxy, [t_l], G[:, 0:2])
+        (B_t2,) = _abs_vjp(Jm, [t_l], B_J)
+        (B_mu1,) = _abs_vjp(t, [mu_l], B_t1 + B_t2)
+        B_sh_v, B_Y = _abs_vjp(rgb, [sh_l, Y_l], G[:, 6:9])
+        (B_d,) = _abs_vjp(Y, [d_l], B_Y)
+        (B_mu2,) = _abs_vjp(dn, [mu_l], B_d)
+        B_mu += B_mu1 + B_mu2
+        B_sh += B_sh_v
+        B_sig += B_s6
+        B_o += G[:, 5:6]
+    # ---- back through the 3D stages
+    (B_M,) = _abs_vjp(Sig6, [M_l], B_sig)
+    B_R, B_s = _abs_vjp(M, [R_l, s_l], B_M)
+    (B_qh,) = _abs_vjp(R, [qh_l], B_R)
+    (B_q,) = _abs_vjp(qh, [qv], B_qh)
+    (B_ls,) = _abs_vjp(s3, [ls], B_s)
+    (B_lg,) = _abs_vjp(o1, [lg], B_o)
+    return {"means": B_mu.T.numpy().copy(), "log_scales": B_ls.T.numpy().copy(), "quats": B_q.T.numpy().copy(),
+            "opacity_logits": B_lg[:, 0].numpy().copy(),
+            "sh": B_sh.view(n, 16, 3).permute(1, 2, 0).numpy().copy()}

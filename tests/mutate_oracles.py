@@ -201,7 +201,9 @@ MUT += [
      "(Tv[:, None] * rgb_e - s_after / (1.0 - alpha)[:, None])"),
     ("gm_suffix_drop", GR, "s_after / (1.0 - alpha)[:, None])", "0.0 * s_after)"),
     ("gm_colour_T", GR, "gabs[:, ch] * Tv * alpha", "gabs[:, ch] * alpha"),
-    ("gm_jac_abs", GR, "out[key] += (g.abs() * G[:, j]).numpy()", "out[key] += (g * G[:, j]).numpy()"),
+    ("gm_jac_abs", GR, "r += g.abs() * b_out[:, c:c + 1]", "r += g * b_out[:, c:c + 1]"),
+    ("gm_centre_cross", GR, "am * ((ca * dx).abs() + (cb * dy).abs())", "am * (ca * dx).abs()"),
+    ("gm_opacity_G", GR, "Mag * G_e * free", "Mag * free"),
     ("gm_resid_abs", GR, "gabs = gc.abs()[:, pix_t].T", "gabs = gc[:, pix_t].T"),
 ]
 
