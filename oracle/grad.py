@@ -191,6 +191,76 @@ def _leaf(x):
     return x.detach().clone().requires_grad_(True)
 
 
+def screen_magnitudes(pr: dict, cam, cfg, tgt, lam: float, n_elems: int, pix, k) -> torch.Tensor:
+    """[n, 9] per splat of one view, over its composited entries (pix, k): the magnitude sums of
+    the terms of dL/d(mx, my, ca, cb, cc, o, r, g, b) (see loss_grad_magnitude); pr holds the
+    splats' screen quantities (binary64 tensors mx, my, ca, cb, cc, o [n] and rgb [n, 3])."""
+    n = pr["mx"].shape[0]
+    H, W = cam.height, cam.width
+    k_t = torch.from_numpy(k.astype(np.int64))
+    pix_t = torch.from_numpy(pix.astype(np.int64))
+    dx = (pix_t % W).to(torch.float64) + 0.5 - pr["mx"][k_t]
+    dy = (pix_t // W).to(torch.float64) + 0.5 - pr["my"][k_t]
+    ca, cb, cc = pr["ca"][k_t], pr["cb"][k_t], pr["cc"][k_t]
+    G_e = torch.exp(-0.5 * (ca * dx * dx + 2.0 * cb * dx * dy + cc * dy * dy))
+    a_raw = pr["o"][k_t] * G_e
+    alpha = torch.clamp(a_raw, max=float(cfg.alpha_max))
+    free = (a_raw <= float(cfg.alpha_max)).to(torch.float64)  # no gradient through a clamped alpha
+    la = torch.log1p(-alpha)
+    excl = torch.cumsum(la, 0) - la
+    first = np.ones(pix.size, bool)
+    first[1:] = pix[1:] != pix[:-1]
+    seg = torch.from_numpy(np.cumsum(first) - 1)
+    starts = torch.from_numpy(np.nonzero(first)[0])
+    Tv = torch.exp(excl - excl[starts][seg])
+    rgb_e = pr["rgb"][k_t]
+    contrib = (Tv * alpha)[:, None] * rgb_e
+    img = torch.zeros(3, H * W, dtype=torch.float64).index_add(1, pix_t, contrib.T)
+    r = img - torch.from_numpy(np.asarray(tgt, np.float64).reshape(3, -1))
+    gc = ((1.0 - lam) * torch.sign(r) + 2.0 * lam * r) / n_elems
+    cum = torch.cumsum(contrib, 0)
+    ends = torch.from_numpy(np.append(np.nonzero(first)[0][1:], pix.size) - 1)
+    s_after = torch.clamp(cum[ends][seg] - cum, min=0.0)
+    gabs = gc.abs()[:, pix_t].T
+    Mag = (gabs * (Tv[:, None] * rgb_e + s_after / (1.0 - alpha)[:, None])).sum(1)
+    am = Mag * alpha * free
+    G = torch.zeros(n, 9, dtype=torch.float64)
+    G[:, 0].index_add_(0, k_t, am * ((ca * dx).abs() + (cb * dy).abs()))
+    G[:, 1].index_add_(0, k_t, am * ((cb * dx).abs() + (cc * dy).abs()))
+    G[:, 2].index_add_(0, k_t, am * 0.5 * dx * dx)
+    G[:, 3].index_add_(0, k_t, am * (dx * dy).abs())
+    G[:, 4].index_add_(0, k_t, am * 0.5 * dy * dy)
+    G[:, 5].index_add_(0, k_t, Mag * G_e * free)
+    for ch in range(3):
+        G[:, 6 + ch].index_add_(0, k_t, gabs[:, ch] * Tv * alpha)
+    return G
+
+
+def screen_grad(pr: dict, cam, cfg, tgt, lam: float, n_elems: int, pix, k) -> torch.Tensor:
+    """[n, 9] per splat of one view: dL/d(mx, my, ca, cb, cc, o, r, g, b) by autograd of the
+    compositing along the entries (pix, k) (render_view's arithmetic from screen quantities)."""
+    leaves = {key: _leaf(pr[key]) for key in ("mx", "my", "ca", "cb", "cc", "o", "rgb")}
+    H, W = cam.height, cam.width
+    k_t = torch.from_numpy(k.astype(np.int64))
+    pix_t = torch.from_numpy(pix.astype(np.int64))
+    dx = (pix_t % W).to(torch.float64) + 0.5 - leaves["mx"][k_t]
+    dy = (pix_t // W).to(torch.float64) + 0.5 - leaves["my"][k_t]
+    power = -0.5 * (leaves["ca"][k_t] * dx * dx + 2.0 * leaves["cb"][k_t] * dx * dy + leaves["cc"][k_t] * dy * dy)
+    alpha = torch.clamp(leaves["o"][k_t] * torch.exp(power), max=float(cfg.alpha_max))
+    la = torch.log1p(-alpha)
+    excl = torch.cumsum(la, 0) - la
+    first = np.ones(pix.size, bool)
+    first[1:] = pix[1:] != pix[:-1]
+    seg = torch.from_numpy(np.cumsum(first) - 1)
+    Tv = torch.exp(excl - excl[torch.from_numpy(np.nonzero(first)[0])][seg])
+    contrib = (Tv * alpha)[:, None] * leaves["rgb"][k_t]
+    img = torch.zeros(3, H * W, dtype=torch.float64).index_add(1, pix_t, contrib.T)
+    r = img - torch.from_numpy(np.asarray(tgt, np.float64).reshape(3, -1))
+    loss = ((1.0 - lam) * torch.abs(r) + lam * r * r).sum() / n_elems
+    g = torch.autograd.grad(loss, [leaves[key] for key in ("mx", "my", "ca", "cb", "cc", "o", "rgb")])
+    return torch.cat([x[:, None] for x in g[:6]] + [g[6]], 1)
+
+
 def loss_grad_magnitude(scene, cams, cfg, targets, lam: float = LAMBDA) -> dict:
     """Per parameter element, a bound B_p >= |dL/dp| that also bounds every term the gradient is
     formed from: the scale against which a binary32 evaluation of the gradient is rounded.
@@ -281,44 +351,8 @@ def loss_grad_magnitude(scene, cams, cfg, targets, lam: float = LAMBDA) -> dict:
         rgb = torch.relu(lin)
         # ---- entry magnitudes -> G [n, 9] (mx, my, ca, cb, cc, o, r, g, b)
         pr = {"mx": mxy[:, 0].detach(), "my": mxy[:, 1].detach(), "ca": conic[:, 0].detach(),
-              "cb": conic[:, 1].detach(), "cc": conic[:, 2].detach(), "rgb": rgb.detach()}
-        H, W = cam.height, cam.width
-        k_t = torch.from_numpy(k.astype(np.int64))
-        pix_t = torch.from_numpy(pix.astype(np.int64))
-        dx = (pix_t % W).to(torch.float64) + 0.5 - pr["mx"][k_t]
-        dy = (pix_t // W).to(torch.float64) + 0.5 - pr["my"][k_t]
-        ca, cb, cc = pr["ca"][k_t], pr["cb"][k_t], pr["cc"][k_t]
-        G_e = torch.exp(-0.5 * (ca * dx * dx + 2.0 * cb * dx * dy + cc * dy * dy))
-        a_raw = o[k_t] * G_e
-        alpha = torch.clamp(a_raw, max=float(cfg.alpha_max))
-        free = (a_raw <= float(cfg.alpha_max)).to(torch.float64)  # no gradient through a clamped alpha
-        la = torch.log1p(-alpha)
-        excl = torch.cumsum(la, 0) - la
-        first = np.ones(pix.size, bool)
-        first[1:] = pix[1:] != pix[:-1]
-        seg = torch.from_numpy(np.cumsum(first) - 1)
-        starts = torch.from_numpy(np.nonzero(first)[0])
-        Tv = torch.exp(excl - excl[starts][seg])
-        rgb_e = pr["rgb"][k_t]
-        contrib = (Tv * alpha)[:, None] * rgb_e
-        img = torch.zeros(3, H * W, dtype=torch.float64).index_add(1, pix_t, contrib.T)
-        r = img - torch.from_numpy(np.asarray(tgt, np.float64).reshape(3, -1))
-        gc = ((1.0 - lam) * torch.sign(r) + 2.0 * lam * r) / n_elems
-        cum = torch.cumsum(contrib, 0)
-        ends = torch.from_numpy(np.append(np.nonzero(first)[0][1:], pix.size) - 1)
-        s_after = torch.clamp(cum[ends][seg] - cum, min=0.0)
-        gabs = gc.abs()[:, pix_t].T
-        Mag = (gabs * (Tv[:, None] * rgb_e + s_after / (1.0 - alpha)[:, None])).sum(1)
-        am = Mag * alpha * free
-        G = torch.zeros(n, 9, dtype=torch.float64)
-        G[:, 0].index_add_(0, k_t, am * ((ca * dx).abs() + (cb * dy).abs()))
-        G[:, 1].index_add_(0, k_t, am * ((cb * dx).abs() + (cc * dy).abs()))
-        G[:, 2].index_add_(0, k_t, am * 0.5 * dx * dx)
-        G[:, 3].index_add_(0, k_t, am * (dx * dy).abs())
-        G[:, 4].index_add_(0, k_t, am * 0.5 * dy * dy)
-        G[:, 5].index_add_(0, k_t, Mag * G_e * free)
-        for ch in range(3):
-            G[:, 6 + ch].index_add_(0, k_t, gabs[:, ch] * Tv * alpha)
+              "cb": conic[:, 1].detach(), "cc": conic[:, 2].detach(), "o": o, "rgb": rgb.detach()}
+        G = screen_magnitudes(pr, cam, cfg, tgt, lam, n_elems, pix, k)
         # ---- back through the view stages
         (B_cov,) = _abs_vjp(conic, [cov_l], G[:, 2:5])
         B_J, B_s6 = _abs_vjp(cov, [J_l, sig_l], B_cov)

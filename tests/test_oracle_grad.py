@@ -222,3 +222,65 @@ def test_gradient_magnitude_closed_form_two_splats():
     assert abs(g["opacity_logits"][1]) == pytest.approx(want1, rel=1e-6)
     assert np.allclose(B["sh"][0, :, 0], np.abs(gc) * a0 * Y0, rtol=1e-6)
     assert np.allclose(np.abs(g["sh"][0, :, 0]), B["sh"][0, :, 0], rtol=1e-9)
+
+
+def _screen(sc, cam, cfg, tg, lam):
+    import torch
+
+    p = G.to_params(sc, requires_grad=False)
+    sigma, o = G.activate(p)
+    pr = G.project(p, sigma, cam, cfg)
+    pr = {k: v.detach() for k, v in pr.items()}
+    pr["o"] = o.detach()
+    v = oracle.prepare_view(sc, cam, cfg)
+    pix, k, _ = oracle.pixel_lists(v, v["vals"], v["ranges"], cam, cfg)
+    n_elems = 3 * cam.pixels
+    return (G.screen_magnitudes(pr, cam, cfg, tg, lam, n_elems, pix, k).numpy(),
+            G.screen_grad(pr, cam, cfg, tg, lam, n_elems, pix, k).numpy(), torch)
+
+
+def test_screen_magnitudes_bound_the_screen_gradients():
+    """Per splat and screen quantity (centre, conic, opacity, colour) the magnitude sum bounds the
+    autograd gradient of the loss with respect to that quantity, on a 200-splat view."""
+    sc = synth.uniform_cube_scene(200, 88)
+    cam = synth.look_at_camera((0.0, 0.3, -3.0), 64, 64)
+    cfg = oracle.make_config()
+    v = oracle.prepare_view(sc, cam, cfg)
+    img, *_ = oracle.render(v, v["vals"], v["ranges"], cam, cfg)
+    tg = (img + synth.target_noise(img.shape, 0.02, 3, 0)).astype(np.float32)
+    for lam in (1.0, 0.2):
+        Gm, Gr, _ = _screen(sc, cam, cfg, tg, lam)
+        assert np.all(Gm >= np.abs(Gr) * (1.0 - 1e-12))
+        assert np.count_nonzero(Gm[:, 0]) > 50
+
+
+def test_screen_magnitudes_equal_the_gradient_without_cancellation():
+    """One splat at one pixel (a 1 x 1 image), its centre off the pixel centre along a diagonal
+    where the conic's cross term has the sign of the diagonal terms, every channel above its
+    target: each screen quantity's gradient is a single product of terms of one sign, so the
+    magnitude sums equal its absolute value exactly (centre terms |ca dx| + |cb dy| added,
+    opacity through exp(power))."""
+    cam = synth.look_at_camera((0.0, 0.0, -3.0), 1, 1)
+    sh = np.zeros((16, 3, 1), np.float32)
+    sh[0, :, 0] = [0.9, 0.4, 0.7]
+    q = np.array([[np.cos(0.3)], [0.0], [0.0], [np.sin(0.3)]], np.float32)  # rotation about z: cb != 0
+    cfg = oracle.make_config()
+    tg = np.zeros((3, 1, 1), np.float32)
+
+    def scene(ox, oy):
+        return synth.Scene(np.array([[ox], [oy], [0.0]], np.float32), np.array([[-1.2], [-2.0], [-1.5]], np.float32),
+                           q, np.array([0.4], np.float32), sh)
+
+    # pick the centre offset whose pixel offsets (dx, dy) have sign(dx) sign(dy) = sign(cb)
+    for ox, oy in [(4e-4, 3e-4), (4e-4, -3e-4)]:
+        sc = scene(ox, oy)
+        pr = G.project(G.to_params(sc, requires_grad=False), G.activate(G.to_params(sc, requires_grad=False))[0], cam, cfg)
+        dx, dy, cb = 0.5 - float(pr["mx"][0]), 0.5 - float(pr["my"][0]), float(pr["cb"][0])
+        if np.sign(dx) * np.sign(dy) == np.sign(cb) and dx != 0 and dy != 0:
+            break
+    else:
+        raise AssertionError("no aligned offset")
+    Gm, Gr, _ = _screen(sc, cam, cfg, tg, 1.0)
+    assert np.all(np.abs(Gr[0]) > 0)
+    # the pixel-centre offsets and the conic make both centre terms of each coordinate one sign
+    assert np.allclose(Gm[0], np.abs(Gr[0]), rtol=1e-9, atol=0), (Gm[0], Gr[0])
