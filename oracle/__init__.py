@@ -114,6 +114,8 @@ def lib():
                                      i64, vp, vp, vp, vp, vp]
             L.orc_removal_effect.argtypes = [C.POINTER(Camera), C.POINTER(Config), i64, vp, vp, vp, vp,
                                              vp, vp, vp, vp, vp, vp, vp, vp]
+            L.orc_removal_magnitude.argtypes = [C.POINTER(Camera), C.POINTER(Config), i64, vp, vp, vp, vp,
+                                                vp, vp, vp, vp, vp, vp]
             L.orc_pixel_lists.restype = i64
             L.orc_pixel_lists.argtypes = [C.POINTER(Camera), C.POINTER(Config), i64, vp, vp, vp, vp, vp, i64, vp,
                                           vp, vp]
@@ -265,6 +267,22 @@ def removal_effect(proj: dict, vals, ranges, cam, cfg: Config, target, tile_mask
     if per_instance:
         return dsse, imp, idse[: vals.size], iimp[: vals.size]
     return dsse, imp
+
+
+def removal_magnitude(proj: dict, vals, ranges, cam, cfg: Config, target, tile_mask=None):
+    """(per splat, per instance) sums of the magnitudes of the terms each dSE is formed from:
+    the rounding scale of a binary32 evaluation (a tolerance quantity, not the method)."""
+    n = proj["depth"].size
+    ccam = make_camera(cam)
+    vals = np.ascontiguousarray(vals, np.uint32)
+    ranges = np.ascontiguousarray(ranges, np.uint32)
+    mask = None if tile_mask is None else np.ascontiguousarray(tile_mask, np.uint8)
+    mag = np.zeros(n, np.float64)
+    imag = np.zeros(max(vals.size, 1), np.float64)
+    lib().orc_removal_magnitude(C.byref(ccam), C.byref(cfg), n, _p(proj["mean2d"]), _p(proj["qcoef"]),
+                                _p(proj["opacity"]), _p(proj["rgb"]), _p(vals), _p(ranges), _p(_f32(target)),
+                                _p(mask), _p(mag), _p(imag))
+    return mag, imag[: vals.size]
 
 
 def removal_bruteforce(proj: dict, vals, ranges, cam, cfg: Config, target, image, k: int) -> float:

@@ -559,6 +559,7 @@ typedef struct {
   const float* target;
   double* part_dse;
   double* part_imp;
+  double* part_mag; /* nullable: per-instance magnitude sums (orc_removal_magnitude) */
   int tiles_x, tiles_y;
   uint32_t cap;
   int64_t next; /* next tile to take (atomic) */
@@ -667,6 +668,8 @@ static void removal_tile(void* arg, int64_t t, orc_entry* ent, double* P, double
   const int tx = (int)(t % job->tiles_x), ty = (int)(t / job->tiles_x);
   uint32_t s = job->ranges[2 * t], e = job->ranges[2 * t + 1];
   for (uint32_t i = s; i < e; ++i) job->part_dse[i] = job->part_imp[i] = 0.0;
+  if (job->part_mag)
+    for (uint32_t i = s; i < e; ++i) job->part_mag[i] = 0.0;
   for (int y = ty * cfg->tile_h; y < (ty + 1) * cfg->tile_h && y < H; ++y)
     for (int x = tx * cfg->tile_w; x < (tx + 1) * cfg->tile_w && x < W; ++x) {
       float T32;
@@ -697,15 +700,29 @@ static void removal_tile(void* arg, int64_t t, orc_entry* ent, double* P, double
         double w = Tv[i] * a;
         job->part_dse[s + ent[i].pos] += dse;
         job->part_imp[s + ent[i].pos] += w;
+        if (job->part_mag) {
+          /* magnitude of the terms dSE is formed from: the two parts of PD (the later splats'
+           * colour behind this one, alpha / (1 - alpha) (P_K - P_{i+1}), and T alpha c) times
+           * |2 PD + 2 (c - c_t)| bounded by 2 |PD| + 2 |c - c_t|, per channel */
+          double mg = 0.0;
+          for (int ch = 0; ch < 3; ++ch) {
+            double PK = P[3 * K + ch];
+            double behind = (PK - P[3 * (i + 1) + ch]) * a / (1.0 - a);
+            double own = Tv[i] * a * rgb[ch * n + ent[i].k];
+            double pd = (P[3 * i + ch] + (PK - P[3 * (i + 1) + ch]) / (1.0 - a)) - PK;
+            mg += (fabs(behind) + fabs(own)) * (2.0 * fabs(pd) + 2.0 * fabs(diff[ch]));
+          }
+          job->part_mag[s + ent[i].pos] += mg;
+        }
       }
     }
 }
 
-void orc_removal_effect(const orc_camera* cam, const orc_config* cfg, int64_t n,
-                        const float* mean2d, const float* qcoef, const float* opacity,
-                        const double* rgb, const uint32_t* vals, const uint32_t* ranges,
-                        const float* target, const uint8_t* tile_mask, double* dsse, double* imp,
-                        double* inst_dse, double* inst_imp) {
+static void removal_effect_impl(const orc_camera* cam, const orc_config* cfg, int64_t n,
+                                const float* mean2d, const float* qcoef, const float* opacity,
+                                const double* rgb, const uint32_t* vals, const uint32_t* ranges,
+                                const float* target, const uint8_t* tile_mask, double* dsse, double* imp,
+                                double* inst_dse, double* inst_imp, double* mag, double* inst_mag) {
   orc_tile_job job;
   memset(&job, 0, sizeof(job));
   job.cam = cam;
@@ -725,6 +742,7 @@ void orc_removal_effect(const orc_camera* cam, const orc_config* cfg, int64_t n,
     if (ranges[2 * t + 1] > m) m = ranges[2 * t + 1];
   job.part_dse = (double*)calloc((size_t)m + 1, sizeof(double));
   job.part_imp = (double*)calloc((size_t)m + 1, sizeof(double));
+  job.part_mag = (mag || inst_mag) ? (double*)calloc((size_t)m + 1, sizeof(double)) : NULL;
   job.tile_fn = removal_tile;
   run_tiles(&job);
   for (int64_t t = 0; t < n_tiles; ++t) {
@@ -735,10 +753,37 @@ void orc_removal_effect(const orc_camera* cam, const orc_config* cfg, int64_t n,
       if (imp) imp[k] += job.part_imp[i];
       if (inst_dse) inst_dse[i] = job.part_dse[i];
       if (inst_imp) inst_imp[i] = job.part_imp[i];
+      if (mag) mag[k] += job.part_mag[i];
+      if (inst_mag) inst_mag[i] = job.part_mag[i];
     }
   }
   free(job.part_dse);
   free(job.part_imp);
+  free(job.part_mag);
+}
+
+void orc_removal_effect(const orc_camera* cam, const orc_config* cfg, int64_t n,
+                        const float* mean2d, const float* qcoef, const float* opacity,
+                        const double* rgb, const uint32_t* vals, const uint32_t* ranges,
+                        const float* target, const uint8_t* tile_mask, double* dsse, double* imp,
+                        double* inst_dse, double* inst_imp) {
+  removal_effect_impl(cam, cfg, n, mean2d, qcoef, opacity, rgb, vals, ranges, target, tile_mask, dsse, imp,
+                      inst_dse, inst_imp, NULL, NULL);
+}
+
+/*
+ * The scale of the rounding of a binary32 evaluation of the removal effect: per splat (mag,
+ * accumulated) and per tile instance (inst_mag), the sum over the composited pixels of
+ * sum_ch (|alpha/(1 - alpha) S_>| + |T alpha c|) (2 |PD| + 2 |c - c_t|) -- the magnitudes of the
+ * two parts of PD times the bound of the factor that multiplies an error of PD in dSE.  A
+ * quantity for tolerances, not part of the method; both outputs nullable.
+ */
+void orc_removal_magnitude(const orc_camera* cam, const orc_config* cfg, int64_t n,
+                           const float* mean2d, const float* qcoef, const float* opacity,
+                           const double* rgb, const uint32_t* vals, const uint32_t* ranges,
+                           const float* target, const uint8_t* tile_mask, double* mag, double* inst_mag) {
+  removal_effect_impl(cam, cfg, n, mean2d, qcoef, opacity, rgb, vals, ranges, target, tile_mask, NULL, NULL,
+                      NULL, NULL, mag, inst_mag);
 }
 
 /*

@@ -2,11 +2,12 @@
 // (Section IV-B), plus the per-splat reduction into dMSE_k and I_k (Section IV-B last
 // equation, Section IV-A).
 //
-// One CTA of 256 threads per (view, tile), one pixel per thread.  The tile's depth-sorted
-// list is walked in batches; each batch's 48-byte raster records are gathered into shared
-// memory with cp.async (16-byte copies), so every pixel of the tile reads them as shared-
-// memory broadcasts.  The per-pair work is plain FP32 ALU: these kernels are bound by
-// FP32 issue, not by HBM (one record gather serves 256 pixels).
+// One CTA of 128 threads per (view, tile): four warps, each on an 8 x 8 block of the tile, two
+// vertically adjacent pixels per lane, their binary32 arithmetic in packed pairs (tile_pass.cuh).
+// The tile's depth-sorted list is walked in batches; each batch's 48-byte raster records are
+// gathered into shared memory with cp.async (16-byte copies), so every pixel of the tile reads
+// them as shared-memory broadcasts.  The per-pair work is plain FP32 ALU: these kernels are
+// bound by instruction issue, not by HBM (one record gather serves 256 pixels).
 //
 // Removal effect: after the forward walk (c, T_final, n_last per pixel) the same list is
 // walked back to front, recovering T_i = T_{i+1} / (1 - alpha_i) and accumulating the
@@ -15,45 +16,49 @@
 // which equals the paper's P_i - P_{i+1} / (1 - alpha_i) + alpha_i / (1 - alpha_i) P_K because
 // P_K - P_{i+1} = S_{>i}; every term is a sum of non-negative numbers, so no prefix sums are
 // subtracted.  dSE_i = sum_ch PD_i (PD_i + 2 (c - c_t)).  Per (tile, splat) the 256 pixel
-// values are summed without atomics: 8 consecutive splats at a time, a warp transpose-sum
-// leaves lane l with its warp's total for splat l, the warp totals of a whole batch go to
-// shared memory, and after one barrier the 8 warp totals are added in warp order.  The order
-// is fixed, so the result does not depend on scheduling.
+// values are summed without atomics: each lane adds its two pixels, then 8 consecutive splats
+// at a time a warp transpose-sum leaves lane l with its warp's total for splat l, the warp
+// totals of a whole batch go to shared memory, and after one barrier the 4 warp totals are
+// added in warp order.  The order is fixed, so the result does not depend on scheduling or on
+// the splat-batch size.
 #include <atomic>
 
 #include "raster_common.cuh"
+#include "tile_pass.cuh"
 
 namespace potr {
 namespace {
 
 template <int BATCH>
-__global__ void __launch_bounds__(kThreads, 6) render_kernel(const float4* __restrict__ raster,
-                                                          const uint32_t* __restrict__ vals,
-                                                          const uint32_t* __restrict__ ranges,
-                                                          const potr_view_info* __restrict__ info, int n_views,
-                                                          potr_raster_config cfg, float* __restrict__ images,
-                                                          float* __restrict__ t_final, uint32_t* __restrict__ n_last,
-                                                          uint8_t* __restrict__ gmask, TileQueue queue) {
+__global__ void __launch_bounds__(kT2, 8) render_kernel(const float4* __restrict__ raster,
+                                                     const uint32_t* __restrict__ vals,
+                                                     const uint32_t* __restrict__ ranges,
+                                                     const potr_view_info* __restrict__ info, int n_views,
+                                                     potr_raster_config cfg, float* __restrict__ images,
+                                                     float* __restrict__ t_final, uint32_t* __restrict__ n_last,
+                                                     TileQueue queue) {
   extern __shared__ float4 smem[];  // two batches of records
-  uint8_t* wmask = reinterpret_cast<uint8_t*>(smem + 2 * kSRec * BATCH);
   __shared__ uint32_t s_slot;
   int64_t tile;
   for (bool first = true; next_tile(queue, &s_slot, first, tile); first = false) {
-    const TileCtx c = tile_ctx(info, n_views, ranges, cfg, tile);
-    float C[3], T;
-    uint32_t last;
-    forward_walk<BATCH>(smem, wmask, nullptr, 0u, raster, vals, c, cfg, C, T, last, gmask ? gmask + c.s : nullptr);
-    if (!c.inside) continue;
-    const int64_t pix = c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
+    const Tile2 c = tile2_ctx(info, n_views, ranges, cfg, tile);
+    f2_t C[3], T;
+    uint32_t last0, last1;
+    forward_walk2<BATCH>(smem, raster, vals, c, cfg, C, T, last0, last1);
     const int64_t plane = (int64_t)c.vi.width * c.vi.height;
-    if (images) {
-      float* im = images + 3 * c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
-      im[0] = C[0];
-      im[plane] = C[1];
-      im[2 * plane] = C[2];
+    const int64_t pix = c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
+    float* im = images ? images + 3 * c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px : nullptr;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (!(h ? c.in1 : c.in0)) continue;
+      const int64_t row = h ? c.vi.width : 0;
+      if (im) {
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) im[row + ch * plane] = h ? f2hi(C[ch]) : f2lo(C[ch]);
+      }
+      if (t_final) t_final[pix + row] = h ? f2hi(T) : f2lo(T);
+      if (n_last) n_last[pix + row] = h ? last1 : last0;
     }
-    if (t_final) t_final[pix] = T;
-    if (n_last) n_last[pix] = last;
   }
 }
 
@@ -77,175 +82,198 @@ __device__ __forceinline__ float warp_transpose_sum8(float (&v)[8]) {
   return r;
 }
 
-constexpr int kChunk = 8;           // splats per warp transpose-sum
-constexpr uint32_t kMaskCache = 2048;  // list positions whose warp masks the back walk reuses
+constexpr int kChunk = 8;  // splats per warp transpose-sum
 
 template <int BATCH, bool IMP>
 constexpr size_t removal_smem_bytes() {
-  return sizeof(float4) * 2 * kSRec * BATCH + sizeof(float) * kWarps * BATCH * (IMP ? 2 : 1) + BATCH + kMaskCache;
+  return sizeof(float4) * 2 * kSRec2 * BATCH + sizeof(float) * kW2 * BATCH * (IMP ? 2 : 1);
 }
 
 template <int BATCH, bool IMP>
-__global__ void __launch_bounds__(kThreads, BATCH <= 128 ? 6 : 5) removal_kernel(const float4* __restrict__ raster,
-                                                           const uint32_t* __restrict__ vals,
-                                                           const uint32_t* __restrict__ ranges,
-                                                           const potr_view_info* __restrict__ info, int n_views,
-                                                           potr_raster_config cfg, const float* __restrict__ targets,
-                                                           float* __restrict__ images, float* __restrict__ inst_dse,
-                                                           float* __restrict__ inst_imp, const uint4* __restrict__ cull,
-                                                           const uint32_t* __restrict__ offsets, TileQueue queue) {
+__global__ void __launch_bounds__(kT2, 8) removal_kernel(const float4* __restrict__ raster,
+                                                       const uint32_t* __restrict__ vals,
+                                                       const uint32_t* __restrict__ ranges,
+                                                       const potr_view_info* __restrict__ info, int n_views,
+                                                       potr_raster_config cfg, const float* __restrict__ targets,
+                                                       float* __restrict__ images, float* __restrict__ inst_dse,
+                                                       float* __restrict__ inst_imp, const uint4* __restrict__ cull,
+                                                       const uint32_t* __restrict__ offsets, TileQueue queue) {
   extern __shared__ float4 dyn[];
-  float4* smem = dyn;                                               // [2][BATCH][kSRec] raster records
-  float* red_d = reinterpret_cast<float*>(dyn + 2 * kSRec * BATCH);  // [kWarps][BATCH] warp sums of dSE
-  float* red_i = red_d + kWarps * BATCH;                            // [kWarps][BATCH] warp sums of T alpha
-  uint8_t* wmask = reinterpret_cast<uint8_t*>(red_d + kWarps * BATCH * (IMP ? 2 : 1));  // [BATCH]
-  uint8_t* mcache = wmask + BATCH;  // [kMaskCache] warp masks of the first list positions
-  __shared__ uint32_t max_last_w[kWarps];
+  float4* smem = dyn;                                                // [2][BATCH][kSRec2] raster records
+  float* red_d = reinterpret_cast<float*>(dyn + 2 * kSRec2 * BATCH);  // [kW2][BATCH] warp sums of dSE
+  float* red_i = red_d + kW2 * BATCH;                                // [kW2][BATCH] warp sums of T alpha
+  __shared__ uint32_t max_last_w[kW2];
   __shared__ uint32_t s_slot;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int64_t tile;
   for (bool first = true; next_tile(queue, &s_slot, first, tile); first = false) {
-  const TileCtx c = tile_ctx(info, n_views, ranges, cfg, tile);
-  float C[3], T;
-  uint32_t last;
-  forward_walk<BATCH>(smem, wmask, mcache, kMaskCache, raster, vals, c, cfg, C, T, last);
+    const Tile2 c = tile2_ctx(info, n_views, ranges, cfg, tile);
+    f2_t C[3], T;
+    uint32_t last0, last1;
+    forward_walk2<BATCH>(smem, raster, vals, c, cfg, C, T, last0, last1);
 
-  float e2[3] = {0.0f, 0.0f, 0.0f};  // 2 (c - c_t)
-  if (c.inside) {
-    const int64_t plane = (int64_t)c.vi.width * c.vi.height;
-    const int64_t o = 3 * c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
+    // 2 (c - c_t) per channel and pixel (0 outside the image)
+    f2_t e2[3];
+    {
+      const int64_t plane = (int64_t)c.vi.width * c.vi.height;
+      const int64_t o = 3 * c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) e2[ch] = 2.0f * (C[ch] - targets[o + ch * plane]);
-    if (images) {
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) images[o + ch * plane] = C[ch];
-    }
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t warp_last = __reduce_max_sync(0xffffffffu, last);
-  if (lane == 0) max_last_w[warp] = warp_last;
-  __syncthreads();
-  uint32_t max_last = 0;
-#pragma unroll
-  for (int w = 0; w < kWarps; ++w) max_last = max(max_last, max_last_w[w]);
-
-  // Back-to-front over list positions [0, max_last): T_i = T_{i+1} / (1 - alpha_i),
-  // S = sum of T_j alpha_j c_j over the composited j > i.  Each warp visits only the splats
-  // of its warp mask, 8 at a time, highest position first.
-  float S[3] = {0.0f, 0.0f, 0.0f};
-  float* my_d = red_d + warp * BATCH;
-  float* my_i = red_i + warp * BATCH;
-  // batch k covers positions [lo_k, hi_k), hi_0 = max_last, going down; double-buffered
-  const uint32_t nb = (max_last + BATCH - 1) / BATCH;
-  BatchStager<BATCH> st;
-  __syncthreads();  // the forward walk's last batch is no longer read
-  if (nb > 0) {
-    const uint32_t lo0 = max_last > (uint32_t)BATCH ? max_last - BATCH : 0u;
-    st.load(vals, c.s + lo0, (int)(max_last - lo0));
-    st.issue(smem, raster);
-  }
-  if (nb > 1) {
-    const uint32_t hi1 = max_last - BATCH, lo1 = hi1 > (uint32_t)BATCH ? hi1 - BATCH : 0u;
-    st.load(vals, c.s + lo1, (int)(hi1 - lo1));
-  }
-  for (uint32_t k = 0; k < nb; ++k) {
-    const uint32_t top = max_last - k * BATCH;
-    const uint32_t lo = top > (uint32_t)BATCH ? top - BATCH : 0u;
-    const int cnt = (int)(top - lo);
-    const float4* buf = smem + kSRec * BATCH * (k & 1);
-    if (k > 0) __syncthreads();  // batch k-1 (records, warp sums) fully consumed
-    if (k + 1 < nb) {
-      st.issue(smem + kSRec * BATCH * ((k + 1) & 1), raster);
-      cp_async_wait<1>();
-      if (k + 2 < nb) {
-        const uint32_t hi2 = lo - BATCH, lo2 = hi2 > (uint32_t)BATCH ? hi2 - BATCH : 0u;
-        st.load(vals, c.s + lo2, (int)(hi2 - lo2));
+      for (int ch = 0; ch < 3; ++ch) {
+        float v0 = 0.0f, v1 = 0.0f;
+        if (c.in0) v0 = 2.0f * (f2lo(C[ch]) - targets[o + ch * plane]);
+        if (c.in1) v1 = 2.0f * (f2hi(C[ch]) - targets[o + c.vi.width + ch * plane]);
+        e2[ch] = f2(v0, v1);
+        if (images) {
+          if (c.in0) images[o + ch * plane] = f2lo(C[ch]);
+          if (c.in1) images[o + c.vi.width + ch * plane] = f2hi(C[ch]);
+        }
       }
-    } else {
-      cp_async_wait<0>();
     }
-    const uint8_t* bm = top <= kMaskCache ? mcache + lo : wmask;  // the forward walk's masks
-    if (top > kMaskCache) compute_masks<BATCH>(buf, wmask, cnt, c, cfg);
-    for (int j = lane; j < cnt; j += 32) {
-      my_d[j] = 0.0f;
-      if (IMP) my_i[j] = 0.0f;
-    }
+    const uint32_t warp_last = __reduce_max_sync(0xffffffffu, max(last0, last1));
+    if (lane == 0) max_last_w[warp] = warp_last;
     __syncthreads();
-    for (int ghi = cnt; ghi > 0; ghi -= 32) {
-      const int glo = ghi > 32 ? ghi - 32 : 0;
-      if (lo + (uint32_t)glo >= warp_last) continue;  // warp-uniform: nothing composited here
-      const int jl = glo + lane;
-      uint32_t m = __ballot_sync(0xffffffffu, jl < ghi && lo + (uint32_t)jl < warp_last && ((bm[jl] >> warp) & 1u));
-      while (m) {
-        float d[kChunk], im[kChunk];
-        int mypos = -1;
-        bool any = false;
+    uint32_t max_last = 0;
 #pragma unroll
-        for (int u = 0; u < kChunk; ++u) {
-          d[u] = 0.0f;
-          if (IMP) im[u] = 0.0f;
-          if (m) {
-            const int b = 31 - __clz(m);
-            m &= ~(1u << b);
-            const int j = glo + b;
-            if (lane == u) mypos = j;
-            if (lo + (uint32_t)j < last) {
-              const float4 r0 = buf[kSRec * j];
-              const float4 r1 = buf[kSRec * j + 1];
-              const float p = pair_exponent(r0.z, r0.w, r1.x, __fsub_rn(c.fx, r0.x), __fsub_rn(c.fy, r0.y));
-              if (p >= r1.z) {
-                const float a = pair_alpha(r1.y, p, cfg.alpha_max);
-                if (a >= cfg.alpha_min) {
-                  const float4 r2 = buf[kSRec * j + 2];
-                  const float rcp = __fdividef(1.0f, 1.0f - a);
-                  T = T * rcp;                  // T_i = T_{i+1} / (1 - alpha_i)
-                  const float w = a * T;        // T_i alpha_i
-                  const float ratio = a * rcp;  // alpha_i / (1 - alpha_i)
-                  const float wc0 = w * r2.x, wc1 = w * r2.y, wc2 = w * r2.z;
-                  const float pd0 = fmaf(ratio, S[0], -wc0);
-                  const float pd1 = fmaf(ratio, S[1], -wc1);
-                  const float pd2 = fmaf(ratio, S[2], -wc2);
-                  float dse = pd0 * (pd0 + e2[0]);
-                  dse = fmaf(pd1, pd1 + e2[1], dse);
-                  dse = fmaf(pd2, pd2 + e2[2], dse);
-                  S[0] += wc0;
-                  S[1] += wc1;
-                  S[2] += wc2;
-                  d[u] = dse;
-                  if (IMP) im[u] = w;
-                  any = true;
+    for (int w = 0; w < kW2; ++w) max_last = max(max_last, max_last_w[w]);
+
+    // Back to front over list positions [0, max_last): T_i = T_{i+1} / (1 - alpha_i),
+    // S = sum of T_j alpha_j c_j over the composited j > i.  Each warp visits the splats its
+    // block test keeps, 8 at a time, highest position first.
+    f2_t S[3] = {f2s(0.0f), f2s(0.0f), f2s(0.0f)};
+    float* my_d = red_d + warp * BATCH;
+    float* my_i = red_i + warp * BATCH;
+    const uint32_t nb = (max_last + BATCH - 1) / BATCH;
+    Stager2<BATCH> st;
+    if (nb > 0) {
+      const uint32_t lo0 = max_last > (uint32_t)BATCH ? max_last - BATCH : 0u;
+      st.load(vals, c.s + lo0, (int)(max_last - lo0));
+      st.issue(smem, raster);  // the forward walk's reads of smem ended at the barrier above
+    }
+    if (nb > 1) {
+      const uint32_t hi1 = max_last - BATCH, lo1 = hi1 > (uint32_t)BATCH ? hi1 - BATCH : 0u;
+      st.load(vals, c.s + lo1, (int)(hi1 - lo1));
+    }
+    for (uint32_t k = 0; k < nb; ++k) {
+      const uint32_t top = max_last - k * BATCH;
+      const uint32_t lo = top > (uint32_t)BATCH ? top - BATCH : 0u;
+      const int cnt = (int)(top - lo);
+      const float4* buf = smem + kSRec2 * BATCH * (k & 1);
+      if (k > 0) __syncthreads();  // batch k-1 (records, warp sums) fully consumed
+      if (k + 1 < nb) {
+        st.issue(smem + kSRec2 * BATCH * ((k + 1) & 1), raster);
+        cp_async_wait2<1>();
+        if (k + 2 < nb) {
+          const uint32_t hi2 = lo - BATCH, lo2 = hi2 > (uint32_t)BATCH ? hi2 - BATCH : 0u;
+          st.load(vals, c.s + lo2, (int)(hi2 - lo2));
+        }
+      } else {
+        cp_async_wait2<0>();
+      }
+      for (int j = lane; j < cnt; j += 32) {
+        my_d[j] = 0.0f;
+        if (IMP) my_i[j] = 0.0f;
+      }
+      __syncthreads();  // every thread's copies of batch k are visible
+      for (int ghi = cnt; ghi > 0; ghi -= 32) {
+        const int glo = ghi > 32 ? ghi - 32 : 0;
+        if (lo + (uint32_t)glo >= warp_last) continue;  // warp-uniform: nothing composited here
+        const int jl = glo + lane;
+        const bool cand = jl < ghi && lo + (uint32_t)jl < warp_last &&
+                          block_may_pass(buf[kSRec2 * jl], buf[kSRec2 * jl + 1], c.bx0, c.by0);
+        uint32_t m = __ballot_sync(0xffffffffu, cand);
+        while (m) {
+          float d[kChunk], im[kChunk];
+          int mypos = -1;
+          bool any = false;
+#pragma unroll
+          for (int u = 0; u < kChunk; ++u) {
+            d[u] = 0.0f;
+            if (IMP) im[u] = 0.0f;
+            if (m) {
+              const int b = 31 - __clz(m);
+              m &= ~(1u << b);
+              const int j = glo + b;
+              if (lane == u) mypos = j;
+              const uint32_t pos = lo + (uint32_t)j;
+              const bool in0 = pos < last0, in1 = pos < last1;
+              if (in0 || in1) {
+                const float4 r0 = buf[kSRec2 * j];
+                const float4 r1 = buf[kSRec2 * j + 1];
+                const f2_t p2 = pair_exponent2(r0.z, r0.w, r1.x, f2s(__fsub_rn(c.fx, r0.x)),
+                                               sub2(f2(c.fy0, c.fy1), f2s(r0.y)));
+                float p0, p1;
+                f2split(p2, p0, p1);
+                const bool pass0 = in0 && p0 >= r1.z, pass1 = in1 && p1 >= r1.z;
+                if (pass0 || pass1) {
+                  float a0, a1;
+                  f2split(mul2(f2s(r1.y), exp2r2(p2)), a0, a1);
+                  a0 = fminf(cfg.alpha_max, a0);
+                  a1 = fminf(cfg.alpha_max, a1);
+                  const bool ok0 = pass0 && a0 >= cfg.alpha_min, ok1 = pass1 && a1 >= cfg.alpha_min;
+                  if (ok0 || ok1) {
+                    const float4 r2 = buf[kSRec2 * j + 2];
+                    // a pixel that does not take the splat: alpha 0 and 1 / (1 - alpha) = 1, so
+                    // its T, S and dSE do not change (every update adds or scales by exact zeros
+                    // and ones)
+                    const f2_t ae = f2(ok0 ? a0 : 0.0f, ok1 ? a1 : 0.0f);
+                    const f2_t rcp = f2(ok0 ? __fdividef(1.0f, 1.0f - a0) : 1.0f,
+                                        ok1 ? __fdividef(1.0f, 1.0f - a1) : 1.0f);
+                    T = mul2(T, rcp);                      // T_i = T_{i+1} / (1 - alpha_i)
+                    const f2_t w = mul2(ae, T);            // T_i alpha_i
+                    const f2_t ratio = mul2(ae, rcp);      // alpha_i / (1 - alpha_i)
+                    const f2_t nw = sub2(f2s(0.0f), w);    // -T_i alpha_i (exact)
+                    const f2_t nwc0 = mul2(nw, f2s(r2.x)), nwc1 = mul2(nw, f2s(r2.y)), nwc2 = mul2(nw, f2s(r2.z));
+                    // PD = alpha / (1 - alpha) S - T alpha c, one rounding per channel
+                    const f2_t pd0 = fma2(ratio, S[0], nwc0);
+                    const f2_t pd1 = fma2(ratio, S[1], nwc1);
+                    const f2_t pd2 = fma2(ratio, S[2], nwc2);
+                    f2_t dse = mul2(pd0, add2(pd0, e2[0]));  // sum_ch PD (PD + 2 (c - c_t))
+                    dse = fma2(pd1, add2(pd1, e2[1]), dse);
+                    dse = fma2(pd2, add2(pd2, e2[2]), dse);
+                    S[0] = sub2(S[0], nwc0);  // S + T alpha c
+                    S[1] = sub2(S[1], nwc1);
+                    S[2] = sub2(S[2], nwc2);
+                    float x0, x1;
+                    f2split(dse, x0, x1);
+                    d[u] = x0 + x1;
+                    if (IMP) {
+                      f2split(w, x0, x1);
+                      im[u] = x0 + x1;
+                    }
+                    any = true;
+                  }
                 }
               }
             }
           }
+          float sd = 0.0f, si = 0.0f;
+          if (__any_sync(0xffffffffu, any)) {
+            sd = warp_transpose_sum8(d);
+            if (IMP) si = warp_transpose_sum8(im);
+          }
+          if (lane < kChunk && mypos >= 0) {
+            my_d[mypos] = sd;
+            if (IMP) my_i[mypos] = si;
+          }
         }
+      }
+      __syncthreads();
+      // per (tile, splat): the 4 warp sums in warp order
+      for (int j = threadIdx.x; j < cnt; j += kT2) {
         float sd = 0.0f, si = 0.0f;
-        if (__any_sync(0xffffffffu, any)) {
-          sd = warp_transpose_sum8(d);
-          if (IMP) si = warp_transpose_sum8(im);
-        }
-        if (lane < kChunk && mypos >= 0) {
-          my_d[mypos] = sd;
-          if (IMP) my_i[mypos] = si;
-        }
-      }
-    }
-    __syncthreads();
-    // per (tile, splat): the 8 warp sums in warp order
-    for (int j = threadIdx.x; j < cnt; j += kThreads) {
-      float sd = 0.0f, si = 0.0f;
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) {
-        sd += red_d[w * BATCH + j];
-        if (IMP) si += red_i[w * BATCH + j];
-      }
-      if (sd != 0.0f || (IMP && si != 0.0f)) {
-        const uint32_t vk = vals[c.s + lo + j];
-        const uint32_t slot = emission_slot(offsets[vk], cull[vk], c.tx, c.ty);  // L2
-        inst_dse[slot] = sd;
-        if (IMP) inst_imp[slot] = si;
+        for (int w = 0; w < kW2; ++w) {
+          sd += red_d[w * BATCH + j];
+          if (IMP) si += red_i[w * BATCH + j];
+        }
+        if (sd != 0.0f || (IMP && si != 0.0f)) {
+          const uint32_t vk = vals[c.s + lo + j];
+          const uint32_t slot = emission_slot(offsets[vk], cull[vk], c.tx, c.ty);  // L2
+          inst_dse[slot] = sd;
+          if (IMP) inst_imp[slot] = si;
+        }
       }
     }
-  }
   }  // tiles
 }
 
@@ -332,17 +360,16 @@ __global__ void __launch_bounds__(256) splat_reduce_kernel(const uint32_t* __res
 template <int BATCH>
 cudaError_t launch_render(const potr_views* views, const potr_frame* frame, const potr_raster_config& cfg,
                           const uint32_t* vals, const uint32_t* ranges, float* images, float* t_final,
-                          uint32_t* n_last, uint8_t* gmask, const TileQueue& q, cudaStream_t s) {
-  const size_t smem = sizeof(float4) * 2 * kSRec * BATCH + BATCH;
-  if (smem > 48 * 1024) {
+                          uint32_t* n_last, const TileQueue& q, cudaStream_t s) {
+  const size_t smem = sizeof(float4) * 2 * kSRec2 * BATCH;
+  {  // 512-splat batches take exactly 48 KB of dynamic shared memory, beyond the default with the static part
     cudaError_t e = cudaFuncSetAttribute(render_kernel<BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  const unsigned grid = tile_grid(render_kernel<BATCH>, smem, q, frame->total_tiles);
+  const unsigned grid = tile_grid(render_kernel<BATCH>, smem, q, frame->total_tiles, kT2);
   tile_timing_begin(s);
-  render_kernel<BATCH><<<grid, kThreads, smem, s>>>(reinterpret_cast<const float4*>(views->raster), vals, ranges,
-                                                    frame->info, frame->n_views, cfg, images, t_final, n_last, gmask,
-                                                    q);
+  render_kernel<BATCH><<<grid, kT2, smem, s>>>(reinterpret_cast<const float4*>(views->raster), vals, ranges,
+                                               frame->info, frame->n_views, cfg, images, t_final, n_last, q);
   tile_timing_end(s);
   note_launches(1);
   return cudaGetLastError();
@@ -353,18 +380,18 @@ cudaError_t launch_removal(const potr_views* views, const potr_frame* frame, con
                            const uint32_t* vals, const uint32_t* ranges, const float* targets, float* images,
                            float* inst_dse, float* inst_imp, const TileQueue& q, cudaStream_t s) {
   constexpr size_t smem = removal_smem_bytes<BATCH, IMP>();
-  if (smem > 48 * 1024) {
+  {
     cudaError_t e = cudaFuncSetAttribute(removal_kernel<BATCH, IMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  // five CTAs of about 43 KB each only fit with the largest shared-memory carveout
+  // several CTAs of up to 64 KB each only fit with the largest shared-memory carveout
   cudaError_t ce = cudaFuncSetAttribute(removal_kernel<BATCH, IMP>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                         (int)cudaSharedmemCarveoutMaxShared);
   if (ce != cudaSuccess) return ce;
-  const unsigned grid = tile_grid(removal_kernel<BATCH, IMP>, smem, q, frame->total_tiles);
+  const unsigned grid = tile_grid(removal_kernel<BATCH, IMP>, smem, q, frame->total_tiles, kT2);
   tile_timing_begin(s);
-  removal_kernel<BATCH, IMP><<<grid, kThreads, smem, s>>>(reinterpret_cast<const float4*>(views->raster), vals, ranges,
+  removal_kernel<BATCH, IMP><<<grid, kT2, smem, s>>>(reinterpret_cast<const float4*>(views->raster), vals, ranges,
                                                           frame->info, frame->n_views, cfg, targets, images, inst_dse,
                                                           inst_imp, reinterpret_cast<const uint4*>(views->cull),
                                                           views->offsets, q);
@@ -399,9 +426,9 @@ extern "C" potr_status potr_render(const potr_views* views, const potr_frame* fr
   if (make_queue(d_tile_order, frame->total_tiles, q, s) != cudaSuccess) return POTR_ERR_CUDA;
   cudaError_t e;
   switch (cfg->batch) {
-    case 128: e = launch_render<128>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, d_warp_masks, q, s); break;
-    case 256: e = launch_render<256>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, d_warp_masks, q, s); break;
-    default: e = launch_render<512>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, d_warp_masks, q, s); break;
+    case 128: e = launch_render<128>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, q, s); break;
+    case 256: e = launch_render<256>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, q, s); break;
+    default: e = launch_render<512>(views, frame, *cfg, d_vals, d_tile_ranges, d_images, d_t_final, d_n_last, q, s); break;
   }
   return e == cudaSuccess ? POTR_OK : POTR_ERR_CUDA;
 }

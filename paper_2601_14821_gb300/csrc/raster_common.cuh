@@ -287,12 +287,12 @@ __device__ __forceinline__ bool next_tile(const TileQueue& q, uint32_t* s_slot, 
 
 // Grid for a tile kernel: one CTA per tile, or as many CTAs as fit on the device at once.
 template <typename K>
-inline unsigned tile_grid(K kernel, size_t smem, const TileQueue& q, int64_t total_tiles) {
+inline unsigned tile_grid(K kernel, size_t smem, const TileQueue& q, int64_t total_tiles, int block = kTilePixels) {
   if (!q.order) return (unsigned)total_tiles;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kTilePixels, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
   int64_t g = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
   if (g > total_tiles) g = total_tiles;
   return (unsigned)(g > 0 ? g : 1);

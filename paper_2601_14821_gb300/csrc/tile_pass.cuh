@@ -1,0 +1,303 @@
+// tile_pass.cuh -- building blocks of the tile kernels that give each lane two pixels.
+//
+// A tile (256 pixels) is one CTA of four warps; warp w covers an 8 x 8 block of the tile and
+// lane l the two vertically adjacent pixels (l mod 8, 2 (l div 8)) and (l mod 8, 2 (l div 8) + 1)
+// of it.  The per-pixel binary32 arithmetic of the two pixels runs as packed pairs (the f32x2
+// add / sub / mul / fma of the sm_100 family: one instruction, two IEEE round-to-nearest
+// results, bit-identical to the scalar operations), so a splat record read once from shared
+// memory, one loop step and one warp vote serve two pixels, and the two pixels' exponent,
+// exp2 and compositing updates issue as one instruction each.
+//
+// Which splats a warp visits: per group of 32 list positions, lane j tests position j against
+// the warp's 8 x 8 block (the exponent's maximum over the block's pixel-centre rectangle, on
+// its edges or at the splat centre, raised by a rounding margin, against the record's
+// prefilter); a position whose bit is clear has alpha < alpha_min at all 64 pixels, so
+// skipping it changes no decision.
+#pragma once
+
+#include "potr_device.cuh"
+
+namespace potr {
+namespace {
+
+constexpr int kT2 = 128;           // threads per CTA: four warps, two pixels per lane
+constexpr int kW2 = kT2 / 32;      // warps per CTA
+constexpr int kSRec2 = 3;          // float4 per staged record
+
+// ---------------------------------------------------------------------------------------
+// packed binary32 pairs
+// ---------------------------------------------------------------------------------------
+typedef unsigned long long f2_t;
+
+__device__ __forceinline__ f2_t f2(float lo, float hi) {
+  f2_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ f2_t f2s(float x) { return f2(x, x); }
+__device__ __forceinline__ float f2lo(f2_t v) {
+  float lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+  return lo;
+}
+__device__ __forceinline__ float f2hi(f2_t v) {
+  float lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+  return hi;
+}
+__device__ __forceinline__ void f2split(f2_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2_t add2(f2_t a, f2_t b) {
+  f2_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t sub2(f2_t a, f2_t b) {
+  f2_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t mul2(f2_t a, f2_t b) {
+  f2_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) {
+  f2_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// exp2r (potr_device.cuh) on a pair: the same clamps, operations and order, so the same bits.
+__device__ __forceinline__ f2_t exp2r2(f2_t yy) {
+  constexpr float c0 = exp2_coef(0), c1 = exp2_coef(1), c2 = exp2_coef(2), c3 = exp2_coef(3);
+  constexpr float c4 = exp2_coef(4), c5 = exp2_coef(5), c6 = exp2_coef(6);
+  float y0, y1;
+  f2split(yy, y0, y1);
+  y0 = (y0 >= -125.0f) ? y0 : -125.0f;
+  y0 = (y0 > 125.0f) ? 125.0f : y0;
+  y1 = (y1 >= -125.0f) ? y1 : -125.0f;
+  y1 = (y1 > 125.0f) ? 125.0f : y1;
+  const f2_t y = f2(y0, y1);
+  const f2_t magic = f2s(12582912.0f);
+  const f2_t t = add2(y, magic);
+  const f2_t n = sub2(t, magic);
+  const f2_t f = sub2(y, n);
+  f2_t p = fma2(f2s(c6), f, f2s(c5));
+  p = fma2(p, f, f2s(c4));
+  p = fma2(p, f, f2s(c3));
+  p = fma2(p, f, f2s(c2));
+  p = fma2(p, f, f2s(c1));
+  p = fma2(p, f, f2s(c0));
+  float p0, p1, t0, t1;
+  f2split(p, p0, p1);
+  f2split(t, t0, t1);
+  return f2(__int_as_float(__float_as_int(p0) + (__float_as_int(t0) << 23)),
+            __int_as_float(__float_as_int(p1) + (__float_as_int(t1) << 23)));
+}
+
+// pair_exponent (potr_device.cuh) for the two pixels of a lane: dx shared, dy per pixel.
+//   u = fma(A, dx, B dy), v = C dy, p = fma(u, dx, v dy)
+__device__ __forceinline__ f2_t pair_exponent2(float A, float B, float C, f2_t dx2, f2_t dy2) {
+  const f2_t u = fma2(f2s(A), dx2, mul2(f2s(B), dy2));
+  const f2_t v = mul2(f2s(C), dy2);
+  return fma2(u, dx2, mul2(v, dy2));
+}
+
+// ---------------------------------------------------------------------------------------
+// cp.async staging of list batches (128 threads)
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16_2(void* smem, const void* gmem) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait2() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// Double-buffered batch staging: the gathers of one batch are in flight (cp.async, one commit
+// group per batch) while the CTA works on the other buffer; every thread holds the list values
+// (vk) of the batch after that in registers, so issuing never waits on a load.
+template <int BATCH>
+struct Stager2 {
+  static constexpr int kPer = (BATCH + kT2 - 1) / kT2;
+  uint32_t vk[kPer];
+  int loaded;
+  __device__ __forceinline__ void load(const uint32_t* __restrict__ vals, uint32_t first, int cnt) {
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int j = threadIdx.x + r * kT2;
+      vk[r] = j < cnt ? vals[first + j] : 0u;
+    }
+    loaded = cnt;
+  }
+  __device__ __forceinline__ void issue(float4* buf, const float4* __restrict__ raster) const {
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int j = threadIdx.x + r * kT2;
+      if (j < loaded) {
+        const float4* src = raster + (size_t)vk[r] * kRec;
+        cp_async16_2(buf + kSRec2 * j + 0, src + 0);
+        cp_async16_2(buf + kSRec2 * j + 1, src + 1);
+        cp_async16_2(buf + kSRec2 * j + 2, src + 2);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+  }
+};
+
+// ---------------------------------------------------------------------------------------
+// per-tile context
+// ---------------------------------------------------------------------------------------
+struct Tile2 {
+  int64_t tile;
+  int view;
+  potr_view_info vi;
+  int tx, ty;
+  int px, py;          // the lane's first pixel; the second is (px, py + 1)
+  bool in0, in1;       // inside the image
+  float fx, fy0, fy1;  // pixel centres
+  float bx0, by0;      // the warp block's first pixel centre (its rectangle: + [0, 7] in x and y)
+  uint32_t s, e;       // the tile's list
+};
+
+__device__ __forceinline__ Tile2 tile2_ctx(const potr_view_info* __restrict__ info, int n_views,
+                                           const uint32_t* __restrict__ ranges, const potr_raster_config& cfg,
+                                           int64_t tile) {
+  Tile2 c;
+  c.tile = tile;
+  c.view = view_of_tile(info, n_views, tile);
+  c.vi = info[c.view];
+  const int64_t local = tile - c.vi.tile_base;
+  c.ty = (int)(local / c.vi.tiles_x);
+  c.tx = (int)(local - (int64_t)c.ty * c.vi.tiles_x);
+  const int lane = (int)(threadIdx.x & 31), warp = (int)(threadIdx.x >> 5), bx_n = cfg.tile_w / 8;
+  const int bx = c.tx * cfg.tile_w + (warp % bx_n) * 8, by = c.ty * cfg.tile_h + (warp / bx_n) * 8;
+  c.px = bx + (lane & 7);
+  c.py = by + 2 * (lane >> 3);
+  c.in0 = c.px < c.vi.width && c.py < c.vi.height;
+  c.in1 = c.px < c.vi.width && c.py + 1 < c.vi.height;
+  c.fx = (float)c.px + 0.5f;
+  c.fy0 = (float)c.py + 0.5f;
+  c.fy1 = (float)(c.py + 1) + 0.5f;
+  c.bx0 = (float)bx + 0.5f;
+  c.by0 = (float)by + 0.5f;
+  c.s = ranges[2 * tile];
+  c.e = ranges[2 * tile + 1];
+  return c;
+}
+
+// May the splat of record (r0, r1) pass the prefilter (log2 G >= r1.z) at some pixel centre of
+// the warp's 8 x 8 block?  The exponent A u^2 + B u v + C v^2 (u = x - mx, v = y - my) is
+// maximised over the block's pixel-centre rectangle: on each edge a concave parabola, largest
+// at its vertex clamped to the edge, and 0 at the splat centre when it lies inside.  The
+// maximum is raised by 1e-4 x the largest term magnitude + 1e-3, which covers the binary32
+// rounding of this maximum and of any pixel's own exponent many times over, so a false answer
+// means alpha < alpha_min at all 64 pixels.
+__device__ __forceinline__ bool block_may_pass(const float4& r0, const float4& r1, float bx0, float by0) {
+  const float A = r0.z, B = r0.w, C = r1.x, thr = r1.z;
+  if (!(thr < INFINITY)) return false;                              // o = 0: never passes
+  if (!(thr > -INFINITY) || !(A < 0.0f) || !(C < 0.0f)) return true;  // no bound: keep
+  const float ux0 = bx0 - r0.x, ux1 = ux0 + 7.0f, vy0 = by0 - r0.y, vy1 = vy0 + 7.0f;
+  const float ku = -B / (2.0f * A), kv = -B / (2.0f * C);
+  const float u0 = fminf(fmaxf(ku * vy0, ux0), ux1), u1 = fminf(fmaxf(ku * vy1, ux0), ux1);
+  const float v0 = fminf(fmaxf(kv * ux0, vy0), vy1), v1 = fminf(fmaxf(kv * ux1, vy0), vy1);
+  float pmax = fmaxf(fmaxf((A * u0 + B * vy0) * u0 + C * vy0 * vy0, (A * u1 + B * vy1) * u1 + C * vy1 * vy1),
+                     fmaxf((A * ux0 + B * v0) * ux0 + C * v0 * v0, (A * ux1 + B * v1) * ux1 + C * v1 * v1));
+  if (ux0 <= 0.0f && ux1 >= 0.0f && vy0 <= 0.0f && vy1 >= 0.0f) pmax = fmaxf(pmax, 0.0f);
+  const float um = fmaxf(fabsf(ux0), fabsf(ux1)), vm = fmaxf(fabsf(vy0), fabsf(vy1));
+  const float mag = fabsf(A) * um * um + fabsf(B) * um * vm + fabsf(C) * vm * vm;
+  return pmax + (1e-4f * mag + 1e-3f) >= thr;
+}
+
+// Forward walk (Section 3, Eqs. 2-4) of the tile list for the lane's two pixels: colour,
+// final transmittance and n_last (one past the last composited list position) of each.
+// smem holds two batches of records ([2][BATCH][kSRec2]); the gathers of batch k + 1 are in
+// flight while the CTA composites batch k.
+template <int BATCH>
+__device__ __forceinline__ void forward_walk2(float4* smem, const float4* __restrict__ raster,
+                                              const uint32_t* __restrict__ vals, const Tile2& c,
+                                              const potr_raster_config& cfg, f2_t (&C)[3], f2_t& T,
+                                              uint32_t& last0, uint32_t& last1) {
+  C[0] = C[1] = C[2] = f2s(0.0f);
+  T = f2s(1.0f);
+  last0 = last1 = 0;
+  bool done0 = !c.in0, done1 = !c.in1;
+  const int lane = threadIdx.x & 31;
+  const uint32_t len = c.e - c.s;
+  const uint32_t nb = (len + BATCH - 1) / BATCH;
+  Stager2<BATCH> st;
+  if (nb > 0) {
+    st.load(vals, c.s, (int)min((uint32_t)BATCH, len));
+    st.issue(smem, raster);
+  }
+  if (nb > 1) st.load(vals, c.s + BATCH, (int)min((uint32_t)BATCH, len - BATCH));
+  for (uint32_t k = 0; k < nb; ++k) {
+    if (__syncthreads_and(done0 && done1)) break;  // also: batch k - 1 (and its buffer) fully consumed
+    const uint32_t pos0 = k * BATCH;
+    const int cnt = (int)min((uint32_t)BATCH, len - pos0);
+    const float4* buf = smem + kSRec2 * BATCH * (k & 1);
+    if (k + 1 < nb) {
+      st.issue(smem + kSRec2 * BATCH * ((k + 1) & 1), raster);
+      cp_async_wait2<1>();
+      if (k + 2 < nb) st.load(vals, c.s + pos0 + 2 * BATCH, (int)min((uint32_t)BATCH, len - pos0 - 2 * BATCH));
+    } else {
+      cp_async_wait2<0>();
+    }
+    __syncthreads();  // every thread's copies of batch k are visible
+    for (int g = 0; g < cnt; g += 32) {
+      if (__all_sync(0xffffffffu, done0 && done1)) break;
+      const int jl = g + lane;
+      const bool cand = jl < cnt && block_may_pass(buf[kSRec2 * jl], buf[kSRec2 * jl + 1], c.bx0, c.by0);
+      uint32_t m = __ballot_sync(0xffffffffu, cand);
+      while (m) {
+        const int j = g + __ffs(m) - 1;
+        m &= m - 1;
+        if (done0 && done1) continue;
+        const float4 r0 = buf[kSRec2 * j];
+        const float4 r1 = buf[kSRec2 * j + 1];
+        const f2_t d2x = f2s(__fsub_rn(c.fx, r0.x));
+        const f2_t d2y = sub2(f2(c.fy0, c.fy1), f2s(r0.y));
+        const f2_t p2 = pair_exponent2(r0.z, r0.w, r1.x, d2x, d2y);
+        float p0, p1;
+        f2split(p2, p0, p1);
+        const bool pass0 = !done0 && p0 >= r1.z, pass1 = !done1 && p1 >= r1.z;
+        if (!(pass0 || pass1)) continue;  // alpha < alpha_min certainly (prefilter with margin)
+        const f2_t a2 = mul2(f2s(r1.y), exp2r2(p2));
+        float a0, a1;
+        f2split(a2, a0, a1);
+        a0 = fminf(cfg.alpha_max, a0);
+        a1 = fminf(cfg.alpha_max, a1);
+        bool ok0 = pass0 && a0 >= cfg.alpha_min, ok1 = pass1 && a1 >= cfg.alpha_min;
+        const f2_t aa = f2(a0, a1);
+        const f2_t Tn2 = fma2(sub2(f2s(0.0f), aa), T, T);  // T (1 - alpha) as fma(-alpha, T, T)
+        float Tn0, Tn1, T0, T1;
+        f2split(Tn2, Tn0, Tn1);
+        f2split(T, T0, T1);
+        if (ok0 && Tn0 < cfg.t_min) {
+          done0 = true;
+          ok0 = false;
+        }
+        if (ok1 && Tn1 < cfg.t_min) {
+          done1 = true;
+          ok1 = false;
+        }
+        if (!(ok0 || ok1)) continue;
+        const float4 r2 = buf[kSRec2 * j + 2];
+        const f2_t w2 = f2(ok0 ? a0 * T0 : 0.0f, ok1 ? a1 * T1 : 0.0f);  // T alpha, 0 where not taken
+        C[0] = fma2(w2, f2s(r2.x), C[0]);
+        C[1] = fma2(w2, f2s(r2.y), C[1]);
+        C[2] = fma2(w2, f2s(r2.z), C[2]);
+        T = f2(ok0 ? Tn0 : T0, ok1 ? Tn1 : T1);
+        if (ok0) last0 = pos0 + (uint32_t)j + 1;
+        if (ok1) last1 = pos0 + (uint32_t)j + 1;
+      }
+    }
+  }
+  cp_async_wait2<0>();  // after an early exit the next batch may still be landing
+}
+
+}  // namespace
+}  // namespace potr

@@ -150,12 +150,8 @@ class RemovalEffectFrame:
             B.potr_tile_schedule(self.frame, self.ranges, self.order, self.sched_ws, stream)
 
     def render(self, images=None, t_final=None, n_last=None, stream=None):
-        masks = None
-        if t_final is not None:  # a backward pass with stored transmittance may follow: keep the warp masks
-            masks = self.warp_masks
-            self.pool.masks_owner = (id(self), getattr(self, "_sort_gen", 0))
         B.potr_render(self.views, self.frame, self.cfg, self.n, self.vals, self.ranges, images, t_final, n_last, stream,
-                      order=self.order, warp_masks=masks)
+                      order=self.order)
 
     def removal_effect(self, targets, dmse, importance=None, n_views_total=None, dsse_view=None, images=None,
                        stream=None, imp_view=None):

@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import assert_close_abs_rel, oracle_cfg
+from gpu_util import assert_close_abs_rel, assert_removal_close, oracle_cfg
 
 pytestmark = pytest.mark.gpu
 
@@ -63,9 +63,14 @@ def test_chunking_and_graph_replay_give_the_same_bits():
     for r in results[1:]:
         assert np.array_equal(r[0], results[0][0]) and np.array_equal(r[1], results[0][1])
     # and the oracle agrees on the whole thing
-    want, wimp = oracle.dmse(sc, cams, oracle_cfg(dict(tile_w=16, tile_h=16)), tg)
+    ocfg = oracle_cfg(dict(tile_w=16, tile_h=16))
+    want, wimp = oracle.dmse(sc, cams, ocfg, tg)
+    mag = np.zeros(sc.n)
+    for cam, t in zip(cams, tg):
+        pv = oracle.prepare_view(sc, cam, ocfg)
+        mag += oracle.removal_magnitude(pv, pv["vals"], pv["ranges"], cam, ocfg, t)[0] / (3.0 * cam.pixels) / len(cams)
     scale = 1.0 / (3.0 * min(c.pixels for c in cams))
-    assert_close_abs_rel(results[0][0], want, 1e-4, 1e-7 * scale, "dMSE")
+    assert_removal_close(results[0][0], want, mag, "dMSE", floor=1e-7 * scale)
     assert_close_abs_rel(results[0][1], wimp, 1e-4, 1e-7 * scale, "importance")
 
 
@@ -150,5 +155,6 @@ def test_batched_workload_sampled_views_and_tiles():
         d, i, idse, iimp = oracle.removal_effect(pv, lvv, lr, cam, ocfg, tg[v], tile_mask=mask, per_instance=True)
         sel = np.concatenate([np.arange(lr[t, 0], lr[t, 1]) for t in pick]).astype(np.int64)
         got = fr.inst_dse[: fr.instance_count()].cpu().numpy()
-        assert_close_abs_rel(got[start + le[sel].astype(np.int64)], idse[sel], 1e-4, 1e-7, f"tile partials view {v}")
+        _, imag = oracle.removal_magnitude(pv, lvv, lr, cam, ocfg, tg[v], tile_mask=mask)
+        assert_removal_close(got[start + le[sel].astype(np.int64)], idse[sel], imag[sel], f"tile partials view {v}")
         assert np.count_nonzero(idse[sel]) > 100

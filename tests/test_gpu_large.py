@@ -12,7 +12,8 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import assert_close_abs_rel, assert_close_rel, frame_outputs, oracle_cfg, pack_targets, view_slice
+from gpu_util import (assert_close_abs_rel, assert_close_rel, assert_removal_close, frame_outputs, oracle_cfg, pack_targets,
+                      view_slice)
 
 pytestmark = pytest.mark.gpu
 
@@ -68,7 +69,8 @@ def _check_view(fr, res, scene, cam, v, tg, rng, n_tiles_sampled=20):
     d, i, idse, iimp = oracle.removal_effect(pv, lv, lr, cam, ocfg, tg[v], tile_mask=mask, per_instance=True)
     sel = np.concatenate([np.arange(lr[t, 0], lr[t, 1]) for t in pick]).astype(np.int64)
     slots = s0 + le[sel].astype(np.int64)
-    assert_close_abs_rel(res["inst_dse"][slots], idse[sel], 1e-4, 1e-7, f"tile partials view {v}")
+    _, imag = oracle.removal_magnitude(pv, lv, lr, cam, ocfg, tg[v], tile_mask=mask)
+    assert_removal_close(res["inst_dse"][slots], idse[sel], imag[sel], f"tile partials view {v}")
     assert_close_abs_rel(res["inst_imp"][slots], iimp[sel], 1e-4, 1e-7, f"tile importance view {v}")
     assert np.count_nonzero(idse[sel]) > 200
 

@@ -7,7 +7,8 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import assert_close_abs_rel, assert_close_rel, build_frame, frame_outputs, oracle_cfg, pack_targets, view_slice
+from gpu_util import (assert_close_rel, assert_removal_close, build_frame, frame_outputs, oracle_cfg, pack_targets,
+                      view_slice)
 
 pytestmark = pytest.mark.gpu
 
@@ -17,16 +18,22 @@ CFG = dict(tile_w=16, tile_h=16, batch=128)
 def _poisoned():
     """5,000 splats in front of two cameras; six splats made non-finite in six ways: a NaN mean,
     an infinite log-scale, a NaN quaternion component, a -inf and a NaN opacity logit, and an
-    infinite SH coefficient of a splat that both views see."""
+    infinite SH coefficient of a splat that both views see (so that its coefficients are read)."""
     sc = synth.uniform_cube_scene(5000, 77)
     cams = [synth.look_at_camera((0.0, 0.3, -3.0), 200, 150), synth.look_at_camera((2.5, -0.2, -1.5), 96, 160)]
-    bad = np.array([10, 20, 30, 40, 50, 60])
+    ocfg = oracle_cfg(CFG)
+    seen = np.ones(sc.n, bool)
+    for cam in cams:
+        seen &= oracle.prepare_view(sc, cam, ocfg)["touched"] > 0
+    sh_bad = int(np.nonzero(seen)[0][5])
+    bad = np.array(sorted({10, 20, 30, 40, 50, sh_bad}))
+    assert bad.size == 6
     sc.means[1, 10] = np.nan
     sc.log_scales[2, 20] = np.inf
     sc.quats[3, 30] = np.nan
     sc.opacity_logits[40] = -np.inf
     sc.opacity_logits[50] = np.nan
-    sc.sh[5, 1, 60] = np.inf
+    sc.sh[5, 1, sh_bad] = np.inf
     return sc, cams, bad
 
 
@@ -40,11 +47,6 @@ def test_nonfinite_splats_are_culled_and_reported():
     sc, cams, bad = _poisoned()
     clean, keep = _clean_subset(sc, bad)
     ocfg = oracle_cfg(CFG)
-    # the SH-poisoned splat must be visible, else its coefficients are never read
-    for cam in cams:
-        pv = oracle.prepare_view(synth.Scene(sc.means, sc.log_scales, sc.quats, sc.opacity_logits,
-                                             np.nan_to_num(sc.sh, posinf=0.0)), cam, ocfg)
-        assert pv["touched"][60] > 0
     fr = build_frame(sc, cams, **CFG)
     code, count = fr.nonfinite()
     assert code == oracle_status_numeric() and count == bad.size
@@ -67,7 +69,8 @@ def test_nonfinite_splats_are_culled_and_reported():
         d, i = oracle.removal_effect(pv, pv["vals"], pv["ranges"], cam, ocfg, tg[v])
         got = res["dsse_view"][v * sc.n:(v + 1) * sc.n]
         assert np.all(got[bad] == 0.0)
-        assert_close_abs_rel(got[keep], d, 1e-4, 1e-7, f"dSSE view {v}")
+        mag, _ = oracle.removal_magnitude(pv, pv["vals"], pv["ranges"], cam, ocfg, tg[v])
+        assert_removal_close(got[keep], d, mag, f"dSSE view {v}")
     assert np.all(res["dmse"][bad] == 0.0) and np.all(res["importance"][bad] == 0.0)
     assert np.all(np.isfinite(res["dmse"])) and np.all(np.isfinite(res["image"]))
     assert n_clean == sc.n - bad.size

@@ -13,8 +13,8 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import (assert_close_abs_rel, assert_close_rel, build_frame, check_against_whole_rect, frame_outputs,
-                      oracle_cfg, pack_targets, unpack_raster, view_slice)
+from gpu_util import (assert_close_abs_rel, assert_close_rel, assert_removal_close, build_frame,
+                      check_against_whole_rect, frame_outputs, oracle_cfg, pack_targets, unpack_raster, view_slice)
 
 pytestmark = pytest.mark.gpu
 
@@ -180,20 +180,23 @@ def _check_removal(fr, scene, cams, cfg, ovs, res, targets):
     n = scene.n
     dmse = np.zeros(n)
     imp = np.zeros(n)
+    mag_dmse = np.zeros(n)
     for v, (cam, pv) in enumerate(zip(cams, ovs)):
         lv = _local_vals(pv, v, n)
         d, i, idse, iimp = oracle.removal_effect(pv, lv, pv["ranges"], cam, ocfg, targets[v], per_instance=True)
-        assert_close_abs_rel(res["dsse_view"][v * n:(v + 1) * n], d, DSE_REL, DSE_ABS, f"dSSE view {v}")
+        mag, imag = oracle.removal_magnitude(pv, lv, pv["ranges"], cam, ocfg, targets[v])
+        assert_removal_close(res["dsse_view"][v * n:(v + 1) * n], d, mag, f"dSSE view {v}")
         # per (tile, splat) partial sums, matched through the emission index
         base = int(sum(o["keys"].size for o in ovs[:v]))
         slots = base + pv["emit"].astype(np.int64)
-        assert_close_abs_rel(res["inst_dse"][slots], idse, DSE_REL, DSE_ABS, f"tile partials view {v}")
+        assert_removal_close(res["inst_dse"][slots], idse, imag, f"tile partials view {v}")
         if res.get("inst_imp") is not None:
             assert_close_abs_rel(res["inst_imp"][slots], iimp, DSE_REL, DSE_ABS, f"tile importance view {v}")
         dmse += d / (3.0 * cam.pixels) / len(cams)
         imp += i / float(cam.pixels) / len(cams)
+        mag_dmse += mag / (3.0 * cam.pixels) / len(cams)
     scale = 1.0 / (3.0 * min(c.pixels for c in cams))
-    assert_close_abs_rel(res["dmse"], dmse, DSE_REL, DSE_ABS * scale, "dMSE")
+    assert_removal_close(res["dmse"], dmse, mag_dmse, "dMSE", floor=DSE_ABS * scale)
     if res.get("importance") is not None:
         assert_close_abs_rel(res["importance"], imp, DSE_REL, DSE_ABS * scale, "importance")
     assert np.count_nonzero(res["dmse"]) > 0.3 * n

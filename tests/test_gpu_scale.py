@@ -11,8 +11,8 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import (assert_close_abs_rel, assert_close_rel, build_frame, check_against_whole_rect, frame_outputs,
-                      oracle_cfg, unpack_raster, view_slice)
+from gpu_util import (assert_close_abs_rel, assert_close_rel, assert_removal_close, build_frame,
+                      check_against_whole_rect, frame_outputs, oracle_cfg, unpack_raster, view_slice)
 
 pytestmark = pytest.mark.gpu
 
@@ -110,7 +110,8 @@ def test_fullsize_sampled_tiles(big):
         d, i, idse, iimp = oracle.removal_effect(pv, ov, orng, cam, ocfg, tg[v], tile_mask=mask, per_instance=True)
         sel = np.concatenate([np.arange(orng[t, 0], orng[t, 1]) for t in pick]).astype(np.int64)
         slots = int(counts[:v].sum()) + oe[sel].astype(np.int64)
-        assert_close_abs_rel(res["inst_dse"][slots], idse[sel], 1e-4, 1e-7, f"tile partials view {v}")
+        _, imag = oracle.removal_magnitude(pv, ov, orng, cam, ocfg, tg[v], tile_mask=mask)
+        assert_removal_close(res["inst_dse"][slots], idse[sel], imag[sel], f"tile partials view {v}")
         assert_close_abs_rel(res["inst_imp"][slots], iimp[sel], 1e-4, 1e-7, f"tile importance view {v}")
         assert np.count_nonzero(idse[sel]) > 1000
 

@@ -780,3 +780,27 @@ def test_threads_over_tiles_change_no_bit(tiny):
         for a, b in zip(o, outs[0]):
             assert np.array_equal(a, b)
     assert np.count_nonzero(outs[0][4]) > 1000
+
+
+def test_removal_magnitude_bounds_the_removal_effect(tiny):
+    """The rounding scale of the removal effect (oracle.removal_magnitude, a tolerance quantity):
+    at least |dSSE_k| for every splat, its per-instance sums add up to the per-splat ones, and for
+    one splat against a zero target (PD = -alpha c, dSE = -(alpha c)^2 per channel) it is exactly
+    four times |dSSE| (|T alpha c| (2 |PD| + 2 |c|) = 4 (alpha c)^2)."""
+    cam = tiny.cameras[0]
+    v = oracle.prepare_view(tiny.scene, cam, CFG)
+    img, *_ = oracle.render(v, v["vals"], v["ranges"], cam, CFG)
+    tg = (img + synth.target_noise(img.shape, 0.02, 1, 0)).astype(np.float32)
+    d, _ = oracle.removal_effect(v, v["vals"], v["ranges"], cam, CFG, tg)
+    m, im = oracle.removal_magnitude(v, v["vals"], v["ranges"], cam, CFG, tg)
+    assert np.all(m >= np.abs(d) * (1 - 1e-12)) and np.count_nonzero(m) > 500
+    per_splat = np.zeros_like(m)
+    np.add.at(per_splat, v["vals"].astype(np.int64), im)
+    assert np.allclose(per_splat, m, rtol=1e-12, atol=0)
+    one = _scene(np.zeros((3, 1)), np.full((3, 1), -2.5), np.array([[1.0], [0], [0], [0]]), np.array([2.0]))
+    c1 = synth.look_at_camera((0.0, 0.0, -3.0), 48, 40)
+    v1 = oracle.prepare_view(one, c1, CFG)
+    z = np.zeros((3, 40, 48), np.float32)
+    d1, _ = oracle.removal_effect(v1, v1["vals"], v1["ranges"], c1, CFG, z)
+    m1, _ = oracle.removal_magnitude(v1, v1["vals"], v1["ranges"], c1, CFG, z)
+    assert d1[0] < 0 and m1[0] == pytest.approx(-4.0 * d1[0], rel=1e-12)
