@@ -29,22 +29,25 @@
 namespace potr {
 namespace {
 
-template <int BATCH>
+// Compositing by independent warps: each takes (tile, 8 x 8 block) items and walks the tile's
+// list on its own (no barrier between the warps of a CTA).
 __global__ void __launch_bounds__(kT2, 8) render_kernel(const float4* __restrict__ raster,
                                                      const uint32_t* __restrict__ vals,
                                                      const uint32_t* __restrict__ ranges,
                                                      const potr_view_info* __restrict__ info, int n_views,
-                                                     potr_raster_config cfg, float* __restrict__ images,
-                                                     float* __restrict__ t_final, uint32_t* __restrict__ n_last,
-                                                     TileQueue queue) {
-  extern __shared__ float4 smem[];  // two batches of records
-  __shared__ uint32_t s_slot;
+                                                     int64_t total_tiles, potr_raster_config cfg,
+                                                     float* __restrict__ images, float* __restrict__ t_final,
+                                                     uint32_t* __restrict__ n_last, TileQueue queue) {
+  extern __shared__ float4 smem[];
+  float4* ring = smem + (threadIdx.x >> 5) * kWarpSmemF4;
+  int64_t stride_next = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   int64_t tile;
-  for (bool first = true; next_tile(queue, &s_slot, first, tile); first = false) {
-    const Tile2 c = tile2_ctx(info, n_views, ranges, cfg, tile);
+  int blk;
+  while (next_block_item(queue, total_tiles, stride_next, tile, blk)) {
+    const Tile2 c = tile2_block_ctx(info, n_views, ranges, cfg, tile, blk);
     f2_t C[3], T;
     uint32_t last0, last1;
-    forward_walk2<BATCH>(smem, raster, vals, c, cfg, C, T, last0, last1);
+    forward_walk_w(ring, raster, vals, c, cfg, C, T, last0, last1);
     const int64_t plane = (int64_t)c.vi.width * c.vi.height;
     const int64_t pix = c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
     float* im = images ? images + 3 * c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px : nullptr;
@@ -52,11 +55,16 @@ __global__ void __launch_bounds__(kT2, 8) render_kernel(const float4* __restrict
     for (int h = 0; h < 2; ++h) {
       if (!(h ? c.in1 : c.in0)) continue;
       const int64_t row = h ? c.vi.width : 0;
+      float lo0, hi0;
       if (im) {
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) im[row + ch * plane] = h ? f2hi(C[ch]) : f2lo(C[ch]);
+        for (int ch = 0; ch < 3; ++ch) {
+          f2split(C[ch], lo0, hi0);
+          im[row + ch * plane] = h ? hi0 : lo0;
+        }
       }
-      if (t_final) t_final[pix + row] = h ? f2hi(T) : f2lo(T);
+      f2split(T, lo0, hi0);
+      if (t_final) t_final[pix + row] = h ? hi0 : lo0;
       if (n_last) n_last[pix + row] = h ? last1 : last0;
     }
   }
@@ -86,7 +94,7 @@ constexpr int kChunk = 8;  // splats per warp transpose-sum
 
 template <int BATCH, bool IMP>
 constexpr size_t removal_smem_bytes() {
-  return sizeof(float4) * 2 * kSRec2 * BATCH + sizeof(float) * kW2 * BATCH * (IMP ? 2 : 1);
+  return sizeof(float4) * (2 * kSRec2 + kERec) * BATCH + sizeof(float) * kW2 * BATCH * (IMP ? 2 : 1);
 }
 
 template <int BATCH, bool IMP>
@@ -100,7 +108,8 @@ __global__ void __launch_bounds__(kT2, 8) removal_kernel(const float4* __restric
                                                        const uint32_t* __restrict__ offsets, TileQueue queue) {
   extern __shared__ float4 dyn[];
   float4* smem = dyn;                                                // [2][BATCH][kSRec2] raster records
-  float* red_d = reinterpret_cast<float*>(dyn + 2 * kSRec2 * BATCH);  // [kW2][BATCH] warp sums of dSE
+  float4* ex = dyn + 2 * kSRec2 * BATCH;                             // [BATCH][kERec] expanded records
+  float* red_d = reinterpret_cast<float*>(ex + kERec * BATCH);       // [kW2][BATCH] warp sums of dSE
   float* red_i = red_d + kW2 * BATCH;                                // [kW2][BATCH] warp sums of T alpha
   __shared__ uint32_t max_last_w[kW2];
   __shared__ uint32_t s_slot;
@@ -110,7 +119,7 @@ __global__ void __launch_bounds__(kT2, 8) removal_kernel(const float4* __restric
     const Tile2 c = tile2_ctx(info, n_views, ranges, cfg, tile);
     f2_t C[3], T;
     uint32_t last0, last1;
-    forward_walk2<BATCH>(smem, raster, vals, c, cfg, C, T, last0, last1);
+    forward_walk2<BATCH>(smem, ex, raster, vals, c, cfg, C, T, last0, last1);
 
     // 2 (c - c_t) per channel and pixel (0 outside the image)
     f2_t e2[3];
@@ -135,6 +144,7 @@ __global__ void __launch_bounds__(kT2, 8) removal_kernel(const float4* __restric
     uint32_t max_last = 0;
 #pragma unroll
     for (int w = 0; w < kW2; ++w) max_last = max(max_last, max_last_w[w]);
+    const f2_t fx2 = f2s(c.fx), fy2 = f2(c.fy0, c.fy1);
 
     // Back to front over list positions [0, max_last): T_i = T_{i+1} / (1 - alpha_i),
     // S = sum of T_j alpha_j c_j over the composited j > i.  Each warp visits the splats its
@@ -173,13 +183,13 @@ __global__ void __launch_bounds__(kT2, 8) removal_kernel(const float4* __restric
         my_d[j] = 0.0f;
         if (IMP) my_i[j] = 0.0f;
       }
-      __syncthreads();  // every thread's copies of batch k are visible
+      expand_own<BATCH>(buf, ex, cnt);
+      __syncthreads();  // every thread's expanded records of batch k are visible
       for (int ghi = cnt; ghi > 0; ghi -= 32) {
         const int glo = ghi > 32 ? ghi - 32 : 0;
         if (lo + (uint32_t)glo >= warp_last) continue;  // warp-uniform: nothing composited here
         const int jl = glo + lane;
-        const bool cand = jl < ghi && lo + (uint32_t)jl < warp_last &&
-                          block_may_pass(buf[kSRec2 * jl], buf[kSRec2 * jl + 1], c.bx0, c.by0);
+        const bool cand = jl < ghi && lo + (uint32_t)jl < warp_last && block_may_pass_e(ex + kERec * jl, c.bx0, c.by0);
         uint32_t m = __ballot_sync(0xffffffffu, cand);
         while (m) {
           float d[kChunk], im[kChunk];
@@ -195,54 +205,49 @@ __global__ void __launch_bounds__(kT2, 8) removal_kernel(const float4* __restric
               const int j = glo + b;
               if (lane == u) mypos = j;
               const uint32_t pos = lo + (uint32_t)j;
-              const bool in0 = pos < last0, in1 = pos < last1;
-              if (in0 || in1) {
-                const float4 r0 = buf[kSRec2 * j];
-                const float4 r1 = buf[kSRec2 * j + 1];
-                const f2_t p2 = pair_exponent2(r0.z, r0.w, r1.x, f2s(__fsub_rn(c.fx, r0.x)),
-                                               sub2(f2(c.fy0, c.fy1), f2s(r0.y)));
-                float p0, p1;
-                f2split(p2, p0, p1);
-                const bool pass0 = in0 && p0 >= r1.z, pass1 = in1 && p1 >= r1.z;
-                if (pass0 || pass1) {
-                  float a0, a1;
-                  f2split(mul2(f2s(r1.y), exp2r2(p2)), a0, a1);
-                  a0 = fminf(cfg.alpha_max, a0);
-                  a1 = fminf(cfg.alpha_max, a1);
-                  const bool ok0 = pass0 && a0 >= cfg.alpha_min, ok1 = pass1 && a1 >= cfg.alpha_min;
-                  if (ok0 || ok1) {
-                    const float4 r2 = buf[kSRec2 * j + 2];
-                    // a pixel that does not take the splat: alpha 0 and 1 / (1 - alpha) = 1, so
-                    // its T, S and dSE do not change (every update adds or scales by exact zeros
-                    // and ones)
-                    const f2_t ae = f2(ok0 ? a0 : 0.0f, ok1 ? a1 : 0.0f);
-                    const f2_t rcp = f2(ok0 ? __fdividef(1.0f, 1.0f - a0) : 1.0f,
-                                        ok1 ? __fdividef(1.0f, 1.0f - a1) : 1.0f);
-                    T = mul2(T, rcp);                      // T_i = T_{i+1} / (1 - alpha_i)
-                    const f2_t w = mul2(ae, T);            // T_i alpha_i
-                    const f2_t ratio = mul2(ae, rcp);      // alpha_i / (1 - alpha_i)
-                    const f2_t nw = sub2(f2s(0.0f), w);    // -T_i alpha_i (exact)
-                    const f2_t nwc0 = mul2(nw, f2s(r2.x)), nwc1 = mul2(nw, f2s(r2.y)), nwc2 = mul2(nw, f2s(r2.z));
-                    // PD = alpha / (1 - alpha) S - T alpha c, one rounding per channel
-                    const f2_t pd0 = fma2(ratio, S[0], nwc0);
-                    const f2_t pd1 = fma2(ratio, S[1], nwc1);
-                    const f2_t pd2 = fma2(ratio, S[2], nwc2);
-                    f2_t dse = mul2(pd0, add2(pd0, e2[0]));  // sum_ch PD (PD + 2 (c - c_t))
-                    dse = fma2(pd1, add2(pd1, e2[1]), dse);
-                    dse = fma2(pd2, add2(pd2, e2[2]), dse);
-                    S[0] = sub2(S[0], nwc0);  // S + T alpha c
-                    S[1] = sub2(S[1], nwc1);
-                    S[2] = sub2(S[2], nwc2);
-                    float x0, x1;
-                    f2split(dse, x0, x1);
-                    d[u] = x0 + x1;
-                    if (IMP) {
-                      f2split(w, x0, x1);
-                      im[u] = x0 + x1;
-                    }
-                    any = true;
-                  }
+              const float4* e = ex + kERec * j;
+              f2_t o2;
+              float thr;
+              const f2_t p2 = exponent_e(e, fx2, fy2, o2, thr);
+              float p0, p1;
+              f2split(p2, p0, p1);
+              const bool pass0 = pos < last0 && p0 >= thr, pass1 = pos < last1 && p1 >= thr;
+              if (__any_sync(0xffffffffu, pass0 || pass1)) {  // warp-uniform: branch-free below
+                float a0, a1;
+                f2split(mul2(o2, exp2r2(p2)), a0, a1);
+                a0 = fminf(cfg.alpha_max, a0);
+                a1 = fminf(cfg.alpha_max, a1);
+                const bool ok0 = pass0 && a0 >= cfg.alpha_min, ok1 = pass1 && a1 >= cfg.alpha_min;
+                // a pixel that does not take the splat: alpha 0 and 1 / (1 - alpha) = 1, so its
+                // T, S and dSE do not change (every update adds or scales by exact zeros and ones)
+                const float q0 = __fdividef(1.0f, 1.0f - a0), q1 = __fdividef(1.0f, 1.0f - a1);
+                const f2_t ae = f2(ok0 ? a0 : 0.0f, ok1 ? a1 : 0.0f);
+                const f2_t rcp = f2(ok0 ? q0 : 1.0f, ok1 ? q1 : 1.0f);
+                T = mul2(T, rcp);                      // T_i = T_{i+1} / (1 - alpha_i)
+                const f2_t w = mul2(ae, T);            // T_i alpha_i
+                const f2_t ratio = mul2(ae, rcp);      // alpha_i / (1 - alpha_i)
+                const f2_t nw = sub2(f2s(0.0f), w);    // -T_i alpha_i (exact)
+                const ulonglong2 q3 = reinterpret_cast<const ulonglong2*>(e)[3];
+                const ulonglong2 q4 = reinterpret_cast<const ulonglong2*>(e)[4];
+                const f2_t nwc0 = mul2(nw, q3.y), nwc1 = mul2(nw, q4.x), nwc2 = mul2(nw, q4.y);
+                // PD = alpha / (1 - alpha) S - T alpha c, one rounding per channel
+                const f2_t pd0 = fma2(ratio, S[0], nwc0);
+                const f2_t pd1 = fma2(ratio, S[1], nwc1);
+                const f2_t pd2 = fma2(ratio, S[2], nwc2);
+                f2_t dse = mul2(pd0, add2(pd0, e2[0]));  // sum_ch PD (PD + 2 (c - c_t))
+                dse = fma2(pd1, add2(pd1, e2[1]), dse);
+                dse = fma2(pd2, add2(pd2, e2[2]), dse);
+                S[0] = sub2(S[0], nwc0);  // S + T alpha c
+                S[1] = sub2(S[1], nwc1);
+                S[2] = sub2(S[2], nwc2);
+                float x0, x1;
+                f2split(dse, x0, x1);
+                d[u] = x0 + x1;
+                if (IMP) {
+                  f2split(w, x0, x1);
+                  im[u] = x0 + x1;
                 }
+                any = true;
               }
             }
           }
@@ -361,15 +366,19 @@ template <int BATCH>
 cudaError_t launch_render(const potr_views* views, const potr_frame* frame, const potr_raster_config& cfg,
                           const uint32_t* vals, const uint32_t* ranges, float* images, float* t_final,
                           uint32_t* n_last, const TileQueue& q, cudaStream_t s) {
-  const size_t smem = sizeof(float4) * 2 * kSRec2 * BATCH;
-  {  // 512-splat batches take exactly 48 KB of dynamic shared memory, beyond the default with the static part
-    cudaError_t e = cudaFuncSetAttribute(render_kernel<BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  const unsigned grid = tile_grid(render_kernel<BATCH>, smem, q, frame->total_tiles, kT2);
+  const size_t smem = sizeof(float4) * kW2 * kWarpSmemF4;
+  // a persistent grid: every CTA that fits on the device at once
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel, kT2, smem);
+  int64_t g = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  const int64_t need = (4 * frame->total_tiles + kW2 - 1) / kW2;
+  if (g > need) g = need;
   tile_timing_begin(s);
-  render_kernel<BATCH><<<grid, kT2, smem, s>>>(reinterpret_cast<const float4*>(views->raster), vals, ranges,
-                                               frame->info, frame->n_views, cfg, images, t_final, n_last, q);
+  render_kernel<<<(unsigned)(g > 0 ? g : 1), kT2, smem, s>>>(reinterpret_cast<const float4*>(views->raster), vals,
+                                                           ranges, frame->info, frame->n_views, frame->total_tiles, cfg,
+                                                           images, t_final, n_last, q);
   tile_timing_end(s);
   note_launches(1);
   return cudaGetLastError();
