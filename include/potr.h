@@ -122,9 +122,10 @@ typedef struct {
  * Per-(view, splat) buffers produced by potr_preprocess and potr_bin_sort (device, caller
  * owned).  raster holds 12 floats (48 bytes) per vk, 16-byte aligned (written for the vk with
  * kept tiles):
- *   [0] mean x  [1] mean y  [2] A  [3] B  [4] C  [5] opacity  [6] prefilter  [7] 0
+ *   [0] mean x  [1] mean y  [2] A  [3] B  [4] C  [5] opacity  [6] prefilter  [7] indefinite
  *   [8] r       [9] g       [10] b [11] rectangle bits (x0 | y0 << 11 | width << 22)
- * where log2 G(dx, dy) = A dx^2 + B dx dy + C dy^2.  cull holds 4 words per vk, 16-byte
+ * where log2 G(dx, dy) = A dx^2 + B dx dy + C dy^2 and [7] is 0 when that form is negative
+ * definite (decided exactly), 1 otherwise.  cull holds 4 words per vk, 16-byte
  * aligned (written for every vk):
  *   [0] kept-tile mask, low word  [1] high word  [2] rectangle bits (as raster [11])
  *   [3] kept tiles | (1 << 31 if every tile is kept)

@@ -217,7 +217,12 @@ __global__ void __launch_bounds__(256) project_kernel(const float* __restrict__ 
       const uint32_t rw = pack_rect_word((uint32_t)x0, (uint32_t)y0, (uint32_t)(x1 - x0));
       float4* rec = raster + vk * kRec;
       rec[0] = make_float4(mx, my, __fmul_rn(ca, kA), __fmul_rn(cb, -kLog2e));
-      rec[1] = make_float4(__fmul_rn(cc, kA), o, pthr, 0.0f);
+      // word 7: 0 when the exponent A u^2 + B u v + C v^2 is negative definite (A < 0, C < 0,
+      // 4 A C - B^2 > 0, decided exactly: the products of binary32 values are exact in
+      // binary64), so that it never exceeds a rounding error above 0; 1 otherwise
+      const float qa = __fmul_rn(ca, kA), qb = __fmul_rn(cb, -kLog2e), qc = __fmul_rn(cc, kA);
+      const bool definite = qa < 0.0f && qc < 0.0f && 4.0 * (double)qa * (double)qc - (double)qb * (double)qb > 0.0;
+      rec[1] = make_float4(qc, o, pthr, definite ? 0.0f : 1.0f);
       rec[2] = make_float4(rgb[0], rgb[1], rgb[2], __uint_as_float(rw));
       depth_out[vk] = t[2];
       rect_out[vk] = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));

@@ -207,14 +207,14 @@ __global__ void __launch_bounds__(kT2, 8) removal_kernel(const float4* __restric
               const uint32_t pos = lo + (uint32_t)j;
               const float4* e = ex + kERec * j;
               f2_t o2;
-              float thr;
-              const f2_t p2 = exponent_e(e, fx2, fy2, o2, thr);
+              float thr, indef;
+              const f2_t p2 = exponent_e(e, fx2, fy2, o2, thr, indef);
               float p0, p1;
               f2split(p2, p0, p1);
               const bool pass0 = pos < last0 && p0 >= thr, pass1 = pos < last1 && p1 >= thr;
               if (__any_sync(0xffffffffu, pass0 || pass1)) {  // warp-uniform: branch-free below
                 float a0, a1;
-                f2split(mul2(o2, exp2r2(p2)), a0, a1);
+                f2split(mul2(o2, exp2r2_rec(p2, indef)), a0, a1);
                 a0 = fminf(cfg.alpha_max, a0);
                 a1 = fminf(cfg.alpha_max, a1);
                 const bool ok0 = pass0 && a0 >= cfg.alpha_min, ok1 = pass1 && a1 >= cfg.alpha_min;

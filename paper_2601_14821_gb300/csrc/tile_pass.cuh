@@ -212,11 +212,38 @@ __device__ __forceinline__ bool block_may_pass(const float4& r0, const float4& r
   return pmax + (1e-4f * mag + 1e-3f) >= thr;
 }
 
+// exp2r (potr_device.cuh) on a pair whose arguments are known to lie in [-125, 125], where its
+// clamps do nothing: the same operations in the same order, so the same bits.  The tile walks
+// take it for a record whose exponent is negative definite (record word 7 = 0): a pixel past the
+// prefilter then has log2(alpha_min / o) - 0.01 <= y (> -9, o <= 1) and y at most a few
+// rounding errors above 0, over any tile of its rectangle.  (The half of a pair that did not pass
+// may hold any value; its result is not used.)
+__device__ __forceinline__ f2_t exp2r2_nc(f2_t y) {
+  constexpr float c0 = exp2_coef(0), c1 = exp2_coef(1), c2 = exp2_coef(2), c3 = exp2_coef(3);
+  constexpr float c4 = exp2_coef(4), c5 = exp2_coef(5), c6 = exp2_coef(6);
+  const f2_t magic = f2s(12582912.0f);
+  const f2_t t = add2(y, magic);
+  const f2_t n = sub2(t, magic);
+  const f2_t f = sub2(y, n);
+  f2_t p = fma2(f2s(c6), f, f2s(c5));
+  p = fma2(p, f, f2s(c4));
+  p = fma2(p, f, f2s(c3));
+  p = fma2(p, f, f2s(c2));
+  p = fma2(p, f, f2s(c1));
+  p = fma2(p, f, f2s(c0));
+  float p0, p1, t0, t1;
+  f2split(p, p0, p1);
+  f2split(t, t0, t1);
+  return f2(__int_as_float(__float_as_int(p0) + (__float_as_int(t0) << 23)),
+            __int_as_float(__float_as_int(p1) + (__float_as_int(t1) << 23)));
+}
+
 // ---------------------------------------------------------------------------------------
 // expanded records: once staged, each 48-byte record is rewritten in shared memory as five
 // float4 holding every operand the two pixels share as a packed pair, so one 128-bit shared
 // load gives two packed operands and no register moves build them:
-//   [0] (A, A, B, B)  [1] (C, C, mx, mx)  [2] (my, my, o, o)  [3] (prefilter, 0, r, r)  [4] (g, g, b, b)
+//   [0] (A, A, B, B)  [1] (C, C, mx, mx)  [2] (my, my, o, o)  [3] (prefilter, indefinite, r, r)
+//   [4] (g, g, b, b)
 // ---------------------------------------------------------------------------------------
 constexpr int kERec = 5;
 
@@ -225,7 +252,7 @@ __device__ __forceinline__ void expand_record(const float4* raw, float4* dst) {
   dst[0] = make_float4(r0.z, r0.z, r0.w, r0.w);
   dst[1] = make_float4(r1.x, r1.x, r0.x, r0.x);
   dst[2] = make_float4(r0.y, r0.y, r1.y, r1.y);
-  dst[3] = make_float4(r1.z, 0.0f, r2.x, r2.x);
+  dst[3] = make_float4(r1.z, r1.w, r2.x, r2.x);
   dst[4] = make_float4(r2.y, r2.y, r2.z, r2.z);
 }
 
@@ -235,12 +262,20 @@ __device__ __forceinline__ bool block_may_pass_e(const float4* e, float bx0, flo
   return block_may_pass(make_float4(q1.z, q2.x, q0.x, q0.z), make_float4(q1.x, q2.z, q3.x, 0.0f), bx0, by0);
 }
 
+// exp2r on the pair of an expanded record's exponents: without the clamps for a definite form.
+__device__ __forceinline__ f2_t exp2r2_rec(f2_t y, float indefinite) {
+  return indefinite == 0.0f ? exp2r2_nc(y) : exp2r2(y);
+}
+
 // The two pixels' exponents of an expanded record (pair_exponent on each).
-__device__ __forceinline__ f2_t exponent_e(const float4* e, f2_t fx2, f2_t fy2, f2_t& o2, float& thr) {
+__device__ __forceinline__ f2_t exponent_e(const float4* e, f2_t fx2, f2_t fy2, f2_t& o2, float& thr,
+                                           float& indefinite) {
   const ulonglong2* q = reinterpret_cast<const ulonglong2*>(e);
   const ulonglong2 q0 = q[0], q1 = q[1], q2 = q[2];
   o2 = q2.y;
-  thr = e[3].x;
+  const float2 t = reinterpret_cast<const float2*>(e + 3)[0];
+  thr = t.x;
+  indefinite = t.y;
   const f2_t dx = sub2(fx2, q1.y), dy = sub2(fy2, q2.x);
   const f2_t u = fma2(q0.x, dx, mul2(q0.y, dy));
   const f2_t v = mul2(q1.x, dy);
@@ -255,14 +290,14 @@ __device__ __forceinline__ void forward_visit_e(const float4* e, uint32_t pos, f
                                                 const potr_raster_config& cfg, f2_t (&C)[3], f2_t& T,
                                                 uint32_t& last0, uint32_t& last1, bool& done0, bool& done1) {
   f2_t o2;
-  float thr;
-  const f2_t p2 = exponent_e(e, fx2, fy2, o2, thr);
+  float thr, indef;
+  const f2_t p2 = exponent_e(e, fx2, fy2, o2, thr, indef);
   float p0, p1;
   f2split(p2, p0, p1);
   const bool pass0 = !done0 && p0 >= thr, pass1 = !done1 && p1 >= thr;
   if (!__any_sync(0xffffffffu, pass0 || pass1)) return;  // alpha < alpha_min at every pixel of the warp
   float a0, a1;
-  f2split(mul2(o2, exp2r2(p2)), a0, a1);
+  f2split(mul2(o2, exp2r2_rec(p2, indef)), a0, a1);
   a0 = fminf(cfg.alpha_max, a0);
   a1 = fminf(cfg.alpha_max, a1);
   const bool ok0 = pass0 && a0 >= cfg.alpha_min, ok1 = pass1 && a1 >= cfg.alpha_min;

@@ -6,7 +6,7 @@ import numpy as np
 import oracle
 import synth
 
-RASTER_FIELDS = ("mx", "my", "A", "B", "C", "o", "pthr", "zero", "r", "g", "b", "rectw")
+RASTER_FIELDS = ("mx", "my", "A", "B", "C", "o", "pthr", "indefinite", "r", "g", "b", "rectw")
 CULL_FIELDS = ("mask_lo", "mask_hi", "rectw2", "kept")
 
 
