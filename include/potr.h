@@ -238,18 +238,15 @@ POTR_API potr_status potr_bin_sort(const potr_views* views, const potr_frame* fr
  * c = sum T_k alpha_k c_k over a black background.  Outputs (device, per frame pixel):
  * d_images planar [3][H][W] per view at offset 3 * pixel_base; d_t_final the final
  * transmittance; d_n_last one past the tile-list position of the last composited splat
- * (0 if none).  d_warp_masks ([instance_capacity] bytes, indexed like d_vals): per list entry,
- * which of the tile's eight 8 x 4 pixel blocks the splat may reach with alpha >= alpha_min (a
- * conservative bound; written for the entries the walk reached), for potr_render_backward to
- * reuse.  Any output may be NULL.  d_tile_order (nullable, [total_tiles + 1]) is a tile
- * order from potr_tile_schedule: with it a persistent grid takes tiles in that order (the last
- * word is the work counter, reset by the call); without it one CTA renders each tile.  The
- * order changes scheduling only, never a result.
+ * (0 if none).  Any output may be NULL.  d_tile_order (nullable, [total_tiles + 1]) is a tile
+ * order from potr_tile_schedule: with it the kernel's warps take (tile, 8 x 8 pixel block) items
+ * in that order (the last word is the work counter, reset by the call); without it they take
+ * the items in tile index order.  The order changes scheduling only, never a result.
  */
 POTR_API potr_status potr_render(const potr_views* views, const potr_frame* frame, const potr_raster_config* cfg,
                                  int64_t n, const uint32_t* d_vals, const uint32_t* d_tile_ranges,
                                  uint32_t* d_tile_order, float* d_images, float* d_t_final, uint32_t* d_n_last,
-                                 uint8_t* d_warp_masks, potr_stream_t stream);
+                                 potr_stream_t stream);
 
 /*
  * Removal effect (Section IV-B).  For every pixel: the render above, then a back-to-front
@@ -323,9 +320,7 @@ POTR_API size_t potr_render_backward_workspace_size(int64_t instance_capacity);
  * composites) are those of the forward pass and carry no gradient.  The depth order and the
  * tile rectangle carry none either.
  * Transmittance: pass the forward render's d_t_final and d_n_last (stored), or NULL for both to
- * recompute them inside the kernel (no per-pixel storage).  With stored transmittance,
- * d_warp_masks (nullable) may pass that render's d_warp_masks so the per-block masks are read
- * instead of recomputed (same frame, list and configuration; results are identical).  The same
+ * recompute them inside the kernel (no per-pixel storage; results are identical).  The same
  * inputs as potr_render plus the scene; writes every plane of *grads.  d_ws:
  * potr_render_backward_workspace_size bytes.  d_tile_order as in potr_render.
  */
@@ -333,8 +328,7 @@ POTR_API potr_status potr_render_backward(const potr_scene* scene, const potr_vi
                                           const potr_raster_config* cfg, const uint32_t* d_vals,
                                           const uint32_t* d_tile_ranges, uint32_t* d_tile_order,
                                           const float* d_t_final,
-                                          const uint32_t* d_n_last, const uint8_t* d_warp_masks,
-                                          const float* d_dL_dimages,
+                                          const uint32_t* d_n_last, const float* d_dL_dimages,
                                           int64_t instance_capacity, const potr_scene_grads* grads, void* d_ws,
                                           size_t ws_bytes, potr_stream_t stream);
 

@@ -93,7 +93,7 @@ SIGNATURES = {
     "potr_bin_sort": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _I64, _P, _P, _P,
                              _P, _P, _SZ, _P]),
     "potr_render": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _P, _P, _P, _P, _P,
-                           _P, _P, _P]),
+                           _P, _P]),
     "potr_removal_effect": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _P, _P, _P,
                                    _P, _I32, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
     "potr_tile_schedule_workspace_size": (_SZ, []),
@@ -106,7 +106,7 @@ SIGNATURES = {
     "potr_loss_grad": (_I32, [C.POINTER(Frame), _P, _P, C.c_float, _P, _P, _P, _SZ, _P]),
     "potr_render_backward_workspace_size": (_SZ, [_I64]),
     "potr_render_backward": (_I32, [C.POINTER(Scene), C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _P,
-                                    _P, _P, _P, _P, _P, _P, _I64, C.POINTER(SceneGrads), _P, _SZ, _P]),
+                                    _P, _P, _P, _P, _P, _I64, C.POINTER(SceneGrads), _P, _SZ, _P]),
     "potr_bin_sort_static": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _I64, _P, _P,
                                     _P, _P, _P]),
     "potr_prune_workspace_size": (_SZ, [_I64]),
@@ -215,9 +215,9 @@ def potr_bin_sort(views: Views, frame: Frame, cfg: RasterConfig, n: int, capacit
 
 
 def potr_render(views: Views, frame: Frame, cfg: RasterConfig, n: int, vals, ranges, images=None, t_final=None,
-                n_last=None, stream=None, order=None, warp_masks=None):
+                n_last=None, stream=None, order=None):
     _check("potr_render", lib().potr_render(C.byref(views), C.byref(frame), C.byref(cfg), n, ptr(vals), ptr(ranges),
-                                            ptr(order), ptr(images), ptr(t_final), ptr(n_last), ptr(warp_masks),
+                                            ptr(order), ptr(images), ptr(t_final), ptr(n_last),
                                             stream_handle(stream)))
 
 
@@ -272,10 +272,10 @@ def potr_render_backward_workspace_size(capacity: int) -> int:
 
 
 def potr_render_backward(scene: Scene, views: Views, frame: Frame, cfg: RasterConfig, vals, ranges, t_final, n_last,
-                         dL_dimages, capacity: int, grads: SceneGrads, ws, stream=None, order=None, warp_masks=None):
+                         dL_dimages, capacity: int, grads: SceneGrads, ws, stream=None, order=None):
     _check("potr_render_backward",
            lib().potr_render_backward(C.byref(scene), C.byref(views), C.byref(frame), C.byref(cfg), ptr(vals),
-                                      ptr(ranges), ptr(order), ptr(t_final), ptr(n_last), ptr(warp_masks),
+                                      ptr(ranges), ptr(order), ptr(t_final), ptr(n_last),
                                       ptr(dL_dimages), capacity, C.byref(grads), ptr(ws), ws.numel(),
                                       stream_handle(stream)))
 

@@ -7,33 +7,32 @@
 //                         S_{>i} = sum_{j>i} T_j alpha_j c_j (the same suffix as the removal
 //                         pass), dc/dalpha_i = T_i c_i - S_{>i} / (1 - alpha_i) and dc/dc_i =
 //                         T_i alpha_i; through alpha = o 2^p (unclamped) to the opacity, the
-//                         exponent coefficients A, B, C and the pixel-space centre.  The nine
-//                         per-pair gradients are summed per (tile, splat) without atomics (warp
-//                         transpose-sums in a fixed order, then warps in order) into per-instance
-//                         slots.  T_i comes either from the stored final transmittance of the
-//                         forward render (whose per-entry warp masks are then read, not
-//                         recomputed) or, with none stored, from re-running the forward walk.
+//                         exponent coefficients A, B, C and the pixel-space centre.  Four warps
+//                         per tile, each on an 8 x 8 block, two pixels per lane in packed f32x2
+//                         arithmetic over expanded records (tile_pass.cuh).  The nine per-pair
+//                         gradients are summed per (tile, splat) without atomics (each lane's two
+//                         pixels, then warp transpose-sums in a fixed order, then warps in
+//                         order) into per-instance slots.  T_i comes either from the stored
+//                         final transmittance of the forward render or, with none stored, from
+//                         re-running the forward walk.
 //   vk_grad_sum_kernel    per (view, splat): its instance slots summed in emission order.
 //   preprocess_bwd_kernel per splat: the adjoint of the projection (conic inverse, Sigma2D = T Sigma T^T,
 //                         clamped Jacobian, pinhole centre, SH colour and its direction) and of
 //                         the activation (Sigma = M M^T, M = R diag(exp(log_scale)), quaternion
 //                         normalisation, sigmoid), accumulated over views in view order.
 // All sums have a fixed order, so the gradients are bit-identical from run to run.
-#include "raster_common.cuh"
+#include "tile_pass.cuh"
 
 namespace potr {
 namespace {
 
 constexpr int kGradQ = 9;     // per-pair gradients: mx, my, A, B, C, opacity, r, g, b
 constexpr int kBwdChunk = 4;  // splats per warp transpose-sum
-constexpr int kBwdBatch = 128;
+constexpr int kBwdBatch = 64;
 constexpr float kLn2 = 0.69314718055994531f;
 
-constexpr uint32_t kBwdMaskCache = 2048;  // list positions whose warp masks the back walk reuses
-
 size_t bwd_smem_bytes() {
-  return sizeof(float4) * 2 * kSRec * kBwdBatch + sizeof(float) * kGradQ * kWarps * kBwdBatch + kBwdBatch +
-         kBwdMaskCache;
+  return sizeof(float4) * (2 * kSRec2 + kERec) * kBwdBatch + sizeof(float) * kGradQ * kW2 * kBwdBatch;
 }
 
 // Lanes l, l^4, l^8, ... receive the sum over all 32 lanes of v[l & 3] (fixed order): a
@@ -98,192 +97,204 @@ __global__ void loss_finish_kernel(const double* __restrict__ block_sums, int nb
 // K9: back-to-front adjoint of the compositing
 // ---------------------------------------------------------------------------------------
 template <bool RECOMPUTE>
-__global__ void __launch_bounds__(kThreads, 4) render_bwd_kernel(const float4* __restrict__ raster,
-                                                              const uint32_t* __restrict__ vals,
-                                                              const uint32_t* __restrict__ ranges,
-                                                              const potr_view_info* __restrict__ info, int n_views,
-                                                              potr_raster_config cfg, const float* __restrict__ t_final,
-                                                              const uint32_t* __restrict__ n_last,
-                                                              const float* __restrict__ dL_dimg, int64_t capacity,
-                                                              float* __restrict__ inst_grad,
-                                                              const uint8_t* __restrict__ gmask,
-                                                              const uint4* __restrict__ cull,
-                                                              const uint32_t* __restrict__ offsets, TileQueue queue) {
+__global__ void __launch_bounds__(kT2, 5) render_bwd_kernel(const float4* __restrict__ raster,
+                                                         const uint32_t* __restrict__ vals,
+                                                         const uint32_t* __restrict__ ranges,
+                                                         const potr_view_info* __restrict__ info, int n_views,
+                                                         potr_raster_config cfg, const float* __restrict__ t_final,
+                                                         const uint32_t* __restrict__ n_last,
+                                                         const float* __restrict__ dL_dimg, int64_t capacity,
+                                                         float* __restrict__ inst_grad,
+                                                         const uint4* __restrict__ cull,
+                                                         const uint32_t* __restrict__ offsets, TileQueue queue) {
   extern __shared__ float4 dyn[];
-  float4* smem = dyn;                                                // [2][kBwdBatch][kSRec]
-  float* red = reinterpret_cast<float*>(dyn + 2 * kSRec * kBwdBatch);        // [kGradQ][kWarps][kBwdBatch]
-  uint8_t* wmask = reinterpret_cast<uint8_t*>(red + kGradQ * kWarps * kBwdBatch);
-  uint8_t* mcache = wmask + kBwdBatch;  // [kBwdMaskCache] the recomputing forward walk's warp masks
-  const bool stored_masks = !RECOMPUTE && gmask != nullptr;
-  __shared__ uint32_t max_last_w[kWarps];
+  constexpr uint32_t B = kBwdBatch;
+  float4* smem = dyn;                                            // [2][B][kSRec2] raster records
+  float4* ex = dyn + 2 * kSRec2 * B;                             // [B][kERec] expanded records
+  float* red = reinterpret_cast<float*>(ex + kERec * B);         // [kGradQ][kW2][B]
+  __shared__ uint32_t max_last_w[kW2];
   __shared__ uint32_t s_slot;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int64_t tile;
   for (bool first = true; next_tile(queue, &s_slot, first, tile); first = false) {
-  const TileCtx c = tile_ctx(info, n_views, ranges, cfg, tile);
-  float T = 1.0f;
-  uint32_t last = 0;
-  if (RECOMPUTE) {
-    float C[3];
-    forward_walk<kBwdBatch>(smem, wmask, mcache, kBwdMaskCache, raster, vals, c, cfg, C, T, last);
-  } else if (c.inside) {
+    const Tile2 c = tile2_ctx(info, n_views, ranges, cfg, tile);
+    f2_t T = f2s(1.0f);
+    uint32_t last0 = 0, last1 = 0;
     const int64_t pix = c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
-    T = t_final[pix];
-    last = n_last[pix];
-  }
-  float g[3] = {0.0f, 0.0f, 0.0f};
-  if (c.inside) {
-    const int64_t plane = (int64_t)c.vi.width * c.vi.height;
-    const int64_t o = 3 * c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) g[ch] = dL_dimg[o + ch * plane];
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t warp_last = __reduce_max_sync(0xffffffffu, last);
-  if (lane == 0) max_last_w[warp] = warp_last;
-  __syncthreads();
-  uint32_t max_last = 0;
-#pragma unroll
-  for (int w = 0; w < kWarps; ++w) max_last = max(max_last, max_last_w[w]);
-
-  float S[3] = {0.0f, 0.0f, 0.0f};
-  constexpr uint32_t B = kBwdBatch;
-  const uint32_t nb = (max_last + B - 1) / B;
-  BatchStager<kBwdBatch> st;
-  uint32_t mk_cur[BatchStager<kBwdBatch>::kPer], mk_nxt[BatchStager<kBwdBatch>::kPer];  // stored masks
-  __syncthreads();  // the forward walk's last batch is no longer read
-  if (nb > 0) {
-    const uint32_t lo0 = max_last > B ? max_last - B : 0u;
-    st.load(vals, c.s + lo0, (int)(max_last - lo0));
-    if (stored_masks) st.load_masks(gmask + c.s, lo0, (int)(max_last - lo0), mk_cur);
-    st.issue(smem, raster);
-  }
-  if (nb > 1) {
-    const uint32_t hi1 = max_last - B, lo1 = hi1 > B ? hi1 - B : 0u;
-    st.load(vals, c.s + lo1, (int)(hi1 - lo1));
-  }
-  for (uint32_t k = 0; k < nb; ++k) {
-    const uint32_t top = max_last - k * B;
-    const uint32_t lo = top > B ? top - B : 0u;
-    const int cnt = (int)(top - lo);
-    const float4* buf = smem + kSRec * B * (k & 1);
-    if (k > 0) __syncthreads();  // batch k-1 fully consumed
-    if (k + 1 < nb) {
-      if (stored_masks) {
-        const uint32_t lo1 = lo > B ? lo - B : 0u;
-        st.load_masks(gmask + c.s, lo1, (int)(lo - lo1), mk_nxt);  // in flight during batch k
-      }
-      st.issue(smem + kSRec * B * ((k + 1) & 1), raster);
-      cp_async_wait<1>();
-      if (k + 2 < nb) {
-        const uint32_t hi2 = lo - B, lo2 = hi2 > B ? hi2 - B : 0u;
-        st.load(vals, c.s + lo2, (int)(hi2 - lo2));
-      }
+    if (RECOMPUTE) {
+      f2_t Cc[3];
+      forward_walk2<B>(smem, ex, raster, vals, c, cfg, Cc, T, last0, last1);
     } else {
-      cp_async_wait<0>();
+      const float T0 = c.in0 ? t_final[pix] : 1.0f, T1 = c.in1 ? t_final[pix + c.vi.width] : 1.0f;
+      T = f2(T0, T1);
+      last0 = c.in0 ? n_last[pix] : 0u;
+      last1 = c.in1 ? n_last[pix + c.vi.width] : 0u;
     }
-    // this batch's warp masks: stored by the render pass, cached by the forward walk above, or
-    // computed here
-    const uint8_t* bm = wmask;
-    if (stored_masks) {
+    // dL/dc of the two pixels per channel (0 outside the image)
+    f2_t gq[3];
+    {
+      const int64_t plane = (int64_t)c.vi.width * c.vi.height;
+      const int64_t o = 3 * c.vi.pixel_base + (int64_t)c.py * c.vi.width + c.px;
 #pragma unroll
-      for (int r = 0; r < BatchStager<kBwdBatch>::kPer; ++r) {
-        const int j = threadIdx.x + r * kThreads;
-        if (j < cnt) wmask[j] = (uint8_t)mk_cur[r];
-        mk_cur[r] = mk_nxt[r];
-      }
-    } else if (RECOMPUTE && top <= kBwdMaskCache) {
-      bm = mcache + lo;
-    } else {
-      compute_masks<kBwdBatch>(buf, wmask, cnt, c, cfg);
+      for (int ch = 0; ch < 3; ++ch)
+        gq[ch] = f2(c.in0 ? dL_dimg[o + ch * plane] : 0.0f, c.in1 ? dL_dimg[o + c.vi.width + ch * plane] : 0.0f);
     }
-    for (int q = 0; q < kGradQ; ++q)
-      for (int j = lane; j < cnt; j += 32) red[(q * kWarps + warp) * kBwdBatch + j] = 0.0f;
+    const uint32_t warp_last = __reduce_max_sync(0xffffffffu, max(last0, last1));
+    if (lane == 0) max_last_w[warp] = warp_last;
     __syncthreads();
-    for (int ghi = cnt; ghi > 0; ghi -= 32) {
-      const int glo = ghi > 32 ? ghi - 32 : 0;
-      if (lo + (uint32_t)glo >= warp_last) continue;
-      const int jl = glo + lane;
-      uint32_t m = __ballot_sync(0xffffffffu, jl < ghi && lo + (uint32_t)jl < warp_last && ((bm[jl] >> warp) & 1u));
-      while (m) {
-        float v[kGradQ][kBwdChunk];
-        int mypos = -1;
-        bool any = false;
+    uint32_t max_last = 0;
 #pragma unroll
-        for (int u = 0; u < kBwdChunk; ++u) {
+    for (int w = 0; w < kW2; ++w) max_last = max(max_last, max_last_w[w]);
+    const f2_t fx2 = f2s(c.fx), fy2 = f2(c.fy0, c.fy1);
+
+    f2_t S[3] = {f2s(0.0f), f2s(0.0f), f2s(0.0f)};
+    const uint32_t nb = (max_last + B - 1) / B;
+    Stager2<B> st;
+    if (nb > 0) {
+      const uint32_t lo0 = max_last > B ? max_last - B : 0u;
+      st.load(vals, c.s + lo0, (int)(max_last - lo0));
+      st.issue(smem, raster);  // the forward walk's reads of smem ended at the barrier above
+    }
+    if (nb > 1) {
+      const uint32_t hi1 = max_last - B, lo1 = hi1 > B ? hi1 - B : 0u;
+      st.load(vals, c.s + lo1, (int)(hi1 - lo1));
+    }
+    for (uint32_t k = 0; k < nb; ++k) {
+      const uint32_t top = max_last - k * B;
+      const uint32_t lo = top > B ? top - B : 0u;
+      const int cnt = (int)(top - lo);
+      const float4* buf = smem + kSRec2 * B * (k & 1);
+      if (k > 0) __syncthreads();  // batch k-1 (records, warp sums) fully consumed
+      if (k + 1 < nb) {
+        st.issue(smem + kSRec2 * B * ((k + 1) & 1), raster);
+        cp_async_wait2<1>();
+        if (k + 2 < nb) {
+          const uint32_t hi2 = lo - B, lo2 = hi2 > B ? hi2 - B : 0u;
+          st.load(vals, c.s + lo2, (int)(hi2 - lo2));
+        }
+      } else {
+        cp_async_wait2<0>();
+      }
+      for (int q = 0; q < kGradQ; ++q)
+        for (int j = lane; j < cnt; j += 32) red[(q * kW2 + warp) * B + j] = 0.0f;
+      expand_own<B>(buf, ex, cnt);
+      __syncthreads();  // every thread's expanded records of batch k are visible
+      for (int ghi = cnt; ghi > 0; ghi -= 32) {
+        const int glo = ghi > 32 ? ghi - 32 : 0;
+        if (lo + (uint32_t)glo >= warp_last) continue;  // warp-uniform: nothing composited here
+        const int jl = glo + lane;
+        const bool cand = jl < ghi && lo + (uint32_t)jl < warp_last && block_may_pass_e(ex + kERec * jl, c.bx0, c.by0);
+        uint32_t m = __ballot_sync(0xffffffffu, cand);
+        while (m) {
+          float v[kGradQ][kBwdChunk];
+          int mypos = -1;
+          bool any = false;
 #pragma unroll
-          for (int q = 0; q < kGradQ; ++q) v[q][u] = 0.0f;
-          if (m) {
-            const int b = 31 - __clz(m);
-            m &= ~(1u << b);
-            const int j = glo + b;
-            if (lane == u) mypos = j;
-            if (lo + (uint32_t)j < last) {
-              const float4 r0 = buf[kSRec * j];
-              const float4 r1 = buf[kSRec * j + 1];
-              const float dx = __fsub_rn(c.fx, r0.x), dy = __fsub_rn(c.fy, r0.y);
-              const float p = pair_exponent(r0.z, r0.w, r1.x, dx, dy);
-              if (p >= r1.z) {
-                const float G = exp2r(p);
-                const float ao = __fmul_rn(r1.y, G);
-                const float a = fminf(cfg.alpha_max, ao);
-                if (a >= cfg.alpha_min) {
-                  const float4 r2 = buf[kSRec * j + 2];
-                  const float rcp = __fdividef(1.0f, 1.0f - a);
-                  T = T * rcp;            // T_i
-                  const float w = a * T;  // T_i alpha_i
-                  v[6][u] = w * g[0];
-                  v[7][u] = w * g[1];
-                  v[8][u] = w * g[2];
-                  const float dot_c = r2.x * g[0] + r2.y * g[1] + r2.z * g[2];
-                  const float dot_s = S[0] * g[0] + S[1] * g[1] + S[2] * g[2];
-                  const float dLda = T * dot_c - dot_s * rcp;
-                  S[0] += w * r2.x;
-                  S[1] += w * r2.y;
-                  S[2] += w * r2.z;
-                  if (ao <= cfg.alpha_max) {  // alpha = o 2^p (clamp inactive)
-                    v[5][u] = dLda * G;
-                    const float dLdp = dLda * ao * kLn2;
-                    v[2][u] = dLdp * dx * dx;
-                    v[3][u] = dLdp * dx * dy;
-                    v[4][u] = dLdp * dy * dy;
-                    v[0][u] = -dLdp * (2.0f * r0.z * dx + r0.w * dy);
-                    v[1][u] = -dLdp * (r0.w * dx + 2.0f * r1.x * dy);
-                  }
-                  any = true;
-                }
+          for (int u = 0; u < kBwdChunk; ++u) {
+#pragma unroll
+            for (int q = 0; q < kGradQ; ++q) v[q][u] = 0.0f;
+            if (m) {
+              const int b = 31 - __clz(m);
+              m &= ~(1u << b);
+              const int j = glo + b;
+              if (lane == u) mypos = j;
+              const uint32_t pos = lo + (uint32_t)j;
+              const float4* e = ex + kERec * j;
+              f2_t o2;
+              float thr, indef;
+              const ulonglong2* qq = reinterpret_cast<const ulonglong2*>(e);
+              const ulonglong2 q0 = qq[0], q1 = qq[1], q2 = qq[2];
+              const f2_t dx = sub2(fx2, q1.y), dy = sub2(fy2, q2.x);
+              const f2_t p2 = exponent_e(e, fx2, fy2, o2, thr, indef);
+              float p0, p1;
+              f2split(p2, p0, p1);
+              const bool pass0 = pos < last0 && p0 >= thr, pass1 = pos < last1 && p1 >= thr;
+              if (__any_sync(0xffffffffu, pass0 || pass1)) {  // warp-uniform: branch-free below
+                const f2_t G2 = exp2r2_rec(p2, indef);
+                const f2_t ao2 = mul2(o2, G2);
+                float ao0, ao1;
+                f2split(ao2, ao0, ao1);
+                const float a0 = fminf(cfg.alpha_max, ao0), a1 = fminf(cfg.alpha_max, ao1);
+                const bool ok0 = pass0 && a0 >= cfg.alpha_min, ok1 = pass1 && a1 >= cfg.alpha_min;
+                // a pixel that does not take the splat: alpha 0 and 1 / (1 - alpha) = 1, so its
+                // T and S do not change and its gradient terms are 0
+                const float r0 = __fdividef(1.0f, 1.0f - a0), r1 = __fdividef(1.0f, 1.0f - a1);
+                const f2_t ae = f2(ok0 ? a0 : 0.0f, ok1 ? a1 : 0.0f);
+                const f2_t rcp = f2(ok0 ? r0 : 1.0f, ok1 ? r1 : 1.0f);
+                T = mul2(T, rcp);          // T_i
+                const f2_t w = mul2(ae, T);  // T_i alpha_i
+                const ulonglong2 q3 = qq[3], q4 = qq[4];
+                const f2_t cr = q3.y, cg = q4.x, cb = q4.y;
+                const f2_t dot_c = fma2(cr, gq[0], fma2(cg, gq[1], mul2(cb, gq[2])));
+                const f2_t dot_s = fma2(S[0], gq[0], fma2(S[1], gq[1], mul2(S[2], gq[2])));
+                const f2_t dLda = sub2(mul2(T, dot_c), mul2(dot_s, rcp));
+                S[0] = fma2(w, cr, S[0]);
+                S[1] = fma2(w, cg, S[1]);
+                S[2] = fma2(w, cb, S[2]);
+                float x0, x1;
+                f2split(mul2(w, gq[0]), x0, x1);
+                v[6][u] = x0 + x1;
+                f2split(mul2(w, gq[1]), x0, x1);
+                v[7][u] = x0 + x1;
+                f2split(mul2(w, gq[2]), x0, x1);
+                v[8][u] = x0 + x1;
+                // through alpha = o 2^p where the pixel takes the splat and the clamp is inactive;
+                // elsewhere 2^p and o 2^p are replaced by 0 (a pixel that did not pass may hold
+                // any value there)
+                float G0, G1;
+                f2split(G2, G0, G1);
+                const bool f0 = ok0 && ao0 <= cfg.alpha_max, f1 = ok1 && ao1 <= cfg.alpha_max;
+                const f2_t Gm = f2(f0 ? G0 : 0.0f, f1 ? G1 : 0.0f), aom = f2(f0 ? ao0 : 0.0f, f1 ? ao1 : 0.0f);
+                f2split(mul2(dLda, Gm), x0, x1);
+                v[5][u] = x0 + x1;
+                const f2_t dLdp = mul2(mul2(dLda, aom), f2s(kLn2));
+                const f2_t dxx = mul2(dx, dx), dxy = mul2(dx, dy), dyy = mul2(dy, dy);
+                f2split(mul2(dLdp, dxx), x0, x1);
+                v[2][u] = x0 + x1;
+                f2split(mul2(dLdp, dxy), x0, x1);
+                v[3][u] = x0 + x1;
+                f2split(mul2(dLdp, dyy), x0, x1);
+                v[4][u] = x0 + x1;
+                const f2_t A2 = q0.x, B2 = q0.y, C2 = q1.x;
+                const f2_t gx = fma2(add2(A2, A2), dx, mul2(B2, dy));  // 2 A dx + B dy
+                const f2_t gy = fma2(B2, dx, mul2(add2(C2, C2), dy));  // B dx + 2 C dy
+                f2split(mul2(dLdp, gx), x0, x1);
+                v[0][u] = -(x0 + x1);
+                f2split(mul2(dLdp, gy), x0, x1);
+                v[1][u] = -(x0 + x1);
+                any = true;
               }
             }
           }
-        }
-        if (__any_sync(0xffffffffu, any)) {
+          if (__any_sync(0xffffffffu, any)) {
 #pragma unroll
-          for (int q = 0; q < kGradQ; ++q) {
-            const float sq = warp_transpose_sum4(v[q]);
-            if (lane < kBwdChunk && mypos >= 0) red[(q * kWarps + warp) * kBwdBatch + mypos] = sq;
+            for (int q = 0; q < kGradQ; ++q) {
+              const float sq = warp_transpose_sum4(v[q]);
+              if (lane < kBwdChunk && mypos >= 0) red[(q * kW2 + warp) * B + mypos] = sq;
+            }
           }
         }
       }
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < cnt; j += kThreads) {
-      float sq[kGradQ];
-      bool nz = false;
+      __syncthreads();
+      for (int j = threadIdx.x; j < cnt; j += kT2) {
+        float sq[kGradQ];
+        bool nz = false;
 #pragma unroll
-      for (int q = 0; q < kGradQ; ++q) {
-        float t = 0.0f;
+        for (int q = 0; q < kGradQ; ++q) {
+          float t = 0.0f;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) t += red[(q * kWarps + w) * kBwdBatch + j];
-        sq[q] = t;
-        nz |= t != 0.0f;
+          for (int w = 0; w < kW2; ++w) t += red[(q * kW2 + w) * B + j];
+          sq[q] = t;
+          nz |= t != 0.0f;
+        }
+        if (nz) {
+          const uint32_t vk = vals[c.s + lo + j];
+          const uint32_t slot = emission_slot(offsets[vk], cull[vk], c.tx, c.ty);  // L2
+#pragma unroll
+          for (int q = 0; q < kGradQ; ++q) inst_grad[(int64_t)q * capacity + slot] = sq[q];
+        }
       }
-      if (nz) {
-        const uint32_t vk = vals[c.s + lo + j];
-        const uint32_t slot = emission_slot(offsets[vk], cull[vk], c.tx, c.ty);  // L2
-#pragma unroll
-        for (int q = 0; q < kGradQ; ++q) inst_grad[(int64_t)q * capacity + slot] = sq[q];
-      }
     }
-  }
   }  // tiles
 }
 
@@ -635,8 +646,7 @@ extern "C" potr_status potr_render_backward(const potr_scene* scene, const potr_
                                             const potr_raster_config* cfg, const uint32_t* d_vals,
                                             const uint32_t* d_tile_ranges, uint32_t* d_tile_order,
                                             const float* d_t_final,
-                                            const uint32_t* d_n_last, const uint8_t* d_warp_masks,
-                                            const float* d_dL_dimages,
+                                            const uint32_t* d_n_last, const float* d_dL_dimages,
                                             int64_t instance_capacity, const potr_scene_grads* grads, void* d_ws,
                                             size_t ws_bytes, potr_stream_t stream) {
   using namespace potr;
@@ -666,26 +676,26 @@ extern "C" potr_status potr_render_backward(const potr_scene* scene, const potr_
   q.total = (uint32_t)frame->total_tiles;
   if (d_tile_order && cudaMemsetAsync(q.counter, 0, sizeof(uint32_t), s) != cudaSuccess) return POTR_ERR_CUDA;
   if (recompute) {
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(render_bwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(render_bwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
       return POTR_ERR_CUDA;
-    const unsigned grid = tile_grid(render_bwd_kernel<true>, smem, q, frame->total_tiles);
+    const unsigned grid = tile_grid(render_bwd_kernel<true>, smem, q, frame->total_tiles, kT2);
     tile_timing_begin(s);
-    render_bwd_kernel<true><<<grid, kThreads, smem, s>>>(
+    render_bwd_kernel<true><<<grid, kT2, smem, s>>>(
         reinterpret_cast<const float4*>(views->raster), d_vals, d_tile_ranges, frame->info, frame->n_views, *cfg,
-        nullptr, nullptr, d_dL_dimages, instance_capacity, inst_grad, nullptr,
-        reinterpret_cast<const uint4*>(views->cull), views->offsets, q);
+        nullptr, nullptr, d_dL_dimages, instance_capacity, inst_grad, reinterpret_cast<const uint4*>(views->cull),
+        views->offsets, q);
     tile_timing_end(s);
   } else {
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(render_bwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(render_bwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
       return POTR_ERR_CUDA;
-    const unsigned grid = tile_grid(render_bwd_kernel<false>, smem, q, frame->total_tiles);
+    const unsigned grid = tile_grid(render_bwd_kernel<false>, smem, q, frame->total_tiles, kT2);
     tile_timing_begin(s);
-    render_bwd_kernel<false><<<grid, kThreads, smem, s>>>(
+    render_bwd_kernel<false><<<grid, kT2, smem, s>>>(
         reinterpret_cast<const float4*>(views->raster), d_vals, d_tile_ranges, frame->info, frame->n_views, *cfg,
-        d_t_final, d_n_last, d_dL_dimages, instance_capacity, inst_grad, d_warp_masks,
-        reinterpret_cast<const uint4*>(views->cull), views->offsets, q);
+        d_t_final, d_n_last, d_dL_dimages, instance_capacity, inst_grad, reinterpret_cast<const uint4*>(views->cull),
+        views->offsets, q);
     tile_timing_end(s);
   }
   POTR_CHECK_LAUNCH();

@@ -424,7 +424,7 @@ cudaError_t make_queue(uint32_t* d_tile_order, int64_t total_tiles, TileQueue& q
 extern "C" potr_status potr_render(const potr_views* views, const potr_frame* frame, const potr_raster_config* cfg,
                                    int64_t n, const uint32_t* d_vals, const uint32_t* d_tile_ranges,
                                    uint32_t* d_tile_order, float* d_images, float* d_t_final, uint32_t* d_n_last,
-                                   uint8_t* d_warp_masks, potr_stream_t stream) {
+                                   potr_stream_t stream) {
   using namespace potr;
   if (!views || !frame || !valid_cfg(cfg) || !d_vals || !d_tile_ranges || !views->raster || !frame->info)
     return POTR_ERR_INVALID_ARGUMENT;

@@ -15,7 +15,7 @@
 // skipping it changes no decision.
 #pragma once
 
-#include "potr_device.cuh"
+#include "raster_common.cuh"
 
 namespace potr {
 namespace {

@@ -110,7 +110,6 @@ class RemovalEffectFrame:
                                                                    self.capacity), torch.uint8)
         self.inst_dse = P.get("inst_dse", self.capacity, torch.float32)
         self.inst_imp = P.get("inst_imp", self.capacity, torch.float32) if self.with_importance else None
-        self.warp_masks = P.get("warp_masks", self.capacity, torch.uint8)  # render -> stored-T backward
 
     def plan(self, slack: float = 1.05) -> int:
         """Run preprocess + binning once, grow the instance capacity to fit, return the count."""
@@ -185,11 +184,8 @@ class RemovalEffectFrame:
         ws = self.pool.get("bwd_ws", B.potr_render_backward_workspace_size(self.capacity)
                            + 36 * self.n_views * self.n, torch.uint8)
         g = B.SceneGrads(*(grads[k].data_ptr() for k in SCENE_KEYS))
-        masks = None
-        if t_final is not None and getattr(self.pool, "masks_owner", None) == (id(self), getattr(self, "_sort_gen", 0)):
-            masks = self.warp_masks
         B.potr_render_backward(self.scene_c, self.views, self.frame, self.cfg, self.vals, self.ranges, t_final, n_last,
-                               dL_dimages, self.capacity, g, ws, stream, order=self.order, warp_masks=masks)
+                               dL_dimages, self.capacity, g, ws, stream, order=self.order)
 
     def pair_stats(self, stream=None) -> dict:
         """Exact pair counts of the forward and removal walks (see potr_pair_stats)."""
