@@ -350,9 +350,11 @@ POTR_API potr_status potr_pair_stats(const potr_views* views, const potr_frame* 
  * potr_bin_sort; the scratch it needs lives in a 56 MiB array inside the library, held by
  * every GPU that loads the library until the process exits.  Limits: instance_capacity <=
  * POTR_STATIC_MAX_INSTANCES and n * n_views <= POTR_STATIC_MAX_VIEW_SPLATS, otherwise it
- * returns POTR_ERR_TOO_LARGE and enqueues nothing.  The first call on a device looks up the
- * array's device address (make it before any stream capture).  Calls share the array: calls
- * that overlap on the GPU race, so serialise them.  It allocates nothing.
+ * returns POTR_ERR_TOO_LARGE and enqueues nothing.  Calls made outside a stream capture look up
+ * the array's device address; calls inside a capture use the address the last such call found,
+ * so the first call on a device must come before any capture (else POTR_ERR_UNSUPPORTED).
+ * Calls share the array: calls that overlap on the GPU race, so serialise them.  It allocates
+ * nothing.
  */
 #define POTR_STATIC_MAX_INSTANCES 4194304LL
 #define POTR_STATIC_MAX_VIEW_SPLATS 1048576LL

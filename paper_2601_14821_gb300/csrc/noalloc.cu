@@ -11,9 +11,11 @@
 //
 // The array is a file-scope __device__ variable: every GPU that loads this library holds
 // its kStaticScratchBytes until the process exits.  Its host-side name is only a stand-in
-// for the symbol, not a device address, so the device address is looked up once per device
-// with cudaGetSymbolAddress (with that device current) and cached.  The first call on a
-// device performs that lookup; make that first call before capturing a stream into a graph.
+// for the symbol, not a device address, so the device address is looked up with
+// cudaGetSymbolAddress (with that device current) on every call made outside a stream capture
+// -- a context that was reset or replaced gets the array's new address -- and cached per device
+// for calls made while their stream is being captured.  The first call on a device must come
+// before any capture (a first call inside a capture is refused with POTR_ERR_UNSUPPORTED).
 // All calls share the one array and it keeps the previous call's contents: nothing in it
 // needs to start at zero (every word is written before it is read within a call), and calls
 // whose work overlaps on the GPU race on it -- serialise them (one stream, or events).
@@ -31,16 +33,21 @@ static __device__ __align__(256) unsigned char g_bin_sort_scratch[kStaticScratch
 std::mutex g_scratch_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of g_bin_sort_scratch on the current device (looked up once per device).
-potr_status scratch_for_current_device(void** out) {
+// Device address of g_bin_sort_scratch on the current device: looked up afresh outside a
+// stream capture, the cached address inside one.
+potr_status scratch_for_current_device(cudaStream_t s, void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return POTR_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return POTR_ERR_UNSUPPORTED;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return POTR_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_bin_sort_scratch) != cudaSuccess || p == nullptr) return POTR_ERR_CUDA;
     g_scratch_ptr[dev] = p;
+  } else if (!g_scratch_ptr[dev]) {
+    return POTR_ERR_UNSUPPORTED;  // the first call on a device came inside a capture
   }
   *out = g_scratch_ptr[dev];
   return POTR_OK;
@@ -60,7 +67,7 @@ extern "C" potr_status potr_bin_sort_static(const potr_views* views, const potr_
   if (need == 0) return POTR_ERR_INVALID_ARGUMENT;
   if (need > kStaticScratchBytes) return POTR_ERR_TOO_LARGE;
   void* scratch = nullptr;
-  const potr_status st = scratch_for_current_device(&scratch);
+  const potr_status st = scratch_for_current_device(reinterpret_cast<cudaStream_t>(stream), &scratch);
   if (st != POTR_OK) return st;
   return potr_bin_sort(views, frame, cfg, n, instance_capacity, d_tiles, d_vals, d_tile_ranges, d_status, scratch,
                        kStaticScratchBytes, stream);

@@ -109,3 +109,14 @@ def test_timing_hook_and_status_word_on_the_host(libpotr):
     assert B.DeviceStatus.code.offset == 0 and B.DeviceStatus.n_nonfinite.offset == 4
     assert B.DeviceStatus.required_instances.offset == 8 and C.sizeof(B.DeviceStatus) == 16
     assert B.status_string(B.POTR_ERR_NUMERIC) == "non-finite input"
+
+
+def test_static_sort_limits_fit_its_scratch(libpotr):
+    """Every call within potr_bin_sort_static's advertised limits fits its 56 MiB scratch: the
+    workspace of the largest instance count and (view, splat) count, split over 1 to 64 views."""
+    from paper_2601_14821_gb300 import _binding as B
+
+    cap, vs = int(B.POTR_STATIC_MAX_INSTANCES), int(B.POTR_STATIC_MAX_VIEW_SPLATS)
+    for views in (1, 2, 4, 16, 64):
+        need = B.potr_bin_sort_workspace_size(vs // views, views, 1 << 20, cap)
+        assert 0 < need <= 56 << 20, (views, need)

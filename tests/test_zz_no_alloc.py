@@ -61,15 +61,31 @@ def test_static_scratch_sort_matches_workspace_sort_twice(which):
             assert np.array_equal(g, e), call
 
 
-def test_static_scratch_sort_rejects_oversize():
+def _check_refused(B, fr, n, capacity):
+    """A refused call enqueues nothing: the outputs keep their sentinel values."""
     import torch
 
+    tiles = torch.full_like(fr.tiles, -7)
+    vals = torch.full_like(fr.vals, -7)
+    ranges = torch.full_like(fr.ranges, -7)
+    status = torch.full((2,), -7, dtype=torch.int64, device=fr.device)
+    with pytest.raises(B.PotrError) as e:
+        B.potr_bin_sort_static(fr.views, fr.frame, fr.cfg, n, capacity, tiles, vals, ranges, status)
+    assert e.value.status == B.POTR_ERR_TOO_LARGE
+    torch.cuda.synchronize()
+    for t in (tiles, vals, ranges, status):
+        assert bool((t == -7).all())
+
+
+def test_static_scratch_sort_rejects_oversize():
+    """Both limits: more instances than POTR_STATIC_MAX_INSTANCES, and more (view, splat) pairs
+    than POTR_STATIC_MAX_VIEW_SPLATS (a 1,048,577-splat scene in one view)."""
     from paper_2601_14821_gb300 import _binding as B
 
     w = synth.workload("tiny")
     fr = _frame(w.scene, w.cameras)
-    status = torch.zeros(2, dtype=torch.int64, device=fr.device)
-    with pytest.raises(B.PotrError) as e:
-        B.potr_bin_sort_static(fr.views, fr.frame, fr.cfg, fr.n, B.POTR_STATIC_MAX_INSTANCES + 1, fr.tiles, fr.vals,
-                               fr.ranges, status)
-    assert e.value.status == B.POTR_ERR_TOO_LARGE
+    _check_refused(B, fr, fr.n, B.POTR_STATIC_MAX_INSTANCES + 1)
+    big = synth.uniform_cube_scene(int(B.POTR_STATIC_MAX_VIEW_SPLATS) + 1, 5)
+    fr2 = _frame(big, w.cameras)
+    assert fr2.n * fr2.n_views == B.POTR_STATIC_MAX_VIEW_SPLATS + 1
+    _check_refused(B, fr2, fr2.n, min(fr2.capacity, int(B.POTR_STATIC_MAX_INSTANCES)))
