@@ -302,10 +302,10 @@ POTR_API potr_status potr_loss_grad(const potr_frame* frame, const float* d_imag
                                     float lambda, double* d_loss, float* d_dL_dimages, void* d_ws, size_t ws_bytes,
                                     potr_stream_t stream);
 
-/* Bytes of potr_render_backward's 9 float partial gradients per instance slot.  The workspace it
- * needs is this plus 9 floats per (view, splat): potr_render_backward_workspace_size(capacity)
- * + 36 * n_views * n bytes. */
-POTR_API size_t potr_render_backward_workspace_size(int64_t instance_capacity);
+/* Workspace bytes of potr_render_backward: 9 floats of partial gradients per instance slot
+ * (instance_capacity) and 13 floats per (view, splat) (n_view_splats = n_views * n).  0 for a
+ * non-positive argument. */
+POTR_API size_t potr_render_backward_workspace_size(int64_t instance_capacity, int64_t n_view_splats);
 
 /*
  * Backward (adjoint) rasterizer, the derivative of potr_render with respect to the scene

@@ -104,7 +104,7 @@ SIGNATURES = {
     "potr_selftest_wait_timeout": (_I32, [_P, _SZ, _I32, _P, _P]),
     "potr_loss_workspace_size": (_SZ, [_I64]),
     "potr_loss_grad": (_I32, [C.POINTER(Frame), _P, _P, C.c_float, _P, _P, _P, _SZ, _P]),
-    "potr_render_backward_workspace_size": (_SZ, [_I64]),
+    "potr_render_backward_workspace_size": (_SZ, [_I64, _I64]),
     "potr_render_backward": (_I32, [C.POINTER(Scene), C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _P,
                                     _P, _P, _P, _P, _P, _I64, C.POINTER(SceneGrads), _P, _SZ, _P]),
     "potr_bin_sort_static": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _I64, _P, _P,
@@ -267,8 +267,8 @@ def potr_loss_grad(frame: Frame, images, targets, lam: float, loss, dL_dimages, 
                                                   stream_handle(stream)))
 
 
-def potr_render_backward_workspace_size(capacity: int) -> int:
-    return int(lib().potr_render_backward_workspace_size(capacity))
+def potr_render_backward_workspace_size(capacity: int, n_view_splats: int) -> int:
+    return int(lib().potr_render_backward_workspace_size(capacity, n_view_splats))
 
 
 def potr_render_backward(scene: Scene, views: Views, frame: Frame, cfg: RasterConfig, vals, ranges, t_final, n_last,

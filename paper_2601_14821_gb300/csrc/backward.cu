@@ -15,11 +15,13 @@
 //                         order) into per-instance slots.  T_i comes either from the stored
 //                         final transmittance of the forward render or, with none stored, from
 //                         re-running the forward walk.
-//   vk_grad_sum_kernel    per (view, splat): its instance slots summed in emission order.
-//   preprocess_bwd_kernel per splat: the adjoint of the projection (conic inverse, Sigma2D = T Sigma T^T,
-//                         clamped Jacobian, pinhole centre, SH colour and its direction) and of
-//                         the activation (Sigma = M M^T, M = R diag(exp(log_scale)), quaternion
-//                         normalisation, sigmoid), accumulated over views in view order.
+//   vk_bwd_kernel         per (view, splat): its instance slots summed (fixed tree), then the
+//                         adjoint of the projection (conic inverse, Sigma2D = T Sigma T^T,
+//                         clamped Jacobian, pinhole centre).
+//   splat_bwd_kernel      per splat: the views' results summed in view order, the SH colour
+//                         adjoint (clamp mask, coefficients, direction) and the adjoint of the
+//                         activation (Sigma = M M^T, M = R diag(exp(log_scale)), quaternion
+//                         normalisation, sigmoid).
 // All sums have a fixed order, so the gradients are bit-identical from run to run.
 #include "tile_pass.cuh"
 
@@ -66,13 +68,16 @@ __global__ void __launch_bounds__(256) loss_grad_kernel(const float* __restrict_
                                                         double* __restrict__ block_sums) {
   __shared__ double warp_sums[8];
   const float inv_n = (float)(1.0 / (double)n_elems);
-  double acc = 0.0;
+  // per thread a compensated binary32 sum (error about 2 ulps of the sum, independent of the
+  // term count; binary64 adds per element would make this kernel FP64-bound), then binary64
+  KahanSum part;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_elems; i += (int64_t)gridDim.x * blockDim.x) {
     const float r = img[i] - tgt[i];
     const float sg = (r > 0.0f) ? 1.0f : ((r < 0.0f) ? -1.0f : 0.0f);
     grad[i] = ((1.0f - lam) * sg + 2.0f * lam * r) * inv_n;
-    acc += (double)((1.0f - lam) * fabsf(r) + lam * r * r);
+    part.add((1.0f - lam) * fabsf(r) + lam * r * r);
   }
+  double acc = part.value();
   if (block_sums) {
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -86,11 +91,21 @@ __global__ void __launch_bounds__(256) loss_grad_kernel(const float* __restrict_
   }
 }
 
-__global__ void loss_finish_kernel(const double* __restrict__ block_sums, int nb, int64_t n_elems,
-                                   double* __restrict__ loss) {
+// Sum of the block sums in a fixed order: thread t adds blocks t, t + 256, ..., then a fixed
+// tree over the threads (one thread adding all of them serially takes ~1000 dependent binary64
+// adds).
+__global__ void __launch_bounds__(256) loss_finish_kernel(const double* __restrict__ block_sums, int nb,
+                                                          int64_t n_elems, double* __restrict__ loss) {
+  __shared__ double part[256];
   double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += block_sums[b];
-  *loss = s / (double)n_elems;
+  for (int b = threadIdx.x; b < nb; b += 256) s += block_sums[b];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *loss = part[0] / (double)n_elems;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -290,8 +305,9 @@ __global__ void __launch_bounds__(kT2, 5) render_bwd_kernel(const float4* __rest
         if (nz) {
           const uint32_t vk = vals[c.s + lo + j];
           const uint32_t slot = emission_slot(offsets[vk], cull[vk], c.tx, c.ty);  // L2
+          float* dst = inst_grad + (int64_t)slot * kGradQ;  // the slot's nine partials, contiguous
 #pragma unroll
-          for (int q = 0; q < kGradQ; ++q) inst_grad[(int64_t)q * capacity + slot] = sq[q];
+          for (int q = 0; q < kGradQ; ++q) dst[q] = sq[q];
         }
       }
     }
@@ -350,21 +366,29 @@ __device__ __forceinline__ void sh_weighted_grad(float x, float y, float z, cons
   gx += w[15] * -3.0f * c3a * (xx - yy);           gy += w[15] * 6.0f * c3a * x * y;
 }
 
-// Per (view, splat): the nine instance partials summed over the vk's emission slots (emission
-// order, compensated).  One warp per 32 consecutive vk, whose slots form one contiguous run:
-// the run is read coalesced into shared memory a chunk at a time and each lane adds the part of
-// its own segment that the chunk holds.  vk_grad[q][vk] receives the sums.
-constexpr int kSumChunk = 128;  // a warp's run is usually shorter (about 32 x 3.5 slots)
+// Per (view, splat): the nine instance partials summed over the vk's emission slots, then the
+// view-dependent part of the adjoint.  One warp per 32 consecutive vk, whose slots form one
+// contiguous run (vk order): the run is read 32 slots at a time, one slot (nine contiguous
+// floats) per lane, and summed per vk by a segmented scan across the lanes (a fixed tree per
+// chunk, chunks in order).  Each lane then takes its vk through the adjoint of the conic
+// inverse, of Sigma2D = T Sigma T^T (T = J W, J with the clamped x/z, y/z) and of the pinhole
+// centre.  out[vk][0..12] receives d/dmean (3), d/dSigma (6: 00 01 02 11 12 22), d/do (1) and
+// d/dcolour (3); all zero where no pixel of the view took the splat.
+constexpr int kVkOut = 13;
+constexpr int kVkThreads = 256;
 
-__global__ void __launch_bounds__(128, 8) vk_grad_sum_kernel(const uint32_t* __restrict__ touched,
-                                                          const uint32_t* __restrict__ offsets,
-                                                          const uint32_t* __restrict__ n_inst, int64_t capacity,
-                                                          int64_t n_vk, const float* __restrict__ inst_grad,
-                                                          float* __restrict__ vk_grad) {
-  __shared__ float buf[4][kGradQ][kSumChunk];
+__global__ void __launch_bounds__(kVkThreads) vk_bwd_kernel(const uint32_t* __restrict__ touched,
+                                                     const uint32_t* __restrict__ offsets,
+                                                     const uint32_t* __restrict__ n_inst, int64_t capacity, int64_t n,
+                                                     int n_views, const float* __restrict__ inst_grad,
+                                                     const float* __restrict__ means, const float* __restrict__ cov3d,
+                                                     const potr_camera* __restrict__ cams, potr_raster_config cfg,
+                                                     float* __restrict__ out) {
   const bool ok = (int64_t)*n_inst <= capacity;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t n_vk = (int64_t)n_views * n;
   const int64_t warps_total = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float kA = -0.5f * kLog2e;
   for (int64_t wv = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wv * 32 < n_vk; wv += warps_total) {
     const int64_t vk = wv * 32 + lane;
     uint32_t cnt = 0, off = 0;
@@ -382,63 +406,62 @@ __global__ void __launch_bounds__(128, 8) vk_grad_sum_kernel(const uint32_t* __r
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
     const uint32_t first_lane = total ? __ffs(__ballot_sync(0xffffffffu, cnt != 0)) - 1 : 0;
     const uint32_t run0 = __shfl_sync(0xffffffffu, off, first_lane);
-    KahanSum acc[kGradQ];
-    for (uint32_t c0 = 0; c0 < total; c0 += kSumChunk) {
-      const uint32_t cn = min((uint32_t)kSumChunk, total - c0);
-      for (uint32_t i = lane; i < cn; i += 32)
+    float gq[kGradQ];
 #pragma unroll
-        for (int q = 0; q < kGradQ; ++q) buf[wib][q][i] = inst_grad[(int64_t)q * capacity + run0 + c0 + i];
-      __syncwarp();
-      const uint32_t a = max(seg0, c0), b = min(seg1, c0 + cn);
-      for (uint32_t i = a; i < b; ++i)
+    for (int q = 0; q < kGradQ; ++q) gq[q] = 0.0f;
+    for (uint32_t c0 = 0; c0 < total; c0 += 32) {
+      const uint32_t e = c0 + lane;
+      float x[kGradQ];
+      if (e < total) {
+        const float* src = inst_grad + (int64_t)(run0 + e) * kGradQ;
 #pragma unroll
-        for (int q = 0; q < kGradQ; ++q) acc[q].add(buf[wib][q][i - c0]);
-      __syncwarp();
-    }
-    if (vk < n_vk) {
+        for (int q = 0; q < kGradQ; ++q) x[q] = src[q];
+      } else {
 #pragma unroll
-      for (int q = 0; q < kGradQ; ++q) vk_grad[(int64_t)q * n_vk + vk] = (float)acc[q].value();
-    }
-  }
-}
-
-__global__ void __launch_bounds__(128, 3) preprocess_bwd_kernel(
-    const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
-    const float* __restrict__ sh, const float* __restrict__ cov3d, const float* __restrict__ opacity, int64_t n,
-    const potr_camera* __restrict__ cams, int n_views, potr_raster_config cfg, const uint32_t* __restrict__ touched,
-    const float* __restrict__ vk_grad, float* __restrict__ g_means, float* __restrict__ g_log_scales,
-    float* __restrict__ g_quats, float* __restrict__ g_logits, float* __restrict__ g_sh) {
-  const float kA = -0.5f * kLog2e;
-  const int64_t n_vk = (int64_t)n_views * n;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    float gmu[3] = {0.0f, 0.0f, 0.0f};
-    float G3[3][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
-    float go = 0.0f;
-    float gsh[48], shc[48];
+        for (int q = 0; q < kGradQ; ++q) x[q] = 0.0f;
+      }
+      // the owner of slot e is the last lane whose segment starts at or before e; its segment
+      // starts at lane `head` of this chunk
+      uint32_t owner = 0;
 #pragma unroll
-    for (int i = 0; i < 48; ++i) gsh[i] = 0.0f;
-    bool have_sh = false, used = false;
-    const float mu[3] = {means[k], means[n + k], means[2 * n + k]};
-    const float Sg[3][3] = {{cov3d[k], cov3d[n + k], cov3d[2 * n + k]},
-                            {cov3d[n + k], cov3d[3 * n + k], cov3d[4 * n + k]},
-                            {cov3d[2 * n + k], cov3d[4 * n + k], cov3d[5 * n + k]}};
-    for (int v = 0; v < n_views; ++v) {
-      const int64_t vk = (int64_t)v * n + k;
-      if (!touched[vk]) continue;
-      float gq[kGradQ];
-      bool nz = false;
+      for (int b = 16; b >= 1; b >>= 1) {
+        const uint32_t cand = owner + b;
+        const uint32_t cs = __shfl_sync(0xffffffffu, seg0, cand & 31);
+        if (cand < 32 && cs <= e) owner = cand;
+      }
+      const uint32_t os = __shfl_sync(0xffffffffu, seg0, owner);
+      const int head = os > c0 ? (int)(os - c0) : 0;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const bool take = lane - d >= head;
+#pragma unroll
+        for (int q = 0; q < kGradQ; ++q) {
+          const float y = __shfl_up_sync(0xffffffffu, x[q], d);
+          if (take) x[q] += y;
+        }
+      }
+      // my segment's slots in this chunk end at lane hi - 1 - c0, which now holds their sum
+      const uint32_t lo = max(seg0, c0), hi = min(seg1, c0 + 32u);
+      const int src_lane = lo < hi ? (int)(hi - 1u - c0) : lane;
 #pragma unroll
       for (int q = 0; q < kGradQ; ++q) {
-        gq[q] = vk_grad[(int64_t)q * n_vk + vk];
-        nz |= gq[q] != 0.0f;
+        const float y = __shfl_sync(0xffffffffu, x[q], src_lane);
+        if (lo < hi) gq[q] += y;
       }
-      if (!nz) continue;
-      used = true;
-      if (!have_sh) {
+    }
+    float res[kVkOut];
 #pragma unroll
-        for (int i = 0; i < 48; ++i) shc[i] = __ldg(sh + (int64_t)i * n + k);
-        have_sh = true;
-      }
+    for (int q = 0; q < kVkOut; ++q) res[q] = 0.0f;
+    bool nz = false;
+#pragma unroll
+    for (int q = 0; q < kGradQ; ++q) nz |= gq[q] != 0.0f;
+    if (vk < n_vk && cnt && nz) {
+      const int v = (int)((uint32_t)vk / (uint32_t)n);  // n_views * n < 2^32
+      const int64_t k = vk - (int64_t)v * n;
+      const float mu[3] = {means[k], means[n + k], means[2 * n + k]};
+      const float Sg[3][3] = {{cov3d[k], cov3d[n + k], cov3d[2 * n + k]},
+                              {cov3d[n + k], cov3d[3 * n + k], cov3d[4 * n + k]},
+                              {cov3d[2 * n + k], cov3d[4 * n + k], cov3d[5 * n + k]}};
       const potr_camera& cam = cams[v];
       const float* W = cam.w2c;
       // forward recomputation (values only)
@@ -476,17 +499,17 @@ __global__ void __launch_bounds__(128, 3) preprocess_bwd_kernel(
       const float gc = -(gca * cb * cb + gcb * cb * cc + gcc * cc * cc);
       const float gb = -(2.0f * gca * ca * cb + gcb * (ca * cc + cb * cb) + 2.0f * gcc * cb * cc);
       const float G2[2][2] = {{ga, 0.5f * gb}, {0.5f * gb, gc}};
-      // Sigma gradient T^T G2 T
+      // Sigma gradient T^T G2 T (symmetric: the six entries on and above the diagonal)
       float G2T[2][3];
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         G2T[0][j] = G2[0][0] * Tm[0][j] + G2[0][1] * Tm[1][j];
         G2T[1][j] = G2[1][0] * Tm[0][j] + G2[1][1] * Tm[1][j];
       }
+      const int ii[6] = {0, 0, 0, 1, 1, 2}, jj[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) G3[i][j] += Tm[0][i] * G2T[0][j] + Tm[1][i] * G2T[1][j];
+      for (int e6 = 0; e6 < 6; ++e6)
+        res[3 + e6] = Tm[0][ii[e6]] * G2T[0][jj[e6]] + Tm[1][ii[e6]] * G2T[1][jj[e6]];
       // T gradient 2 G2 T Sigma, then J gradient (dL/dT) W_rot^T
       float gT[2][3];
 #pragma unroll
@@ -516,9 +539,83 @@ __global__ void __launch_bounds__(128, 3) preprocess_bwd_kernel(
       gt[1] += gq[1] * cam.fy * iz;
       gt[2] += -gq[0] * cam.fx * t[0] * iz2 - gq[1] * cam.fy * t[1] * iz2;
 #pragma unroll
-      for (int j = 0; j < 3; ++j) gmu[j] += W[j] * gt[0] + W[4 + j] * gt[1] + W[8 + j] * gt[2];
-      // colour: clamp mask, SH coefficients, direction
-      float shc_w[16];
+      for (int j = 0; j < 3; ++j) res[j] = W[j] * gt[0] + W[4 + j] * gt[1] + W[8 + j] * gt[2];
+      res[9] = gq[5];
+      res[10] = gq[6];
+      res[11] = gq[7];
+      res[12] = gq[8];
+    }
+    if (vk < n_vk) {
+#pragma unroll
+      for (int q = 0; q < kVkOut; ++q) out[vk * kVkOut + q] = res[q];
+    }
+  }
+}
+
+// Per splat: the per-view results summed in view order, the SH colour adjoint (clamp mask,
+// coefficients and the direction from the camera), then the activation adjoint (Sigma = M M^T,
+// M = R diag(exp(log_scale)), quaternion normalisation, sigmoid).  A block takes 32 splats with
+// one warp per colour channel: warp c holds the 16 coefficients of channel c and their 16
+// gradients, and its share of the direction gradient (linear in the weighted coefficients);
+// warp 0 adds the three shares in channel order and finishes the splat.
+constexpr int kSplatBwdThreads = 96;
+
+__global__ void __launch_bounds__(kSplatBwdThreads, 5) splat_bwd_kernel(
+    const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
+    const float* __restrict__ sh, const float* __restrict__ opacity, int64_t n, const potr_camera* __restrict__ cams,
+    int n_views, const float* __restrict__ vk_res, float* __restrict__ g_means, float* __restrict__ g_log_scales,
+    float* __restrict__ g_quats, float* __restrict__ g_logits, float* __restrict__ g_sh) {
+  __shared__ float s_gdir[2][3][32];  // channels 1 and 2: their direction gradients
+  const int lane = threadIdx.x & 31, ch = threadIdx.x >> 5;
+  const int64_t n_vk = (int64_t)n_views * n;
+  for (int64_t k0 = (int64_t)blockIdx.x * 32; k0 < n; k0 += (int64_t)gridDim.x * 32) {
+    const int64_t k = k0 + lane;
+    const bool live = k < n;
+    float gp[3] = {0.0f, 0.0f, 0.0f}, gd[3] = {0.0f, 0.0f, 0.0f};
+    float G6[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    float go = 0.0f;
+    float gsh[16], shc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) gsh[i] = 0.0f;
+    bool used = false;
+    float mu[3] = {0.0f, 0.0f, 0.0f};
+    if (live) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) shc[i] = __ldg(sh + (int64_t)(i * 3 + ch) * n + k);
+      mu[0] = means[k];
+      mu[1] = means[n + k];
+      mu[2] = means[2 * n + k];
+    }
+    float rn[kVkOut];  // the next view's values, loaded one view ahead
+    if (live) {
+#pragma unroll
+      for (int q = 0; q < kVkOut; ++q) rn[q] = vk_res[k * kVkOut + q];
+    }
+#pragma unroll 1
+    for (int v = 0; live && v < n_views; ++v) {
+      float r[kVkOut];
+      bool nz = false;
+#pragma unroll
+      for (int q = 0; q < kVkOut; ++q) {
+        r[q] = rn[q];
+        nz |= r[q] != 0.0f;
+      }
+      if (v + 1 < n_views) {
+        const int64_t vk1 = (int64_t)(v + 1) * n + k;
+#pragma unroll
+        for (int q = 0; q < kVkOut; ++q) rn[q] = vk_res[vk1 * kVkOut + q];
+      }
+      if (!nz) continue;
+      used = true;
+      if (ch == 0) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gp[j] += r[j];
+#pragma unroll
+        for (int e6 = 0; e6 < 6; ++e6) G6[e6] += r[3 + e6];
+        go += r[9];
+      }
+      // colour of this channel: clamp mask, coefficients, direction
+      const float* W = cams[v].w2c;
       float cpos[3];
 #pragma unroll
       for (int j = 0; j < 3; ++j) cpos[j] = -(W[j] * W[3] + W[4 + j] * W[7] + W[8 + j] * W[11]);
@@ -527,84 +624,90 @@ __global__ void __launch_bounds__(128, 3) preprocess_bwd_kernel(
       const float dx = u0 * inv_len, dy = u1 * inv_len, dz = u2 * inv_len;
       float Y[16];
       sh_basis16(dx, dy, dz, Y);
-      float gv[3];
+      float acc = 0.0f;
 #pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        float acc = 0.0f;
+      for (int i = 0; i < 16; ++i) acc = fmaf(shc[i], Y[i], acc);
+      const float gcol = ch == 0 ? r[10] : (ch == 1 ? r[11] : r[12]);  // (no dynamic register index)
+      const float gv = (acc + 0.5f > 0.0f) ? gcol : 0.0f;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) acc = fmaf(shc[i * 3 + ch], Y[i], acc);
-        gv[ch] = (acc + 0.5f > 0.0f) ? gq[6 + ch] : 0.0f;
+      for (int i = 0; i < 16; ++i) gsh[i] += gv * Y[i];
+      if (gv != 0.0f) {  // d colour / d direction = sum_i shc_i grad Y_i, times gv
+        float gdx, gdy, gdz;
+        sh_weighted_grad(dx, dy, dz, shc, gdx, gdy, gdz);
+        gdx *= gv;
+        gdy *= gv;
+        gdz *= gv;
+        const float dotg = gdx * dx + gdy * dy + gdz * dz;
+        gd[0] += (gdx - dx * dotg) * inv_len;
+        gd[1] += (gdy - dy * dotg) * inv_len;
+        gd[2] += (gdz - dz * dotg) * inv_len;
       }
+    }
+    if (ch > 0) {
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        shc_w[i] = 0.0f;
+      for (int j = 0; j < 3; ++j) s_gdir[ch - 1][j][lane] = gd[j];
+    }
+    __syncthreads();
+    if (live) {
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-          gsh[i * 3 + ch] += gv[ch] * Y[i];
-          shc_w[i] += gv[ch] * shc[i * 3 + ch];
+      for (int i = 0; i < 16; ++i) g_sh[(int64_t)(i * 3 + ch) * n + k] = used ? gsh[i] : 0.0f;
+    }
+    if (live && ch == 0) {
+      if (!used) {  // no pixel of any view took the splat (also a splat culled for non-finite parameters)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) g_means[j * n + k] = g_log_scales[j * n + k] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) g_quats[j * n + k] = 0.0f;
+        g_logits[k] = 0.0f;
+      } else {
+        float gmu[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gmu[j] = gp[j] + ((gd[j] + s_gdir[0][j][lane]) + s_gdir[1][j][lane]);
+        const float G3[3][3] = {{G6[0], G6[1], G6[2]}, {G6[1], G6[3], G6[4]}, {G6[2], G6[4], G6[5]}};
+        // activation adjoint: Sigma = M M^T, M = R diag(s), s = exp(log_scale), R(q / |q|)
+        float s[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) s[j] = expf(log_scales[j * n + k]);
+        float qw = quats[k], qx = quats[n + k], qy = quats[2 * n + k], qz = quats[3 * n + k];
+        const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+        const float iqn = qn > 0.0f ? 1.0f / qn : 0.0f;
+        qw *= iqn; qx *= iqn; qy *= iqn; qz *= iqn;
+        const float R[3][3] = {{1.0f - 2.0f * (qy * qy + qz * qz), 2.0f * (qx * qy - qw * qz), 2.0f * (qx * qz + qw * qy)},
+                               {2.0f * (qx * qy + qw * qz), 1.0f - 2.0f * (qx * qx + qz * qz), 2.0f * (qy * qz - qw * qx)},
+                               {2.0f * (qx * qz - qw * qy), 2.0f * (qy * qz + qw * qx), 1.0f - 2.0f * (qx * qx + qy * qy)}};
+        float gs[3] = {0.0f, 0.0f, 0.0f};
+        float gR[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            // dL/dM_ij = 2 (G3 M)_ij with M_lj = R_lj s_j
+            const float gM = 2.0f * (G3[i][0] * R[0][j] + G3[i][1] * R[1][j] + G3[i][2] * R[2][j]) * s[j];
+            gs[j] += gM * R[i][j];
+            gR[i][j] = gM * s[j];
+          }
+        const float gqw = 2.0f * (-qz * gR[0][1] + qy * gR[0][2] + qz * gR[1][0] - qx * gR[1][2] - qy * gR[2][0] + qx * gR[2][1]);
+        const float gqx = 2.0f * (qy * gR[0][1] + qz * gR[0][2] + qy * gR[1][0] - 2.0f * qx * gR[1][1] - qw * gR[1][2] +
+                                  qz * gR[2][0] + qw * gR[2][1] - 2.0f * qx * gR[2][2]);
+        const float gqy = 2.0f * (-2.0f * qy * gR[0][0] + qx * gR[0][1] + qw * gR[0][2] + qx * gR[1][0] + qz * gR[1][2] -
+                                  qw * gR[2][0] + qz * gR[2][1] - 2.0f * qy * gR[2][2]);
+        const float gqz = 2.0f * (-2.0f * qz * gR[0][0] - qw * gR[0][1] + qx * gR[0][2] + qw * gR[1][0] - 2.0f * qz * gR[1][1] +
+                                  qy * gR[1][2] + qx * gR[2][0] + qy * gR[2][1]);
+        const float dq = gqw * qw + gqx * qx + gqy * qy + gqz * qz;
+        g_quats[k] = (gqw - qw * dq) * iqn;
+        g_quats[n + k] = (gqx - qx * dq) * iqn;
+        g_quats[2 * n + k] = (gqy - qy * dq) * iqn;
+        g_quats[3 * n + k] = (gqz - qz * dq) * iqn;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          g_log_scales[j * n + k] = gs[j] * s[j];
+          g_means[j * n + k] = gmu[j];
         }
+        const float o = opacity[k];
+        g_logits[k] = go * o * (1.0f - o);
       }
-      float gdx, gdy, gdz;
-      sh_weighted_grad(dx, dy, dz, shc_w, gdx, gdy, gdz);
-      const float dotg = gdx * dx + gdy * dy + gdz * dz;
-      gmu[0] += (gdx - dx * dotg) * inv_len;
-      gmu[1] += (gdy - dy * dotg) * inv_len;
-      gmu[2] += (gdz - dz * dotg) * inv_len;
-      go += gq[5];
     }
-    if (!used) {  // no pixel of any view took the splat (also a splat culled for non-finite parameters)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) g_means[j * n + k] = g_log_scales[j * n + k] = 0.0f;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) g_quats[j * n + k] = 0.0f;
-      g_logits[k] = 0.0f;
-#pragma unroll
-      for (int i = 0; i < 48; ++i) g_sh[(int64_t)i * n + k] = 0.0f;
-      continue;
-    }
-    // activation adjoint: Sigma = M M^T, M = R diag(s), s = exp(log_scale), R(q / |q|)
-    float s[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) s[j] = expf(log_scales[j * n + k]);
-    float qw = quats[k], qx = quats[n + k], qy = quats[2 * n + k], qz = quats[3 * n + k];
-    const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-    const float iqn = qn > 0.0f ? 1.0f / qn : 0.0f;
-    qw *= iqn; qx *= iqn; qy *= iqn; qz *= iqn;
-    const float R[3][3] = {{1.0f - 2.0f * (qy * qy + qz * qz), 2.0f * (qx * qy - qw * qz), 2.0f * (qx * qz + qw * qy)},
-                           {2.0f * (qx * qy + qw * qz), 1.0f - 2.0f * (qx * qx + qz * qz), 2.0f * (qy * qz - qw * qx)},
-                           {2.0f * (qx * qz - qw * qy), 2.0f * (qy * qz + qw * qx), 1.0f - 2.0f * (qx * qx + qy * qy)}};
-    float gs[3] = {0.0f, 0.0f, 0.0f};
-    float gR[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        // dL/dM_ij = 2 (G3 M)_ij with M_lj = R_lj s_j
-        const float gM = 2.0f * (G3[i][0] * R[0][j] + G3[i][1] * R[1][j] + G3[i][2] * R[2][j]) * s[j];
-        gs[j] += gM * R[i][j];
-        gR[i][j] = gM * s[j];
-      }
-    const float gqw = 2.0f * (-qz * gR[0][1] + qy * gR[0][2] + qz * gR[1][0] - qx * gR[1][2] - qy * gR[2][0] + qx * gR[2][1]);
-    const float gqx = 2.0f * (qy * gR[0][1] + qz * gR[0][2] + qy * gR[1][0] - 2.0f * qx * gR[1][1] - qw * gR[1][2] +
-                              qz * gR[2][0] + qw * gR[2][1] - 2.0f * qx * gR[2][2]);
-    const float gqy = 2.0f * (-2.0f * qy * gR[0][0] + qx * gR[0][1] + qw * gR[0][2] + qx * gR[1][0] + qz * gR[1][2] -
-                              qw * gR[2][0] + qz * gR[2][1] - 2.0f * qy * gR[2][2]);
-    const float gqz = 2.0f * (-2.0f * qz * gR[0][0] - qw * gR[0][1] + qx * gR[0][2] + qw * gR[1][0] - 2.0f * qz * gR[1][1] +
-                              qy * gR[1][2] + qx * gR[2][0] + qy * gR[2][1]);
-    const float dq = gqw * qw + gqx * qx + gqy * qy + gqz * qz;
-    g_quats[k] = (gqw - qw * dq) * iqn;
-    g_quats[n + k] = (gqx - qx * dq) * iqn;
-    g_quats[2 * n + k] = (gqy - qy * dq) * iqn;
-    g_quats[3 * n + k] = (gqz - qz * dq) * iqn;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      g_log_scales[j * n + k] = gs[j] * s[j];
-      g_means[j * n + k] = gmu[j];
-    }
-    const float o = opacity[k];
-    g_logits[k] = go * o * (1.0f - o);
-#pragma unroll
-    for (int i = 0; i < 48; ++i) g_sh[(int64_t)i * n + k] = gsh[i];
+    __syncthreads();  // s_gdir is rewritten by the next group of splats
   }
 }
 
@@ -629,18 +732,17 @@ extern "C" potr_status potr_loss_grad(const potr_frame* frame, const float* d_im
   loss_grad_kernel<<<kLossBlocks, 256, 0, s>>>(d_images, d_targets, n_elems, lambda, d_dL_dimages, block_sums);
   POTR_CHECK_LAUNCH();
   if (d_loss) {
-    loss_finish_kernel<<<1, 1, 0, s>>>(block_sums, kLossBlocks, n_elems, d_loss);
+    loss_finish_kernel<<<1, 256, 0, s>>>(block_sums, kLossBlocks, n_elems, d_loss);
     POTR_CHECK_LAUNCH();
   }
   return POTR_OK;
 }
 
-extern "C" size_t potr_render_backward_workspace_size(int64_t instance_capacity) {
-  return sizeof(float) * (size_t)potr::kGradQ * (size_t)(instance_capacity > 0 ? instance_capacity : 0);
+extern "C" size_t potr_render_backward_workspace_size(int64_t instance_capacity, int64_t n_view_splats) {
+  if (instance_capacity <= 0 || n_view_splats <= 0) return 0;
+  return sizeof(float) * ((size_t)potr::kGradQ * (size_t)instance_capacity +
+                          (size_t)potr::kVkOut * (size_t)n_view_splats);
 }
-
-// Extra workspace for the per-(view, splat) sums: 9 floats per vk, after the instance partials.
-static size_t vk_grad_bytes(int64_t n_vk) { return sizeof(float) * (size_t)potr::kGradQ * (size_t)n_vk; }
 
 extern "C" potr_status potr_render_backward(const potr_scene* scene, const potr_views* views, const potr_frame* frame,
                                             const potr_raster_config* cfg, const uint32_t* d_vals,
@@ -662,12 +764,12 @@ extern "C" potr_status potr_render_backward(const potr_scene* scene, const potr_
   if (frame->total_tiles <= 0 || frame->total_tiles > 0x7fffffffll || !frame->cams || !frame->info)
     return POTR_ERR_INVALID_ARGUMENT;
   const int64_t n_vk = (int64_t)frame->n_views * scene->n;
-  const size_t inst_bytes = potr_render_backward_workspace_size(instance_capacity);
-  if (instance_capacity <= 0 || !d_ws || ws_bytes < inst_bytes + vk_grad_bytes(n_vk)) return POTR_ERR_INVALID_ARGUMENT;
+  if (instance_capacity <= 0 || !d_ws || ws_bytes < potr_render_backward_workspace_size(instance_capacity, n_vk))
+    return POTR_ERR_INVALID_ARGUMENT;
+  const size_t inst_bytes = sizeof(float) * (size_t)kGradQ * (size_t)instance_capacity;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   float* inst_grad = static_cast<float*>(d_ws);
-  if (cudaMemsetAsync(inst_grad, 0, potr_render_backward_workspace_size(instance_capacity), s) != cudaSuccess)
-    return POTR_ERR_CUDA;
+  if (cudaMemsetAsync(inst_grad, 0, inst_bytes, s) != cudaSuccess) return POTR_ERR_CUDA;
   const size_t smem = bwd_smem_bytes();
   const bool recompute = d_t_final == nullptr;
   TileQueue q;
@@ -700,20 +802,20 @@ extern "C" potr_status potr_render_backward(const potr_scene* scene, const potr_
   }
   POTR_CHECK_LAUNCH();
   const int64_t n = scene->n;
-  float* vk_grad = reinterpret_cast<float*>(static_cast<char*>(d_ws) + inst_bytes);
+  float* vk_res = reinterpret_cast<float*>(static_cast<char*>(d_ws) + inst_bytes);
   {
-    int64_t gw = (n_vk + 127) / 128;
-    if (gw > 152 * 32) gw = 152 * 32;
-    vk_grad_sum_kernel<<<(unsigned)gw, 128, 0, s>>>(views->touched, views->offsets, views->n_instances,
-                                                     instance_capacity, n_vk, inst_grad, vk_grad);
+    int64_t gw = (n_vk + kVkThreads - 1) / kVkThreads;
+    if (gw > 152 * 8) gw = 152 * 8;
+    vk_bwd_kernel<<<(unsigned)gw, kVkThreads, 0, s>>>(views->touched, views->offsets, views->n_instances, instance_capacity,
+                                               n, frame->n_views, inst_grad, scene->means, views->cov3d, frame->cams,
+                                               *cfg, vk_res);
     POTR_CHECK_LAUNCH();
   }
-  int64_t g = (n + 127) / 128;
+  int64_t g = (n + 31) / 32;
   if (g > 152 * 64) g = 152 * 64;
-  preprocess_bwd_kernel<<<(unsigned)g, 128, 0, s>>>(
-      scene->means, scene->log_scales, scene->quats, scene->sh, views->cov3d, views->opacity, n, frame->cams,
-      frame->n_views, *cfg, views->touched, vk_grad, grads->means, grads->log_scales, grads->quats,
-      grads->opacity_logits, grads->sh);
+  splat_bwd_kernel<<<(unsigned)g, kSplatBwdThreads, 0, s>>>(scene->means, scene->log_scales, scene->quats, scene->sh,
+                                               views->opacity, n, frame->cams, frame->n_views, vk_res, grads->means,
+                                               grads->log_scales, grads->quats, grads->opacity_logits, grads->sh);
   POTR_CHECK_LAUNCH();
   return POTR_OK;
 }

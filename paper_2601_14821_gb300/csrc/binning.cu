@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
       const uint4 m = cull[vk];
       cnt = m.w & 0x7fffffffu;
       if (cnt) {
-        const potr_view_info& vi = info[(int)(vk / (uint64_t)n)];
+        const potr_view_info& vi = info[(int)(vk / (uint32_t)n)];  // n * n_views < 2^32
         const uint32_t rw = m.z;
         const uint32_t tiles_x = (uint32_t)vi.tiles_x;
         corner = (uint32_t)vi.tile_base + ((rw >> 11) & 0x7ffu) * tiles_x + (rw & 0x7ffu);

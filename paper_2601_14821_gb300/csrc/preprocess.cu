@@ -5,8 +5,9 @@
 //   activate_kernel   one thread per splat: scale = exp(log_scale), q / |q|, Sigma = (R S)(R S)^T,
 //                     o = sigmoid(logit).  View independent, so it runs once per frame.
 //   project_kernel    one thread per splat, looping over the frame's views: the splat's
-//                     centre, covariance, opacity and (on first visibility) its 48 SH
-//                     coefficients are read once and kept in registers for all views.
+//                     centre, covariance and opacity are read once and kept in registers, its
+//                     48 SH coefficients (on first visibility) in the thread's own column of
+//                     shared memory, for all views.
 // Both are HBM-bound: 32 B read / 28 B written per splat for activation; 40 B read per splat
 // plus 192 B of SH per splat visible in the frame, and 48 B written per visible (view, splat).
 #include "potr_device.cuh"
@@ -91,7 +92,9 @@ __device__ __forceinline__ void sh_basis16(float x, float y, float z, float* Y) 
   Y[15] = -0.5900435899266435f * x * (xx - 3.0f * yy);
 }
 
-__global__ void __launch_bounds__(256) project_kernel(const float* __restrict__ means, const float* __restrict__ cov3d,
+constexpr int kProjectThreads = 128;
+
+__global__ void __launch_bounds__(kProjectThreads, 8) project_kernel(const float* __restrict__ means, const float* __restrict__ cov3d,
                                                       const float* __restrict__ opacity, const float* __restrict__ sh,
                                                       int64_t n, const potr_camera* __restrict__ cams,
                                                       const potr_view_info* __restrict__ info, int n_views,
@@ -99,6 +102,7 @@ __global__ void __launch_bounds__(256) project_kernel(const float* __restrict__ 
                                                       float* __restrict__ depth_out, uint2* __restrict__ rect_out,
                                                       uint32_t* __restrict__ touched_out,
                                                       potr_device_status* __restrict__ status) {
+  __shared__ float s_sh[48][kProjectThreads];  // each thread's own column: no sharing, no barrier
   const float kA = -0.5f * kLog2e;  // exact: a power-of-two scaling
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     const float mu0 = means[k], mu1 = means[n + k], mu2 = means[2 * n + k];
@@ -106,10 +110,10 @@ __global__ void __launch_bounds__(256) project_kernel(const float* __restrict__ 
     const float S11 = cov3d[3 * n + k], S12 = cov3d[4 * n + k], S22 = cov3d[5 * n + k];
     const float o = opacity[k];
     const float pthr = log2f(cfg.alpha_min / o) - 0.01f;  // conservative prefilter, see render
-    float shc[48];
-    bool have_sh = false;
+    bool sh_checked = false;  // the SH coefficients wait in shared memory after the first use
     // non-finite centre or activation input (NaN opacity from activate_kernel): culled in every view
     bool bad = !(isfinite(mu0) && isfinite(mu1) && isfinite(mu2) && isfinite(o));
+#pragma unroll 1
     for (int v = 0; v < n_views; ++v) {
       const int64_t vk = (int64_t)v * n + k;
       if (bad) {
@@ -184,14 +188,15 @@ __global__ void __launch_bounds__(256) project_kernel(const float* __restrict__ 
         continue;
       }
       // SH colour along the camera-to-splat direction (values only: plain fp32 arithmetic)
-      if (!have_sh) {
+      if (!sh_checked) {
         bool fin = true;
 #pragma unroll
         for (int i = 0; i < 48; ++i) {
-          shc[i] = __ldg(sh + (int64_t)i * n + k);
-          fin = fin && isfinite(shc[i]);
+          const float c = __ldg(sh + (int64_t)i * n + k);
+          s_sh[i][threadIdx.x] = c;
+          fin = fin && isfinite(c);
         }
-        have_sh = true;
+        sh_checked = true;
         if (!fin) {  // a non-finite SH coefficient: culled here and in the later views (not seen before)
           bad = true;
           touched_out[vk] = 0;
@@ -211,7 +216,7 @@ __global__ void __launch_bounds__(256) project_kernel(const float* __restrict__ 
       for (int ch = 0; ch < 3; ++ch) {
         float acc = 0.0f;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) acc = fmaf(shc[i * 3 + ch], Y[i], acc);
+        for (int i = 0; i < 16; ++i) acc = fmaf(s_sh[i * 3 + ch][threadIdx.x], Y[i], acc);
         rgb[ch] = fmaxf(acc + 0.5f, 0.0f);
       }
       const uint32_t rw = pack_rect_word((uint32_t)x0, (uint32_t)y0, (uint32_t)(x1 - x0));
@@ -375,7 +380,7 @@ extern "C" potr_status potr_preprocess(const potr_scene* scene, const potr_frame
                                                                           scene->opacity_logits, n, views->cov3d,
                                                                           views->opacity);
   POTR_CHECK_LAUNCH();
-  potr::project_kernel<<<potr::grid_for(n, 256, 152 * 16), 256, 0, s>>>(
+  potr::project_kernel<<<potr::grid_for(n, potr::kProjectThreads, 152 * 32), potr::kProjectThreads, 0, s>>>(
       scene->means, views->cov3d, views->opacity, scene->sh, n, frame->cams, frame->info, frame->n_views, *cfg,
       reinterpret_cast<float4*>(views->raster), views->depth, reinterpret_cast<uint2*>(views->rect), views->touched,
       d_status);

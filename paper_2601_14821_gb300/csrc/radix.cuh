@@ -17,8 +17,8 @@ constexpr int kSpinLimit = 1 << 22;
 // -----------------------------------------------------------------------------------------
 // Stable LSD radix sort, 8-bit digits, one kernel per pass ("onesweep": Adinets & Merrill,
 // 2022).  One read of the keys builds the digit histograms of every pass; then each pass
-// ranks 4096 items per block stably (per-warp equal-digit masks from ballots, warps in
-// order), publishes its per-digit counts, finds the counts of all earlier blocks by decoupled
+// ranks 4096 items per block stably (per-warp equal-digit masks built by shared-memory ORs,
+// warps in order), publishes its per-digit counts, finds the counts of all earlier blocks by decoupled
 // look-back over the published words, and writes its items grouped by digit through shared
 // memory so that the global stores are contiguous runs.  Blocks take their item range from an
 // atomic counter, so every block a look-back waits on is already running; the wait is bounded
@@ -44,7 +44,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan256(uint32_t x, uint32_t
 }
 
 // Decoupled look-back for digit t of block `tile`: the sum of the counts published by blocks
-// 0 .. tile-1 (walking back until an inclusive prefix).  Eight predecessors' words are loaded
+// 0 .. tile-1 (walking back until an inclusive prefix).  Four predecessors' words are loaded
 // at once (independent loads) and consumed nearest first; a word that is not yet published
 // restarts the window there.  After spin_limit such restarts the wait ends: *err is set and the
 // partial sum returned.
@@ -74,9 +74,12 @@ __device__ __forceinline__ uint64_t lookback_prefix(volatile unsigned long long*
     }
     if (done) break;
     p -= used;
-    if (stalled && ++spins > spin_limit) {
-      *err = 1;
-      break;
+    if (stalled) {
+      if (++spins > spin_limit) {
+        *err = 1;
+        break;
+      }
+      __nanosleep(64);  // leave the issue slots to the blocks that do work meanwhile
     }
   }
   return excl;
@@ -113,8 +116,8 @@ __global__ void __launch_bounds__(kOsThreads, 5) onesweep_kernel(const uint32_t*
     s_tile = atomicAdd(tile_counter, 1u);
     s_err = 0;
   }
-  for (int w = 0; w < 8; ++w) warp_cnt[w * 257 + threadIdx.x] = 0;
-  if (threadIdx.x < 8) warp_cnt[threadIdx.x * 257 + 256] = 0;
+  for (int w = 0; w < 8; ++w) warp_cnt[w * 257 + threadIdx.x] = s_vals[w * 257 + threadIdx.x] = 0;
+  if (threadIdx.x < 8) warp_cnt[threadIdx.x * 257 + 256] = s_vals[threadIdx.x * 257 + 256] = 0;
   __syncthreads();
   const uint32_t tile = s_tile;
   const int64_t m = m_dev ? (int64_t)*m_dev : m_host;
@@ -123,22 +126,31 @@ __global__ void __launch_bounds__(kOsThreads, 5) onesweep_kernel(const uint32_t*
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   // Keys (and ranks) stay in registers; values are loaded only when they are scattered, and
-  // digits are recomputed from the keys, so that four blocks fit on an SM.
+  // digits are recomputed from the keys, so that five blocks fit on an SM.
   const int64_t ibase = base + warp * (kOsItems * 32) + lane;  // item r is ibase + 32 r
   const int nv = (int)min((int64_t)kOsItems, (m - ibase + 31) / 32);  // items r < nv are valid
   uint32_t k[kOsItems], lr[kOsItems];
 #pragma unroll
   for (int r = 0; r < kOsItems; ++r) k[r] = r < nv ? keys_in[ibase + 32 * r] : 0u;
-  // stable rank inside the warp: rounds in order, lanes in order
+  // stable rank inside the warp: rounds in order, lanes in order.  The lanes holding the same
+  // digit find each other through a per-warp mask word per digit (each lane ORs in its bit; the
+  // result does not depend on the order of the ORs), kept in the value staging area, which is
+  // unused until the scatter; the round's lowest such lane adds the count and clears the word.
   uint32_t* wc = warp_cnt + warp * 257;
+  uint32_t* wm = s_vals + warp * 257;
 #pragma unroll
   for (int r = 0; r < kOsItems; ++r) {
     const uint32_t d = r < nv ? (k[r] >> shift) & 0xffu : 256u;
-    const uint32_t peers = match_low_bits<9>(d);  // d <= 256
+    atomicOr(&wm[d], 1u << lane);
+    __syncwarp();
+    const uint32_t peers = wm[d];
     const uint32_t rank = __popc(peers & lt);
     const uint32_t c0 = wc[d];
     __syncwarp();
-    if (rank == 0) wc[d] = c0 + __popc(peers);
+    if (rank == 0) {
+      wc[d] = c0 + __popc(peers);
+      wm[d] = 0u;
+    }
     __syncwarp();
     lr[r] = c0 + rank;
   }

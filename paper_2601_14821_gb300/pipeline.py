@@ -181,8 +181,8 @@ class RemovalEffectFrame:
 
     def render_backward(self, dL_dimages, grads: dict, t_final=None, n_last=None, stream=None):
         """Parameter gradients (dict of tensors shaped like the scene, overwritten)."""
-        ws = self.pool.get("bwd_ws", B.potr_render_backward_workspace_size(self.capacity)
-                           + 36 * self.n_views * self.n, torch.uint8)
+        ws = self.pool.get("bwd_ws", B.potr_render_backward_workspace_size(self.capacity, self.n_views * self.n),
+                           torch.uint8)
         g = B.SceneGrads(*(grads[k].data_ptr() for k in SCENE_KEYS))
         B.potr_render_backward(self.scene_c, self.views, self.frame, self.cfg, self.vals, self.ranges, t_final, n_last,
                                dL_dimages, self.capacity, g, ws, stream, order=self.order)
