@@ -253,7 +253,8 @@ POTR_API potr_status potr_render(const potr_views* views, const potr_frame* fram
  * pass over the composited splats that forms, with S_{>i} = P_K - P_{i+1} (suffix sum),
  *   PD_i  = alpha_i / (1 - alpha_i) S_{>i} - T_i alpha_i c_i     (Eq. pruning difference)
  *   dSE_i = sum_ch PD_i (PD_i + 2 (c - c_t))                      (Eq. pixel squared error)
- * reduced per (tile, splat) in a fixed order (warp transpose-sum, then warps in order) into
+ * reduced per (tile, splat) in a fixed order (warp transpose-sums over each 8 x 8 pixel block,
+ * then the tile's blocks in order) into
  * d_inst_dse[emission slot] (float, instance_capacity entries, required; the same capacity
  * as potr_bin_sort -- when the frame's instance count exceeded it, nothing is reduced and
  * d_dmse / d_importance / d_dsse_view are left untouched).  Then, per
@@ -267,15 +268,18 @@ POTR_API potr_status potr_render(const potr_views* views, const potr_frame* fram
  * binary64, needs d_inst_imp) the per-view importance I_k(v) = (sum_x T alpha) / P_v (the
  * weights of the SH energy compaction).  d_images (nullable) receives the
  * render.  d_targets: planar [3][H][W] per view at offset 3 * pixel_base.  d_tile_order as in
- * potr_render.
+ * potr_render.  d_ws: potr_removal_workspace_size(instance_capacity, total_tiles, d_inst_imp !=
+ * NULL) bytes of device scratch (the per-block sums before they are added per tile).
  */
+POTR_API size_t potr_removal_workspace_size(int64_t instance_capacity, int64_t total_tiles, int32_t with_importance);
 POTR_API potr_status potr_removal_effect(const potr_views* views, const potr_frame* frame, const potr_raster_config* cfg,
                                 int64_t n, const uint32_t* d_vals, const uint32_t* d_tile_ranges,
                                 uint32_t* d_tile_order, const float* d_targets, int32_t n_views_total,
                                 int64_t instance_capacity,
                                 float* d_inst_dse,
                                 float* d_inst_imp, double* d_dmse, double* d_importance, double* d_dsse_view,
-                                double* d_imp_view, float* d_images, potr_stream_t stream);
+                                double* d_imp_view, float* d_images, void* d_ws, size_t ws_bytes,
+                                potr_stream_t stream);
 
 /* Gradients of a scene's parameters: the same SoA planes as potr_scene (device, overwritten). */
 typedef struct {

@@ -94,8 +94,9 @@ SIGNATURES = {
                              _P, _P, _SZ, _P]),
     "potr_render": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _P, _P, _P, _P, _P,
                            _P, _P]),
+    "potr_removal_workspace_size": (_SZ, [_I64, _I64, _I32]),
     "potr_removal_effect": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _P, _P, _P,
-                                   _P, _I32, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
+                                   _P, _I32, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "potr_tile_schedule_workspace_size": (_SZ, []),
     "potr_tile_schedule": (_I32, [C.POINTER(Frame), _P, _P, _P, _SZ, _P]),
     "potr_pair_stats": (_I32, [C.POINTER(Views), C.POINTER(Frame), C.POINTER(RasterConfig), _I64, _P, _P, _P, _P]),
@@ -221,14 +222,18 @@ def potr_render(views: Views, frame: Frame, cfg: RasterConfig, n: int, vals, ran
                                             stream_handle(stream)))
 
 
+def potr_removal_workspace_size(capacity: int, total_tiles: int, with_importance: bool) -> int:
+    return int(lib().potr_removal_workspace_size(capacity, total_tiles, 1 if with_importance else 0))
+
+
 def potr_removal_effect(views: Views, frame: Frame, cfg: RasterConfig, n: int, vals, ranges, targets,
                         n_views_total: int, capacity: int, inst_dse, inst_imp=None, dmse=None, importance=None,
-                        dsse_view=None, images=None, stream=None, order=None, imp_view=None):
+                        dsse_view=None, images=None, stream=None, order=None, imp_view=None, ws=None):
     _check("potr_removal_effect",
            lib().potr_removal_effect(C.byref(views), C.byref(frame), C.byref(cfg), n, ptr(vals), ptr(ranges),
                                      ptr(order), ptr(targets), n_views_total, capacity, ptr(inst_dse), ptr(inst_imp),
                                      ptr(dmse), ptr(importance), ptr(dsse_view), ptr(imp_view), ptr(images),
-                                     stream_handle(stream)))
+                                     ptr(ws), 0 if ws is None else ws.numel(), stream_handle(stream)))
 
 
 def potr_tile_schedule_workspace_size() -> int:

@@ -2,12 +2,12 @@
 // (Section IV-B), plus the per-splat reduction into dMSE_k and I_k (Section IV-B last
 // equation, Section IV-A).
 //
-// One CTA of 128 threads per (view, tile): four warps, each on an 8 x 8 block of the tile, two
-// vertically adjacent pixels per lane, their binary32 arithmetic in packed pairs (tile_pass.cuh).
-// The tile's depth-sorted list is walked in batches; each batch's 48-byte raster records are
-// gathered into shared memory with cp.async (16-byte copies), so every pixel of the tile reads
-// them as shared-memory broadcasts.  The per-pair work is plain FP32 ALU: these kernels are
-// bound by instruction issue, not by HBM (one record gather serves 256 pixels).
+// Warps work on their own: each takes (tile, 8 x 8 block) items from a queue (longest tile
+// lists first), two vertically adjacent pixels per lane, their binary32 arithmetic in packed
+// pairs (tile_pass.cuh).  A warp gathers the 48-byte raster records of its tile's depth-sorted
+// list into a ring of its own in shared memory with cp.async (16-byte copies), 32 list
+// positions at a time, so its 64 pixels read them as shared-memory broadcasts.  The per-pair
+// work is plain FP32 ALU: these kernels are bound by instruction issue, not by HBM.
 //
 // Removal effect: after the forward walk (c, T_final, n_last per pixel) the same list is
 // walked back to front, recovering T_i = T_{i+1} / (1 - alpha_i) and accumulating the
@@ -16,11 +16,10 @@
 // which equals the paper's P_i - P_{i+1} / (1 - alpha_i) + alpha_i / (1 - alpha_i) P_K because
 // P_K - P_{i+1} = S_{>i}; every term is a sum of non-negative numbers, so no prefix sums are
 // subtracted.  dSE_i = sum_ch PD_i (PD_i + 2 (c - c_t)).  Per (tile, splat) the 256 pixel
-// values are summed without atomics: each lane adds its two pixels, then 8 consecutive splats
-// at a time a warp transpose-sum leaves lane l with its warp's total for splat l, the warp
-// totals of a whole batch go to shared memory, and after one barrier the 4 warp totals are
-// added in warp order.  The order is fixed, so the result does not depend on scheduling or on
-// the splat-batch size.
+// values are summed without atomics: each lane adds its two pixels, then 8 splats at a time a
+// warp transpose-sum leaves a lane with its block's total for one splat, and the last of the
+// tile's four blocks to finish adds the four block totals in block order.  The order is fixed,
+// so the result does not depend on scheduling.
 #include <atomic>
 
 #include "raster_common.cuh"
@@ -92,34 +91,51 @@ __device__ __forceinline__ float warp_transpose_sum8(float (&v)[8]) {
 
 constexpr int kChunk = 8;  // splats per warp transpose-sum
 
-template <int BATCH, bool IMP>
-constexpr size_t removal_smem_bytes() {
-  return sizeof(float4) * (2 * kSRec2 + kERec) * BATCH + sizeof(float) * kW2 * BATCH * (IMP ? 2 : 1);
-}
+// Removal pass with independent warps.  Each warp takes (tile, 8 x 8 block) items of its own
+// (longest lists first), walks the tile's list forward at its 64 pixels, then back to front
+// over positions [0, top) of its block (top = the block's largest n_last), staging the records
+// itself, 32 positions at a time, in its own ring: no barrier couples the warps.  Per position,
+// the block's sums over its pixels (warp transpose-sums) go to part[position][block] in global
+// memory; the last of a tile's four blocks to finish (an arrival counter per tile) adds the four
+// blocks in block order -- a block contributes 0 at positions it never reached -- and writes each
+// (tile, splat) sum to the instance's emission slot.  The sums and their order are those of a
+// tile-wide walk whose warps meet at every batch; only the waiting is gone.
+struct RemovalScratch {
+  float4* part_d;        // [instances] block sums of dSE, blocks 0..3 in x..w
+  float4* part_i;        // [instances] block sums of T alpha (importance), or null
+  uint4* tile_top;       // [tiles] the four blocks' top positions
+  uint32_t* tile_arrive;  // [tiles] blocks finished (zero before the launch)
+};
 
-template <int BATCH, bool IMP>
+constexpr size_t kRemovalWarpF4 = kWarpSmemF4 + 16;  // + 64 floats of group sums per warp
+
+template <bool IMP>
 __global__ void __launch_bounds__(kT2, 8) removal_kernel(const float4* __restrict__ raster,
                                                        const uint32_t* __restrict__ vals,
                                                        const uint32_t* __restrict__ ranges,
                                                        const potr_view_info* __restrict__ info, int n_views,
-                                                       potr_raster_config cfg, const float* __restrict__ targets,
-                                                       float* __restrict__ images, float* __restrict__ inst_dse,
-                                                       float* __restrict__ inst_imp, const uint4* __restrict__ cull,
-                                                       const uint32_t* __restrict__ offsets, TileQueue queue) {
+                                                       int64_t total_tiles, potr_raster_config cfg,
+                                                       const float* __restrict__ targets, float* __restrict__ images,
+                                                       float* __restrict__ inst_dse, float* __restrict__ inst_imp,
+                                                       const uint4* __restrict__ cull,
+                                                       const uint32_t* __restrict__ offsets, TileQueue queue,
+                                                       RemovalScratch scr) {
   extern __shared__ float4 dyn[];
-  float4* smem = dyn;                                                // [2][BATCH][kSRec2] raster records
-  float4* ex = dyn + 2 * kSRec2 * BATCH;                             // [BATCH][kERec] expanded records
-  float* red_d = reinterpret_cast<float*>(ex + kERec * BATCH);       // [kW2][BATCH] warp sums of dSE
-  float* red_i = red_d + kW2 * BATCH;                                // [kW2][BATCH] warp sums of T alpha
-  __shared__ uint32_t max_last_w[kW2];
-  __shared__ uint32_t s_slot;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4* ring = dyn + warp * kRemovalWarpF4;                               // kWRing staged groups
+  float4* ex = ring + kWRing * kWSlot;                                      // [32][kERec] expanded
+  float* gsum_d = reinterpret_cast<float*>(ring + kWarpSmemF4);             // [32] this group's sums
+  float* gsum_i = gsum_d + 32;                                              // [32]
+  float* part_d = reinterpret_cast<float*>(scr.part_d);
+  float* part_i = reinterpret_cast<float*>(scr.part_i);
+  int64_t stride_next = (int64_t)blockIdx.x * kW2 + warp;
   int64_t tile;
-  for (bool first = true; next_tile(queue, &s_slot, first, tile); first = false) {
-    const Tile2 c = tile2_ctx(info, n_views, ranges, cfg, tile);
+  int blk;
+  while (next_block_item(queue, total_tiles, stride_next, tile, blk)) {
+    const Tile2 c = tile2_block_ctx(info, n_views, ranges, cfg, tile, blk);
     f2_t C[3], T;
     uint32_t last0, last1;
-    forward_walk2<BATCH>(smem, ex, raster, vals, c, cfg, C, T, last0, last1);
+    forward_walk_w(ring, raster, vals, c, cfg, C, T, last0, last1);
 
     // 2 (c - c_t) per channel and pixel (0 outside the image)
     f2_t e2[3];
@@ -138,148 +154,151 @@ __global__ void __launch_bounds__(kT2, 8) removal_kernel(const float4* __restric
         }
       }
     }
-    const uint32_t warp_last = __reduce_max_sync(0xffffffffu, max(last0, last1));
-    if (lane == 0) max_last_w[warp] = warp_last;
-    __syncthreads();
-    uint32_t max_last = 0;
-#pragma unroll
-    for (int w = 0; w < kW2; ++w) max_last = max(max_last, max_last_w[w]);
+    const uint32_t top = __reduce_max_sync(0xffffffffu, max(last0, last1));
     const f2_t fx2 = f2s(c.fx), fy2 = f2(c.fy0, c.fy1);
 
-    // Back to front over list positions [0, max_last): T_i = T_{i+1} / (1 - alpha_i),
-    // S = sum of T_j alpha_j c_j over the composited j > i.  Each warp visits the splats its
-    // block test keeps, 8 at a time, highest position first.
+    // Back to front over positions [0, top): T_i = T_{i+1} / (1 - alpha_i), S = sum of
+    // T_j alpha_j c_j over the composited j > i.  The splats the block test keeps are visited
+    // 8 at a time, highest position first.
     f2_t S[3] = {f2s(0.0f), f2s(0.0f), f2s(0.0f)};
-    float* my_d = red_d + warp * BATCH;
-    float* my_i = red_i + warp * BATCH;
-    const uint32_t nb = (max_last + BATCH - 1) / BATCH;
-    Stager2<BATCH> st;
-    if (nb > 0) {
-      const uint32_t lo0 = max_last > (uint32_t)BATCH ? max_last - BATCH : 0u;
-      st.load(vals, c.s + lo0, (int)(max_last - lo0));
-      st.issue(smem, raster);  // the forward walk's reads of smem ended at the barrier above
+    const uint32_t ng = (top + 31) / 32;
+    if (ng > 0) {
+      const uint32_t g0 = 32 * (ng - 1);
+      warp_stage(ring + kWSlot * ((ng - 1) % kWRing), raster, vals, c.s + g0, (int)(top - g0));
     }
-    if (nb > 1) {
-      const uint32_t hi1 = max_last - BATCH, lo1 = hi1 > (uint32_t)BATCH ? hi1 - BATCH : 0u;
-      st.load(vals, c.s + lo1, (int)(hi1 - lo1));
-    }
-    for (uint32_t k = 0; k < nb; ++k) {
-      const uint32_t top = max_last - k * BATCH;
-      const uint32_t lo = top > (uint32_t)BATCH ? top - BATCH : 0u;
-      const int cnt = (int)(top - lo);
-      const float4* buf = smem + kSRec2 * BATCH * (k & 1);
-      if (k > 0) __syncthreads();  // batch k-1 (records, warp sums) fully consumed
-      if (k + 1 < nb) {
-        st.issue(smem + kSRec2 * BATCH * ((k + 1) & 1), raster);
+    for (uint32_t gg = ng; gg-- > 0;) {
+      const uint32_t g0 = 32 * gg;
+      const int cnt = (int)min(32u, top - g0);
+      if (gg > 0) {
+        warp_stage(ring + kWSlot * ((gg - 1) % kWRing), raster, vals, c.s + g0 - 32, 32);
         cp_async_wait2<1>();
-        if (k + 2 < nb) {
-          const uint32_t hi2 = lo - BATCH, lo2 = hi2 > (uint32_t)BATCH ? hi2 - BATCH : 0u;
-          st.load(vals, c.s + lo2, (int)(hi2 - lo2));
-        }
       } else {
         cp_async_wait2<0>();
       }
-      for (int j = lane; j < cnt; j += 32) {
-        my_d[j] = 0.0f;
-        if (IMP) my_i[j] = 0.0f;
-      }
-      expand_own<BATCH>(buf, ex, cnt);
-      __syncthreads();  // every thread's expanded records of batch k are visible
-      for (int ghi = cnt; ghi > 0; ghi -= 32) {
-        const int glo = ghi > 32 ? ghi - 32 : 0;
-        if (lo + (uint32_t)glo >= warp_last) continue;  // warp-uniform: nothing composited here
-        const int jl = glo + lane;
-        const bool cand = jl < ghi && lo + (uint32_t)jl < warp_last && block_may_pass_e(ex + kERec * jl, c.bx0, c.by0);
-        uint32_t m = __ballot_sync(0xffffffffu, cand);
-        while (m) {
-          float d[kChunk], im[kChunk];
-          int mypos = -1;
-          bool any = false;
+      if (lane < cnt) expand_record(ring + kWSlot * (gg % kWRing) + kSRec2 * lane, ex + kERec * lane);
+      gsum_d[lane] = 0.0f;
+      if (IMP) gsum_i[lane] = 0.0f;
+      __syncwarp();  // the group's expanded records and zeroed sums are visible
+      const bool cand = lane < cnt && block_may_pass_e(ex + kERec * lane, c.bx0, c.by0);
+      uint32_t m = __ballot_sync(0xffffffffu, cand);
+      while (m) {
+        float d[kChunk], im[kChunk];
+        int mypos = -1;
+        bool any = false;
 #pragma unroll
-          for (int u = 0; u < kChunk; ++u) {
-            d[u] = 0.0f;
-            if (IMP) im[u] = 0.0f;
-            if (m) {
-              const int b = 31 - __clz(m);
-              m &= ~(1u << b);
-              const int j = glo + b;
-              if (lane == u) mypos = j;
-              const uint32_t pos = lo + (uint32_t)j;
-              const float4* e = ex + kERec * j;
-              f2_t o2;
-              float thr, indef;
-              const f2_t p2 = exponent_e(e, fx2, fy2, o2, thr, indef);
-              float p0, p1;
-              f2split(p2, p0, p1);
-              const bool pass0 = pos < last0 && p0 >= thr, pass1 = pos < last1 && p1 >= thr;
-              if (__any_sync(0xffffffffu, pass0 || pass1)) {  // warp-uniform: branch-free below
-                float a0, a1;
-                f2split(mul2(o2, exp2r2_rec(p2, indef)), a0, a1);
-                a0 = fminf(cfg.alpha_max, a0);
-                a1 = fminf(cfg.alpha_max, a1);
-                const bool ok0 = pass0 && a0 >= cfg.alpha_min, ok1 = pass1 && a1 >= cfg.alpha_min;
-                // a pixel that does not take the splat: alpha 0 and 1 / (1 - alpha) = 1, so its
-                // T, S and dSE do not change (every update adds or scales by exact zeros and ones)
-                const float q0 = __fdividef(1.0f, 1.0f - a0), q1 = __fdividef(1.0f, 1.0f - a1);
-                const f2_t ae = f2(ok0 ? a0 : 0.0f, ok1 ? a1 : 0.0f);
-                const f2_t rcp = f2(ok0 ? q0 : 1.0f, ok1 ? q1 : 1.0f);
-                T = mul2(T, rcp);                      // T_i = T_{i+1} / (1 - alpha_i)
-                const f2_t w = mul2(ae, T);            // T_i alpha_i
-                const f2_t ratio = mul2(ae, rcp);      // alpha_i / (1 - alpha_i)
-                const f2_t nw = sub2(f2s(0.0f), w);    // -T_i alpha_i (exact)
-                const ulonglong2 q3 = reinterpret_cast<const ulonglong2*>(e)[3];
-                const ulonglong2 q4 = reinterpret_cast<const ulonglong2*>(e)[4];
-                const f2_t nwc0 = mul2(nw, q3.y), nwc1 = mul2(nw, q4.x), nwc2 = mul2(nw, q4.y);
-                // PD = alpha / (1 - alpha) S - T alpha c, one rounding per channel
-                const f2_t pd0 = fma2(ratio, S[0], nwc0);
-                const f2_t pd1 = fma2(ratio, S[1], nwc1);
-                const f2_t pd2 = fma2(ratio, S[2], nwc2);
-                f2_t dse = mul2(pd0, add2(pd0, e2[0]));  // sum_ch PD (PD + 2 (c - c_t))
-                dse = fma2(pd1, add2(pd1, e2[1]), dse);
-                dse = fma2(pd2, add2(pd2, e2[2]), dse);
-                S[0] = sub2(S[0], nwc0);  // S + T alpha c
-                S[1] = sub2(S[1], nwc1);
-                S[2] = sub2(S[2], nwc2);
-                float x0, x1;
-                f2split(dse, x0, x1);
-                d[u] = x0 + x1;
-                if (IMP) {
-                  f2split(w, x0, x1);
-                  im[u] = x0 + x1;
-                }
-                any = true;
+        for (int u = 0; u < kChunk; ++u) {
+          d[u] = 0.0f;
+          if (IMP) im[u] = 0.0f;
+          if (m) {
+            const int j = 31 - __clz(m);
+            m &= ~(1u << j);
+            if (lane == u) mypos = j;
+            const uint32_t pos = g0 + (uint32_t)j;
+            const float4* e = ex + kERec * j;
+            f2_t o2;
+            float thr, indef;
+            const f2_t p2 = exponent_e(e, fx2, fy2, o2, thr, indef);
+            float p0, p1;
+            f2split(p2, p0, p1);
+            const bool pass0 = pos < last0 && p0 >= thr, pass1 = pos < last1 && p1 >= thr;
+            if (__any_sync(0xffffffffu, pass0 || pass1)) {  // warp-uniform: branch-free below
+              float a0, a1;
+              f2split(mul2(o2, exp2r2_rec(p2, indef)), a0, a1);
+              a0 = fminf(cfg.alpha_max, a0);
+              a1 = fminf(cfg.alpha_max, a1);
+              const bool ok0 = pass0 && a0 >= cfg.alpha_min, ok1 = pass1 && a1 >= cfg.alpha_min;
+              // a pixel that does not take the splat: alpha 0 and 1 / (1 - alpha) = 1, so its
+              // T, S and dSE do not change (every update adds or scales by exact zeros and ones)
+              const float q0 = __fdividef(1.0f, 1.0f - a0), q1 = __fdividef(1.0f, 1.0f - a1);
+              const f2_t ae = f2(ok0 ? a0 : 0.0f, ok1 ? a1 : 0.0f);
+              const f2_t rcp = f2(ok0 ? q0 : 1.0f, ok1 ? q1 : 1.0f);
+              T = mul2(T, rcp);                      // T_i = T_{i+1} / (1 - alpha_i)
+              const f2_t w = mul2(ae, T);            // T_i alpha_i
+              const f2_t ratio = mul2(ae, rcp);      // alpha_i / (1 - alpha_i)
+              const f2_t nw = sub2(f2s(0.0f), w);    // -T_i alpha_i (exact)
+              const ulonglong2 q3 = reinterpret_cast<const ulonglong2*>(e)[3];
+              const ulonglong2 q4 = reinterpret_cast<const ulonglong2*>(e)[4];
+              const f2_t nwc0 = mul2(nw, q3.y), nwc1 = mul2(nw, q4.x), nwc2 = mul2(nw, q4.y);
+              // PD = alpha / (1 - alpha) S - T alpha c, one rounding per channel
+              const f2_t pd0 = fma2(ratio, S[0], nwc0);
+              const f2_t pd1 = fma2(ratio, S[1], nwc1);
+              const f2_t pd2 = fma2(ratio, S[2], nwc2);
+              f2_t dse = mul2(pd0, add2(pd0, e2[0]));  // sum_ch PD (PD + 2 (c - c_t))
+              dse = fma2(pd1, add2(pd1, e2[1]), dse);
+              dse = fma2(pd2, add2(pd2, e2[2]), dse);
+              S[0] = sub2(S[0], nwc0);  // S + T alpha c
+              S[1] = sub2(S[1], nwc1);
+              S[2] = sub2(S[2], nwc2);
+              float x0, x1;
+              f2split(dse, x0, x1);
+              d[u] = x0 + x1;
+              if (IMP) {
+                f2split(w, x0, x1);
+                im[u] = x0 + x1;
               }
+              any = true;
             }
           }
-          float sd = 0.0f, si = 0.0f;
-          if (__any_sync(0xffffffffu, any)) {
-            sd = warp_transpose_sum8(d);
-            if (IMP) si = warp_transpose_sum8(im);
-          }
-          if (lane < kChunk && mypos >= 0) {
-            my_d[mypos] = sd;
-            if (IMP) my_i[mypos] = si;
-          }
+        }
+        float sd = 0.0f, si = 0.0f;
+        if (__any_sync(0xffffffffu, any)) {
+          sd = warp_transpose_sum8(d);
+          if (IMP) si = warp_transpose_sum8(im);
+        }
+        if (lane < kChunk && mypos >= 0) {
+          gsum_d[mypos] = sd;
+          if (IMP) gsum_i[mypos] = si;
         }
       }
-      __syncthreads();
-      // per (tile, splat): the 4 warp sums in warp order
-      for (int j = threadIdx.x; j < cnt; j += kT2) {
+      __syncwarp();  // the group's sums are complete
+      if (lane < cnt) {
+        part_d[(int64_t)(c.s + g0 + lane) * 4 + blk] = gsum_d[lane];
+        if (IMP) part_i[(int64_t)(c.s + g0 + lane) * 4 + blk] = gsum_i[lane];
+      }
+      __syncwarp();  // this slot, the expanded records and the sums are rewritten next
+    }
+
+    // arrival: the tile's last block to finish adds the four blocks' sums in block order
+    uint32_t arrived = 0;
+    if (lane == 0) reinterpret_cast<uint32_t*>(scr.tile_top)[tile * 4 + blk] = top;
+    __threadfence();  // every lane's sums, and the top, are visible device-wide before the count
+    __syncwarp();
+    if (lane == 0) arrived = atomicAdd(scr.tile_arrive + tile, 1u);
+    arrived = __shfl_sync(0xffffffffu, arrived, 0);
+    if (arrived == 3u) {
+      __threadfence();
+      const uint4 tops = __ldcg(scr.tile_top + tile);
+      const uint32_t mt = max(max(tops.x, tops.y), max(tops.z, tops.w));
+      for (uint32_t p0 = 0; p0 < mt; p0 += 32) {
+        const uint32_t pos = p0 + (uint32_t)lane;
+        if (pos >= mt) break;
+        const float4 bd = __ldcg(scr.part_d + c.s + pos);
         float sd = 0.0f, si = 0.0f;
-#pragma unroll
-        for (int w = 0; w < kW2; ++w) {
-          sd += red_d[w * BATCH + j];
-          if (IMP) si += red_i[w * BATCH + j];
+        sd += pos < tops.x ? bd.x : 0.0f;
+        sd += pos < tops.y ? bd.y : 0.0f;
+        sd += pos < tops.z ? bd.z : 0.0f;
+        sd += pos < tops.w ? bd.w : 0.0f;
+        if (IMP) {
+          const float4 bi = __ldcg(scr.part_i + c.s + pos);
+          si += pos < tops.x ? bi.x : 0.0f;
+          si += pos < tops.y ? bi.y : 0.0f;
+          si += pos < tops.z ? bi.z : 0.0f;
+          si += pos < tops.w ? bi.w : 0.0f;
         }
         if (sd != 0.0f || (IMP && si != 0.0f)) {
-          const uint32_t vk = vals[c.s + lo + j];
+          const uint32_t vk = vals[c.s + pos];
           const uint32_t slot = emission_slot(offsets[vk], cull[vk], c.tx, c.ty);  // L2
           inst_dse[slot] = sd;
           if (IMP) inst_imp[slot] = si;
         }
       }
     }
-  }  // tiles
+  }  // items
+}
+
+template <bool IMP>
+constexpr size_t removal_smem_bytes() {
+  return sizeof(float4) * kW2 * kRemovalWarpF4;
 }
 
 // Per splat k: dSSE_k(v) = sum over its emission slots (emission order), then
@@ -384,26 +403,33 @@ cudaError_t launch_render(const potr_views* views, const potr_frame* frame, cons
   return cudaGetLastError();
 }
 
-template <int BATCH, bool IMP>
+
+template <bool IMP>
 cudaError_t launch_removal(const potr_views* views, const potr_frame* frame, const potr_raster_config& cfg,
                            const uint32_t* vals, const uint32_t* ranges, const float* targets, float* images,
-                           float* inst_dse, float* inst_imp, const TileQueue& q, cudaStream_t s) {
-  constexpr size_t smem = removal_smem_bytes<BATCH, IMP>();
-  {
-    cudaError_t e = cudaFuncSetAttribute(removal_kernel<BATCH, IMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  // several CTAs of up to 64 KB each only fit with the largest shared-memory carveout
-  cudaError_t ce = cudaFuncSetAttribute(removal_kernel<BATCH, IMP>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                        (int)cudaSharedmemCarveoutMaxShared);
-  if (ce != cudaSuccess) return ce;
-  const unsigned grid = tile_grid(removal_kernel<BATCH, IMP>, smem, q, frame->total_tiles, kT2);
+                           float* inst_dse, float* inst_imp, const TileQueue& q, const RemovalScratch& scr,
+                           cudaStream_t s) {
+  constexpr size_t smem = removal_smem_bytes<IMP>();
+  cudaError_t e = cudaFuncSetAttribute(removal_kernel<IMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  // several CTAs per SM only fit with the largest shared-memory carveout
+  e = cudaFuncSetAttribute(removal_kernel<IMP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(scr.tile_arrive, 0, sizeof(uint32_t) * (size_t)frame->total_tiles, s);
+  if (e != cudaSuccess) return e;
+  // a persistent grid: every CTA that fits on the device at once, at most one warp per item
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, removal_kernel<IMP>, kT2, smem);
+  int64_t g = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  const int64_t need = (4 * frame->total_tiles + kW2 - 1) / kW2;
+  if (g > need) g = need;
   tile_timing_begin(s);
-  removal_kernel<BATCH, IMP><<<grid, kT2, smem, s>>>(reinterpret_cast<const float4*>(views->raster), vals, ranges,
-                                                          frame->info, frame->n_views, cfg, targets, images, inst_dse,
-                                                          inst_imp, reinterpret_cast<const uint4*>(views->cull),
-                                                          views->offsets, q);
+  removal_kernel<IMP><<<(unsigned)(g > 0 ? g : 1), kT2, smem, s>>>(
+      reinterpret_cast<const float4*>(views->raster), vals, ranges, frame->info, frame->n_views, frame->total_tiles,
+      cfg, targets, images, inst_dse, inst_imp, reinterpret_cast<const uint4*>(views->cull), views->offsets, q, scr);
   tile_timing_end(s);
   note_launches(1);
   return cudaGetLastError();
@@ -442,38 +468,67 @@ extern "C" potr_status potr_render(const potr_views* views, const potr_frame* fr
   return e == cudaSuccess ? POTR_OK : POTR_ERR_CUDA;
 }
 
+namespace potr {
+namespace {
+struct RemovalLayout {
+  size_t off_part_d, off_part_i, off_top, off_arrive, bytes;
+};
+RemovalLayout removal_layout(int64_t capacity, int64_t total_tiles, bool imp) {
+  auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+  RemovalLayout L{};
+  size_t o = 0;
+  L.off_part_d = o; o = up(o + sizeof(float4) * (size_t)capacity);
+  L.off_part_i = o; if (imp) o = up(o + sizeof(float4) * (size_t)capacity);
+  L.off_top = o; o = up(o + sizeof(uint4) * (size_t)total_tiles);
+  L.off_arrive = o; o = up(o + sizeof(uint32_t) * (size_t)total_tiles);
+  L.bytes = o;
+  return L;
+}
+}  // namespace
+}  // namespace potr
+
+extern "C" size_t potr_removal_workspace_size(int64_t instance_capacity, int64_t total_tiles,
+                                              int32_t with_importance) {
+  if (instance_capacity <= 0 || total_tiles <= 0) return 0;
+  return potr::removal_layout(instance_capacity, total_tiles, with_importance != 0).bytes;
+}
+
 extern "C" potr_status potr_removal_effect(const potr_views* views, const potr_frame* frame,
                                            const potr_raster_config* cfg, int64_t n, const uint32_t* d_vals,
                                            const uint32_t* d_tile_ranges, uint32_t* d_tile_order,
                                            const float* d_targets, int32_t n_views_total,
                                            int64_t instance_capacity, float* d_inst_dse, float* d_inst_imp,
                                            double* d_dmse, double* d_importance, double* d_dsse_view,
-                                           double* d_imp_view, float* d_images,
+                                           double* d_imp_view, float* d_images, void* d_ws, size_t ws_bytes,
                                            potr_stream_t stream) {
   using namespace potr;
-  if (!views || !frame || !valid_cfg(cfg) || !d_vals || !d_tile_ranges || !d_targets || !d_inst_dse)
+  if (!views || !frame || !valid_cfg(cfg) || !d_vals || !d_tile_ranges || !d_targets || !d_inst_dse || !d_ws)
     return POTR_ERR_INVALID_ARGUMENT;
   if (!views->raster || !views->touched || !views->offsets || !views->n_instances || !views->cull || !frame->info)
     return POTR_ERR_INVALID_ARGUMENT;
   if (n <= 0 || frame->n_views < 1 || n_views_total < 1 || instance_capacity <= 0) return POTR_ERR_INVALID_ARGUMENT;
   if (frame->total_tiles <= 0 || frame->total_tiles > 0x7fffffffll) return POTR_ERR_INVALID_ARGUMENT;
   if ((d_importance || d_imp_view) && !d_inst_imp) return POTR_ERR_INVALID_ARGUMENT;
+  const bool imp = d_inst_imp != nullptr;
+  if (ws_bytes < potr_removal_workspace_size(instance_capacity, frame->total_tiles, imp ? 1 : 0))
+    return POTR_ERR_INVALID_ARGUMENT;
+  const RemovalLayout L = removal_layout(instance_capacity, frame->total_tiles, imp);
+  char* ws = static_cast<char*>(d_ws);
+  RemovalScratch scr;
+  scr.part_d = reinterpret_cast<float4*>(ws + L.off_part_d);
+  scr.part_i = imp ? reinterpret_cast<float4*>(ws + L.off_part_i) : nullptr;
+  scr.tile_top = reinterpret_cast<uint4*>(ws + L.off_top);
+  scr.tile_arrive = reinterpret_cast<uint32_t*>(ws + L.off_arrive);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaMemsetAsync(d_inst_dse, 0, sizeof(float) * (size_t)instance_capacity, s) != cudaSuccess) return POTR_ERR_CUDA;
   if (d_inst_imp && cudaMemsetAsync(d_inst_imp, 0, sizeof(float) * (size_t)instance_capacity, s) != cudaSuccess)
     return POTR_ERR_CUDA;
-  const bool imp = d_inst_imp != nullptr;
   TileQueue q;
   if (make_queue(d_tile_order, frame->total_tiles, q, s) != cudaSuccess) return POTR_ERR_CUDA;
-  cudaError_t e;
-  switch (cfg->batch * 2 + (imp ? 1 : 0)) {
-    case 256: e = launch_removal<128, false>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, q, s); break;
-    case 257: e = launch_removal<128, true>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, q, s); break;
-    case 512: e = launch_removal<256, false>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, q, s); break;
-    case 513: e = launch_removal<256, true>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, q, s); break;
-    case 1024: e = launch_removal<512, false>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, q, s); break;
-    default: e = launch_removal<512, true>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images, d_inst_dse, d_inst_imp, q, s); break;
-  }
+  const cudaError_t e = imp ? launch_removal<true>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images,
+                                                   d_inst_dse, d_inst_imp, q, scr, s)
+                            : launch_removal<false>(views, frame, *cfg, d_vals, d_tile_ranges, d_targets, d_images,
+                                                    d_inst_dse, d_inst_imp, q, scr, s);
   if (e != cudaSuccess) return POTR_ERR_CUDA;
   if (d_dmse || d_importance || d_dsse_view || d_imp_view) {
     const int64_t g = (n + 255) / 256;  // one block per 256 splats (a warp per 32)

@@ -155,10 +155,12 @@ class RemovalEffectFrame:
     def removal_effect(self, targets, dmse, importance=None, n_views_total=None, dsse_view=None, images=None,
                        stream=None, imp_view=None):
         want_imp = importance is not None or imp_view is not None
+        ws = self.pool.get("removal_ws", B.potr_removal_workspace_size(self.capacity, self.total_tiles, want_imp),
+                           torch.uint8)
         B.potr_removal_effect(self.views, self.frame, self.cfg, self.n, self.vals, self.ranges, targets,
                               int(n_views_total or self.n_views), self.capacity, self.inst_dse,
                               self.inst_imp if want_imp else None, dmse, importance, dsse_view,
-                              images, stream, order=self.order, imp_view=imp_view)
+                              images, stream, order=self.order, imp_view=imp_view, ws=ws)
 
     def bind_scene(self, scene: dict):
         """Point the frame at other parameter tensors of the same size (e.g. autograd inputs)."""
