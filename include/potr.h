@@ -86,8 +86,9 @@ typedef struct {
 } potr_camera;
 
 /*
- * Rasterizer configuration.  tile_w * tile_h must be 256 (16x16, 8x32 or 32x8); batch is
- * the number of splats staged in shared memory per step (128, 256 or 512).  The remaining
+ * Rasterizer configuration.  tile_w * tile_h must be 256 (16x16, 8x32 or 32x8); batch must be
+ * 128, 256 or 512 and no longer changes anything (the tile kernels size their own staging of
+ * records; the field keeps earlier configurations valid).  The remaining
  * fields are the readings of the original 3DGS renderer the paper modifies (Section 3):
  *   near_z     cull when camera-space z <= near_z                         (default 0.2)
  *   lowpass    added to the diagonal of the 2D covariance, pixel^2       (default 0.3)

@@ -1,4 +1,4 @@
-"""Batched removal effect over many views, and the tile-shape x splat-batch autotuner.
+"""Batched removal effect over many views, and the tile-shape autotuner.
 
 The removal effect is summed over every view (Section IV-B), so a pass over hundreds of views of
 uneven resolution is split into view chunks; each chunk is one frame (one launch per stage
@@ -85,7 +85,7 @@ class BatchedRemovalEffect:
 
 
 TILE_SHAPES = ((16, 16), (8, 32), (32, 8))
-SPLAT_BATCHES = (128, 256, 512)
+SPLAT_BATCHES = (256,)  # the kernels no longer depend on the config field
 _CACHE: dict = {}
 
 

@@ -567,7 +567,6 @@ __global__ void __launch_bounds__(kSplatBwdThreads, 5) splat_bwd_kernel(
     float* __restrict__ g_quats, float* __restrict__ g_logits, float* __restrict__ g_sh) {
   __shared__ float s_gdir[2][3][32];  // channels 1 and 2: their direction gradients
   const int lane = threadIdx.x & 31, ch = threadIdx.x >> 5;
-  const int64_t n_vk = (int64_t)n_views * n;
   for (int64_t k0 = (int64_t)blockIdx.x * 32; k0 < n; k0 += (int64_t)gridDim.x * 32) {
     const int64_t k = k0 + lane;
     const bool live = k < n;

@@ -35,18 +35,20 @@ __device__ __forceinline__ f2_t f2(float lo, float hi) {
   return r;
 }
 __device__ __forceinline__ f2_t f2s(float x) { return f2(x, x); }
+__device__ __forceinline__ void f2split(f2_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
 __device__ __forceinline__ float f2lo(f2_t v) {
   float lo, hi;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+  f2split(v, lo, hi);
+  (void)hi;
   return lo;
 }
 __device__ __forceinline__ float f2hi(f2_t v) {
   float lo, hi;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+  f2split(v, lo, hi);
+  (void)lo;
   return hi;
-}
-__device__ __forceinline__ void f2split(f2_t v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
 __device__ __forceinline__ f2_t add2(f2_t a, f2_t b) {
   f2_t d;
