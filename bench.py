@@ -40,11 +40,14 @@ import numpy as np  # noqa: E402
 METRIC = "removal-effect views/s & Gblend/s (batched vs per-view); fwd+bwd ms/step"
 WORKLOAD = "scene"
 CFG = dict(tile_w=16, tile_h=16, batch=128)
-# Algorithmic FP32 work per pair (FMA = 2 FLOP), counted from the kernel's operation spec.
-# Only pairs whose opacity reaches the prefilter count (the rest provably have alpha < alpha_min
-# and are skipped without evaluation), once in the front-to-back walk and once back to front:
-FLOP_EXPONENT = 9        # dx, dy, A dx^2 + B dx dy + C dy^2
-FLOP_ALPHA = 17          # exp2 (3 add + 6 FMA), o * G, min
+# Algorithmic FP32 work (FMA = 2 FLOP), counted from the operation spec, in the units of the
+# method's per-pixel walks: every evaluated (pixel, list position) pair -- front to back up to the
+# pixel's termination, back to front over positions below its n_last -- needs its exponent and the
+# opacity decision; exp2 and alpha only where the exponent can reach alpha_min (the log-domain
+# comparison decides the rest exactly); compositing and the removal terms where the pixel
+# composites the splat.
+FLOP_EXPONENT = 9        # dx, dy, A dx^2 + B dx dy + C dy^2 (per evaluated pair)
+FLOP_ALPHA = 17          # exp2 (3 add + 6 FMA), o * G, min (per pair past the log-domain test)
 FLOP_COMPOSITE = 9       # T (1 - alpha), w = alpha T, three colour FMAs (composited pairs)
 FLOP_REMOVAL = 26        # T recovery, ratio, PD and dSE over 3 channels, suffix update (composited pairs)
 FLOP_BWD = 45            # backward, per composited pair: T recovery, dL/dalpha from the suffix, the nine
@@ -228,6 +231,19 @@ def tile_kernel_ms(B, torch, fn, reps: int) -> float:
     return float(np.mean([a.elapsed_time(b) for a, b in evs]))
 
 
+def render_flops(pc: dict) -> float:
+    return FLOP_EXPONENT * pc["examined"] + FLOP_ALPHA * pc["passed"] + FLOP_COMPOSITE * pc["composited"]
+
+
+def removal_flops(pc: dict) -> float:
+    return (FLOP_EXPONENT * (pc["examined"] + pc["back_positions"]) + FLOP_ALPHA * (pc["passed"] + pc["back_passed"])
+            + (FLOP_COMPOSITE + FLOP_REMOVAL) * pc["composited"])
+
+
+def bwd_flops(pc: dict) -> float:
+    return FLOP_EXPONENT * pc["back_positions"] + FLOP_ALPHA * pc["back_passed"] + FLOP_BWD * pc["composited"]
+
+
 def roofline_entry(kernel: str, flops: float, ms: float, views: int, workload: str) -> dict:
     achieved = flops / (ms / 1e3) / 1e12
     per_view = DRAM_BYTES_PER_VIEW.get(kernel)
@@ -385,14 +401,13 @@ def run_ours(args):
     pc = frame.pair_stats()
     torch.cuda.synchronize()
     pairs = pc["examined"] + pc["back_positions"]
-    flops = ((FLOP_EXPONENT + FLOP_ALPHA) * (pc["passed"] + pc["back_passed"])
-             + (FLOP_COMPOSITE + FLOP_REMOVAL) * pc["composited"])
+    flops = removal_flops(pc)
     t_removal = stage_ms[2] / 1e3
     gblend = world * pairs / t_removal / 1e9
     ms_removal_kernel = tile_kernel_ms(B, torch, lambda: frame.removal_effect(targets, dmse, imp), K)
     img_buf = frame.image_buffer()
     ms_render_kernel = tile_kernel_ms(B, torch, lambda: frame.render(img_buf), K)
-    flops_render = (FLOP_EXPONENT + FLOP_ALPHA) * pc["passed"] + FLOP_COMPOSITE * pc["composited"]
+    flops_render = render_flops(pc)
     rl_removal = roofline_entry("removal_kernel", flops, ms_removal_kernel, n_views, "scene")
     rl_render = roofline_entry("render_kernel", flops_render, ms_render_kernel, n_views, "scene")
     del img_buf
@@ -539,7 +554,7 @@ def fwd_bwd_step_ms(args, dev, D) -> dict:
     fr.loss_grad(img, targets, 0.2, dL, loss)
     ms_k = tile_kernel_ms(B, torch, lambda: fr.render_backward(dL, grads, tf, nl), max(3, args.steps))
     pc = fr.pair_stats()
-    flops = (FLOP_EXPONENT + FLOP_ALPHA) * pc["back_passed"] + FLOP_BWD * pc["composited"]
+    flops = bwd_flops(pc)
     out["pairs"] = pc
     out["roofline"] = roofline_entry("render_bwd_kernel", flops, ms_k, len(w.cameras), "grad")
     del fr
@@ -890,8 +905,7 @@ def multiview_config(args, dev, D, name: str, views_per_chunk, fwd_bwd: bool = F
     t0 = targets[: 3 * f0.total_pixels]
     pc0 = f0.pair_stats()
     ms_k = tile_kernel_ms(B, torch, lambda: f0.removal_effect(t0, dmse, imp, n_views_total=len(w.cameras)), steps)
-    flops0 = ((FLOP_EXPONENT + FLOP_ALPHA) * (pc0["passed"] + pc0["back_passed"])
-              + (FLOP_COMPOSITE + FLOP_REMOVAL) * pc0["composited"])
+    flops0 = removal_flops(pc0)
     out.update({"instances": int(n_inst), "pass_ms": eager_ms, "views_per_s": world * be.n_views / (eager_ms / 1e3),
                 "graph_pass_ms": graph_ms,
                 "graph_views_per_s": world * be.n_views / (graph_ms / 1e3) if isinstance(graph_ms, float) else None,
