@@ -24,7 +24,7 @@ constexpr int kSpinLimit = 1 << 22;
 // atomic counter, so every block a look-back waits on is already running; the wait is bounded
 // and reports POTR_ERR_TIMEOUT instead of hanging.
 // -----------------------------------------------------------------------------------------
-size_t onesweep_smem_bytes() { return sizeof(uint32_t) * 2 * kOsTile + sizeof(uint32_t) * (8 * 257 + 3 * 256); }
+size_t onesweep_smem_bytes() { return sizeof(uint32_t) * 2 * kOsTile + sizeof(uint32_t) * (8 * 257 + 2 * 256); }
 
 // Exclusive scan of one value per thread over a 256-thread block (returns this thread's prefix).
 __device__ __forceinline__ uint32_t block_exclusive_scan256(uint32_t x, uint32_t* tmp8) {
@@ -107,8 +107,7 @@ __global__ void __launch_bounds__(kOsThreads, 5) onesweep_kernel(const uint32_t*
   uint32_t* s_keys = os_smem;                                          // [kOsTile]
   uint32_t* s_vals = s_keys + kOsTile;                                 // [kOsTile]
   uint32_t* warp_cnt = s_vals + kOsTile;                               // [8][257]
-  uint32_t* blk_off = warp_cnt + 8 * 257;                              // [256]
-  uint32_t* dig_glob = blk_off + 256;                                  // [256]
+  uint32_t* dig_glob = warp_cnt + 8 * 257;                             // [256]
   uint32_t* tmp8 = dig_glob + 256;                                     // [8]
   __shared__ uint32_t s_tile;
   __shared__ int s_err;
@@ -173,15 +172,18 @@ __global__ void __launch_bounds__(kOsThreads, 5) onesweep_kernel(const uint32_t*
     excl = lookback_prefix(vst, tile, t, kSpinLimit, &s_err);
     vst[si] = kFlagInc | (excl + run);
   }
-  dig_glob[t] = gbase[t] + (uint32_t)excl;
-  blk_off[t] = block_exclusive_scan256(run, tmp8);
+  // the block's digit-t items start at bo in the block's digit order: item i of that order (a
+  // digit-t item) goes to dig_glob[t] + i, and an item of warp w goes to warp_cnt[w][t] + rank
+  const uint32_t bo = block_exclusive_scan256(run, tmp8);
+  dig_glob[t] = gbase[t] + (uint32_t)excl - bo;
+  for (int w = 0; w < 8; ++w) warp_cnt[w * 257 + t] += bo;
   __syncthreads();
   // items grouped by digit in shared memory: keys, then the values (loaded now)
 #pragma unroll
   for (int r = 0; r < kOsItems; ++r) {
     if (r < nv) {
       const uint32_t d = (k[r] >> shift) & 0xffu;
-      const uint32_t pos = blk_off[d] + warp_cnt[warp * 257 + d] + lr[r];
+      const uint32_t pos = warp_cnt[warp * 257 + d] + lr[r];
       s_keys[pos] = k[r];
       lr[r] = pos;
     }
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(kOsThreads, 5) onesweep_kernel(const uint32_t*
   for (int i = threadIdx.x; i < nvalid; i += kOsThreads) {
     const uint32_t key = s_keys[i];
     const uint32_t d = (key >> shift) & 0xffu;
-    const uint32_t o = dig_glob[d] + ((uint32_t)i - blk_off[d]);
+    const uint32_t o = dig_glob[d] + (uint32_t)i;
     keys_out[o] = key;
     vals_out[o] = s_vals[i];
   }
