@@ -248,7 +248,9 @@ def bwd_flops(pc: dict) -> float:
 
 def roofline_entry(kernel: str, flops: float, ms: float, views: int, workload: str) -> dict:
     achieved = flops / (ms / 1e3) / 1e12
-    per_view = DRAM_BYTES_PER_VIEW.get(kernel)
+    # the captures were made on the scene (tile kernels) and grad (backward) workloads; other
+    # workloads (other resolutions and densities) get no traffic figure
+    per_view = DRAM_BYTES_PER_VIEW.get(kernel) if workload in ("scene", "grad") else None
     return {"kernel": kernel, "workload": workload, "bound": "alu", "achieved": achieved,
             "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s", "frac": achieved / PEAK_FP32_TFLOPS,
             "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts and maximum clock)",
