@@ -551,6 +551,9 @@ def fwd_bwd_step_ms(args, dev, D) -> dict:
         torch.cuda.synchronize()
         out[mode] = D.max_over_ranks(a.elapsed_time(b), dev) / args.steps
     out["per_pixel_bytes_stored"] = 8
+    # memory of the two transmittance modes: the stored form keeps T_final (f32) and n_last (u32)
+    # per pixel between the forward and the backward pass; the recomputed form keeps nothing
+    out["memory_bytes"] = {"store": 8 * fr.total_pixels, "recompute": 0}
     # the backward tile kernel alone (stored transmittance), and its pair counts
     from paper_2601_14821_gb300 import _binding as B
 

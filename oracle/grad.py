@@ -139,23 +139,45 @@ def to_params(scene, requires_grad=True) -> dict:
             for k in PARAM_KEYS}
 
 
-def loss_and_grad(scene, cams, cfg, targets, lam: float = LAMBDA):
-    """(L, {param: dL/dparam as numpy binary64}, [images]) for the given views and targets."""
+def _masked_lists(lists, mask):
+    """The entries of the pixels where mask (bool [H * W]) holds; a pixel's list stays whole."""
+    if mask is None:
+        return lists
+    pix, k, rest = lists
+    keep = np.asarray(mask, bool).reshape(-1)[pix]
+    return pix[keep], k[keep], rest[keep]
+
+
+def loss_and_grad(scene, cams, cfg, targets, lam: float = LAMBDA, masks=None, n_elems: int | None = None):
+    """(L, {param: dL/dparam as numpy binary64}, [images]) for the given views and targets.
+
+    masks (optional, one bool [H, W] per view or None): the loss counts only those pixels (the
+    images are computed there only); n_elems (optional): the loss normaliser, 3 x the pixels of
+    the given views by default (a caller restricting a larger frame to some views passes the
+    frame's)."""
     p = to_params(scene)
     sigma, o = activate(p)
     imgs, terms = [], []
-    n_elems = sum(3 * c.pixels for c in cams)
+    if n_elems is None:
+        n_elems = sum(3 * c.pixels for c in cams)
     act = oracle.activate(scene)
-    for cam, tgt in zip(cams, targets):
+    for vi, (cam, tgt) in enumerate(zip(cams, targets)):
         v = oracle.prepare_view(scene, cam, cfg, act)
-        lists = oracle.pixel_lists(v, v["vals"], v["ranges"], cam, cfg)
+        mask = None if masks is None else masks[vi]
+        lists = _masked_lists(oracle.pixel_lists(v, v["vals"], v["ranges"], cam, cfg), mask)
         img = render_view(p, sigma, o, cam, cfg, lists)
         r = img - torch.from_numpy(np.asarray(tgt, np.float64))
-        terms.append(((1.0 - lam) * torch.abs(r) + lam * r * r).sum())
+        term = (1.0 - lam) * torch.abs(r) + lam * r * r
+        if mask is not None:
+            term = term * torch.from_numpy(np.asarray(mask, np.float64).reshape(cam.height, cam.width))
+        terms.append(term.sum())
         imgs.append(img.detach().numpy())
     loss = torch.stack(terms).sum() / n_elems
+    if not loss.requires_grad:  # no composited entry in any view: the loss does not depend on p
+        return float(loss), {k: np.zeros(v.shape) for k, v in p.items()}, imgs
     loss.backward()
-    return float(loss.detach()), {k: v.grad.numpy().copy() for k, v in p.items()}, imgs
+    return float(loss.detach()), {k: (v.grad.numpy().copy() if v.grad is not None else np.zeros(v.shape))
+                                  for k, v in p.items()}, imgs
 
 
 def oracle_loss(scene, cams, cfg, targets, lam: float = LAMBDA) -> tuple[float, list]:
@@ -261,7 +283,8 @@ def screen_grad(pr: dict, cam, cfg, tgt, lam: float, n_elems: int, pix, k) -> to
     return torch.cat([x[:, None] for x in g[:6]] + [g[6]], 1)
 
 
-def loss_grad_magnitude(scene, cams, cfg, targets, lam: float = LAMBDA) -> dict:
+def loss_grad_magnitude(scene, cams, cfg, targets, lam: float = LAMBDA, masks=None,
+                        n_elems: int | None = None) -> dict:
     """Per parameter element, a bound B_p >= |dL/dp| that also bounds every term the gradient is
     formed from: the scale against which a binary32 evaluation of the gradient is rounded.
 
@@ -277,8 +300,10 @@ def loss_grad_magnitude(scene, cams, cfg, targets, lam: float = LAMBDA) -> dict:
     at every stage: conic <- 2D covariance <- (Jacobian, Sigma); Jacobian and centre <- camera-
     space mean <- mean; colour <- (SH coefficients, basis); basis <- direction <- mean;
     Sigma <- M M^T <- (R, scales); R <- normalised quaternion <- quaternion; scale <- log-scale;
-    opacity <- logit.  Returns {param: B as numpy binary64 of the parameter's shape}."""
-    n_elems = sum(3 * c.pixels for c in cams)
+    opacity <- logit.  Returns {param: B as numpy binary64 of the parameter's shape}.  masks and
+    n_elems as in loss_and_grad."""
+    if n_elems is None:
+        n_elems = sum(3 * c.pixels for c in cams)
     act = oracle.activate(scene)
     n = scene.n
     P = {k: torch.tensor(np.asarray(getattr(scene, k), np.float64)) for k in PARAM_KEYS}
@@ -309,9 +334,10 @@ def loss_grad_magnitude(scene, cams, cfg, targets, lam: float = LAMBDA) -> dict:
     mu_l = _leaf(P["means"].T)                                       # [n, 3]
     sh_l = _leaf(P["sh"].permute(2, 0, 1).reshape(n, 48))            # [n, 16 * 3], index 3 i + ch
     sig_l = _leaf(Sig6)
-    for cam, tgt in zip(cams, targets):
+    for vi, (cam, tgt) in enumerate(zip(cams, targets)):
         v = oracle.prepare_view(scene, cam, cfg, act)
-        pix, k, _ = oracle.pixel_lists(v, v["vals"], v["ranges"], cam, cfg)
+        pix, k, _ = _masked_lists(oracle.pixel_lists(v, v["vals"], v["ranges"], cam, cfg),
+                                  None if masks is None else masks[vi])
         if pix.size == 0:
             continue
         # ---- view stages

@@ -284,3 +284,38 @@ def test_screen_magnitudes_equal_the_gradient_without_cancellation():
     assert np.all(np.abs(Gr[0]) > 0)
     # the pixel-centre offsets and the conic make both centre terms of each coordinate one sign
     assert np.allclose(Gm[0], np.abs(Gr[0]), rtol=1e-9, atol=0), (Gm[0], Gr[0])
+
+
+def test_pixel_masks_partition_the_loss_and_its_gradient(tiny):
+    """The loss is a sum over pixels, so restricting it to a set of pixels and to the rest
+    gives two losses and two gradients that add up to the whole (linearity over a partition);
+    a mask that holds everywhere changes nothing, one that holds nowhere gives exactly zero, and
+    the magnitude bounds of the two halves add up to the whole's."""
+    cfg = oracle.make_config()
+    cam = tiny.cameras[0]
+    v = oracle.prepare_view(tiny.scene, cam, cfg)
+    img, *_ = oracle.render(v, v["vals"], v["ranges"], cam, cfg)
+    tg = [(img + synth.target_noise(img.shape, 0.02, tiny.seed, 0)).astype(np.float32)]
+    H, W = cam.height, cam.width
+    rng = np.random.default_rng(5)
+    mask = np.zeros((H, W), bool)
+    for ty, tx in rng.integers(0, [H // 16, W // 16], size=(12, 2)):  # whole tiles, like the device test
+        mask[16 * ty:16 * ty + 16, 16 * tx:16 * tx + 16] = True
+    L, g, _ = G.loss_and_grad(tiny.scene, tiny.cameras, cfg, tg)
+    La, ga, _ = G.loss_and_grad(tiny.scene, tiny.cameras, cfg, tg, masks=[mask])
+    Lb, gb, _ = G.loss_and_grad(tiny.scene, tiny.cameras, cfg, tg, masks=[~mask])
+    L1, g1, _ = G.loss_and_grad(tiny.scene, tiny.cameras, cfg, tg, masks=[np.ones((H, W), bool)])
+    L0, g0, _ = G.loss_and_grad(tiny.scene, tiny.cameras, cfg, tg, masks=[np.zeros((H, W), bool)])
+    assert 0.0 < La < L and La + Lb == pytest.approx(L, rel=1e-12)
+    assert L1 == L and L0 == 0.0
+    for k in G.PARAM_KEYS:
+        np.testing.assert_allclose(ga[k] + gb[k], g[k], rtol=1e-9, atol=1e-15 * np.abs(g[k]).max())
+        assert np.array_equal(g1[k], g[k])
+        assert not np.any(g0[k])
+        assert np.count_nonzero(ga[k]) > 0
+    Ma = G.loss_grad_magnitude(tiny.scene, tiny.cameras, cfg, tg, masks=[mask])
+    Mb = G.loss_grad_magnitude(tiny.scene, tiny.cameras, cfg, tg, masks=[~mask])
+    M = G.loss_grad_magnitude(tiny.scene, tiny.cameras, cfg, tg)
+    for k in G.PARAM_KEYS:
+        np.testing.assert_allclose(Ma[k] + Mb[k], M[k], rtol=1e-9, atol=1e-15 * M[k].max())
+        assert np.all(np.abs(ga[k]) <= Ma[k] * (1 + 1e-9) + 1e-300)
