@@ -205,6 +205,10 @@ MUT += [
     ("gm_centre_cross", GR, "am * ((ca * dx).abs() + (cb * dy).abs())", "am * (ca * dx).abs()"),
     ("gm_opacity_G", GR, "Mag * G_e * free", "Mag * free"),
     ("gm_resid_abs", GR, "gabs = gc.abs()[:, pix_t].T", "gabs = gc[:, pix_t].T"),
+    # pixel masks of the gradient oracle
+    ("g_mask_loss", GR, "term = term * torch.from_numpy(np.asarray(mask, np.float64).reshape(cam.height, cam.width))",
+     "term = term"),
+    ("g_mask_lists", GR, "keep = np.asarray(mask, bool).reshape(-1)[pix]", "keep = np.ones(pix.size, bool)"),
 ]
 
 
