@@ -180,7 +180,7 @@ MUT += [
     ("pass2_lam_luma", SH, "second[:, ch] = _ridge(G, b[:, ch], keep2, lams[ch])", "second[:, ch] = _ridge(G, b[:, ch], keep2, lams[0])"),
     ("dup_range", CO, "for _ in range(1 + extra.get(leaf[0], 0)):", "for _ in range(max(1, extra.get(leaf[0], 0))):"),
     ("tol_sq", CO, "return np.maximum(gamma, beta * np.min(np.array(d), axis=0))", "return np.maximum(gamma, beta * np.min(np.array(d), axis=0) ** 2)"),
-    ("g_power_half", GR, "power = -0.5 * (", "power = -1.0 * ("),
+    ("g_power_half", GR, "power = -0.5 * (pr[\"ca\"]", "power = -1.0 * (pr[\"ca\"]"),
     ("adam_bc2", AD, "bc2 = 1.0 - b2 ** t", "bc2 = 1.0 - b2 ** (t + 1)"),
     ("dmse_3P", OI, "out += d / (3.0 * cam.pixels) / n_views", "out += d / float(cam.pixels) / n_views"),
     ("imp_P", OI, "imp += i / float(cam.pixels) / n_views", "imp += i / n_views"),
@@ -192,7 +192,7 @@ MUT += [
     ("g_lowpass", GR, "c = cov[:, 1, 1] + cfg.lowpass", "c = cov[:, 1, 1]"),
     ("g_T_incl", GR, "Tv = torch.exp(excl - start[seg])", "Tv = torch.exp(cs - start[seg])"),
     ("g_relu", GR, "rgb = torch.relu(torch.einsum(\"icn,ni->nc\", p[\"sh\"], Y) + 0.5)", "rgb = torch.einsum(\"icn,ni->nc\", p[\"sh\"], Y) + 0.5"),
-    ("g_campos", GR, "campos = -(Wr.T @ tw)", "campos = -(Wr @ tw)"),
+    ("g_campos", GR, "campos = -(Wr.T @ tw)\n    d = mu - campos", "campos = -(Wr @ tw)\n    d = mu - campos"),
     ("g_qnorm", GR, "q = p[\"quats\"] / torch.linalg.norm(p[\"quats\"], dim=0, keepdim=True)", "q = p[\"quats\"]"),
     ("g_amax", GR, "alpha = torch.clamp(o[k_t] * torch.exp(power), max=float(cfg.alpha_max))", "alpha = o[k_t] * torch.exp(power)"),
     ("adam_v", AD, "v += (1.0 - b2) * g * g", "v += (1.0 - b2) * abs(g)"),
