@@ -259,9 +259,9 @@ POTR_API potr_status potr_render(const potr_views* views, const potr_frame* fram
  * d_inst_dse[emission slot] (float, instance_capacity entries, required; the same capacity
  * as potr_bin_sort -- when the frame's instance count exceeded it, nothing is reduced and
  * d_dmse / d_importance / d_dsse_view are left untouched).  Then, per
- * splat, the tile partials are summed in binary64 in emission order, giving
+ * splat, the tile partials are summed in emission order (a compensated binary32 sum), giving
  * dSSE_k(v) = sum_x dSE, and
- *   d_dmse[k] += dSSE_k(v) / (3 P_v n_views_total)        (views added in order)
+ *   d_dmse[k] += dSSE_k(v) / (3 P_v n_views_total)        (binary64, views added in order)
  * so that calls over consecutive view chunks compose (zero d_dmse before the first call).
  * With d_inst_imp / d_importance non-NULL the same is done for T_i alpha_i, giving
  * I_k += (sum_x T alpha) / (P_v n_views_total) (Section IV-A).  d_dsse_view (nullable,
