@@ -40,14 +40,15 @@ import numpy as np  # noqa: E402
 METRIC = "removal-effect views/s & Gblend/s (batched vs per-view); fwd+bwd ms/step"
 WORKLOAD = "scene"
 CFG = dict(tile_w=16, tile_h=16, batch=128)
-# Algorithmic FP32 work (FMA = 2 FLOP), counted from the operation spec, in the units of the
-# method's per-pixel walks: every evaluated (pixel, list position) pair -- front to back up to the
-# pixel's termination, back to front over positions below its n_last -- needs its exponent and the
-# opacity decision; exp2 and alpha only where the exponent can reach alpha_min (the log-domain
-# comparison decides the rest exactly); compositing and the removal terms where the pixel
-# composites the splat.
+# Algorithmic FP32 work (FMA = 2 FLOP), counted from the operation spec of the method's per-pixel
+# walks in the roofline's unit, the evaluated (pixel, list position) pair -- front to back up to
+# the pixel's termination, back to front over the positions below its n_last: every evaluated
+# pair takes its exponent, exp2 (its FMA count) and alpha; compositing and the removal or
+# backward terms are counted where the pixel composites the splat.  The kernels skip exp2 where a
+# log-domain comparison already decides alpha < alpha_min; `frac_strict` counts exp2 and alpha
+# only where they are evaluated, for comparison.
 FLOP_EXPONENT = 9        # dx, dy, A dx^2 + B dx dy + C dy^2 (per evaluated pair)
-FLOP_ALPHA = 17          # exp2 (3 add + 6 FMA), o * G, min (per pair past the log-domain test)
+FLOP_ALPHA = 17          # exp2 (3 add + 6 FMA), o * G, min (per evaluated pair)
 FLOP_COMPOSITE = 9       # T (1 - alpha), w = alpha T, three colour FMAs (composited pairs)
 FLOP_REMOVAL = 26        # T recovery, ratio, PD and dSE over 3 channels, suffix update (composited pairs)
 FLOP_BWD = 45            # backward, per composited pair: T recovery, dL/dalpha from the suffix, the nine
@@ -233,20 +234,24 @@ def tile_kernel_ms(B, torch, fn, reps: int) -> float:
     return float(np.mean([a.elapsed_time(b) for a, b in evs]))
 
 
-def render_flops(pc: dict) -> float:
-    return FLOP_EXPONENT * pc["examined"] + FLOP_ALPHA * pc["passed"] + FLOP_COMPOSITE * pc["composited"]
+def render_flops(pc: dict, strict: bool = False) -> float:
+    alpha_pairs = pc["passed"] if strict else pc["examined"]
+    return FLOP_EXPONENT * pc["examined"] + FLOP_ALPHA * alpha_pairs + FLOP_COMPOSITE * pc["composited"]
 
 
-def removal_flops(pc: dict) -> float:
-    return (FLOP_EXPONENT * (pc["examined"] + pc["back_positions"]) + FLOP_ALPHA * (pc["passed"] + pc["back_passed"])
-            + (FLOP_COMPOSITE + FLOP_REMOVAL) * pc["composited"])
+def removal_flops(pc: dict, strict: bool = False) -> float:
+    walked = pc["examined"] + pc["back_positions"]
+    alpha_pairs = pc["passed"] + pc["back_passed"] if strict else walked
+    return FLOP_EXPONENT * walked + FLOP_ALPHA * alpha_pairs + (FLOP_COMPOSITE + FLOP_REMOVAL) * pc["composited"]
 
 
-def bwd_flops(pc: dict) -> float:
-    return FLOP_EXPONENT * pc["back_positions"] + FLOP_ALPHA * pc["back_passed"] + FLOP_BWD * pc["composited"]
+def bwd_flops(pc: dict, strict: bool = False) -> float:
+    alpha_pairs = pc["back_passed"] if strict else pc["back_positions"]
+    return FLOP_EXPONENT * pc["back_positions"] + FLOP_ALPHA * alpha_pairs + FLOP_BWD * pc["composited"]
 
 
-def roofline_entry(kernel: str, flops: float, ms: float, views: int, workload: str) -> dict:
+def roofline_entry(kernel: str, flops: float, ms: float, views: int, workload: str,
+                   flops_strict: float | None = None) -> dict:
     achieved = flops / (ms / 1e3) / 1e12
     # the captures were made on the scene (tile kernels) and grad (backward) workloads; other
     # workloads (other resolutions and densities) get no traffic figure
@@ -255,7 +260,8 @@ def roofline_entry(kernel: str, flops: float, ms: float, views: int, workload: s
             "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s", "frac": achieved / PEAK_FP32_TFLOPS,
             "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts and maximum clock)",
             "traffic": None if per_view is None else per_view * views, "flops_per_launch": flops,
-            "kernel_ms": ms}
+            "kernel_ms": ms,
+            "frac_strict": None if flops_strict is None else flops_strict / (ms / 1e3) / 1e12 / PEAK_FP32_TFLOPS}
 
 
 # ------------------------------------------------------------------------------------------
@@ -412,8 +418,10 @@ def run_ours(args):
     img_buf = frame.image_buffer()
     ms_render_kernel = tile_kernel_ms(B, torch, lambda: frame.render(img_buf), K)
     flops_render = render_flops(pc)
-    rl_removal = roofline_entry("removal_kernel", flops, ms_removal_kernel, n_views, "scene")
-    rl_render = roofline_entry("render_kernel", flops_render, ms_render_kernel, n_views, "scene")
+    rl_removal = roofline_entry("removal_kernel", flops, ms_removal_kernel, n_views, "scene",
+                                removal_flops(pc, strict=True))
+    rl_render = roofline_entry("render_kernel", flops_render, ms_render_kernel, n_views, "scene",
+                               render_flops(pc, strict=True))
     del img_buf
 
     # ---- end to end through host buffers (pinned): parameters + targets in, dMSE + I out
@@ -563,7 +571,7 @@ def fwd_bwd_step_ms(args, dev, D) -> dict:
     pc = fr.pair_stats()
     flops = bwd_flops(pc)
     out["pairs"] = pc
-    out["roofline"] = roofline_entry("render_bwd_kernel", flops, ms_k, len(w.cameras), "grad")
+    out["roofline"] = roofline_entry("render_bwd_kernel", flops, ms_k, len(w.cameras), "grad", bwd_flops(pc, strict=True))
     del fr
     out["finetune"] = finetune_run(args, dev, D, w, scene_d, cams_rec, img, targets)
     return out
@@ -918,7 +926,8 @@ def multiview_config(args, dev, D, name: str, views_per_chunk, fwd_bwd: bool = F
                 "graph_views_per_s": world * be.n_views / (graph_ms / 1e3) if isinstance(graph_ms, float) else None,
                 "gblend_per_s_pass": world * (pc["examined"] + pc["back_positions"]) / (eager_ms / 1e3) / 1e9,
                 "pairs": pc, "pool_gb": be.pool.nbytes() / 1e9,
-                "roofline_first_chunk": roofline_entry("removal_kernel", flops0, ms_k, f0.n_views, name)})
+                "roofline_first_chunk": roofline_entry("removal_kernel", flops0, ms_k, f0.n_views, name,
+                                                       removal_flops(pc0, strict=True))})
     del be, f0
     torch.cuda.empty_cache()
     if fwd_bwd:
