@@ -270,7 +270,9 @@ POTR_API potr_status potr_render(const potr_views* views, const potr_frame* fram
  * weights of the SH energy compaction).  d_images (nullable) receives the
  * render.  d_targets: planar [3][H][W] per view at offset 3 * pixel_base.  d_tile_order as in
  * potr_render.  d_ws: potr_removal_workspace_size(instance_capacity, total_tiles, d_inst_imp !=
- * NULL) bytes of device scratch (the per-block sums before they are added per tile).
+ * NULL) bytes of device scratch (the per-block sums before they are added per tile: 16 bytes per
+ * instance, 32 with importance, and 20 bytes per tile, each part aligned to 256 bytes; 0 for a
+ * non-positive size).
  */
 POTR_API size_t potr_removal_workspace_size(int64_t instance_capacity, int64_t total_tiles, int32_t with_importance);
 POTR_API potr_status potr_removal_effect(const potr_views* views, const potr_frame* frame, const potr_raster_config* cfg,

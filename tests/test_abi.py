@@ -120,3 +120,23 @@ def test_static_sort_limits_fit_its_scratch(libpotr):
     for views in (1, 2, 4, 16, 64):
         need = B.potr_bin_sort_workspace_size(vs // views, views, 1 << 20, cap)
         assert 0 < need <= 56 << 20, (views, need)
+
+
+def test_workspace_sizes_of_the_removal_and_backward_passes(libpotr):
+    """The documented workspace formulas (host only): the removal pass keeps 16 bytes of block
+    sums per instance (32 with importance) and 20 bytes per tile, the backward pass 36 bytes of
+    partials per instance and 52 bytes per (view, splat); both are 0 for non-positive sizes and
+    grow with every argument."""
+    from paper_2601_14821_gb300 import _binding as B
+
+    cap, tiles, vk = 1_000_000, 3600, 500_000
+    r0 = B.potr_removal_workspace_size(cap, tiles, False)
+    r1 = B.potr_removal_workspace_size(cap, tiles, True)
+    assert 16 * cap + 20 * tiles <= r0 < 16 * cap + 20 * tiles + 4 * 256
+    assert 32 * cap + 20 * tiles <= r1 < 32 * cap + 20 * tiles + 4 * 256
+    assert B.potr_removal_workspace_size(cap + 1000, tiles, True) > r1
+    assert B.potr_removal_workspace_size(cap, tiles + 1000, True) > r1
+    assert B.potr_removal_workspace_size(0, tiles, True) == 0 and B.potr_removal_workspace_size(cap, 0, True) == 0
+    b = B.potr_render_backward_workspace_size(cap, vk)
+    assert b == 36 * cap + 52 * vk
+    assert B.potr_render_backward_workspace_size(0, vk) == 0 and B.potr_render_backward_workspace_size(cap, 0) == 0
