@@ -392,9 +392,9 @@ __global__ void __launch_bounds__(kVkThreads) vk_bwd_kernel(const uint32_t* __re
   for (int64_t wv = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wv * 32 < n_vk; wv += warps_total) {
     const int64_t vk = wv * 32 + lane;
     uint32_t cnt = 0, off = 0;
-    if (ok && vk < n_vk) {
+    if (ok && vk < n_vk) {  // independent loads: the run starts at lane 0's offset whatever its count
       cnt = touched[vk];
-      if (cnt) off = offsets[vk];
+      off = offsets[vk];
     }
     uint32_t incl = cnt;
 #pragma unroll
@@ -404,8 +404,7 @@ __global__ void __launch_bounds__(kVkThreads) vk_bwd_kernel(const uint32_t* __re
     }
     const uint32_t seg0 = incl - cnt, seg1 = incl;  // my segment inside the warp's run
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    const uint32_t first_lane = total ? __ffs(__ballot_sync(0xffffffffu, cnt != 0)) - 1 : 0;
-    const uint32_t run0 = __shfl_sync(0xffffffffu, off, first_lane);
+    const uint32_t run0 = __shfl_sync(0xffffffffu, off, 0);  // offsets are the exclusive prefix in vk order
     float gq[kGradQ];
 #pragma unroll
     for (int q = 0; q < kGradQ; ++q) gq[q] = 0.0f;
