@@ -305,31 +305,46 @@ constexpr size_t removal_smem_bytes() {
 // dmse[k] += dSSE_k(v) * scale_d[v] with scale_d[v] = 1 / (3 P_v N), views in order; the
 // importance likewise with scale_i[v] = 1 / (P_v N).  The per-view scales are computed once
 // per view (binary64), so the loop has no division.
-constexpr int kReduceChunk = 512;  // partials staged per warp and round
+constexpr int kReduceChunk = 256;  // partials staged per warp, view and array
 
-__global__ void __launch_bounds__(256) splat_reduce_kernel(const uint32_t* __restrict__ touched,
-                                                           const uint32_t* __restrict__ offsets,
-                                                           const uint32_t* __restrict__ n_inst, int64_t capacity,
-                                                           const float* __restrict__ inst_dse,
-                                                           const float* __restrict__ inst_imp, int64_t n, int n_views,
-                                                           const potr_view_info* __restrict__ info, double n_total,
-                                                           double* __restrict__ dmse, double* __restrict__ importance,
-                                                           double* __restrict__ dsse_view,
-                                                           double* __restrict__ imp_view) {
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+
+// The warp's slots [c0, c0 + m) of both partial arrays into one staging buffer, as one group.
+__device__ __forceinline__ void stage_partials(float* wd, float* wi, const float* __restrict__ inst_dse,
+                                               const float* __restrict__ inst_imp, uint32_t c0, uint32_t m, int lane) {
+  for (uint32_t i = (uint32_t)lane; i < m; i += 32) {
+    cp_async4(wd + i, inst_dse + c0 + i);
+    if (inst_imp) cp_async4(wi + i, inst_imp + c0 + i);
+  }
+  asm volatile("cp.async.commit_group;\n" ::);
+}
+
+__global__ void __launch_bounds__(256, 5) splat_reduce_kernel(const uint32_t* __restrict__ touched,
+                                                              const uint32_t* __restrict__ offsets,
+                                                              const uint32_t* __restrict__ n_inst, int64_t capacity,
+                                                              const float* __restrict__ inst_dse,
+                                                              const float* __restrict__ inst_imp, int64_t n, int n_views,
+                                                              const potr_view_info* __restrict__ info, double n_total,
+                                                              double* __restrict__ dmse, double* __restrict__ importance,
+                                                              double* __restrict__ dsse_view,
+                                                              double* __restrict__ imp_view) {
   // One warp per 32 consecutive splats.  For one view their emission slots form one contiguous
   // range (offsets are the exclusive prefix in vk order), which the warp stages through its own
-  // shared memory with coalesced loads; each lane then adds its own slots, in slot order, from
-  // there.  Warps synchronise only among their own lanes.
+  // shared memory with coalesced copies; each lane then adds its own slots, in slot order, from
+  // there.  The views are pipelined: while a view is summed, the next view's slots are in
+  // flight to the other buffer and the counts and offsets of the one after are being loaded.
+  // Warps synchronise only among their own lanes.
   __shared__ double scale_d[64], scale_i[64], inv_p[64];
-  __shared__ float s_d[kWarps][kReduceChunk], s_i[kWarps][kReduceChunk];
+  __shared__ float s_d[kWarps][2][kReduceChunk], s_i[kWarps][2][kReduceChunk];
   if ((int64_t)*n_inst > capacity) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t k0 = ((int64_t)blockIdx.x * kWarps + warp) * 32;
   const int64_t k = k0 + lane;
   const bool active = k0 < n;  // warp-uniform
   const int last_lane = active ? (int)(min(k0 + 32, n) - 1 - k0) : 0;
-  float* wd = s_d[warp];
-  float* wi = s_i[warp];
   double acc_d = (dmse && k < n) ? dmse[k] : 0.0;
   double acc_i = (importance && k < n) ? importance[k] : 0.0;
   for (int v0 = 0; v0 < n_views; v0 += 64) {
@@ -343,30 +358,56 @@ __global__ void __launch_bounds__(256) splat_reduce_kernel(const uint32_t* __res
     }
     __syncthreads();
     if (!active) continue;
+    // count and offset of this lane's splat in the next view (a) and the one after (b)
+    uint32_t cnt_a = 0, off_a = 0, cnt_b = 0, off_b = 0;
+    if (k < n) {
+      cnt_a = touched[(int64_t)v0 * n + k];
+      off_a = offsets[(int64_t)v0 * n + k];
+      if (nv > 1) {
+        cnt_b = touched[(int64_t)(v0 + 1) * n + k];
+        off_b = offsets[(int64_t)(v0 + 1) * n + k];
+      }
+    }
+    uint32_t lo = __shfl_sync(0xffffffffu, off_a, 0);
+    uint32_t hi = __shfl_sync(0xffffffffu, off_a + cnt_a, last_lane);
+    stage_partials(s_d[warp][0], s_i[warp][0], inst_dse, inst_imp, lo, min((uint32_t)kReduceChunk, hi - lo), lane);
     for (int vv = 0; vv < nv; ++vv) {
       const int64_t row = (int64_t)(v0 + vv) * n;
-      uint32_t cnt = 0, off = 0;
-      if (k < n) {
-        cnt = touched[row + k];
-        off = offsets[row + k];
+      const uint32_t cnt = cnt_a, off = off_a, vlo = lo, vhi = hi;
+      float* wd = s_d[warp][vv & 1];
+      float* wi = s_i[warp][vv & 1];
+      cnt_a = cnt_b;
+      off_a = off_b;
+      if (k < n && vv + 2 < nv) {
+        cnt_b = touched[row + 2 * n + k];
+        off_b = offsets[row + 2 * n + k];
       }
-      const uint32_t lo = __shfl_sync(0xffffffffu, off, 0);
-      const uint32_t hi = __shfl_sync(0xffffffffu, off + cnt, last_lane);
+      if (vv + 1 < nv) {  // the next view's first chunk, into the other buffer
+        lo = __shfl_sync(0xffffffffu, off_a, 0);
+        hi = __shfl_sync(0xffffffffu, off_a + cnt_a, last_lane);
+        stage_partials(s_d[warp][(vv + 1) & 1], s_i[warp][(vv + 1) & 1], inst_dse, inst_imp, lo,
+                       min((uint32_t)kReduceChunk, hi - lo), lane);
+        asm volatile("cp.async.wait_group 1;\n" ::);
+      } else {
+        asm volatile("cp.async.wait_group 0;\n" ::);
+      }
+      __syncwarp();  // this view's first chunk is visible to every lane
       KahanSum kd, ki;
-      for (uint32_t c0 = lo; c0 < hi; c0 += kReduceChunk) {
-        const uint32_t m = min((uint32_t)kReduceChunk, hi - c0);
-        for (uint32_t i = lane; i < m; i += 32) {
-          wd[i] = inst_dse[c0 + i];
-          if (inst_imp) wi[i] = inst_imp[c0 + i];
+      for (uint32_t c0 = vlo; c0 < vhi; c0 += kReduceChunk) {
+        const uint32_t m = min((uint32_t)kReduceChunk, vhi - c0);
+        if (c0 != vlo) {  // a range longer than one chunk: the rest is staged here and waited for
+          __syncwarp();   // every lane is done with the previous chunk
+          stage_partials(wd, wi, inst_dse, inst_imp, c0, m, lane);
+          asm volatile("cp.async.wait_group 0;\n" ::);
+          __syncwarp();
         }
-        __syncwarp();
         const uint32_t a = max(off, c0), b = min(off + cnt, c0 + m);
         for (uint32_t i = a; i < b; ++i) {
           kd.add(wd[i - c0]);
           if (inst_imp) ki.add(wi[i - c0]);
         }
-        __syncwarp();
       }
+      __syncwarp();  // every lane is done with this buffer, which the next iteration restages
       const double sd = cnt ? (double)kd.value() : 0.0;
       const double si = (cnt && inst_imp) ? (double)ki.value() : 0.0;
       acc_d += sd * scale_d[vv];
