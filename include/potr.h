@@ -259,10 +259,12 @@ POTR_API potr_status potr_render(const potr_views* views, const potr_frame* fram
  * d_inst_dse[emission slot] (float, instance_capacity entries, required; the same capacity
  * as potr_bin_sort -- when the frame's instance count exceeded it, nothing is reduced and
  * d_dmse / d_importance / d_dsse_view are left untouched).  Then, per
- * splat, the tile partials are summed in emission order (a compensated binary32 sum), giving
- * dSSE_k(v) = sum_x dSE, and
+ * splat, the tile partials are summed in emission order (a compensated binary32 sum, rounded
+ * to binary32), giving dSSE_k(v) = sum_x dSE, and
  *   d_dmse[k] += dSSE_k(v) / (3 P_v n_views_total)        (binary64, views added in order)
- * so that calls over consecutive view chunks compose (zero d_dmse before the first call).
+ * where the term is dSSE_k(v) times the binary32 rounding of 1 / (3 P_v n_views_total),
+ * rounded to binary32, so that calls over consecutive view chunks add the same terms in the
+ * same order as one call over all of them (zero d_dmse before the first call).
  * With d_inst_imp / d_importance non-NULL the same is done for T_i alpha_i, giving
  * I_k += (sum_x T alpha) / (P_v n_views_total) (Section IV-A).  d_dsse_view (nullable,
  * [n_views][n] binary64) receives dSSE_k(v) itself, and d_imp_view (nullable, [n_views][n]

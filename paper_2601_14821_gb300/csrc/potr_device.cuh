@@ -56,6 +56,53 @@ __device__ __forceinline__ float exp2r(float y) {
   return __int_as_float(__float_as_int(p) + (__float_as_int(t) << 23));
 }
 
+// ---------------------------------------------------------------------------------------
+// packed binary32 pairs: one f32x2 instruction rounds each half as its scalar form would
+// ---------------------------------------------------------------------------------------
+typedef unsigned long long f2_t;
+
+__device__ __forceinline__ f2_t f2(float lo, float hi) {
+  f2_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ f2_t f2s(float x) { return f2(x, x); }
+__device__ __forceinline__ void f2split(f2_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ float f2lo(f2_t v) {
+  float lo, hi;
+  f2split(v, lo, hi);
+  (void)hi;
+  return lo;
+}
+__device__ __forceinline__ float f2hi(f2_t v) {
+  float lo, hi;
+  f2split(v, lo, hi);
+  (void)lo;
+  return hi;
+}
+__device__ __forceinline__ f2_t add2(f2_t a, f2_t b) {
+  f2_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t sub2(f2_t a, f2_t b) {
+  f2_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t mul2(f2_t a, f2_t b) {
+  f2_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) {
+  f2_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 // Per-pair opacity exponent: log2 G = A dx^2 + B dx dy + C dy^2, evaluated as
 // fma(fma(A, dx, B dy), dx, (C dy) dy).
 __device__ __forceinline__ float pair_exponent(float A, float B, float C, float dx, float dy) {
@@ -78,10 +125,9 @@ __device__ __forceinline__ float trans_next(float a, float T) { return __fmaf_rn
 // its vertex clamped to the edge, and the splat centre counts when it lies inside.  The tile
 // is kept when o * exp2r(max + margin) >= alpha_min, the margin 1e-5 |terms| + 1e-4 covering
 // the binary32 rounding of this maximum and of any pixel's own exponent and the error of
-// exp2r, so every pixel that takes the splat lies in a kept tile.  Fixed operation order.
-__device__ __forceinline__ float tile_edge_exponent(float A, float B, float C, float u, float v) {
-  return __fadd_rn(__fmul_rn(__fadd_rn(__fmul_rn(A, u), __fmul_rn(B, v)), u), __fmul_rn(__fmul_rn(C, v), v));
-}
+// exp2r, so every pixel that takes the splat lies in a kept tile.  Fixed operation order: the
+// exponent at an edge point (u, v) is ((A u + B v) u) + (C v) v, every product and sum rounded
+// on its own.
 
 // The per-splat part: the parabola vertices along the two edge directions, u = ku v and
 // v = kv u (only meaningful when A < 0 and C < 0; otherwise every tile is kept).
@@ -98,14 +144,24 @@ __device__ __forceinline__ bool tile_hit_concave(float mx, float my, float A, fl
                                                  float alpha_min) {
   const float X0 = __fadd_rn((float)(tx * tile_w), 0.5f), X1 = __fadd_rn(X0, (float)(tile_w - 1));
   const float Y0 = __fadd_rn((float)(ty * tile_h), 0.5f), Y1 = __fadd_rn(Y0, (float)(tile_h - 1));
-  const float ux0 = __fsub_rn(X0, mx), ux1 = __fsub_rn(X1, mx);
-  const float vy0 = __fsub_rn(Y0, my), vy1 = __fsub_rn(Y1, my);
-  const float u0 = fminf(fmaxf(__fmul_rn(ku, vy0), ux0), ux1);
-  const float u1 = fminf(fmaxf(__fmul_rn(ku, vy1), ux0), ux1);
-  const float v0 = fminf(fmaxf(__fmul_rn(kv, ux0), vy0), vy1);
-  const float v1 = fminf(fmaxf(__fmul_rn(kv, ux1), vy0), vy1);
-  float pmax = fmaxf(fmaxf(tile_edge_exponent(A, B, C, u0, vy0), tile_edge_exponent(A, B, C, u1, vy1)),
-                     fmaxf(tile_edge_exponent(A, B, C, ux0, v0), tile_edge_exponent(A, B, C, ux1, v1)));
+  // the two edges of each direction as one pair: (ux0, ux1) and (vy0, vy1)
+  const f2_t ux = sub2(f2(X0, X1), f2s(mx)), vy = sub2(f2(Y0, Y1), f2s(my));
+  float ux0, ux1, vy0, vy1, kuv0, kuv1, kvu0, kvu1;
+  f2split(ux, ux0, ux1);
+  f2split(vy, vy0, vy1);
+  f2split(mul2(f2s(ku), vy), kuv0, kuv1);
+  f2split(mul2(f2s(kv), ux), kvu0, kvu1);
+  // vertices on the edges v = vy0, vy1 (u clamped to [ux0, ux1]) and on u = ux0, ux1
+  const f2_t uh = f2(fminf(fmaxf(kuv0, ux0), ux1), fminf(fmaxf(kuv1, ux0), ux1));
+  const f2_t vv = f2(fminf(fmaxf(kvu0, vy0), vy1), fminf(fmaxf(kvu1, vy0), vy1));
+  // the edge exponents ((A u + B v) u) + (C v) v, two edges per instruction
+  const f2_t A2 = f2s(A), B2 = f2s(B), C2 = f2s(C);
+  const f2_t eh = add2(mul2(add2(mul2(A2, uh), mul2(B2, vy)), uh), mul2(mul2(C2, vy), vy));
+  const f2_t ev = add2(mul2(add2(mul2(A2, ux), mul2(B2, vv)), ux), mul2(mul2(C2, vv), vv));
+  float p0, p1, p2, p3;
+  f2split(eh, p0, p1);
+  f2split(ev, p2, p3);
+  float pmax = fmaxf(fmaxf(p0, p1), fmaxf(p2, p3));
   if (ux0 <= 0.0f && ux1 >= 0.0f && vy0 <= 0.0f && vy1 >= 0.0f) pmax = fmaxf(pmax, 0.0f);
   const float um = fmaxf(fabsf(ux0), fabsf(ux1)), vm = fmaxf(fabsf(vy0), fabsf(vy1));
   const float mag = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(fabsf(A), um), um), __fmul_rn(__fmul_rn(fabsf(B), um), vm)),

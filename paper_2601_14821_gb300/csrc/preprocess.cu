@@ -242,16 +242,23 @@ __global__ void __launch_bounds__(kProjectThreads, 8) project_kernel(const float
 
 // Kept tiles of every (view, splat) rectangle of at most kCullMaxTiles tiles.  One warp per 32
 // consecutive vk: their candidate tiles (rectangle cells, row-major) are dealt to the lanes 32
-// at a time, each lane runs the tile test for one candidate (owner found by a shuffle search over
-// the warp's exclusive candidate counts), and every owner collects its bits from the ballot.
-// Writes the culling word of every vk -- mask low, mask high, the rectangle word (as record
-// word 11) and the kept count | all-kept flag << 31 (0 for a culled vk) -- to its own 16-byte
-// array (coalesced whole-sector stores, not a partial rewrite of the record), and touched = the
-// kept count, so that the emission reads one 16-byte word per vk.
+// at a time, each lane runs the tile test for one candidate, and every owner collects its bits
+// from the ballot.  Each lane's splat parameters sit in its row of the warp's shared memory; a
+// candidate's owner is the lane whose candidates start at the last start position at or before
+// it (a bitmap of the round's start positions, and the lane starting at each), or the owner of
+// the previous round's last candidate.  Writes the culling word of every vk -- mask low, mask
+// high, the rectangle word (as record word 11) and the kept count | all-kept flag << 31 (0 for
+// a culled vk) -- to its own 16-byte array (coalesced whole-sector stores, not a partial
+// rewrite of the record), and touched = the kept count, so that the emission reads one 16-byte
+// word per vk.
 __global__ void __launch_bounds__(256) tile_mask_kernel(const uint2* __restrict__ rect, int64_t n_vk,
                                                         potr_raster_config cfg, const float4* __restrict__ raster,
                                                         uint4* __restrict__ cull, uint32_t* __restrict__ touched) {
-  const int lane = threadIdx.x & 31;
+  // per warp and lane: {mx, my, A, B}, {C, o, ku, kv}, {pthr, x0 | y0 << 16, w | concave << 31,
+  // first candidate}; 48-byte rows, so 16-byte reads of 8 consecutive rows hit distinct banks
+  __shared__ float4 s_par[8][32][3];
+  __shared__ uint8_t s_start[8][32];  // lane whose candidates start at each position of the round
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t warps_total = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t wv = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wv * 32 < n_vk; wv += warps_total) {
     const int64_t vk = wv * 32 + lane;
@@ -285,29 +292,38 @@ __global__ void __launch_bounds__(256) tile_mask_kernel(const uint2* __restrict_
     }
     const uint32_t excl = incl - cand;
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    __syncwarp();  // the previous item's rows are no longer read
+    s_par[warp][lane][0] = make_float4(mx, my, qa, qb);
+    s_par[warp][lane][1] = make_float4(qc, o, ku, kv);
+    s_par[warp][lane][2] = make_float4(pthr, __uint_as_float(x0 | (y0 << 16)),
+                                       __uint_as_float(w | (concave ? 0x80000000u : 0u)), __uint_as_float(excl));
     uint64_t mask = 0;
+    uint32_t carry = 0;  // owner of the previous round's last position
     for (uint32_t e0 = 0; e0 < total; e0 += 32) {
       const uint32_t e = e0 + lane;
-      uint32_t owner = 0;
-#pragma unroll
-      for (int b = 16; b >= 1; b >>= 1) {
-        const uint32_t c = owner + b;
-        const uint32_t ce = __shfl_sync(0xffffffffu, excl, c & 31);
-        if (c < 32 && ce <= e) owner = c;
+      const bool starts = cand > 0 && excl >= e0 && excl < e0 + 32u;
+      if (starts) s_start[warp][excl - e0] = (uint8_t)lane;
+      const uint32_t S = __reduce_or_sync(0xffffffffu, starts ? 1u << (excl - e0) : 0u);
+      __syncwarp();  // the rows and the round's starts are visible
+      const uint32_t below = S & (0xffffffffu >> (31 - lane));  // starts at positions e0 .. e
+      const uint32_t owner = below ? (uint32_t)s_start[warp][31 - __clz(below)] : carry;
+      carry = __shfl_sync(0xffffffffu, owner, 31);
+      const float4 p2 = s_par[warp][owner][2];
+      const uint32_t li = e - __float_as_uint(p2.w);
+      const uint32_t wb = __float_as_uint(p2.z), xy = __float_as_uint(p2.y);
+      const uint32_t ow = wb & 0xffffu;
+      const uint32_t dy = small_div(li, ow);  // li < 96
+      const int tx = (int)((xy & 0xffffu) + (li - dy * ow));
+      const int ty = (int)((xy >> 16) + dy);
+      bool hit = false;
+      if (e < total) {
+        hit = true;
+        if (wb >> 31) {
+          const float4 p0 = s_par[warp][owner][0], p1 = s_par[warp][owner][1];
+          hit = tile_hit_concave(p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w, p2.x, tx, ty, cfg.tile_w,
+                                 cfg.tile_h, cfg.alpha_min);
+        }
       }
-      const uint32_t li = e - __shfl_sync(0xffffffffu, excl, owner);
-      const uint32_t ow = __shfl_sync(0xffffffffu, w, owner);
-      const uint32_t dy = small_div(li, ow);  // li < 64
-      const int tx = (int)(__shfl_sync(0xffffffffu, x0, owner) + (li - dy * ow));
-      const int ty = (int)(__shfl_sync(0xffffffffu, y0, owner) + dy);
-      const float omx = __shfl_sync(0xffffffffu, mx, owner), omy = __shfl_sync(0xffffffffu, my, owner);
-      const float oa = __shfl_sync(0xffffffffu, qa, owner), ob = __shfl_sync(0xffffffffu, qb, owner);
-      const float oc = __shfl_sync(0xffffffffu, qc, owner), oo = __shfl_sync(0xffffffffu, o, owner);
-      const float oku = __shfl_sync(0xffffffffu, ku, owner), okv = __shfl_sync(0xffffffffu, kv, owner);
-      const float opt = __shfl_sync(0xffffffffu, pthr, owner);
-      const bool oconc = __shfl_sync(0xffffffffu, concave ? 1u : 0u, owner) != 0u;
-      const bool hit = e < total && (!oconc || tile_hit_concave(omx, omy, oa, ob, oc, oo, oku, okv, opt, tx, ty,
-                                                                cfg.tile_w, cfg.tile_h, cfg.alpha_min));
       const uint32_t bal = __ballot_sync(0xffffffffu, hit);
       // this lane's candidates [excl, excl + cand) overlapping [e0, e0 + 32)
       const uint32_t lo = max(excl, e0), hi = min(excl + cand, e0 + 32u);
@@ -316,6 +332,7 @@ __global__ void __launch_bounds__(256) tile_mask_kernel(const uint2* __restrict_
         const uint32_t bits = (bal >> (lo - e0)) & (len == 32u ? 0xffffffffu : ((1u << len) - 1u));
         mask |= (uint64_t)bits << (lo - excl);
       }
+      __syncwarp();  // the starts are rewritten next round
     }
     if (vk < n_vk) {
       const bool all = area > (uint32_t)kCullMaxTiles;

@@ -301,11 +301,26 @@ constexpr size_t removal_smem_bytes() {
   return sizeof(float4) * kW2 * kRemovalWarpF4;
 }
 
-// Per splat k: dSSE_k(v) = sum over its emission slots (emission order), then
-// dmse[k] += dSSE_k(v) * scale_d[v] with scale_d[v] = 1 / (3 P_v N), views in order; the
-// importance likewise with scale_i[v] = 1 / (P_v N).  The per-view scales are computed once
-// per view (binary64), so the loop has no division.
+// Per splat k: dSSE_k(v) = sum over its emission slots (emission order, compensated binary32),
+// then dmse[k] += dSSE_k(v) * scale_d[v] in binary64, views in order, with the term
+// dSSE_k(v) * scale_d[v] rounded to binary32 and scale_d[v] the binary32 rounding of
+// 1 / (3 P_v N); the importance likewise with scale_i[v] = 1 / (P_v N).  The scales are
+// computed once per view, so the loop has no division; a call over one view chunk adds the
+// same binary64 terms in the same order as a call over the whole frame.  The binary64 pipe
+// runs 2 lane operations per SM and cycle, so a view costs it one addition per output: the
+// terms are widened to binary64 by moving their bits (widen_f32).
 constexpr int kReduceChunk = 256;  // partials staged per warp, view and array
+
+// The binary64 value of a binary32 x, by moving its bits: the exponent rebiased by 1023 - 127
+// and the 23 mantissa bits placed at the top of the 52 (exact for zeros and normal numbers,
+// IEEE 754 formats); subnormals, infinities and NaN take the conversion instruction.
+__device__ __forceinline__ double widen_f32(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const uint32_t e = (b >> 23) & 0xffu;
+  if (e == 0xffu || (e == 0u && (b << 1) != 0u)) return (double)x;
+  const uint32_t hi = (b & 0x80000000u) | (e ? (e + 896u) << 20 : 0u) | ((b >> 3) & 0xfffffu);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
 
 __device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
   const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
@@ -322,12 +337,25 @@ __device__ __forceinline__ void stage_partials(float* wd, float* wi, const float
   asm volatile("cp.async.commit_group;\n" ::);
 }
 
+// Per-view scales of the reduce, one 16-byte word per view: the binary32 roundings of
+// 1 / (3 P_v N) and 1 / (P_v N), and 1 / P_v in binary64 (computed once here, so the reduce
+// has no division).
+__global__ void view_scale_kernel(const potr_view_info* __restrict__ info, int n_views, double n_total,
+                                  uint4* __restrict__ scales) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n_views) return;
+  const double P = (double)info[v].width * (double)info[v].height;
+  const double ip = 1.0 / P;
+  scales[v] = make_uint4(__float_as_uint((float)(1.0 / (3.0 * P * n_total))), __float_as_uint((float)(1.0 / (P * n_total))),
+                         (uint32_t)__double2loint(ip), (uint32_t)__double2hiint(ip));
+}
+
 __global__ void __launch_bounds__(256, 5) splat_reduce_kernel(const uint32_t* __restrict__ touched,
                                                               const uint32_t* __restrict__ offsets,
                                                               const uint32_t* __restrict__ n_inst, int64_t capacity,
                                                               const float* __restrict__ inst_dse,
                                                               const float* __restrict__ inst_imp, int64_t n, int n_views,
-                                                              const potr_view_info* __restrict__ info, double n_total,
+                                                              const uint4* __restrict__ scales,
                                                               double* __restrict__ dmse, double* __restrict__ importance,
                                                               double* __restrict__ dsse_view,
                                                               double* __restrict__ imp_view) {
@@ -337,84 +365,71 @@ __global__ void __launch_bounds__(256, 5) splat_reduce_kernel(const uint32_t* __
   // there.  The views are pipelined: while a view is summed, the next view's slots are in
   // flight to the other buffer and the counts and offsets of the one after are being loaded.
   // Warps synchronise only among their own lanes.
-  __shared__ double scale_d[64], scale_i[64], inv_p[64];
   __shared__ float s_d[kWarps][2][kReduceChunk], s_i[kWarps][2][kReduceChunk];
   if ((int64_t)*n_inst > capacity) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t k0 = ((int64_t)blockIdx.x * kWarps + warp) * 32;
   const int64_t k = k0 + lane;
-  const bool active = k0 < n;  // warp-uniform
-  const int last_lane = active ? (int)(min(k0 + 32, n) - 1 - k0) : 0;
+  if (k0 >= n) return;  // warp-uniform
+  const int last_lane = (int)(min(k0 + 32, n) - 1 - k0);
   double acc_d = (dmse && k < n) ? dmse[k] : 0.0;
   double acc_i = (importance && k < n) ? importance[k] : 0.0;
-  for (int v0 = 0; v0 < n_views; v0 += 64) {
-    const int nv = min(64, n_views - v0);
-    __syncthreads();
-    if (threadIdx.x < nv) {
-      const double P = (double)info[v0 + threadIdx.x].width * (double)info[v0 + threadIdx.x].height;
-      scale_d[threadIdx.x] = 1.0 / (3.0 * P * n_total);
-      scale_i[threadIdx.x] = 1.0 / (P * n_total);
-      inv_p[threadIdx.x] = 1.0 / P;
+  // count and offset of this lane's splat in the next view (a) and the one after (b)
+  uint32_t cnt_a = 0, off_a = 0, cnt_b = 0, off_b = 0;
+  if (k < n) {
+    cnt_a = touched[k];
+    off_a = offsets[k];
+    if (n_views > 1) {
+      cnt_b = touched[n + k];
+      off_b = offsets[n + k];
     }
-    __syncthreads();
-    if (!active) continue;
-    // count and offset of this lane's splat in the next view (a) and the one after (b)
-    uint32_t cnt_a = 0, off_a = 0, cnt_b = 0, off_b = 0;
-    if (k < n) {
-      cnt_a = touched[(int64_t)v0 * n + k];
-      off_a = offsets[(int64_t)v0 * n + k];
-      if (nv > 1) {
-        cnt_b = touched[(int64_t)(v0 + 1) * n + k];
-        off_b = offsets[(int64_t)(v0 + 1) * n + k];
-      }
+  }
+  uint32_t lo = __shfl_sync(0xffffffffu, off_a, 0);
+  uint32_t hi = __shfl_sync(0xffffffffu, off_a + cnt_a, last_lane);
+  stage_partials(s_d[warp][0], s_i[warp][0], inst_dse, inst_imp, lo, min((uint32_t)kReduceChunk, hi - lo), lane);
+  for (int v = 0; v < n_views; ++v) {
+    const int64_t row = (int64_t)v * n;
+    const uint32_t cnt = cnt_a, off = off_a, vlo = lo, vhi = hi;
+    float* wd = s_d[warp][v & 1];
+    float* wi = s_i[warp][v & 1];
+    const uint4 sc = scales[v];  // the same word for every lane
+    cnt_a = cnt_b;
+    off_a = off_b;
+    if (k < n && v + 2 < n_views) {
+      cnt_b = touched[row + 2 * n + k];
+      off_b = offsets[row + 2 * n + k];
     }
-    uint32_t lo = __shfl_sync(0xffffffffu, off_a, 0);
-    uint32_t hi = __shfl_sync(0xffffffffu, off_a + cnt_a, last_lane);
-    stage_partials(s_d[warp][0], s_i[warp][0], inst_dse, inst_imp, lo, min((uint32_t)kReduceChunk, hi - lo), lane);
-    for (int vv = 0; vv < nv; ++vv) {
-      const int64_t row = (int64_t)(v0 + vv) * n;
-      const uint32_t cnt = cnt_a, off = off_a, vlo = lo, vhi = hi;
-      float* wd = s_d[warp][vv & 1];
-      float* wi = s_i[warp][vv & 1];
-      cnt_a = cnt_b;
-      off_a = off_b;
-      if (k < n && vv + 2 < nv) {
-        cnt_b = touched[row + 2 * n + k];
-        off_b = offsets[row + 2 * n + k];
-      }
-      if (vv + 1 < nv) {  // the next view's first chunk, into the other buffer
-        lo = __shfl_sync(0xffffffffu, off_a, 0);
-        hi = __shfl_sync(0xffffffffu, off_a + cnt_a, last_lane);
-        stage_partials(s_d[warp][(vv + 1) & 1], s_i[warp][(vv + 1) & 1], inst_dse, inst_imp, lo,
-                       min((uint32_t)kReduceChunk, hi - lo), lane);
-        asm volatile("cp.async.wait_group 1;\n" ::);
-      } else {
+    if (v + 1 < n_views) {  // the next view's first chunk, into the other buffer
+      lo = __shfl_sync(0xffffffffu, off_a, 0);
+      hi = __shfl_sync(0xffffffffu, off_a + cnt_a, last_lane);
+      stage_partials(s_d[warp][(v + 1) & 1], s_i[warp][(v + 1) & 1], inst_dse, inst_imp, lo,
+                     min((uint32_t)kReduceChunk, hi - lo), lane);
+      asm volatile("cp.async.wait_group 1;\n" ::);
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::);
+    }
+    __syncwarp();  // this view's first chunk is visible to every lane
+    KahanSum kd, ki;
+    for (uint32_t c0 = vlo; c0 < vhi; c0 += kReduceChunk) {
+      const uint32_t m = min((uint32_t)kReduceChunk, vhi - c0);
+      if (c0 != vlo) {  // a range longer than one chunk: the rest is staged here and waited for
+        __syncwarp();   // every lane is done with the previous chunk
+        stage_partials(wd, wi, inst_dse, inst_imp, c0, m, lane);
         asm volatile("cp.async.wait_group 0;\n" ::);
+        __syncwarp();
       }
-      __syncwarp();  // this view's first chunk is visible to every lane
-      KahanSum kd, ki;
-      for (uint32_t c0 = vlo; c0 < vhi; c0 += kReduceChunk) {
-        const uint32_t m = min((uint32_t)kReduceChunk, vhi - c0);
-        if (c0 != vlo) {  // a range longer than one chunk: the rest is staged here and waited for
-          __syncwarp();   // every lane is done with the previous chunk
-          stage_partials(wd, wi, inst_dse, inst_imp, c0, m, lane);
-          asm volatile("cp.async.wait_group 0;\n" ::);
-          __syncwarp();
-        }
-        const uint32_t a = max(off, c0), b = min(off + cnt, c0 + m);
-        for (uint32_t i = a; i < b; ++i) {
-          kd.add(wd[i - c0]);
-          if (inst_imp) ki.add(wi[i - c0]);
-        }
+      const uint32_t a = max(off, c0), b = min(off + cnt, c0 + m);
+      for (uint32_t i = a; i < b; ++i) {
+        kd.add(wd[i - c0]);
+        if (inst_imp) ki.add(wi[i - c0]);
       }
-      __syncwarp();  // every lane is done with this buffer, which the next iteration restages
-      const double sd = cnt ? (double)kd.value() : 0.0;
-      const double si = (cnt && inst_imp) ? (double)ki.value() : 0.0;
-      acc_d += sd * scale_d[vv];
-      acc_i += si * scale_i[vv];
-      if (dsse_view && k < n) dsse_view[row + k] = sd;
-      if (imp_view && k < n) imp_view[row + k] = si * inv_p[vv];
     }
+    __syncwarp();  // every lane is done with this buffer, which the next iteration restages
+    const float sd = kd.sum(), si = ki.sum();  // 0 for a splat without slots in the view
+    acc_d = __dadd_rn(acc_d, widen_f32(__fmul_rn(sd, __uint_as_float(sc.x))));
+    if (importance) acc_i = __dadd_rn(acc_i, widen_f32(__fmul_rn(si, __uint_as_float(sc.y))));
+    if (dsse_view && k < n) dsse_view[row + k] = (double)sd;
+    if (imp_view && k < n) imp_view[row + k] = (double)si * __hiloint2double((int)sc.w, (int)sc.z);
   }
   if (k < n) {
     if (dmse) dmse[k] = acc_d;
@@ -572,12 +587,15 @@ extern "C" potr_status potr_removal_effect(const potr_views* views, const potr_f
                                                     d_inst_dse, d_inst_imp, q, scr, s);
   if (e != cudaSuccess) return POTR_ERR_CUDA;
   if (d_dmse || d_importance || d_dsse_view || d_imp_view) {
+    // the per-view scales in the tile tops' words, free once the removal kernel has finished
+    // (a frame has at least one tile per view)
+    view_scale_kernel<<<(unsigned)((frame->n_views + 127) / 128), 128, 0, s>>>(frame->info, frame->n_views,
+                                                                             (double)n_views_total, scr.tile_top);
     const int64_t g = (n + 255) / 256;  // one block per 256 splats (a warp per 32)
     splat_reduce_kernel<<<(unsigned)g, 256, 0, s>>>(views->touched, views->offsets, views->n_instances,
                                                      instance_capacity, d_inst_dse, d_inst_imp, n, frame->n_views,
-                                                     frame->info, (double)n_views_total, d_dmse, d_importance,
-                                                     d_dsse_view, d_imp_view);
-    note_launches(1);
+                                                     scr.tile_top, d_dmse, d_importance, d_dsse_view, d_imp_view);
+    note_launches(2);
     if (cudaGetLastError() != cudaSuccess) return POTR_ERR_CUDA;
   }
   return POTR_OK;

@@ -97,6 +97,7 @@ struct KahanSum {
     s = t;
   }
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+  __device__ __forceinline__ float sum() const { return __fsub_rn(s, c); }  // rounded to binary32
 };
 
 // Tile scheduling.  Without an order every CTA renders the tile of its block index.  With an

@@ -24,53 +24,6 @@ constexpr int kT2 = 128;           // threads per CTA: four warps, two pixels pe
 constexpr int kW2 = kT2 / 32;      // warps per CTA
 constexpr int kSRec2 = 3;          // float4 per staged record
 
-// ---------------------------------------------------------------------------------------
-// packed binary32 pairs
-// ---------------------------------------------------------------------------------------
-typedef unsigned long long f2_t;
-
-__device__ __forceinline__ f2_t f2(float lo, float hi) {
-  f2_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ f2_t f2s(float x) { return f2(x, x); }
-__device__ __forceinline__ void f2split(f2_t v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ float f2lo(f2_t v) {
-  float lo, hi;
-  f2split(v, lo, hi);
-  (void)hi;
-  return lo;
-}
-__device__ __forceinline__ float f2hi(f2_t v) {
-  float lo, hi;
-  f2split(v, lo, hi);
-  (void)lo;
-  return hi;
-}
-__device__ __forceinline__ f2_t add2(f2_t a, f2_t b) {
-  f2_t d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2_t sub2(f2_t a, f2_t b) {
-  f2_t d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2_t mul2(f2_t a, f2_t b) {
-  f2_t d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) {
-  f2_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-
 // exp2r (potr_device.cuh) on a pair: the same clamps, operations and order, so the same bits.
 __device__ __forceinline__ f2_t exp2r2(f2_t yy) {
   constexpr float c0 = exp2_coef(0), c1 = exp2_coef(1), c2 = exp2_coef(2), c3 = exp2_coef(3);
