@@ -193,6 +193,8 @@ POTR_API potr_status potr_view_layout(const potr_camera* h_cams, int32_t n_views
  * list, image, removal effect or gradient; its opacity is stored as NaN).  Each such splat adds
  * 1 to d_status->n_nonfinite and the first one writes POTR_ERR_NUMERIC to d_status->code
  * (d_status: device, caller-zeroed, nullable -- then the splats are still culled, silently).
+ * cfg->tile_w * cfg->tile_h must be 256 (as for potr_view_layout), else
+ * POTR_ERR_INVALID_ARGUMENT.
  */
 POTR_API potr_status potr_preprocess(const potr_scene* scene, const potr_frame* frame, const potr_raster_config* cfg,
                             const potr_views* views, potr_device_status* d_status, potr_stream_t stream);

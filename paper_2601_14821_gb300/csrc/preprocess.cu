@@ -174,11 +174,13 @@ __global__ void __launch_bounds__(kProjectThreads, 8) project_kernel(const float
       const float mx = __fadd_rn(__fmul_rn(cam.fx, txz), cam.cx);
       const float my = __fadd_rn(__fmul_rn(cam.fy, tyz), cam.cy);
       const potr_view_info vi = info[v];
-      const float tw = (float)cfg.tile_w, th = (float)cfg.tile_h;
-      const float fx0 = floorf(__fdiv_rn(__fsub_rn(mx, r), tw));
-      const float fx1 = __fadd_rn(floorf(__fdiv_rn(__fadd_rn(mx, r), tw)), 1.0f);
-      const float fy0 = floorf(__fdiv_rn(__fsub_rn(my, r), th));
-      const float fy1 = __fadd_rn(floorf(__fdiv_rn(__fadd_rn(my, r), th)), 1.0f);
+      // x / tile_w as x * (1 / tile_w): tile_w tile_h = 256 makes both powers of two, so the
+      // reciprocal is exact and the product is the correctly rounded quotient
+      const float itw = 1.0f / (float)cfg.tile_w, ith = 1.0f / (float)cfg.tile_h;
+      const float fx0 = floorf(__fmul_rn(__fsub_rn(mx, r), itw));
+      const float fx1 = __fadd_rn(floorf(__fmul_rn(__fadd_rn(mx, r), itw)), 1.0f);
+      const float fy0 = floorf(__fmul_rn(__fsub_rn(my, r), ith));
+      const float fy1 = __fadd_rn(floorf(__fmul_rn(__fadd_rn(my, r), ith)), 1.0f);
       const int x0 = (int)fminf(fmaxf(fx0, 0.0f), (float)vi.tiles_x);
       const int x1 = (int)fminf(fmaxf(fx1, 0.0f), (float)vi.tiles_x);
       const int y0 = (int)fminf(fmaxf(fy0, 0.0f), (float)vi.tiles_y);
@@ -382,6 +384,8 @@ extern "C" potr_status potr_view_layout(const potr_camera* h_cams, int32_t n_vie
 extern "C" potr_status potr_preprocess(const potr_scene* scene, const potr_frame* frame, const potr_raster_config* cfg,
                                        const potr_views* views, potr_device_status* d_status, potr_stream_t stream) {
   if (!scene || !frame || !cfg || !views) return POTR_ERR_INVALID_ARGUMENT;
+  if (cfg->tile_w <= 0 || cfg->tile_h <= 0 || cfg->tile_w * cfg->tile_h != potr::kTilePixels)
+    return POTR_ERR_INVALID_ARGUMENT;
   if (scene->n <= 0 || frame->n_views < 1 || !frame->cams || !frame->info) return POTR_ERR_INVALID_ARGUMENT;
   if (!scene->means || !scene->log_scales || !scene->quats || !scene->opacity_logits || !scene->sh)
     return POTR_ERR_INVALID_ARGUMENT;

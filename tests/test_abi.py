@@ -140,3 +140,26 @@ def test_workspace_sizes_of_the_removal_and_backward_passes(libpotr):
     b = B.potr_render_backward_workspace_size(cap, vk)
     assert b == 36 * cap + 52 * vk
     assert B.potr_render_backward_workspace_size(0, vk) == 0 and B.potr_render_backward_workspace_size(cap, 0) == 0
+
+
+def test_preprocess_rejects_tile_shapes_other_than_256_pixels(libpotr):
+    """The projection divides by the tile size as a product with its reciprocal, exact only for
+    the power-of-two sizes that tile_w tile_h = 256 allows: any other shape is refused on the
+    host.  The structs hold host addresses, so this runs only where no GPU is visible."""
+    import ctypes as C
+
+    import torch
+
+    from paper_2601_14821_gb300 import _binding as B
+
+    if torch.cuda.is_available():
+        pytest.skip("host-only check")
+    buf = (C.c_float * 64)()
+    addr = C.cast(buf, C.c_void_p).value
+    scene = B.Scene(addr, addr, addr, addr, addr, 1)
+    frame = B.Frame(addr, addr, 1, 1, 1)
+    views = B.Views(*([addr] * len(B.Views._fields_)))
+    for tw, th in ((12, 12), (16, 8), (0, 256), (-16, -16)):
+        cfg = B.make_config(tile_w=tw, tile_h=th)
+        st = B.lib().potr_preprocess(C.byref(scene), C.byref(frame), C.byref(cfg), C.byref(views), None, None)
+        assert st == B.POTR_ERR_INVALID_ARGUMENT, (tw, th)
