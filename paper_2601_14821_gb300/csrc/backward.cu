@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(256) loss_finish_kernel(const double* __restri
 // K9: back-to-front adjoint of the compositing
 // ---------------------------------------------------------------------------------------
 template <bool RECOMPUTE>
-__global__ void __launch_bounds__(kT2, 5) render_bwd_kernel(const float4* __restrict__ raster,
+__global__ void __launch_bounds__(kT2, 6) render_bwd_kernel(const float4* __restrict__ raster,
                                                          const uint32_t* __restrict__ vals,
                                                          const uint32_t* __restrict__ ranges,
                                                          const potr_view_info* __restrict__ info, int n_views,
