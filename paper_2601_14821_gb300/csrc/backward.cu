@@ -408,16 +408,19 @@ __global__ void __launch_bounds__(kVkThreads) vk_bwd_kernel(const uint32_t* __re
     float gq[kGradQ];
 #pragma unroll
     for (int q = 0; q < kGradQ; ++q) gq[q] = 0.0f;
+    // the chunk's partials, loaded one chunk ahead of its scan
+    float nx[kGradQ];
+#pragma unroll
+    for (int q = 0; q < kGradQ; ++q) nx[q] = lane < total ? inst_grad[(int64_t)(run0 + lane) * kGradQ + q] : 0.0f;
     for (uint32_t c0 = 0; c0 < total; c0 += 32) {
       const uint32_t e = c0 + lane;
       float x[kGradQ];
-      if (e < total) {
-        const float* src = inst_grad + (int64_t)(run0 + e) * kGradQ;
 #pragma unroll
-        for (int q = 0; q < kGradQ; ++q) x[q] = src[q];
-      } else {
+      for (int q = 0; q < kGradQ; ++q) x[q] = nx[q];
+      if (c0 + 32 < total) {
+        const uint32_t en = e + 32;
 #pragma unroll
-        for (int q = 0; q < kGradQ; ++q) x[q] = 0.0f;
+        for (int q = 0; q < kGradQ; ++q) nx[q] = en < total ? inst_grad[(int64_t)(run0 + en) * kGradQ + q] : 0.0f;
       }
       // the owner of slot e is the last lane whose segment starts at or before e; its segment
       // starts at lane `head` of this chunk
@@ -559,7 +562,7 @@ __global__ void __launch_bounds__(kVkThreads) vk_bwd_kernel(const uint32_t* __re
 // warp 0 adds the three shares in channel order and finishes the splat.
 constexpr int kSplatBwdThreads = 96;
 
-__global__ void __launch_bounds__(kSplatBwdThreads, 5) splat_bwd_kernel(
+__global__ void __launch_bounds__(kSplatBwdThreads, 6) splat_bwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ sh, const float* __restrict__ opacity, int64_t n, const potr_camera* __restrict__ cams,
     int n_views, const float* __restrict__ vk_res, float* __restrict__ g_means, float* __restrict__ g_log_scales,
