@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(kProjectThreads, 8) project_kernel(const float
 // a culled vk) -- to its own 16-byte array (coalesced whole-sector stores, not a partial
 // rewrite of the record), and touched = the kept count, so that the emission reads one 16-byte
 // word per vk.
-__global__ void __launch_bounds__(256) tile_mask_kernel(const uint2* __restrict__ rect, int64_t n_vk,
+__global__ void __launch_bounds__(256, 5) tile_mask_kernel(const uint2* __restrict__ rect, int64_t n_vk,
                                                         potr_raster_config cfg, const float4* __restrict__ raster,
                                                         uint4* __restrict__ cull, uint32_t* __restrict__ touched) {
   // per warp and lane: {mx, my, A, B}, {C, o, ku, kv}, {pthr, x0 | y0 << 16, w | concave << 31,
