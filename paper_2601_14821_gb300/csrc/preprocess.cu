@@ -254,8 +254,8 @@ __global__ void __launch_bounds__(kProjectThreads, 8) project_kernel(const float
 // rewrite of the record), and touched = the kept count, so that the emission reads one 16-byte
 // word per vk.
 __global__ void __launch_bounds__(256, 5) tile_mask_kernel(const uint2* __restrict__ rect, int64_t n_vk,
-                                                        potr_raster_config cfg, const float4* __restrict__ raster,
-                                                        uint4* __restrict__ cull, uint32_t* __restrict__ touched) {
+                                                           potr_raster_config cfg, const float4* __restrict__ raster,
+                                                           uint4* __restrict__ cull, uint32_t* __restrict__ touched) {
   // per warp and lane: {mx, my, A, B}, {C, o, ku, kv}, {pthr, x0 | y0 << 16, w | concave << 31,
   // first candidate}; 48-byte rows, so 16-byte reads of 8 consecutive rows hit distinct banks
   __shared__ float4 s_par[8][32][3];
