@@ -399,3 +399,45 @@ def test_bounded_wait_times_out_and_reports():
     assert int(status[0].item()) == B.POTR_ERR_TIMEOUT
     fr = build_frame(*mixed_workload(), **CFG16)  # the device is still usable afterwards
     assert fr.instance_count() > 0
+
+
+def test_per_splat_reduce_over_many_views_and_long_runs():
+    """The per-splat reduce against binary64 sums of the device's own instance partials, on a
+    frame of 70 views (the views as one pipelined sequence, past 64) whose splats are large
+    enough (about 6 x 6 tiles each) that a warp's 32 splats hold more than 256 slots in a view,
+    so their runs are staged in several chunks.  dSSE_k(v), dMSE_k and I_k must match those sums
+    within the rounding of binary32 view sums and terms: 1e-6 of the sums of magnitudes."""
+    import torch
+
+    sc = synth.uniform_cube_scene(4000, 77)
+    sc.log_scales = (sc.log_scales + 2.5).astype(np.float32)
+    cams = synth.ring_cameras(70, 3.5, 0.5, (320, 240))
+    fr = build_frame(sc, cams, **CFG16)
+    tg = [np.full((3, c.height, c.width), 0.3, np.float32) for c in cams]
+    res = frame_outputs(fr, pack_targets(fr, tg), images=False)
+    n, nv = sc.n, len(cams)
+    touched = fr.touched.cpu().numpy().view(np.uint32).astype(np.int64)
+    offsets = fr.offsets.cpu().numpy().view(np.uint32).astype(np.int64)
+    P = np.array([c.width * c.height for c in cams], np.float64)
+
+    nz = touched > 0
+
+    def view_sums(x):  # each (view, splat)'s run of slots, summed on its own in binary64
+        out = np.zeros(nv * n)
+        out[nz] = np.add.reduceat(x.astype(np.float64), offsets[nz])  # runs are contiguous, in vk order
+        return out.reshape(nv, n)
+
+    s_d, a_d = view_sums(res["inst_dse"]), view_sums(np.abs(res["inst_dse"]))
+    s_i, a_i = view_sums(res["inst_imp"]), view_sums(np.abs(res["inst_imp"]))
+    runs = np.add.reduceat(touched.reshape(nv, n), np.arange(0, n, 32), axis=1)
+    assert runs.max() > 256 and (runs > 256).sum() > 100  # many warps stage more than one chunk
+    assert np.count_nonzero(s_d) > 0.2 * s_d.size  # large splats hide many others
+    err = np.abs(res["dsse_view"].reshape(nv, n) - s_d)
+    assert np.all(err <= 1e-6 * a_d), float(np.max(err - 1e-6 * a_d))
+    w = 1.0 / (P[:, None] * nv)
+    want_d, mag_d = (s_d * w / 3.0).sum(axis=0), (a_d * w / 3.0).sum(axis=0)
+    want_i, mag_i = (s_i * w).sum(axis=0), (a_i * w).sum(axis=0)
+    assert np.all(np.abs(res["dmse"] - want_d) <= 1e-6 * mag_d)
+    assert np.all(np.abs(res["importance"] - want_i) <= 1e-6 * mag_i)
+    del fr
+    torch.cuda.empty_cache()
