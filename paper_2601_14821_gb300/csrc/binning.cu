@@ -46,9 +46,24 @@ __global__ void __launch_bounds__(256) depth_key_kernel(const uint32_t* __restri
     if (h[p][threadIdx.x]) atomicAdd(&ghist[p * 256 + threadIdx.x], h[p][threadIdx.x]);
 }
 
+// Kept-tile count of every group of 32 consecutive entries of the depth-sorted vk order (one
+// warp per group: the counts gathered from touched and added by a warp reduction).
+__global__ void __launch_bounds__(256) group_count_kernel(const uint32_t* __restrict__ order,
+                                                          const uint32_t* __restrict__ touched, int64_t n_vk,
+                                                          uint32_t* __restrict__ gcount) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps_total = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t wv = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wv * 32 < n_vk; wv += warps_total) {
+    const int64_t i = wv * 32 + lane;
+    const uint32_t c = i < n_vk ? touched[order[i]] : 0u;
+    const uint32_t sum = __reduce_add_sync(0xffffffffu, c);  // a count is below 2^21
+    if (lane == 0) gcount[wv] = sum;
+  }
+}
+
 // Emission in depth order.  One warp per 32 consecutive entries of the depth-sorted vk order;
-// their emission slots form one contiguous run (eoff is the exclusive prefix of the kept-tile
-// counts in that order), so lane l takes slots l, l + 32, ... of the run, finds the owning
+// their emission slots form one contiguous run, which starts at gbase[group] (the exclusive
+// prefix of the groups' kept-tile counts), so lane l takes slots l, l + 32, ... of the run, finds the owning
 // entry by a 5-step shuffle search over the warp's exclusive counts, and derives the tile
 // from the slot's rank among that vk's kept tiles (row-major in its rectangle, through the
 // kept-tile mask).  Stores are coalesced whatever the rectangle sizes.  Each instance gets key
@@ -57,7 +72,7 @@ __global__ void __launch_bounds__(256) depth_key_kernel(const uint32_t* __restri
 // and rectangle width | all-kept flag << 11 | view tiles_x << 12.  The tile digits of every
 // partition pass are counted here in shared memory: one add per warp when the warp's 32 keys
 // share the digit (the usual case above the lowest byte), else one add per lane.
-__global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ eoff,
+__global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ gbase,
                                                    const potr_view_info* __restrict__ info, int64_t n, int64_t n_vk,
                                                    const uint64_t* __restrict__ m_eff,
                                                    const uint4* __restrict__ cull, uint32_t* __restrict__ keys,
@@ -70,10 +85,9 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
   const int64_t warps_total = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t wv = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wv * 32 < n_vk; wv += warps_total) {
     const int64_t i = wv * 32 + lane;
-    uint32_t vk = 0, cnt = 0, off = 0, corner = 0, pk = 1u, m_lo = 0, m_hi = 0;
+    uint32_t vk = 0, cnt = 0, corner = 0, pk = 1u, m_lo = 0, m_hi = 0;
     if (i < n_vk) {
       vk = order[i];
-      off = eoff[i];
       // culling word: kept-tile mask, rectangle word, kept count | all-kept << 31
       const uint4 m = cull[vk];
       cnt = m.w & 0x7fffffffu;
@@ -96,8 +110,7 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
     const uint32_t excl = incl - cnt;
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
     if (total == 0) continue;
-    const uint32_t first_lane = __ffs(__ballot_sync(0xffffffffu, cnt != 0)) - 1;
-    const uint32_t run0 = __shfl_sync(0xffffffffu, off, first_lane);
+    const uint32_t run0 = gbase[wv];  // below the capacity when m_eff is not 0
     for (uint32_t e0 = 0; e0 < total; e0 += 32) {
       const uint32_t e = e0 + lane;
       // owner: the last lane whose exclusive count is <= e (lanes with cnt = 0 never win ties
@@ -238,7 +251,7 @@ extern "C" size_t potr_bin_sort_workspace_size(int64_t n, int32_t n_views, int64
 //   1. exclusive scan of the kept-tile counts in vk order -> offsets (emission slots of the
 //      vk-order definition, in views->offsets) and the instance total;
 //   2. a stable LSD radix sort (4 x 8-bit passes) of the vk by depth bits: ties keep vk order;
-//   3. emission in that depth order (slots from a second scan of the counts, in depth order),
+//   3. emission in that depth order (slots from a scan of the counts of its groups of 32 entries),
 //      key = global tile, value = vk;
 //   4. a stable LSD radix sort of the instances by tile (8-bit passes over its significant
 //      bits).  Per tile the instances keep step 3's order, (depth bits, vk), which is the
@@ -309,8 +322,17 @@ extern "C" potr_status potr_bin_sort(const potr_views* views, const potr_frame* 
   }
   const uint32_t* order = va;  // dv0: vk in (depth bits, vk) order
 
-  // 3. slots in depth order (dv1 is free now), emission
-  if (scan_exclusive<uint32_t, uint32_t>(views->touched, dv1, L.n_vk, total + 1, scan_ws, s, order) != cudaSuccess)
+  // 3. slots in depth order: counts of the groups of 32 entries, their exclusive scan (dv1 is free
+  // now: the counts in its first half, the scan in its second), then the emission
+  const int64_t n_groups = ceil_div(L.n_vk, 32);
+  uint32_t* gcount = dv1;
+  uint32_t* group_base = dv1 + n_groups;
+  {
+    const int64_t g = ceil_div(L.n_vk, 256);
+    group_count_kernel<<<(unsigned)(g < 152 * 16 ? g : 152 * 16), 256, 0, s>>>(order, views->touched, L.n_vk, gcount);
+    POTR_CHECK_LAUNCH();
+  }
+  if (scan_exclusive<uint32_t, uint32_t>(gcount, group_base, n_groups, total + 1, scan_ws, s) != cudaSuccess)
     return POTR_ERR_CUDA;
   // emit where the last tile pass lands in d_tiles / d_vals
   uint32_t* k_src = (tile_passes & 1) ? keys_alt : d_tiles;
@@ -320,7 +342,7 @@ extern "C" potr_status potr_bin_sort(const potr_views* views, const potr_frame* 
   {
     const int64_t g = ceil_div(L.n_vk, 256);
     emit_kernel<<<(unsigned)(g < 152 * 16 ? g : 152 * 16), 256, 0, s>>>(
-        order, dv1, frame->info, n, L.n_vk, m_eff, reinterpret_cast<const uint4*>(views->cull), k_src, v_src,
+        order, group_base, frame->info, n, L.n_vk, m_eff, reinterpret_cast<const uint4*>(views->cull), k_src, v_src,
         tile_passes, ghist + 256 * 4);
     POTR_CHECK_LAUNCH();
     digit_base_kernel<<<1, 256, 0, s>>>(ghist + 256 * 4, tile_passes, gbase + 256 * 4);
