@@ -341,7 +341,7 @@ extern "C" potr_status potr_bin_sort(const potr_views* views, const potr_frame* 
   uint32_t* v_dst = (tile_passes & 1) ? d_vals : vals_alt;
   {
     const int64_t g = ceil_div(L.n_vk, 256);
-    emit_kernel<<<(unsigned)(g < 152 * 16 ? g : 152 * 16), 256, 0, s>>>(
+    emit_kernel<<<(unsigned)(g < 152 * 32 ? g : 152 * 32), 256, 0, s>>>(
         order, group_base, frame->info, n, L.n_vk, m_eff, reinterpret_cast<const uint4*>(views->cull), k_src, v_src,
         tile_passes, ghist + 256 * 4);
     POTR_CHECK_LAUNCH();
