@@ -1,5 +1,5 @@
 // scan.cuh -- exclusive prefix sums on the device: a two-level reduce-then-scan (no waiting
-// between blocks), with an optional gather of the inputs.  Shared by the binning and the codec.
+// between blocks).  Shared by the binning and the codec.
 #pragma once
 
 #include "potr_device.cuh"
@@ -18,8 +18,8 @@ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // lane l holding items l + 32 j (j = 0..7): loads and stores are coalesced.
 // -----------------------------------------------------------------------------------------
 template <typename Tin, typename Tacc, typename Tout>
-__global__ void __launch_bounds__(kScanThreads) scan_chunks_kernel(const Tin* in, const uint32_t* __restrict__ gather,
-                                                                   Tout* out, int64_t n, Tacc* __restrict__ chunk_sums) {
+__global__ void __launch_bounds__(kScanThreads) scan_chunks_kernel(const Tin* in, Tout* out, int64_t n,
+                                                                   Tacc* __restrict__ chunk_sums) {
   __shared__ Tacc warp_tot[kScanThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)warp * 256;
@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_chunks_kernel(const Tin* in
 #pragma unroll
   for (int j = 0; j < kScanItems; ++j) {
     const int64_t i = base + lane + 32 * j;
-    v[j] = (i < n) ? (Tacc)in[gather ? (int64_t)gather[i] : i] : (Tacc)0;
+    v[j] = (i < n) ? (Tacc)in[i] : (Tacc)0;
   }
   Tacc carry = 0;
 #pragma unroll
@@ -81,14 +81,13 @@ int64_t scan_ws_words(int64_t n) {
   return w + 1;
 }
 
-// Exclusive scan of x_i = in[i] (or in[gather[i]]) for i in [0, n) -> out, total (u64) ->
-// *total.  ws: scan_ws_words(n) u64 words.
+// Exclusive scan of x_i = in[i] for i in [0, n) -> out, total (u64) -> *total.  ws:
+// scan_ws_words(n) u64 words.
 template <typename Tin, typename Tout>
-cudaError_t scan_exclusive(const Tin* in, Tout* out, int64_t n, uint64_t* total, uint64_t* ws, cudaStream_t s,
-                           const uint32_t* gather = nullptr) {
+cudaError_t scan_exclusive(const Tin* in, Tout* out, int64_t n, uint64_t* total, uint64_t* ws, cudaStream_t s) {
   const int64_t nb = ceil_div(n, kScanChunk);
   uint64_t* sums = ws;
-  scan_chunks_kernel<Tin, uint64_t, Tout><<<(unsigned)nb, kScanThreads, 0, s>>>(in, gather, out, n, sums);
+  scan_chunks_kernel<Tin, uint64_t, Tout><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, sums);
   note_launches(2);  // this level's scan plus the store or the add below
   if (nb == 1) {
     store_total_kernel<<<1, 1, 0, s>>>(sums, total);
