@@ -15,7 +15,8 @@ C = "oracle/potr_oracle.c"
 
 MUT = [
     # removal effect
-    ("pd_mul", C, "(PK - P[3 * (i + 1) + ch]) / (1.0 - a)", "(PK - P[3 * (i + 1) + ch]) * (1.0 - a)"),
+    ("pd_mul", C, "(PK - P[3 * (i + 1) + ch]) / (1.0 - a)) - PK;\n          dse +=",
+     "(PK - P[3 * (i + 1) + ch]) * (1.0 - a)) - PK;\n          dse +="),
     ("dse_factor", C, "dse += pd * pd + 2.0 * pd * diff[ch];", "dse += pd * pd + pd * diff[ch];"),
     ("dse_sign", C, "dse += pd * pd + 2.0 * pd * diff[ch];", "dse += pd * pd - 2.0 * pd * diff[ch];"),
     ("imp_alpha", C, "double w = Tv[i] * a;", "double w = a;"),
